@@ -1,0 +1,29 @@
+"""FP64 CPU oracle for the BRAS mass-inverse approximation (test infrastructure only).
+
+This package is the slow, plain reference that the CUDA path is checked against.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg of
+``bench.py`` may import it; the product path never does.  It shares no code with the
+CUDA library: the only common input is the seeded generator
+``paper_2607_12138_b300.meshgen``, which holds none of the method's arithmetic.
+
+Modules
+-------
+``polynomials``  dense monomial polynomials and exact simplex integrals.
+``elements``     reference Lagrange / Nedelec (first kind) / Raviart-Thomas elements by
+                 monomial spans dualised against the documented dof functionals.
+``assembly``     Piola metrics (Sec. 2.4, Eq. piola_mass_pullbacks), element matrices,
+                 assembled M (Eq. M_PMbrP), multiplicity D, explicit BRAS
+                 (Eq. mhatinvbras_def), Jacobi diag(M).
+``solvers``      textbook PCG with the paper's stopping rule (Sec. 3), damped
+                 fixed point, dense spectral tools (Eq. spectral-kappa).
+``gradient``     adjoint gradient of the density-weighted mass solve.
+``sampled``      one-dof-at-a-time BRAS / mass outputs for meshes too large to assemble.
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test against a
+closed form, a theorem of the paper, a value printed in the paper, or brute force.
+The Lagrange elements of order 3-4 and the Nedelec / Raviart-Thomas elements of order
+2-3 use this project's documented node / moment convention, which differs from the
+paper's (GLL nodes, Firedrake moments): their kappa values are unpinned against the
+paper's tables, while the theorems (SPD, lambda_min >= 1, one-element exactness,
+Lemma bras_exact_inverse_correction, Theorem bras_lambda_max_projector) pin them.
+"""

@@ -1,0 +1,158 @@
+"""Pins of the oracle's reference elements against closed forms and conformity.
+
+* P1 element mass = |K| (1 + delta_ij) / ((d+1)(d+2))  (closed form).
+* Lagrange partition of unity and polynomial reproduction (definition of the nodal basis).
+* N1curl_1 = Whitney edge forms, RT_1 = Whitney face forms: element mass matrices from
+  the closed form int_K lambda_i lambda_j = |K| (1 + delta_ij) / 20, on a random tetrahedron
+  (this also pins the covariant / contravariant Piola metrics, Eq. piola_mass_pullbacks).
+* Conformity: on two tetrahedra sharing a face, a random global coefficient vector gives
+  a field whose value (H1), tangential part (H(curl)) or normal part (H(div)) agrees from
+  both sides of the shared face -- this pins the dof functionals, the signs and the
+  generator's dof numbering together.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import assembly, elements
+from oracle.polynomials import monomials, eval_monomials
+from paper_2607_12138_b300 import meshgen as mg
+
+
+def _rand_tet(seed):
+    return mg.single_simplex_mesh(3, seed=seed, jitter=0.25)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p1_closed_form(dim):
+    mesh = mg.single_simplex_mesh(dim, seed=3)
+    Me = assembly.element_matrices(mesh.coords, mesh.cells, "h1", 1)[0]
+    J = assembly.jacobians(mesh.coords, mesh.cells)[0]
+    vol = abs(np.linalg.det(J)) / math.factorial(dim)
+    ref = vol / ((dim + 1) * (dim + 2)) * (np.ones((dim + 1, dim + 1)) + np.eye(dim + 1))
+    np.testing.assert_allclose(Me, ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3), (3, 4)])
+def test_lagrange_partition_of_unity_and_reproduction(dim, p):
+    e = elements.lagrange(dim, p)
+    rng = np.random.default_rng(0)
+    pts = rng.dirichlet(np.ones(dim + 1), size=50)[:, 1:]
+    vals = e.evaluate(pts)[:, :, 0]
+    np.testing.assert_allclose(vals.sum(axis=1), 1.0, atol=1e-12)
+    # a random polynomial of degree p equals its interpolant
+    coef = rng.standard_normal(len(monomials(dim, p)))
+    nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
+    V = np.vstack([np.zeros(dim), np.eye(dim)])
+    npts = np.array([np.asarray(a, float) @ V / p for a in nodes])
+    f_nodes = eval_monomials(dim, p, npts) @ coef
+    f_pts = eval_monomials(dim, p, pts) @ coef
+    np.testing.assert_allclose(vals @ f_nodes, f_pts, atol=1e-11)
+    # integral of 1 = |K_ref| = 1/d!
+    assert abs(e.mass_blocks()[0, 0].sum() - 1 / math.factorial(dim)) < 1e-12
+
+
+def _bary_grads(J):
+    Jinv = np.linalg.inv(J)
+    return np.vstack([-Jinv.sum(axis=0), Jinv])          # row i = grad lambda_i
+
+
+def _lamlam(vol):
+    return vol * (np.ones((4, 4)) + np.eye(4)) / 20.0
+
+
+def test_whitney_edge_forms():
+    mesh = _rand_tet(7)
+    J = assembly.jacobians(mesh.coords, mesh.cells)[0]
+    vol = abs(np.linalg.det(J)) / 6
+    g = _bary_grads(J)
+    LL = _lamlam(vol)
+    E = elements.EDGES_3D
+    W = np.zeros((6, 6))
+    for i, (a, b) in enumerate(E):
+        for j, (c, d) in enumerate(E):
+            W[i, j] = (LL[a, c] * g[b] @ g[d] - LL[a, d] * g[b] @ g[c]
+                       - LL[b, c] * g[a] @ g[d] + LL[b, d] * g[a] @ g[c])
+    Me = assembly.element_matrices(mesh.coords, mesh.cells, "hcurl", 1)[0]
+    np.testing.assert_allclose(Me, W, rtol=1e-12, atol=1e-15)
+
+
+def test_whitney_face_forms():
+    mesh = _rand_tet(11)
+    J = assembly.jacobians(mesh.coords, mesh.cells)[0]
+    vol = abs(np.linalg.det(J)) / 6
+    g = _bary_grads(J)
+    LL = _lamlam(vol)
+    F = elements.FACES_3D
+
+    def terms(a, b, c):   # w = 2 sum_cyc lambda_a grad b x grad c
+        return [(a, 2 * np.cross(g[b], g[c])), (b, 2 * np.cross(g[c], g[a])), (c, 2 * np.cross(g[a], g[b]))]
+
+    W = np.zeros((4, 4))
+    for i, f in enumerate(F):
+        for j, h in enumerate(F):
+            W[i, j] = sum(LL[p, q] * u @ v for p, u in terms(*f) for q, v in terms(*h))
+    Me = assembly.element_matrices(mesh.coords, mesh.cells, "hdiv", 1)[0]
+    S = np.sign(Me[0] / W[0])
+    np.testing.assert_allclose(Me, S[:, None] * W * S[None, :], rtol=1e-12, atol=1e-15)
+
+
+def _two_tets(seed, sort=True):
+    rng = np.random.default_rng(seed)
+    coords = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1.0]]) + rng.uniform(-0.15, 0.15, (5, 3))
+    cells = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], dtype=np.int32)
+    if not sort:
+        cells = np.array([[2, 0, 3, 1], [4, 3, 1, 2]], dtype=np.int32)
+    return mg.Mesh(coords, cells, 3)
+
+
+def _field(mesh, space, order, l2g, signs, coef, k, x):
+    ref = elements.reference_element(space, 3, order)
+    X = mesh.coords[mesh.cells[k]]
+    J = (X[1:] - X[0]).T
+    xh = np.linalg.solve(J, (x - X[0]).T).T
+    s = np.ones(l2g.shape[1]) if signs is None else signs[k].astype(float)
+    vals = ref.evaluate(xh)                             # [pts, n_loc, comp]
+    loc = s * coef[l2g[k]]
+    u = np.einsum("pnc,n->pc", vals, loc)
+    if space == "hcurl":
+        return u @ np.linalg.inv(J)                     # J^{-T} u (row vectors)
+    if space == "hdiv":
+        return u @ J.T / np.linalg.det(J)
+    return u
+
+
+@pytest.mark.parametrize("space,order,sort", [
+    ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False),
+    ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True),
+    ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True),
+    ("hcurl", 2, False)])
+def test_conformity_across_shared_face(space, order, sort):
+    if space == "hcurl" and order == 2 and not sort:
+        with pytest.raises(ValueError):
+            mg.dof_map(_two_tets(0, sort), space, order)
+        return
+    mesh = _two_tets(5, sort)
+    n, l2g, signs = mg.dof_map(mesh, space, order)
+    shared = sorted(set(mesh.cells[0]) & set(mesh.cells[1]))
+    V = mesh.coords[shared]
+    rng = np.random.default_rng(1)
+    bc = rng.dirichlet(np.ones(3), size=20)
+    x = bc @ V
+    nrm = np.cross(V[1] - V[0], V[2] - V[0])
+    nrm /= np.linalg.norm(nrm)
+    for trial in range(3):
+        coef = rng.standard_normal(n)
+        u0 = _field(mesh, space, order, l2g, signs, coef, 0, x)
+        u1 = _field(mesh, space, order, l2g, signs, coef, 1, x)
+        if space == "h1":
+            np.testing.assert_allclose(u0, u1, atol=1e-10)
+        elif space == "hcurl":
+            t0 = u0 - np.outer(u0 @ nrm, nrm)
+            t1 = u1 - np.outer(u1 @ nrm, nrm)
+            np.testing.assert_allclose(t0, t1, atol=1e-10)
+            assert np.abs(u0 - u1).max() > 1e-6        # normal part is free to jump
+        else:
+            np.testing.assert_allclose(u0 @ nrm, u1 @ nrm, atol=1e-10)

@@ -1,0 +1,112 @@
+"""Pins of the oracle's PCG, fixed point, gradient and sampled outputs.
+
+* PCG against a dense direct solve (textbook CG reaches the exact solution);
+* CG iteration counts against Tables 1-3 (lowest order, uniform meshes, random RHS,
+  stop at 1e-10, Sec. 3), +-1 since our meshes are smaller than the paper's 1e6 dofs;
+* the Chebyshev bound 2((sqrt k - 1)/(sqrt k + 1))^k of Sec. 3 on the A-norm error;
+* damped fixed point with omega = 2 / (1 + lambda_max) (Sec. 3) converges;
+* adjoint gradient of the weighted solve against central differences and the closed
+  form for a uniform density scale (x(c rho) = x / c);
+* one-dof-at-a-time outputs against the assembled operators.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import gradient, sampled
+from oracle.assembly import Problem, element_matrices
+from oracle.solvers import fixed_point, kappa_hat, pcg, pencil_eigs
+from paper_2607_12138_b300 import meshgen as mg
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def _problem(mesh, space, order, rho=None):
+    n, l2g, s = mg.dof_map(mesh, space, order)
+    return Problem(mesh, space, order, l2g, s, n, rho)
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi", "bras"])
+def test_pcg_matches_dense_solve(pc):
+    pr = _problem(mg.unit_cube_mesh(3, jitter=0.15), "h1", 2)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    pre = {"none": None, "jacobi": pr.jacobi_apply, "bras": pr.bras_apply}[pc]
+    x, its, hist = pcg(pr.mass_apply, b, pre, rtol=1e-12)
+    xd = np.linalg.solve(pr.M.toarray(), b)
+    assert hist[-1] <= 1e-12
+    np.testing.assert_allclose(x, xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+
+
+ITS_MESHES = {
+    "h1_2d_p1": (lambda: mg.unit_square_mesh(160), "h1", 1),
+    "h1_2d_p2": (lambda: mg.unit_square_mesh(96), "h1", 2),
+    "h1_3d_p1": (lambda: mg.unit_cube_mesh(20), "h1", 1),
+    "h1_3d_p2": (lambda: mg.unit_cube_mesh(12), "h1", 2),
+    "hcurl_3d_k1": (lambda: mg.unit_cube_mesh(14), "hcurl", 1),
+    "hdiv_3d_k1": (lambda: mg.unit_cube_mesh(16), "hdiv", 1),
+}
+
+
+@pytest.mark.parametrize("key", sorted(ITS_MESHES))
+def test_cg_iterations_match_paper(key):
+    make, space, order = ITS_MESHES[key]
+    pr = _problem(make(), space, order)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    _, itd, _ = pcg(pr.mass_apply, b, pr.jacobi_apply, rtol=1e-10)
+    _, itb, _ = pcg(pr.mass_apply, b, pr.bras_apply, rtol=1e-10)
+    gold = GOLD["cg_iterations"][key]
+    assert abs(itd - gold["diag"]) <= 1 and abs(itb - gold["bras"]) <= 1, (key, itd, itb, gold)
+
+
+def test_chebyshev_bound_and_fixed_point():
+    pr = _problem(mg.unit_square_mesh(12, jitter=0.2), "h1", 2)
+    M = pr.M.toarray()
+    B = pr.B.toarray()
+    kap = kappa_hat(M, B)
+    b = mg.rhs(pr.n_dof, 1, seed=2)
+    xs = np.linalg.solve(M, b)
+    rate = (np.sqrt(kap) - 1) / (np.sqrt(kap) + 1)
+    for k in range(1, 12):
+        x, _, _ = pcg(pr.mass_apply, b, pr.bras_apply, max_its=k)
+        e, e0 = x - xs, xs
+        assert np.sqrt(e @ M @ e) <= 2 * rate ** k * np.sqrt(e0 @ M @ e0) * (1 + 1e-9)
+    lam_max = pencil_eigs(M, B)[-1]
+    u, its = fixed_point(pr.mass_apply, b, pr.bras_apply, 2.0 / (1.0 + lam_max), rtol=1e-10)
+    assert its < 5000 and np.linalg.norm(b - M @ u) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_gradient_central_differences():
+    mesh = mg.unit_cube_mesh(2, jitter=0.1)
+    n, l2g, s = mg.dof_map(mesh, "h1", 3)
+    rng = np.random.default_rng(2)
+    z = rng.normal(0, 0.5, mesh.n_cell)
+    b = mg.rhs(n, 1, seed=1)
+    xs = mg.rhs(n, 1, seed=3)
+    L, bbar, zbar, x = gradient.loss_and_grad(mesh, "h1", 3, l2g, s, n, z, b, xs)
+    h = 1e-6
+    for trial in range(4):
+        v = rng.standard_normal(mesh.n_cell)
+        Lp = gradient.loss_and_grad(mesh, "h1", 3, l2g, s, n, z + h * v, b, xs)[0]
+        Lm = gradient.loss_and_grad(mesh, "h1", 3, l2g, s, n, z - h * v, b, xs)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - zbar @ v) <= 1e-6 * max(1.0, abs(fd))
+        Lp = gradient.loss_and_grad(mesh, "h1", 3, l2g, s, n, z, b + h * v[:1] * xs, xs)[0]
+        Lm = gradient.loss_and_grad(mesh, "h1", 3, l2g, s, n, z, b - h * v[:1] * xs, xs)[0]
+        assert abs((Lp - Lm) / (2 * h) - v[0] * (bbar @ xs)) <= 1e-6 * max(1.0, abs(bbar @ xs))
+    # uniform scale: d/dc L(x(c rho)) at c = 1 is -x.(x - x*)
+    assert abs(zbar.sum() - (-(x @ (x - xs)))) <= 1e-9 * abs(x @ (x - xs))
+
+
+@pytest.mark.parametrize("space,order", [("h1", 3), ("hcurl", 2), ("hdiv", 1)])
+def test_sampled_outputs_match_assembled(space, order):
+    mesh = mg.unit_cube_mesh(3, jitter=0.15)
+    pr = _problem(mesh, space, order)
+    x = mg.rhs(pr.n_dof, 1, seed=5)
+    dofs = np.random.default_rng(0).choice(pr.n_dof, 25, replace=False)
+    yb = sampled.bras_apply_at(mesh, space, order, pr.l2g, pr.signs, pr.n_dof, x, dofs)
+    ym = sampled.mass_apply_at(mesh, space, order, pr.l2g, pr.signs, pr.n_dof, x, dofs)
+    np.testing.assert_allclose(yb, (pr.B @ x)[dofs], rtol=1e-12, atol=1e-12 * np.abs(pr.B @ x).max())
+    np.testing.assert_allclose(ym, (pr.M @ x)[dofs], rtol=1e-12, atol=1e-12 * np.abs(pr.M @ x).max())
