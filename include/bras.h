@@ -1,0 +1,180 @@
+/*
+ * bras.h -- C ABI of the B300 BRAS mass-solve library (libbras.so).
+ *
+ * The library applies, on one GPU, the broken-space additive Schwarz (BRAS) approximation
+ * of a conforming finite-element mass inverse,
+ *
+ *     M_bras^{-1} = D^{-1} P^T M_br^{-1} P D^{-1} = D^{-1} (sum_K P_K^T M_K^{-1} P_K) D^{-1}
+ *
+ * (Sec. 2.2, Eq. mhatinvbras_def and its element-sum form), together with the conforming
+ * mass matrix M = P^T M_br P = sum_K P_K^T M_K P_K (Sec. 2.2, Eq. M_PMbrP), the diagonal
+ * approximation diag(M)^{-1} (Sec. 2.1) and a preconditioned-CG mass solve with the
+ * paper's stopping rule ||r_k||_2 / ||r_0||_2 <= rtol, u_0 = 0 (Sec. 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * Pointers are DEVICE pointers unless a call says otherwise; the caller owns them.
+ *    The context owns every table it builds, until bras_destroy.
+ *  * Calls are ordered on the CUDA stream passed as `stream` (a cudaStream_t, may be
+ *    NULL for the legacy default stream).  Apply calls are asynchronous; bras_setup and
+ *    bras_pcg_solve synchronise the stream before they return.
+ *  * Vectors with nrhs > 1 right-hand sides are RHS-interleaved: entry (i, r) is at
+ *    i * nrhs + r.  Dof i is the global dof number used in `l2g`.
+ *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange P_p on triangles (dim 2) or tetrahedra
+ *    (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind of order k = 1..3 and BRAS_HDIV =
+ *    Raviart-Thomas of order k = 1..3, on tetrahedra, mapped by the covariant /
+ *    contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with |det J|.
+ *    Local dof order and dof functionals are the ones documented with the mesh
+ *    generator and the reference elements (vertices of each cell listed in ascending
+ *    global id for face moments of order >= 2).
+ *  * Return codes: 0 = success, > 0 = non-fatal status, < 0 = error (nothing written
+ *    to the outputs except where stated).  No call prints, throws or exits.
+ *    bras_status_string() names a code; bras_last_error_detail() gives the element or
+ *    dof index that caused the last error of this thread (-1 if none).
+ *  * Determinism: every reduction (scatter-average, dot products) runs in a fixed order
+ *    with no floating-point atomics, so two calls with the same inputs give bit-identical
+ *    outputs.
+ */
+#ifndef BRAS_H
+#define BRAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bras_ctx bras_ctx;
+
+enum { BRAS_H1 = 0, BRAS_HCURL = 1, BRAS_HDIV = 2 };
+
+/* Precision of an apply (the element data it streams and the arithmetic it runs in).
+ * BRAS_FP64: double vectors, double element data, double arithmetic.
+ * BRAS_FP32: float vectors, float element data, float arithmetic.
+ * BRAS_BF16: float vectors and arithmetic; H(curl)/H(div) local inverses stored in
+ *            bfloat16 (H1 has no per-element matrix: same as BRAS_FP32 there).       */
+enum { BRAS_FP64 = 0, BRAS_FP32 = 1, BRAS_BF16 = 2 };
+
+/* Preconditioner of a solve: none, diag(M)^{-1} (Jacobi), or BRAS. */
+enum { BRAS_PC_NONE = 0, BRAS_PC_JACOBI = 1, BRAS_PC_BRAS = 2 };
+
+/* Solve modes: plain FP64 PCG, or FP32 inner PCG (FP64 dot products and scalars)
+ * inside an FP64 iterative-refinement loop r = b - M x, x += d. */
+enum { BRAS_SOLVE_FP64 = 0, BRAS_SOLVE_MIXED = 1 };
+
+enum {
+    BRAS_OK = 0,
+    BRAS_NOT_CONVERGED = 1,       /* maxit reached; x, iters, relres are still written */
+    BRAS_ERR_INVALID = -1,        /* bad argument (null pointer, size, enum, order)     */
+    BRAS_ERR_L2G_RANGE = -2,      /* l2g entry outside [0, n_dof) (detail = flat index) */
+    BRAS_ERR_NO_COPY = -3,        /* a dof no element references (detail = dof)        */
+    BRAS_ERR_DEGENERATE = -4,     /* det J = 0 (detail = element)                        */
+    BRAS_ERR_NOT_SPD = -5,        /* local Cholesky pivot <= 0 (detail = element)        */
+    BRAS_ERR_CUDA = -6,           /* a CUDA call failed                                  */
+    BRAS_ERR_OOM = -7,            /* device or host allocation failed                    */
+    BRAS_ERR_BREAKDOWN = -8,      /* CG breakdown: p^T M p <= 0 or not finite            */
+    BRAS_ERR_PRECISION = -9,      /* the context holds no tables for this precision      */
+    BRAS_ERR_TOO_LARGE = -10      /* a size exceeds a documented library limit           */
+};
+
+/* Options of bras_setup.  Zero-initialise, then set what you need. */
+typedef struct {
+    int precisions;      /* bit mask of (1 << BRAS_FP64 | 1 << BRAS_FP32 | 1 << BRAS_BF16);
+                            0 means all three                                           */
+    int block_elems;     /* elements per scatter block, 32..256; 0 = 256                 */
+    int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
+} bras_options;
+
+/*
+ * bras_setup -- build a context for one conforming space on one simplicial mesh.
+ *
+ * Computes, all on the device: J_K, |det J_K| and the Piola metric G_K of every cell
+ * (Sec. 2.4); for H1 the single reference mass M_ref and its inverse (the affine
+ * element inverse is M_K^{-1} = M_ref^{-1} / (rho_K |det J_K|)); for H(curl) and H(div)
+ * every M_K = sum_ab G_K,ab R_ab and its FP64 Cholesky inverse (Sec. 2.2: M_K is SPD);
+ * the multiplicities d_i = #{broken copies of dof i} (D = P^T P); diag(M); and the
+ * deterministic scatter tables.  Not timed in solves (Sec. 3).
+ *
+ *   out      receives the new context (set to NULL on error).
+ *   dim      2 or 3 (2 only with BRAS_H1).
+ *   space    BRAS_H1, BRAS_HCURL or BRAS_HDIV;  order p or k (see above).
+ *   coords   [n_vert * dim] double, vertex coordinates.
+ *   cells    [n_cell * (dim+1)] int32, vertex ids of each simplex.
+ *   l2g      [n_cell * n_loc] int32, local-to-global dof map (the map pi of Sec. 2.2).
+ *   signs    [n_cell * n_loc] int8 in {+1, -1} (signed injection P), or NULL (all +1).
+ *   rho      [n_cell] double > 0 element weights (mass density), or NULL (all 1).
+ *   opt      options or NULL (defaults).
+ * Limits: n_cell, n_dof < 2^31; n_cell * n_loc < 2^31.
+ */
+int bras_setup(bras_ctx** out, int dim, int space, int order,
+               int64_t n_vert, const double* coords,
+               int64_t n_cell, const int32_t* cells,
+               int64_t n_dof, const int32_t* l2g, const int8_t* signs,
+               const double* rho, const bras_options* opt, void* stream);
+
+/* Number of local dofs per cell for (dim, space, order), or -1 if unsupported. */
+int bras_n_local(int dim, int space, int order);
+
+/* bras_mass_apply -- y = M x  (Eq. M_PMbrP, element by element).
+ * x, y: [n_dof * nrhs] of double (BRAS_FP64) or float (BRAS_FP32 / BRAS_BF16); x and y
+ * must not overlap.  nrhs >= 1. */
+int bras_mass_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
+                    void* stream);
+
+/* bras_apply -- y = M_bras^{-1} x = D^{-1} P^T M_br^{-1} P D^{-1} x  (Eq. mhatinvbras_def):
+ * signed gather with D^{-1}, exact element-local inverse, multiplicity-weighted scatter.
+ * Same argument rules as bras_mass_apply. */
+int bras_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
+               void* stream);
+
+/* bras_jacobi_apply -- y = diag(M)^{-1} x  (Sec. 2.1).  Same argument rules. */
+int bras_jacobi_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
+                      void* stream);
+
+/*
+ * bras_pcg_solve -- solve M x = b by preconditioned CG (Sec. 3): u_0 = 0, stop when
+ * ||r_k||_2 / ||r_0||_2 <= rtol for every right-hand side, or after maxit iterations.
+ *   pc     BRAS_PC_NONE, BRAS_PC_JACOBI or BRAS_PC_BRAS.
+ *   mode   BRAS_SOLVE_FP64: FP64 PCG, recurrence residual tested.
+ *          BRAS_SOLVE_MIXED: FP32 (or BF16-inverse, if inner_precision = BRAS_BF16) inner
+ *          PCG with FP64 dot products and scalars inside an FP64 refinement loop; the
+ *          TRUE residual ||b - M x|| (FP64) is tested.
+ *   inner_precision  BRAS_FP32 or BRAS_BF16 (mixed mode only; ignored in FP64 mode).
+ *   b, x   [n_dof * nrhs] double; host OR device pointers (both on the same side).  With
+ *          host pointers the copies in and out are part of the call.
+ *   iters  [nrhs] int, host: CG iterations (mixed mode: total inner iterations).
+ *   relres [nrhs] double, host: final ||r|| / ||b|| (recurrence residual in FP64 mode,
+ *          true residual in mixed mode).
+ * Returns BRAS_OK, BRAS_NOT_CONVERGED, or an error.  Synchronises `stream`.
+ */
+int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision,
+                   const double* b, double* x, int nrhs, double rtol, int maxit,
+                   int* iters, double* relres, void* stream);
+
+/* bras_grad_rho -- rho_bar_K = -lambda_K^T M_K^1 x_K for the weighted mass M(rho) =
+ * sum_K rho_K P_K^T M_K^1 P_K (M_K^1 = unit-density element matrix): the element part of
+ * the adjoint gradient of x = M(rho)^{-1} b, with lambda = M^{-1} xbar (H1 only).
+ * x, lam: [n_dof] double; rho_bar: [n_cell] double in the caller's cell order. */
+int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar,
+                  void* stream);
+
+/* bras_update_rho -- replace the element weights (H1 only): rescales the per-element
+ * factors and diag(M) without rebuilding the scatter tables.  rho: [n_cell] double > 0. */
+int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream);
+
+/* Sizes of a context: n_dof, n_cell, n_loc, number of scatter blocks. */
+int bras_info(const bras_ctx* ctx, int64_t* n_dof, int64_t* n_cell, int* n_loc, int* n_blocks);
+
+/* Bytes one apply moves by the algorithmic count: l2g map (4 B per local dof), the
+ * per-element factor (H1) or packed local inverse (H(curl)/H(div)), x read and y written,
+ * and one multiplicity byte per dof (BRAS apply only).  For roofline reporting. */
+int64_t bras_algorithmic_bytes(const bras_ctx* ctx, int precision, int nrhs, int bras);
+
+void bras_destroy(bras_ctx* ctx);
+const char* bras_status_string(int code);
+int64_t bras_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRAS_H */

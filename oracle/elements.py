@@ -2,9 +2,13 @@
 
 Construction, identical for every family:
   1. a spanning set of the polynomial space written in monomial coefficients;
-  2. an orthonormal basis Q of its span (SVD; the rank must equal the known dimension);
+  2. a basis Q of its span (the first linearly independent members, by exact rational
+     elimination; the rank must equal the known dimension);
   3. the dof functionals F as row vectors over the coefficients;
   4. nodal basis Phi = Q (F Q)^{-1}, so that F Phi = I.
+All of this runs in exact rationals and 40-digit mpmath; the reference mass blocks are
+rounded to FP64 once (the FP64 results are then correctly rounded to about 1e-16, which
+keeps the oracle's inverses accurate to cond(M_ref) * 1e-16).
 
 Spaces (reference tetrahedron / triangle with vertices 0, e_1, .., e_d):
   * Lagrange P_p: all monomials of degree <= p; dofs = values at the equispaced nodes
@@ -30,17 +34,22 @@ from __future__ import annotations
 
 import functools
 import itertools
-import math
 from dataclasses import dataclass
+from fractions import Fraction
 
+import mpmath
 import numpy as np
 
 from .polynomials import (gram, integrate_segment, integrate_triangle, monomials,
                           eval_monomials, restrict_to_param, shifted_legendre,
-                          simplex_monomial_integral)
+                          simplex_monomial_integral, to_mpf)
 
 EDGES_3D = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
 FACES_3D = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+
+
+def _np(m: mpmath.matrix) -> np.ndarray:
+    return np.array([[float(m[i, j]) for j in range(m.cols)] for i in range(m.rows)])
 
 
 @dataclass(frozen=True)
@@ -49,46 +58,80 @@ class RefElement:
     dim: int
     order: int
     degree: int         # max polynomial degree of the basis
-    phi: np.ndarray     # [n_comp * n_mono, n_loc] nodal basis coefficients
+    phi_mp: mpmath.matrix   # [n_comp * n_mono, n_loc] nodal basis coefficients
     n_comp: int
 
     @property
     def n_loc(self) -> int:
-        return self.phi.shape[1]
+        return self.phi_mp.cols
+
+    @functools.cached_property
+    def phi(self) -> np.ndarray:
+        return _np(self.phi_mp)
+
+    def _component_mp(self, c: int) -> mpmath.matrix:
+        nm = len(monomials(self.dim, self.degree))
+        return self.phi_mp[c * nm:(c + 1) * nm, :]
 
     def component(self, c: int) -> np.ndarray:
         nm = len(monomials(self.dim, self.degree))
         return self.phi[c * nm:(c + 1) * nm, :]
 
-    def mass_blocks(self) -> np.ndarray:
-        """R[a, b] = int_ref phi^a phi^b^T  (shape [n_comp, n_comp, n_loc, n_loc])."""
+    @functools.cached_property
+    def _mass_blocks(self) -> np.ndarray:
         G = gram(self.dim, self.degree)
         R = np.empty((self.n_comp, self.n_comp, self.n_loc, self.n_loc))
+        comps = [self._component_mp(c) for c in range(self.n_comp)]
         for a in range(self.n_comp):
+            GA = comps[a].T * G
             for b in range(self.n_comp):
-                R[a, b] = self.component(a).T @ G @ self.component(b)
+                R[a, b] = _np(GA * comps[b])
         return R
 
+    def mass_blocks(self) -> np.ndarray:
+        """R[a, b] = int_ref phi^a phi^b^T  (shape [n_comp, n_comp, n_loc, n_loc])."""
+        return self._mass_blocks.copy()
+
     def evaluate(self, pts: np.ndarray) -> np.ndarray:
-        """Reference basis values [n_pts, n_loc, n_comp] at reference points."""
+        """Reference basis values [n_pts, n_loc, n_comp] at reference points (FP64)."""
         V = eval_monomials(self.dim, self.degree, pts)
         return np.stack([V @ self.component(c) for c in range(self.n_comp)], axis=2)
 
 
-def _ref_vertices(d: int) -> np.ndarray:
-    return np.vstack([np.zeros(d), np.eye(d)])
+def _ref_vertices(d: int) -> list[list[int]]:
+    return [[0] * d] + [[1 if i == j else 0 for i in range(d)] for j in range(d)]
 
 
-def _dualise(span: np.ndarray, F: np.ndarray, dim_expected: int) -> np.ndarray:
-    U, s, _ = np.linalg.svd(span, full_matrices=False)
-    rank = int(np.sum(s > 1e-10 * s[0]))
-    if rank != dim_expected:
-        raise AssertionError(f"span rank {rank} != {dim_expected}")
-    Q = U[:, :rank]
-    A = F @ Q
-    if A.shape != (rank, rank):
-        raise AssertionError(f"{A.shape[0]} functionals for a space of dimension {rank}")
-    return Q @ np.linalg.inv(A)
+def _independent_columns(cols: list[list[Fraction]]) -> list[int]:
+    """Indices of the first linearly independent columns (exact Gaussian elimination)."""
+    basis: list[tuple[int, list[Fraction]]] = []       # (pivot row, reduced vector)
+    keep = []
+    for j, v in enumerate(cols):
+        v = list(v)
+        for piv, b in basis:
+            if v[piv] != 0:
+                f = v[piv] / b[piv]
+                v = [x - f * y for x, y in zip(v, b)]
+        nz = next((i for i, x in enumerate(v) if x != 0), None)
+        if nz is not None:
+            basis.append((nz, v))
+            keep.append(j)
+    return keep
+
+
+def _dualise(span: list[list[Fraction]], F: mpmath.matrix, dim_expected: int) -> mpmath.matrix:
+    keep = _independent_columns(span)
+    if len(keep) != dim_expected:
+        raise AssertionError(f"span rank {len(keep)} != {dim_expected}")
+    n_coef = len(span[0])
+    Q = mpmath.matrix(n_coef, len(keep))
+    for jj, j in enumerate(keep):
+        for i in range(n_coef):
+            Q[i, jj] = to_mpf(span[j][i])
+    A = F * Q
+    if A.rows != A.cols:
+        raise AssertionError(f"{A.rows} functionals for a space of dimension {A.cols}")
+    return Q * mpmath.inverse(A)
 
 
 @functools.lru_cache(maxsize=None)
@@ -96,56 +139,50 @@ def lagrange(dim: int, p: int) -> RefElement:
     ms = monomials(dim, p)
     nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
     V = _ref_vertices(dim)
-    pts = np.array([np.asarray(a, dtype=np.float64) @ V / p for a in nodes])
-    F = eval_monomials(dim, p, pts)                      # point evaluations
-    phi = _dualise(np.eye(len(ms)), F, len(ms))
+    F = mpmath.matrix(len(nodes), len(ms))                  # point evaluations (exact nodes)
+    for r, a in enumerate(nodes):
+        pt = [Fraction(sum(a[i] * V[i][c] for i in range(dim + 1)), p) for c in range(dim)]
+        for j, m in enumerate(ms):
+            val = Fraction(1)
+            for c in range(dim):
+                val *= pt[c] ** m[c]
+            F[r, j] = to_mpf(val)
+    eye = [[Fraction(int(i == j)) for i in range(len(ms))] for j in range(len(ms))]
+    phi = _dualise(eye, F, len(ms))
     return RefElement("h1", dim, p, p, phi, 1)
 
 
-def _vec(c: int, j: int, nm: int) -> np.ndarray:
-    v = np.zeros(3 * nm)
-    v[c * nm + j] = 1.0
+def _vec(c: int, j: int, nm: int) -> list[Fraction]:
+    v = [Fraction(0)] * (3 * nm)
+    v[c * nm + j] = Fraction(1)
     return v
 
 
-def _edge_functionals(k: int, nm: int, ms) -> list[np.ndarray]:
+def _edge_functionals(k: int, nm: int, ms) -> list[list]:
     V = _ref_vertices(3)
     rows = []
     for a, b in EDGES_3D:
-        tau = V[b] - V[a]
+        tau = [V[b][c] - V[a][c] for c in range(3)]
+        restricted = [restrict_to_param(m, V[a], [tau]) for m in ms]
         for j in range(k):
-            L = shifted_legendre(j)[:, None]
-            row = np.zeros(3 * nm)
-            for mi, m in enumerate(ms):
-                P = restrict_to_param(m, V[a], [tau])
-                val = integrate_segment(np.convolve(P[:, 0], L[:, 0])[:, None])
+            L = shifted_legendre(j)
+            row = [mpmath.mpf(0)] * (3 * nm)
+            for mi, P in enumerate(restricted):
+                prod = {}
+                for (i, _), cf in P.items():
+                    for l, cl in enumerate(L):
+                        prod[(i + l, 0)] = prod.get((i + l, 0), 0) + cf * cl
+                val = to_mpf(integrate_segment(prod))
                 for c in range(3):
                     row[c * nm + mi] = tau[c] * val
             rows.append(row)
     return rows
 
 
-def _orthonormalise(G: np.ndarray) -> np.ndarray:
+def _orthonormalise(G: mpmath.matrix) -> mpmath.matrix:
     """Rows r of C give q_r = sum_i C[r, i] m_i, orthonormal for the Gram matrix G (Gram-Schmidt
     in the given monomial order, positive leading coefficient): C = L^{-1}, G = L L^T."""
-    L = np.linalg.cholesky(G)
-    return np.linalg.inv(L)
-
-
-def _orthonormal_coeffs_triangle(deg: int) -> np.ndarray:
-    tm = _face_test_monomials(deg)
-    G = np.array([[integrate_triangle(_mono2(a[0] + b[0], a[1] + b[1])) for b in tm] for a in tm])
-    return _orthonormalise(G / 0.5)          # mean inner product on T (area 1/2)
-
-
-def _orthonormal_coeffs_tet(deg: int) -> np.ndarray:
-    return _orthonormalise(gram(3, deg) * 6.0)   # mean inner product on K (volume 1/6)
-
-
-def _mono2(i: int, j: int) -> np.ndarray:
-    P = np.zeros((i + 1, j + 1))
-    P[i, j] = 1.0
-    return P
+    return mpmath.inverse(mpmath.cholesky(G))
 
 
 def _face_test_monomials(deg: int) -> list[tuple[int, int]]:
@@ -153,29 +190,44 @@ def _face_test_monomials(deg: int) -> list[tuple[int, int]]:
     return [(d - j, j) for d in range(deg + 1) for j in range(d + 1)]
 
 
-def _face_functionals(space: str, k: int, nm: int, ms) -> list[np.ndarray]:
+@functools.lru_cache(maxsize=None)
+def _orthonormal_coeffs_triangle(deg: int) -> mpmath.matrix:
+    tm = _face_test_monomials(deg)
+    G = mpmath.matrix(len(tm), len(tm))
+    for i, a in enumerate(tm):
+        for j, b in enumerate(tm):
+            G[i, j] = to_mpf(integrate_triangle({(a[0] + b[0], a[1] + b[1]): Fraction(1)}) * 2)
+    return _orthonormalise(G)            # mean inner product on T (area 1/2)
+
+
+@functools.lru_cache(maxsize=None)
+def _orthonormal_coeffs_tet(deg: int) -> mpmath.matrix:
+    return _orthonormalise(gram(3, deg) * 6)   # mean inner product on K (volume 1/6)
+
+
+def _face_functionals(space: str, k: int, nm: int, ms) -> list[list]:
     V = _ref_vertices(3)
     rows = []
     qdeg = k - 2 if space == "hcurl" else k - 1
     if qdeg < 0:
         return rows
+    tm = _face_test_monomials(qdeg)
+    C = _orthonormal_coeffs_triangle(qdeg)          # q_r = sum_i C[r, i] s^a_i t^b_i
     for a, b, c in FACES_3D:
-        t1, t2 = V[b] - V[a], V[c] - V[a]
-        dirs = [t1, t2] if space == "hcurl" else [np.cross(t1, t2)]
+        t1 = [V[b][i] - V[a][i] for i in range(3)]
+        t2 = [V[c][i] - V[a][i] for i in range(3)]
+        if space == "hcurl":
+            dirs = [t1, t2]
+        else:
+            dirs = [[t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]]]
         restricted = [restrict_to_param(m, V[a], [t1, t2]) for m in ms]
-        tm = _face_test_monomials(qdeg)
-        # ints_mono[i, mi] = int_T m_mi(x(s,t)) s^a t^b ds dt for the i-th face monomial
-        ints_mono = np.zeros((len(tm), nm))
-        for i, (qi, qj) in enumerate(tm):
-            for mi, P in enumerate(restricted):
-                pq = np.zeros((P.shape[0] + qi, P.shape[1] + qj))
-                pq[qi:, qj:] = P
-                ints_mono[i, mi] = integrate_triangle(pq)
-        C = _orthonormal_coeffs_triangle(qdeg)          # q_r = sum_i C[r, i] s^a_i t^b_i
+        # ints_mono[i][mi] = int_T m_mi(x(s,t)) s^a t^b ds dt for the i-th face monomial
+        ints_mono = [[to_mpf(integrate_triangle({(ii + qi, jj + qj): cf for (ii, jj), cf in P.items()}))
+                      for P in restricted] for (qi, qj) in tm]
         for r in range(len(tm)):
-            ints = C[r] @ ints_mono
+            ints = [mpmath.fsum(C[r, i] * ints_mono[i][mi] for i in range(len(tm))) for mi in range(nm)]
             for w in dirs:
-                row = np.zeros(3 * nm)
+                row = [mpmath.mpf(0)] * (3 * nm)
                 for mi in range(nm):
                     for comp in range(3):
                         row[comp * nm + mi] = w[comp] * ints[mi]
@@ -183,18 +235,18 @@ def _face_functionals(space: str, k: int, nm: int, ms) -> list[np.ndarray]:
     return rows
 
 
-def _interior_functionals(qdeg: int, nm: int, ms) -> list[np.ndarray]:
+def _interior_functionals(qdeg: int, nm: int, ms) -> list[list]:
     rows = []
     if qdeg < 0:
         return rows
     qs = monomials(3, qdeg)
     C = _orthonormal_coeffs_tet(qdeg)
-    mono_int = np.array([[simplex_monomial_integral(tuple(x + y for x, y in zip(m, q))) for m in ms]
-                         for q in qs])                    # [n_q, nm]
+    mono_int = [[to_mpf(simplex_monomial_integral(tuple(x + y for x, y in zip(m, q)))) for m in ms]
+                for q in qs]                                  # [n_q][nm]
     for r in range(len(qs)):
-        vals = C[r] @ mono_int
+        vals = [mpmath.fsum(C[r, i] * mono_int[i][mi] for i in range(len(qs))) for mi in range(nm)]
         for comp in range(3):
-            row = np.zeros(3 * nm)
+            row = [mpmath.mpf(0)] * (3 * nm)
             row[comp * nm:(comp + 1) * nm] = vals
             rows.append(row)
     return rows
@@ -202,6 +254,17 @@ def _interior_functionals(qdeg: int, nm: int, ms) -> list[np.ndarray]:
 
 def _homogeneous(deg: int):
     return [m for m in monomials(3, deg) if sum(m) == deg]
+
+
+def _functional_matrix(space: str, k: int) -> mpmath.matrix:
+    ms = monomials(3, k)
+    nm = len(ms)
+    if space == "hcurl":
+        rows = (_edge_functionals(k, nm, ms) + _face_functionals("hcurl", k, nm, ms)
+                + _interior_functionals(k - 3, nm, ms))
+    else:
+        rows = _face_functionals("hdiv", k, nm, ms) + _interior_functionals(k - 2, nm, ms)
+    return mpmath.matrix(rows)
 
 
 @functools.lru_cache(maxsize=None)
@@ -213,9 +276,9 @@ def nedelec1(k: int) -> RefElement:
     for m in _homogeneous(k - 1):
         for c in range(3):
             # x cross (m e_c): components (y w_z - z w_y, z w_x - x w_z, x w_y - y w_x)
-            w = np.zeros(3)
-            w[c] = 1.0
-            v = np.zeros(3 * nm)
+            w = [0, 0, 0]
+            w[c] = 1
+            v = [Fraction(0)] * (3 * nm)
             shift = lambda axis: tuple(e + (1 if i == axis else 0) for i, e in enumerate(m))
             v[0 * nm + idx[shift(1)]] += w[2]
             v[0 * nm + idx[shift(2)]] -= w[1]
@@ -224,9 +287,7 @@ def nedelec1(k: int) -> RefElement:
             v[2 * nm + idx[shift(0)]] += w[1]
             v[2 * nm + idx[shift(1)]] -= w[0]
             span.append(v)
-    F = np.array(_edge_functionals(k, nm, ms) + _face_functionals("hcurl", k, nm, ms)
-                 + _interior_functionals(k - 3, nm, ms))
-    phi = _dualise(np.array(span).T, F, k * (k + 2) * (k + 3) // 2)
+    phi = _dualise(span, _functional_matrix("hcurl", k), k * (k + 2) * (k + 3) // 2)
     return RefElement("hcurl", 3, k, k, phi, 3)
 
 
@@ -237,12 +298,11 @@ def raviart_thomas(k: int) -> RefElement:
     idx = {m: i for i, m in enumerate(ms)}
     span = [_vec(c, idx[m], nm) for c in range(3) for m in monomials(3, k - 1)]
     for m in _homogeneous(k - 1):
-        v = np.zeros(3 * nm)
+        v = [Fraction(0)] * (3 * nm)
         for c in range(3):
-            v[c * nm + idx[tuple(e + (1 if i == c else 0) for i, e in enumerate(m))]] = 1.0
+            v[c * nm + idx[tuple(e + (1 if i == c else 0) for i, e in enumerate(m))]] = Fraction(1)
         span.append(v)
-    F = np.array(_face_functionals("hdiv", k, nm, ms) + _interior_functionals(k - 2, nm, ms))
-    phi = _dualise(np.array(span).T, F, k * (k + 1) * (k + 3) // 2)
+    phi = _dualise(span, _functional_matrix("hdiv", k), k * (k + 1) * (k + 3) // 2)
     return RefElement("hdiv", 3, k, k, phi, 3)
 
 
@@ -256,14 +316,3 @@ def reference_element(space: str, dim: int, order: int) -> RefElement:
     if space == "hdiv":
         return raviart_thomas(order)
     raise ValueError(space)
-
-
-def dof_functionals(space: str, order: int) -> np.ndarray:
-    """The functional matrix F of a vector element (rows = dofs), for tests."""
-    k = order
-    ms = monomials(3, k)
-    nm = len(ms)
-    if space == "hcurl":
-        return np.array(_edge_functionals(k, nm, ms) + _face_functionals("hcurl", k, nm, ms)
-                        + _interior_functionals(k - 3, nm, ms))
-    return np.array(_face_functionals("hdiv", k, nm, ms) + _interior_functionals(k - 2, nm, ms))

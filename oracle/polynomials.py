@@ -1,16 +1,22 @@
-"""Dense monomial polynomials on the reference simplex, integrated exactly.
+"""Monomial polynomials on the reference simplex, integrated exactly.
 
 A scalar polynomial in d variables of degree <= D is a coefficient vector over
 ``monomials(d, D)``.  The reference simplex has vertices 0, e_1, .., e_d and the exact
 integral of a monomial over it is ``prod(a_i!) / (|a| + d)!`` (Dirichlet integral).
+Integrals are exact rationals (``fractions.Fraction``); the element construction carries
+them in 40-digit ``mpmath`` arithmetic and rounds to FP64 once, at the end.
 """
 from __future__ import annotations
 
 import functools
 import itertools
 import math
+from fractions import Fraction
 
+import mpmath
 import numpy as np
+
+mpmath.mp.dps = 40
 
 
 @functools.lru_cache(maxsize=None)
@@ -23,24 +29,25 @@ def monomials(d: int, D: int) -> tuple[tuple[int, ...], ...]:
     return tuple(out)
 
 
-def simplex_monomial_integral(a: tuple[int, ...]) -> float:
+def simplex_monomial_integral(a: tuple[int, ...]) -> Fraction:
     d = len(a)
-    return math.prod(math.factorial(x) for x in a) / math.factorial(sum(a) + d)
+    return Fraction(math.prod(math.factorial(x) for x in a), math.factorial(sum(a) + d))
 
 
 @functools.lru_cache(maxsize=None)
-def gram(d: int, D: int) -> np.ndarray:
-    """G[i, j] = integral over the reference simplex of m_i * m_j."""
+def gram(d: int, D: int) -> mpmath.matrix:
+    """G[i, j] = integral over the reference simplex of m_i * m_j (exact, as mpf)."""
     ms = monomials(d, D)
-    G = np.empty((len(ms), len(ms)))
+    G = mpmath.matrix(len(ms), len(ms))
     for i, a in enumerate(ms):
         for j, b in enumerate(ms):
-            G[i, j] = simplex_monomial_integral(tuple(x + y for x, y in zip(a, b)))
+            f = simplex_monomial_integral(tuple(x + y for x, y in zip(a, b)))
+            G[i, j] = mpmath.mpf(f.numerator) / f.denominator
     return G
 
 
 def eval_monomials(d: int, D: int, pts: np.ndarray) -> np.ndarray:
-    """[n_pts, n_mono] values of the monomials at points [n_pts, d]."""
+    """[n_pts, n_mono] FP64 values of the monomials at points [n_pts, d]."""
     ms = monomials(d, D)
     pts = np.atleast_2d(pts)
     out = np.ones((pts.shape[0], len(ms)))
@@ -51,50 +58,45 @@ def eval_monomials(d: int, D: int, pts: np.ndarray) -> np.ndarray:
     return out
 
 
-def _poly2_mul(p: np.ndarray, q: np.ndarray) -> np.ndarray:
-    """Product of two polynomials in (s, t) stored as arrays P[i, j] -> s^i t^j."""
-    out = np.zeros((p.shape[0] + q.shape[0] - 1, p.shape[1] + q.shape[1] - 1))
-    for i in range(p.shape[0]):
-        for j in range(p.shape[1]):
-            if p[i, j] != 0.0:
-                out[i:i + q.shape[0], j:j + q.shape[1]] += p[i, j] * q
+def _poly2_mul(p: dict, q: dict) -> dict:
+    out: dict = {}
+    for (i, j), a in p.items():
+        for (k, l), b in q.items():
+            out[(i + k, j + l)] = out.get((i + k, j + l), 0) + a * b
     return out
 
 
-def restrict_to_param(a: tuple[int, ...], origin: np.ndarray, tangents: list[np.ndarray]) -> np.ndarray:
-    """Monomial x^a along x = origin + sum_r u_r tangents[r], as a 2-variable array.
+def restrict_to_param(a: tuple[int, ...], origin, tangents) -> dict:
+    """Monomial x^a along x = origin + sum_r u_r tangents[r] as {(i, j): Fraction} in (u_1, u_2).
 
-    With one tangent the second axis has length 1 (a polynomial in u_1 only).
+    origin / tangents have rational entries; with one tangent only j = 0 appears.
     """
-    n_par = len(tangents)
-    out = np.ones((1, 1))
+    out = {(0, 0): Fraction(1)}
     for c, e in enumerate(a):
-        lin = np.zeros((2, 2)) if n_par == 2 else np.zeros((2, 1))
-        lin[0, 0] = origin[c]
-        lin[1, 0] = tangents[0][c]
-        if n_par == 2:
-            lin[0, 1] = tangents[1][c]
+        lin = {(0, 0): Fraction(origin[c]), (1, 0): Fraction(tangents[0][c])}
+        if len(tangents) == 2:
+            lin[(0, 1)] = Fraction(tangents[1][c])
         for _ in range(e):
             out = _poly2_mul(out, lin)
     return out
 
 
-def integrate_segment(P: np.ndarray) -> float:
-    """Integral over u in [0, 1] of sum_i P[i, 0] u^i."""
-    return float(sum(P[i, 0] / (i + 1) for i in range(P.shape[0])))
+def integrate_segment(P: dict) -> Fraction:
+    """Integral over u in [0, 1] of sum P[(i, 0)] u^i."""
+    return sum((c / (i + 1) for (i, j), c in P.items()), Fraction(0))
 
 
-def integrate_triangle(P: np.ndarray) -> float:
-    """Integral over the reference triangle {s, t >= 0, s + t <= 1} of sum P[i, j] s^i t^j."""
-    tot = 0.0
-    for i in range(P.shape[0]):
-        for j in range(P.shape[1]):
-            if P[i, j] != 0.0:
-                tot += P[i, j] * math.factorial(i) * math.factorial(j) / math.factorial(i + j + 2)
-    return tot
+def integrate_triangle(P: dict) -> Fraction:
+    """Integral over {s, t >= 0, s + t <= 1} of sum P[(i, j)] s^i t^j."""
+    return sum((c * Fraction(math.factorial(i) * math.factorial(j), math.factorial(i + j + 2))
+                for (i, j), c in P.items()), Fraction(0))
 
 
-def shifted_legendre(j: int) -> np.ndarray:
-    """Power-basis coefficients (ascending) of P_j(2u - 1) on [0, 1]."""
-    leg = np.polynomial.Legendre.basis(j, domain=[0.0, 1.0]).convert(kind=np.polynomial.Polynomial)
-    return np.asarray(leg.coef, dtype=np.float64)
+def shifted_legendre(j: int) -> list[Fraction]:
+    """Power-basis coefficients (ascending) of P_j(2u - 1) on [0, 1] (Rodrigues form:
+    P_j(2u - 1) = sum_i (-1)^(j+i) C(j, i) C(j+i, i) u^i)."""
+    return [Fraction((-1) ** (j + i) * math.comb(j, i) * math.comb(j + i, i)) for i in range(j + 1)]
+
+
+def to_mpf(f: Fraction) -> mpmath.mpf:
+    return mpmath.mpf(f.numerator) / f.denominator

@@ -1,0 +1,413 @@
+// Reference-element tables for the BRAS library (host side, computed once per setup).
+//
+// What is computed: the reference mass blocks R_ab[i][j] = int_Kref phi_i^a phi_j^b of the
+// nodal basis of each element family, from which every physical element matrix follows by
+// the Piola pullbacks of Sec. 2.4 (Eq. piola_mass_pullbacks):
+//   H1:      M_K = |det J| R_00
+//   H(curl): M_K = sum_ab G_ab R_ab,  G = |det J| J^{-1} J^{-T}
+//   H(div):  M_K = sum_ab G_ab R_ab,  G = J^T J / |det J|
+//
+// How (this library's own construction):
+//   * integrals by collapsed (Duffy) tensor Gauss-Legendre rules, exact for the degrees used;
+//   * Lagrange: Silvester's product form of the nodal basis in barycentric coordinates,
+//     phi_alpha = prod_i prod_{m < alpha_i} (p lambda_i - m) / (m + 1);
+//   * Nedelec / Raviart-Thomas: the Arnold-Falk-Winther geometric bases of P_k^- Lambda^1
+//     and P_k^- Lambda^2 (lambda^alpha times Whitney forms, alpha_m = 0 below the first
+//     vertex of the form) as a spanning basis, dualised against the documented dof
+//     functionals (edge Legendre moments, face moments against mean-orthonormal
+//     polynomials, interior moments) by an LU solve in long double.
+#include "refelem.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <vector>
+
+namespace bras {
+namespace {
+
+struct QP { double x[3]; double w; };
+
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        long double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        long double dp = 1;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs((double)dz) < 1e-19) break;
+        }
+        x[i] = (double)((1 - z) / 2);
+        w[i] = (double)(1 / ((1 - z * z) * dp * dp));   // 2/((1-z^2)p'^2) scaled by 1/2
+    }
+}
+
+constexpr int kQuad = 9;   // 9-point rules: exact to degree 17 per collapsed direction
+
+std::vector<QP> segment_rule() {
+    std::vector<double> x, w;
+    gauss_legendre01(kQuad, x, w);
+    std::vector<QP> q;
+    for (int i = 0; i < kQuad; ++i) q.push_back({{x[i], 0, 0}, w[i]});
+    return q;
+}
+
+std::vector<QP> triangle_rule() {   // (s, t) = (u, v (1-u)), weight (1-u)
+    std::vector<double> x, w;
+    gauss_legendre01(kQuad, x, w);
+    std::vector<QP> q;
+    for (int i = 0; i < kQuad; ++i)
+        for (int j = 0; j < kQuad; ++j)
+            q.push_back({{x[i], x[j] * (1 - x[i]), 0}, w[i] * w[j] * (1 - x[i])});
+    return q;
+}
+
+std::vector<QP> tet_rule() {        // (x, y, z) = (u, v (1-u), w (1-u)(1-v))
+    std::vector<double> x, w;
+    gauss_legendre01(kQuad, x, w);
+    std::vector<QP> q;
+    for (int i = 0; i < kQuad; ++i)
+        for (int j = 0; j < kQuad; ++j)
+            for (int k = 0; k < kQuad; ++k) {
+                double u = x[i], v = x[j], s = x[k];
+                q.push_back({{u, v * (1 - u), s * (1 - u) * (1 - v)},
+                             w[i] * w[j] * w[k] * (1 - u) * (1 - u) * (1 - v)});
+            }
+    return q;
+}
+
+// barycentric coordinates on the reference simplex, vertices 0, e_1, .., e_d
+void bary(int dim, const double* x, double* lam) {
+    double s = 0;
+    for (int i = 0; i < dim; ++i) { lam[i + 1] = x[i]; s += x[i]; }
+    lam[0] = 1 - s;
+}
+
+void bary_grad(int i, double g[3]) {
+    for (int c = 0; c < 3; ++c) g[c] = (i == 0) ? -1.0 : (c == i - 1 ? 1.0 : 0.0);
+}
+
+// multi-indices of length m and sum s, ascending lexicographic
+void compositions(int m, int s, std::vector<std::vector<int>>& out) {
+    std::vector<int> a(m, 0);
+    out.clear();
+    std::function<void(int, int)> rec = [&](int pos, int left) {
+        if (pos == m - 1) { a[pos] = left; out.push_back(a); return; }
+        for (int v = 0; v <= left; ++v) { a[pos] = v; rec(pos + 1, left - v); }
+    };
+    rec(0, s);
+}
+
+// ---- Lagrange -------------------------------------------------------------------------
+double silvester(int p, const std::vector<int>& alpha, const double* lam) {
+    double v = 1;
+    for (size_t i = 0; i < alpha.size(); ++i)
+        for (int m = 0; m < alpha[i]; ++m) v *= (p * lam[i] - m) / (m + 1);
+    return v;
+}
+
+int build_lagrange(int dim, int p, RefTables* out) {
+    std::vector<std::vector<int>> nodes;
+    compositions(dim + 1, p, nodes);             // ascending lexicographic in (a_0..a_d)
+    const int n = (int)nodes.size();
+    auto rule = dim == 3 ? tet_rule() : triangle_rule();
+    out->nloc = n;
+    out->ncomp = 1;
+    out->R.assign((size_t)n * n, 0.0);
+    std::vector<double> phi(n);
+    for (const QP& q : rule) {
+        double lam[4];
+        bary(dim, q.x, lam);
+        for (int i = 0; i < n; ++i) phi[i] = silvester(p, nodes[i], lam);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) out->R[(size_t)i * n + j] += q.w * phi[i] * phi[j];
+    }
+    return 0;
+}
+
+// ---- vector elements ------------------------------------------------------------------
+using Vec3 = std::array<double, 3>;
+
+struct SpanFn {            // lambda^alpha * form(vertices)
+    std::array<int, 4> alpha;
+    std::array<int, 3> v;  // edge (v0, v1) or face (v0, v1, v2)
+};
+
+Vec3 cross(const Vec3& a, const Vec3& b) {
+    return {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+}
+
+Vec3 eval_span(bool curl, const SpanFn& f, const double* x) {
+    double lam[4];
+    bary(3, x, lam);
+    double pw = 1;
+    for (int i = 0; i < 4; ++i)
+        for (int m = 0; m < f.alpha[i]; ++m) pw *= lam[i];
+    Vec3 g[4];
+    for (int i = 0; i < 4; ++i) { double t[3]; bary_grad(i, t); g[i] = {t[0], t[1], t[2]}; }
+    Vec3 r{0, 0, 0};
+    if (curl) {            // Whitney edge form lam_a grad lam_b - lam_b grad lam_a
+        int a = f.v[0], b = f.v[1];
+        for (int c = 0; c < 3; ++c) r[c] = lam[a] * g[b][c] - lam[b] * g[a][c];
+    } else {               // Whitney face form lam_a gb x gc - lam_b ga x gc + lam_c ga x gb
+        int a = f.v[0], b = f.v[1], c = f.v[2];
+        Vec3 bc = cross(g[b], g[c]), ac = cross(g[a], g[c]), ab = cross(g[a], g[b]);
+        for (int d = 0; d < 3; ++d) r[d] = lam[a] * bc[d] - lam[b] * ac[d] + lam[c] * ab[d];
+    }
+    for (int c = 0; c < 3; ++c) r[c] *= pw;
+    return r;
+}
+
+std::vector<SpanFn> afw_span(bool curl, int k) {
+    std::vector<SpanFn> out;
+    std::vector<std::vector<int>> al;
+    compositions(4, k - 1, al);
+    if (curl) {
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                for (auto& m : al) {
+                    bool ok = true;
+                    for (int i = 0; i < a; ++i) ok &= (m[i] == 0);
+                    if (ok) out.push_back({{m[0], m[1], m[2], m[3]}, {a, b, -1}});
+                }
+    } else {
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                for (int c = b + 1; c < 4; ++c)
+                    for (auto& m : al) {
+                        bool ok = true;
+                        for (int i = 0; i < a; ++i) ok &= (m[i] == 0);
+                        if (ok) out.push_back({{m[0], m[1], m[2], m[3]}, {a, b, c}});
+                    }
+    }
+    return out;
+}
+
+// Gram-Schmidt (mean inner product) of monomials sampled at quadrature points.
+// Returns values [n_poly][n_pts].
+std::vector<std::vector<double>> orthonormal_values(const std::vector<QP>& rule, double measure,
+                                                    const std::vector<std::array<int, 3>>& monos) {
+    std::vector<std::vector<double>> q;
+    for (const auto& e : monos) {
+        std::vector<double> v(rule.size());
+        for (size_t i = 0; i < rule.size(); ++i)
+            v[i] = std::pow(rule[i].x[0], e[0]) * std::pow(rule[i].x[1], e[1]) * std::pow(rule[i].x[2], e[2]);
+        for (const auto& prev : q) {          // classical GS against the finished ones
+            double dot = 0;
+            for (size_t i = 0; i < rule.size(); ++i) dot += rule[i].w * v[i] * prev[i];
+            dot /= measure;
+            for (size_t i = 0; i < rule.size(); ++i) v[i] -= dot * prev[i];
+        }
+        double nn = 0;
+        for (size_t i = 0; i < rule.size(); ++i) nn += rule[i].w * v[i] * v[i];
+        nn = std::sqrt(nn / measure);
+        for (double& t : v) t /= nn;
+        q.push_back(v);
+    }
+    return q;
+}
+
+// triangle test monomials s^i t^j: degree ascending, then power of t ascending
+std::vector<std::array<int, 3>> triangle_monos(int deg) {
+    std::vector<std::array<int, 3>> m;
+    for (int d = 0; d <= deg; ++d)
+        for (int j = 0; j <= d; ++j) m.push_back({d - j, j, 0});
+    return m;
+}
+
+// tetrahedron monomials: degree ascending, then descending lexicographic exponent tuple
+std::vector<std::array<int, 3>> tet_monos(int deg) {
+    std::vector<std::array<int, 3>> m;
+    for (int d = 0; d <= deg; ++d) {
+        std::vector<std::array<int, 3>> lvl;
+        for (int a = 0; a <= d; ++a)
+            for (int b = 0; a + b <= d; ++b) lvl.push_back({a, b, d - a - b});
+        std::sort(lvl.begin(), lvl.end(), [](auto& u, auto& v) { return u > v; });
+        m.insert(m.end(), lvl.begin(), lvl.end());
+    }
+    return m;
+}
+
+double shifted_legendre(int j, double u) {
+    double z = 2 * u - 1, p0 = 1, p1 = z;
+    if (j == 0) return 1;
+    for (int k = 2; k <= j; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+bool lu_inverse(std::vector<long double> A, int n, std::vector<long double>& inv) {
+    std::vector<int> piv(n);
+    for (int i = 0; i < n; ++i) piv[i] = i;
+    for (int k = 0; k < n; ++k) {
+        int m = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs((double)A[(size_t)i * n + k]) > std::fabs((double)A[(size_t)m * n + k])) m = i;
+        if (A[(size_t)m * n + k] == 0) return false;
+        if (m != k) {
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)m * n + j]);
+            std::swap(piv[k], piv[m]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            long double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            A[(size_t)i * n + k] = f;
+            for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+        }
+    }
+    inv.assign((size_t)n * n, 0);
+    for (int c = 0; c < n; ++c) {
+        std::vector<long double> y(n);
+        for (int i = 0; i < n; ++i) {
+            long double s = (piv[i] == c) ? 1 : 0;
+            for (int j = 0; j < i; ++j) s -= A[(size_t)i * n + j] * y[j];
+            y[i] = s;
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            long double s = y[i];
+            for (int j = i + 1; j < n; ++j) s -= A[(size_t)i * n + j] * y[j];
+            y[i] = s / A[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
+    }
+    return true;
+}
+
+const int kEdges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+const int kFaces[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+const double kVert[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+int build_vector(bool curl, int k, RefTables* out) {
+    const auto span = afw_span(curl, k);
+    const int n = (int)span.size();
+    const int expect = curl ? k * (k + 2) * (k + 3) / 2 : k * (k + 1) * (k + 3) / 2;
+    if (n != expect) return -1;
+    const auto seg = segment_rule();
+    const auto tri = triangle_rule();
+    const auto tet = tet_rule();
+    // functional rows A[i][j] = l_i(span_j)
+    std::vector<long double> A;
+    A.reserve((size_t)n * n);
+    auto push_row = [&](auto&& fn) {   // fn(span index) -> value
+        for (int j = 0; j < n; ++j) A.push_back((long double)fn(j));
+    };
+    if (curl) {
+        for (auto& e : kEdges) {
+            Vec3 tau;
+            for (int c = 0; c < 3; ++c) tau[c] = kVert[e[1]][c] - kVert[e[0]][c];
+            for (int jm = 0; jm < k; ++jm)
+                push_row([&](int j) {
+                    double s = 0;
+                    for (const QP& q : seg) {
+                        double x[3];
+                        for (int c = 0; c < 3; ++c) x[c] = kVert[e[0]][c] + q.x[0] * tau[c];
+                        Vec3 v = eval_span(true, span[j], x);
+                        s += q.w * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2]) * shifted_legendre(jm, q.x[0]);
+                    }
+                    return s;
+                });
+        }
+    }
+    const int fdeg = curl ? k - 2 : k - 1;
+    if (fdeg >= 0) {
+        auto fq = orthonormal_values(tri, 0.5, triangle_monos(fdeg));
+        for (auto& f : kFaces) {
+            Vec3 t1, t2;
+            for (int c = 0; c < 3; ++c) {
+                t1[c] = kVert[f[1]][c] - kVert[f[0]][c];
+                t2[c] = kVert[f[2]][c] - kVert[f[0]][c];
+            }
+            std::vector<Vec3> dirs = curl ? std::vector<Vec3>{t1, t2} : std::vector<Vec3>{cross(t1, t2)};
+            for (size_t r = 0; r < fq.size(); ++r)
+                for (const Vec3& d : dirs)
+                    push_row([&](int j) {
+                        double s = 0;
+                        for (size_t qi = 0; qi < tri.size(); ++qi) {
+                            double x[3];
+                            for (int c = 0; c < 3; ++c)
+                                x[c] = kVert[f[0]][c] + tri[qi].x[0] * t1[c] + tri[qi].x[1] * t2[c];
+                            Vec3 v = eval_span(curl, span[j], x);
+                            s += tri[qi].w * (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) * fq[r][qi];
+                        }
+                        return s;
+                    });
+        }
+    }
+    const int ideg = curl ? k - 3 : k - 2;
+    if (ideg >= 0) {
+        auto iq = orthonormal_values(tet, 1.0 / 6.0, tet_monos(ideg));
+        for (size_t r = 0; r < iq.size(); ++r)
+            for (int comp = 0; comp < 3; ++comp)
+                push_row([&](int j) {
+                    double s = 0;
+                    for (size_t qi = 0; qi < tet.size(); ++qi)
+                        s += tet[qi].w * eval_span(curl, span[j], tet[qi].x)[comp] * iq[r][qi];
+                    return s;
+                });
+    }
+    if ((int)A.size() != n * n) return -2;
+    std::vector<long double> C;
+    if (!lu_inverse(A, n, C)) return -3;
+    // nodal basis phi_i = sum_j span_j C[j][i]; R_ab = int phi^a phi^b
+    out->nloc = n;
+    out->ncomp = 3;
+    out->R.assign((size_t)9 * n * n, 0.0);
+    std::vector<double> sv((size_t)n * 3), ph((size_t)n * 3);
+    for (const QP& q : tet) {
+        for (int j = 0; j < n; ++j) {
+            Vec3 v = eval_span(curl, span[j], q.x);
+            for (int c = 0; c < 3; ++c) sv[(size_t)j * 3 + c] = v[c];
+        }
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) {
+                long double s = 0;
+                for (int j = 0; j < n; ++j) s += (long double)sv[(size_t)j * 3 + c] * C[(size_t)j * n + i];
+                ph[(size_t)i * 3 + c] = (double)s;
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double* R = &out->R[(size_t)(a * 3 + b) * n * n];
+                for (int i = 0; i < n; ++i) {
+                    double wa = q.w * ph[(size_t)i * 3 + a];
+                    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] += wa * ph[(size_t)j * 3 + b];
+                }
+            }
+    }
+    return 0;
+}
+
+}  // namespace
+
+int n_local(int dim, int space, int order) {
+    if (space == 0) {
+        if (dim == 2 && order >= 1 && order <= 4) return (order + 1) * (order + 2) / 2;
+        if (dim == 3 && order >= 1 && order <= 4) return (order + 1) * (order + 2) * (order + 3) / 6;
+        return -1;
+    }
+    if (dim != 3 || order < 1 || order > 3) return -1;
+    if (space == 1) return order * (order + 2) * (order + 3) / 2;
+    if (space == 2) return order * (order + 1) * (order + 3) / 2;
+    return -1;
+}
+
+int build_reference(int dim, int space, int order, RefTables* out) {
+    if (n_local(dim, space, order) < 0) return -1;
+    out->dim = dim;
+    out->space = space;
+    out->order = order;
+    if (space == 0) return build_lagrange(dim, order, out);
+    return build_vector(space == 1, order, out);
+}
+
+}  // namespace bras

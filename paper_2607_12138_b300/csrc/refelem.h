@@ -1,0 +1,17 @@
+// Reference-element mass blocks of the supported element families (host side).
+#pragma once
+#include <functional>
+#include <vector>
+
+namespace bras {
+
+struct RefTables {
+    int dim = 0, space = 0, order = 0, nloc = 0, ncomp = 0;
+    // R[(a * ncomp + b) * nloc * nloc + i * nloc + j] = int_ref phi_i^a phi_j^b
+    std::vector<double> R;
+};
+
+int n_local(int dim, int space, int order);
+int build_reference(int dim, int space, int order, RefTables* out);
+
+}  // namespace bras
