@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the BRAS-PCG mass solve on one B300 (or N replicas under torchrun).
+
+Workload (the H1 configuration of the headline metric): unit cube, 48^3 cells x 6 Kuhn
+tetrahedra = 663,552 cells, interior vertices jittered by U(-0.15h, 0.15h) (seed 0), H1
+Lagrange p = 1, 2, 3, 4 (117,649 / 912,673 / 3,048,625 / 7,189,057 dofs), right-hand side
+N(0, 1) (seed 1), u_0 = 0, stop at ||r||/||b|| <= 1e-10 (Sec. 3).  One step = one solve for
+each of the four orders with the library's fast path: BRAS-preconditioned CG in FP32 (FP64
+dot products and scalars) inside FP64 iterative refinement, the TRUE FP64 residual tested.
+The metric is conforming dofs solved per second (sum of n over the step / step time).
+Setup (tables, element inverses) is excluded, as in the paper.
+
+Comparison rows on the same GPU (plain FP64 BRAS-PCG, FP64 Jacobi-PCG, mixed Jacobi-PCG),
+the end-to-end number through host buffers, the live roofline of the dominant kernel and
+the FP64 CPU oracle baseline are reported in the same JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BRAS-PCG mass-solve DOF/s to 1e-10 rel. residual (H1 p=1..4, 48^3x6 jittered tets)"
+WORKLOAD = "H1 Lagrange p=1,2,3,4 on 48^3x6 Kuhn tets (663,552), jitter 0.15h, 1 RHS N(0,1), rtol 1e-10"
+N_CELLS = 48
+JITTER = 0.15
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--orders", default="1,2,3,4")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---- CPU oracle timing (the baseline leg; the only place bench.py runs the oracle) ----------
+def oracle_solve_rate(orders=(1, 2), repeats=3):
+    """FP64 oracle BRAS-PCG (assembled CSR M and BRAS, scipy) on the same inputs; setup
+    excluded; mean of `repeats` solves per order (Sec. 3 reports means of 3)."""
+    from oracle.assembly import Problem
+    from oracle.solvers import pcg
+    from paper_2607_12138_b300 import meshgen as mg
+    mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
+    tot_n, tot_t, detail = 0, 0.0, []
+    for p in orders:
+        n, l2g, s = mg.dof_map(mesh, "h1", p)
+        pr = Problem(mesh, "h1", p, l2g, s, n)
+        b = mg.rhs(n, 1, seed=1)
+        ts = []
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            _, its, hist = pcg(pr.mass_apply, b, pr.bras_apply, rtol=1e-10)
+            ts.append(time.perf_counter() - t0)
+        t = float(np.mean(ts))
+        tot_n += n
+        tot_t += t
+        detail.append({"p": p, "n": n, "its": its, "s": round(t, 4)})
+    return tot_n / tot_t, detail
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    orders = (1, 2)
+    for _ in range(a.warmup):
+        oracle_solve_rate(orders, repeats=1)
+    vals, t_all = [], []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        v, detail = oracle_solve_rate(orders, repeats=1)
+        t_all.append(time.perf_counter() - t0)
+        vals.append(v)
+    value = float(np.mean(vals))
+    sample = "oracle FP64 BRAS-PCG (scipy CSR, 1 thread) on the same 48^3x6 mesh at p=1,2 (sample of p=1..4)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(t_all)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "p=1,2 only", "detail": detail},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- clocks ------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in open(self.path):
+            c = [x.strip() for x in row.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                mhz.append(float(c[1]))
+                mx = max(mx, float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---- our arm --------------------------------------------------------------------------------------
+def run_ours(a):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2607_12138_b300 import bras as B
+    from paper_2607_12138_b300 import meshgen as mg
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    orders = [int(p) for p in a.orders.split(",")]
+    mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
+    probs = []
+    for p in orders:
+        n, l2g, s = mg.dof_map(mesh, "h1", p)
+        ctx = B.Context(mesh.coords, mesh.cells, "h1", p, n, l2g, s)
+        b = torch.as_tensor(mg.rhs(n, 1, seed=1), device="cuda")
+        x = torch.empty_like(b)
+        bh = b.cpu().pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        probs.append({"p": p, "n": n, "ctx": ctx, "b": b, "x": x, "bh": bh, "xh": xh})
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    st = torch.cuda.current_stream()
+
+    def step(mode=B.SOLVE_MIXED, pc=B.PC_BRAS, host=False):
+        out = []
+        for pr in probs:
+            b, x = (pr["bh"], pr["xh"]) if host else (pr["b"], pr["x"])
+            _, its, rel, status = pr["ctx"].pcg_solve(b, pc=pc, mode=mode, inner_precision=B.FP32, rtol=1e-10, out=x)
+            out.append((int(its[0]), float(rel[0]), status))
+        return out
+
+    def timed(fn, steps):
+        ts = []
+        res = None
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            res = fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        barrier()
+        return ts, res
+
+    for _ in range(a.warmup):
+        step()
+    total_n = sum(pr["n"] for pr in probs)
+    clocks = Clocks(local)
+    launches0 = B._lib.bras_kernel_launches()
+    ts, res = timed(step, a.steps)
+    launches = B._lib.bras_kernel_launches() - launches0
+    clk = clocks.stop()
+    t_step = float(np.mean(ts))
+    t_max = t_step
+    if ws > 1:
+        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * total_n / t_max
+    for its, rel, status in res:
+        if status != 0 or rel > 1e-10:
+            raise RuntimeError(f"solve did not reach 1e-10: {res}")
+
+    # end to end through host buffers (H2D of b and D2H of x inside the call)
+    for _ in range(1):
+        step(host=True)
+    ts_e2e = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(host=True)
+        ts_e2e.append(time.perf_counter() - t0)
+    e2e = {"value": ws * total_n / float(np.mean(ts_e2e)), "unit": "DOF/s",
+           "h2d_bytes_per_step": 8 * total_n, "d2h_bytes_per_step": 8 * total_n}
+
+    if rank != 0:
+        return 0
+
+    # per-order detail, comparison rows and per-kernel live timings
+    detail = []
+    compare = {}
+    for i, pr in enumerate(probs):
+        its, rel, _ = res[i]
+        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel})
+    if not a.no_compare:
+        for name, mode, pc in (("fp64_bras", B.SOLVE_FP64, B.PC_BRAS), ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI),
+                               ("mixed_jacobi", B.SOLVE_MIXED, B.PC_JACOBI)):
+            step(mode, pc)
+            tsc, rc = timed(lambda: step(mode, pc), 1)
+            compare[name] = {"dof_per_s": total_n / tsc[0], "ms": 1e3 * tsc[0], "its": [r[0] for r in rc]}
+        compare["mixed_bras"] = {"dof_per_s": value / ws, "ms": 1e3 * t_step, "its": [r[0] for r in res]}
+
+    # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
+    kern = {}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    for pr in probs:
+        ctx = pr["ctx"]
+        x32 = pr["b"].float()
+        y32 = torch.empty_like(x32)
+        for name, fn, prec, xx, yy in (("bras_f32", ctx.bras_apply, B.FP32, x32, y32),
+                                       ("mass_f32", ctx.mass_apply, B.FP32, x32, y32),
+                                       ("mass_f64", ctx.mass_apply, B.FP64, pr["b"], pr["x"])):
+            for _ in range(3):
+                fn(xx, prec, out=yy)
+            reps = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                fn(xx, prec, out=yy)
+            e1.record(st)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            by = ctx.algorithmic_bytes(prec, 1, name.startswith("bras"))
+            kern[f"{name}_p{pr['p']}"] = {"us": us, "alg_bytes": by, "gbs": by / us / 1e3}
+    # dominant FP32 kernel by time per solve: bras apply and mass apply run once per inner iteration
+    top = max(probs, key=lambda pr: kern[f"bras_f32_p{pr['p']}"]["us"])
+    kb = kern[f"bras_f32_p{top['p']}"]
+    roofline = {"bound": "hbm", "achieved": kb["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": kb["gbs"] / hbm_peak, "traffic": None,
+                "kernel": f"bras_apply FP32 (block kernel + combine), H1 p={top['p']}",
+                "alg_bytes_per_launch": kb["alg_bytes"], "launch_us": kb["us"], "peak_source": "measured"}
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        rate, cdetail = oracle_solve_rate((1, 2), repeats=3)
+        cpu = {"value": rate, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle BRAS-PCG (scipy CSR, single thread) on the same mesh at p=1,2, mean of 3",
+               "detail": cdetail}
+
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "orders": orders, "cells": int(mesh.n_cell), "dofs_per_step": total_n,
+                       "solver": "mixed: FP32 BRAS-PCG (FP64 dots) in FP64 refinement",
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}",
+                       "detail": detail},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "compare": compare, "kernels": kern}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,6 +174,10 @@ void bras_destroy(bras_ctx* ctx);
 const char* bras_status_string(int code);
 int64_t bras_last_error_detail(void);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all contexts, all
+ * threads); a host-side counter for launch accounting. */
+int64_t bras_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

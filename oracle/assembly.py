@@ -14,7 +14,6 @@ Each M_K^{-1} comes from an FP64 Cholesky factorisation of M_K.
 from __future__ import annotations
 
 import numpy as np
-import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .elements import reference_element
@@ -82,12 +81,11 @@ def assemble_mass(l2g, signs, Me, n_dof) -> sp.csr_matrix:
 
 
 def local_inverses(Me: np.ndarray) -> np.ndarray:
-    """M_K^{-1} from an FP64 Cholesky factor of each M_K."""
-    out = np.empty_like(Me)
-    for k in range(Me.shape[0]):
-        c = sla.cho_factor(Me[k], lower=True)
-        out[k] = sla.cho_solve(c, np.eye(Me.shape[1]))
-    return out
+    """M_K^{-1} = L^{-T} L^{-1} from the FP64 Cholesky factor M_K = L L^T of each cell."""
+    L = np.linalg.cholesky(Me)
+    eye = np.broadcast_to(np.eye(Me.shape[1]), Me.shape)
+    W = np.linalg.solve(L, eye)                       # L^{-1}, batched
+    return np.transpose(W, (0, 2, 1)) @ W
 
 
 def bras_inverse(l2g, signs, Me, n_dof, Minv=None) -> sp.csr_matrix:

@@ -1,0 +1,241 @@
+"""Thin Python binding of libbras (argument marshalling only).
+
+Every numerical step runs inside ``libbras.so`` (sm_103a CUDA kernels); this module only
+converts torch tensors to raw pointers and checks return codes.  If the shared library is
+missing the import fails loudly: there is no Python or CPU fallback.
+
+Low-level functions carry the C names (``bras_setup``, ``bras_apply``, ...); ``Context`` is a
+small convenience wrapper around one ``bras_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbras.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bras.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_12138_b300.build`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+H1, HCURL, HDIV = 0, 1, 2
+FP64, FP32, BF16 = 0, 1, 2
+PC_NONE, PC_JACOBI, PC_BRAS = 0, 1, 2
+SOLVE_FP64, SOLVE_MIXED = 0, 1
+SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV}
+
+OK, NOT_CONVERGED = 0, 1
+ERR = {-1: "INVALID", -2: "L2G_RANGE", -3: "NO_COPY", -4: "DEGENERATE", -5: "NOT_SPD", -6: "CUDA",
+       -7: "OOM", -8: "BREAKDOWN", -9: "PRECISION", -10: "TOO_LARGE"}
+
+
+class BrasError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.detail = int(_lib.bras_last_error_detail())
+        super().__init__(f"{where}: {bras_status_string(code)} (code {code}, detail {self.detail})")
+
+
+class bras_options(ctypes.Structure):
+    _fields_ = [("precisions", ctypes.c_int), ("block_elems", ctypes.c_int), ("max_nrhs", ctypes.c_int)]
+
+
+_vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_lib.bras_setup.argtypes = [ctypes.POINTER(_vp), _int, _int, _int, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp,
+                            ctypes.POINTER(bras_options), _vp]
+_lib.bras_setup.restype = _int
+_lib.bras_n_local.argtypes = [_int, _int, _int]
+_lib.bras_n_local.restype = _int
+for _name in ("bras_mass_apply", "bras_apply", "bras_jacobi_apply"):
+    getattr(_lib, _name).argtypes = [_vp, _int, _vp, _vp, _int, _vp]
+    getattr(_lib, _name).restype = _int
+_lib.bras_pcg_solve.argtypes = [_vp, _int, _int, _int, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
+_lib.bras_pcg_solve.restype = _int
+_lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.bras_grad_rho.restype = _int
+_lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
+_lib.bras_update_rho.restype = _int
+_lib.bras_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int), ctypes.POINTER(_int)]
+_lib.bras_info.restype = _int
+_lib.bras_algorithmic_bytes.argtypes = [_vp, _int, _int, _int]
+_lib.bras_algorithmic_bytes.restype = _i64
+_lib.bras_destroy.argtypes = [_vp]
+_lib.bras_destroy.restype = None
+_lib.bras_status_string.argtypes = [_int]
+_lib.bras_status_string.restype = ctypes.c_char_p
+_lib.bras_last_error_detail.argtypes = []
+_lib.bras_last_error_detail.restype = _i64
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/bras.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bras_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise BrasError(rc, where)
+    return rc
+
+
+# ---- low-level names (same as the C ABI) -------------------------------------------------
+def bras_status_string(code: int) -> str:
+    return _lib.bras_status_string(code).decode()
+
+
+def bras_n_local(dim: int, space: int, order: int) -> int:
+    return _lib.bras_n_local(dim, space, order)
+
+
+def bras_setup(dim, space, order, coords, cells, n_dof, l2g, signs=None, rho=None, options=None, stream=None):
+    ctx = _vp()
+    opt = options or bras_options(0, 0, 1)
+    rc = _lib.bras_setup(ctypes.byref(ctx), dim, space, order, coords.shape[0], _ptr(coords), cells.shape[0],
+                         _ptr(cells), n_dof, _ptr(l2g), _ptr(signs), _ptr(rho), ctypes.byref(opt), _stream(stream))
+    _check(rc, "bras_setup")
+    return ctx
+
+
+def bras_mass_apply(ctx, precision, x, y, nrhs=1, stream=None):
+    return _check(_lib.bras_mass_apply(ctx, precision, _ptr(x), _ptr(y), nrhs, _stream(stream)), "bras_mass_apply")
+
+
+def bras_apply(ctx, precision, x, y, nrhs=1, stream=None):
+    return _check(_lib.bras_apply(ctx, precision, _ptr(x), _ptr(y), nrhs, _stream(stream)), "bras_apply")
+
+
+def bras_jacobi_apply(ctx, precision, x, y, nrhs=1, stream=None):
+    return _check(_lib.bras_jacobi_apply(ctx, precision, _ptr(x), _ptr(y), nrhs, _stream(stream)), "bras_jacobi_apply")
+
+
+def bras_pcg_solve(ctx, pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters, relres, stream=None):
+    rc = _lib.bras_pcg_solve(ctx, pc, mode, inner_precision, _ptr(b), _ptr(x), nrhs, rtol, maxit, _ptr(iters),
+                             _ptr(relres), _stream(stream))
+    return _check(rc, "bras_pcg_solve")
+
+
+def bras_grad_rho(ctx, x, lam, rho_bar, stream=None):
+    return _check(_lib.bras_grad_rho(ctx, _ptr(x), _ptr(lam), _ptr(rho_bar), _stream(stream)), "bras_grad_rho")
+
+
+def bras_update_rho(ctx, rho, stream=None):
+    return _check(_lib.bras_update_rho(ctx, _ptr(rho), _stream(stream)), "bras_update_rho")
+
+
+def bras_info(ctx):
+    n, e, nl, nb = _i64(), _i64(), _int(), _int()
+    _check(_lib.bras_info(ctx, ctypes.byref(n), ctypes.byref(e), ctypes.byref(nl), ctypes.byref(nb)), "bras_info")
+    return n.value, e.value, nl.value, nb.value
+
+
+def bras_algorithmic_bytes(ctx, precision, nrhs, bras):
+    return int(_lib.bras_algorithmic_bytes(ctx, precision, nrhs, int(bras)))
+
+
+def bras_destroy(ctx):
+    _lib.bras_destroy(ctx)
+
+
+def bras_last_error_detail() -> int:
+    return int(_lib.bras_last_error_detail())
+
+
+# ---- convenience wrapper -----------------------------------------------------------------
+class Context:
+    """One BRAS context on the current CUDA device (tensors in, tensors out)."""
+
+    def __init__(self, coords, cells, space: str, order: int, n_dof: int, l2g, signs=None, rho=None,
+                 precisions: int = 0, block_elems: int = 0, max_nrhs: int = 1, stream=None):
+        dev = torch.device("cuda")
+        self.dim = coords.shape[1]
+        self.space = SPACES[space]
+        self.order = order
+        self.n_dof = int(n_dof)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev) if a is not None else None
+        self._coords = t(coords, torch.float64)
+        self._cells = t(cells, torch.int32)
+        self._l2g = t(l2g, torch.int32)
+        self._signs = t(signs, torch.int8)
+        self._rho = t(rho, torch.float64)
+        self.n_cell = int(self._cells.shape[0])
+        opt = bras_options(precisions, block_elems, max_nrhs)
+        self.ctx = bras_setup(self.dim, self.space, order, self._coords, self._cells, self.n_dof, self._l2g,
+                              self._signs, self._rho, opt, stream)
+        _, _, self.n_loc, self.n_blocks = bras_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            bras_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _dtype(precision):
+        return torch.float64 if precision == FP64 else torch.float32
+
+    def _apply(self, fn, x, precision, out=None, stream=None):
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        y = out if out is not None else torch.empty_like(x)
+        fn(self.ctx, precision, x, y, nrhs, stream)
+        return y
+
+    def mass_apply(self, x, precision=FP64, out=None, stream=None):
+        return self._apply(bras_mass_apply, x, precision, out, stream)
+
+    def bras_apply(self, x, precision=FP64, out=None, stream=None):
+        return self._apply(bras_apply, x, precision, out, stream)
+
+    def jacobi_apply(self, x, precision=FP64, out=None, stream=None):
+        return self._apply(bras_jacobi_apply, x, precision, out, stream)
+
+    def pcg_solve(self, b, pc=PC_BRAS, mode=SOLVE_FP64, inner_precision=FP32, rtol=1e-10, maxit=5000,
+                  out=None, stream=None):
+        """Returns (x, iters, relres, status); b/x may be CUDA or CPU float64 tensors."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        x = out if out is not None else torch.empty_like(b)
+        iters = np.zeros(nrhs, dtype=np.int32)
+        relres = np.zeros(nrhs, dtype=np.float64)
+        st = bras_pcg_solve(self.ctx, pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters, relres, stream)
+        return x, iters, relres, st
+
+    def grad_rho(self, x, lam, stream=None):
+        out = torch.empty(self.n_cell, dtype=torch.float64, device=x.device)
+        bras_grad_rho(self.ctx, x.contiguous(), lam.contiguous(), out, stream)
+        return out
+
+    def update_rho(self, rho, stream=None):
+        self._rho = torch.as_tensor(rho, dtype=torch.float64, device="cuda").contiguous()
+        bras_update_rho(self.ctx, self._rho, stream)
+
+    def algorithmic_bytes(self, precision, nrhs=1, bras=True):
+        return bras_algorithmic_bytes(self.ctx, precision, nrhs, bras)

@@ -1,0 +1,484 @@
+// extern "C" entry points of libbras: setup, applies, solve, gradient, info, teardown.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ctx.h"
+#include "dispatch.h"
+#include "internal.h"
+#include "refelem.h"
+#include "setup_dev.h"
+
+namespace bras {
+
+thread_local int64_t g_detail = -1;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+void set_detail(int64_t d) { g_detail = d; }
+
+void* dalloc_bytes(bras_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    c->owned.push_back(p);
+    return p;
+}
+
+void dfree(bras_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it != c->owned.end()) c->owned.erase(it);
+    cudaFree(p);
+}
+
+namespace {
+
+template <typename T>
+T* dalloc(bras_ctx* c, size_t count) {
+    return static_cast<T*>(dalloc_bytes(c, count * sizeof(T)));
+}
+
+template <typename T>
+int upload(bras_ctx* c, T** dst, const T* src, size_t count) {
+    *dst = dalloc<T>(c, count);
+    if (!*dst) return BRAS_ERR_OOM;
+    if (count && cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return BRAS_ERR_CUDA;
+    return BRAS_OK;
+}
+
+template <typename T>
+int fetch(std::vector<T>& dst, const T* src, size_t count) {
+    dst.resize(count);
+    if (count && cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDefault) != cudaSuccess) return BRAS_ERR_CUDA;
+    return BRAS_OK;
+}
+
+// Cholesky inverse of an SPD matrix in long double (the H1 reference mass, once per setup).
+bool spd_inverse(const std::vector<double>& M, int n, std::vector<double>& inv) {
+    std::vector<long double> L((size_t)n * n, 0);
+    for (int j = 0; j < n; ++j) {
+        long double s = M[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(s > 0)) return false;
+        L[(size_t)j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            long double t = M[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = t / L[(size_t)j * n + j];
+        }
+    }
+    std::vector<long double> W((size_t)n * n, 0);   // W = L^{-1}
+    for (int c = 0; c < n; ++c) {
+        W[(size_t)c * n + c] = 1 / L[(size_t)c * n + c];
+        for (int i = c + 1; i < n; ++i) {
+            long double s = 0;
+            for (int k = c; k < i; ++k) s += L[(size_t)i * n + k] * W[(size_t)k * n + c];
+            W[(size_t)i * n + c] = -s / L[(size_t)i * n + i];
+        }
+    }
+    inv.assign((size_t)n * n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            long double s = 0;
+            for (int k = std::max(i, j); k < n; ++k) s += W[(size_t)k * n + i] * W[(size_t)k * n + j];
+            inv[(size_t)i * n + j] = (double)s;
+        }
+    return true;
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+cudaError_t to_float(const double* a, float* b, int64_t n, cudaStream_t st) {
+    int nb = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+    if (nb < 1) nb = 1;
+    k_to_float<<<nb, 256, 0, st>>>(a, b, n);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const double* coords,
+               int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
+               const double* rho, const bras_options* opt, cudaStream_t st) {
+    const int nloc = n_local(dim, space, order);
+    c->dim = dim;
+    c->space = space;
+    c->order = order;
+    c->nloc = nloc;
+    c->ncomp = space == BRAS_H1 ? 1 : 3;
+    c->E = n_cell;
+    c->n = n_dof;
+    c->nvert = n_vert;
+    c->precisions = (opt && opt->precisions) ? opt->precisions : 7;
+    c->max_nrhs = (opt && opt->max_nrhs > 0) ? opt->max_nrhs : 1;
+    int BE = (opt && opt->block_elems) ? opt->block_elems : 256;
+    if (BE < 32 || BE > 256) return BRAS_ERR_INVALID;
+    c->BE = BE;
+    const bool want64 = c->precisions & 1, want32 = c->precisions & 2, wantbf = c->precisions & 4;
+
+    // host copies (inputs may live on either side)
+    std::vector<double> h_coords;
+    std::vector<int32_t> h_cells, h_l2g;
+    std::vector<int8_t> h_signs;
+    int rc;
+    if ((rc = fetch(h_coords, coords, (size_t)n_vert * dim))) return rc;
+    if ((rc = fetch(h_cells, cells, (size_t)n_cell * (dim + 1)))) return rc;
+    if ((rc = fetch(h_l2g, l2g, (size_t)n_cell * nloc))) return rc;
+    if (signs && (rc = fetch(h_signs, signs, (size_t)n_cell * nloc))) return rc;
+    for (size_t i = 0; i < h_cells.size(); ++i)
+        if (h_cells[i] < 0 || h_cells[i] >= n_vert) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
+    for (size_t i = 0; i < h_signs.size(); ++i)
+        if (h_signs[i] != 1 && h_signs[i] != -1) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
+
+    HostTables t;
+    int64_t detail = -1;
+    rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
+                      h_cells.data(), dim, BE, &t, &detail);
+    if (rc) { set_detail(detail); return rc; }
+    c->nblk = t.nblk;
+    c->max_u = t.max_u;
+    c->max_ne = t.max_ne;
+    c->U_tot = (int64_t)t.ids.size();
+    c->npart = t.npart;
+    c->nsh = (int64_t)t.sh_ids.size();
+    if ((rc = upload(c, &c->perm, t.perm.data(), t.perm.size()))) return rc;
+    if ((rc = upload(c, &c->blk_e0, t.blk_e0.data(), t.blk_e0.size()))) return rc;
+    if ((rc = upload(c, &c->blk_u0, t.blk_u0.data(), t.blk_u0.size()))) return rc;
+    if ((rc = upload(c, &c->blk_nint, t.blk_nint.data(), t.blk_nint.size()))) return rc;
+    if ((rc = upload(c, &c->blk_p0, t.blk_p0.data(), t.blk_p0.size()))) return rc;
+    if ((rc = upload(c, &c->ids, t.ids.data(), t.ids.size()))) return rc;
+    if ((rc = upload(c, &c->incoff, t.incoff.data(), t.incoff.size()))) return rc;
+    if ((rc = upload(c, &c->loc, t.loc.data(), t.loc.size()))) return rc;
+    if ((rc = upload(c, &c->inc, t.inc.data(), t.inc.size()))) return rc;
+    if ((rc = upload(c, &c->sh_ids, t.sh_ids.data(), t.sh_ids.size()))) return rc;
+    if ((rc = upload(c, &c->sh_off, t.sh_off.data(), t.sh_off.size()))) return rc;
+    if ((rc = upload(c, &c->sh_slots, t.sh_slots.data(), t.sh_slots.size()))) return rc;
+    if ((rc = upload(c, &c->dinv64, t.dinv.data(), t.dinv.size()))) return rc;
+    if (!(c->dinv32 = dalloc<float>(c, n_dof))) return BRAS_ERR_OOM;
+    if (to_float(c->dinv64, c->dinv32, n_dof, st) != cudaSuccess) return BRAS_ERR_CUDA;
+
+    // reference tables (library construction, host)
+    RefTables ref;
+    if (build_reference(dim, space, order, &ref) != 0) return BRAS_ERR_INVALID;
+
+    // device copies of the geometry inputs
+    const double* d_coords = coords;
+    const int32_t* d_cells = cells;
+    const double* d_rho = rho;
+    if (!is_device_ptr(coords)) {
+        double* p;
+        if ((rc = upload(c, &p, h_coords.data(), h_coords.size()))) return rc;
+        d_coords = p;
+    }
+    if (!is_device_ptr(cells)) {
+        int32_t* p;
+        if ((rc = upload(c, &p, h_cells.data(), h_cells.size()))) return rc;
+        d_cells = p;
+    }
+    if (rho && !is_device_ptr(rho)) {
+        std::vector<double> h_rho(rho, rho + n_cell);
+        double* p;
+        if ((rc = upload(c, &p, h_rho.data(), h_rho.size()))) return rc;
+        d_rho = p;
+    }
+
+    unsigned long long* bad = dalloc<unsigned long long>(c, 1);
+    int* nfixed = dalloc<int>(c, 1);
+    if (!bad || !nfixed) return BRAS_ERR_OOM;
+    const unsigned long long none = ~0ull;
+    cudaMemcpy(bad, &none, sizeof(none), cudaMemcpyHostToDevice);
+    cudaMemset(nfixed, 0, sizeof(int));
+
+    if (!(c->absdet = dalloc<double>(c, n_cell)) || !(c->rho = dalloc<double>(c, n_cell))) return BRAS_ERR_OOM;
+    const bool h1 = space == BRAS_H1;
+    if (h1) {
+        const int n = nloc;
+        std::vector<double> inv;
+        if (!spd_inverse(ref.R, n, inv)) return BRAS_ERR_NOT_SPD;
+        std::vector<float> R32(ref.R.begin(), ref.R.end()), I32(inv.begin(), inv.end());
+        if ((rc = upload(c, &c->Mref64, ref.R.data(), ref.R.size()))) return rc;
+        if ((rc = upload(c, &c->Minvref64, inv.data(), inv.size()))) return rc;
+        if ((rc = upload(c, &c->Mref32, R32.data(), R32.size()))) return rc;
+        if ((rc = upload(c, &c->Minvref32, I32.data(), I32.size()))) return rc;
+        if (!(c->mscale64 = dalloc<double>(c, n_cell)) || !(c->bscale64 = dalloc<double>(c, n_cell)) ||
+            !(c->mscale32 = dalloc<float>(c, n_cell)) || !(c->bscale32 = dalloc<float>(c, n_cell)))
+            return BRAS_ERR_OOM;
+    } else {
+        if (!(c->metric = dalloc<double>(c, (size_t)6 * n_cell))) return BRAS_ERR_OOM;
+        if ((rc = upload(c, &c->Rref, ref.R.data(), ref.R.size()))) return rc;
+    }
+    if (run_geometry(dim, space, n_cell, c->perm, d_coords, d_cells, d_rho, c->absdet, c->rho, c->metric,
+                     c->mscale64, c->bscale64, c->mscale32, c->bscale32, bad, st) != cudaSuccess)
+        return BRAS_ERR_CUDA;
+    unsigned long long hbad = 0;
+    if (cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return BRAS_ERR_CUDA;
+    if (hbad != none) { set_detail((int64_t)hbad); return BRAS_ERR_DEGENERATE; }
+
+    if (!h1) {
+        c->npk = nloc * (nloc + 1) / 2;
+        c->Epad = (n_cell + 31) / 32 * 32;
+        const size_t cnt = (size_t)c->npk * c->Epad;
+        // FP64 tables are always built (outer residual, diag); FP32 / bf16 on request
+        if (!(c->Mpk64 = dalloc<double>(c, cnt)) || !(c->Minvpk64 = dalloc<double>(c, cnt))) return BRAS_ERR_OOM;
+        if (want32 || wantbf) {
+            if (!(c->Mpk32 = dalloc<float>(c, cnt))) return BRAS_ERR_OOM;
+        }
+        if (want32 && !(c->Minvpk32 = dalloc<float>(c, cnt))) return BRAS_ERR_OOM;
+        if (wantbf && !(c->Minvpkbf = dalloc<__nv_bfloat16>(c, cnt))) return BRAS_ERR_OOM;
+        if (run_element_inverse(nloc, n_cell, c->Epad, c->Rref, c->metric, c->Mpk64, c->Mpk32, c->Minvpk64,
+                                c->Minvpk32, c->Minvpkbf, bad, nfixed, c->perm, st) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        if (cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&c->bf16_fixed, nfixed, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        if (hbad != none) { set_detail((int64_t)hbad); return BRAS_ERR_NOT_SPD; }
+    }
+    (void)want64;
+
+    // partial-sum workspace and diag(M) (Jacobi, Sec. 2.1) through the same deterministic scatter
+    if (ensure_part(c, c->max_nrhs) != BRAS_OK) return BRAS_ERR_OOM;
+    if (!(c->diag64 = dalloc<double>(c, n_dof)) || !(c->diag32 = dalloc<float>(c, n_dof))) return BRAS_ERR_OOM;
+    if (run_op(c, BRAS_FP64, OP_DIAG, nullptr, c->diag64, 1, st) != BRAS_OK) return BRAS_ERR_CUDA;
+    if (to_float(c->diag64, c->diag32, n_dof, st) != cudaSuccess) return BRAS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BRAS_ERR_CUDA;
+    return BRAS_OK;
+}
+
+}  // namespace
+
+int ensure_part(bras_ctx* c, int nrhs) {
+    size_t need = (size_t)std::max<int64_t>(c->npart, 1) * nrhs * sizeof(double);
+    if (need <= c->part_bytes) return BRAS_OK;
+    dfree(c, c->part);
+    c->part = dalloc_bytes(c, need);
+    if (!c->part) { c->part_bytes = 0; return BRAS_ERR_OOM; }
+    c->part_bytes = need;
+    return BRAS_OK;
+}
+
+LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
+    LaunchCommon L{};
+    BlockArgs& A = L.A;
+    A.blk_e0 = c->blk_e0;
+    A.blk_u0 = c->blk_u0;
+    A.blk_nint = c->blk_nint;
+    A.blk_p0 = c->blk_p0;
+    A.ids = c->ids;
+    A.incoff = c->incoff;
+    A.loc = c->loc;
+    A.inc = c->inc;
+    A.Epad = c->Epad;
+    A.npart = c->npart;
+    A.max_u = c->max_u;
+    A.max_ne = c->max_ne;
+    const bool f64 = prec == BRAS_FP64;
+    A.dinv = f64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
+    if (c->space == BRAS_H1) {
+        if (op == OP_BRAS) {
+            A.refmat = f64 ? (const void*)c->Minvref64 : (const void*)c->Minvref32;
+            A.scale = f64 ? (const void*)c->bscale64 : (const void*)c->bscale32;
+        } else {
+            A.refmat = f64 ? (const void*)c->Mref64 : (const void*)c->Mref32;
+            A.scale = f64 ? (const void*)c->mscale64 : (const void*)c->mscale32;
+        }
+    } else {
+        if (op == OP_BRAS)
+            A.pk = f64 ? (const void*)c->Minvpk64 : prec == BRAS_BF16 ? (const void*)c->Minvpkbf : (const void*)c->Minvpk32;
+        else
+            A.pk = f64 ? (const void*)c->Mpk64 : (const void*)c->Mpk32;
+    }
+    L.nblk = c->nblk;
+    L.nsh = c->nsh;
+    L.sh_ids = c->sh_ids;
+    L.sh_off = c->sh_off;
+    L.sh_slots = c->sh_slots;
+    return L;
+}
+
+int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st) {
+    if (ensure_part(c, nrhs) != BRAS_OK) return BRAS_ERR_OOM;
+    LaunchCommon L = make_launch(c, prec, op);
+    cudaError_t err;
+    const bool h1 = c->space == BRAS_H1;
+    if (prec == BRAS_FP64) {
+        auto* xx = static_cast<const double*>(x);
+        auto* yy = static_cast<double*>(y);
+        auto* pp = static_cast<double*>(c->part);
+        err = h1 ? launch_h1_f64(L, c->nloc, op, xx, yy, pp, nrhs, st) : launch_pk_f64(L, c->nloc, op, xx, yy, pp, nrhs, st);
+    } else {
+        auto* xx = static_cast<const float*>(x);
+        auto* yy = static_cast<float*>(y);
+        auto* pp = static_cast<float*>(c->part);
+        if (h1) err = launch_h1_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
+        else if (prec == BRAS_BF16 && op == OP_BRAS) err = launch_pk_bf16(L, c->nloc, op, xx, yy, pp, nrhs, st);
+        else err = launch_pk_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
+    }
+    return err == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
+}
+
+bool has_precision(const bras_ctx* c, int prec) {
+    if (prec == BRAS_FP64) return true;
+    if (c->space == BRAS_H1) return prec == BRAS_FP32 || prec == BRAS_BF16;
+    if (prec == BRAS_FP32) return c->Minvpk32 && c->Mpk32;
+    if (prec == BRAS_BF16) return c->Minvpkbf && c->Mpk32;
+    return false;
+}
+
+}  // namespace bras
+
+using namespace bras;
+
+extern "C" {
+
+int bras_n_local(int dim, int space, int order) { return n_local(dim, space, order); }
+
+int bras_setup(bras_ctx** out, int dim, int space, int order, int64_t n_vert, const double* coords,
+               int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
+               const double* rho, const bras_options* opt, void* stream) {
+    set_detail(-1);
+    if (!out) return BRAS_ERR_INVALID;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || space < 0 || space > 2 || (space != BRAS_H1 && dim != 3)) return BRAS_ERR_INVALID;
+    const int nloc = n_local(dim, space, order);
+    if (nloc < 0) return BRAS_ERR_INVALID;
+    if (!coords || !cells || !l2g || n_vert <= dim || n_cell <= 0 || n_dof <= 0) return BRAS_ERR_INVALID;
+    if (n_cell >= (1ll << 31) || n_dof >= (1ll << 31) || n_cell * nloc >= (1ll << 31)) return BRAS_ERR_TOO_LARGE;
+    bras_ctx* c = new (std::nothrow) bras_ctx();
+    if (!c) return BRAS_ERR_OOM;
+    int rc = setup_impl(c, dim, space, order, n_vert, coords, n_cell, cells, n_dof, l2g, signs, rho, opt,
+                        static_cast<cudaStream_t>(stream));
+    if (rc != BRAS_OK) {
+        bras_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return BRAS_OK;
+}
+
+static int apply_common(const bras_ctx* cc, int prec, int op, const void* x, void* y, int nrhs, void* stream) {
+    set_detail(-1);
+    if (!cc || !x || !y || nrhs < 1 || prec < 0 || prec > 2) return BRAS_ERR_INVALID;
+    if (!has_precision(cc, prec)) return BRAS_ERR_PRECISION;
+    return run_op(const_cast<bras_ctx*>(cc), prec, op, x, y, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+int bras_mass_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs, void* stream) {
+    return apply_common(ctx, precision, OP_MASS, x, y, nrhs, stream);
+}
+
+int bras_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs, void* stream) {
+    return apply_common(ctx, precision, OP_BRAS, x, y, nrhs, stream);
+}
+
+int bras_jacobi_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs, void* stream) {
+    set_detail(-1);
+    if (!ctx || !x || !y || nrhs < 1 || precision < 0 || precision > 2) return BRAS_ERR_INVALID;
+    return jacobi_launch(ctx, precision, x, y, nrhs, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BRAS_OK
+                                                                                                        : BRAS_ERR_CUDA;
+}
+
+int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision, const double* b, double* x,
+                   int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream) {
+    set_detail(-1);
+    if (!ctx || !b || !x || nrhs < 1 || pc < 0 || pc > 2 || mode < 0 || mode > 1 || !(rtol >= 0) || maxit < 0)
+        return BRAS_ERR_INVALID;
+    if (mode == BRAS_SOLVE_MIXED && inner_precision != BRAS_FP32 && inner_precision != BRAS_BF16)
+        return BRAS_ERR_INVALID;
+    if (mode == BRAS_SOLVE_MIXED && !has_precision(ctx, inner_precision)) return BRAS_ERR_PRECISION;
+    return pcg_solve_impl(const_cast<bras_ctx*>(ctx), pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters,
+                          relres, static_cast<cudaStream_t>(stream));
+}
+
+int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar, void* stream) {
+    set_detail(-1);
+    if (!ctx || !x || !lam || !rho_bar || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
+    return grad_rho_launch(ctx, x, lam, rho_bar, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BRAS_OK
+                                                                                                     : BRAS_ERR_CUDA;
+}
+
+int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream) {
+    set_detail(-1);
+    if (!ctx || !rho || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (update_rho_launch(ctx, rho, st) != cudaSuccess) return BRAS_ERR_CUDA;
+    if (run_op(ctx, BRAS_FP64, OP_DIAG, nullptr, ctx->diag64, 1, st) != BRAS_OK) return BRAS_ERR_CUDA;
+    if (to_float(ctx->diag64, ctx->diag32, ctx->n, st) != cudaSuccess) return BRAS_ERR_CUDA;
+    return BRAS_OK;
+}
+
+int bras_info(const bras_ctx* ctx, int64_t* n_dof, int64_t* n_cell, int* n_loc, int* n_blocks) {
+    if (!ctx) return BRAS_ERR_INVALID;
+    if (n_dof) *n_dof = ctx->n;
+    if (n_cell) *n_cell = ctx->E;
+    if (n_loc) *n_loc = ctx->nloc;
+    if (n_blocks) *n_blocks = ctx->nblk;
+    return BRAS_OK;
+}
+
+int64_t bras_algorithmic_bytes(const bras_ctx* ctx, int precision, int nrhs, int bras) {
+    if (!ctx || nrhs < 1) return -1;
+    const int64_t w = precision == BRAS_FP64 ? 8 : 4;
+    int64_t bytes = ctx->E * ctx->nloc * 4;                          // l2g map
+    if (ctx->space == BRAS_H1) bytes += ctx->E * w;                  // per-cell factor
+    else {
+        const int64_t wi = precision == BRAS_FP64 ? 8 : (precision == BRAS_BF16 && bras ? 2 : 4);
+        bytes += ctx->E * (int64_t)ctx->npk * wi;                     // packed local matrix
+    }
+    bytes += 2 * ctx->n * nrhs * w;                                   // x read, y written
+    if (bras) bytes += ctx->n;                                        // multiplicity byte
+    return bytes;
+}
+
+void bras_destroy(bras_ctx* ctx) {
+    if (!ctx) return;
+    free_pcg(ctx);
+    for (void* p : ctx->owned) cudaFree(p);
+    ctx->owned.clear();
+    delete ctx;
+}
+
+const char* bras_status_string(int code) {
+    switch (code) {
+        case BRAS_OK: return "ok";
+        case BRAS_NOT_CONVERGED: return "not converged (maxit reached)";
+        case BRAS_ERR_INVALID: return "invalid argument";
+        case BRAS_ERR_L2G_RANGE: return "l2g entry out of range";
+        case BRAS_ERR_NO_COPY: return "dof referenced by no cell";
+        case BRAS_ERR_DEGENERATE: return "degenerate cell (det J = 0) or non-positive weight";
+        case BRAS_ERR_NOT_SPD: return "local mass matrix not SPD";
+        case BRAS_ERR_CUDA: return "CUDA error";
+        case BRAS_ERR_OOM: return "out of memory";
+        case BRAS_ERR_BREAKDOWN: return "CG breakdown";
+        case BRAS_ERR_PRECISION: return "precision not built in this context";
+        case BRAS_ERR_TOO_LARGE: return "size above a library limit";
+        default: return "unknown status";
+    }
+}
+
+int64_t bras_last_error_detail(void) { return g_detail; }
+
+int64_t bras_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

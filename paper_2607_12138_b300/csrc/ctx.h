@@ -1,0 +1,85 @@
+// Internal context of libbras (not part of the ABI).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/bras.h"
+
+namespace bras {
+
+struct PcgWork;
+
+// ---- scatter tables ---------------------------------------------------------------
+// Cells are reordered along a Morton curve of their centroids and cut into blocks of at
+// most BE consecutive cells.  Block b owns cells [blk_e0[b], blk_e0[b+1]) and the dof list
+// ids[blk_u0[b] .. blk_u0[b+1]): first the dofs all of whose broken copies lie inside the
+// block ("interior", blk_nint[b] of them), then the others ("shared").
+//   loc[e0*nloc + a*ne + e]  = block-local index of dof (cell e, local a), bit 15 = sign -1
+//   inc[e0*nloc + s], s in [incoff[blk_u0[b]+b+u], incoff[blk_u0[b]+b+u+1]) = broken slots
+//       a*ne + e of block-local dof u, ascending (fixed summation order)
+//   shared dof j of block b writes partial slot blk_p0[b] + j; sh_off / sh_slots list, per
+//   globally shared dof sh_ids[i], its partial slots in ascending block order.
+struct HostTables {
+    int BE = 256, nblk = 0, max_u = 0, max_ne = 0;
+    std::vector<int32_t> perm, blk_e0, blk_u0, blk_nint, blk_p0, ids, sh_ids, sh_off, sh_slots;
+    std::vector<uint16_t> incoff, loc, inc;
+    std::vector<double> dinv;
+    int64_t npart = 0;
+};
+
+int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
+                 const double* coords, const int32_t* cells, int dim, int BE, HostTables* t,
+                 int64_t* detail);
+
+}  // namespace bras
+
+struct bras_ctx {
+    int dim = 0, space = 0, order = 0, nloc = 0, ncomp = 0;
+    int64_t E = 0, n = 0, nvert = 0;
+    int BE = 256, nblk = 0, max_u = 0, max_ne = 0;
+    int precisions = 0, max_nrhs = 1;
+    int64_t U_tot = 0, npart = 0, nsh = 0;
+    int64_t Epad = 0;   // padded cell count of the packed (SoA) per-cell matrices
+    int npk = 0;        // nloc (nloc + 1) / 2
+    int bf16_fixed = 0; // cells whose bf16-rounded inverse needed a diagonal shift
+
+    // scatter tables (device)
+    int32_t *blk_e0 = nullptr, *blk_u0 = nullptr, *blk_nint = nullptr, *blk_p0 = nullptr;
+    int32_t *ids = nullptr, *sh_ids = nullptr, *sh_off = nullptr, *sh_slots = nullptr;
+    int32_t *perm = nullptr;
+    uint16_t *incoff = nullptr, *loc = nullptr, *inc = nullptr;
+
+    // per dof
+    double* dinv64 = nullptr;
+    float* dinv32 = nullptr;
+    double* diag64 = nullptr;
+    float* diag32 = nullptr;
+
+    // geometry (internal cell order)
+    double* absdet = nullptr;    // |det J_K|
+    double* rho = nullptr;       // weights
+    double* metric = nullptr;    // [6][E] symmetric Piola metric (vector spaces)
+
+    // H1: reference mass and inverse, per-cell factors
+    double *Mref64 = nullptr, *Minvref64 = nullptr;
+    float *Mref32 = nullptr, *Minvref32 = nullptr;
+    double *mscale64 = nullptr, *bscale64 = nullptr;
+    float *mscale32 = nullptr, *bscale32 = nullptr;
+
+    // H(curl)/H(div): packed lower-triangular-by-rows symmetric matrices, SoA [npk][Epad]
+    double* Rref = nullptr;      // [ncomp*ncomp][nloc][nloc] reference blocks
+    double *Mpk64 = nullptr, *Minvpk64 = nullptr;
+    float *Mpk32 = nullptr, *Minvpk32 = nullptr;
+    __nv_bfloat16* Minvpkbf = nullptr;
+
+    // workspace
+    void* part = nullptr;        // partial sums of shared dofs [npart * nrhs] (double)
+    size_t part_bytes = 0;
+    int* status = nullptr;       // device status words
+    bras::PcgWork* pcg = nullptr;
+
+    std::vector<void*> owned;    // every device allocation, freed by bras_destroy
+};

@@ -1,0 +1,26 @@
+// Internal cross-file declarations of libbras.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ctx.h"
+#include "dispatch.h"
+
+namespace bras {
+
+void set_detail(int64_t d);
+void* dalloc_bytes(bras_ctx* c, size_t bytes);
+void dfree(bras_ctx* c, void* p);
+int ensure_part(bras_ctx* c, int nrhs);
+LaunchCommon make_launch(const bras_ctx* c, int prec, int op);
+int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st);
+bool has_precision(const bras_ctx* c, int prec);
+
+cudaError_t jacobi_launch(const bras_ctx* c, int prec, const void* x, void* y, int nrhs, cudaStream_t st);
+int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* b, double* x, int nrhs,
+                   double rtol, int maxit, int* iters, double* relres, cudaStream_t st);
+void free_pcg(bras_ctx* c);
+
+cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* lam, double* rho_bar, cudaStream_t st);
+cudaError_t update_rho_launch(bras_ctx* c, const double* rho, cudaStream_t st);
+
+}  // namespace bras

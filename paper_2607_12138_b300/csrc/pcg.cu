@@ -1,0 +1,485 @@
+// Preconditioned CG mass solve (Sec. 3) and FP64 iterative refinement around an FP32 inner
+// solve.  Dot products accumulate in FP64 through a fixed two-level tree (per-block partial
+// sums, then one block summing them in block order): results are bit-reproducible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace bras {
+
+constexpr int kDotBlocks = 296;    // 2 per SM on a 148-SM B300
+constexpr int kMaxRhs = 256;
+
+enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_BN, S_SCALE, S_COUNT };
+enum { FIN_INIT_RR = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_NORM };
+
+struct SolveGraph {
+    int prec = 0, pc = 0, R = 0, tsize = 0;
+    const void *x = nullptr, *part = nullptr;
+    int kernels_per_iter = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct PcgWork {
+    cudaStream_t cap = nullptr;   // private stream used only to capture solve graphs
+    std::vector<SolveGraph> graphs;
+    double* dparam = nullptr;     // [0] = rtol^2
+    int* iparam = nullptr;        // [0] = maxit, [1] = iterations done
+    double* h_param = nullptr;    // pinned staging of dparam/iparam
+    int nrhs = 0;
+    int64_t n = 0;
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xs = nullptr, *bs = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr;
+    double* partial = nullptr;    // [kDotBlocks][nrhs]
+    double* sc = nullptr;         // [S_COUNT][nrhs]
+    int* flags = nullptr;         // [0..nrhs): active, [nrhs..2nrhs): its, [2nrhs]: n active, [2nrhs+1]: status
+    int* h_flags = nullptr;       // pinned
+    double* h_sc = nullptr;       // pinned
+};
+
+void free_pcg(bras_ctx* c) {
+    if (!c->pcg) return;
+    for (auto& g : c->pcg->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    c->pcg->graphs.clear();
+    if (c->pcg->cap) cudaStreamDestroy(c->pcg->cap);
+    if (c->pcg->h_param) cudaFreeHost(c->pcg->h_param);
+    if (c->pcg->h_flags) cudaFreeHost(c->pcg->h_flags);
+    if (c->pcg->h_sc) cudaFreeHost(c->pcg->h_sc);
+    delete c->pcg;       // device buffers are in c->owned
+    c->pcg = nullptr;
+}
+
+static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
+    PcgWork* w = c->pcg;
+    if (w && w->nrhs >= R && (!mixed || w->r32)) return BRAS_OK;
+    if (w) {
+        for (void* p : {(void*)w->r, (void*)w->z, (void*)w->p, (void*)w->q, (void*)w->xs, (void*)w->bs,
+                        (void*)w->r32, (void*)w->z32, (void*)w->p32, (void*)w->q32, (void*)w->x32,
+                        (void*)w->partial, (void*)w->sc, (void*)w->flags, (void*)w->dparam, (void*)w->iparam})
+            dfree(c, p);
+        free_pcg(c);
+    }
+    w = new PcgWork();
+    c->pcg = w;
+    w->nrhs = std::max(R, c->max_nrhs);
+    w->n = c->n;
+    const size_t nv = (size_t)c->n * w->nrhs;
+    auto d = [&](size_t b) { return dalloc_bytes(c, b); };
+    w->r = (double*)d(nv * 8);
+    w->z = (double*)d(nv * 8);
+    w->p = (double*)d(nv * 8);
+    w->q = (double*)d(nv * 8);
+    w->xs = (double*)d(nv * 8);
+    w->bs = (double*)d(nv * 8);
+    w->partial = (double*)d((size_t)kDotBlocks * w->nrhs * 8);
+    w->sc = (double*)d((size_t)S_COUNT * w->nrhs * 8);
+    w->flags = (int*)d((size_t)(2 * w->nrhs + 2) * 4);
+    w->dparam = (double*)d(8 * 2);
+    w->iparam = (int*)d(4 * 4);
+    if (!w->dparam || !w->iparam) return BRAS_ERR_OOM;
+    if (cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess) return BRAS_ERR_CUDA;
+    if (cudaMallocHost(&w->h_param, 64) != cudaSuccess) return BRAS_ERR_OOM;
+    if (!w->r || !w->z || !w->p || !w->q || !w->xs || !w->bs || !w->partial || !w->sc || !w->flags) return BRAS_ERR_OOM;
+    if (mixed) {
+        w->r32 = (float*)d(nv * 4);
+        w->z32 = (float*)d(nv * 4);
+        w->p32 = (float*)d(nv * 4);
+        w->q32 = (float*)d(nv * 4);
+        w->x32 = (float*)d(nv * 4);
+        if (!w->r32 || !w->z32 || !w->p32 || !w->q32 || !w->x32) return BRAS_ERR_OOM;
+    }
+    if (cudaMallocHost(&w->h_flags, (2 * w->nrhs + 2) * sizeof(int)) != cudaSuccess) return BRAS_ERR_OOM;
+    if (cudaMallocHost(&w->h_sc, (size_t)S_COUNT * w->nrhs * sizeof(double)) != cudaSuccess) return BRAS_ERR_OOM;
+    return BRAS_OK;
+}
+
+// ---- kernels ---------------------------------------------------------------------------
+// Thread t of a block handles rhs t % R of rows t / R, so every thread sticks to one rhs.
+template <typename TA, typename TB>
+__global__ void k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int64_t n, int R, double* __restrict__ partial) {
+    __shared__ double sh[256];
+    const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
+    double acc = 0.0;
+    if (lr < rows)
+        for (int64_t i = (int64_t)blockIdx.x * rows + lr; i < n; i += (int64_t)gridDim.x * rows)
+            acc += (double)a[i * R + r] * (double)b[i * R + r];
+    sh[tid] = acc;
+    __syncthreads();
+    if (tid < R) {
+        double s = 0.0;
+        for (int k = 0; k < rows; ++k) s += sh[k * R + tid];
+        partial[blockIdx.x * R + tid] = s;
+    }
+}
+
+// x += alpha p; r -= alpha q; partial sums of r.r  (fused, one pass)
+template <typename T>
+__global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
+                            const double* __restrict__ alpha, int64_t n, int R, double* __restrict__ partial) {
+    __shared__ double sh[256];
+    const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
+    double acc = 0.0;
+    if (lr < rows) {
+        const T a = (T)alpha[rr];
+        for (int64_t i = (int64_t)blockIdx.x * rows + lr; i < n; i += (int64_t)gridDim.x * rows) {
+            const int64_t k = i * R + rr;
+            x[k] = fma(a, p[k], x[k]);
+            const T v = fma(-a, q[k], r[k]);
+            r[k] = v;
+            acc += (double)v * (double)v;
+        }
+    }
+    sh[tid] = acc;
+    __syncthreads();
+    if (tid < R) {
+        double s = 0.0;
+        for (int k = 0; k < rows; ++k) s += sh[k * R + tid];
+        partial[blockIdx.x * R + tid] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma((T)beta[i % R], p[i], z[i]);
+}
+
+template <typename T>
+__global__ void k_jacobi(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ diag, int64_t nv, int R) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] / diag[i / R];
+}
+
+// r32 = (float)(r64 * s_r)   and   x64 += (double)d32 / s_r   and   r = b - q
+__global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ s,
+                               int64_t nv, int R) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        r32[i] = (float)(r[i] * s[i % R]);
+}
+__global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ s,
+                            int64_t nv, int R) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const double sr = s[i % R];
+        if (sr > 0.0) x[i] += (double)d[i] / sr;
+    }
+}
+__global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q, int64_t nv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = b[i] - q[i];
+}
+
+// Per-rhs scalar updates from the partial sums (one thread per rhs, fixed summation order).
+__global__ void k_fin(int kind, const double* __restrict__ partial, int G, int R, double* __restrict__ sc,
+                      int* __restrict__ flags, const double* __restrict__ dparam, int* __restrict__ iparam,
+                      cudaGraphConditionalHandle cond) {
+    const double tol2 = dparam ? dparam[0] : 0.0;
+    const int r = threadIdx.x;
+    if (r < R) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += partial[g * R + r];
+        int* active = flags;
+        int* its = flags + R;
+        switch (kind) {
+            case FIN_INIT_RR:
+                sc[S_RR0 * R + r] = s;
+                sc[S_RR * R + r] = s;
+                active[r] = s > 0.0 ? 1 : 0;
+                its[r] = 0;
+                break;
+            case FIN_INIT_RZ:
+                sc[S_RZ * R + r] = s;
+                break;
+            case FIN_ALPHA: {
+                sc[S_PQ * R + r] = s;
+                double a = 0.0;
+                if (active[r]) {
+                    if (!(s > 0.0) || !isfinite(s)) {
+                        active[r] = 0;
+                        flags[2 * R + 1] = BRAS_ERR_BREAKDOWN;
+                    } else {
+                        a = sc[S_RZ * R + r] / s;
+                    }
+                }
+                sc[S_ALPHA * R + r] = a;
+                break;
+            }
+            case FIN_RR:
+                sc[S_RR * R + r] = s;
+                if (active[r]) {
+                    its[r] += 1;
+                    if (s <= tol2 * sc[S_RR0 * R + r]) active[r] = 0;
+                }
+                break;
+            case FIN_BETA: {   // beta = 0 on the first iteration (p = z)
+                double bta = 0.0;
+                if (active[r]) {
+                    bta = its[r] == 0 ? 0.0 : s / sc[S_RZ * R + r];
+                    sc[S_RZ * R + r] = s;
+                }
+                sc[S_BETA * R + r] = bta;
+                break;
+            }
+            case FIN_NORM:
+                sc[S_RR * R + r] = s;
+                break;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int k = 0; k < R; ++k) cnt += flags[k];
+        flags[2 * R] = cnt;
+        if (kind == FIN_RR && iparam) {
+            const int done = ++iparam[1];
+            cudaGraphSetConditional(cond, (cnt > 0 && done < iparam[0]) ? 1u : 0u);
+        }
+    }
+}
+
+// ---- host helpers ------------------------------------------------------------------------
+static int grid_for(int64_t nv) { return (int)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 148 * 8)); }
+
+template <typename TA, typename TB>
+static cudaError_t dot(PcgWork* w, const TA* a, const TB* b, int64_t n, int R, int kind, cudaStream_t st) {
+    k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, n, R, w->partial);
+    k_fin<<<1, 256, 0, st>>>(kind, w->partial, kDotBlocks, R, w->sc, w->flags, w->dparam, nullptr, 0);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t jacobi_launch(const bras_ctx* c, int prec, const void* x, void* y, int nrhs, cudaStream_t st) {
+    const int64_t nv = c->n * nrhs;
+    if (prec == BRAS_FP64)
+        k_jacobi<double><<<grid_for(nv), 256, 0, st>>>((const double*)x, (double*)y, c->diag64, nv, nrhs);
+    else
+        k_jacobi<float><<<grid_for(nv), 256, 0, st>>>((const float*)x, (float*)y, c->diag32, nv, nrhs);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static int precond(bras_ctx* c, int pc, int prec, const T* r, T* z, int R, cudaStream_t st) {
+    if (pc == BRAS_PC_BRAS) return run_op(c, prec, OP_BRAS, r, z, R, st);
+    if (pc == BRAS_PC_JACOBI) return jacobi_launch(c, prec, r, z, R, st) == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
+    return cudaMemcpyAsync(z, r, sizeof(T) * c->n * R, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? BRAS_OK
+                                                                                                   : BRAS_ERR_CUDA;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        if ((x) != cudaSuccess) return BRAS_ERR_CUDA; \
+    } while (0)
+#define RC(x)                         \
+    do {                              \
+        int _rc = (x);                \
+        if (_rc != BRAS_OK) return _rc; \
+    } while (0)
+
+// One CG iteration (the body of the device-side while loop), enqueued on `st`:
+//   z = Pr; beta = (r,z)/(r,z)_old (0 on the first pass); p = z + beta p;
+//   q = M p; alpha = (r,z)/(p,q); x += alpha p; r -= alpha q; (r,r) -> convergence masks,
+// and the loop condition (some rhs still active and fewer than maxit iterations).
+template <typename T>
+static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T* p, T* q, int R,
+                             cudaGraphConditionalHandle cond, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    const int64_t n = c->n, nv = n * R;
+    RC(precond(c, pc, prec, r, z, R, st));
+    CK(dot(w, r, z, n, R, FIN_BETA, st));
+    k_update_p<T><<<grid_for(nv), 256, 0, st>>>(p, z, w->sc + S_BETA * R, nv, R);
+    count_launch(1);
+    RC(run_op(c, prec, OP_MASS, p, q, R, st));
+    CK(dot(w, p, q, n, R, FIN_ALPHA, st));
+    k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * R, n, R, w->partial);
+    k_fin<<<1, 256, 0, st>>>(FIN_RR, w->partial, kDotBlocks, R, w->sc, w->flags, w->dparam, w->iparam, cond);
+    count_launch(2);
+    CK(cudaGetLastError());
+    return BRAS_OK;
+}
+
+// The whole CG loop as one graph: a conditional WHILE node (default value 1 at every launch)
+// whose body is one iteration; the residual-check kernel sets the condition on the device,
+// so a solve costs one graph launch and one host synchronisation.  Graphs are cached per
+// (precision, preconditioner, nrhs, value type, buffers) and rebuilt if buffers change.
+template <typename T>
+static int get_graph(bras_ctx* c, int prec, int pc, int R, T* x, T* r, T* z, T* p, T* q, cudaGraphExec_t* out,
+                     int* kernels_per_iter) {
+    PcgWork* w = c->pcg;
+    for (auto& g : w->graphs)
+        if (g.prec == prec && g.pc == pc && g.R == R && g.tsize == (int)sizeof(T) && g.x == x && g.part == c->part) {
+            *out = g.exec;
+            *kernels_per_iter = g.kernels_per_iter;
+            return BRAS_OK;
+        }
+    SolveGraph g;
+    g.prec = prec;
+    g.pc = pc;
+    g.R = R;
+    g.tsize = (int)sizeof(T);
+    g.x = x;
+    g.part = c->part;
+    CK(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const int64_t before = launches_so_far();
+    int rc = enqueue_iteration<T>(c, prec, pc, x, r, z, p, q, R, cond, w->cap);
+    g.kernels_per_iter = (int)(launches_so_far() - before);
+    count_launch(-g.kernels_per_iter);      // captured, not launched
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(w->cap, &captured);
+    if (rc != BRAS_OK || ec != cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        cudaGetLastError();
+        return rc != BRAS_OK ? rc : BRAS_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        return BRAS_ERR_CUDA;
+    }
+    w->graphs.push_back(g);
+    *out = g.exec;
+    *kernels_per_iter = g.kernels_per_iter;
+    return BRAS_OK;
+}
+
+// PCG on M x = b (b on the device, type T); x starts at 0.  Per-rhs iteration counts land in
+// w->flags[R..2R), squared residual norms in w->sc[S_RR], [S_RR0].
+template <typename T>
+static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z, T* p, T* q, int R, double rtol,
+                    int maxit, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    const int64_t n = c->n, nv = n * R;
+    cudaGraphExec_t exec = nullptr;
+    int kpi = 0;
+    RC(get_graph<T>(c, prec, pc, R, x, r, z, p, q, &exec, &kpi));
+    w->h_param[0] = rtol * rtol;
+    int* hp = reinterpret_cast<int*>(w->h_param + 1);
+    hp[0] = maxit;
+    hp[1] = 0;
+    CK(cudaMemcpyAsync(w->dparam, w->h_param, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->iparam, hp, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(x, 0, sizeof(T) * nv, st));
+    CK(cudaMemsetAsync(p, 0, sizeof(T) * nv, st));
+    CK(cudaMemcpyAsync(r, b, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w->flags + 2 * R + 1, 0, sizeof(int), st));
+    CK(dot(w, r, r, n, R, FIN_INIT_RR, st));
+    if (maxit > 0) CK(cudaGraphLaunch(exec, st));
+    CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * R + 2), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp, w->iparam, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (maxit > 0) count_launch(kpi * hp[1]);
+    if (w->h_flags[2 * R + 1] != 0) return w->h_flags[2 * R + 1];
+    return w->h_flags[2 * R] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
+}
+
+static bool host_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* b, double* x, int R, double rtol,
+                   int maxit, int* iters, double* relres, cudaStream_t st) {
+    if (R > kMaxRhs) return BRAS_ERR_TOO_LARGE;
+    const bool mixed = mode == BRAS_SOLVE_MIXED;
+    RC(ensure_pcg(c, R, mixed));
+    RC(ensure_part(c, R));
+    PcgWork* w = c->pcg;
+    const int64_t n = c->n, nv = n * R;
+    const bool hb = host_ptr(b), hx = host_ptr(x);
+    const double* db = b;
+    double* dx = x;
+    if (hb) {
+        CK(cudaMemcpyAsync(w->bs, b, sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+        db = w->bs;
+    }
+    if (hx) dx = w->xs;
+    int status = BRAS_OK;
+    std::vector<int> its(R, 0);
+    std::vector<double> rel(R, 0.0);
+    if (!mixed) {
+        status = pcg_core<double>(c, BRAS_FP64, pc, db, w->xs, w->r, w->z, w->p, w->q, R, rtol, maxit, st);
+        if (status < 0) return status;
+        if (dx != w->xs) CK(cudaMemcpyAsync(dx, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+        for (int r = 0; r < R; ++r) {
+            its[r] = w->h_flags[R + r];
+            const double rr0 = w->h_sc[S_RR0 * R + r];
+            rel[r] = rr0 > 0 ? std::sqrt(w->h_sc[S_RR * R + r] / rr0) : 0.0;
+        }
+    } else {
+        // x = 0, r = b; ||b||
+        CK(cudaMemsetAsync(dx, 0, sizeof(double) * nv, st));
+        CK(cudaMemcpyAsync(w->r, db, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+        CK(dot(w, db, db, n, R, FIN_NORM, st));
+        CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<double> bn(R), rn(R), scale(R);
+        for (int r = 0; r < R; ++r) { bn[r] = std::sqrt(w->h_sc[r]); rn[r] = bn[r]; }
+        int total_inner = 0;
+        bool done = false;
+        for (int outer = 0; outer < 60 && !done; ++outer) {
+            double worst = 0.0;
+            for (int r = 0; r < R; ++r) {
+                rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+                worst = std::max(worst, rel[r]);
+                scale[r] = (bn[r] > 0 && rel[r] > rtol) ? 1.0 / rn[r] : 0.0;
+            }
+            if (worst <= rtol) { done = true; break; }
+            if (total_inner >= maxit) break;
+            // inner tolerance: as deep as FP32 allows, no deeper than needed
+            const double tin = std::max(1e-6, std::min(1e-2, 0.5 * rtol / worst));
+            CK(cudaMemcpyAsync(w->sc + S_SCALE * R, scale.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+            k_scale_to_f32<<<grid_for(nv), 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * R, nv, R); count_launch(1);
+            CK(cudaGetLastError());
+            int s = pcg_core<float>(c, inner_prec, pc, w->r32, w->x32, w->q32 /*r*/, w->z32, w->p32,
+                                    reinterpret_cast<float*>(w->z) /*q*/, R, tin, maxit - total_inner, st);
+            if (s < 0) return s;
+            int mx = 0;
+            for (int r = 0; r < R; ++r) { its[r] += w->h_flags[R + r]; mx = std::max(mx, w->h_flags[R + r]); }
+            total_inner += std::max(mx, 1);
+            k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * R, nv, R); count_launch(1);
+            RC(run_op(c, BRAS_FP64, OP_MASS, dx, w->q, R, st));
+            k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv); count_launch(1);
+            CK(dot(w, w->r, w->r, n, R, FIN_NORM, st));
+            CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int r = 0; r < R; ++r) rn[r] = std::sqrt(w->h_sc[r]);
+        }
+        double worst = 0.0;
+        for (int r = 0; r < R; ++r) {
+            rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+            worst = std::max(worst, rel[r]);
+        }
+        status = worst <= rtol ? BRAS_OK : BRAS_NOT_CONVERGED;
+    }
+    if (hx) CK(cudaMemcpyAsync(x, dx, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) {
+        if (iters) iters[r] = its[r];
+        if (relres) relres[r] = rel[r];
+    }
+    return status;
+}
+
+}  // namespace bras

@@ -1,0 +1,40 @@
+"""The C-ABI library loads without a GPU and exports every function include/bras.h declares."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2607_12138_b300", "libbras.so")
+HEADER = os.path.join(ROOT, "include", "bras.h")
+
+
+def _declared():
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(bras_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_header_symbols():
+    if not os.path.exists(LIB):
+        from paper_2607_12138_b300 import build
+        build.build()
+    lib = ctypes.CDLL(LIB)
+    names = _declared()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points():
+    lib = ctypes.CDLL(LIB)
+    lib.bras_n_local.restype = ctypes.c_int
+    assert [lib.bras_n_local(3, 0, p) for p in (1, 2, 3, 4)] == [4, 10, 20, 35]
+    assert [lib.bras_n_local(2, 0, p) for p in (1, 2, 3, 4)] == [3, 6, 10, 15]
+    assert [lib.bras_n_local(3, 1, k) for k in (1, 2, 3)] == [6, 20, 45]
+    assert [lib.bras_n_local(3, 2, k) for k in (1, 2, 3)] == [4, 15, 36]
+    assert lib.bras_n_local(2, 1, 1) == -1 and lib.bras_n_local(3, 0, 5) == -1
+    lib.bras_status_string.restype = ctypes.c_char_p
+    assert lib.bras_status_string(-5) == b"local mass matrix not SPD"
+    out = ctypes.c_void_p(1)
+    # invalid arguments are rejected before any device work
+    assert lib.bras_setup(ctypes.byref(out), 4, 0, 1, 0, None, 0, None, 0, None, None, None, None, None) == -1
+    assert out.value is None

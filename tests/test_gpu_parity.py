@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (max-abs error / max-abs of the oracle result):
+  * FP64 applies: 1e-12 (the FP64 target); both sides round the same exact operator, so
+    they differ by about cond(M_K) * 1e-16.
+  * FP32 applies: 2e-5 for H1, 1e-4 for H(curl)/H(div) (FP32 storage of local inverses
+    with cond up to ~1e4 and sums of up to 45 terms, each rounded at 6e-8).
+  * bf16-stored inverses: 2e-2 (8-bit mantissa, 4e-3 per entry, plus the SPD repair shift).
+Solves are checked by iteration count (oracle +-1) and by the oracle's own FP64 residual of
+the GPU solution (<= the requested 1e-10).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gradient as ograd
+from oracle import sampled
+from oracle.assembly import Problem, element_matrices
+from oracle.solvers import pcg
+from paper_2607_12138_b300 import meshgen as mg
+
+from _cases import SMALL_CASES, build, cube, rel_err
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2607_12138_b300 import bras as B
+
+_PROBLEMS = {}
+
+
+def _setup(case, **kw):
+    key = (case, tuple(sorted(kw.items())))
+    if key not in _PROBLEMS:
+        mesh, space, order, n, l2g, signs = build(case)
+        pr = Problem(mesh, space, order, l2g, signs, n)
+        ctx = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs, **kw)
+        _PROBLEMS[key] = (mesh, pr, ctx)
+    return _PROBLEMS[key]
+
+
+def _vec(n, nrhs=1, seed=5, dtype=torch.float64):
+    x = mg.rhs(n, nrhs, seed=seed)
+    return x, torch.as_tensor(x, dtype=dtype, device="cuda")
+
+
+TOL32 = {"h1": 2e-5, "hcurl": 1e-4, "hdiv": 1e-4}
+
+
+@pytest.mark.parametrize("case", sorted(SMALL_CASES))
+def test_fp64_applies(case):
+    mesh, pr, ctx = _setup(case)
+    x, xt = _vec(pr.n_dof)
+    assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
+    assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr.diag) <= 1e-12
+
+
+@pytest.mark.parametrize("case", sorted(SMALL_CASES))
+def test_fp32_and_bf16_applies(case):
+    mesh, pr, ctx = _setup(case)
+    space = SMALL_CASES[case][1]
+    x, xt = _vec(pr.n_dof, dtype=torch.float32)
+    assert rel_err(ctx.mass_apply(xt, B.FP32).cpu(), pr.M @ x) <= TOL32[space]
+    assert rel_err(ctx.bras_apply(xt, B.FP32).cpu(), pr.B @ x) <= TOL32[space]
+    assert rel_err(ctx.jacobi_apply(xt, B.FP32).cpu(), x / pr.diag) <= 1e-6
+    assert rel_err(ctx.bras_apply(xt, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space != "h1" else TOL32[space])
+
+
+@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2"])
+@pytest.mark.parametrize("nrhs", [3, 8])
+def test_multi_rhs_interleaved(case, nrhs):
+    mesh, pr, ctx = _setup(case)
+    x, xt = _vec(pr.n_dof, nrhs)
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
+    assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr.diag[:, None]) <= 1e-12
+
+
+@pytest.mark.parametrize("case", ["3d_p4", "hcurl3"])
+def test_bit_reproducible(case):
+    mesh, pr, ctx = _setup(case)
+    _, xt = _vec(pr.n_dof)
+    for prec, dt in ((B.FP64, torch.float64), (B.FP32, torch.float32)):
+        a = ctx.bras_apply(xt.to(dt), prec)
+        b = ctx.bras_apply(xt.to(dt), prec)
+        assert torch.equal(a, b)
+        assert torch.equal(ctx.mass_apply(xt.to(dt), prec), ctx.mass_apply(xt.to(dt), prec))
+
+
+@pytest.mark.parametrize("block_elems", [32, 100])
+def test_small_blocks_and_single_cell(block_elems):
+    mesh, pr, ctx = _setup("3d_p3", block_elems=block_elems)
+    x, xt = _vec(pr.n_dof)
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
+    one = mg.single_simplex_mesh(3, seed=4)
+    n, l2g, s = mg.dof_map(one, "hcurl", 3)
+    p1 = Problem(one, "hcurl", 3, l2g, s, n)
+    c1 = B.Context(one.coords, one.cells, "hcurl", 3, n, l2g, s)
+    x = mg.rhs(n, 1, seed=2)
+    y = c1.bras_apply(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    assert rel_err(y, np.linalg.solve(p1.M.toarray(), x)) <= 1e-12   # one cell: BRAS = M^{-1}
+
+
+@pytest.mark.parametrize("case,pc", [("c1_2d_p2", 2),
+                                     ("c1_2d_p2", 1), ("3d_p2", 2), ("hcurl2", 2), ("hdiv2", 2), ("hcurl1_signed", 1)])
+def test_pcg_fp64_iterations_and_residual(case, pc):
+    mesh, pr, ctx = _setup(case)
+    b, bt = _vec(pr.n_dof, seed=1)
+    x, its, rel, st = ctx.pcg_solve(bt, pc=pc, mode=B.SOLVE_FP64, rtol=1e-10)
+    assert st == B.OK
+    pre = pr.bras_apply if pc == 2 else pr.jacobi_apply
+    _, its_o, _ = pcg(pr.mass_apply, b, pre, rtol=1e-10)
+    assert abs(int(its[0]) - its_o) <= 1
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(b - pr.M @ xg) <= 1.05e-10 * np.linalg.norm(b)
+
+
+def test_pcg_fixed_iterations_match_oracle_iterates():
+    mesh, pr, ctx = _setup("3d_p2")
+    b, bt = _vec(pr.n_dof, seed=1)
+    for K in (1, 5, 10):
+        x, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_FP64, rtol=0.0, maxit=K)
+        assert st == B.NOT_CONVERGED and its[0] == K
+        xo, _, _ = pcg(pr.mass_apply, b, pr.bras_apply, max_its=K)
+        assert rel_err(x.cpu(), xo) <= 1e-12 * K
+
+
+@pytest.mark.parametrize("case,inner", [("c1_2d_p2", 1), ("3d_p3", 1), ("hcurl3", 1), ("hcurl3", 2), ("hdiv3", 2)])
+def test_pcg_mixed_refinement_reaches_fp64_residual(case, inner):
+    mesh, pr, ctx = _setup(case)
+    b, bt = _vec(pr.n_dof, seed=1)
+    x, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, inner_precision=inner, rtol=1e-10)
+    assert st == B.OK
+    xg = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - pr.M @ xg) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 and abs(true_rel - rel[0]) <= 1e-3 * 1e-10 + 1e-6 * true_rel
+
+
+def test_pcg_multi_rhs_and_host_buffers():
+    mesh, pr, ctx = _setup("3d_p2")
+    b, bt = _vec(pr.n_dof, 4, seed=1)
+    x, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, rtol=1e-10)
+    assert st == B.OK
+    for r in range(4):
+        _, its_o, _ = pcg(pr.mass_apply, b[:, r], pr.bras_apply, rtol=1e-10)
+        assert abs(int(its[r]) - its_o) <= 1
+        assert np.linalg.norm(b[:, r] - pr.M @ x.cpu().numpy()[:, r]) <= 1.05e-10 * np.linalg.norm(b[:, r])
+    bh = torch.as_tensor(b)                               # host buffers through the same call
+    xh, its_h, rel_h, st_h = ctx.pcg_solve(bh, pc=B.PC_BRAS, rtol=1e-10)
+    assert st_h == B.OK and xh.device.type == "cpu"
+    assert torch.equal(xh, x.cpu()) and np.array_equal(its_h, its)
+    xm, its_m, rel_m, st_m = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
+    assert st_m == B.OK and rel_m.max() <= 1e-10
+
+
+def test_gradient_and_weight_update():
+    mesh = cube(3, 0.1)
+    n, l2g, s = mg.dof_map(mesh, "h1", 3)
+    z = np.random.default_rng(2).normal(0, 0.5, mesh.n_cell)
+    rho = np.exp(z)
+    ctx = B.Context(mesh.coords, mesh.cells, "h1", 3, n, l2g, s, rho=rho)
+    x = mg.rhs(n, 1, seed=3)
+    lam = mg.rhs(n, 1, seed=4)
+    g = ctx.grad_rho(torch.as_tensor(x, device="cuda"), torch.as_tensor(lam, device="cuda")).cpu().numpy()
+    Me1 = element_matrices(mesh.coords, mesh.cells, "h1", 3)
+    assert rel_err(g, ograd.rho_bar(Me1, l2g, s, x, lam)) <= 1e-12
+    rho2 = np.exp(-z)
+    ctx.update_rho(rho2)
+    pr2 = Problem(mesh, "h1", 3, l2g, s, n, rho2)
+    xt = torch.as_tensor(x, device="cuda")
+    assert rel_err(ctx.mass_apply(xt).cpu(), pr2.M @ x) <= 1e-12
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr2.B @ x) <= 1e-12
+    assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr2.diag) <= 1e-12
+
+
+def test_error_codes():
+    mesh = cube(2)
+    n, l2g, s = mg.dof_map(mesh, "h1", 2)
+    bad = l2g.copy()
+    bad[3, 4] = n
+    with pytest.raises(B.BrasError) as e:
+        B.Context(mesh.coords, mesh.cells, "h1", 2, n, bad)
+    assert e.value.code == -2 and e.value.detail == 3 * 10 + 4
+    with pytest.raises(B.BrasError) as e:
+        B.Context(mesh.coords, mesh.cells, "h1", 2, n + 1, l2g)
+    assert e.value.code == -3 and e.value.detail == n
+    flat = mesh.coords.copy()
+    flat[mesh.cells[5]] = flat[mesh.cells[5][0]]                  # collapse cell 5
+    with pytest.raises(B.BrasError) as e:
+        B.Context(flat, mesh.cells, "h1", 2, n, l2g)
+    assert e.value.code == -4
+    with pytest.raises(B.BrasError) as e:
+        B.Context(mesh.coords, mesh.cells, "h1", 2, n, l2g, rho=-np.ones(mesh.n_cell))
+    assert e.value.code == -4
+    n1, l1, s1 = mg.dof_map(mesh, "hcurl", 1)
+    s1 = s1.copy()
+    s1[0, 0] = 0
+    with pytest.raises(B.BrasError) as e:
+        B.Context(mesh.coords, mesh.cells, "hcurl", 1, n1, l1, s1)
+    assert e.value.code == -1
+    ctx = B.Context(mesh.coords, mesh.cells, "hcurl", 1, n1, l1, precisions=1)
+    with pytest.raises(B.BrasError) as e:
+        ctx.bras_apply(torch.zeros(n1, dtype=torch.float32, device="cuda"), B.FP32)
+    assert e.value.code == -9
+
+
+FULL = {
+    "c2_p2": (48, "h1", 2),
+    "c2_p4": (48, "h1", 4),
+    "c3_k3": (40, "hcurl", 3),
+}
+
+
+@pytest.mark.parametrize("key", sorted(FULL))
+def test_full_size_sampled_parity(key):
+    """Full-size meshes in the launch configuration of the benchmark; 200 sampled dofs are
+    computed one at a time by the oracle."""
+    ncell, space, order = FULL[key]
+    mesh = cube(ncell, 0.15, seed=0)
+    n, l2g, s = mg.dof_map(mesh, space, order)
+    ctx = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, s)
+    x = mg.rhs(n, 1, seed=1)
+    xt = torch.as_tensor(x, device="cuda")
+    dofs = np.random.default_rng(3).choice(n, 200, replace=False)
+    yb = ctx.bras_apply(xt).cpu().numpy()[dofs]
+    ym = ctx.mass_apply(xt).cpu().numpy()[dofs]
+    ob = sampled.bras_apply_at(mesh, space, order, l2g, s, n, x, dofs)
+    om = sampled.mass_apply_at(mesh, space, order, l2g, s, n, x, dofs)
+    assert rel_err(yb, ob) <= 1e-12 and rel_err(ym, om) <= 1e-12
+    y32 = ctx.bras_apply(xt.float(), B.FP32).cpu().numpy()[dofs]
+    assert rel_err(y32, ob) <= TOL32[space]
+
+
+def test_autograd_weighted_solve():
+    """x = M(exp z)^{-1} b as a torch.autograd.Function: gradients against the oracle's exact
+    adjoint gradient and against central differences of the GPU loss (h = 1e-6, FP64)."""
+    from paper_2607_12138_b300.autograd import WeightedMassSolver
+    mesh = cube(3, 0.1)
+    n, l2g, s = mg.dof_map(mesh, "h1", 3)
+    rng = np.random.default_rng(2)
+    z0 = rng.normal(0, 0.5, mesh.n_cell)
+    b0 = mg.rhs(n, 1, seed=1)
+    xs0 = mg.rhs(n, 1, seed=3)
+    solver = WeightedMassSolver(mesh.coords, mesh.cells, 3, n, l2g, rtol=1e-14)
+    z = torch.tensor(z0, device="cuda", requires_grad=True)
+    b = torch.tensor(b0, device="cuda", requires_grad=True)
+    xs = torch.tensor(xs0, device="cuda")
+    x = solver(z, b)
+    loss = 0.5 * ((x - xs) ** 2).sum()
+    loss.backward()
+    L_o, bbar_o, zbar_o, _ = ograd.loss_and_grad(mesh, "h1", 3, l2g, s, n, z0, b0, xs0)
+    assert abs(loss.item() - L_o) <= 1e-11 * abs(L_o)
+    assert rel_err(z.grad.cpu(), zbar_o) <= 1e-9
+    assert rel_err(b.grad.cpu(), bbar_o) <= 1e-9
+    h = 1e-6
+    with torch.no_grad():
+        for trial in range(3):
+            v = torch.tensor(rng.standard_normal(mesh.n_cell), device="cuda")
+            lp = 0.5 * ((solver(z + h * v, b) - xs) ** 2).sum().item()
+            lm = 0.5 * ((solver(z - h * v, b) - xs) ** 2).sum().item()
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - (z.grad @ v).item()) <= 1e-6 * max(1.0, abs(fd))
