@@ -127,6 +127,27 @@ int bras_mass_apply(const bras_ctx* ctx, int precision, const void* x, void* y, 
 int bras_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
                void* stream);
 
+/* bras_apply_noalloc -- the same y = M_bras^{-1} x as bras_apply (the paper has no
+ * counterpart: this is a memory-management variant of this library), for callers that must
+ * not have the library allocate device memory: code that owns all device memory through its
+ * own pool or caching allocator, loops where the implicit synchronisation of cudaMalloc is not
+ * acceptable, or a process with a device-memory budget fixed up front.  bras_apply may grow
+ * its workspace on a call with a larger nrhs; this call never allocates or frees anything
+ * (no cudaMalloc, no cudaFree, no allocating library routine).
+ *   Scratch: the partial sums of cell-block boundary dofs go to one fixed 16 MiB array in
+ *   device memory, part of the library image, which every GPU that loads the library keeps
+ *   until the process exits.  A call whose partials (ctx's boundary partial count x nrhs x
+ *   element size) exceed 16 MiB returns BRAS_ERR_TOO_LARGE (detail = bytes it would need)
+ *   and launches nothing.
+ *   The first call on a device looks the array's device address up (once per device, with
+ *   that device current); make that first call before any stream capture on the device.
+ *   All calls share the array and it keeps the last call's contents; nothing in it needs to
+ *   start at zero.  Calls that may overlap on the GPU (on different streams, or different
+ *   contexts at the same time) race on the array: order them on one stream.
+ * Arguments, precisions and errors are those of bras_apply. */
+int bras_apply_noalloc(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
+                       void* stream);
+
 /* bras_jacobi_apply -- y = diag(M)^{-1} x  (Sec. 2.1).  Same argument rules. */
 int bras_jacobi_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
                       void* stream);

@@ -52,7 +52,7 @@ _lib.bras_setup.argtypes = [ctypes.POINTER(_vp), _int, _int, _int, _i64, _vp, _i
 _lib.bras_setup.restype = _int
 _lib.bras_n_local.argtypes = [_int, _int, _int]
 _lib.bras_n_local.restype = _int
-for _name in ("bras_mass_apply", "bras_apply", "bras_jacobi_apply"):
+for _name in ("bras_mass_apply", "bras_apply", "bras_apply_noalloc", "bras_jacobi_apply"):
     getattr(_lib, _name).argtypes = [_vp, _int, _vp, _vp, _int, _vp]
     getattr(_lib, _name).restype = _int
 _lib.bras_pcg_solve.argtypes = [_vp, _int, _int, _int, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
@@ -126,6 +126,12 @@ def bras_mass_apply(ctx, precision, x, y, nrhs=1, stream=None):
 
 def bras_apply(ctx, precision, x, y, nrhs=1, stream=None):
     return _check(_lib.bras_apply(ctx, precision, _ptr(x), _ptr(y), nrhs, _stream(stream)), "bras_apply")
+
+
+def bras_apply_noalloc(ctx, precision, x, y, nrhs=1, stream=None):
+    """bras_apply without any device allocation (fixed library-owned scratch; see bras.h)."""
+    return _check(_lib.bras_apply_noalloc(ctx, precision, _ptr(x), _ptr(y), nrhs, _stream(stream)),
+                  "bras_apply_noalloc")
 
 
 def bras_jacobi_apply(ctx, precision, x, y, nrhs=1, stream=None):
