@@ -149,26 +149,45 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     for (size_t i = 0; i < h_signs.size(); ++i)
         if (h_signs[i] != 1 && h_signs[i] != -1) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
 
+    // Block size: the largest multiple of 32 (<= BE) whose FP64 kernel fits the device's
+    // shared memory and, unless the caller fixed it, whose FP32 kernel fits twice per SM.
+    int smem_optin = 0, smem_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const bool fixed_be = opt && opt->block_elems;
     HostTables t;
     int64_t detail = -1;
-    rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
-                      h_cells.data(), dim, BE, &t, &detail);
-    if (rc) { set_detail(detail); return rc; }
+    for (;;) {
+        rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
+                          h_cells.data(), dim, BE, &t, &detail);
+        if (rc) { set_detail(detail); return rc; }
+        const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
+        const size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
+        const bool fits = s64 <= (size_t)smem_optin && (fixed_be || 2 * (s32 + 1024) <= (size_t)smem_sm);
+        if (fits || BE <= 32) {
+            if (s64 > (size_t)smem_optin) return BRAS_ERR_TOO_LARGE;
+            break;
+        }
+        BE = std::max(32, (BE - 32) & ~31);
+    }
+    c->BE = BE;
     c->nblk = t.nblk;
     c->max_u = t.max_u;
     c->max_ne = t.max_ne;
-    c->U_tot = (int64_t)t.ids.size();
+    c->U_tot = t.U_tot;
     c->npart = t.npart;
     c->nsh = (int64_t)t.sh_ids.size();
+    c->max_pkt = t.max_pkt;
     if ((rc = upload(c, &c->perm, t.perm.data(), t.perm.size()))) return rc;
     if ((rc = upload(c, &c->blk_e0, t.blk_e0.data(), t.blk_e0.size()))) return rc;
     if ((rc = upload(c, &c->blk_u0, t.blk_u0.data(), t.blk_u0.size()))) return rc;
     if ((rc = upload(c, &c->blk_nint, t.blk_nint.data(), t.blk_nint.size()))) return rc;
     if ((rc = upload(c, &c->blk_p0, t.blk_p0.data(), t.blk_p0.size()))) return rc;
-    if ((rc = upload(c, &c->ids, t.ids.data(), t.ids.size()))) return rc;
-    if ((rc = upload(c, &c->incoff, t.incoff.data(), t.incoff.size()))) return rc;
-    if ((rc = upload(c, &c->loc, t.loc.data(), t.loc.size()))) return rc;
-    if ((rc = upload(c, &c->inc, t.inc.data(), t.inc.size()))) return rc;
+    if ((rc = upload(c, &c->blk_pkt, t.blk_pkt.data(), t.blk_pkt.size()))) return rc;
+    if ((rc = upload(c, &c->pkt, t.pkt.data(), t.pkt.size()))) return rc;
+    if (!(c->status = dalloc<int>(c, 1))) return BRAS_ERR_OOM;
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return BRAS_ERR_CUDA;
     if ((rc = upload(c, &c->sh_ids, t.sh_ids.data(), t.sh_ids.size()))) return rc;
     if ((rc = upload(c, &c->sh_off, t.sh_off.data(), t.sh_off.size()))) return rc;
     if ((rc = upload(c, &c->sh_slots, t.sh_slots.data(), t.sh_slots.size()))) return rc;
@@ -268,6 +287,13 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
 
 }  // namespace
 
+size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int max_u, int max_ne) {
+    const int w = tsize == 4 ? 4 : 2;
+    const size_t npad = (size_t)((nloc + w - 1) / w * w);
+    return 128 + ((max_pkt + 127u) & ~127u) +
+           (size_t)tsize * (((size_t)max_u + 3) / 4 * 4 + ((size_t)nloc * max_ne + 3) / 4 * 4 + (h1 ? nloc * npad : 0));
+}
+
 int ensure_part(bras_ctx* c, int nrhs) {
     size_t need = (size_t)std::max<int64_t>(c->npart, 1) * nrhs * sizeof(double);
     if (need <= c->part_bytes) return BRAS_OK;
@@ -285,16 +311,16 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.blk_u0 = c->blk_u0;
     A.blk_nint = c->blk_nint;
     A.blk_p0 = c->blk_p0;
-    A.ids = c->ids;
-    A.incoff = c->incoff;
-    A.loc = c->loc;
-    A.inc = c->inc;
+    A.blk_pkt = c->blk_pkt;
+    A.pkt = c->pkt;
+    A.status = c->status;
     A.Epad = c->Epad;
     A.npart = c->npart;
     A.max_u = c->max_u;
     A.max_ne = c->max_ne;
+    A.max_pkt = c->max_pkt;
     const bool f64 = prec == BRAS_FP64;
-    A.dinv = f64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
+    L.dinv = f64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
     if (c->space == BRAS_H1) {
         if (op == OP_BRAS) {
             A.refmat = f64 ? (const void*)c->Minvref64 : (const void*)c->Minvref32;

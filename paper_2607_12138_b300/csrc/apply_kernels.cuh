@@ -1,12 +1,18 @@
 // Block-fused element kernels: signed gather -> local dense multiply -> scatter.
 //
 // One CUDA thread block per cell block (up to 256 cells, one thread per cell):
-//   1. stage the block's dofs in shared memory, x_s[u] = x[ids[u]] (times 1/d for BRAS:
+//   0. one thread issues two bulk asynchronous copies (TMA, cp.async.bulk) of the block's
+//      contiguous table packet into shared memory: part A (dof ids, multiplicities,
+//      incidence offsets) and part B (local indices with signs, incidence lists), each
+//      completing on its own mbarrier, so no table load sits on a dependent-latency chain;
+//   1. stage the block's dofs in shared memory, x_s[u] = x[ids[u]] (times 1/d_u for BRAS:
 //      the right factor D^{-1} of Eq. mhatinvbras_def);
 //   2. each thread gathers its cell's local vector with the signs of P (the injection P_K of
 //      Sec. 2.2) and multiplies by the local matrix in registers:
 //        H1 (affine):   z_K = c_K * A_ref x_K, A_ref = M_ref (mass) or M_ref^{-1} (BRAS),
 //                       c_K = rho_K |det J_K| or its reciprocal (Eq. piola_mass_pullbacks);
+//                       A_ref sits in shared memory with 16-byte rows, read as 16-byte
+//                       broadcasts;
 //        H(curl)/H(div): z_K = A_K x_K with A_K = M_K or M_K^{-1} streamed per cell as a
 //                       packed symmetric matrix in a cell-interleaved layout (coalesced);
 //   3. the signed local results go to shared memory, and every block-local dof sums its
@@ -18,6 +24,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "packet.h"
+
 namespace bras {
 
 void count_launch(int k);
@@ -26,63 +34,150 @@ enum { OP_MASS = 0, OP_BRAS = 1, OP_DIAG = 2 };
 enum { KIND_H1 = 0, KIND_PACKED = 1 };
 
 struct BlockArgs {
-    const int32_t* blk_e0;
-    const int32_t* blk_u0;
-    const int32_t* blk_nint;
-    const int32_t* blk_p0;
-    const int32_t* ids;
-    const uint16_t* incoff;
-    const uint16_t* loc;
-    const uint16_t* inc;
-    const void* dinv;    // T[n]
-    const void* refmat;  // T[nloc*nloc]   (H1)
-    const void* scale;   // T[E]           (H1)
-    const void* pk;      // S[npk][Epad]   (packed)
+    const int32_t* blk_e0;     // [nblk + 1] first cell of each block
+    const int32_t* blk_u0;     // [nblk + 1] first block-local dof (prefix of nu)
+    const int32_t* blk_nint;   // [nblk] interior dofs (all copies inside the block)
+    const int32_t* blk_p0;     // [nblk] first partial slot
+    const int64_t* blk_pkt;    // [nblk] byte offset of the block's packet
+    const unsigned char* pkt;  // packets
+    const void* refmat;        // T[nloc*nloc]   (H1)
+    const void* scale;         // T[E]           (H1)
+    const void* pk;            // S[npk][Epad]   (packed)
+    int* status;               // device status word (bit 0: a bulk-copy wait timed out)
     int64_t Epad;
     int64_t npart;
     int max_u;
     int max_ne;
+    uint32_t max_pkt;          // largest packet (bytes)
 };
 
-template <typename T> __device__ __forceinline__ T to_t(double v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T ld_mat(const double* p) { return (T)__ldg(p); }
 template <typename T> __device__ __forceinline__ T ld_mat(const float* p) { return (T)__ldg(p); }
 template <typename T> __device__ __forceinline__ T ld_mat(const __nv_bfloat16* p) {
     return (T)__bfloat162float(*p);
 }
 
+// ---- bulk asynchronous copy + mbarrier helpers (sm_90+ PTX) -------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on phase 0 of `bar`: gives up after ~2^22 polls (each try_wait itself
+// suspends for a hardware-chosen interval), records the failure and tells the caller.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, 0)) return true;
+    atomicOr(status, 1);
+    return false;
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec4<double> { using type = double2; static constexpr int W = 2; };
+
+template <int N, typename T> struct PadTo {
+    static constexpr int W = Vec4<T>::W;
+    static constexpr int value = (N + W - 1) / W * W;
+};
+
 template <int NLOC, typename T, typename S, int KIND, int OP>
 __global__ void __launch_bounds__(256, 1)
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NPAD = PadTo<NLOC, T>::value;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // 2 mbarriers
+    unsigned char* tab = smem_raw + 128;                                 // table packet
+    T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));
+    T* zs = xs + ((A.max_u + 3) & ~3);
+    T* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                            // [NLOC][NPAD] (H1), 16-B aligned
+
     const int b = blockIdx.x, r = blockIdx.y, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
-    T* xs = reinterpret_cast<T*>(smem_raw);
-    T* zs = xs + ((A.max_u + 1) & ~1);
-    T* Ms = zs + NLOC * A.max_ne;
-    const T* __restrict__ dinv = static_cast<const T*>(A.dinv);
-
+    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+        const unsigned char* src = A.pkt + A.blk_pkt[b];
+        mbar_expect_tx(&bars[0], sa);
+        bulk_copy_g2s(tab, src, sa, &bars[0]);
+        mbar_expect_tx(&bars[1], sb);
+        bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
+    }
     if (KIND == KIND_H1) {
         const T* ref = static_cast<const T*>(A.refmat);
-        for (int i = tid; i < NLOC * NLOC; i += blockDim.x) Ms[i] = ref[i];
-    }
-    if (OP != OP_DIAG) {
-        for (int u = tid; u < nu; u += blockDim.x) {
-            const int g = A.ids[u0 + u];
-            T v = x[(size_t)g * nrhs + r];
-            if (OP == OP_BRAS) v *= dinv[g];
-            xs[u] = v;
+        for (int i = tid; i < NLOC * NPAD; i += blockDim.x) {
+            const int a = i / NPAD, q = i - a * NPAD;
+            Ms[i] = q < NLOC ? ref[a * NLOC + q] : T(0);
         }
     }
-    __syncthreads();
+    __syncthreads();   // barriers initialised before anyone polls them
+    const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
+    const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
+    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
+    const uint16_t* inc = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+
+    bool ok = mbar_wait_bounded(&bars[0], A.status);
+    if (OP != OP_DIAG && ok) {
+        // independent loads, four per thread in flight
+        for (int u = tid; u < nu; u += 4 * blockDim.x) {
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int uu = u + k * blockDim.x;
+                v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int uu = u + k * blockDim.x;
+                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? v[k] / T(dmul[uu]) : v[k];
+            }
+        }
+    }
+    ok = mbar_wait_bounded(&bars[1], A.status) && ok;
+    if (!__syncthreads_and(ok)) {   // block-uniform decision
+        // let any copy still in flight land before the block's shared memory is released
+        if (tid == 0) {
+            mbar_wait_bounded(&bars[0], A.status);
+            mbar_wait_bounded(&bars[1], A.status);
+        }
+        return;
+    }
 
     const int e = tid;
     if (e < ne) {
-        const uint16_t* __restrict__ L = A.loc + (size_t)e0 * NLOC + e;
+        const uint16_t* L = loc + e;
         uint64_t neg = 0;
-        T xl[NLOC];
+        T xl[NPAD];
 #pragma unroll
         for (int a = 0; a < NLOC; ++a) {
             const uint16_t c = L[a * ne];
@@ -91,16 +186,32 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             neg |= (uint64_t)s << a;
             xl[a] = s ? -v : v;
         }
+#pragma unroll
+        for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
         if (KIND == KIND_H1) {
+            using V = typename Vec4<T>::type;
+            constexpr int W = Vec4<T>::W;
             const T c = static_cast<const T*>(A.scale)[e0 + e];
 #pragma unroll
             for (int a = 0; a < NLOC; ++a) {
                 T acc = T(0);
                 if (OP == OP_DIAG) {
-                    acc = Ms[a * NLOC + a];
+                    acc = Ms[a * NPAD + a];
                 } else {
+                    const V* row = reinterpret_cast<const V*>(Ms + a * NPAD);
 #pragma unroll
-                    for (int q = 0; q < NLOC; ++q) acc = fma(Ms[a * NLOC + q], xl[q], acc);
+                    for (int q = 0; q < NPAD / W; ++q) {
+                        const V m = row[q];
+                        if constexpr (W == 4) {
+                            acc = fma(m.x, xl[4 * q + 0], acc);
+                            acc = fma(m.y, xl[4 * q + 1], acc);
+                            acc = fma(m.z, xl[4 * q + 2], acc);
+                            acc = fma(m.w, xl[4 * q + 3], acc);
+                        } else {
+                            acc = fma(m.x, xl[2 * q + 0], acc);
+                            acc = fma(m.y, xl[2 * q + 1], acc);
+                        }
+                    }
                 }
                 acc *= c;
                 zs[a * ne + e] = ((neg >> a) & 1) && OP != OP_DIAG ? -acc : acc;
@@ -131,15 +242,12 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     }
     __syncthreads();
 
-    const uint16_t* __restrict__ I = A.inc + (size_t)e0 * NLOC;
-    const uint16_t* __restrict__ IO = A.incoff + u0 + b;
     for (int u = tid; u < nu; u += blockDim.x) {
-        const int s0 = IO[u], s1 = IO[u + 1];
+        const int s0 = incoff[u], s1 = incoff[u + 1];
         T acc = T(0);
-        for (int s = s0; s < s1; ++s) acc += zs[I[s]];
+        for (int s = s0; s < s1; ++s) acc += zs[inc[s]];
         if (u < nint) {
-            const int g = A.ids[u0 + u];
-            y[(size_t)g * nrhs + r] = (OP == OP_BRAS) ? acc * dinv[g] : acc;
+            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? acc / T(dmul[u]) : acc;
         } else {
             part[(size_t)r * A.npart + A.blk_p0[b] + (u - nint)] = acc;
         }
@@ -161,14 +269,24 @@ __global__ void k_combine(int64_t nsh, const int32_t* __restrict__ sh_ids, const
     }
 }
 
+template <int NLOC, typename T, int KIND>
+size_t block_smem_bytes(const BlockArgs& A) {
+    constexpr int NPAD = PadTo<NLOC, T>::value;
+    return 128 + ((A.max_pkt + 127u) & ~127u) +
+           sizeof(T) * (((A.max_u + 3) & ~3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) +
+                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
+}
+
 // Launch one block apply (block kernel + combine).  Returns a cudaError_t.
 template <int NLOC, typename T, typename S, int KIND, int OP>
-cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs,
+cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
                          int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
                          cudaStream_t st) {
-    size_t smem = sizeof(T) * (((A.max_u + 1) & ~1) + (size_t)NLOC * A.max_ne + (KIND == KIND_H1 ? NLOC * NLOC : 0));
+    const size_t smem = block_smem_bytes<NLOC, T, KIND>(A);
     auto kern = k_block<NLOC, T, S, KIND, OP>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
     dim3 grid(nblk, nrhs);
     kern<<<grid, 256, smem, st>>>(A, x, y, part, nrhs);
@@ -178,8 +296,7 @@ cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part
     if (nsh > 0) {
         int64_t total = nsh * nrhs;
         int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
-        k_combine<T, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, A.npart,
-                                              static_cast<const T*>(A.dinv), y, nrhs);
+        k_combine<T, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, dinv, y, nrhs);
         count_launch(1);
         err = cudaGetLastError();
     }

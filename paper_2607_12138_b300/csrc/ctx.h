@@ -14,20 +14,25 @@ struct PcgWork;
 
 // ---- scatter tables ---------------------------------------------------------------
 // Cells are reordered along a Morton curve of their centroids and cut into blocks of at
-// most BE consecutive cells.  Block b owns cells [blk_e0[b], blk_e0[b+1]) and the dof list
-// ids[blk_u0[b] .. blk_u0[b+1]): first the dofs all of whose broken copies lie inside the
-// block ("interior", blk_nint[b] of them), then the others ("shared").
-//   loc[e0*nloc + a*ne + e]  = block-local index of dof (cell e, local a), bit 15 = sign -1
-//   inc[e0*nloc + s], s in [incoff[blk_u0[b]+b+u], incoff[blk_u0[b]+b+u+1]) = broken slots
-//       a*ne + e of block-local dof u, ascending (fixed summation order)
-//   shared dof j of block b writes partial slot blk_p0[b] + j; sh_off / sh_slots list, per
-//   globally shared dof sh_ids[i], its partial slots in ascending block order.
+// most BE consecutive cells.  Block b owns cells [blk_e0[b], blk_e0[b+1]) and nu_b =
+// blk_u0[b+1] - blk_u0[b] block-local dofs: first the dofs all of whose broken copies lie
+// inside the block ("interior", blk_nint[b] of them), then the others ("shared").  Its table
+// packet (byte offset blk_pkt[b], layout in apply_kernels.cuh) holds
+//   ids[u]      global dof of block-local dof u
+//   d[u]        multiplicity of that dof (D = P^T P)
+//   incoff[u]   incidence offsets: the broken slots a*ne + e of dof u are inc[incoff[u]..)
+//   loc[a*ne+e] block-local dof of (cell e, local a); bit 15 = sign -1 of P
+//   inc[s]      broken slots, ascending per dof (fixed summation order)
+// Shared dof j of block b writes partial slot blk_p0[b] + j; sh_off / sh_slots list, per
+// globally shared dof sh_ids[i], its partial slots in ascending block order.
 struct HostTables {
     int BE = 256, nblk = 0, max_u = 0, max_ne = 0;
-    std::vector<int32_t> perm, blk_e0, blk_u0, blk_nint, blk_p0, ids, sh_ids, sh_off, sh_slots;
-    std::vector<uint16_t> incoff, loc, inc;
+    uint32_t max_pkt = 0;
+    std::vector<int32_t> perm, blk_e0, blk_u0, blk_nint, blk_p0, sh_ids, sh_off, sh_slots;
+    std::vector<int64_t> blk_pkt;
+    std::vector<unsigned char> pkt;
     std::vector<double> dinv;
-    int64_t npart = 0;
+    int64_t npart = 0, U_tot = 0;
 };
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
@@ -48,9 +53,11 @@ struct bras_ctx {
 
     // scatter tables (device)
     int32_t *blk_e0 = nullptr, *blk_u0 = nullptr, *blk_nint = nullptr, *blk_p0 = nullptr;
-    int32_t *ids = nullptr, *sh_ids = nullptr, *sh_off = nullptr, *sh_slots = nullptr;
+    int32_t *sh_ids = nullptr, *sh_off = nullptr, *sh_slots = nullptr;
     int32_t *perm = nullptr;
-    uint16_t *incoff = nullptr, *loc = nullptr, *inc = nullptr;
+    int64_t* blk_pkt = nullptr;
+    unsigned char* pkt = nullptr;
+    uint32_t max_pkt = 0;
 
     // per dof
     double* dinv64 = nullptr;

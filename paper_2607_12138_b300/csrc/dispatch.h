@@ -12,6 +12,7 @@ int64_t launches_so_far();
 
 struct LaunchCommon {
     BlockArgs A;
+    const void* dinv;   // T[n] 1/d for the combine pass
     int nblk;
     int64_t nsh;
     const int32_t *sh_ids, *sh_off, *sh_slots;

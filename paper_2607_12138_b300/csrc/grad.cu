@@ -9,12 +9,13 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "packet.h"
 
 namespace bras {
 
 template <int NLOC>
 __global__ void k_grad_rho(int64_t E, int BE, const int32_t* __restrict__ blk_e0, const int32_t* __restrict__ blk_u0,
-                           const int32_t* __restrict__ ids, const uint16_t* __restrict__ loc,
+                           const int64_t* __restrict__ blk_pkt, const unsigned char* __restrict__ pkt,
                            const int32_t* __restrict__ perm, const double* __restrict__ absdet,
                            const double* __restrict__ Mref, const double* __restrict__ x,
                            const double* __restrict__ lam, double* __restrict__ rho_bar) {
@@ -23,13 +24,16 @@ __global__ void k_grad_rho(int64_t E, int BE, const int32_t* __restrict__ blk_e0
     __syncthreads();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(e / BE);
-        const int e0 = blk_e0[b], ne = blk_e0[b + 1] - e0, el = (int)(e - e0), u0 = blk_u0[b];
-        const uint16_t* L = loc + (size_t)e0 * NLOC + el;
+        const int e0 = blk_e0[b], ne = blk_e0[b + 1] - e0, el = (int)(e - e0);
+        const uint32_t nu = (uint32_t)(blk_u0[b + 1] - blk_u0[b]);
+        const unsigned char* P = pkt + blk_pkt[b];
+        const int32_t* ids = reinterpret_cast<const int32_t*>(P);
+        const uint16_t* L = reinterpret_cast<const uint16_t*>(P + pkt_size_a(nu)) + el;
         double xl[NLOC], ll[NLOC];
 #pragma unroll
         for (int a = 0; a < NLOC; ++a) {
             const uint16_t c = L[a * ne];
-            const int g = ids[u0 + (c & 0x7fff)];
+            const int g = ids[c & 0x7fff];
             const double s = (c & 0x8000) ? -1.0 : 1.0;
             xl[a] = s * x[g];
             ll[a] = s * lam[g];
@@ -50,7 +54,7 @@ cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* la
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((c->E + 127) / 128, 148 * 8));
 #define GRAD_CASE(N)                                                                                              \
     case N:                                                                                                       \
-        k_grad_rho<N><<<nb, 128, 0, st>>>(c->E, c->BE, c->blk_e0, c->blk_u0, c->ids, c->loc, c->perm, c->absdet, \
+        k_grad_rho<N><<<nb, 128, 0, st>>>(c->E, c->BE, c->blk_e0, c->blk_u0, c->blk_pkt, c->pkt, c->perm, c->absdet, \
                                           c->Mref64, x, lam, rho_bar);                                            \
         count_launch(1);                                                                                          \
         break;

@@ -36,6 +36,7 @@ struct PcgWork {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xs = nullptr, *bs = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr;
     double* partial = nullptr;    // [kDotBlocks][nrhs]
+    unsigned int* ticket = nullptr;  // arrival counter of the fused reductions
     double* sc = nullptr;         // [S_COUNT][nrhs]
     int* flags = nullptr;         // [0..nrhs): active, [nrhs..2nrhs): its, [2nrhs]: n active, [2nrhs+1]: status
     int* h_flags = nullptr;       // pinned
@@ -63,7 +64,7 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
     if (w) {
         for (void* p : {(void*)w->r, (void*)w->z, (void*)w->p, (void*)w->q, (void*)w->xs, (void*)w->bs,
                         (void*)w->r32, (void*)w->z32, (void*)w->p32, (void*)w->q32, (void*)w->x32,
-                        (void*)w->partial, (void*)w->sc, (void*)w->flags, (void*)w->dparam, (void*)w->iparam})
+                        (void*)w->partial, (void*)w->sc, (void*)w->flags, (void*)w->dparam, (void*)w->iparam, (void*)w->ticket})
             dfree(c, p);
         free_pcg(c);
     }
@@ -83,6 +84,8 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
     w->sc = (double*)d((size_t)S_COUNT * w->nrhs * 8);
     w->flags = (int*)d((size_t)(2 * w->nrhs + 2) * 4);
     w->dparam = (double*)d(8 * 2);
+    w->ticket = (unsigned int*)d(16);
+    if (!w->ticket || cudaMemset(w->ticket, 0, 16) != cudaSuccess) return BRAS_ERR_OOM;
     w->iparam = (int*)d(4 * 4);
     if (!w->dparam || !w->iparam) return BRAS_ERR_OOM;
     if (cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess) return BRAS_ERR_CUDA;
@@ -102,29 +105,134 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
 }
 
 // ---- kernels ---------------------------------------------------------------------------
+// Every dot product ends in a fixed-order two-level reduction: each block writes its partial
+// sum, takes a ticket (an integer atomic, so the order of arrival does not matter), and the
+// last block to arrive reduces all partials in a fixed tree order and applies the scalar
+// update of the CG step (alpha, beta, convergence masks, loop condition).  No floating-point
+// atomics; results are bit-reproducible.
+struct FinArgs {
+    int kind;
+    double* partial;               // [G][R] per-block partial sums
+    unsigned int* ticket;          // arrival counter, returned to 0 by the last block
+    double* sc;                    // per-rhs scalars [S_COUNT][R]
+    int* flags;                    // active[R], its[R], n_active, status
+    const double* dparam;          // [0] = rtol^2
+    int* iparam;                   // [0] = maxit, [1] = iterations done (solve graph only)
+    cudaGraphConditionalHandle cond;
+};
+
+__device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
+    double* sc = F.sc;
+    int* active = F.flags;
+    int* its = F.flags + R;
+    const double tol2 = F.dparam ? F.dparam[0] : 0.0;
+    switch (F.kind) {
+        case FIN_INIT_RR:
+            sc[S_RR0 * R + r] = s;
+            sc[S_RR * R + r] = s;
+            active[r] = s > 0.0 ? 1 : 0;
+            its[r] = 0;
+            break;
+        case FIN_INIT_RZ:
+            sc[S_RZ * R + r] = s;
+            break;
+        case FIN_ALPHA: {
+            sc[S_PQ * R + r] = s;
+            double a = 0.0;
+            if (active[r]) {
+                if (!(s > 0.0) || !isfinite(s)) {
+                    active[r] = 0;
+                    F.flags[2 * R + 1] = BRAS_ERR_BREAKDOWN;
+                } else {
+                    a = sc[S_RZ * R + r] / s;
+                }
+            }
+            sc[S_ALPHA * R + r] = a;
+            break;
+        }
+        case FIN_RR:
+            sc[S_RR * R + r] = s;
+            if (active[r]) {
+                its[r] += 1;
+                if (s <= tol2 * sc[S_RR0 * R + r]) active[r] = 0;
+            }
+            break;
+        case FIN_BETA: {   // beta = 0 on the first iteration (p = z)
+            double bta = 0.0;
+            if (active[r]) {
+                bta = its[r] == 0 ? 0.0 : s / sc[S_RZ * R + r];
+                sc[S_RZ * R + r] = s;
+            }
+            sc[S_BETA * R + r] = bta;
+            break;
+        }
+        case FIN_NORM:
+            sc[S_RR * R + r] = s;
+            break;
+    }
+}
+
+// `red` holds this block's 256 per-thread sums (thread t: rhs t % R, group t / R).
+__device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
+    const int tid = threadIdx.x, J = 256 / R, r = tid % R, j = tid / R;
+    __shared__ unsigned int s_last;
+    // fixed tree over the J groups of this block
+    for (int h = 1; h < J; h *= 2) {
+        __syncthreads();
+        if (j < J && (j % (2 * h)) == 0 && j + h < J) red[tid] += red[tid + h * R];
+    }
+    __syncthreads();
+    if (tid < R) F.partial[blockIdx.x * R + tid] = red[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(F.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last block: fixed-order reduction of all G partials
+    double s = 0.0;
+    if (j < J)
+        for (int g = j; g < (int)gridDim.x; g += J) s += __ldcg(&F.partial[g * R + r]);
+    red[tid] = s;
+    for (int h = 1; h < J; h *= 2) {
+        __syncthreads();
+        if (j < J && (j % (2 * h)) == 0 && j + h < J) red[tid] += red[tid + h * R];
+    }
+    __syncthreads();
+    if (tid < R) apply_fin(F, R, tid, red[tid]);
+    __syncthreads();
+    if (tid == 0) {
+        int cnt = 0;
+        for (int k = 0; k < R; ++k) cnt += F.flags[k];
+        F.flags[2 * R] = cnt;
+        if (F.kind == FIN_RR && F.iparam) {
+            const int done = ++F.iparam[1];
+            cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
+        }
+        *F.ticket = 0u;
+    }
+}
+
 // Thread t of a block handles rhs t % R of rows t / R, so every thread sticks to one rhs.
 template <typename TA, typename TB>
-__global__ void k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int64_t n, int R, double* __restrict__ partial) {
-    __shared__ double sh[256];
+__global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int64_t n, int R,
+                                             FinArgs F) {
+    __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
     double acc = 0.0;
     if (lr < rows)
         for (int64_t i = (int64_t)blockIdx.x * rows + lr; i < n; i += (int64_t)gridDim.x * rows)
             acc += (double)a[i * R + r] * (double)b[i * R + r];
-    sh[tid] = acc;
-    __syncthreads();
-    if (tid < R) {
-        double s = 0.0;
-        for (int k = 0; k < rows; ++k) s += sh[k * R + tid];
-        partial[blockIdx.x * R + tid] = s;
-    }
+    red[tid] = acc;
+    block_partial_and_finish(F, R, red);
 }
 
-// x += alpha p; r -= alpha q; partial sums of r.r  (fused, one pass)
+// x += alpha p; r -= alpha q; and r.r with the convergence test  (fused, one pass)
 template <typename T>
-__global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
-                            const double* __restrict__ alpha, int64_t n, int R, double* __restrict__ partial) {
-    __shared__ double sh[256];
+__global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                   const T* __restrict__ q, const double* __restrict__ alpha,
+                                                   int64_t n, int R, FinArgs F) {
+    __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
     double acc = 0.0;
     if (lr < rows) {
@@ -137,13 +245,8 @@ __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __res
             acc += (double)v * (double)v;
         }
     }
-    sh[tid] = acc;
-    __syncthreads();
-    if (tid < R) {
-        double s = 0.0;
-        for (int k = 0; k < rows; ++k) s += sh[k * R + tid];
-        partial[blockIdx.x * R + tid] = s;
-    }
+    red[tid] = acc;
+    block_partial_and_finish(F, R, red);
 }
 
 template <typename T>
@@ -176,82 +279,26 @@ __global__ void k_residual(double* __restrict__ r, const double* __restrict__ b,
         r[i] = b[i] - q[i];
 }
 
-// Per-rhs scalar updates from the partial sums (one thread per rhs, fixed summation order).
-__global__ void k_fin(int kind, const double* __restrict__ partial, int G, int R, double* __restrict__ sc,
-                      int* __restrict__ flags, const double* __restrict__ dparam, int* __restrict__ iparam,
-                      cudaGraphConditionalHandle cond) {
-    const double tol2 = dparam ? dparam[0] : 0.0;
-    const int r = threadIdx.x;
-    if (r < R) {
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += partial[g * R + r];
-        int* active = flags;
-        int* its = flags + R;
-        switch (kind) {
-            case FIN_INIT_RR:
-                sc[S_RR0 * R + r] = s;
-                sc[S_RR * R + r] = s;
-                active[r] = s > 0.0 ? 1 : 0;
-                its[r] = 0;
-                break;
-            case FIN_INIT_RZ:
-                sc[S_RZ * R + r] = s;
-                break;
-            case FIN_ALPHA: {
-                sc[S_PQ * R + r] = s;
-                double a = 0.0;
-                if (active[r]) {
-                    if (!(s > 0.0) || !isfinite(s)) {
-                        active[r] = 0;
-                        flags[2 * R + 1] = BRAS_ERR_BREAKDOWN;
-                    } else {
-                        a = sc[S_RZ * R + r] / s;
-                    }
-                }
-                sc[S_ALPHA * R + r] = a;
-                break;
-            }
-            case FIN_RR:
-                sc[S_RR * R + r] = s;
-                if (active[r]) {
-                    its[r] += 1;
-                    if (s <= tol2 * sc[S_RR0 * R + r]) active[r] = 0;
-                }
-                break;
-            case FIN_BETA: {   // beta = 0 on the first iteration (p = z)
-                double bta = 0.0;
-                if (active[r]) {
-                    bta = its[r] == 0 ? 0.0 : s / sc[S_RZ * R + r];
-                    sc[S_RZ * R + r] = s;
-                }
-                sc[S_BETA * R + r] = bta;
-                break;
-            }
-            case FIN_NORM:
-                sc[S_RR * R + r] = s;
-                break;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int cnt = 0;
-        for (int k = 0; k < R; ++k) cnt += flags[k];
-        flags[2 * R] = cnt;
-        if (kind == FIN_RR && iparam) {
-            const int done = ++iparam[1];
-            cudaGraphSetConditional(cond, (cnt > 0 && done < iparam[0]) ? 1u : 0u);
-        }
-    }
-}
-
 // ---- host helpers ------------------------------------------------------------------------
 static int grid_for(int64_t nv) { return (int)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 148 * 8)); }
 
+static FinArgs fin_args(PcgWork* w, int kind, int* iparam = nullptr, cudaGraphConditionalHandle cond = 0) {
+    FinArgs F;
+    F.kind = kind;
+    F.partial = w->partial;
+    F.ticket = w->ticket;
+    F.sc = w->sc;
+    F.flags = w->flags;
+    F.dparam = w->dparam;
+    F.iparam = iparam;
+    F.cond = cond;
+    return F;
+}
+
 template <typename TA, typename TB>
 static cudaError_t dot(PcgWork* w, const TA* a, const TB* b, int64_t n, int R, int kind, cudaStream_t st) {
-    k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, n, R, w->partial);
-    k_fin<<<1, 256, 0, st>>>(kind, w->partial, kDotBlocks, R, w->sc, w->flags, w->dparam, nullptr, 0);
-    count_launch(2);
+    k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, n, R, fin_args(w, kind));
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -298,9 +345,9 @@ static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T*
     count_launch(1);
     RC(run_op(c, prec, OP_MASS, p, q, R, st));
     CK(dot(w, p, q, n, R, FIN_ALPHA, st));
-    k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * R, n, R, w->partial);
-    k_fin<<<1, 256, 0, st>>>(FIN_RR, w->partial, kDotBlocks, R, w->sc, w->flags, w->dparam, w->iparam, cond);
-    count_launch(2);
+    k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * R, n, R,
+                                                fin_args(w, FIN_RR, w->iparam, cond));
+    count_launch(1);
     CK(cudaGetLastError());
     return BRAS_OK;
 }

@@ -13,6 +13,7 @@
 #include <numeric>
 
 #include "ctx.h"
+#include "packet.h"
 
 namespace bras {
 namespace {
@@ -39,8 +40,10 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         if (g < 0 || g >= n) { *detail = i; return BRAS_ERR_L2G_RANGE; }
         d[g]++;
     }
-    for (int64_t i = 0; i < n; ++i)
+    for (int64_t i = 0; i < n; ++i) {
         if (d[i] == 0) { *detail = i; return BRAS_ERR_NO_COPY; }
+        if (d[i] > 65535) { *detail = i; return BRAS_ERR_TOO_LARGE; }
+    }
     t->dinv.resize(n);
     for (int64_t i = 0; i < n; ++i) t->dinv[i] = 1.0 / (double)d[i];
 
@@ -134,31 +137,45 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
     }
     t->max_u = max_u;
     t->max_ne = max_ne;
-    // concatenate
+    // packets: part A = ids | d | incoff, part B = loc | inc, 16-byte aligned sections
     t->blk_u0.resize(nblk + 1);
     t->blk_nint.resize(nblk);
     t->blk_p0.resize(nblk);
-    int64_t U = 0, P = 0;
+    t->blk_pkt.resize(nblk + 1);
+    int64_t U = 0, P = 0, bytes = 0;
+    uint32_t max_pkt = 0;
     for (int b = 0; b < nblk; ++b) {
+        const uint32_t nu = (uint32_t)blk[b].ids.size();
+        const uint32_t m = (uint32_t)(t->blk_e0[b + 1] - t->blk_e0[b]) * (uint32_t)nloc;
+        const uint32_t sz = pkt_size_a(nu) + pkt_size_b(m);
         t->blk_u0[b] = (int32_t)U;
         t->blk_nint[b] = blk[b].nint;
         t->blk_p0[b] = (int32_t)P;
-        U += blk[b].ids.size();
-        P += (int64_t)blk[b].ids.size() - blk[b].nint;
+        t->blk_pkt[b] = bytes;
+        U += nu;
+        P += (int64_t)nu - blk[b].nint;
+        bytes += sz;
+        max_pkt = std::max(max_pkt, sz);
     }
     t->blk_u0[nblk] = (int32_t)U;
+    t->blk_pkt[nblk] = bytes;
     t->npart = P;
-    t->ids.resize(U);
-    t->incoff.resize(U + nblk);
-    t->loc.resize((size_t)E * nloc);
-    t->inc.resize((size_t)E * nloc);
+    t->U_tot = U;
+    t->max_pkt = max_pkt;
+    t->pkt.assign((size_t)bytes, 0);
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < nblk; ++b) {
         const Blk& B = blk[b];
-        std::copy(B.ids.begin(), B.ids.end(), t->ids.begin() + t->blk_u0[b]);
-        std::copy(B.incoff.begin(), B.incoff.end(), t->incoff.begin() + t->blk_u0[b] + b);
-        std::copy(B.loc.begin(), B.loc.end(), t->loc.begin() + (size_t)t->blk_e0[b] * nloc);
-        std::copy(B.inc.begin(), B.inc.end(), t->inc.begin() + (size_t)t->blk_e0[b] * nloc);
+        const uint32_t nu = (uint32_t)B.ids.size();
+        const uint32_t m = (uint32_t)B.loc.size();
+        unsigned char* p = t->pkt.data() + t->blk_pkt[b];
+        std::memcpy(p, B.ids.data(), 4 * (size_t)nu);
+        uint16_t* dm = reinterpret_cast<uint16_t*>(p + pkt_off_d(nu));
+        for (uint32_t u = 0; u < nu; ++u) dm[u] = (uint16_t)std::min<int32_t>(d[B.ids[u]], 65535);
+        std::memcpy(p + pkt_off_incoff(nu), B.incoff.data(), 2 * (size_t)(nu + 1));
+        const uint32_t sa = pkt_size_a(nu);
+        std::memcpy(p + sa, B.loc.data(), 2 * (size_t)m);
+        std::memcpy(p + sa + pad16(2u * m), B.inc.data(), 2 * (size_t)m);
     }
     // shared dofs: partial slots in ascending block order per dof
     std::vector<std::pair<int32_t, int32_t>> sh;   // (dof, slot)

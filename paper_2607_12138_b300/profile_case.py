@@ -26,23 +26,28 @@ def main() -> None:
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--block-elems", type=int, default=0)
     a = ap.parse_args()
     mesh = mg.unit_cube_mesh(a.cells, jitter=0.15, seed=0)
     n, l2g, s = mg.dof_map(mesh, a.space, a.order)
-    ctx = B.Context(mesh.coords, mesh.cells, a.space, a.order, n, l2g, s, max_nrhs=a.nrhs)
+    ctx = B.Context(mesh.coords, mesh.cells, a.space, a.order, n, l2g, s, max_nrhs=a.nrhs,
+                    block_elems=a.block_elems)
     prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16}[a.prec]
     dt = torch.float64 if prec == B.FP64 else torch.float32
     x = torch.as_tensor(mg.rhs(n, a.nrhs, seed=1), device="cuda").to(dt)
     y = torch.empty_like(x)
     fn = {"bras": ctx.bras_apply, "mass": ctx.mass_apply, "jacobi": ctx.jacobi_apply}[a.op]
+    fn(x, prec, out=y)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
     for _ in range(a.reps):
         fn(x, prec, out=y)
+    e1.record()
     torch.cuda.synchronize()
-    dt_s = (time.perf_counter() - t0) / a.reps
+    dt_s = e0.elapsed_time(e1) / 1e3 / a.reps
     print(f"{a.space} p={a.order} cells={mesh.n_cell} dofs={n} op={a.op} prec={a.prec} nrhs={a.nrhs} "
-          f"blocks={ctx.n_blocks} avg_wall_us={dt_s * 1e6:.1f} alg_bytes={ctx.algorithmic_bytes(prec, a.nrhs, a.op == 'bras')}")
+          f"blocks={ctx.n_blocks} avg_event_us={dt_s * 1e6:.1f} alg_bytes={ctx.algorithmic_bytes(prec, a.nrhs, a.op == 'bras')}")
 
 
 if __name__ == "__main__":
