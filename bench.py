@@ -178,12 +178,19 @@ def run_ours(a):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
     st = torch.cuda.current_stream()
 
+    order_ms = {}
+
     def step(mode=B.SOLVE_MIXED, pc=B.PC_BRAS, host=False):
         out = []
-        for pr in probs:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(probs) + 1)]
+        evs[0].record(st)
+        for i, pr in enumerate(probs):
             b, x = (pr["bh"], pr["xh"]) if host else (pr["b"], pr["x"])
             _, its, rel, status = pr["ctx"].pcg_solve(b, pc=pc, mode=mode, inner_precision=B.FP32, rtol=1e-10, out=x)
+            evs[i + 1].record(st)
             out.append((int(its[0]), float(rel[0]), status))
+        torch.cuda.synchronize()
+        order_ms[(mode, pc, host)] = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(probs))]
         return out
 
     def timed(fn, steps):
@@ -240,15 +247,17 @@ def run_ours(a):
     # per-order detail, comparison rows and per-kernel live timings
     detail = []
     compare = {}
+    last_ms = order_ms.get((B.SOLVE_MIXED, B.PC_BRAS, False), [None] * len(probs))
     for i, pr in enumerate(probs):
         its, rel, _ = res[i]
-        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel})
+        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel, "solve_ms": last_ms[i]})
     if not a.no_compare:
         for name, mode, pc in (("fp64_bras", B.SOLVE_FP64, B.PC_BRAS), ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI),
                                ("mixed_jacobi", B.SOLVE_MIXED, B.PC_JACOBI)):
             step(mode, pc)
             tsc, rc = timed(lambda: step(mode, pc), 1)
-            compare[name] = {"dof_per_s": total_n / tsc[0], "ms": 1e3 * tsc[0], "its": [r[0] for r in rc]}
+            compare[name] = {"dof_per_s": total_n / tsc[0], "ms": 1e3 * tsc[0], "its": [r[0] for r in rc],
+                             "solve_ms": order_ms.get((mode, pc, False))}
         compare["mixed_bras"] = {"dof_per_s": value / ws, "ms": 1e3 * t_step, "its": [r[0] for r in res]}
 
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply

@@ -112,6 +112,34 @@ int bras_setup(bras_ctx** out, int dim, int space, int order,
                int64_t n_dof, const int32_t* l2g, const int8_t* signs,
                const double* rho, const bras_options* opt, void* stream);
 
+/* One mesh of a batch (all pointers host or device; same meaning as in bras_setup). */
+typedef struct {
+    int64_t n_vert;
+    const double* coords;    /* [n_vert * dim]          */
+    int64_t n_cell;
+    const int32_t* cells;    /* [n_cell * (dim+1)]      */
+    int64_t n_dof;
+    const int32_t* l2g;      /* [n_cell * n_loc], dofs 0..n_dof-1 of this mesh */
+    const int8_t* signs;     /* [n_cell * n_loc] or NULL */
+    const double* rho;       /* [n_cell] or NULL          */
+} bras_mesh_desc;
+
+/*
+ * bras_setup_batched -- one context for n_mesh independent meshes of the same space and
+ * order (uneven sizes allowed).  The conforming systems stay independent: the context's
+ * dof space is the concatenation of the meshes' dof spaces (mesh m owns the dofs
+ * [off[m], off[m+1]) reported by bras_batch_offsets), every apply works on the whole
+ * concatenation, and bras_pcg_solve with nrhs = 1 solves all meshes at once with
+ * per-mesh CG scalars and per-mesh stopping tests (iters / relres then have n_mesh
+ * entries).  Same limits as bras_setup on the totals.
+ */
+int bras_setup_batched(bras_ctx** out, int dim, int space, int order, int n_mesh,
+                       const bras_mesh_desc* meshes, const bras_options* opt, void* stream);
+
+/* Number of meshes of a context (1 unless batched) and, if dof_offsets is not NULL, the
+ * n_mesh + 1 dof offsets (host array). */
+int bras_batch_offsets(const bras_ctx* ctx, int* n_mesh, int64_t* dof_offsets);
+
 /* Number of local dofs per cell for (dim, space, order), or -1 if unsupported. */
 int bras_n_local(int dim, int space, int order);
 
@@ -155,6 +183,8 @@ int bras_jacobi_apply(const bras_ctx* ctx, int precision, const void* x, void* y
 /*
  * bras_pcg_solve -- solve M x = b by preconditioned CG (Sec. 3): u_0 = 0, stop when
  * ||r_k||_2 / ||r_0||_2 <= rtol for every right-hand side, or after maxit iterations.
+ * On a batched context nrhs must be 1 and every mesh is its own system (iters and relres
+ * have n_mesh entries).  A context's solve workspace serves one solve at a time.
  *   pc     BRAS_PC_NONE, BRAS_PC_JACOBI or BRAS_PC_BRAS.
  *   mode   BRAS_SOLVE_FP64: FP64 PCG, recurrence residual tested.
  *          BRAS_SOLVE_MIXED: FP32 (or BF16-inverse, if inner_precision = BRAS_BF16) inner

@@ -65,6 +65,16 @@ _lib.bras_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctyp
 _lib.bras_info.restype = _int
 _lib.bras_algorithmic_bytes.argtypes = [_vp, _int, _int, _int]
 _lib.bras_algorithmic_bytes.restype = _i64
+class bras_mesh_desc(ctypes.Structure):
+    _fields_ = [("n_vert", _i64), ("coords", _vp), ("n_cell", _i64), ("cells", _vp), ("n_dof", _i64),
+                ("l2g", _vp), ("signs", _vp), ("rho", _vp)]
+
+
+_lib.bras_setup_batched.argtypes = [ctypes.POINTER(_vp), _int, _int, _int, _int, ctypes.POINTER(bras_mesh_desc),
+                                    ctypes.POINTER(bras_options), _vp]
+_lib.bras_setup_batched.restype = _int
+_lib.bras_batch_offsets.argtypes = [_vp, ctypes.POINTER(_int), _vp]
+_lib.bras_batch_offsets.restype = _int
 _lib.bras_destroy.argtypes = [_vp]
 _lib.bras_destroy.restype = None
 _lib.bras_status_string.argtypes = [_int]
@@ -118,6 +128,29 @@ def bras_setup(dim, space, order, coords, cells, n_dof, l2g, signs=None, rho=Non
                          _ptr(cells), n_dof, _ptr(l2g), _ptr(signs), _ptr(rho), ctypes.byref(opt), _stream(stream))
     _check(rc, "bras_setup")
     return ctx
+
+
+def bras_setup_batched(dim, space, order, meshes, options=None, stream=None):
+    """meshes: list of dicts with torch/numpy arrays coords, cells, l2g and optional signs, rho
+    and the integer n_dof (the arrays must stay alive during the call)."""
+    descs = (bras_mesh_desc * len(meshes))()
+    for i, m in enumerate(meshes):
+        descs[i] = bras_mesh_desc(m["coords"].shape[0], _ptr(m["coords"]), m["cells"].shape[0], _ptr(m["cells"]),
+                                  int(m["n_dof"]), _ptr(m["l2g"]), _ptr(m.get("signs")), _ptr(m.get("rho")))
+    ctx = _vp()
+    opt = options or bras_options(0, 0, 1)
+    rc = _lib.bras_setup_batched(ctypes.byref(ctx), dim, space, order, len(meshes), descs, ctypes.byref(opt),
+                                 _stream(stream))
+    _check(rc, "bras_setup_batched")
+    return ctx
+
+
+def bras_batch_offsets(ctx):
+    n = _int()
+    _check(_lib.bras_batch_offsets(ctx, ctypes.byref(n), None), "bras_batch_offsets")
+    off = np.zeros(n.value + 1, dtype=np.int64)
+    _check(_lib.bras_batch_offsets(ctx, ctypes.byref(n), off.ctypes.data), "bras_batch_offsets")
+    return off
 
 
 def bras_mass_apply(ctx, precision, x, y, nrhs=1, stream=None):
@@ -193,6 +226,30 @@ class Context:
                               self._signs, self._rho, opt, stream)
         _, _, self.n_loc, self.n_blocks = bras_info(self.ctx)
 
+    @classmethod
+    def batched(cls, meshes, space: str, order: int, precisions: int = 0, block_elems: int = 0, stream=None):
+        """One context over several independent meshes: ``meshes`` is a list of
+        (coords, cells, n_dof, l2g, signs) tuples (numpy); vectors are concatenated per mesh."""
+        self = cls.__new__(cls)
+        keep = []
+        descs = []
+        for coords, cells, n_dof, l2g, signs in meshes:
+            d = {"coords": np.ascontiguousarray(coords, dtype=np.float64),
+                 "cells": np.ascontiguousarray(cells, dtype=np.int32),
+                 "l2g": np.ascontiguousarray(l2g, dtype=np.int32), "n_dof": int(n_dof),
+                 "signs": None if signs is None else np.ascontiguousarray(signs, dtype=np.int8)}
+            keep.append(d)
+            descs.append(d)
+        self.dim = meshes[0][0].shape[1]
+        self.space = SPACES[space]
+        self.order = order
+        opt = bras_options(precisions, block_elems, 1)
+        self.ctx = bras_setup_batched(self.dim, self.space, order, descs, opt, stream)
+        self.offsets = bras_batch_offsets(self.ctx)
+        self.n_dof, self.n_cell, self.n_loc, self.n_blocks = bras_info(self.ctx)
+        self.n_mesh = len(meshes)
+        return self
+
     def close(self):
         if getattr(self, "ctx", None):
             bras_destroy(self.ctx)
@@ -229,8 +286,9 @@ class Context:
         """Returns (x, iters, relres, status); b/x may be CUDA or CPU float64 tensors."""
         nrhs = 1 if b.dim() == 1 else b.shape[1]
         x = out if out is not None else torch.empty_like(b)
-        iters = np.zeros(nrhs, dtype=np.int32)
-        relres = np.zeros(nrhs, dtype=np.float64)
+        slots = max(nrhs, getattr(self, "n_mesh", 1))
+        iters = np.zeros(slots, dtype=np.int32)
+        relres = np.zeros(slots, dtype=np.float64)
         st = bras_pcg_solve(self.ctx, pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters, relres, stream)
         return x, iters, relres, st
 

@@ -118,7 +118,7 @@ bool is_device_ptr(const void* p) {
 
 int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const double* coords,
                int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
-               const double* rho, const bras_options* opt, cudaStream_t st) {
+               const double* rho, const bras_options* opt, cudaStream_t st, const int32_t* cell_group = nullptr) {
     const int nloc = n_local(dim, space, order);
     c->dim = dim;
     c->space = space;
@@ -160,7 +160,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     int64_t detail = -1;
     for (;;) {
         rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
-                          h_cells.data(), dim, BE, &t, &detail);
+                          h_cells.data(), dim, BE, &t, &detail, cell_group);
         if (rc) { set_detail(detail); return rc; }
         const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
         const size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
@@ -403,11 +403,129 @@ int bras_setup(bras_ctx** out, int dim, int space, int order, int64_t n_vert, co
     return BRAS_OK;
 }
 
+// Segments of at most kSegDofs dofs, each inside one mesh (the vector kernels of a batched
+// solve give one thread block per segment and reduce per mesh in a fixed order).
+static int build_segments(bras_ctx* c) {
+    constexpr int64_t kSegDofs = 8192;
+    std::vector<int32_t> smesh, mseg;
+    std::vector<int64_t> sbeg;
+    for (int m = 0; m < c->n_mesh; ++m) {
+        mseg.push_back((int32_t)smesh.size());
+        for (int64_t b = c->dof_off[m]; b < c->dof_off[m + 1]; b += kSegDofs) {
+            smesh.push_back(m);
+            sbeg.push_back(b);
+        }
+    }
+    mseg.push_back((int32_t)smesh.size());
+    sbeg.push_back(c->dof_off[c->n_mesh]);
+    c->nseg = (int)smesh.size();
+    // segment s ends at min(next start, end of its mesh)
+    std::vector<int64_t> bounds(2 * (size_t)c->nseg);
+    for (int s = 0; s < c->nseg; ++s) {
+        bounds[2 * s] = sbeg[s];
+        bounds[2 * s + 1] = std::min(sbeg[s] + kSegDofs, c->dof_off[smesh[s] + 1]);
+    }
+    int rc;
+    if ((rc = upload(c, &c->seg_mesh, smesh.data(), smesh.size()))) return rc;
+    if ((rc = upload(c, &c->seg_beg, bounds.data(), bounds.size()))) return rc;
+    if ((rc = upload(c, &c->mseg, mseg.data(), mseg.size()))) return rc;
+    return BRAS_OK;
+}
+
 static int apply_common(const bras_ctx* cc, int prec, int op, const void* x, void* y, int nrhs, void* stream) {
     set_detail(-1);
     if (!cc || !x || !y || nrhs < 1 || prec < 0 || prec > 2) return BRAS_ERR_INVALID;
     if (!has_precision(cc, prec)) return BRAS_ERR_PRECISION;
     return run_op(const_cast<bras_ctx*>(cc), prec, op, x, y, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+int bras_setup_batched(bras_ctx** out, int dim, int space, int order, int n_mesh, const bras_mesh_desc* meshes,
+                       const bras_options* opt, void* stream) {
+    set_detail(-1);
+    if (!out) return BRAS_ERR_INVALID;
+    *out = nullptr;
+    if (!meshes || n_mesh < 1 || (dim != 2 && dim != 3) || space < 0 || space > 2 || (space != BRAS_H1 && dim != 3))
+        return BRAS_ERR_INVALID;
+    const int nloc = n_local(dim, space, order);
+    if (nloc < 0) return BRAS_ERR_INVALID;
+    int64_t V = 0, E = 0, N = 0;
+    bool any_signs = false, any_rho = false;
+    for (int m = 0; m < n_mesh; ++m) {
+        const bras_mesh_desc& d = meshes[m];
+        if (!d.coords || !d.cells || !d.l2g || d.n_vert <= dim || d.n_cell <= 0 || d.n_dof <= 0) {
+            set_detail(m);
+            return BRAS_ERR_INVALID;
+        }
+        V += d.n_vert;
+        E += d.n_cell;
+        N += d.n_dof;
+        any_signs |= d.signs != nullptr;
+        any_rho |= d.rho != nullptr;
+    }
+    if (E >= (1ll << 31) || N >= (1ll << 31) || E * nloc >= (1ll << 31) || V >= (1ll << 31)) return BRAS_ERR_TOO_LARGE;
+    // concatenate (vertex ids and dofs shifted by the earlier meshes' counts)
+    std::vector<double> coords((size_t)V * dim), rho(any_rho ? (size_t)E : 0, 1.0);
+    std::vector<int32_t> cells((size_t)E * (dim + 1)), l2g((size_t)E * nloc), group((size_t)E);
+    std::vector<int8_t> signs(any_signs ? (size_t)E * nloc : 0, 1);
+    std::vector<int64_t> dof_off(n_mesh + 1, 0);
+    int64_t v0 = 0, e0 = 0, n0 = 0;
+    for (int m = 0; m < n_mesh; ++m) {
+        const bras_mesh_desc& d = meshes[m];
+        const size_t nc = (size_t)d.n_cell;
+        if (cudaMemcpy(coords.data() + v0 * dim, d.coords, sizeof(double) * d.n_vert * dim, cudaMemcpyDefault) != cudaSuccess ||
+            cudaMemcpy(cells.data() + e0 * (dim + 1), d.cells, sizeof(int32_t) * nc * (dim + 1), cudaMemcpyDefault) != cudaSuccess ||
+            cudaMemcpy(l2g.data() + e0 * nloc, d.l2g, sizeof(int32_t) * nc * nloc, cudaMemcpyDefault) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        if (d.signs && cudaMemcpy(signs.data() + e0 * nloc, d.signs, nc * nloc, cudaMemcpyDefault) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        if (d.rho && cudaMemcpy(rho.data() + e0, d.rho, sizeof(double) * nc, cudaMemcpyDefault) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        for (size_t i = 0; i < nc * (dim + 1); ++i) {
+            const int32_t vtx = cells[e0 * (dim + 1) + i];
+            if (vtx < 0 || vtx >= d.n_vert) { set_detail(m); return BRAS_ERR_INVALID; }
+            cells[e0 * (dim + 1) + i] = (int32_t)(vtx + v0);
+        }
+        for (size_t i = 0; i < nc * nloc; ++i) {
+            const int32_t g = l2g[e0 * nloc + i];
+            if (g < 0 || g >= d.n_dof) { set_detail(e0 * nloc + (int64_t)i); return BRAS_ERR_L2G_RANGE; }
+            l2g[e0 * nloc + i] = (int32_t)(g + n0);
+        }
+        for (size_t k = 0; k < nc; ++k) group[e0 + k] = m;
+        v0 += d.n_vert;
+        e0 += d.n_cell;
+        n0 += d.n_dof;
+        dof_off[m + 1] = n0;
+    }
+    bras_ctx* c = new (std::nothrow) bras_ctx();
+    if (!c) return BRAS_ERR_OOM;
+    int rc = setup_impl(c, dim, space, order, V, coords.data(), E, cells.data(), N, l2g.data(),
+                        any_signs ? signs.data() : nullptr, any_rho ? rho.data() : nullptr, opt,
+                        static_cast<cudaStream_t>(stream), group.data());
+    if (rc == BRAS_OK) {
+        c->n_mesh = n_mesh;
+        c->dof_off = dof_off;
+        rc = build_segments(c);
+    }
+    if (rc != BRAS_OK) {
+        bras_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return BRAS_OK;
+}
+
+int bras_batch_offsets(const bras_ctx* ctx, int* n_mesh, int64_t* dof_offsets) {
+    if (!ctx) return BRAS_ERR_INVALID;
+    if (n_mesh) *n_mesh = ctx->n_mesh;
+    if (dof_offsets) {
+        if (ctx->dof_off.empty()) {
+            dof_offsets[0] = 0;
+            dof_offsets[1] = ctx->n;
+        } else {
+            for (int m = 0; m <= ctx->n_mesh; ++m) dof_offsets[m] = ctx->dof_off[m];
+        }
+    }
+    return BRAS_OK;
 }
 
 int bras_mass_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs, void* stream) {

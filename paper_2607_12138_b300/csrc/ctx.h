@@ -37,7 +37,7 @@ struct HostTables {
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
                  const double* coords, const int32_t* cells, int dim, int BE, HostTables* t,
-                 int64_t* detail);
+                 int64_t* detail, const int32_t* cell_group = nullptr);
 
 }  // namespace bras
 
@@ -87,6 +87,16 @@ struct bras_ctx {
     size_t part_bytes = 0;
     int* status = nullptr;       // device status words
     bras::PcgWork* pcg = nullptr;
+
+    // batched multi-mesh contexts: mesh m owns dofs [dof_off[m], dof_off[m+1]); the vector
+    // kernels of the solve work on segments of one mesh each (seg_beg[s]..seg_beg[s+1]),
+    // mesh m owning segments [mseg[m], mseg[m+1])
+    int n_mesh = 1;
+    int nseg = 0;
+    std::vector<int64_t> dof_off;
+    int32_t* seg_mesh = nullptr;
+    int64_t* seg_beg = nullptr;
+    int32_t* mseg = nullptr;
 
     std::vector<void*> owned;    // every device allocation, freed by bras_destroy
 };

@@ -32,6 +32,7 @@ struct PcgWork {
     int* iparam = nullptr;        // [0] = maxit, [1] = iterations done
     double* h_param = nullptr;    // pinned staging of dparam/iparam
     int nrhs = 0;
+    int slots = 0;                // scalar slots: max(nrhs, meshes of a batch)
     int64_t n = 0;
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xs = nullptr, *bs = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr;
@@ -80,9 +81,11 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
     w->q = (double*)d(nv * 8);
     w->xs = (double*)d(nv * 8);
     w->bs = (double*)d(nv * 8);
-    w->partial = (double*)d((size_t)kDotBlocks * w->nrhs * 8);
-    w->sc = (double*)d((size_t)S_COUNT * w->nrhs * 8);
-    w->flags = (int*)d((size_t)(2 * w->nrhs + 2) * 4);
+    const size_t slots = (size_t)std::max(w->nrhs, c->n_mesh);
+    w->slots = (int)slots;
+    w->partial = (double*)d(std::max((size_t)kDotBlocks * w->nrhs, (size_t)c->nseg) * 8);
+    w->sc = (double*)d((size_t)S_COUNT * slots * 8);
+    w->flags = (int*)d((2 * slots + 2) * 4);
     w->dparam = (double*)d(8 * 2);
     w->ticket = (unsigned int*)d(16);
     if (!w->ticket || cudaMemset(w->ticket, 0, 16) != cudaSuccess) return BRAS_ERR_OOM;
@@ -99,8 +102,8 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
         w->x32 = (float*)d(nv * 4);
         if (!w->r32 || !w->z32 || !w->p32 || !w->q32 || !w->x32) return BRAS_ERR_OOM;
     }
-    if (cudaMallocHost(&w->h_flags, (2 * w->nrhs + 2) * sizeof(int)) != cudaSuccess) return BRAS_ERR_OOM;
-    if (cudaMallocHost(&w->h_sc, (size_t)S_COUNT * w->nrhs * sizeof(double)) != cudaSuccess) return BRAS_ERR_OOM;
+    if (cudaMallocHost(&w->h_flags, (2 * slots + 2) * sizeof(int)) != cudaSuccess) return BRAS_ERR_OOM;
+    if (cudaMallocHost(&w->h_sc, S_COUNT * slots * sizeof(double)) != cudaSuccess) return BRAS_ERR_OOM;
     return BRAS_OK;
 }
 
@@ -249,6 +252,112 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
     block_partial_and_finish(F, R, red);
 }
 
+// ---- batched (segmented) variants: vectors are one rhs each of n_mesh independent systems;
+// thread block s works on the dofs [seg[2s], seg[2s+1]) of mesh seg_mesh[s] and the last block
+// reduces, mesh by mesh, the partials of that mesh's blocks in a fixed order (one warp per
+// mesh: fixed lane assignment, fixed shuffle tree).
+struct SegArgs {
+    const int32_t* seg_mesh;   // [nseg] mesh of each segment
+    const int64_t* seg;        // [2 * nseg] begin, end of each segment
+    const int32_t* mseg;       // [M + 1] first segment of each mesh
+    int M;
+};
+
+__device__ void seg_partial_and_finish(const FinArgs& F, const SegArgs& G, double* red) {
+    const int tid = threadIdx.x;
+    __shared__ unsigned int s_last;
+    __shared__ int cnt_s[256];
+    for (int h = 128; h > 0; h >>= 1) {
+        __syncthreads();
+        if (tid < h) red[tid] += red[tid + h];
+    }
+    __syncthreads();
+    if (tid == 0) F.partial[blockIdx.x] = red[0];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(F.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int warp = tid / 32, lane = tid % 32;
+    for (int m = warp; m < G.M; m += 8) {
+        const int g0 = G.mseg[m], g1 = G.mseg[m + 1];
+        double v = 0.0;
+        for (int g = g0 + lane; g < g1; g += 32) v += __ldcg(&F.partial[g]);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) apply_fin(F, G.M, m, v);
+    }
+    __syncthreads();
+    int c = 0;
+    for (int m = tid; m < G.M; m += 256) c += F.flags[m];
+    cnt_s[tid] = c;
+    for (int h = 128; h > 0; h >>= 1) {
+        __syncthreads();
+        if (tid < h) cnt_s[tid] += cnt_s[tid + h];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int cnt = cnt_s[0];
+        F.flags[2 * G.M] = cnt;
+        if (F.kind == FIN_RR && F.iparam) {
+            const int done = ++F.iparam[1];
+            cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
+        }
+        *F.ticket = 0u;
+    }
+}
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_seg_dot(const TA* __restrict__ a, const TB* __restrict__ b, SegArgs G,
+                                                 FinArgs F) {
+    __shared__ double red[256];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    double acc = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) acc += (double)a[i] * (double)b[i];
+    red[threadIdx.x] = acc;
+    seg_partial_and_finish(F, G, red);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_seg_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                       const T* __restrict__ q, const double* __restrict__ alpha,
+                                                       SegArgs G, FinArgs F) {
+    __shared__ double red[256];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    const T a = (T)alpha[G.seg_mesh[blockIdx.x]];
+    double acc = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) {
+        x[i] = fma(a, p[i], x[i]);
+        const T v = fma(-a, q[i], r[i]);
+        r[i] = v;
+        acc += (double)v * (double)v;
+    }
+    red[threadIdx.x] = acc;
+    seg_partial_and_finish(F, G, red);
+}
+
+template <typename T>
+__global__ void k_seg_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, SegArgs G) {
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    const T bt = (T)beta[G.seg_mesh[blockIdx.x]];
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) p[i] = fma(bt, p[i], z[i]);
+}
+
+__global__ void k_seg_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ s,
+                                   SegArgs G) {
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    const double sc = s[G.seg_mesh[blockIdx.x]];
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) r32[i] = (float)(r[i] * sc);
+}
+
+__global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ s,
+                                SegArgs G) {
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    const double sc = s[G.seg_mesh[blockIdx.x]];
+    if (!(sc > 0.0)) return;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) x[i] += (double)d[i] / sc;
+}
+
 template <typename T>
 __global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
@@ -295,9 +404,49 @@ static FinArgs fin_args(PcgWork* w, int kind, int* iparam = nullptr, cudaGraphCo
     return F;
 }
 
+static SegArgs seg_args(const bras_ctx* c) {
+    SegArgs G;
+    G.seg_mesh = c->seg_mesh;
+    G.seg = c->seg_beg;
+    G.mseg = c->mseg;
+    G.M = c->n_mesh;
+    return G;
+}
+
+static bool batched(const bras_ctx* c) { return c->n_mesh > 1 && c->nseg > 0; }
+
+// Dot products / fused updates on either layout: R interleaved rhs, or (batched) one rhs per
+// mesh with n_mesh scalar slots.
 template <typename TA, typename TB>
-static cudaError_t dot(PcgWork* w, const TA* a, const TB* b, int64_t n, int R, int kind, cudaStream_t st) {
-    k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, n, R, fin_args(w, kind));
+static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    if (batched(c)) k_seg_dot<TA, TB><<<c->nseg, 256, 0, st>>>(a, b, seg_args(c), fin_args(w, kind));
+    else k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, int R, cudaGraphConditionalHandle cond,
+                              cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    if (batched(c))
+        k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
+                                                     fin_args(w, FIN_RR, w->iparam, cond));
+    else
+        k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
+                                                    fin_args(w, FIN_RR, w->iparam, cond));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t vupdate_p(bras_ctx* c, T* p, const T* z, int R, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    if (batched(c)) k_seg_update_p<T><<<c->nseg, 256, 0, st>>>(p, z, w->sc + S_BETA * S, seg_args(c));
+    else k_update_p<T><<<grid_for(c->n * R), 256, 0, st>>>(p, z, w->sc + S_BETA * S, c->n * R, R);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -340,15 +489,14 @@ static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T*
     PcgWork* w = c->pcg;
     const int64_t n = c->n, nv = n * R;
     RC(precond(c, pc, prec, r, z, R, st));
-    CK(dot(w, r, z, n, R, FIN_BETA, st));
-    k_update_p<T><<<grid_for(nv), 256, 0, st>>>(p, z, w->sc + S_BETA * R, nv, R);
-    count_launch(1);
+    CK(vdot(c, r, z, R, FIN_BETA, st));
+    CK(vupdate_p<T>(c, p, z, R, st));
     RC(run_op(c, prec, OP_MASS, p, q, R, st));
-    CK(dot(w, p, q, n, R, FIN_ALPHA, st));
-    k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * R, n, R,
-                                                fin_args(w, FIN_RR, w->iparam, cond));
-    count_launch(1);
-    CK(cudaGetLastError());
+    CK(vdot(c, p, q, R, FIN_ALPHA, st));
+    CK(vupdate_xr<T>(c, x, r, p, q, R, cond, st));
+    (void)w;
+    (void)n;
+    (void)nv;
     return BRAS_OK;
 }
 
@@ -413,6 +561,8 @@ static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z,
                     int maxit, cudaStream_t st) {
     PcgWork* w = c->pcg;
     const int64_t n = c->n, nv = n * R;
+    const int S = batched(c) ? c->n_mesh : R;    // scalar slots (rhs, or meshes of a batch)
+    (void)n;
     cudaGraphExec_t exec = nullptr;
     int kpi = 0;
     RC(get_graph<T>(c, prec, pc, R, x, r, z, p, q, &exec, &kpi));
@@ -425,16 +575,16 @@ static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z,
     CK(cudaMemsetAsync(x, 0, sizeof(T) * nv, st));
     CK(cudaMemsetAsync(p, 0, sizeof(T) * nv, st));
     CK(cudaMemcpyAsync(r, b, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemsetAsync(w->flags + 2 * R + 1, 0, sizeof(int), st));
-    CK(dot(w, r, r, n, R, FIN_INIT_RR, st));
+    CK(cudaMemsetAsync(w->flags + 2 * S + 1, 0, sizeof(int), st));
+    CK(vdot(c, r, r, R, FIN_INIT_RR, st));
     if (maxit > 0) CK(cudaGraphLaunch(exec, st));
-    CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * R + 2), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hp, w->iparam, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (maxit > 0) count_launch(kpi * hp[1]);
-    if (w->h_flags[2 * R + 1] != 0) return w->h_flags[2 * R + 1];
-    return w->h_flags[2 * R] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
+    if (w->h_flags[2 * S + 1] != 0) return w->h_flags[2 * S + 1];
+    return w->h_flags[2 * S] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
 }
 
 static bool host_ptr(const void* p) {
@@ -449,6 +599,8 @@ static bool host_ptr(const void* p) {
 int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* b, double* x, int R, double rtol,
                    int maxit, int* iters, double* relres, cudaStream_t st) {
     if (R > kMaxRhs) return BRAS_ERR_TOO_LARGE;
+    if (batched(c) && R != 1) return BRAS_ERR_INVALID;
+    const int S = batched(c) ? c->n_mesh : R;     // scalar slots: rhs, or meshes of a batch
     const bool mixed = mode == BRAS_SOLVE_MIXED;
     RC(ensure_pcg(c, R, mixed));
     RC(ensure_part(c, R));
@@ -463,31 +615,31 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
     }
     if (hx) dx = w->xs;
     int status = BRAS_OK;
-    std::vector<int> its(R, 0);
-    std::vector<double> rel(R, 0.0);
+    std::vector<int> its(S, 0);
+    std::vector<double> rel(S, 0.0);
     if (!mixed) {
         status = pcg_core<double>(c, BRAS_FP64, pc, db, w->xs, w->r, w->z, w->p, w->q, R, rtol, maxit, st);
         if (status < 0) return status;
         if (dx != w->xs) CK(cudaMemcpyAsync(dx, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-        for (int r = 0; r < R; ++r) {
-            its[r] = w->h_flags[R + r];
-            const double rr0 = w->h_sc[S_RR0 * R + r];
-            rel[r] = rr0 > 0 ? std::sqrt(w->h_sc[S_RR * R + r] / rr0) : 0.0;
+        for (int r = 0; r < S; ++r) {
+            its[r] = w->h_flags[S + r];
+            const double rr0 = w->h_sc[S_RR0 * S + r];
+            rel[r] = rr0 > 0 ? std::sqrt(w->h_sc[S_RR * S + r] / rr0) : 0.0;
         }
     } else {
-        // x = 0, r = b; ||b||
+        // x = 0, r = b; ||b|| per slot
         CK(cudaMemsetAsync(dx, 0, sizeof(double) * nv, st));
         CK(cudaMemcpyAsync(w->r, db, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-        CK(dot(w, db, db, n, R, FIN_NORM, st));
-        CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        CK(vdot(c, db, db, R, FIN_NORM, st));
+        CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * S, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        std::vector<double> bn(R), rn(R), scale(R);
-        for (int r = 0; r < R; ++r) { bn[r] = std::sqrt(w->h_sc[r]); rn[r] = bn[r]; }
+        std::vector<double> bn(S), rn(S), scale(S);
+        for (int r = 0; r < S; ++r) { bn[r] = std::sqrt(w->h_sc[r]); rn[r] = bn[r]; }
         int total_inner = 0;
         bool done = false;
         for (int outer = 0; outer < 60 && !done; ++outer) {
             double worst = 0.0;
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < S; ++r) {
                 rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
                 worst = std::max(worst, rel[r]);
                 scale[r] = (bn[r] > 0 && rel[r] > rtol) ? 1.0 / rn[r] : 0.0;
@@ -496,25 +648,34 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
             if (total_inner >= maxit) break;
             // inner tolerance: as deep as FP32 allows, no deeper than needed
             const double tin = std::max(1e-6, std::min(1e-2, 0.5 * rtol / worst));
-            CK(cudaMemcpyAsync(w->sc + S_SCALE * R, scale.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
-            k_scale_to_f32<<<grid_for(nv), 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * R, nv, R); count_launch(1);
+            CK(cudaMemcpyAsync(w->sc + S_SCALE * S, scale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+            if (batched(c))
+                k_seg_scale_to_f32<<<c->nseg, 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * S, seg_args(c));
+            else
+                k_scale_to_f32<<<grid_for(nv), 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * S, nv, R);
+            count_launch(1);
             CK(cudaGetLastError());
             int s = pcg_core<float>(c, inner_prec, pc, w->r32, w->x32, w->q32 /*r*/, w->z32, w->p32,
                                     reinterpret_cast<float*>(w->z) /*q*/, R, tin, maxit - total_inner, st);
             if (s < 0) return s;
             int mx = 0;
-            for (int r = 0; r < R; ++r) { its[r] += w->h_flags[R + r]; mx = std::max(mx, w->h_flags[R + r]); }
+            for (int r = 0; r < S; ++r) { its[r] += w->h_flags[S + r]; mx = std::max(mx, w->h_flags[S + r]); }
             total_inner += std::max(mx, 1);
-            k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * R, nv, R); count_launch(1);
+            if (batched(c))
+                k_seg_accum_f32<<<c->nseg, 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * S, seg_args(c));
+            else
+                k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * S, nv, R);
+            count_launch(1);
             RC(run_op(c, BRAS_FP64, OP_MASS, dx, w->q, R, st));
-            k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv); count_launch(1);
-            CK(dot(w, w->r, w->r, n, R, FIN_NORM, st));
-            CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv);
+            count_launch(1);
+            CK(vdot(c, w->r, w->r, R, FIN_NORM, st));
+            CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * S, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            for (int r = 0; r < R; ++r) rn[r] = std::sqrt(w->h_sc[r]);
+            for (int r = 0; r < S; ++r) rn[r] = std::sqrt(w->h_sc[r]);
         }
         double worst = 0.0;
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < S; ++r) {
             rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
             worst = std::max(worst, rel[r]);
         }
@@ -522,7 +683,7 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
     }
     if (hx) CK(cudaMemcpyAsync(x, dx, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < S; ++r) {
         if (iters) iters[r] = its[r];
         if (relres) relres[r] = rel[r];
     }

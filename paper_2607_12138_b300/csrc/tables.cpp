@@ -32,7 +32,7 @@ uint64_t spread3(uint64_t v) {          // 21 bits -> every third bit
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
                  const double* coords, const int32_t* cells, int dim, int BE, HostTables* t,
-                 int64_t* detail) {
+                 int64_t* detail, const int32_t* cell_group) {
     // multiplicities d_i = #{(K, a) : l2g[K, a] = i}  (D = P^T P)
     std::vector<int32_t> d(n, 0);
     for (int64_t i = 0; i < E * nloc; ++i) {
@@ -59,7 +59,8 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
             lo[c] = std::min(lo[c], s);
             hi[c] = std::max(hi[c], s);
         }
-    std::vector<std::pair<uint64_t, int32_t>> key(E);
+    // cells of one group (one mesh of a batch) stay contiguous: sort by (group, Morton code)
+    std::vector<std::pair<std::pair<int32_t, uint64_t>, int32_t>> key(E);
     for (int64_t k = 0; k < E; ++k) {
         uint64_t code = 0;
         for (int c = 0; c < dim; ++c) {
@@ -68,7 +69,7 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
             uint64_t q = (uint64_t)std::min(2097151.0, std::floor(f * 2097151.0));
             code |= spread3(q) << c;
         }
-        key[k] = {code, (int32_t)k};
+        key[k] = {{cell_group ? cell_group[k] : 0, code}, (int32_t)k};
     }
     std::sort(key.begin(), key.end());
     t->perm.resize(E);

@@ -261,3 +261,42 @@ def test_autograd_weighted_solve():
             lm = 0.5 * ((solver(z - h * v, b) - xs) ** 2).sum().item()
             fd = (lp - lm) / (2 * h)
             assert abs(fd - (z.grad @ v).item()) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _batch(space, order, sizes, seed0=10):
+    meshes, probs = [], []
+    for i, (nx, nz) in enumerate(sizes):
+        mesh = mg.unit_cube_mesh(nx, jitter=0.15, seed=seed0 + i, nz=nz)
+        n, l2g, s = mg.dof_map(mesh, space, order)
+        meshes.append((mesh.coords, mesh.cells, n, l2g, s))
+        probs.append(Problem(mesh, space, order, l2g, s, n))
+    return meshes, probs
+
+
+@pytest.mark.parametrize("space,order", [("hdiv", 1), ("hdiv", 2), ("h1", 2)])
+def test_batched_multi_mesh(space, order):
+    """Several uneven meshes in one context: applies equal the per-mesh oracle operators and
+    one solve reaches each mesh's own tolerance with the oracle's iteration count."""
+    sizes = [(2, 1), (4, 3), (3, 5), (1, 1), (5, 2)]
+    meshes, probs = _batch(space, order, sizes)
+    ctx = B.Context.batched(meshes, space, order)
+    off = ctx.offsets
+    assert ctx.n_mesh == len(sizes) and off[-1] == sum(p.n_dof for p in probs)
+    b = np.concatenate([mg.rhs(p.n_dof, 1, seed=20 + i) for i, p in enumerate(probs)])
+    bt = torch.as_tensor(b, device="cuda")
+    yb = ctx.bras_apply(bt).cpu().numpy()
+    ym = ctx.mass_apply(bt).cpu().numpy()
+    for i, p in enumerate(probs):
+        seg = slice(off[i], off[i + 1])
+        assert rel_err(yb[seg], p.B @ b[seg]) <= 1e-12
+        assert rel_err(ym[seg], p.M @ b[seg]) <= 1e-12
+    for mode in (B.SOLVE_FP64, B.SOLVE_MIXED):
+        x, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=mode, rtol=1e-10)
+        assert st == B.OK and len(its) == len(sizes)
+        xg = x.cpu().numpy()
+        for i, p in enumerate(probs):
+            seg = slice(off[i], off[i + 1])
+            assert np.linalg.norm(b[seg] - p.M @ xg[seg]) <= 1.05e-10 * np.linalg.norm(b[seg])
+            if mode == B.SOLVE_FP64:
+                _, its_o, _ = pcg(p.mass_apply, b[seg], p.bras_apply, rtol=1e-10)
+                assert abs(int(its[i]) - its_o) <= 1
