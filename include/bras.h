@@ -53,7 +53,11 @@ enum { BRAS_H1 = 0, BRAS_HCURL = 1, BRAS_HDIV = 2 };
  * BRAS_FP32: float vectors, float element data, float arithmetic.
  * BRAS_BF16: float vectors and arithmetic; H(curl)/H(div) local inverses stored in
  *            bfloat16 (H1 has no per-element matrix: same as BRAS_FP32 there).       */
-enum { BRAS_FP64 = 0, BRAS_FP32 = 1, BRAS_BF16 = 2 };
+enum { BRAS_FP64 = 0, BRAS_FP32 = 1, BRAS_BF16 = 2, BRAS_FP64X = 3 };
+/* BRAS_FP64X (bras_mass_apply only): double vectors and scatter sums; for H1 the local
+ * products run in float-float arithmetic on the FP32 units (an error-free split of each
+ * product into two floats and a compensated sum, about 2^-48 relative per term), the form
+ * the mixed solve uses for its refinement residual b - M x; other spaces use FP64. */
 
 /* Preconditioner of a solve: none, diag(M)^{-1} (Jacobi), or BRAS. */
 enum { BRAS_PC_NONE = 0, BRAS_PC_JACOBI = 1, BRAS_PC_BRAS = 2 };
@@ -83,6 +87,8 @@ typedef struct {
                             0 means all three                                           */
     int block_elems;     /* elements per scatter block, 32..256; 0 = 256                 */
     int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
+    int simt_only;       /* 1: H1 FP32 applies on the FP32 units instead of the tensor-core
+                            (3xTF32 tcgen05) local GEMM; 0 = tensor cores where supported  */
 } bras_options;
 
 /*

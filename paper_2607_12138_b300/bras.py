@@ -25,7 +25,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 H1, HCURL, HDIV = 0, 1, 2
-FP64, FP32, BF16 = 0, 1, 2
+FP64, FP32, BF16, FP64X = 0, 1, 2, 3
 PC_NONE, PC_JACOBI, PC_BRAS = 0, 1, 2
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV}
@@ -43,7 +43,8 @@ class BrasError(RuntimeError):
 
 
 class bras_options(ctypes.Structure):
-    _fields_ = [("precisions", ctypes.c_int), ("block_elems", ctypes.c_int), ("max_nrhs", ctypes.c_int)]
+    _fields_ = [("precisions", ctypes.c_int), ("block_elems", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("simt_only", ctypes.c_int)]
 
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -123,7 +124,7 @@ def bras_n_local(dim: int, space: int, order: int) -> int:
 
 def bras_setup(dim, space, order, coords, cells, n_dof, l2g, signs=None, rho=None, options=None, stream=None):
     ctx = _vp()
-    opt = options or bras_options(0, 0, 1)
+    opt = options or bras_options(0, 0, 1, 0)
     rc = _lib.bras_setup(ctypes.byref(ctx), dim, space, order, coords.shape[0], _ptr(coords), cells.shape[0],
                          _ptr(cells), n_dof, _ptr(l2g), _ptr(signs), _ptr(rho), ctypes.byref(opt), _stream(stream))
     _check(rc, "bras_setup")
@@ -138,7 +139,7 @@ def bras_setup_batched(dim, space, order, meshes, options=None, stream=None):
         descs[i] = bras_mesh_desc(m["coords"].shape[0], _ptr(m["coords"]), m["cells"].shape[0], _ptr(m["cells"]),
                                   int(m["n_dof"]), _ptr(m["l2g"]), _ptr(m.get("signs")), _ptr(m.get("rho")))
     ctx = _vp()
-    opt = options or bras_options(0, 0, 1)
+    opt = options or bras_options(0, 0, 1, 0)
     rc = _lib.bras_setup_batched(ctypes.byref(ctx), dim, space, order, len(meshes), descs, ctypes.byref(opt),
                                  _stream(stream))
     _check(rc, "bras_setup_batched")
@@ -208,7 +209,8 @@ class Context:
     """One BRAS context on the current CUDA device (tensors in, tensors out)."""
 
     def __init__(self, coords, cells, space: str, order: int, n_dof: int, l2g, signs=None, rho=None,
-                 precisions: int = 0, block_elems: int = 0, max_nrhs: int = 1, stream=None):
+                 precisions: int = 0, block_elems: int = 0, max_nrhs: int = 1, simt_only: bool = False,
+                 stream=None):
         dev = torch.device("cuda")
         self.dim = coords.shape[1]
         self.space = SPACES[space]
@@ -221,7 +223,7 @@ class Context:
         self._signs = t(signs, torch.int8)
         self._rho = t(rho, torch.float64)
         self.n_cell = int(self._cells.shape[0])
-        opt = bras_options(precisions, block_elems, max_nrhs)
+        opt = bras_options(precisions, block_elems, max_nrhs, int(simt_only))
         self.ctx = bras_setup(self.dim, self.space, order, self._coords, self._cells, self.n_dof, self._l2g,
                               self._signs, self._rho, opt, stream)
         _, _, self.n_loc, self.n_blocks = bras_info(self.ctx)
@@ -243,7 +245,7 @@ class Context:
         self.dim = meshes[0][0].shape[1]
         self.space = SPACES[space]
         self.order = order
-        opt = bras_options(precisions, block_elems, 1)
+        opt = bras_options(precisions, block_elems, 1, 0)
         self.ctx = bras_setup_batched(self.dim, self.space, order, descs, opt, stream)
         self.offsets = bras_batch_offsets(self.ctx)
         self.n_dof, self.n_cell, self.n_loc, self.n_blocks = bras_info(self.ctx)
@@ -263,7 +265,7 @@ class Context:
 
     @staticmethod
     def _dtype(precision):
-        return torch.float64 if precision == FP64 else torch.float32
+        return torch.float64 if precision in (FP64, FP64X) else torch.float32
 
     def _apply(self, fn, x, precision, out=None, stream=None):
         x = x.contiguous()

@@ -156,6 +156,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const bool fixed_be = opt && opt->block_elems;
+    const bool want_tc = space == BRAS_H1 && h1_tc_supported(nloc) && !(opt && opt->simt_only);
     HostTables t;
     int64_t detail = -1;
     for (;;) {
@@ -163,7 +164,14 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
                           h_cells.data(), dim, BE, &t, &detail, cell_group);
         if (rc) { set_detail(detail); return rc; }
         const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
-        const size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
+        size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
+        if (want_tc) {   // the FP32 tensor-core kernel: B tiles instead of the SIMT reference copy
+            BlockArgs tmp{};
+            tmp.max_pkt = t.max_pkt;
+            tmp.max_u = t.max_u;
+            tmp.max_ne = t.max_ne;
+            s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
+        }
         const bool fits = s64 <= (size_t)smem_optin && (fixed_be || 2 * (s32 + 1024) <= (size_t)smem_sm);
         if (fits || BE <= 32) {
             if (s64 > (size_t)smem_optin) return BRAS_ERR_TOO_LARGE;
@@ -238,6 +246,14 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         if ((rc = upload(c, &c->Minvref64, inv.data(), inv.size()))) return rc;
         if ((rc = upload(c, &c->Mref32, R32.data(), R32.size()))) return rc;
         if ((rc = upload(c, &c->Minvref32, I32.data(), I32.size()))) return rc;
+        if (want_tc) {
+            std::vector<unsigned char> tm, ti;
+            h1_tc_build_btile(ref.R.data(), n, tm);
+            h1_tc_build_btile(inv.data(), n, ti);
+            if ((rc = upload(c, &c->btile_mass, tm.data(), tm.size()))) return rc;
+            if ((rc = upload(c, &c->btile_bras, ti.data(), ti.size()))) return rc;
+            c->use_tc = true;
+        }
         if (!(c->mscale64 = dalloc<double>(c, n_cell)) || !(c->bscale64 = dalloc<double>(c, n_cell)) ||
             !(c->mscale32 = dalloc<float>(c, n_cell)) || !(c->bscale32 = dalloc<float>(c, n_cell)))
             return BRAS_ERR_OOM;
@@ -305,6 +321,7 @@ int ensure_part(bras_ctx* c, int nrhs) {
 }
 
 LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
+    if (prec == BRAS_FP64X) prec = BRAS_FP64;
     LaunchCommon L{};
     BlockArgs& A = L.A;
     A.blk_e0 = c->blk_e0;
@@ -348,16 +365,19 @@ int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cuda
     LaunchCommon L = make_launch(c, prec, op);
     cudaError_t err;
     const bool h1 = c->space == BRAS_H1;
-    if (prec == BRAS_FP64) {
+    if (prec == BRAS_FP64 || prec == BRAS_FP64X) {
         auto* xx = static_cast<const double*>(x);
         auto* yy = static_cast<double*>(y);
         auto* pp = static_cast<double*>(c->part);
-        err = h1 ? launch_h1_f64(L, c->nloc, op, xx, yy, pp, nrhs, st) : launch_pk_f64(L, c->nloc, op, xx, yy, pp, nrhs, st);
+        if (h1 && prec == BRAS_FP64X && op == OP_MASS) err = launch_h1_df(L, c->nloc, xx, yy, pp, nrhs, st);
+        else err = h1 ? launch_h1_f64(L, c->nloc, op, xx, yy, pp, nrhs, st) : launch_pk_f64(L, c->nloc, op, xx, yy, pp, nrhs, st);
     } else {
         auto* xx = static_cast<const float*>(x);
         auto* yy = static_cast<float*>(y);
         auto* pp = static_cast<float*>(c->part);
-        if (h1) err = launch_h1_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
+        if (h1 && c->use_tc && (op == OP_MASS || op == OP_BRAS))
+            err = launch_h1_tc(L, op == OP_MASS ? c->btile_mass : c->btile_bras, c->nloc, op, xx, yy, pp, nrhs, st);
+        else if (h1) err = launch_h1_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
         else if (prec == BRAS_BF16 && op == OP_BRAS) err = launch_pk_bf16(L, c->nloc, op, xx, yy, pp, nrhs, st);
         else err = launch_pk_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
     }
@@ -365,7 +385,7 @@ int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cuda
 }
 
 bool has_precision(const bras_ctx* c, int prec) {
-    if (prec == BRAS_FP64) return true;
+    if (prec == BRAS_FP64 || prec == BRAS_FP64X) return true;
     if (c->space == BRAS_H1) return prec == BRAS_FP32 || prec == BRAS_BF16;
     if (prec == BRAS_FP32) return c->Minvpk32 && c->Mpk32;
     if (prec == BRAS_BF16) return c->Minvpkbf && c->Mpk32;
@@ -434,7 +454,8 @@ static int build_segments(bras_ctx* c) {
 
 static int apply_common(const bras_ctx* cc, int prec, int op, const void* x, void* y, int nrhs, void* stream) {
     set_detail(-1);
-    if (!cc || !x || !y || nrhs < 1 || prec < 0 || prec > 2) return BRAS_ERR_INVALID;
+    if (!cc || !x || !y || nrhs < 1 || prec < 0 || prec > 3) return BRAS_ERR_INVALID;
+    if (prec == BRAS_FP64X && op != OP_MASS) return BRAS_ERR_INVALID;
     if (!has_precision(cc, prec)) return BRAS_ERR_PRECISION;
     return run_op(const_cast<bras_ctx*>(cc), prec, op, x, y, nrhs, static_cast<cudaStream_t>(stream));
 }
@@ -583,7 +604,7 @@ int bras_info(const bras_ctx* ctx, int64_t* n_dof, int64_t* n_cell, int* n_loc, 
 
 int64_t bras_algorithmic_bytes(const bras_ctx* ctx, int precision, int nrhs, int bras) {
     if (!ctx || nrhs < 1) return -1;
-    const int64_t w = precision == BRAS_FP64 ? 8 : 4;
+    const int64_t w = (precision == BRAS_FP64 || precision == BRAS_FP64X) ? 8 : 4;
     int64_t bytes = ctx->E * ctx->nloc * 4;                          // l2g map
     if (ctx->space == BRAS_H1) bytes += ctx->E * w;                  // per-cell factor
     else {

@@ -106,10 +106,35 @@ template <int N, typename T> struct PadTo {
     static constexpr int value = (N + W - 1) / W * W;
 };
 
-template <int NLOC, typename T, typename S, int KIND, int OP>
+// Float-float product term: (sh, sl) += (mh + ml) * (vh + vl) to about 2^-48 relative, on the
+// FP32 units (B300 runs FP32 at 64x its FP64 rate).  Error-free product of the high parts
+// (p + e = mh * vh exactly, by an FMA), first-order cross terms, and a Knuth two-sum into the
+// running pair; the _rn intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void df_term(float mh, float ml, float vh, float vl, float& sh, float& sl) {
+    const float p = __fmul_rn(mh, vh);
+    const float e = __fmaf_rn(mh, vh, -p);
+    const float t = __fmaf_rn(mh, vl, __fmaf_rn(ml, vh, e));
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, t));
+}
+
+// (ah, al) += (bh, bl) as float-float pairs (two-sum of the high parts, low parts added).
+__device__ __forceinline__ void df_merge(float& ah, float& al, float bh, float bl) {
+    const float s = __fadd_rn(ah, bh);
+    const float bp = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+    ah = s;
+    al = __fadd_rn(__fadd_rn(al, bl), err);
+}
+
+template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
 __global__ void __launch_bounds__(256, 1)
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
+    static_assert(!DF || (sizeof(T) == 8 && KIND == KIND_H1), "float-float path: FP64 vectors, H1 only");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // 2 mbarriers
     unsigned char* tab = smem_raw + 128;                                 // table packet
@@ -136,7 +161,13 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         const T* ref = static_cast<const T*>(A.refmat);
         for (int i = tid; i < NLOC * NPAD; i += blockDim.x) {
             const int a = i / NPAD, q = i - a * NPAD;
-            Ms[i] = q < NLOC ? ref[a * NLOC + q] : T(0);
+            const T v = q < NLOC ? ref[a * NLOC + q] : T(0);
+            if constexpr (DF) {   // (hi, lo) float pair in the slot of one double
+                const float hi = (float)v;
+                reinterpret_cast<float2*>(Ms)[i] = make_float2(hi, (float)((double)v - (double)hi));
+            } else {
+                Ms[i] = v;
+            }
         }
     }
     __syncthreads();   // barriers initialised before anyone polls them
@@ -188,7 +219,32 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
 #pragma unroll
         for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
-        if (KIND == KIND_H1) {
+        if constexpr (DF) {
+            const T c = static_cast<const T*>(A.scale)[e0 + e];
+            float vh[NPAD], vl[NPAD];
+#pragma unroll
+            for (int a = 0; a < NPAD; ++a) {
+                vh[a] = (float)xl[a];
+                vl[a] = (float)((double)xl[a] - (double)vh[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < NLOC; ++a) {
+                // four independent compensated chains (terms q mod 4), merged at the end
+                float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+                const float4* row = reinterpret_cast<const float4*>(Ms + a * NPAD);   // two (hi, lo) pairs
+#pragma unroll
+                for (int q = 0; q < NPAD / 2; ++q) {
+                    const float4 m = row[q];
+                    df_term(m.x, m.y, vh[2 * q], vl[2 * q], sh[(2 * q) & 3], sl[(2 * q) & 3]);
+                    df_term(m.z, m.w, vh[2 * q + 1], vl[2 * q + 1], sh[(2 * q + 1) & 3], sl[(2 * q + 1) & 3]);
+                }
+                df_merge(sh[0], sl[0], sh[1], sl[1]);
+                df_merge(sh[2], sl[2], sh[3], sl[3]);
+                df_merge(sh[0], sl[0], sh[2], sl[2]);
+                T acc = ((double)sh[0] + (double)sl[0]) * c;
+                zs[a * ne + e] = ((neg >> a) & 1) ? -acc : acc;
+            }
+        } else if (KIND == KIND_H1) {
             using V = typename Vec4<T>::type;
             constexpr int W = Vec4<T>::W;
             const T c = static_cast<const T*>(A.scale)[e0 + e];
@@ -278,12 +334,12 @@ size_t block_smem_bytes(const BlockArgs& A) {
 }
 
 // Launch one block apply (block kernel + combine).  Returns a cudaError_t.
-template <int NLOC, typename T, typename S, int KIND, int OP>
+template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
 cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
                          int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
                          cudaStream_t st) {
     const size_t smem = block_smem_bytes<NLOC, T, KIND>(A);
-    auto kern = k_block<NLOC, T, S, KIND, OP>;
+    auto kern = k_block<NLOC, T, S, KIND, OP, DF>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

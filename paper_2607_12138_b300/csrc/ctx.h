@@ -82,6 +82,11 @@ struct bras_ctx {
     float *Mpk32 = nullptr, *Minvpk32 = nullptr;
     __nv_bfloat16* Minvpkbf = nullptr;
 
+    // H1 tensor-core path: reference matrices pre-split (TF32 big | remainder) and laid out
+    // as the GEMM's shared-memory B operand
+    bool use_tc = false;
+    unsigned char *btile_mass = nullptr, *btile_bras = nullptr;
+
     // workspace
     void* part = nullptr;        // partial sums of shared dofs [npart * nrhs] (double)
     size_t part_bytes = 0;

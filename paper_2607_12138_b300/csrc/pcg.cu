@@ -5,13 +5,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
 
 namespace bras {
 
-constexpr int kDotBlocks = 296;    // 2 per SM on a 148-SM B300
+constexpr int kDotBlocks = 1184;   // 8 per SM on a 148-SM B300 (fixed: it fixes the summation order)
 constexpr int kMaxRhs = 256;
 
 enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_BN, S_SCALE, S_COUNT };
@@ -223,9 +224,20 @@ __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB*
     __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
     double acc = 0.0;
-    if (lr < rows)
-        for (int64_t i = (int64_t)blockIdx.x * rows + lr; i < n; i += (int64_t)gridDim.x * rows)
-            acc += (double)a[i * R + r] * (double)b[i * R + r];
+    if (lr < rows) {
+        // four independent accumulators (loads in flight), combined in a fixed order
+        const int64_t stride = (int64_t)gridDim.x * rows;
+        int64_t i = (int64_t)blockIdx.x * rows + lr;
+        double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            c0 += (double)a[i * R + r] * (double)b[i * R + r];
+            c1 += (double)a[(i + stride) * R + r] * (double)b[(i + stride) * R + r];
+            c2 += (double)a[(i + 2 * stride) * R + r] * (double)b[(i + 2 * stride) * R + r];
+            c3 += (double)a[(i + 3 * stride) * R + r] * (double)b[(i + 3 * stride) * R + r];
+        }
+        for (; i < n; i += stride) c0 += (double)a[i * R + r] * (double)b[i * R + r];
+        acc = (c0 + c1) + (c2 + c3);
+    }
     red[tid] = acc;
     block_partial_and_finish(F, R, red);
 }
@@ -240,13 +252,36 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
     double acc = 0.0;
     if (lr < rows) {
         const T a = (T)alpha[rr];
-        for (int64_t i = (int64_t)blockIdx.x * rows + lr; i < n; i += (int64_t)gridDim.x * rows) {
+        const int64_t stride = (int64_t)gridDim.x * rows;
+        int64_t i = (int64_t)blockIdx.x * rows + lr;
+        double c[4] = {0.0, 0.0, 0.0, 0.0};
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            T pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = (i + u * stride) * R + rr;
+                pv[u] = p[k];
+                qv[u] = q[k];
+                xv[u] = x[k];
+                rv[u] = r[k];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = (i + u * stride) * R + rr;
+                x[k] = fma(a, pv[u], xv[u]);
+                const T v = fma(-a, qv[u], rv[u]);
+                r[k] = v;
+                c[u] += (double)v * (double)v;
+            }
+        }
+        for (; i < n; i += stride) {
             const int64_t k = i * R + rr;
             x[k] = fma(a, p[k], x[k]);
             const T v = fma(-a, q[k], r[k]);
             r[k] = v;
-            acc += (double)v * (double)v;
+            c[0] += (double)v * (double)v;
         }
+        acc = (c[0] + c[1]) + (c[2] + c[3]);
     }
     red[tid] = acc;
     block_partial_and_finish(F, R, red);
@@ -428,15 +463,16 @@ static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, 
 
 template <typename T>
 static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, int R, cudaGraphConditionalHandle cond,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool in_graph) {
     PcgWork* w = c->pcg;
     const int S = batched(c) ? c->n_mesh : R;
+    int* ip = in_graph ? w->iparam : nullptr;    // the loop condition exists only inside the graph
     if (batched(c))
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
-                                                     fin_args(w, FIN_RR, w->iparam, cond));
+                                                     fin_args(w, FIN_RR, ip, cond));
     else
         k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
-                                                    fin_args(w, FIN_RR, w->iparam, cond));
+                                                    fin_args(w, FIN_RR, ip, cond));
     count_launch(1);
     return cudaGetLastError();
 }
@@ -485,7 +521,7 @@ static int precond(bras_ctx* c, int pc, int prec, const T* r, T* z, int R, cudaS
 // and the loop condition (some rhs still active and fewer than maxit iterations).
 template <typename T>
 static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T* p, T* q, int R,
-                             cudaGraphConditionalHandle cond, cudaStream_t st) {
+                             cudaGraphConditionalHandle cond, cudaStream_t st, bool in_graph = true) {
     PcgWork* w = c->pcg;
     const int64_t n = c->n, nv = n * R;
     RC(precond(c, pc, prec, r, z, R, st));
@@ -493,7 +529,7 @@ static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T*
     CK(vupdate_p<T>(c, p, z, R, st));
     RC(run_op(c, prec, OP_MASS, p, q, R, st));
     CK(vdot(c, p, q, R, FIN_ALPHA, st));
-    CK(vupdate_xr<T>(c, x, r, p, q, R, cond, st));
+    CK(vupdate_xr<T>(c, x, r, p, q, R, cond, st, in_graph));
     (void)w;
     (void)n;
     (void)nv;
@@ -554,6 +590,16 @@ static int get_graph(bras_ctx* c, int prec, int pc, int R, T* x, T* r, T* z, T* 
     return BRAS_OK;
 }
 
+// BRAS_SOLVE_HOST_LOOP=1 in the environment runs the CG iterations from a host loop instead of
+// the conditional-while graph (identical kernels; for profilers).
+static bool host_loop() {
+    static const bool on = [] {
+        const char* e = std::getenv("BRAS_SOLVE_HOST_LOOP");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
 // PCG on M x = b (b on the device, type T); x starts at 0.  Per-rhs iteration counts land in
 // w->flags[R..2R), squared residual norms in w->sc[S_RR], [S_RR0].
 template <typename T>
@@ -577,7 +623,19 @@ static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z,
     CK(cudaMemcpyAsync(r, b, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(w->flags + 2 * S + 1, 0, sizeof(int), st));
     CK(vdot(c, r, r, R, FIN_INIT_RR, st));
-    if (maxit > 0) CK(cudaGraphLaunch(exec, st));
+    if (maxit > 0 && host_loop()) {
+        // profiling aid: the same iteration kernels launched one by one, the stopping test read
+        // back after every iteration (tools that cannot look inside conditional graphs see them)
+        for (int it = 0; it < maxit; ++it) {
+            RC(enqueue_iteration<T>(c, prec, pc, x, r, z, p, q, R, 0, st, false));
+            CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (w->h_flags[2 * S] == 0 || w->h_flags[2 * S + 1] != 0) break;
+        }
+        kpi = 0;
+    } else if (maxit > 0) {
+        CK(cudaGraphLaunch(exec, st));
+    }
     CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hp, w->iparam, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -666,7 +724,7 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
             else
                 k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * S, nv, R);
             count_launch(1);
-            RC(run_op(c, BRAS_FP64, OP_MASS, dx, w->q, R, st));
+            RC(run_op(c, BRAS_FP64X, OP_MASS, dx, w->q, R, st));   // refinement residual b - M x
             k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv);
             count_launch(1);
             CK(vdot(c, w->r, w->r, R, FIN_NORM, st));

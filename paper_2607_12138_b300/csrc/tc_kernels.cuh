@@ -1,0 +1,330 @@
+// H1 block kernel with the local multiply on the 5th-generation tensor cores (tcgen05).
+//
+// Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async
+// copies, x staged in shared memory, fixed-order in-block incidence sums, partials of
+// boundary dofs.  The difference is stage 2: for an affine H1 cell the local operator is
+// c_K * A_ref with one reference matrix shared by all cells (A_ref = M_ref or M_ref^{-1},
+// Eq. piola_mass_pullbacks), so a block's local products form one GEMM
+//      Z[cells x n] = Xt[cells x k] * A_ref^T,
+// issued by one thread as tcgen05.mma (kind::tf32, M = 128 cells per tile, N = n_loc
+// rounded up to 16, K = n_loc rounded up to 8):
+//   * each thread writes its cell's signed local vector (row of Xt) straight into tensor
+//     memory with tcgen05.st -- row = TMEM lane, k = column -- split into a TF32 "big" part
+//     and the exact FP32 remainder ("small");
+//   * A_ref, pre-split the same way and pre-arranged in the canonical no-swizzle K-major
+//     core-matrix layout (8 rows x 16 bytes per core matrix) at setup, arrives in shared
+//     memory with one bulk copy;
+//   * Z = Xbig*Abig + Xbig*Asmall + Xsmall*Abig accumulates in FP32 in tensor memory
+//     (the 3xTF32 split: about FP32 accuracy), completion signalled by tcgen05.commit on an
+//     mbarrier;
+//   * each thread reads its row back with tcgen05.ld and continues as in k_block.
+// Tensor memory: 256 columns per CTA (two 128-cell tiles x [Xbig | Xsmall | Z]), allocated
+// and released by warp 0; every wait is bounded and every exit path releases it.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apply_kernels.cuh"
+
+namespace bras {
+
+template <int NLOC> struct TcShape {
+    static constexpr int K = (NLOC + 7) / 8 * 8;     // reduction dim, multiple of 8 (tf32 K step)
+    static constexpr int N = (NLOC + 15) / 16 * 16;  // output dim, multiple of 16 (M = 128)
+    static constexpr int TILE_COLS = 128;            // per-tile TMEM columns: Xbig | Xsmall | Z
+    static_assert(2 * K + N <= TILE_COLS, "tile does not fit 128 TMEM columns");
+    static constexpr uint32_t B_BYTES = (uint32_t)N * K * 4;   // one split of A_ref
+};
+
+// Byte offset of element (row n, col k) of an N x K K-major operand in the no-swizzle
+// canonical layout: core matrix (n/8, k/4) at ((n/8) * (K/4) + k/4) * 128 bytes, row n%8 at
+// 16 bytes each, element k%4 at 4 bytes each.  Leading (K) core-matrix stride 128 bytes,
+// stride (N) core-matrix-group stride (K/4) * 128 bytes.
+__host__ __device__ inline uint32_t umma_kmajor_offset(int n, int k, int K) {
+    return (uint32_t)(((n / 8) * (K / 4) + k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4);
+}
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
+    // base offset 0, absolute-offset mode off, swizzle mode 0 (none)
+    return d;
+}
+
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128.
+template <int N> __device__ __forceinline__ uint32_t umma_idesc_tf32_m128() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {   // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {   // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+        "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem desc]^T, kind::tf32, one thread.
+__device__ __forceinline__ void umma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+struct TcArgs {
+    BlockArgs A;
+    const unsigned char* btile;   // [Abig | Asmall] pre-arranged, 2 * N * K * 4 bytes
+};
+
+template <int NLOC, int OP>
+__global__ void __launch_bounds__(256, 1)
+k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs) {
+    using Sh = TcShape<NLOC>;
+    constexpr int K = Sh::K, N = Sh::N;
+    constexpr uint32_t TMEM_COLS = 2 * Sh::TILE_COLS;
+    const BlockArgs& A = TA.A;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);         // [0] tab A, [1] tab B, [2] B tile, [3] MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + 64);
+    unsigned char* btile = smem_raw + 128;                           // 2 * B_BYTES, 128-B aligned
+    unsigned char* tab = btile + 2 * Sh::B_BYTES;
+    float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));
+    float* zs = xs + ((A.max_u + 3) & ~3);
+
+    const int b = blockIdx.x, r = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+    const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
+    const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
+    const int nint = A.blk_nint[b];
+    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        mbar_fence_init();
+        const unsigned char* src = A.pkt + A.blk_pkt[b];
+        mbar_expect_tx(&bars[0], sa);
+        bulk_copy_g2s(tab, src, sa, &bars[0]);
+        mbar_expect_tx(&bars[1], sb);
+        bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
+        mbar_expect_tx(&bars[2], 2 * Sh::B_BYTES);
+        bulk_copy_g2s(btile, TA.btile, 2 * Sh::B_BYTES, &bars[2]);
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
+    const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
+    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
+    const uint16_t* inc = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+
+    bool ok = mbar_wait_bounded(&bars[0], A.status);
+    if (ok) {
+        for (int u = tid; u < nu; u += 4 * blockDim.x) {
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int uu = u + k * blockDim.x;
+                v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int uu = u + k * blockDim.x;
+                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? v[k] / (float)dmul[uu] : v[k];
+            }
+        }
+    }
+    ok = mbar_wait_bounded(&bars[1], A.status) && ok;
+    ok = __syncthreads_and(ok);
+
+    // stage 2a: this thread's cell row -> tensor memory (big TF32 part, exact remainder)
+    const int e = tid;                                  // cell of this thread (tile e / 128, lane e % 128)
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tile_col = (uint32_t)(warp >> 2) * Sh::TILE_COLS;
+    uint64_t neg = 0;
+    if (ok) {
+        float xl[K];
+#pragma unroll
+        for (int a = 0; a < K; ++a) xl[a] = 0.f;
+        if (e < ne) {
+#pragma unroll
+            for (int a = 0; a < NLOC; ++a) {
+                const uint16_t c = loc[a * ne + e];
+                const float v = xs[c & 0x7fff];
+                const bool s = (c & 0x8000) != 0;
+                neg |= (uint64_t)s << a;
+                xl[a] = s ? -v : v;
+            }
+        }
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hi[j] = f32_to_tf32(xl[k0 + j]);
+                lo[j] = __float_as_uint(xl[k0 + j] - __uint_as_float(hi[j]));
+            }
+            tmem_st8(tmem + lane_base + tile_col + k0, hi);
+            tmem_st8(tmem + lane_base + tile_col + K + k0, lo);
+        }
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+
+    // stage 2b: one thread issues the 3xTF32 GEMM for both 128-cell tiles
+    if (ok && tid == 0) {
+        ok = mbar_wait_bounded(&bars[2], A.status);
+        if (ok) {
+            tc_fence_after();
+            const uint32_t bb = smem_addr(btile), bs = bb + Sh::B_BYTES;
+            constexpr uint32_t LBO = 128, SBO = (K / 4) * 128;
+            const uint32_t idesc = umma_idesc_tf32_m128<N>();
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t base = tmem + (uint32_t)t * Sh::TILE_COLS;
+                const uint32_t d = base + 2 * K;
+#pragma unroll
+                for (int s = 0; s < K / 8; ++s) {
+                    const uint64_t db = umma_smem_desc(bb + s * 2 * 128, LBO, SBO);
+                    const uint64_t ds = umma_smem_desc(bs + s * 2 * 128, LBO, SBO);
+                    umma_tf32_ts(d, base + 8 * s, db, idesc, s > 0 ? 1u : 0u);      // big * big
+                    umma_tf32_ts(d, base + 8 * s, ds, idesc, 1u);                   // big * small
+                    umma_tf32_ts(d, base + K + 8 * s, db, idesc, 1u);               // small * big
+                }
+            }
+            umma_commit(&bars[3]);
+        } else {
+            atomicOr(A.status, 2);
+        }
+    }
+    // everyone learns whether the GEMM was issued
+    const bool issued = __syncthreads_and(ok) != 0;
+    bool mma_done = false;
+    if (issued) mma_done = mbar_wait_bounded(&bars[3], A.status);
+    mma_done = __syncthreads_and(mma_done) != 0;
+    if (issued && !mma_done && tid == 0) mbar_wait_bounded(&bars[3], A.status);   // drain before release
+    tc_fence_after();
+
+    // stage 2c: read this cell's row of Z, scale, sign, stage for the incidence sums
+    if (mma_done) {
+        const float c = (e < ne) ? static_cast<const float*>(A.scale)[e0 + e] : 0.f;
+#pragma unroll
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_base + tile_col + 2 * K + n0, v);
+            tmem_wait_ld();
+            if (e < ne) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int a = n0 + j;
+                    if (a < NLOC) {
+                        const float acc = __uint_as_float(v[j]) * c;
+                        zs[a * ne + e] = ((neg >> a) & 1) ? -acc : acc;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (!mma_done) {
+        // leave after the copies that may still be in flight have landed
+        if (tid == 0) {
+            mbar_wait_bounded(&bars[0], A.status);
+            mbar_wait_bounded(&bars[1], A.status);
+            mbar_wait_bounded(&bars[2], A.status);
+        }
+        return;
+    }
+
+    for (int u = tid; u < nu; u += blockDim.x) {
+        const int s0 = incoff[u], s1 = incoff[u + 1];
+        float acc = 0.f;
+        for (int s = s0; s < s1; ++s) acc += zs[inc[s]];
+        if (u < nint) {
+            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? acc / (float)dmul[u] : acc;
+        } else {
+            part[(size_t)r * A.npart + A.blk_p0[b] + (u - nint)] = acc;
+        }
+    }
+}
+
+template <int NLOC>
+size_t tc_smem_bytes(const BlockArgs& A) {
+    using Sh = TcShape<NLOC>;
+    return 128 + 2 * (size_t)Sh::B_BYTES + ((A.max_pkt + 127u) & ~127u) +
+           sizeof(float) * (((A.max_u + 3) & ~3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3));
+}
+
+template <int NLOC, int OP>
+cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y, float* part, int nrhs,
+                            const float* dinv, int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off,
+                            const int32_t* sh_slots, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes<NLOC>(TA.A);
+    auto kern = k_block_tc<NLOC, OP>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (err != cudaSuccess) return err;
+    dim3 grid(nblk, nrhs);
+    kern<<<grid, 256, smem, st>>>(TA, x, y, part, nrhs);
+    count_launch(1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (nsh > 0) {
+        int64_t total = nsh * nrhs;
+        int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+        k_combine<float, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, TA.A.npart, dinv, y, nrhs);
+        count_launch(1);
+        err = cudaGetLastError();
+    }
+    return err;
+}
+
+}  // namespace bras

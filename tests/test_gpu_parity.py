@@ -54,6 +54,8 @@ def test_fp64_applies(case):
     assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
     assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
     assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr.diag) <= 1e-12
+    # float-float local products (refinement residual form): same 1e-12 bar
+    assert rel_err(ctx.mass_apply(xt, B.FP64X).cpu(), pr.M @ x) <= 1e-12
 
 
 @pytest.mark.parametrize("case", sorted(SMALL_CASES))
@@ -300,3 +302,18 @@ def test_batched_multi_mesh(space, order):
             if mode == B.SOLVE_FP64:
                 _, its_o, _ = pcg(p.mass_apply, b[seg], p.bras_apply, rtol=1e-10)
                 assert abs(int(its[i]) - its_o) <= 1
+
+
+@pytest.mark.parametrize("case", ["2d_p3", "2d_p4", "3d_p3", "3d_p4", "c1_2d_p2"])
+def test_tensor_core_vs_simt_fp32(case):
+    """H1 FP32 applies: 3xTF32 tcgen05 local GEMM against the FP32-unit path and the oracle."""
+    mesh, space, order, n, l2g, signs = build(case)
+    pr = Problem(mesh, space, order, l2g, signs, n)
+    tc = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs)
+    simt = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs, simt_only=True)
+    x, xt = _vec(n, dtype=torch.float32)
+    for op, ref in (("bras_apply", pr.B @ x), ("mass_apply", pr.M @ x)):
+        a = getattr(tc, op)(xt, B.FP32).cpu()
+        s = getattr(simt, op)(xt, B.FP32).cpu()
+        assert rel_err(a, ref) <= 2e-5 and rel_err(s, ref) <= 2e-5
+        assert rel_err(a, s) <= 2e-5
