@@ -6,7 +6,8 @@
 
 namespace bras {
 
-bool h1_tc_supported(int nloc) { return nloc == 10 || nloc == 15 || nloc == 20 || nloc == 35; }
+// tensor cores pay off from n_loc = 20 (3D P3) on; smaller local matrices stay on the FP32 units
+bool h1_tc_supported(int nloc) { return nloc == 20 || nloc == 35; }
 
 uint32_t h1_tc_btile_bytes(int nloc) {
     switch (nloc) {

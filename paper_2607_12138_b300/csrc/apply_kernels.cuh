@@ -97,6 +97,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
     return false;
 }
 
+// v / d for the multiplicity d: FP64 divides; FP32 multiplies by the correctly rounded
+// reciprocal (within one unit in the last place of the quotient, no division subroutine).
+__device__ __forceinline__ double div_by_count(double v, uint16_t d) { return v / (double)d; }
+__device__ __forceinline__ float div_by_count(float v, uint16_t d) { return v * __frcp_rn((float)d); }
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec4<double> { using type = double2; static constexpr int W = 2; };
@@ -146,7 +151,10 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
+    const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];   // first partial slot of this block
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    // this thread's cell factor (H1), fetched now so that its latency hides behind the copies
+    const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -175,22 +183,22 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
     const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* inc = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
 
     bool ok = mbar_wait_bounded(&bars[0], A.status);
     if (OP != OP_DIAG && ok) {
-        // independent loads, four per thread in flight
-        for (int u = tid; u < nu; u += 4 * blockDim.x) {
-            T v[4];
+        // all of this thread's loads in flight at once (up to 16 per pass)
+        for (int u = tid; u < nu; u += 16 * blockDim.x) {
+            T v[16];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 const int uu = u + k * blockDim.x;
                 v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : T(0);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 const int uu = u + k * blockDim.x;
-                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? v[k] / T(dmul[uu]) : v[k];
+                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
             }
         }
     }
@@ -220,7 +228,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
         for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
         if constexpr (DF) {
-            const T c = static_cast<const T*>(A.scale)[e0 + e];
+            const T c = cfac;
             float vh[NPAD], vl[NPAD];
 #pragma unroll
             for (int a = 0; a < NPAD; ++a) {
@@ -242,12 +250,12 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 df_merge(sh[2], sl[2], sh[3], sl[3]);
                 df_merge(sh[0], sl[0], sh[2], sl[2]);
                 T acc = ((double)sh[0] + (double)sl[0]) * c;
-                zs[a * ne + e] = ((neg >> a) & 1) ? -acc : acc;
+                zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -acc : acc;
             }
         } else if (KIND == KIND_H1) {
             using V = typename Vec4<T>::type;
             constexpr int W = Vec4<T>::W;
-            const T c = static_cast<const T*>(A.scale)[e0 + e];
+            const T c = cfac;
 #pragma unroll
             for (int a = 0; a < NLOC; ++a) {
                 T acc = T(0);
@@ -270,7 +278,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     }
                 }
                 acc *= c;
-                zs[a * ne + e] = ((neg >> a) & 1) && OP != OP_DIAG ? -acc : acc;
+                zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -acc : acc;
             }
         } else {
             const S* __restrict__ pk = static_cast<const S*>(A.pk) + e0 + e;
@@ -293,19 +301,20 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             }
 #pragma unroll
             for (int a = 0; a < NLOC; ++a)
-                zs[a * ne + e] = ((neg >> a) & 1) && OP != OP_DIAG ? -zl[a] : zl[a];
+                zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -zl[a] : zl[a];
         }
     }
     __syncthreads();
 
     for (int u = tid; u < nu; u += blockDim.x) {
         const int s0 = incoff[u], s1 = incoff[u + 1];
+        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
         T acc = T(0);
-        for (int s = s0; s < s1; ++s) acc += zs[inc[s]];
+        for (int s = s0; s < s1; ++s) acc += zs[s];
         if (u < nint) {
-            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? acc / T(dmul[u]) : acc;
+            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
         } else {
-            part[(size_t)r * A.npart + A.blk_p0[b] + (u - nint)] = acc;
+            part[p0 + (u - nint)] = acc;
         }
     }
 }
@@ -345,7 +354,8 @@ cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
     dim3 grid(nblk, nrhs);
-    kern<<<grid, 256, smem, st>>>(A, x, y, part, nrhs);
+    const int threads = (A.max_ne + 31) / 32 * 32;         // one thread per cell of the largest block
+    kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs);
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;

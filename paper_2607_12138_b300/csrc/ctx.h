@@ -20,9 +20,10 @@ struct PcgWork;
 // packet (byte offset blk_pkt[b], layout in apply_kernels.cuh) holds
 //   ids[u]      global dof of block-local dof u
 //   d[u]        multiplicity of that dof (D = P^T P)
-//   incoff[u]   incidence offsets: the broken slots a*ne + e of dof u are inc[incoff[u]..)
+//   incoff[u]   dof u's copies occupy positions [incoff[u], incoff[u+1]) of the dof-sorted order
 //   loc[a*ne+e] block-local dof of (cell e, local a); bit 15 = sign -1 of P
-//   inc[s]      broken slots, ascending per dof (fixed summation order)
+//   pos[a*ne+e] position of copy (cell e, local a) in the dof-sorted order (copies of one dof
+//               by ascending slot a*ne + e: the fixed summation order)
 // Shared dof j of block b writes partial slot blk_p0[b] + j; sh_off / sh_slots list, per
 // globally shared dof sh_ids[i], its partial slots in ascending block order.
 struct HostTables {

@@ -1,6 +1,6 @@
 // Byte layout of one cell block's table packet (host and device share it).
 //   part A: ids int32[nu] | d uint16[nu] | incoff uint16[nu + 1]
-//   part B: loc uint16[ne * nloc] | inc uint16[ne * nloc]
+//   part B: loc uint16[ne * nloc] | pos uint16[ne * nloc]
 // Every section starts on a 16-byte boundary so that each part is one bulk copy.
 #pragma once
 #include <stdint.h>

@@ -104,7 +104,9 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
             if (i == 0 || srt[i].first != srt[i - 1].first) { uq.push_back(srt[i].first); first.push_back((int32_t)i); }
         first.push_back((int32_t)srt.size());
         const int nu = (int)uq.size();
-        std::vector<int32_t> order;   // interior first, then shared (each ascending dof id)
+        // interior first, then shared, each in ascending dof id (neighbouring threads touch
+        // neighbouring entries of x and y)
+        std::vector<int32_t> order;
         order.reserve(nu);
         for (int i = 0; i < nu; ++i) if (first[i + 1] - first[i] == d[uq[i]]) order.push_back(i);
         const int nint = (int)order.size();
@@ -176,7 +178,11 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         std::memcpy(p + pkt_off_incoff(nu), B.incoff.data(), 2 * (size_t)(nu + 1));
         const uint32_t sa = pkt_size_a(nu);
         std::memcpy(p + sa, B.loc.data(), 2 * (size_t)m);
-        std::memcpy(p + sa + pad16(2u * m), B.inc.data(), 2 * (size_t)m);
+        // position of every broken copy in the dof-sorted order (the inverse of the incidence
+        // list): a cell writes its result for copy (a, e) there, and each dof then sums one
+        // contiguous run
+        uint16_t* pos = reinterpret_cast<uint16_t*>(p + sa + pad16(2u * m));
+        for (uint32_t s = 0; s < m; ++s) pos[B.inc[s]] = (uint16_t)s;
     }
     // shared dofs: partial slots in ascending block order per dof
     std::vector<std::pair<int32_t, int32_t>> sh;   // (dof, slot)

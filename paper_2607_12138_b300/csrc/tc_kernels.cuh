@@ -18,7 +18,7 @@
 //     (the 3xTF32 split: about FP32 accuracy), completion signalled by tcgen05.commit on an
 //     mbarrier;
 //   * each thread reads its row back with tcgen05.ld and continues as in k_block.
-// Tensor memory: 256 columns per CTA (two 128-cell tiles x [Xbig | Xsmall | Z]), allocated
+// Tensor memory: 128 columns per 128-cell tile ([Xbig | Xsmall | Z]), one or two tiles, allocated
 // and released by warp 0; every wait is bounded and every exit path releases it.
 #pragma once
 #include <cuda_runtime.h>
@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(256, 1)
 k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs) {
     using Sh = TcShape<NLOC>;
     constexpr int K = Sh::K, N = Sh::N;
-    constexpr uint32_t TMEM_COLS = 2 * Sh::TILE_COLS;
+    const int tiles = blockDim.x / 128;                       // 128 cells (TMEM lanes) per tile
+    const uint32_t TMEM_COLS = (uint32_t)tiles * Sh::TILE_COLS;   // 128 or 256
     const BlockArgs& A = TA.A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);         // [0] tab A, [1] tab B, [2] B tile, [3] MMA
@@ -135,7 +136,10 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
+    const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];   // first partial slot of this block
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    // this thread's cell factor, fetched now so that its latency hides behind the copies
+    const float cfac = (tid < ne) ? static_cast<const float*>(A.scale)[e0 + tid] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -157,21 +161,22 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
     const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* inc = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
 
     bool ok = mbar_wait_bounded(&bars[0], A.status);
     if (ok) {
-        for (int u = tid; u < nu; u += 4 * blockDim.x) {
-            float v[4];
+        // all of this thread's loads in flight at once (up to 16 per pass)
+        for (int u = tid; u < nu; u += 16 * blockDim.x) {
+            float v[16];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 const int uu = u + k * blockDim.x;
                 v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : 0.f;
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 const int uu = u + k * blockDim.x;
-                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? v[k] / (float)dmul[uu] : v[k];
+                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
             }
         }
     }
@@ -221,8 +226,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
             const uint32_t bb = smem_addr(btile), bs = bb + Sh::B_BYTES;
             constexpr uint32_t LBO = 128, SBO = (K / 4) * 128;
             const uint32_t idesc = umma_idesc_tf32_m128<N>();
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < tiles; ++t) {
                 const uint32_t base = tmem + (uint32_t)t * Sh::TILE_COLS;
                 const uint32_t d = base + 2 * K;
 #pragma unroll
@@ -249,7 +253,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 
     // stage 2c: read this cell's row of Z, scale, sign, stage for the incidence sums
     if (mma_done) {
-        const float c = (e < ne) ? static_cast<const float*>(A.scale)[e0 + e] : 0.f;
+        const float c = cfac;
 #pragma unroll
         for (int n0 = 0; n0 < N; n0 += 16) {
             uint32_t v[16];
@@ -261,7 +265,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                     const int a = n0 + j;
                     if (a < NLOC) {
                         const float acc = __uint_as_float(v[j]) * c;
-                        zs[a * ne + e] = ((neg >> a) & 1) ? -acc : acc;
+                        zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -acc : acc;
                     }
                 }
             }
@@ -285,12 +289,13 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 
     for (int u = tid; u < nu; u += blockDim.x) {
         const int s0 = incoff[u], s1 = incoff[u + 1];
+        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
         float acc = 0.f;
-        for (int s = s0; s < s1; ++s) acc += zs[inc[s]];
+        for (int s = s0; s < s1; ++s) acc += zs[s];
         if (u < nint) {
-            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? acc / (float)dmul[u] : acc;
+            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
         } else {
-            part[(size_t)r * A.npart + A.blk_p0[b] + (u - nint)] = acc;
+            part[p0 + (u - nint)] = acc;
         }
     }
 }
@@ -313,7 +318,8 @@ cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
     dim3 grid(nblk, nrhs);
-    kern<<<grid, 256, smem, st>>>(TA, x, y, part, nrhs);
+    const int threads = TA.A.max_ne > 128 ? 256 : 128;    // one or two 128-cell tensor tiles
+    kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs);
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
