@@ -11,6 +11,7 @@
 #include "ctx.h"
 #include "dispatch.h"
 #include "internal.h"
+#include "packet.h"
 #include "refelem.h"
 #include "setup_dev.h"
 
@@ -273,7 +274,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     if (!h1) {
         c->npk = nloc * (nloc + 1) / 2;
         c->Epad = (n_cell + 31) / 32 * 32;
-        const size_t cnt = (size_t)c->npk * c->Epad;
+        const size_t cnt = (size_t)pk_groups(c->npk, 8) * 8 * c->Epad;   // whole 16-byte groups
         // FP64 tables are always built (outer residual, diag); FP32 / bf16 on request
         if (!(c->Mpk64 = dalloc<double>(c, cnt)) || !(c->Minvpk64 = dalloc<double>(c, cnt))) return BRAS_ERR_OOM;
         if (want32 || wantbf) {
@@ -281,6 +282,12 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         }
         if (want32 && !(c->Minvpk32 = dalloc<float>(c, cnt))) return BRAS_ERR_OOM;
         if (wantbf && !(c->Minvpkbf = dalloc<__nv_bfloat16>(c, cnt))) return BRAS_ERR_OOM;
+        // zero the padding entries of the last 16-byte groups
+        if (cudaMemsetAsync(c->Mpk64, 0, cnt * 8, st) != cudaSuccess || cudaMemsetAsync(c->Minvpk64, 0, cnt * 8, st) != cudaSuccess ||
+            (c->Mpk32 && cudaMemsetAsync(c->Mpk32, 0, cnt * 4, st) != cudaSuccess) ||
+            (c->Minvpk32 && cudaMemsetAsync(c->Minvpk32, 0, cnt * 4, st) != cudaSuccess) ||
+            (c->Minvpkbf && cudaMemsetAsync(c->Minvpkbf, 0, cnt * 2, st) != cudaSuccess))
+            return BRAS_ERR_CUDA;
         if (run_element_inverse(nloc, n_cell, c->Epad, c->Rref, c->metric, c->Mpk64, c->Mpk32, c->Minvpk64,
                                 c->Minvpk32, c->Minvpkbf, bad, nfixed, c->perm, st) != cudaSuccess)
             return BRAS_ERR_CUDA;

@@ -51,10 +51,46 @@ struct BlockArgs {
     uint32_t max_pkt;          // largest packet (bytes)
 };
 
-template <typename T> __device__ __forceinline__ T ld_mat(const double* p) { return (T)__ldg(p); }
-template <typename T> __device__ __forceinline__ T ld_mat(const float* p) { return (T)__ldg(p); }
-template <typename T> __device__ __forceinline__ T ld_mat(const __nv_bfloat16* p) {
-    return (T)__bfloat162float(*p);
+// 16-byte groups of a cell's packed matrix (layout: pk_index in packet.h)
+template <typename S> struct PkVec;
+template <> struct PkVec<float> { static constexpr int G = 4; using V = float4; };
+template <> struct PkVec<double> { static constexpr int G = 2; using V = double2; };
+template <> struct PkVec<__nv_bfloat16> { static constexpr int G = 8; using V = uint4; };
+
+__device__ __forceinline__ float4 ld_vec(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_vec(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ld_vec(const uint4* p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ T vec_elem(const float4& v, int j) {
+    return (T)(j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w);
+}
+template <typename T> __device__ __forceinline__ T vec_elem(const double2& v, int j) { return (T)(j == 0 ? v.x : v.y); }
+template <typename T> __device__ __forceinline__ T vec_elem(const uint4& v, int j) {   // 8 bfloat16
+    const uint32_t w = j < 2 ? v.x : j < 4 ? v.y : j < 6 ? v.z : v.w;
+    return (T)__uint_as_float((j & 1) ? (w & 0xFFFF0000u) : (w << 16));
+}
+
+// Visit the packed entries (a, q <= a) of this thread's cell in order, 16 bytes per load;
+// f(a, q, m) is inlined with compile-time a, q after unrolling.
+template <int NLOC, typename T, typename S, typename F>
+__device__ __forceinline__ void for_packed(const S* pk_base, int64_t cell, int64_t Epad, F&& f) {
+    using V = typename PkVec<S>::V;
+    constexpr int G = PkVec<S>::G, NPK = NLOC * (NLOC + 1) / 2;
+    const V* base = reinterpret_cast<const V*>(pk_base) + cell;
+    int a = 0, q = 0;
+#pragma unroll
+    for (int g = 0; g < (NPK + G - 1) / G; ++g) {
+        const V v = ld_vec(base + (size_t)g * Epad);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (g * G + j < NPK) {
+                f(a, q, vec_elem<T>(v, j));
+                if (++q > a) {
+                    ++a;
+                    q = 0;
+                }
+            }
+        }
+    }
 }
 
 // ---- bulk asynchronous copy + mbarrier helpers (sm_90+ PTX) -------------------------------
@@ -135,8 +171,14 @@ __device__ __forceinline__ void df_merge(float& ah, float& al, float bh, float b
     al = __fadd_rn(__fadd_rn(al, bl), err);
 }
 
+// Streamed FP32/bf16 cell matrices: ask for two resident blocks per SM (at most 128 registers a
+// thread), so that twice as many matrix loads are in flight.
+template <int KIND, typename T, int NLOC> struct MinBlocks {
+    static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4) ? 2 : 1;
+};
+
 template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC>::value))
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
     static_assert(!DF || (sizeof(T) == 8 && KIND == KIND_H1), "float-float path: FP64 vectors, H1 only");
@@ -213,7 +255,38 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     }
 
     const int e = tid;
-    if (e < ne) {
+    // Large streamed cell matrices (n_loc >= 36): the signed local vector waits in shared memory,
+    // column e of a [a][cell] array (only this thread touches it), so that registers hold just
+    // the accumulators and the matrix loads in flight; the results go out after a barrier,
+    // over the same array.
+    constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36 && OP != OP_DIAG;
+    if constexpr (XS) {
+        T* xt = zs;
+        uint64_t neg = 0;
+        T zl[NLOC];
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
+        if (e < ne) {
+            const uint16_t* L = loc + e;
+#pragma unroll
+            for (int a = 0; a < NLOC; ++a) {
+                const uint16_t c = L[a * ne];
+                const T v = xs[c & 0x7fff];
+                const bool s = (c & 0x8000) != 0;
+                neg |= (uint64_t)s << a;
+                xt[a * ne + e] = s ? -v : v;
+            }
+            for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                zl[a] = fma(m, xt[q * ne + e], zl[a]);
+                if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
+            });
+        }
+        __syncthreads();
+        if (e < ne) {
+#pragma unroll
+            for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -zl[a] : zl[a];
+        }
+    } else if (e < ne) {
         const uint16_t* L = loc + e;
         uint64_t neg = 0;
         T xl[NPAD];
@@ -281,24 +354,17 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -acc : acc;
             }
         } else {
-            const S* __restrict__ pk = static_cast<const S*>(A.pk) + e0 + e;
             T zl[NLOC];
 #pragma unroll
             for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-#pragma unroll
-            for (int a = 0; a < NLOC; ++a) {
-#pragma unroll
-                for (int q = 0; q <= a; ++q) {
-                    const int idx = a * (a + 1) / 2 + q;
-                    if (OP == OP_DIAG) {
-                        if (q == a) zl[a] = ld_mat<T>(pk + (size_t)idx * A.Epad);
-                    } else {
-                        const T m = ld_mat<T>(pk + (size_t)idx * A.Epad);
-                        zl[a] = fma(m, xl[q], zl[a]);
-                        if (q < a) zl[q] = fma(m, xl[a], zl[q]);
-                    }
+            for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                if (OP == OP_DIAG) {
+                    if (q == a) zl[a] = m;
+                } else {
+                    zl[a] = fma(m, xl[q], zl[a]);
+                    if (q < a) zl[q] = fma(m, xl[a], zl[q]);
                 }
-            }
+            });
 #pragma unroll
             for (int a = 0; a < NLOC; ++a)
                 zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -zl[a] : zl[a];

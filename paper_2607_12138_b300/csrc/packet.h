@@ -3,6 +3,7 @@
 //   part B: loc uint16[ne * nloc] | pos uint16[ne * nloc]
 // Every section starts on a 16-byte boundary so that each part is one bulk copy.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __CUDACC__
@@ -17,4 +18,13 @@ BRAS_HD inline uint32_t pkt_off_d(uint32_t nu) { return pad16(4u * nu); }
 BRAS_HD inline uint32_t pkt_off_incoff(uint32_t nu) { return pkt_off_d(nu) + pad16(2u * nu); }
 BRAS_HD inline uint32_t pkt_size_a(uint32_t nu) { return pkt_off_incoff(nu) + pad16(2u * nu + 2u); }
 BRAS_HD inline uint32_t pkt_size_b(uint32_t m) { return 2u * pad16(2u * m); }
+
+// Per-cell packed symmetric matrices (lower triangle by rows, entry idx = a (a + 1) / 2 + q)
+// are stored vector-interleaved: groups of G consecutive entries of one cell are contiguous
+// (16 bytes: G = 4 floats, 8 bfloat16, 2 doubles), groups of consecutive cells follow, so that
+// each thread of a warp loads 16 bytes of its own cell and the warp reads whole sectors.
+BRAS_HD inline size_t pk_index(int idx, int64_t e, int64_t Epad, int G) {
+    return ((size_t)(idx / G) * (size_t)Epad + (size_t)e) * (size_t)G + (size_t)(idx % G);
+}
+BRAS_HD inline int pk_groups(int npk, int G) { return (npk + G - 1) / G; }
 }  // namespace bras

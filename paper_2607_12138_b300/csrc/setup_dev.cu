@@ -4,6 +4,7 @@
 
 #include <algorithm>
 
+#include "packet.h"
 #include "setup_dev.h"
 #include "dispatch.h"
 
@@ -132,9 +133,9 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
         __syncwarp();
         for (int i = 0; i < n; ++i)
             for (int j = lane; j <= i; j += 32) {
-                const size_t idx = (size_t)(i * (i + 1) / 2 + j) * Epad + e;
-                if (Mpk64) Mpk64[idx] = A[i * n + j];
-                if (Mpk32) Mpk32[idx] = (float)A[i * n + j];
+                const int idx = i * (i + 1) / 2 + j;
+                if (Mpk64) Mpk64[pk_index(idx, e, Epad, 2)] = A[i * n + j];
+                if (Mpk32) Mpk32[pk_index(idx, e, Epad, 4)] = (float)A[i * n + j];
             }
         __syncwarp();
         if (!warp_cholesky(A, n, lane)) {
@@ -158,9 +159,9 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
             if (j > i) continue;
             double s = 0;
             for (int k = i; k < n; ++k) s += W[k * n + i] * W[k * n + j];
-            const size_t idx = (size_t)(i * (i + 1) / 2 + j) * Epad + e;
-            if (Minv64) Minv64[idx] = s;
-            if (Minv32) Minv32[idx] = (float)s;
+            const int idx = i * (i + 1) / 2 + j;
+            if (Minv64) Minv64[pk_index(idx, e, Epad, 2)] = s;
+            if (Minv32) Minv32[pk_index(idx, e, Epad, 4)] = (float)s;
             A[i * n + j] = s;
             A[j * n + i] = s;
         }
@@ -185,7 +186,7 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
             for (int i = 0; i < n; ++i)
                 for (int j = lane; j <= i; j += 32) {
                     const double v = A[i * n + j] + (i == j ? shift : 0.0);
-                    Minvbf[(size_t)(i * (i + 1) / 2 + j) * Epad + e] = __float2bfloat16_rn((float)v);
+                    Minvbf[pk_index(i * (i + 1) / 2 + j, e, Epad, 8)] = __float2bfloat16_rn((float)v);
                 }
         }
         __syncwarp();
