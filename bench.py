@@ -105,6 +105,32 @@ def run_reference(a):
     return 0
 
 
+# ---- ncu DRAM traffic of a kernel, if the committed capture matches the current source ---------
+KERNEL_SOURCES = ["paper_2607_12138_b300/csrc/apply_kernels.cuh", "paper_2607_12138_b300/csrc/tc_kernels.cuh",
+                  "paper_2607_12138_b300/csrc/packet.h", "paper_2607_12138_b300/csrc/tables.cpp"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key, alg_bytes):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/dram_traffic.json, or None
+    when that capture was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(path))[key]
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 # ---- clocks ------------------------------------------------------------------------------------
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -174,7 +200,7 @@ def run_ours(a):
         x = torch.empty_like(b)
         bh = b.cpu().pin_memory()
         xh = torch.empty_like(bh).pin_memory()
-        probs.append({"p": p, "n": n, "ctx": ctx, "b": b, "x": x, "bh": bh, "xh": xh})
+        probs.append({"p": p, "n": n, "ctx": ctx, "b": b, "x": x, "bh": bh, "xh": xh, "l2g": l2g})
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
     st = torch.cuda.current_stream()
 
@@ -260,6 +286,30 @@ def run_ours(a):
                              "solve_ms": order_ms.get((mode, pc, False))}
         compare["mixed_bras"] = {"dof_per_s": value / ws, "ms": 1e3 * t_step, "its": [r[0] for r in res]}
 
+    # multi-RHS rows: 32 right-hand sides per solve, one context per order (p = 2, 4)
+    if not a.no_compare:
+        for pr in probs:
+            if pr["p"] not in (2, 4):
+                continue
+            R = 32
+            n = pr["n"]
+            ctxR = B.Context(mesh.coords, mesh.cells, "h1", pr["p"], n, pr["l2g"], None, max_nrhs=R)
+            bR = torch.as_tensor(mg.rhs(n, R, seed=1), device="cuda")
+            xR = torch.empty_like(bR)
+            ctxR.pcg_solve(bR, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10, out=xR)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, itsR, relR, stR = ctxR.pcg_solve(bR, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10, out=xR)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            compare[f"mixed_bras_r32_p{pr['p']}"] = {"dof_per_s": n * R / (ms / 1e3), "ms": ms,
+                                                   "its_max": int(max(itsR)), "relres_max": float(max(relR)),
+                                                   "status": int(stR)}
+            del ctxR, bR, xR
+
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -289,9 +339,38 @@ def run_ours(a):
     top = max(probs, key=lambda pr: kern[f"bras_f32_p{pr['p']}"]["us"])
     kb = kern[f"bras_f32_p{top['p']}"]
     roofline = {"bound": "hbm", "achieved": kb["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": kb["gbs"] / hbm_peak, "traffic": None,
-                "kernel": f"bras_apply FP32 (block kernel + combine), H1 p={top['p']}",
+                "frac": kb["gbs"] / hbm_peak, "traffic": _traffic("h1_p4_bras_f32", kb["alg_bytes"]),
+                "kernel": f"bras_apply FP32 (tcgen05 block kernel + combine), H1 p={top['p']}",
                 "alg_bytes_per_launch": kb["alg_bytes"], "launch_us": kb["us"], "peak_source": "measured"}
+
+    # streamed path: H(curl) Nedelec k=3 on 40^3 x 6 tets, per-cell inverses FP32 / bf16
+    streamed = None
+    if not a.no_compare:
+        m40 = mg.unit_cube_mesh(40, jitter=JITTER, seed=0)
+        n3, l3, s3 = mg.dof_map(m40, "hcurl", 3)
+        c3 = B.Context(m40.coords, m40.cells, "hcurl", 3, n3, l3, s3)
+        x3 = torch.as_tensor(mg.rhs(n3, 1, seed=1), device="cuda").float()
+        y3 = torch.empty_like(x3)
+        for name, fn, prec in (("bras_f32_hcurl3", c3.bras_apply, B.FP32), ("bras_bf16_hcurl3", c3.bras_apply, B.BF16),
+                               ("mass_f32_hcurl3", c3.mass_apply, B.FP32)):
+            for _ in range(3):
+                fn(x3, prec, out=y3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(10):
+                fn(x3, prec, out=y3)
+            e1.record(st)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / 10
+            by = c3.algorithmic_bytes(prec, 1, name.startswith("bras"))
+            kern[name] = {"us": us, "alg_bytes": by, "gbs": by / us / 1e3}
+        ks = kern["bras_f32_hcurl3"]
+        streamed = {"bound": "hbm", "achieved": ks["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ks["gbs"] / hbm_peak, "traffic": _traffic("hcurl3_bras_f32", ks["alg_bytes"]),
+                    "kernel": "bras_apply FP32 streamed per-cell inverses, N1curl k=3, 40^3x6 tets",
+                    "alg_bytes_per_launch": ks["alg_bytes"], "launch_us": ks["us"], "peak_source": "measured"}
+        del c3
 
     cpu = None
     if not a.no_cpu_baseline:
@@ -307,7 +386,8 @@ def run_ours(a):
                        "solver": "mixed: FP32 BRAS-PCG (FP64 dots) in FP64 refinement",
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}",
                        "detail": detail},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "roofline_streamed": streamed, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clk, "compare": compare, "kernels": kern}
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -189,7 +189,9 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     T* zs = xs + ((A.max_u + 3) & ~3);
     T* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                            // [NLOC][NPAD] (H1), 16-B aligned
 
-    const int b = blockIdx.x, r = blockIdx.y, tid = threadIdx.x;
+    // the nrhs CTAs of one cell block are neighbours in the grid: they share the block's
+    // tables and x cache lines in L2
+    const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
@@ -419,7 +421,7 @@ cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    dim3 grid(nblk, nrhs);
+    dim3 grid(nblk * nrhs);
     const int threads = (A.max_ne + 31) / 32 * 32;         // one thread per cell of the largest block
     kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs);
     count_launch(1);

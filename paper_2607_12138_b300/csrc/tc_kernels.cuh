@@ -132,7 +132,9 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));
     float* zs = xs + ((A.max_u + 3) & ~3);
 
-    const int b = blockIdx.x, r = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+    // the nrhs CTAs of one cell block are neighbours in the grid: they share the block's
+    // tables and x cache lines in L2
+    const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x, warp = tid >> 5;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
@@ -317,7 +319,7 @@ cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    dim3 grid(nblk, nrhs);
+    dim3 grid(nblk * nrhs);
     const int threads = TA.A.max_ne > 128 ? 256 : 128;    // one or two 128-cell tensor tiles
     kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs);
     count_launch(1);
