@@ -108,6 +108,8 @@ typedef struct {
  *   cells    [n_cell * (dim+1)] int32, vertex ids of each simplex.
  *   l2g      [n_cell * n_loc] int32, local-to-global dof map (the map pi of Sec. 2.2).
  *   signs    [n_cell * n_loc] int8 in {+1, -1} (signed injection P), or NULL (all +1).
+ *            Lagrange (H1) dofs have no orientation: for BRAS_H1 every sign must be +1
+ *            (else BRAS_ERR_INVALID, the offending entry in bras_last_error_detail).
  *   rho      [n_cell] double > 0 element weights (mass density), or NULL (all 1).
  *   opt      options or NULL (defaults).
  * Limits: n_cell, n_dof < 2^31; n_cell * n_loc < 2^31.

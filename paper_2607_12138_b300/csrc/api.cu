@@ -149,6 +149,10 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         if (h_cells[i] < 0 || h_cells[i] >= n_vert) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
     for (size_t i = 0; i < h_signs.size(); ++i)
         if (h_signs[i] != 1 && h_signs[i] != -1) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
+    // Lagrange (H1) dofs are point values with no orientation: every sign must be +1
+    if (space == BRAS_H1)
+        for (size_t i = 0; i < h_signs.size(); ++i)
+            if (h_signs[i] != 1) { set_detail((int64_t)i); return BRAS_ERR_INVALID; }
 
     // Block size: the largest multiple of 32 (<= BE) whose FP64 kernel fits the device's
     // shared memory and, unless the caller fixed it, whose FP32 kernel fits twice per SM.
@@ -315,6 +319,19 @@ size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int m
     const size_t npad = (size_t)((nloc + w - 1) / w * w);
     return 128 + ((max_pkt + 127u) & ~127u) +
            (size_t)tsize * (((size_t)max_u + 3) / 4 * 4 + ((size_t)nloc * max_ne + 3) / 4 * 4 + (h1 ? nloc * npad : 0));
+}
+
+int smem_optin_bytes() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cached[dev] = v;
+    }
+    return cached[dev];
 }
 
 int ensure_part(bras_ctx* c, int nrhs) {

@@ -133,6 +133,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
     return false;
 }
 
+// Bounded wait on the phase of `bar` with the given parity (barriers reused across phases).
+__device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t parity, int* status) {
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(status, 1);
+    return false;
+}
+
 // v / d for the multiplicity d: FP64 divides; FP32 multiplies by the correctly rounded
 // reciprocal (within one unit in the last place of the quotient, no division subroutine).
 __device__ __forceinline__ double div_by_count(double v, uint16_t d) { return v / (double)d; }
@@ -177,28 +185,85 @@ template <int KIND, typename T, int NLOC> struct MinBlocks {
     static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4) ? 2 : 1;
 };
 
-template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
+// ---- multi-RHS row segments --------------------------------------------------------------
+// A chunk is CW = 16 / sizeof(T) consecutive right-hand sides (4 FP32 or 2 FP64): one 16-byte
+// vector per dof row of x, y, the staged x and the staged local results.
+template <typename T> struct Chunk {
+    using V = typename Vec4<T>::type;   // float4 / double2
+    static constexpr int CW = Vec4<T>::W;
+};
+__device__ __forceinline__ float4 vzero(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ void vadd(float4& a, const float4& b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+__device__ __forceinline__ void vadd(double2& a, const double2& b) { a.x += b.x; a.y += b.y; }
+__device__ __forceinline__ float& vget(float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ double& vget(double2& v, int j) { return j == 0 ? v.x : v.y; }
+
+// Row segment [r0, r0 + rc) of one dof (rc <= CW; the rest of the vector is zero).  vec: rows
+// 16-byte aligned and a full chunk.
+template <typename T>
+__device__ __forceinline__ typename Chunk<T>::V ld_seg(const T* p, int rc, bool vec) {
+    using V = typename Chunk<T>::V;
+    if (vec) return __ldg(reinterpret_cast<const V*>(p));
+    V v = vzero(V{});
+#pragma unroll
+    for (int j = 0; j < Chunk<T>::CW; ++j)
+        if (j < rc) vget(v, j) = p[j];
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ void st_seg(T* p, int rc, bool vec, typename Chunk<T>::V v) {
+    using V = typename Chunk<T>::V;
+    if (vec) {
+        *reinterpret_cast<V*>(p) = v;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < Chunk<T>::CW; ++j)
+        if (j < rc) p[j] = vget(v, j);
+}
+
+// One thread polls the mbarrier (bounded) while the rest of the CTA sleeps in the CTA barrier;
+// returns the block-uniform outcome.  `prior` = false skips the poll and propagates the failure.
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status, bool prior) {
+    bool ok = true;
+    if (threadIdx.x == 0) ok = prior && mbar_wait_parity_bounded(bar, parity, status);
+    return __syncthreads_and(ok) != 0;
+}
+
+// Kernel modes.  MR = false: one right-hand side per CTA (grid = blocks x nrhs), vectors read
+// with stride nrhs, partial sums laid out [nrhs][npart].  MR = true (multi-RHS): one CTA per
+// cell block (grid = blocks) walks the right-hand sides in chunks of CW; each cell of the block
+// is CW work items (cell, rhs), rows of x and y move as 16-byte vectors, partial sums are laid
+// out [npart][nrhs].  The block's tables (and streamed cell matrices, re-read from L2) serve
+// every chunk.
+template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false, bool MR = false>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC>::value))
-k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs) {
+k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs, int vec_ok) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
+    constexpr int CW = MR ? Chunk<T>::CW : 1;
+    using V = typename Chunk<T>::V;
+    // Lagrange (H1) dofs carry no orientation: the sign bit of a local index is only read for
+    // H(curl)/H(div)
+    constexpr bool SIGNED = KIND == KIND_PACKED;
     static_assert(!DF || (sizeof(T) == 8 && KIND == KIND_H1), "float-float path: FP64 vectors, H1 only");
+    constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36 && OP != OP_DIAG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // 2 mbarriers
     unsigned char* tab = smem_raw + 128;                                 // table packet
-    T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));
-    T* zs = xs + ((A.max_u + 3) & ~3);
-    T* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                            // [NLOC][NPAD] (H1), 16-B aligned
+    T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW]
+    T* zs = xs + ((A.max_u * CW + 3) & ~3);                               // [slot][CW]
+    T* Ms = zs + ((NLOC * A.max_ne * CW + 3) & ~3);                       // [NLOC][NPAD] (H1), 16-B aligned
+    T* xt_mr = Ms + (KIND == KIND_H1 ? NLOC * NPAD : 0);                  // [NLOC][blockDim] (MR, XS)
 
-    // the nrhs CTAs of one cell block are neighbours in the grid: they share the block's
-    // tables and x cache lines in L2
-    const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x;
+    const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
-    const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];   // first partial slot of this block
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
-    // this thread's cell factor (H1), fetched now so that its latency hides behind the copies
-    const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
+    // this thread's cell factor (H1, one cell per thread), fetched now so that its latency
+    // hides behind the copies
+    const T cfac = (!MR && KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -229,212 +294,329 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
     const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
 
-    bool ok = mbar_wait_bounded(&bars[0], A.status);
-    if (OP != OP_DIAG && ok) {
-        // all of this thread's loads in flight at once (up to 16 per pass)
-        for (int u = tid; u < nu; u += 16 * blockDim.x) {
-            T v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int uu = u + k * blockDim.x;
-                v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : T(0);
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int uu = u + k * blockDim.x;
-                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
-            }
-        }
-    }
-    ok = mbar_wait_bounded(&bars[1], A.status) && ok;
-    if (!__syncthreads_and(ok)) {   // block-uniform decision
-        // let any copy still in flight land before the block's shared memory is released
-        if (tid == 0) {
-            mbar_wait_bounded(&bars[0], A.status);
-            mbar_wait_bounded(&bars[1], A.status);
-        }
-        return;
-    }
+    const bool okA = cta_wait(&bars[0], 0, A.status, true);
+    const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int r0 = MR ? ch * CW : blockIdx.x % nrhs;
+        const int rc = MR ? min(CW, nrhs - r0) : 1;
+        const bool vec = MR && vec_ok && rc == CW;
+        // first partial slot of this block (MR: row of [npart][nrhs])
+        const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
 
-    const int e = tid;
-    // Large streamed cell matrices (n_loc >= 36): the signed local vector waits in shared memory,
-    // column e of a [a][cell] array (only this thread touches it), so that registers hold just
-    // the accumulators and the matrix loads in flight; the results go out after a barrier,
-    // over the same array.
-    constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36 && OP != OP_DIAG;
-    if constexpr (XS) {
-        T* xt = zs;
-        uint64_t neg = 0;
-        T zl[NLOC];
+        if (OP != OP_DIAG && okA) {
+            if constexpr (MR) {
+                // one 16-byte row segment per dof, four in flight per thread
+                for (int u = tid; u < nu; u += 4 * blockDim.x) {
+                    V v[4];
 #pragma unroll
-        for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-        if (e < ne) {
-            const uint16_t* L = loc + e;
+                    for (int k = 0; k < 4; ++k) {
+                        const int uu = u + k * blockDim.x;
+                        if (uu < nu) v[k] = ld_seg(x + (size_t)ids[uu] * nrhs + r0, rc, vec);
+                    }
 #pragma unroll
-            for (int a = 0; a < NLOC; ++a) {
-                const uint16_t c = L[a * ne];
-                const T v = xs[c & 0x7fff];
-                const bool s = (c & 0x8000) != 0;
-                neg |= (uint64_t)s << a;
-                xt[a * ne + e] = s ? -v : v;
-            }
-            for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
-                zl[a] = fma(m, xt[q * ne + e], zl[a]);
-                if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
-            });
-        }
-        __syncthreads();
-        if (e < ne) {
+                    for (int k = 0; k < 4; ++k) {
+                        const int uu = u + k * blockDim.x;
+                        if (uu < nu) {
+                            if (OP == OP_BRAS) {
 #pragma unroll
-            for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -zl[a] : zl[a];
-        }
-    } else if (e < ne) {
-        const uint16_t* L = loc + e;
-        uint64_t neg = 0;
-        T xl[NPAD];
-#pragma unroll
-        for (int a = 0; a < NLOC; ++a) {
-            const uint16_t c = L[a * ne];
-            const T v = (OP == OP_DIAG) ? T(0) : xs[c & 0x7fff];
-            const bool s = (c & 0x8000) != 0;
-            neg |= (uint64_t)s << a;
-            xl[a] = s ? -v : v;
-        }
-#pragma unroll
-        for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
-        if constexpr (DF) {
-            const T c = cfac;
-            float vh[NPAD], vl[NPAD];
-#pragma unroll
-            for (int a = 0; a < NPAD; ++a) {
-                vh[a] = (float)xl[a];
-                vl[a] = (float)((double)xl[a] - (double)vh[a]);
-            }
-#pragma unroll
-            for (int a = 0; a < NLOC; ++a) {
-                // four independent compensated chains (terms q mod 4), merged at the end
-                float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
-                const float4* row = reinterpret_cast<const float4*>(Ms + a * NPAD);   // two (hi, lo) pairs
-#pragma unroll
-                for (int q = 0; q < NPAD / 2; ++q) {
-                    const float4 m = row[q];
-                    df_term(m.x, m.y, vh[2 * q], vl[2 * q], sh[(2 * q) & 3], sl[(2 * q) & 3]);
-                    df_term(m.z, m.w, vh[2 * q + 1], vl[2 * q + 1], sh[(2 * q + 1) & 3], sl[(2 * q + 1) & 3]);
-                }
-                df_merge(sh[0], sl[0], sh[1], sl[1]);
-                df_merge(sh[2], sl[2], sh[3], sl[3]);
-                df_merge(sh[0], sl[0], sh[2], sl[2]);
-                T acc = ((double)sh[0] + (double)sl[0]) * c;
-                zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -acc : acc;
-            }
-        } else if (KIND == KIND_H1) {
-            using V = typename Vec4<T>::type;
-            constexpr int W = Vec4<T>::W;
-            const T c = cfac;
-#pragma unroll
-            for (int a = 0; a < NLOC; ++a) {
-                T acc = T(0);
-                if (OP == OP_DIAG) {
-                    acc = Ms[a * NPAD + a];
-                } else {
-                    const V* row = reinterpret_cast<const V*>(Ms + a * NPAD);
-#pragma unroll
-                    for (int q = 0; q < NPAD / W; ++q) {
-                        const V m = row[q];
-                        if constexpr (W == 4) {
-                            acc = fma(m.x, xl[4 * q + 0], acc);
-                            acc = fma(m.y, xl[4 * q + 1], acc);
-                            acc = fma(m.z, xl[4 * q + 2], acc);
-                            acc = fma(m.w, xl[4 * q + 3], acc);
-                        } else {
-                            acc = fma(m.x, xl[2 * q + 0], acc);
-                            acc = fma(m.y, xl[2 * q + 1], acc);
+                                for (int j = 0; j < CW; ++j) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                            }
+                            reinterpret_cast<V*>(xs)[uu] = v[k];
                         }
                     }
                 }
-                acc *= c;
-                zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -acc : acc;
+            } else {
+                // all of this thread's loads in flight at once (up to 16 per pass)
+                for (int u = tid; u < nu; u += 16 * blockDim.x) {
+                    T v[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int uu = u + k * blockDim.x;
+                        v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : T(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int uu = u + k * blockDim.x;
+                        if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                    }
+                }
+            }
+        }
+        if (ch == 0) {
+            if (!cta_wait(&bars[1], 0, A.status, okA)) {   // block-uniform decision
+                // let any copy still in flight land before the block's shared memory is released
+                if (tid == 0) {
+                    mbar_wait_bounded(&bars[0], A.status);
+                    mbar_wait_bounded(&bars[1], A.status);
+                }
+                return;
             }
         } else {
+            __syncthreads();
+        }
+
+        // Work items: (cell e, rhs rr) -> item e * CW + rr.  One item per thread without MR.
+        const int nitem = ne * CW;
+        if constexpr (XS && !MR) {
+            // Large streamed cell matrices (n_loc >= 36): the signed local vector waits in shared
+            // memory, column e of a [a][cell] array (only this thread touches it), so that
+            // registers hold just the accumulators and the matrix loads in flight; the results go
+            // out after a barrier, over the same array.
+            const int e = tid;
+            T* xt = zs;
+            uint64_t neg = 0;
             T zl[NLOC];
 #pragma unroll
             for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-            for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
-                if (OP == OP_DIAG) {
-                    if (q == a) zl[a] = m;
-                } else {
-                    zl[a] = fma(m, xl[q], zl[a]);
-                    if (q < a) zl[q] = fma(m, xl[a], zl[q]);
-                }
-            });
+            if (e < ne) {
+                const uint16_t* L = loc + e;
 #pragma unroll
-            for (int a = 0; a < NLOC; ++a)
-                zs[pos[a * ne + e]] = ((neg >> a) & 1) && OP != OP_DIAG ? -zl[a] : zl[a];
-        }
-    }
-    __syncthreads();
-
-    for (int u = tid; u < nu; u += blockDim.x) {
-        const int s0 = incoff[u], s1 = incoff[u + 1];
-        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-        T acc = T(0);
-        for (int s = s0; s < s1; ++s) acc += zs[s];
-        if (u < nint) {
-            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
+                for (int a = 0; a < NLOC; ++a) {
+                    const uint16_t c = L[a * ne];
+                    const T v = xs[c & 0x7fff];
+                    const bool s = (c & 0x8000) != 0;
+                    neg |= (uint64_t)s << a;
+                    xt[a * ne + e] = s ? -v : v;
+                }
+                for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                    zl[a] = fma(m, xt[q * ne + e], zl[a]);
+                    if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
+                });
+            }
+            __syncthreads();
+            if (e < ne) {
+#pragma unroll
+                for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -zl[a] : zl[a];
+            }
         } else {
-            part[p0 + (u - nint)] = acc;
+            for (int it = tid; it < nitem; it += blockDim.x) {
+                const int e = MR ? it / CW : it;
+                const int rr = MR ? it % CW : 0;
+                const uint16_t* L = loc + e;
+                if constexpr (XS) {   // MR: the local vector in a private column of xt_mr
+                    T* xt = xt_mr + tid;
+                    const int ld = blockDim.x;
+                    uint64_t neg = 0;
+                    T zl[NLOC];
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) {
+                        const uint16_t c = L[a * ne];
+                        const T v = xs[(c & 0x7fff) * CW + rr];
+                        const bool s = (c & 0x8000) != 0;
+                        neg |= (uint64_t)s << a;
+                        xt[a * ld] = s ? -v : v;
+                    }
+                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                        zl[a] = fma(m, xt[q * ld], zl[a]);
+                        if (q < a) zl[q] = fma(m, xt[a * ld], zl[q]);
+                    });
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e] * CW + rr] = ((neg >> a) & 1) ? -zl[a] : zl[a];
+                } else {
+                    uint64_t neg = 0;
+                    T xl[NPAD];
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) {
+                        const uint16_t c = L[a * ne];
+                        if constexpr (SIGNED) {
+                            const T v = (OP == OP_DIAG) ? T(0) : xs[(c & 0x7fff) * CW + rr];
+                            const bool s = (c & 0x8000) != 0;
+                            neg |= (uint64_t)s << a;
+                            xl[a] = s ? -v : v;
+                        } else {
+                            xl[a] = (OP == OP_DIAG) ? T(0) : xs[c * CW + rr];
+                        }
+                    }
+#pragma unroll
+                    for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
+                    auto out = [&](int a, T v) {
+                        const bool s = SIGNED && OP != OP_DIAG && ((neg >> a) & 1);
+                        zs[pos[a * ne + e] * CW + rr] = s ? -v : v;
+                    };
+                    if constexpr (DF) {
+                        const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
+                        float vh[NPAD], vl[NPAD];
+#pragma unroll
+                        for (int a = 0; a < NPAD; ++a) {
+                            vh[a] = (float)xl[a];
+                            vl[a] = (float)((double)xl[a] - (double)vh[a]);
+                        }
+#pragma unroll
+                        for (int a = 0; a < NLOC; ++a) {
+                            // four independent compensated chains (terms q mod 4), merged at the end
+                            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+                            const float4* row = reinterpret_cast<const float4*>(Ms + a * NPAD);   // two (hi, lo) pairs
+#pragma unroll
+                            for (int q = 0; q < NPAD / 2; ++q) {
+                                const float4 m = row[q];
+                                df_term(m.x, m.y, vh[2 * q], vl[2 * q], sh[(2 * q) & 3], sl[(2 * q) & 3]);
+                                df_term(m.z, m.w, vh[2 * q + 1], vl[2 * q + 1], sh[(2 * q + 1) & 3], sl[(2 * q + 1) & 3]);
+                            }
+                            df_merge(sh[0], sl[0], sh[1], sl[1]);
+                            df_merge(sh[2], sl[2], sh[3], sl[3]);
+                            df_merge(sh[0], sl[0], sh[2], sl[2]);
+                            out(a, ((double)sh[0] + (double)sl[0]) * c);
+                        }
+                    } else if (KIND == KIND_H1) {
+                        using VM = typename Vec4<T>::type;
+                        constexpr int W = Vec4<T>::W;
+                        const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
+#pragma unroll
+                        for (int a = 0; a < NLOC; ++a) {
+                            T acc = T(0);
+                            if (OP == OP_DIAG) {
+                                acc = Ms[a * NPAD + a];
+                            } else {
+                                const VM* row = reinterpret_cast<const VM*>(Ms + a * NPAD);
+#pragma unroll
+                                for (int q = 0; q < NPAD / W; ++q) {
+                                    const VM m = row[q];
+                                    if constexpr (W == 4) {
+                                        acc = fma(m.x, xl[4 * q + 0], acc);
+                                        acc = fma(m.y, xl[4 * q + 1], acc);
+                                        acc = fma(m.z, xl[4 * q + 2], acc);
+                                        acc = fma(m.w, xl[4 * q + 3], acc);
+                                    } else {
+                                        acc = fma(m.x, xl[2 * q + 0], acc);
+                                        acc = fma(m.y, xl[2 * q + 1], acc);
+                                    }
+                                }
+                            }
+                            out(a, acc * c);
+                        }
+                    } else {
+                        T zl[NLOC];
+#pragma unroll
+                        for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
+                        for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                            if (OP == OP_DIAG) {
+                                if (q == a) zl[a] = m;
+                            } else {
+                                zl[a] = fma(m, xl[q], zl[a]);
+                                if (q < a) zl[q] = fma(m, xl[a], zl[q]);
+                            }
+                        });
+#pragma unroll
+                        for (int a = 0; a < NLOC; ++a) out(a, zl[a]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        if constexpr (MR) {
+            const V* zv = reinterpret_cast<const V*>(zs);
+            for (int u = tid; u < nu; u += blockDim.x) {
+                const int s0 = incoff[u], s1 = incoff[u + 1];
+                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
+                V acc = vzero(V{});
+                for (int s = s0; s < s1; ++s) vadd(acc, zv[s]);
+                if (u < nint) {
+                    if (OP == OP_BRAS) {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) vget(acc, j) = div_by_count(vget(acc, j), dmul[u]);
+                    }
+                    st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, acc);
+                } else {
+                    st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, acc);
+                }
+            }
+        } else {
+            for (int u = tid; u < nu; u += blockDim.x) {
+                const int s0 = incoff[u], s1 = incoff[u + 1];
+                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
+                T acc = T(0);
+                for (int s = s0; s < s1; ++s) acc += zs[s];
+                if (u < nint) {
+                    y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
+                } else {
+                    part[p0 + (u - nint)] = acc;
+                }
+            }
         }
     }
 }
 
+// Fixed-order sums of the partials of dofs shared between blocks; slot_major: partials laid
+// out [npart][nrhs] (multi-RHS kernels), else [nrhs][npart].
 template <typename T, int OP>
 __global__ void k_combine(int64_t nsh, const int32_t* __restrict__ sh_ids, const int32_t* __restrict__ sh_off,
                           const int32_t* __restrict__ sh_slots, const T* __restrict__ part, int64_t npart,
-                          const T* __restrict__ dinv, T* __restrict__ y, int nrhs) {
+                          const T* __restrict__ dinv, T* __restrict__ y, int nrhs, int slot_major) {
     const int64_t total = nsh * nrhs;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = i / nrhs;
         const int r = (int)(i - j * nrhs);
         T acc = T(0);
-        for (int s = sh_off[j]; s < sh_off[j + 1]; ++s) acc += part[(size_t)r * npart + sh_slots[s]];
+        if (slot_major) {
+            for (int s = sh_off[j]; s < sh_off[j + 1]; ++s) acc += part[(size_t)sh_slots[s] * nrhs + r];
+        } else {
+            for (int s = sh_off[j]; s < sh_off[j + 1]; ++s) acc += part[(size_t)r * npart + sh_slots[s]];
+        }
         const int g = sh_ids[j];
         y[(size_t)g * nrhs + r] = (OP == OP_BRAS) ? acc * dinv[g] : acc;
     }
 }
 
-template <int NLOC, typename T, int KIND>
-size_t block_smem_bytes(const BlockArgs& A) {
-    constexpr int NPAD = PadTo<NLOC, T>::value;
-    return 128 + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(T) * (((A.max_u + 3) & ~3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) +
-                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
+template <typename T, int OP>
+cudaError_t launch_combine(int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
+                           const T* part, int64_t npart, const T* dinv, T* y, int nrhs, bool slot_major,
+                           cudaStream_t st) {
+    if (nsh <= 0) return cudaSuccess;
+    const int64_t total = nsh * nrhs;
+    const int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+    k_combine<T, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, npart, dinv, y, nrhs, slot_major ? 1 : 0);
+    count_launch(1);
+    return cudaGetLastError();
 }
 
-// Launch one block apply (block kernel + combine).  Returns a cudaError_t.
+template <int NLOC, typename T, int KIND>
+size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
+    constexpr int NPAD = PadTo<NLOC, T>::value;
+    const int cw = mr ? Chunk<T>::CW : 1;
+    const bool xs_mr = mr && KIND == KIND_PACKED && NLOC >= 36;
+    return 128 + ((A.max_pkt + 127u) & ~127u) +
+           sizeof(T) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) +
+                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0) + (xs_mr ? (size_t)NLOC * 256 : 0));
+}
+
+// Largest dynamic shared memory one CTA may opt into on the current device.
+int smem_optin_bytes();
+
+// Rows of nrhs values 16-byte aligned, so that full chunks load and store as one vector.
+template <typename T>
+inline bool rows_vectorisable(int nrhs, const void* x, const void* y, const void* part) {
+    const int per16 = 16 / (int)sizeof(T);
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    return nrhs % per16 == 0 && al(x) && al(y) && al(part);
+}
+
+// Launch one block apply (block kernel + combine).  Returns a cudaError_t.  Several right-hand
+// sides go to the multi-RHS kernel when its chunk buffers fit shared memory, else to one CTA
+// per (block, rhs).
 template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
 cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
                          int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
                          cudaStream_t st) {
-    const size_t smem = block_smem_bytes<NLOC, T, KIND>(A);
-    auto kern = k_block<NLOC, T, S, KIND, OP, DF>;
+    const bool mr = nrhs > 1 && OP != OP_DIAG &&
+                    block_smem_bytes<NLOC, T, KIND>(A, true) <= (size_t)smem_optin_bytes();
+    const size_t smem = block_smem_bytes<NLOC, T, KIND>(A, mr);
+    auto kern = mr ? k_block<NLOC, T, S, KIND, OP, DF, true> : k_block<NLOC, T, S, KIND, OP, DF, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    dim3 grid(nblk * nrhs);
-    const int threads = (A.max_ne + 31) / 32 * 32;         // one thread per cell of the largest block
-    kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs);
+    dim3 grid(mr ? nblk : nblk * nrhs);
+    // one thread per cell of the largest block; multi-RHS: 256 threads over the block's items
+    const int threads = mr ? 256 : (A.max_ne + 31) / 32 * 32;
+    const int vec = rows_vectorisable<T>(nrhs, x, y, part) ? 1 : 0;
+    kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs, vec);
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    if (nsh > 0) {
-        int64_t total = nsh * nrhs;
-        int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
-        k_combine<T, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, dinv, y, nrhs);
-        count_launch(1);
-        err = cudaGetLastError();
-    }
-    return err;
+    return launch_combine<T, OP>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, dinv, y, nrhs, mr, st);
 }
 
 }  // namespace bras

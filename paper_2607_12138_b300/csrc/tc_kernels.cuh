@@ -116,12 +116,18 @@ struct TcArgs {
     const unsigned char* btile;   // [Abig | Asmall] pre-arranged, 2 * N * K * 4 bytes
 };
 
-template <int NLOC, int OP>
+// MR = false: one cell per thread, one right-hand side per CTA (as k_block).  MR = true: one
+// CTA per cell block walks the right-hand sides in chunks of 4; the block's ne * 4 items
+// (cell, rhs) fill the tensor-memory lanes in passes of blockDim items (two 128-lane tiles),
+// each pass one GEMM (the E*R rows of the local product on the M side).
+template <int NLOC, int OP, bool MR = false>
 __global__ void __launch_bounds__(256, 1)
-k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs) {
+k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs,
+           int vec_ok) {
     using Sh = TcShape<NLOC>;
     constexpr int K = Sh::K, N = Sh::N;
-    const int tiles = blockDim.x / 128;                       // 128 cells (TMEM lanes) per tile
+    constexpr int CW = MR ? Chunk<float>::CW : 1;
+    const int tiles = blockDim.x / 128;                       // 128 items (TMEM lanes) per tile
     const uint32_t TMEM_COLS = (uint32_t)tiles * Sh::TILE_COLS;   // 128 or 256
     const BlockArgs& A = TA.A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -129,19 +135,17 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + 64);
     unsigned char* btile = smem_raw + 128;                           // 2 * B_BYTES, 128-B aligned
     unsigned char* tab = btile + 2 * Sh::B_BYTES;
-    float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));
-    float* zs = xs + ((A.max_u + 3) & ~3);
+    float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u][CW]
+    float* zs = xs + ((A.max_u * CW + 3) & ~3);                                  // [slot][CW]
 
-    // the nrhs CTAs of one cell block are neighbours in the grid: they share the block's
-    // tables and x cache lines in L2
-    const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x, warp = tid >> 5;
+    const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x, warp = tid >> 5;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
-    const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];   // first partial slot of this block
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
-    // this thread's cell factor, fetched now so that its latency hides behind the copies
-    const float cfac = (tid < ne) ? static_cast<const float*>(A.scale)[e0 + tid] : 0.f;
+    // this thread's cell factor (one cell per thread), fetched now so that its latency hides
+    // behind the copies
+    const float cfac = (!MR && tid < ne) ? static_cast<const float*>(A.scale)[e0 + tid] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -165,174 +169,225 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
     const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
 
-    bool ok = mbar_wait_bounded(&bars[0], A.status);
-    if (ok) {
-        // all of this thread's loads in flight at once (up to 16 per pass)
-        for (int u = tid; u < nu; u += 16 * blockDim.x) {
-            float v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int uu = u + k * blockDim.x;
-                v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int uu = u + k * blockDim.x;
-                if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
-            }
-        }
-    }
-    ok = mbar_wait_bounded(&bars[1], A.status) && ok;
-    ok = __syncthreads_and(ok);
-
-    // stage 2a: this thread's cell row -> tensor memory (big TF32 part, exact remainder)
-    const int e = tid;                                  // cell of this thread (tile e / 128, lane e % 128)
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t tile_col = (uint32_t)(warp >> 2) * Sh::TILE_COLS;
-    uint64_t neg = 0;
-    if (ok) {
-        float xl[K];
+    bool ok = cta_wait(&bars[0], 0, A.status, true);
+    int pending = -1;        // (thread 0) parity of a committed GEMM whose completion was not seen
+    uint32_t commits = 0;    // GEMMs committed on bars[3] so far (its phase parity)
+    const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
+    for (int ch = 0; ch < nchunk && ok; ++ch) {
+        const int r0 = MR ? ch * CW : blockIdx.x % nrhs;
+        const int rc = MR ? min(CW, nrhs - r0) : 1;
+        const bool vec = MR && vec_ok && rc == CW;
+        const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
+        if constexpr (MR) {
+            using V = Chunk<float>::V;
+            for (int u = tid; u < nu; u += 4 * blockDim.x) {
+                V v[4];
 #pragma unroll
-        for (int a = 0; a < K; ++a) xl[a] = 0.f;
-        if (e < ne) {
-#pragma unroll
-            for (int a = 0; a < NLOC; ++a) {
-                const uint16_t c = loc[a * ne + e];
-                const float v = xs[c & 0x7fff];
-                const bool s = (c & 0x8000) != 0;
-                neg |= (uint64_t)s << a;
-                xl[a] = s ? -v : v;
-            }
-        }
-#pragma unroll
-        for (int k0 = 0; k0 < K; k0 += 8) {
-            uint32_t hi[8], lo[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                hi[j] = f32_to_tf32(xl[k0 + j]);
-                lo[j] = __float_as_uint(xl[k0 + j] - __uint_as_float(hi[j]));
-            }
-            tmem_st8(tmem + lane_base + tile_col + k0, hi);
-            tmem_st8(tmem + lane_base + tile_col + K + k0, lo);
-        }
-        tmem_wait_st();
-    }
-    tc_fence_before();
-    __syncthreads();
-
-    // stage 2b: one thread issues the 3xTF32 GEMM for both 128-cell tiles
-    if (ok && tid == 0) {
-        ok = mbar_wait_bounded(&bars[2], A.status);
-        if (ok) {
-            tc_fence_after();
-            const uint32_t bb = smem_addr(btile), bs = bb + Sh::B_BYTES;
-            constexpr uint32_t LBO = 128, SBO = (K / 4) * 128;
-            const uint32_t idesc = umma_idesc_tf32_m128<N>();
-            for (int t = 0; t < tiles; ++t) {
-                const uint32_t base = tmem + (uint32_t)t * Sh::TILE_COLS;
-                const uint32_t d = base + 2 * K;
-#pragma unroll
-                for (int s = 0; s < K / 8; ++s) {
-                    const uint64_t db = umma_smem_desc(bb + s * 2 * 128, LBO, SBO);
-                    const uint64_t ds = umma_smem_desc(bs + s * 2 * 128, LBO, SBO);
-                    umma_tf32_ts(d, base + 8 * s, db, idesc, s > 0 ? 1u : 0u);      // big * big
-                    umma_tf32_ts(d, base + 8 * s, ds, idesc, 1u);                   // big * small
-                    umma_tf32_ts(d, base + K + 8 * s, db, idesc, 1u);               // small * big
+                for (int k = 0; k < 4; ++k) {
+                    const int uu = u + k * blockDim.x;
+                    if (uu < nu) v[k] = ld_seg(x + (size_t)ids[uu] * nrhs + r0, rc, vec);
                 }
-            }
-            umma_commit(&bars[3]);
-        } else {
-            atomicOr(A.status, 2);
-        }
-    }
-    // everyone learns whether the GEMM was issued
-    const bool issued = __syncthreads_and(ok) != 0;
-    bool mma_done = false;
-    if (issued) mma_done = mbar_wait_bounded(&bars[3], A.status);
-    mma_done = __syncthreads_and(mma_done) != 0;
-    if (issued && !mma_done && tid == 0) mbar_wait_bounded(&bars[3], A.status);   // drain before release
-    tc_fence_after();
-
-    // stage 2c: read this cell's row of Z, scale, sign, stage for the incidence sums
-    if (mma_done) {
-        const float c = cfac;
 #pragma unroll
-        for (int n0 = 0; n0 < N; n0 += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + lane_base + tile_col + 2 * K + n0, v);
-            tmem_wait_ld();
-            if (e < ne) {
+                for (int k = 0; k < 4; ++k) {
+                    const int uu = u + k * blockDim.x;
+                    if (uu < nu) {
+                        if (OP == OP_BRAS) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int a = n0 + j;
-                    if (a < NLOC) {
-                        const float acc = __uint_as_float(v[j]) * c;
-                        zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -acc : acc;
+                            for (int j = 0; j < CW; ++j) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                        }
+                        reinterpret_cast<V*>(xs)[uu] = v[k];
                     }
                 }
             }
+        } else {
+            // all of this thread's loads in flight at once (up to 16 per pass)
+            for (int u = tid; u < nu; u += 16 * blockDim.x) {
+                float v[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int uu = u + k * blockDim.x;
+                    v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int uu = u + k * blockDim.x;
+                    if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                }
+            }
+        }
+        if (ch == 0) {
+            ok = cta_wait(&bars[1], 0, A.status, ok);
+            if (!ok) break;
+        } else {
+            __syncthreads();
+        }
+
+        const int nitem = ne * CW;
+        const int npass = (nitem + blockDim.x - 1) / blockDim.x;   // block-uniform (1 without MR)
+        for (int pass = 0; pass < npass; ++pass) {
+            // stage 2a: this thread's item row -> tensor memory (big TF32 part, exact remainder)
+            const int it = pass * blockDim.x + tid;   // item of this thread (tile tid / 128, lane tid % 128)
+            const bool valid = it < nitem;
+            const int e = valid ? it / CW : 0;
+            const int rr = it % CW;
+            {
+                float xl[K];
+#pragma unroll
+                for (int a = 0; a < K; ++a) xl[a] = 0.f;
+                if (valid) {
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) xl[a] = xs[loc[a * ne + e] * CW + rr];
+                }
+#pragma unroll
+                for (int k0 = 0; k0 < K; k0 += 8) {
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        hi[j] = f32_to_tf32(xl[k0 + j]);
+                        lo[j] = __float_as_uint(xl[k0 + j] - __uint_as_float(hi[j]));
+                    }
+                    tmem_st8(tmem + lane_base + tile_col + k0, hi);
+                    tmem_st8(tmem + lane_base + tile_col + K + k0, lo);
+                }
+                tmem_wait_st();
+            }
+            tc_fence_before();
+            __syncthreads();
+
+            // stage 2b: one thread issues the 3xTF32 GEMM for the pass's tiles and waits for it;
+            // the rest of the CTA sleeps in the barrier
+            bool done = true;
+            if (tid == 0) {
+                if (ch == 0 && pass == 0) done = mbar_wait_bounded(&bars[2], A.status);
+                if (done) {
+                    tc_fence_after();
+                    const uint32_t bb = smem_addr(btile), bs = bb + Sh::B_BYTES;
+                    constexpr uint32_t LBO = 128, SBO = (K / 4) * 128;
+                    const uint32_t idesc = umma_idesc_tf32_m128<N>();
+                    const int ptiles = min(tiles, (nitem - pass * (int)blockDim.x + 127) / 128);
+                    for (int t = 0; t < ptiles; ++t) {
+                        const uint32_t base = tmem + (uint32_t)t * Sh::TILE_COLS;
+                        const uint32_t d = base + 2 * K;
+#pragma unroll
+                        for (int s = 0; s < K / 8; ++s) {
+                            const uint64_t db = umma_smem_desc(bb + s * 2 * 128, LBO, SBO);
+                            const uint64_t ds = umma_smem_desc(bs + s * 2 * 128, LBO, SBO);
+                            umma_tf32_ts(d, base + 8 * s, db, idesc, s > 0 ? 1u : 0u);      // big * big
+                            umma_tf32_ts(d, base + 8 * s, ds, idesc, 1u);                   // big * small
+                            umma_tf32_ts(d, base + K + 8 * s, db, idesc, 1u);               // small * big
+                        }
+                    }
+                    umma_commit(&bars[3]);
+                    const uint32_t par = commits & 1u;
+                    done = mbar_wait_parity_bounded(&bars[3], par, A.status);
+                    if (!done) pending = (int)par;
+                } else {
+                    atomicOr(A.status, 2);
+                }
+            }
+            ++commits;
+            ok = __syncthreads_and(done) != 0;
+            tc_fence_after();
+            if (!ok) break;
+
+            // stage 2c: read this item's row of Z, scale, stage for the incidence sums
+            const float c = MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac;
+#pragma unroll
+            for (int n0 = 0; n0 < N; n0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + lane_base + tile_col + 2 * K + n0, v);
+                tmem_wait_ld();
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int a = n0 + j;
+                        if (a < NLOC) zs[pos[a * ne + e] * CW + rr] = __uint_as_float(v[j]) * c;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();   // zs complete; the next pass may overwrite tensor memory
+        }
+        if (!ok) break;
+
+        if constexpr (MR) {
+            using V = Chunk<float>::V;
+            const V* zv = reinterpret_cast<const V*>(zs);
+            for (int u = tid; u < nu; u += blockDim.x) {
+                const int s0 = incoff[u], s1 = incoff[u + 1];
+                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
+                V acc = vzero(V{});
+                for (int s = s0; s < s1; ++s) vadd(acc, zv[s]);
+                if (u < nint) {
+                    if (OP == OP_BRAS) {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) vget(acc, j) = div_by_count(vget(acc, j), dmul[u]);
+                    }
+                    st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, acc);
+                } else {
+                    st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, acc);
+                }
+            }
+        } else {
+            for (int u = tid; u < nu; u += blockDim.x) {
+                const int s0 = incoff[u], s1 = incoff[u + 1];
+                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
+                float acc = 0.f;
+                for (int s = s0; s < s1; ++s) acc += zs[s];
+                if (u < nint) {
+                    y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
+                } else {
+                    part[p0 + (u - nint)] = acc;
+                }
+            }
         }
     }
+    // a GEMM committed but not seen complete: drain it before the columns are released
+    if (pending >= 0 && tid == 0) mbar_wait_parity_bounded(&bars[3], (uint32_t)pending, A.status);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (!mma_done) {
+    if (!ok && tid == 0) {
         // leave after the copies that may still be in flight have landed
-        if (tid == 0) {
-            mbar_wait_bounded(&bars[0], A.status);
-            mbar_wait_bounded(&bars[1], A.status);
-            mbar_wait_bounded(&bars[2], A.status);
-        }
-        return;
-    }
-
-    for (int u = tid; u < nu; u += blockDim.x) {
-        const int s0 = incoff[u], s1 = incoff[u + 1];
-        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-        float acc = 0.f;
-        for (int s = s0; s < s1; ++s) acc += zs[s];
-        if (u < nint) {
-            y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
-        } else {
-            part[p0 + (u - nint)] = acc;
-        }
+        mbar_wait_bounded(&bars[0], A.status);
+        mbar_wait_bounded(&bars[1], A.status);
+        mbar_wait_bounded(&bars[2], A.status);
     }
 }
 
 template <int NLOC>
-size_t tc_smem_bytes(const BlockArgs& A) {
+size_t tc_smem_bytes(const BlockArgs& A, bool mr = false) {
     using Sh = TcShape<NLOC>;
+    const size_t cw = mr ? Chunk<float>::CW : 1;
     return 128 + 2 * (size_t)Sh::B_BYTES + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(float) * (((A.max_u + 3) & ~3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3));
+           sizeof(float) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3));
 }
 
 template <int NLOC, int OP>
 cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y, float* part, int nrhs,
                             const float* dinv, int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off,
                             const int32_t* sh_slots, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes<NLOC>(TA.A);
-    auto kern = k_block_tc<NLOC, OP>;
+    const bool mr = nrhs > 1 && tc_smem_bytes<NLOC>(TA.A, true) <= (size_t)smem_optin_bytes();
+    const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr);
+    auto kern = mr ? k_block_tc<NLOC, OP, true> : k_block_tc<NLOC, OP, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    dim3 grid(nblk * nrhs);
-    const int threads = TA.A.max_ne > 128 ? 256 : 128;    // one or two 128-cell tensor tiles
-    kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs);
+    dim3 grid(mr ? nblk : nblk * nrhs);
+    // one or two 128-cell tensor tiles; multi-RHS: two tiles of items per pass
+    const int threads = (mr || TA.A.max_ne > 128) ? 256 : 128;
+    const int vec = rows_vectorisable<float>(nrhs, x, y, part) ? 1 : 0;
+    kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs, vec);
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    if (nsh > 0) {
-        int64_t total = nsh * nrhs;
-        int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
-        k_combine<float, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, TA.A.npart, dinv, y, nrhs);
-        count_launch(1);
-        err = cudaGetLastError();
-    }
-    return err;
+    return launch_combine<float, OP>(nsh, sh_ids, sh_off, sh_slots, part, TA.A.npart, dinv, y, nrhs, mr, st);
 }
 
 }  // namespace bras

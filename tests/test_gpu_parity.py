@@ -69,14 +69,28 @@ def test_fp32_and_bf16_applies(case):
     assert rel_err(ctx.bras_apply(xt, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space != "h1" else TOL32[space])
 
 
-@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2"])
-@pytest.mark.parametrize("nrhs", [3, 8])
+@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2", "3d_p3", "3d_p4", "hcurl3", "hdiv3"])
+@pytest.mark.parametrize("nrhs", [2, 3, 5, 8])
 def test_multi_rhs_interleaved(case, nrhs):
+    """[n][R] vectors: chunks of up to 4 right-hand sides per CTA (ragged last chunk for R = 3, 5),
+    every precision against the oracle, and each column against the single-RHS apply."""
     mesh, pr, ctx = _setup(case)
+    space = SMALL_CASES[case][1]
     x, xt = _vec(pr.n_dof, nrhs)
-    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
-    assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
+    yb, ym = ctx.bras_apply(xt), ctx.mass_apply(xt)
+    assert rel_err(yb.cpu(), pr.B @ x) <= 1e-12
+    assert rel_err(ym.cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.mass_apply(xt, B.FP64X).cpu(), pr.M @ x) <= 1e-12
     assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr.diag[:, None]) <= 1e-12
+    x32 = xt.float()
+    yb32, ym32 = ctx.bras_apply(x32, B.FP32), ctx.mass_apply(x32, B.FP32)
+    assert rel_err(yb32.cpu(), pr.B @ x) <= TOL32[space]
+    assert rel_err(ym32.cpu(), pr.M @ x) <= TOL32[space]
+    assert rel_err(ctx.bras_apply(x32, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space != "h1" else TOL32[space])
+    for r in (0, nrhs - 1):
+        col = xt[:, r].contiguous()
+        assert rel_err(yb[:, r].cpu(), ctx.bras_apply(col).cpu()) <= 1e-15
+        assert rel_err(ym32[:, r].cpu(), ctx.mass_apply(col.float(), B.FP32).cpu()) <= 1e-6
 
 
 @pytest.mark.parametrize("case", ["3d_p4", "hcurl3"])
@@ -139,12 +153,13 @@ def test_pcg_mixed_refinement_reaches_fp64_residual(case, inner):
     assert true_rel <= 1e-10 and abs(true_rel - rel[0]) <= 1e-3 * 1e-10 + 1e-6 * true_rel
 
 
-def test_pcg_multi_rhs_and_host_buffers():
-    mesh, pr, ctx = _setup("3d_p2")
-    b, bt = _vec(pr.n_dof, 4, seed=1)
+@pytest.mark.parametrize("case,nrhs", [("3d_p2", 4), ("3d_p4", 5), ("hcurl3", 3)])
+def test_pcg_multi_rhs_and_host_buffers(case, nrhs):
+    mesh, pr, ctx = _setup(case)
+    b, bt = _vec(pr.n_dof, nrhs, seed=1)
     x, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, rtol=1e-10)
     assert st == B.OK
-    for r in range(4):
+    for r in range(nrhs):
         _, its_o, _ = pcg(pr.mass_apply, b[:, r], pr.bras_apply, rtol=1e-10)
         assert abs(int(its[r]) - its_o) <= 1
         assert np.linalg.norm(b[:, r] - pr.M @ x.cpu().numpy()[:, r]) <= 1.05e-10 * np.linalg.norm(b[:, r])
@@ -201,6 +216,11 @@ def test_error_codes():
     with pytest.raises(B.BrasError) as e:
         B.Context(mesh.coords, mesh.cells, "hcurl", 1, n1, l1, s1)
     assert e.value.code == -1
+    neg = np.ones_like(l2g, dtype=np.int8)
+    neg[7, 2] = -1                                                # Lagrange dofs carry no sign
+    with pytest.raises(B.BrasError) as e:
+        B.Context(mesh.coords, mesh.cells, "h1", 2, n, l2g, neg)
+    assert e.value.code == -1 and e.value.detail == 7 * 10 + 2
     ctx = B.Context(mesh.coords, mesh.cells, "hcurl", 1, n1, l1, precisions=1)
     with pytest.raises(B.BrasError) as e:
         ctx.bras_apply(torch.zeros(n1, dtype=torch.float32, device="cuda"), B.FP32)
