@@ -4,7 +4,13 @@
 * CG iteration counts against Tables 1-3 (lowest order, uniform meshes, random RHS,
   stop at 1e-10, Sec. 3), +-1 since our meshes are smaller than the paper's 1e6 dofs;
 * the Chebyshev bound 2((sqrt k - 1)/(sqrt k + 1))^k of Sec. 3 on the A-norm error;
-* damped fixed point with omega = 2 / (1 + lambda_max) (Sec. 3) converges;
+* damped fixed point with omega = 2 / (1 + lambda_max) (Sec. 3) converges; its iteration
+  counts against the fixed-point columns of Tables 1-3 (omega from the power iteration, as in
+  Sec. 3), and its error against the closed form (I - omega Mt^{-1} M)^k e_0;
+* the power iteration against the dense pencil eigensolve (and the Rayleigh lower bound);
+* the Chebyshev semi-iteration against its closed form T_k((theta - T)/delta)/T_k(sigma) e_0
+  (eigendecomposition of the pencil), its error bound 1/T_k(sigma), and the observation of
+  Sec. 3 that it converges like CG;
 * adjoint gradient of the weighted solve against central differences and the closed
   form for a uniform density scale (x(c rho) = x / c);
 * one-dof-at-a-time outputs against the assembled operators.
@@ -18,7 +24,7 @@ import scipy.sparse.linalg as spla
 
 from oracle import gradient, sampled
 from oracle.assembly import Problem, element_matrices
-from oracle.solvers import fixed_point, kappa_hat, pcg, pencil_eigs
+from oracle.solvers import chebyshev, fixed_point, kappa_hat, pcg, pencil_eigs, power_lambda_max
 from paper_2607_12138_b300 import meshgen as mg
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
@@ -110,3 +116,80 @@ def test_sampled_outputs_match_assembled(space, order):
     ym = sampled.mass_apply_at(mesh, space, order, pr.l2g, pr.signs, pr.n_dof, x, dofs)
     np.testing.assert_allclose(yb, (pr.B @ x)[dofs], rtol=1e-12, atol=1e-12 * np.abs(pr.B @ x).max())
     np.testing.assert_allclose(ym, (pr.M @ x)[dofs], rtol=1e-12, atol=1e-12 * np.abs(pr.M @ x).max())
+
+
+@pytest.mark.parametrize("key", sorted(ITS_MESHES))
+def test_fixed_point_iterations_match_paper(key):
+    """omega from 100 power-iteration steps (seeded start), then the damped fixed point to
+    1e-10; BRAS within one iteration of the paper, diagonal within 2%.  Chebyshev on
+    [1, lambda_max] (lambda_min >= 1 for BRAS) converges like CG (Sec. 3): within one
+    iteration of the oracle's CG, which is itself pinned to the paper."""
+    make, space, order = ITS_MESHES[key]
+    pr = _problem(make(), space, order)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    v0 = mg.rhs(pr.n_dof, 1, seed=4)
+    gold = GOLD["fixed_point_iterations"][key]
+    lam_d = power_lambda_max(pr.mass_apply, pr.jacobi_apply, v0, 100)
+    lam_b = power_lambda_max(pr.mass_apply, pr.bras_apply, v0, 100)
+    _, itd = fixed_point(pr.mass_apply, b, pr.jacobi_apply, 1.0 / lam_d)
+    _, itb = fixed_point(pr.mass_apply, b, pr.bras_apply, 2.0 / (1.0 + lam_b))
+    assert abs(itb - gold["bras"]) <= 1, (key, itb, gold)
+    assert abs(itd - gold["diag"]) <= max(2, 0.02 * gold["diag"]), (key, itd, gold)
+    _, itc = chebyshev(pr.mass_apply, b, pr.bras_apply, 1.0, lam_b)
+    _, itg, _ = pcg(pr.mass_apply, b, pr.bras_apply)
+    assert abs(itc - itg) <= 1, (key, itc, itg)
+
+
+def _tiny():
+    pr = _problem(mg.unit_square_mesh(8, jitter=0.2), "h1", 2)
+    M, X = pr.M.toarray(), pr.B.toarray()
+    return pr, M, X
+
+
+def _matfun(M, X, f):
+    """f(X M) through the symmetric similarity L^T X L (M = L L^T)."""
+    L = np.linalg.cholesky(M)
+    lam, Q = np.linalg.eigh(L.T @ X @ L)
+    return np.linalg.solve(L.T, Q @ np.diag(f(lam)) @ Q.T @ L.T)
+
+
+def test_power_iteration_against_dense_eigensolve():
+    pr, M, X = _tiny()
+    lam_max = pencil_eigs(M, X)[-1]
+    v0 = mg.rhs(pr.n_dof, 1, seed=4)
+    prev = 0.0
+    for k in (5, 20, 80, 400):
+        lam = power_lambda_max(pr.mass_apply, pr.bras_apply, v0, k)
+        assert lam <= lam_max * (1 + 1e-12)            # a Rayleigh quotient: never above lambda_max
+        assert lam >= prev * (1 - 1e-12)               # and non-decreasing
+        prev = lam
+    assert abs(prev - lam_max) <= 1e-8 * lam_max
+
+
+def test_fixed_point_error_closed_form():
+    pr, M, X = _tiny()
+    b = mg.rhs(pr.n_dof, 1, seed=2)
+    xs = np.linalg.solve(M, b)
+    lam = pencil_eigs(M, X)
+    omega = 2.0 / (1.0 + lam[-1])
+    for k in (1, 3, 8):
+        u, _ = fixed_point(pr.mass_apply, b, pr.bras_apply, omega, max_its=k)
+        ek = _matfun(M, X, lambda t: (1.0 - omega * t) ** k) @ (0.0 - xs)
+        assert np.abs((u - xs) - ek).max() <= 1e-11 * np.abs(xs).max()
+
+
+def test_chebyshev_error_closed_form_and_bound():
+    pr, M, X = _tiny()
+    b = mg.rhs(pr.n_dof, 1, seed=2)
+    xs = np.linalg.solve(M, b)
+    lam = pencil_eigs(M, X)
+    lmin, lmax = 1.0, lam[-1] * 1.01                     # an interval containing the spectrum
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    e0 = -xs
+    for k in (1, 2, 5, 10):
+        u, _ = chebyshev(pr.mass_apply, b, pr.bras_apply, lmin, lmax, max_its=k)
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(k)
+        ek = _matfun(M, X, lambda t: Tk((theta - t) / delta) / Tk(theta / delta)) @ e0
+        assert np.abs((u - xs) - ek).max() <= 1e-10 * np.abs(xs).max()
+        e = u - xs
+        assert np.sqrt(e @ M @ e) <= np.sqrt(e0 @ M @ e0) / Tk(theta / delta) * (1 + 1e-9)
