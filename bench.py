@@ -310,6 +310,38 @@ def run_ours(a):
                                                    "status": int(stR)}
             del ctxR, bR, xR
 
+    # stationary iterations (Sec. 3), FP64: damped fixed point with omega = 2 / (1 + lambda_max)
+    # and Chebyshev on [1, lambda_max] with BRAS; fixed point with omega = 1 / lambda_max with
+    # Jacobi for p <= 2 (its count grows like kappa).  lambda_max from 100 power-iteration steps,
+    # outside the timed region, as in the paper's tables.
+    if not a.no_compare:
+        stat = {}
+        for pr in probs:
+            ctx, n = pr["ctx"], pr["n"]
+            v0 = torch.as_tensor(mg.rhs(n, 1, seed=4), device="cuda")
+            lb = float(ctx.lambda_max(v0, B.PC_BRAS, iters=100)[0])
+            runs = [("bras_fixed_point", lambda: ctx.fixed_point_solve(pr["b"], 2.0 / (1.0 + lb), B.PC_BRAS, out=pr["x"])),
+                    ("bras_chebyshev", lambda: ctx.chebyshev_solve(pr["b"], 1.0, lb, B.PC_BRAS, out=pr["x"]))]
+            row = {"lambda_max_bras": lb}
+            if pr["p"] <= 2:
+                ld = float(ctx.lambda_max(v0, B.PC_JACOBI, iters=100)[0])
+                row["lambda_max_jacobi"] = ld
+                runs.append(("jacobi_fixed_point",
+                             lambda: ctx.fixed_point_solve(pr["b"], 1.0 / ld, B.PC_JACOBI, out=pr["x"])))
+            for name, fn in runs:
+                fn()
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                _, its_s, rel_s, st_s = fn()
+                e1.record(st)
+                torch.cuda.synchronize()
+                row[name] = {"its": int(its_s[0]), "relres": float(rel_s[0]), "status": int(st_s),
+                             "ms": e0.elapsed_time(e1)}
+            stat[f"p{pr['p']}"] = row
+        compare["fp64_stationary"] = stat
+
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

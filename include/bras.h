@@ -210,6 +210,42 @@ int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision,
                    const double* b, double* x, int nrhs, double rtol, int maxit,
                    int* iters, double* relres, void* stream);
 
+/*
+ * Stationary iterations (Sec. 3): linear in b, no inner products in the update, so they suit
+ * settings where CG's global dot products cost (the stopping test still takes one norm per
+ * iteration).  FP64 throughout; u_0 = 0; stop when ||r_k||_2 / ||r_0||_2 <= rtol (r_k the
+ * recurrence residual) for every right-hand side, or after maxit iterations.  b, x, nrhs,
+ * iters, relres, the batched-context rule and the return codes are those of bras_pcg_solve.
+ * Scalar arrays (omega, lmin, lmax, lambda) are host arrays with one entry per right-hand
+ * side (per mesh on a batched context).
+ *
+ * bras_lambda_max -- lambda_max(Mt^{-1} M) by the power iteration that the paper uses for
+ * the fixed-point weights: v <- Mt^{-1} M v / ||.||_2, `iters` steps from v0, reporting the
+ * Rayleigh quotient (M v, Mt^{-1} M v) / (M v, v) of the last step (a lower bound that
+ * converges to lambda_max).  Mt = diag(M) for BRAS_PC_JACOBI, BRAS for BRAS_PC_BRAS.
+ *   v0     [n_dof * nrhs] double, host or device, nonzero start vectors (not modified).
+ *   lambda [nrhs] double, host (output).
+ *
+ * bras_fixed_point_solve -- damped fixed point u_{k+1} = u_k + omega Mt^{-1} (b - M u_k).
+ * It converges for 0 < omega < 2 / lambda_max; the paper's weights are omega = 1 / lambda_max
+ * (Jacobi) and omega = 2 / (1 + lambda_max) (BRAS, whose lambda_min >= 1, Sec. 2.3).
+ *   omega  [nrhs] double > 0.
+ *
+ * bras_chebyshev_solve -- Chebyshev semi-iteration for the interval [lmin, lmax] that holds
+ * the spectrum of Mt^{-1} M (for BRAS lmin = 1): with theta, delta the interval's centre and
+ * half-width, d_k = c1_k d_{k-1} + c2_k Mt^{-1} r_k, u_{k+1} = u_k + d_k, r_{k+1} = r_k - M d_k,
+ * where c1_0 = 0, c2_0 = 1/theta, rho_0 = delta/theta, rho_k = 1/(2 theta/delta - rho_{k-1}),
+ * c1_k = rho_k rho_{k-1}, c2_k = 2 rho_k / delta.
+ *   lmin, lmax  [nrhs] double, 0 < lmin < lmax.
+ */
+int bras_lambda_max(const bras_ctx* ctx, int pc, const double* v0, int nrhs, int iters, double* lambda,
+                    void* stream);
+int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, const double* b, double* x,
+                           int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);
+int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const double* lmax, const double* b,
+                         double* x, int nrhs, double rtol, int maxit, int* iters, double* relres,
+                         void* stream);
+
 /* bras_grad_rho -- rho_bar_K = -lambda_K^T M_K^1 x_K for the weighted mass M(rho) =
  * sum_K rho_K P_K^T M_K^1 P_K (M_K^1 = unit-density element matrix): the element part of
  * the adjoint gradient of x = M(rho)^{-1} b, with lambda = M^{-1} xbar (H1 only).

@@ -58,6 +58,12 @@ for _name in ("bras_mass_apply", "bras_apply", "bras_apply_noalloc", "bras_jacob
     getattr(_lib, _name).restype = _int
 _lib.bras_pcg_solve.argtypes = [_vp, _int, _int, _int, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
 _lib.bras_pcg_solve.restype = _int
+_lib.bras_lambda_max.argtypes = [_vp, _int, _vp, _int, _int, _vp, _vp]
+_lib.bras_lambda_max.restype = _int
+_lib.bras_fixed_point_solve.argtypes = [_vp, _int, _vp, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
+_lib.bras_fixed_point_solve.restype = _int
+_lib.bras_chebyshev_solve.argtypes = [_vp, _int, _vp, _vp, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
+_lib.bras_chebyshev_solve.restype = _int
 _lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.bras_grad_rho.restype = _int
 _lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
@@ -178,6 +184,22 @@ def bras_pcg_solve(ctx, pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iter
     return _check(rc, "bras_pcg_solve")
 
 
+def bras_lambda_max(ctx, pc, v0, nrhs, iters, lam, stream=None):
+    return _check(_lib.bras_lambda_max(ctx, pc, _ptr(v0), nrhs, iters, _ptr(lam), _stream(stream)), "bras_lambda_max")
+
+
+def bras_fixed_point_solve(ctx, pc, omega, b, x, nrhs, rtol, maxit, iters, relres, stream=None):
+    rc = _lib.bras_fixed_point_solve(ctx, pc, _ptr(omega), _ptr(b), _ptr(x), nrhs, rtol, maxit, _ptr(iters),
+                                     _ptr(relres), _stream(stream))
+    return _check(rc, "bras_fixed_point_solve")
+
+
+def bras_chebyshev_solve(ctx, pc, lmin, lmax, b, x, nrhs, rtol, maxit, iters, relres, stream=None):
+    rc = _lib.bras_chebyshev_solve(ctx, pc, _ptr(lmin), _ptr(lmax), _ptr(b), _ptr(x), nrhs, rtol, maxit, _ptr(iters),
+                                   _ptr(relres), _stream(stream))
+    return _check(rc, "bras_chebyshev_solve")
+
+
 def bras_grad_rho(ctx, x, lam, rho_bar, stream=None):
     return _check(_lib.bras_grad_rho(ctx, _ptr(x), _ptr(lam), _ptr(rho_bar), _stream(stream)), "bras_grad_rho")
 
@@ -282,6 +304,37 @@ class Context:
 
     def jacobi_apply(self, x, precision=FP64, out=None, stream=None):
         return self._apply(bras_jacobi_apply, x, precision, out, stream)
+
+    def _slot_array(self, v, nrhs):
+        slots = max(nrhs, getattr(self, "n_mesh", 1))
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (slots,)))
+
+    def lambda_max(self, v0, pc=PC_BRAS, iters=100, stream=None):
+        """Power-iteration lambda_max(Mt^{-1} M) from the start vector(s) v0 (float64 tensor)."""
+        nrhs = 1 if v0.dim() == 1 else v0.shape[1]
+        lam = np.zeros(max(nrhs, getattr(self, "n_mesh", 1)), dtype=np.float64)
+        bras_lambda_max(self.ctx, pc, v0, nrhs, iters, lam, stream)
+        return lam
+
+    def fixed_point_solve(self, b, omega, pc=PC_BRAS, rtol=1e-10, maxit=5000, out=None, stream=None):
+        """Damped fixed point; omega scalar or per rhs.  Returns (x, iters, relres, status)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        x = out if out is not None else torch.empty_like(b)
+        om = self._slot_array(omega, nrhs)
+        iters = np.zeros(om.size, dtype=np.int32)
+        relres = np.zeros(om.size, dtype=np.float64)
+        st = bras_fixed_point_solve(self.ctx, pc, om, b, x, nrhs, rtol, maxit, iters, relres, stream)
+        return x, iters, relres, st
+
+    def chebyshev_solve(self, b, lmin, lmax, pc=PC_BRAS, rtol=1e-10, maxit=5000, out=None, stream=None):
+        """Chebyshev semi-iteration on [lmin, lmax].  Returns (x, iters, relres, status)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        x = out if out is not None else torch.empty_like(b)
+        lo, hi = self._slot_array(lmin, nrhs), self._slot_array(lmax, nrhs)
+        iters = np.zeros(lo.size, dtype=np.int32)
+        relres = np.zeros(lo.size, dtype=np.float64)
+        st = bras_chebyshev_solve(self.ctx, pc, lo, hi, b, x, nrhs, rtol, maxit, iters, relres, stream)
+        return x, iters, relres, st
 
     def pcg_solve(self, b, pc=PC_BRAS, mode=SOLVE_FP64, inner_precision=FP32, rtol=1e-10, maxit=5000,
                   out=None, stream=None):

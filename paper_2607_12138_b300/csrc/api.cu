@@ -600,6 +600,39 @@ int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision, c
                           relres, static_cast<cudaStream_t>(stream));
 }
 
+static int slots_of(const bras_ctx* c, int nrhs) { return (c->n_mesh > 1 && c->nseg > 0) ? c->n_mesh : nrhs; }
+
+int bras_lambda_max(const bras_ctx* ctx, int pc, const double* v0, int nrhs, int iters, double* lambda,
+                    void* stream) {
+    set_detail(-1);
+    if (!ctx || !v0 || !lambda || nrhs < 1 || iters < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
+    return lambda_max_impl(const_cast<bras_ctx*>(ctx), pc, v0, nrhs, iters, lambda, static_cast<cudaStream_t>(stream));
+}
+
+int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, const double* b, double* x, int nrhs,
+                           double rtol, int maxit, int* iters, double* relres, void* stream) {
+    set_detail(-1);
+    if (!ctx || !omega || !b || !x || nrhs < 1 || pc < 0 || pc > 2 || !(rtol >= 0) || maxit < 0)
+        return BRAS_ERR_INVALID;
+    const int S = slots_of(ctx, nrhs);
+    for (int s = 0; s < S; ++s)
+        if (!(omega[s] > 0) || !std::isfinite(omega[s])) { set_detail(s); return BRAS_ERR_INVALID; }
+    return stationary_solve_impl(const_cast<bras_ctx*>(ctx), 1, pc, omega, nullptr, nullptr, b, x, nrhs, rtol, maxit,
+                                 iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const double* lmax, const double* b,
+                         double* x, int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream) {
+    set_detail(-1);
+    if (!ctx || !lmin || !lmax || !b || !x || nrhs < 1 || pc < 0 || pc > 2 || !(rtol >= 0) || maxit < 0)
+        return BRAS_ERR_INVALID;
+    const int S = slots_of(ctx, nrhs);
+    for (int s = 0; s < S; ++s)
+        if (!(lmin[s] > 0) || !(lmax[s] > lmin[s]) || !std::isfinite(lmax[s])) { set_detail(s); return BRAS_ERR_INVALID; }
+    return stationary_solve_impl(const_cast<bras_ctx*>(ctx), 2, pc, nullptr, lmin, lmax, b, x, nrhs, rtol, maxit,
+                                 iters, relres, static_cast<cudaStream_t>(stream));
+}
+
 int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar, void* stream) {
     set_detail(-1);
     if (!ctx || !x || !lam || !rho_bar || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;

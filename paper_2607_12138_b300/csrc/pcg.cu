@@ -16,11 +16,19 @@ constexpr int kDotBlocks = 1184;   // 8 per SM on a 148-SM B300 (fixed: it fixes
 constexpr int kMaxRhs = 256;
 
 enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_BN, S_SCALE, S_COUNT };
-enum { FIN_INIT_RR = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_NORM };
+enum { FIN_INIT_RR = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_NORM,
+       // stationary iterations: as FIN_INIT_RR / FIN_RR, then the step of the next update is
+       // sc[S_SCALE] for an active rhs and 0 for a converged one
+       FIN_INIT_STAT, FIN_RR_STAT,
+       // power iteration: store the dot product in S_RZ / S_PQ
+       FIN_STORE_A, FIN_STORE_B };
+enum { SOLVER_CG = 0, SOLVER_FIXED_POINT = 1, SOLVER_CHEBYSHEV = 2 };
 
 struct SolveGraph {
-    int prec = 0, pc = 0, R = 0, tsize = 0;
+    int solver = SOLVER_CG, prec = 0, pc = 0, R = 0, tsize = 0;
     const void *x = nullptr, *part = nullptr;
+    const void* coef = nullptr;   // Chebyshev coefficient table captured in the body
+    int coef_k = 0;
     int kernels_per_iter = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -43,6 +51,8 @@ struct PcgWork {
     int* flags = nullptr;         // [0..nrhs): active, [nrhs..2nrhs): its, [2nrhs]: n active, [2nrhs+1]: status
     int* h_flags = nullptr;       // pinned
     double* h_sc = nullptr;       // pinned
+    double* coef = nullptr;       // Chebyshev direction coefficients [2][kmax + 1][slots]
+    int coef_k = 0;               // kmax of the allocation
 };
 
 void free_pcg(bras_ctx* c) {
@@ -66,7 +76,8 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
     if (w) {
         for (void* p : {(void*)w->r, (void*)w->z, (void*)w->p, (void*)w->q, (void*)w->xs, (void*)w->bs,
                         (void*)w->r32, (void*)w->z32, (void*)w->p32, (void*)w->q32, (void*)w->x32,
-                        (void*)w->partial, (void*)w->sc, (void*)w->flags, (void*)w->dparam, (void*)w->iparam, (void*)w->ticket})
+                        (void*)w->partial, (void*)w->sc, (void*)w->flags, (void*)w->dparam, (void*)w->iparam, (void*)w->ticket,
+                        (void*)w->coef})
             dfree(c, p);
         free_pcg(c);
     }
@@ -121,8 +132,9 @@ struct FinArgs {
     double* sc;                    // per-rhs scalars [S_COUNT][R]
     int* flags;                    // active[R], its[R], n_active, status
     const double* dparam;          // [0] = rtol^2
-    int* iparam;                   // [0] = maxit, [1] = iterations done (solve graph only)
+    int* iparam;                   // [0] = maxit, [1] = iterations done
     cudaGraphConditionalHandle cond;
+    int in_graph;                  // the loop condition exists (solve graph)
 };
 
 __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
@@ -173,8 +185,36 @@ __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
         case FIN_NORM:
             sc[S_RR * R + r] = s;
             break;
+        case FIN_INIT_STAT:
+            sc[S_RR0 * R + r] = s;
+            sc[S_RR * R + r] = s;
+            active[r] = s > 0.0 ? 1 : 0;
+            its[r] = 0;
+            sc[S_ALPHA * R + r] = active[r] ? sc[S_SCALE * R + r] : 0.0;
+            break;
+        case FIN_RR_STAT:
+            sc[S_RR * R + r] = s;
+            if (active[r]) {
+                its[r] += 1;
+                if (!isfinite(s)) {
+                    active[r] = 0;
+                    F.flags[2 * R + 1] = BRAS_ERR_BREAKDOWN;
+                } else if (s <= tol2 * sc[S_RR0 * R + r]) {
+                    active[r] = 0;
+                }
+            }
+            sc[S_ALPHA * R + r] = active[r] ? sc[S_SCALE * R + r] : 0.0;
+            break;
+        case FIN_STORE_A:
+            sc[S_RZ * R + r] = s;
+            break;
+        case FIN_STORE_B:
+            sc[S_PQ * R + r] = s;
+            break;
     }
 }
+
+__device__ __forceinline__ bool fin_counts_iteration(int kind) { return kind == FIN_RR || kind == FIN_RR_STAT; }
 
 // `red` holds this block's 256 per-thread sums (thread t: rhs t % R, group t / R).
 __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
@@ -209,9 +249,9 @@ __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
         int cnt = 0;
         for (int k = 0; k < R; ++k) cnt += F.flags[k];
         F.flags[2 * R] = cnt;
-        if (F.kind == FIN_RR && F.iparam) {
+        if (fin_counts_iteration(F.kind) && F.iparam) {
             const int done = ++F.iparam[1];
-            cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
+            if (F.in_graph) cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
         }
         *F.ticket = 0u;
     }
@@ -334,9 +374,9 @@ __device__ void seg_partial_and_finish(const FinArgs& F, const SegArgs& G, doubl
     if (tid == 0) {
         const int cnt = cnt_s[0];
         F.flags[2 * G.M] = cnt;
-        if (F.kind == FIN_RR && F.iparam) {
+        if (fin_counts_iteration(F.kind) && F.iparam) {
             const int done = ++F.iparam[1];
-            cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
+            if (F.in_graph) cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
         }
         *F.ticket = 0u;
     }
@@ -423,11 +463,52 @@ __global__ void k_residual(double* __restrict__ r, const double* __restrict__ b,
         r[i] = b[i] - q[i];
 }
 
+// Chebyshev direction update d = c1[k] d + c2[k] z, k = iterations done (read on the device,
+// so that one captured body serves every iteration); coefficients [2][kmax + 1][S].
+__global__ void k_update_d(double* __restrict__ d, const double* __restrict__ z, const double* __restrict__ coef,
+                           const int* __restrict__ iparam, int kmax, int64_t nv, int R) {
+    const int k = min(iparam[1], kmax);
+    const double* c1 = coef + (size_t)k * R;
+    const double* c2 = coef + (size_t)(kmax + 1 + k) * R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i % R);
+        d[i] = fma(c1[r], d[i], c2[r] * z[i]);
+    }
+}
+template <typename SA>
+__global__ void k_seg_update_d(double* __restrict__ d, const double* __restrict__ z, const double* __restrict__ coef,
+                               const int* __restrict__ iparam, int kmax, SA G) {
+    const int k = min(iparam[1], kmax);
+    const int m = G.seg_mesh[blockIdx.x];
+    const double a = coef[(size_t)k * G.M + m], b = coef[(size_t)(kmax + 1 + k) * G.M + m];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) d[i] = fma(a, d[i], b * z[i]);
+}
+
+// Power iteration: v = z / sqrt(s) per rhs (or per mesh)
+__global__ void k_scale_cols(double* __restrict__ v, const double* __restrict__ z, const double* __restrict__ s,
+                             int64_t nv, int R) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const double sr = s[i % R];
+        v[i] = sr > 0.0 ? z[i] / sqrt(sr) : 0.0;
+    }
+}
+template <typename SA>
+__global__ void k_seg_scale_cols(double* __restrict__ v, const double* __restrict__ z, const double* __restrict__ s,
+                                 SA G) {
+    const double sr = s[G.seg_mesh[blockIdx.x]];
+    const double f = sr > 0.0 ? 1.0 / sqrt(sr) : 0.0;
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) v[i] = z[i] * f;
+}
+
 // ---- host helpers ------------------------------------------------------------------------
 static int grid_for(int64_t nv) { return (int)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 148 * 8)); }
 
-static FinArgs fin_args(PcgWork* w, int kind, int* iparam = nullptr, cudaGraphConditionalHandle cond = 0) {
+static FinArgs fin_args(PcgWork* w, int kind, int* iparam = nullptr, cudaGraphConditionalHandle cond = 0,
+                        bool in_graph = false) {
     FinArgs F;
+    F.in_graph = in_graph ? 1 : 0;
     F.kind = kind;
     F.partial = w->partial;
     F.ticket = w->ticket;
@@ -461,18 +542,42 @@ static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, 
     return cudaGetLastError();
 }
 
+// x += alpha p; r -= alpha q; (r, r) -> `kind` (FIN_RR for CG, FIN_RR_STAT for the stationary
+// iterations).  CG counts iterations on the device only inside its solve graph; the stationary
+// iterations always do (Chebyshev indexes its coefficients by the count).
 template <typename T>
 static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, int R, cudaGraphConditionalHandle cond,
-                              cudaStream_t st, bool in_graph) {
+                              cudaStream_t st, bool in_graph, int kind = FIN_RR) {
     PcgWork* w = c->pcg;
     const int S = batched(c) ? c->n_mesh : R;
-    int* ip = in_graph ? w->iparam : nullptr;    // the loop condition exists only inside the graph
+    int* ip = (in_graph || kind == FIN_RR_STAT) ? w->iparam : nullptr;
     if (batched(c))
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
-                                                     fin_args(w, FIN_RR, ip, cond));
+                                                     fin_args(w, kind, ip, cond, in_graph));
     else
         k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
-                                                    fin_args(w, FIN_RR, ip, cond));
+                                                    fin_args(w, kind, ip, cond, in_graph));
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t vupdate_d(bras_ctx* c, double* d, const double* z, int R, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    if (batched(c))
+        k_seg_update_d<SegArgs><<<c->nseg, 256, 0, st>>>(d, z, w->coef, w->iparam, w->coef_k, seg_args(c));
+    else
+        k_update_d<<<grid_for(c->n * R), 256, 0, st>>>(d, z, w->coef, w->iparam, w->coef_k, c->n * R, R);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t vscale_cols(bras_ctx* c, double* v, const double* z, int R, cudaStream_t st) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    if (batched(c))
+        k_seg_scale_cols<SegArgs><<<c->nseg, 256, 0, st>>>(v, z, w->sc + S_RR * S, seg_args(c));
+    else
+        k_scale_cols<<<grid_for(c->n * R), 256, 0, st>>>(v, z, w->sc + S_RR * S, c->n * R, R);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -536,21 +641,43 @@ static int enqueue_iteration(bras_ctx* c, int prec, int pc, T* x, T* r, T* z, T*
     return BRAS_OK;
 }
 
+// One iteration of a stationary method (FP64), enqueued on `st`:
+//   fixed point (Sec. 3):  z = Mt^{-1} r;  q = M z;  x += w z;  r -= w q
+//   Chebyshev (Sec. 3):    z = Mt^{-1} r;  d = c1[k] d + c2[k] z;  q = M d;  x += d;  r -= q
+// w = omega (1 for Chebyshev) while the rhs is active, 0 once it has converged; (r, r) gives
+// the stopping test and the loop condition, as in CG.  r is the recurrence residual.
+static int enqueue_stationary(bras_ctx* c, int solver, int pc, double* x, double* r, double* z, double* d, double* q,
+                              int R, cudaGraphConditionalHandle cond, cudaStream_t st, bool in_graph) {
+    RC(precond(c, pc, BRAS_FP64, r, z, R, st));
+    double* dir = z;
+    if (solver == SOLVER_CHEBYSHEV) {
+        CK(vupdate_d(c, d, z, R, st));
+        dir = d;
+    }
+    RC(run_op(c, BRAS_FP64, OP_MASS, dir, q, R, st));
+    CK(vupdate_xr<double>(c, x, r, dir, q, R, cond, st, in_graph, FIN_RR_STAT));
+    return BRAS_OK;
+}
+
 // The whole CG loop as one graph: a conditional WHILE node (default value 1 at every launch)
 // whose body is one iteration; the residual-check kernel sets the condition on the device,
 // so a solve costs one graph launch and one host synchronisation.  Graphs are cached per
 // (precision, preconditioner, nrhs, value type, buffers) and rebuilt if buffers change.
 template <typename T>
 static int get_graph(bras_ctx* c, int prec, int pc, int R, T* x, T* r, T* z, T* p, T* q, cudaGraphExec_t* out,
-                     int* kernels_per_iter) {
+                     int* kernels_per_iter, int solver = SOLVER_CG) {
     PcgWork* w = c->pcg;
     for (auto& g : w->graphs)
-        if (g.prec == prec && g.pc == pc && g.R == R && g.tsize == (int)sizeof(T) && g.x == x && g.part == c->part) {
+        if (g.solver == solver && g.prec == prec && g.pc == pc && g.R == R && g.tsize == (int)sizeof(T) && g.x == x &&
+            g.part == c->part && (solver != SOLVER_CHEBYSHEV || (g.coef == w->coef && g.coef_k == w->coef_k))) {
             *out = g.exec;
             *kernels_per_iter = g.kernels_per_iter;
             return BRAS_OK;
         }
     SolveGraph g;
+    g.solver = solver;
+    g.coef = w->coef;
+    g.coef_k = w->coef_k;
     g.prec = prec;
     g.pc = pc;
     g.R = R;
@@ -570,7 +697,14 @@ static int get_graph(bras_ctx* c, int prec, int pc, int R, T* x, T* r, T* z, T* 
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     const int64_t before = launches_so_far();
-    int rc = enqueue_iteration<T>(c, prec, pc, x, r, z, p, q, R, cond, w->cap);
+    int rc = BRAS_ERR_INVALID;
+    if (solver == SOLVER_CG) {
+        rc = enqueue_iteration<T>(c, prec, pc, x, r, z, p, q, R, cond, w->cap);
+    } else if constexpr (sizeof(T) == 8) {
+        rc = enqueue_stationary(c, solver, pc, reinterpret_cast<double*>(x), reinterpret_cast<double*>(r),
+                                reinterpret_cast<double*>(z), reinterpret_cast<double*>(p),
+                                reinterpret_cast<double*>(q), R, cond, w->cap, true);
+    }
     g.kernels_per_iter = (int)(launches_so_far() - before);
     count_launch(-g.kernels_per_iter);      // captured, not launched
     cudaGraph_t captured = nullptr;
@@ -746,6 +880,123 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
         if (relres) relres[r] = rel[r];
     }
     return status;
+}
+
+// Damped fixed point or Chebyshev semi-iteration in FP64 (Sec. 3).  step[s] = omega (fixed
+// point) per scalar slot; lo[s], hi[s] = the spectral interval (Chebyshev).
+int stationary_solve_impl(bras_ctx* c, int solver, int pc, const double* step, const double* lo, const double* hi,
+                          const double* b, double* x, int R, double rtol, int maxit, int* iters, double* relres,
+                          cudaStream_t st) {
+    if (R > kMaxRhs) return BRAS_ERR_TOO_LARGE;
+    if (batched(c) && R != 1) return BRAS_ERR_INVALID;
+    const int S = batched(c) ? c->n_mesh : R;
+    RC(ensure_pcg(c, R, false));
+    RC(ensure_part(c, R));
+    PcgWork* w = c->pcg;
+    const int64_t nv = c->n * R;
+    std::vector<double> scale(S, 1.0);
+    if (solver == SOLVER_FIXED_POINT)
+        for (int s = 0; s < S; ++s) scale[s] = step[s];
+    if (solver == SOLVER_CHEBYSHEV) {
+        // direction coefficients, data independent: c1[0] = 0, c2[0] = 1/theta; for k >= 1
+        // rho_k = 1 / (2 sigma - rho_{k-1}) (rho_0 = 1/sigma), c1[k] = rho_k rho_{k-1}, c2[k] = 2 rho_k / delta
+        const int K = std::max(maxit, 1);
+        if (w->coef_k < K) {
+            dfree(c, w->coef);
+            w->coef = (double*)dalloc_bytes(c, sizeof(double) * 2 * (size_t)(K + 1) * w->slots);
+            if (!w->coef) { w->coef_k = 0; return BRAS_ERR_OOM; }
+            w->coef_k = K;
+        }
+        const int KM = w->coef_k;
+        std::vector<double> cf(2 * (size_t)(KM + 1) * S, 0.0);
+        for (int s = 0; s < S; ++s) {
+            const double theta = 0.5 * (hi[s] + lo[s]), delta = 0.5 * (hi[s] - lo[s]), sigma = theta / delta;
+            cf[(size_t)(KM + 1) * S + s] = 1.0 / theta;
+            double rho = 1.0 / sigma;
+            for (int k = 1; k <= KM; ++k) {
+                const double rn = 1.0 / (2.0 * sigma - rho);
+                cf[(size_t)k * S + s] = rn * rho;
+                cf[(size_t)(KM + 1 + k) * S + s] = 2.0 * rn / delta;
+                rho = rn;
+            }
+        }
+        // slot stride S: the update kernels index [k][S]
+        CK(cudaMemcpyAsync(w->coef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, st));
+    }
+    const bool hb = host_ptr(b), hx = host_ptr(x);
+    const double* db = b;
+    if (hb) {
+        CK(cudaMemcpyAsync(w->bs, b, sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+        db = w->bs;
+    }
+    cudaGraphExec_t exec = nullptr;
+    int kpi = 0;
+    RC(get_graph<double>(c, BRAS_FP64, pc, R, w->xs, w->r, w->z, w->p, w->q, &exec, &kpi, solver));
+    w->h_param[0] = rtol * rtol;
+    int* hp = reinterpret_cast<int*>(w->h_param + 1);
+    hp[0] = maxit;
+    hp[1] = 0;
+    CK(cudaMemcpyAsync(w->dparam, w->h_param, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->iparam, hp, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->sc + S_SCALE * S, scale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w->xs, 0, sizeof(double) * nv, st));
+    CK(cudaMemsetAsync(w->p, 0, sizeof(double) * nv, st));
+    CK(cudaMemcpyAsync(w->r, db, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w->flags + 2 * S + 1, 0, sizeof(int), st));
+    CK(vdot(c, w->r, w->r, R, FIN_INIT_STAT, st));
+    if (maxit > 0 && host_loop()) {
+        for (int it = 0; it < maxit; ++it) {
+            RC(enqueue_stationary(c, solver, pc, w->xs, w->r, w->z, w->p, w->q, R, 0, st, false));
+            CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (w->h_flags[2 * S] == 0 || w->h_flags[2 * S + 1] != 0) break;
+        }
+        kpi = 0;
+    } else if (maxit > 0) {
+        CK(cudaGraphLaunch(exec, st));
+    }
+    if (hx) CK(cudaMemcpyAsync(x, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
+    else if (x != w->xs) CK(cudaMemcpyAsync(x, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp, w->iparam, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (maxit > 0 && kpi > 0) count_launch(kpi * hp[1]);
+    for (int s = 0; s < S; ++s) {
+        const double rr0 = w->h_sc[S_RR0 * S + s];
+        if (iters) iters[s] = w->h_flags[S + s];
+        if (relres) relres[s] = rr0 > 0 ? std::sqrt(w->h_sc[S_RR * S + s] / rr0) : 0.0;
+    }
+    if (w->h_flags[2 * S + 1] != 0) return w->h_flags[2 * S + 1];
+    return w->h_flags[2 * S] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
+}
+
+// lambda_max of Mt^{-1} M by the power iteration (Sec. 3): w = M v; z = Mt^{-1} w;
+// lambda = (w, z) / (w, v) (the Rayleigh quotient in the M inner product); v = z / ||z||.
+int lambda_max_impl(bras_ctx* c, int pc, const double* v0, int R, int iters, double* lambda, cudaStream_t st) {
+    if (R > kMaxRhs) return BRAS_ERR_TOO_LARGE;
+    if (batched(c) && R != 1) return BRAS_ERR_INVALID;
+    const int S = batched(c) ? c->n_mesh : R;
+    RC(ensure_pcg(c, R, false));
+    RC(ensure_part(c, R));
+    PcgWork* w = c->pcg;
+    const int64_t nv = c->n * R;
+    CK(cudaMemcpyAsync(w->xs, v0, sizeof(double) * nv, host_ptr(v0) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < iters; ++it) {
+        RC(run_op(c, BRAS_FP64, OP_MASS, w->xs, w->q, R, st));
+        RC(precond(c, pc, BRAS_FP64, w->q, w->z, R, st));
+        CK(vdot(c, w->q, w->z, R, FIN_STORE_A, st));
+        CK(vdot(c, w->q, w->xs, R, FIN_STORE_B, st));
+        CK(vdot(c, w->z, w->z, R, FIN_NORM, st));
+        CK(vscale_cols(c, w->xs, w->z, R, st));
+    }
+    CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int s = 0; s < S; ++s) {
+        const double den = w->h_sc[S_PQ * S + s];
+        lambda[s] = den > 0 ? w->h_sc[S_RZ * S + s] / den : 0.0;
+    }
+    return BRAS_OK;
 }
 
 }  // namespace bras

@@ -16,7 +16,7 @@ import torch
 from oracle import gradient as ograd
 from oracle import sampled
 from oracle.assembly import Problem, element_matrices
-from oracle.solvers import pcg
+from oracle.solvers import chebyshev, fixed_point, pcg, power_lambda_max
 from paper_2607_12138_b300 import meshgen as mg
 
 from _cases import SMALL_CASES, build, cube, rel_err
@@ -337,3 +337,65 @@ def test_tensor_core_vs_simt_fp32(case):
         s = getattr(simt, op)(xt, B.FP32).cpu()
         assert rel_err(a, ref) <= 2e-5 and rel_err(s, ref) <= 2e-5
         assert rel_err(a, s) <= 2e-5
+
+
+@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "c1_2d_p2", "3d_p4", "hdiv1_signed"])
+def test_stationary_iterations(case):
+    """Power iteration, damped fixed point and Chebyshev semi-iteration (Sec. 3) against the
+    oracle: lambda_max from the same start vector, iteration counts (oracle +-1), the oracle's
+    FP64 residual of the GPU solution, and the iterates after a fixed number of steps."""
+    mesh, pr, ctx = _setup(case)
+    n = pr.n_dof
+    v0 = mg.rhs(n, 1, seed=4)
+    v0t = torch.as_tensor(v0, device="cuda")
+    for pc, P in ((B.PC_JACOBI, pr.jacobi_apply), (B.PC_BRAS, pr.bras_apply)):
+        lam = ctx.lambda_max(v0t, pc, iters=40)[0]
+        assert abs(lam - power_lambda_max(pr.mass_apply, P, v0, 40)) <= 1e-10 * lam
+    lam_b = ctx.lambda_max(v0t, B.PC_BRAS, iters=100)[0]
+    omega = 2.0 / (1.0 + lam_b)
+    b, bt = _vec(n, 1, seed=1)
+    for name, run, ref in (
+            ("fixed point", lambda **k: ctx.fixed_point_solve(bt, omega, B.PC_BRAS, **k),
+             lambda **k: fixed_point(pr.mass_apply, b, pr.bras_apply, omega, **k)),
+            ("chebyshev", lambda **k: ctx.chebyshev_solve(bt, 1.0, lam_b, B.PC_BRAS, **k),
+             lambda **k: chebyshev(pr.mass_apply, b, pr.bras_apply, 1.0, lam_b, **k))):
+        x, its, rel, st = run(rtol=1e-10)
+        _, its_o = ref(rtol=1e-10)
+        assert st == B.OK and abs(int(its[0]) - its_o) <= 1, (name, its, its_o)
+        assert np.linalg.norm(b - pr.M @ x.cpu().numpy()) <= 1.05e-10 * np.linalg.norm(b), name
+        x6, its6, _, st6 = run(rtol=0.0, maxit=6)
+        u6, _ = ref(max_its=6)
+        assert st6 == B.NOT_CONVERGED and int(its6[0]) == 6
+        assert rel_err(x6.cpu().numpy(), u6) <= 1e-12, name
+    xh, itsh, _, sth = ctx.chebyshev_solve(bt.cpu(), 1.0, lam_b, B.PC_BRAS)   # host buffers
+    assert sth == B.OK and xh.device.type == "cpu"
+
+
+def test_stationary_multi_rhs_and_batched():
+    mesh, pr, ctx = _setup("3d_p2")
+    b, bt = _vec(pr.n_dof, 3, seed=1)
+    lam = ctx.lambda_max(torch.as_tensor(mg.rhs(pr.n_dof, 3, seed=4), device="cuda"), B.PC_BRAS, iters=60)
+    assert lam.shape == (3,)
+    x, its, rel, st = ctx.chebyshev_solve(bt, 1.0, lam, B.PC_BRAS)
+    assert st == B.OK
+    for r in range(3):
+        assert np.linalg.norm(b[:, r] - pr.M @ x.cpu().numpy()[:, r]) <= 1.05e-10 * np.linalg.norm(b[:, r])
+    sizes = [(2, 1), (4, 3), (3, 5), (1, 1)]
+    meshes, probs = _batch("hdiv", 1, sizes)
+    bc = B.Context.batched(meshes, "hdiv", 1)
+    off = bc.offsets
+    v0 = np.concatenate([mg.rhs(p.n_dof, 1, seed=40 + i) for i, p in enumerate(probs)])
+    lam = bc.lambda_max(torch.as_tensor(v0, device="cuda"), B.PC_BRAS, iters=50)
+    assert lam.shape == (len(sizes),)
+    for i, p in enumerate(probs):
+        seg = slice(off[i], off[i + 1])
+        assert abs(lam[i] - power_lambda_max(p.mass_apply, p.bras_apply, v0[seg], 50)) <= 1e-10 * lam[i]
+    bb = np.concatenate([mg.rhs(p.n_dof, 1, seed=20 + i) for i, p in enumerate(probs)])
+    x, its, rel, st = bc.fixed_point_solve(torch.as_tensor(bb, device="cuda"), 2.0 / (1.0 + lam), B.PC_BRAS)
+    assert st == B.OK and len(its) == len(sizes)
+    xg = x.cpu().numpy()
+    for i, p in enumerate(probs):
+        seg = slice(off[i], off[i + 1])
+        _, its_o = fixed_point(p.mass_apply, bb[seg], p.bras_apply, 2.0 / (1.0 + lam[i]))
+        assert abs(int(its[i]) - its_o) <= 1
+        assert np.linalg.norm(bb[seg] - p.M @ xg[seg]) <= 1.05e-10 * np.linalg.norm(bb[seg])
