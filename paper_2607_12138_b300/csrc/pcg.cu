@@ -15,7 +15,7 @@ namespace bras {
 constexpr int kDotBlocks = 1184;   // 8 per SM on a 148-SM B300 (fixed: it fixes the summation order)
 constexpr int kMaxRhs = 256;
 
-enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_BN, S_SCALE, S_COUNT };
+enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_ISCALE, S_SCALE, S_COUNT };
 enum { FIN_INIT_RR = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_NORM,
        // stationary iterations: as FIN_INIT_RR / FIN_RR, then the step of the next update is
        // sc[S_SCALE] for an active rhs and 0 for a converged one
@@ -257,10 +257,38 @@ __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
     }
 }
 
+// Per-thread sums of products.  FP64 vectors: FP64 products and sums.  FP32 vectors: the
+// products are formed exactly (p + e = a b by an FMA) and summed as float-float pairs with a
+// two-sum (about 2^-48 relative per step, like an FP64 sum) on the FP32 units -- B300 issues
+// FP64 at 1/64 of the FP32 rate -- and each thread's pair is finished in FP64 for the
+// fixed-order block and grid reductions.
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(h, p);
+        const float bp = __fsub_rn(t, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        h = t;
+        l = __fadd_rn(l, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+template <typename TA, typename TB> struct DotType { using type = double; };
+template <> struct DotType<float, float> { using type = float; };
+
 // Thread t of a block handles rhs t % R of rows t / R, so every thread sticks to one rhs.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int64_t n, int R,
                                              FinArgs F) {
+    using TD = typename DotType<TA, TB>::type;
     __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
     double acc = 0.0;
@@ -268,15 +296,15 @@ __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB*
         // four independent accumulators (loads in flight), combined in a fixed order
         const int64_t stride = (int64_t)gridDim.x * rows;
         int64_t i = (int64_t)blockIdx.x * rows + lr;
-        double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+        DotAcc<TD> c0, c1, c2, c3;
         for (; i + 3 * stride < n; i += 4 * stride) {
-            c0 += (double)a[i * R + r] * (double)b[i * R + r];
-            c1 += (double)a[(i + stride) * R + r] * (double)b[(i + stride) * R + r];
-            c2 += (double)a[(i + 2 * stride) * R + r] * (double)b[(i + 2 * stride) * R + r];
-            c3 += (double)a[(i + 3 * stride) * R + r] * (double)b[(i + 3 * stride) * R + r];
+            c0.add((TD)a[i * R + r], (TD)b[i * R + r]);
+            c1.add((TD)a[(i + stride) * R + r], (TD)b[(i + stride) * R + r]);
+            c2.add((TD)a[(i + 2 * stride) * R + r], (TD)b[(i + 2 * stride) * R + r]);
+            c3.add((TD)a[(i + 3 * stride) * R + r], (TD)b[(i + 3 * stride) * R + r]);
         }
-        for (; i < n; i += stride) c0 += (double)a[i * R + r] * (double)b[i * R + r];
-        acc = (c0 + c1) + (c2 + c3);
+        for (; i < n; i += stride) c0.add((TD)a[i * R + r], (TD)b[i * R + r]);
+        acc = (c0.value() + c1.value()) + (c2.value() + c3.value());
     }
     red[tid] = acc;
     block_partial_and_finish(F, R, red);
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
         const T a = (T)alpha[rr];
         const int64_t stride = (int64_t)gridDim.x * rows;
         int64_t i = (int64_t)blockIdx.x * rows + lr;
-        double c[4] = {0.0, 0.0, 0.0, 0.0};
+        DotAcc<T> c[4];
         for (; i + 3 * stride < n; i += 4 * stride) {
             T pv[4], qv[4], xv[4], rv[4];
 #pragma unroll
@@ -311,7 +339,7 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
                 x[k] = fma(a, pv[u], xv[u]);
                 const T v = fma(-a, qv[u], rv[u]);
                 r[k] = v;
-                c[u] += (double)v * (double)v;
+                c[u].add(v, v);
             }
         }
         for (; i < n; i += stride) {
@@ -319,9 +347,9 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
             x[k] = fma(a, p[k], x[k]);
             const T v = fma(-a, q[k], r[k]);
             r[k] = v;
-            c[0] += (double)v * (double)v;
+            c[0].add(v, v);
         }
-        acc = (c[0] + c[1]) + (c[2] + c[3]);
+        acc = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
     }
     red[tid] = acc;
     block_partial_and_finish(F, R, red);
@@ -386,10 +414,11 @@ template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) k_seg_dot(const TA* __restrict__ a, const TB* __restrict__ b, SegArgs G,
                                                  FinArgs F) {
     __shared__ double red[256];
+    using TD = typename DotType<TA, TB>::type;
     const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
-    double acc = 0.0;
-    for (int64_t i = beg + threadIdx.x; i < end; i += 256) acc += (double)a[i] * (double)b[i];
-    red[threadIdx.x] = acc;
+    DotAcc<TD> acc;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) acc.add((TD)a[i], (TD)b[i]);
+    red[threadIdx.x] = acc.value();
     seg_partial_and_finish(F, G, red);
 }
 
@@ -400,14 +429,14 @@ __global__ void __launch_bounds__(256) k_seg_update_xr(T* __restrict__ x, T* __r
     __shared__ double red[256];
     const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
     const T a = (T)alpha[G.seg_mesh[blockIdx.x]];
-    double acc = 0.0;
+    DotAcc<T> acc;
     for (int64_t i = beg + threadIdx.x; i < end; i += 256) {
         x[i] = fma(a, p[i], x[i]);
         const T v = fma(-a, q[i], r[i]);
         r[i] = v;
-        acc += (double)v * (double)v;
+        acc.add(v, v);
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = acc.value();
     seg_partial_and_finish(F, G, red);
 }
 
@@ -425,12 +454,14 @@ __global__ void k_seg_scale_to_f32(const double* __restrict__ r, float* __restri
     for (int64_t i = beg + threadIdx.x; i < end; i += 256) r32[i] = (float)(r[i] * sc);
 }
 
-__global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ s,
+// x += d * f with f = ||r|| (the inverse of the scale that made the inner right-hand side;
+// 0 for a slot that is not refined)
+__global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ f,
                                 SegArgs G) {
     const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
-    const double sc = s[G.seg_mesh[blockIdx.x]];
+    const double sc = f[G.seg_mesh[blockIdx.x]];
     if (!(sc > 0.0)) return;
-    for (int64_t i = beg + threadIdx.x; i < end; i += 256) x[i] += (double)d[i] / sc;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) x[i] = fma((double)d[i], sc, x[i]);
 }
 
 template <typename T>
@@ -451,11 +482,11 @@ __global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
         r32[i] = (float)(r[i] * s[i % R]);
 }
-__global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ s,
+__global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ f,
                             int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const double sr = s[i % R];
-        if (sr > 0.0) x[i] += (double)d[i] / sr;
+        const double sr = f[i % R];
+        if (sr > 0.0) x[i] = fma((double)d[i], sr, x[i]);
     }
 }
 __global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q, int64_t nv) {
@@ -825,7 +856,7 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
         CK(vdot(c, db, db, R, FIN_NORM, st));
         CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * S, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        std::vector<double> bn(S), rn(S), scale(S);
+        std::vector<double> bn(S), rn(S), scale(S), iscale(S);
         for (int r = 0; r < S; ++r) { bn[r] = std::sqrt(w->h_sc[r]); rn[r] = bn[r]; }
         int total_inner = 0;
         bool done = false;
@@ -840,7 +871,9 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
             if (total_inner >= maxit) break;
             // inner tolerance: as deep as FP32 allows, no deeper than needed
             const double tin = std::max(1e-6, std::min(1e-2, 0.5 * rtol / worst));
+            for (int r = 0; r < S; ++r) iscale[r] = scale[r] > 0 ? rn[r] : 0.0;
             CK(cudaMemcpyAsync(w->sc + S_SCALE * S, scale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(w->sc + S_ISCALE * S, iscale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
             if (batched(c))
                 k_seg_scale_to_f32<<<c->nseg, 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * S, seg_args(c));
             else
@@ -854,9 +887,9 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
             for (int r = 0; r < S; ++r) { its[r] += w->h_flags[S + r]; mx = std::max(mx, w->h_flags[S + r]); }
             total_inner += std::max(mx, 1);
             if (batched(c))
-                k_seg_accum_f32<<<c->nseg, 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * S, seg_args(c));
+                k_seg_accum_f32<<<c->nseg, 256, 0, st>>>(dx, w->x32, w->sc + S_ISCALE * S, seg_args(c));
             else
-                k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_SCALE * S, nv, R);
+                k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_ISCALE * S, nv, R);
             count_launch(1);
             RC(run_op(c, BRAS_FP64X, OP_MASS, dx, w->q, R, st));   // refinement residual b - M x
             k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv);

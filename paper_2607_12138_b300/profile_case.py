@@ -27,11 +27,13 @@ def main() -> None:
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--block-elems", type=int, default=0)
+    ap.add_argument("--precisions", type=int, default=0,
+                    help="bit mask of precisions the context builds (1 << FP64 | 1 << FP32 | 1 << BF16); 0 = all")
     a = ap.parse_args()
     mesh = mg.unit_cube_mesh(a.cells, jitter=0.15, seed=0)
     n, l2g, s = mg.dof_map(mesh, a.space, a.order)
     ctx = B.Context(mesh.coords, mesh.cells, a.space, a.order, n, l2g, s, max_nrhs=a.nrhs,
-                    block_elems=a.block_elems)
+                    block_elems=a.block_elems, precisions=a.precisions)
     prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16}[a.prec]
     dt = torch.float64 if prec == B.FP64 else torch.float32
     x = torch.as_tensor(mg.rhs(n, a.nrhs, seed=1), device="cuda").to(dt)
