@@ -1,18 +1,17 @@
-// Instantiations of the block kernels: H1 mass apply with float-float local products
-// (FP64 vectors and scatter sums), used for the refinement residual.
+// Instantiations of the H1 mass apply with float-float local products (FP64 vectors and
+// scatter sums), used for the refinement residual.
 #include <algorithm>
 
+#include "df_kernels.cuh"
 #include "dispatch.h"
 
 namespace bras {
 
 cudaError_t launch_h1_df(const LaunchCommon& L, int nloc, const double* x, double* y, double* part, int nrhs,
                          cudaStream_t st) {
-#define BRAS_CASE(N)                                                                                          \
-    if (nloc == N)                                                                                            \
-        return launch_block<N, double, double, KIND_H1, OP_MASS, true>(L.A, L.nblk, x, y, part, nrhs,        \
-                                                                      static_cast<const double*>(L.dinv), \
-                                                                      L.nsh, L.sh_ids, L.sh_off, L.sh_slots, st);
+#define BRAS_CASE(N)                                                                                    \
+    if (nloc == N)                                                                                      \
+        return launch_block_df<N>(L.A, L.nblk, x, y, part, nrhs, L.nsh, L.sh_ids, L.sh_off, L.sh_slots, st);
     BRAS_CASE(3)
     BRAS_CASE(4)
     BRAS_CASE(6)

@@ -237,7 +237,7 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 // is CW work items (cell, rhs), rows of x and y move as 16-byte vectors, partial sums are laid
 // out [npart][nrhs].  The block's tables (and streamed cell matrices, re-read from L2) serve
 // every chunk.
-template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false, bool MR = false>
+template <int NLOC, typename T, typename S, int KIND, int OP, bool MR = false>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC>::value))
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs, int vec_ok) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
@@ -246,7 +246,6 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     // Lagrange (H1) dofs carry no orientation: the sign bit of a local index is only read for
     // H(curl)/H(div)
     constexpr bool SIGNED = KIND == KIND_PACKED;
-    static_assert(!DF || (sizeof(T) == 8 && KIND == KIND_H1), "float-float path: FP64 vectors, H1 only");
     constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36 && OP != OP_DIAG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // 2 mbarriers
@@ -279,12 +278,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         for (int i = tid; i < NLOC * NPAD; i += blockDim.x) {
             const int a = i / NPAD, q = i - a * NPAD;
             const T v = q < NLOC ? ref[a * NLOC + q] : T(0);
-            if constexpr (DF) {   // (hi, lo) float pair in the slot of one double
-                const float hi = (float)v;
-                reinterpret_cast<float2*>(Ms)[i] = make_float2(hi, (float)((double)v - (double)hi));
-            } else {
-                Ms[i] = v;
-            }
+            Ms[i] = v;
         }
     }
     __syncthreads();   // barriers initialised before anyone polls them
@@ -435,31 +429,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                         const bool s = SIGNED && OP != OP_DIAG && ((neg >> a) & 1);
                         zs[pos[a * ne + e] * CW + rr] = s ? -v : v;
                     };
-                    if constexpr (DF) {
-                        const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
-                        float vh[NPAD], vl[NPAD];
-#pragma unroll
-                        for (int a = 0; a < NPAD; ++a) {
-                            vh[a] = (float)xl[a];
-                            vl[a] = (float)((double)xl[a] - (double)vh[a]);
-                        }
-#pragma unroll
-                        for (int a = 0; a < NLOC; ++a) {
-                            // four independent compensated chains (terms q mod 4), merged at the end
-                            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
-                            const float4* row = reinterpret_cast<const float4*>(Ms + a * NPAD);   // two (hi, lo) pairs
-#pragma unroll
-                            for (int q = 0; q < NPAD / 2; ++q) {
-                                const float4 m = row[q];
-                                df_term(m.x, m.y, vh[2 * q], vl[2 * q], sh[(2 * q) & 3], sl[(2 * q) & 3]);
-                                df_term(m.z, m.w, vh[2 * q + 1], vl[2 * q + 1], sh[(2 * q + 1) & 3], sl[(2 * q + 1) & 3]);
-                            }
-                            df_merge(sh[0], sl[0], sh[1], sl[1]);
-                            df_merge(sh[2], sl[2], sh[3], sl[3]);
-                            df_merge(sh[0], sl[0], sh[2], sl[2]);
-                            out(a, ((double)sh[0] + (double)sl[0]) * c);
-                        }
-                    } else if (KIND == KIND_H1) {
+                    if constexpr (KIND == KIND_H1) {
                         using VM = typename Vec4<T>::type;
                         constexpr int W = Vec4<T>::W;
                         const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
@@ -596,14 +566,14 @@ inline bool rows_vectorisable(int nrhs, const void* x, const void* y, const void
 // Launch one block apply (block kernel + combine).  Returns a cudaError_t.  Several right-hand
 // sides go to the multi-RHS kernel when its chunk buffers fit shared memory, else to one CTA
 // per (block, rhs).
-template <int NLOC, typename T, typename S, int KIND, int OP, bool DF = false>
+template <int NLOC, typename T, typename S, int KIND, int OP>
 cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
                          int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
                          cudaStream_t st) {
     const bool mr = nrhs > 1 && OP != OP_DIAG &&
                     block_smem_bytes<NLOC, T, KIND>(A, true) <= (size_t)smem_optin_bytes();
     const size_t smem = block_smem_bytes<NLOC, T, KIND>(A, mr);
-    auto kern = mr ? k_block<NLOC, T, S, KIND, OP, DF, true> : k_block<NLOC, T, S, KIND, OP, DF, false>;
+    auto kern = mr ? k_block<NLOC, T, S, KIND, OP, true> : k_block<NLOC, T, S, KIND, OP, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

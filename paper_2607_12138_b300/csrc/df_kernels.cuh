@@ -1,0 +1,174 @@
+// H1 mass apply with float-float local products (FP64 vectors, FP64 results): the residual
+// b - M x of the FP64 refinement loop around the FP32 inner solve.
+//
+// Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async copies,
+// x staged in shared memory, fixed-order in-block incidence sums, partials of boundary dofs.
+// All arithmetic runs on the FP32 units as float-float pairs (about 2^-48 relative, the
+// accuracy of FP64 sums) -- B300 issues FP64, and conversions to and from it, at 1/64 of the
+// FP32 rate:
+//   * x is split once per block-local dof into (vh, vl) with vh + vl = x to 2^-48;
+//   * each cell is split over TPC = ceil(n_loc / 8) threads, thread g owning the output rows
+//     [8g, 8g + 8) of z_K = c_K M_ref x_K (Eq. piola_mass_pullbacks); each row is one
+//     compensated chain (leading product exact by an FMA, cross terms into the low part,
+//     running sum by a two-sum), and c_K multiplies it as a float pair;
+//   * the staged copies are float pairs, summed per dof by two-sums in a fixed order, and
+//     converted to FP64 once per dof.
+// Eight independent rows per thread and ~60 registers keep many warps in flight; lanes of a
+// warp hold different cells of the same row group, so the rows of M_ref are broadcast reads.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "apply_kernels.cuh"
+
+namespace bras {
+
+constexpr int kDfRows = 8;   // output rows per thread
+
+template <int NLOC> struct DfShape {
+    static constexpr int TPC = (NLOC + kDfRows - 1) / kDfRows;   // threads per cell
+};
+
+template <int NLOC>
+__global__ void __launch_bounds__(1024, 1)
+k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__ y, double* __restrict__ part,
+           int nrhs) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    unsigned char* tab = smem_raw + 128;
+    float2* xs = reinterpret_cast<float2*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u] (hi, lo)
+    float2* zs = xs + ((A.max_u + 3) & ~3);                                          // [slot] (hi, lo)
+    float2* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                                  // [NLOC][NLOC] (hi, lo)
+
+    const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x;
+    const int cw = blockDim.x / DfShape<NLOC>::TPC;   // cells per row group
+    const int g = tid / cw;                           // this thread: rows [8g, 8g + 8) of cells tid % cw + k cw
+    const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
+    const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
+    const int nint = A.blk_nint[b];
+    const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];
+    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+        const unsigned char* src = A.pkt + A.blk_pkt[b];
+        mbar_expect_tx(&bars[0], sa);
+        bulk_copy_g2s(tab, src, sa, &bars[0]);
+        mbar_expect_tx(&bars[1], sb);
+        bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
+    }
+    const double* ref = static_cast<const double*>(A.refmat);
+    for (int i = tid; i < NLOC * NLOC; i += blockDim.x) {
+        const double v = ref[i];
+        const float hi = (float)v;
+        Ms[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+    __syncthreads();   // barriers initialised before anyone polls them
+    const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
+    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+
+    const bool okA = cta_wait(&bars[0], 0, A.status, true);
+    if (okA) {
+        for (int u = tid; u < nu; u += 8 * blockDim.x) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int uu = u + k * blockDim.x;
+                v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int uu = u + k * blockDim.x;
+                if (uu < nu) {
+                    const float hi = (float)v[k];
+                    xs[uu] = make_float2(hi, (float)(v[k] - (double)hi));
+                }
+            }
+        }
+    }
+    if (!cta_wait(&bars[1], 0, A.status, okA)) {
+        if (tid == 0) {
+            mbar_wait_bounded(&bars[0], A.status);
+            mbar_wait_bounded(&bars[1], A.status);
+        }
+        return;
+    }
+
+    for (int e = tid % cw; e < ne; e += cw) {
+        const double c = static_cast<const double*>(A.scale)[e0 + e];
+        const float ch = (float)c, cl = (float)(c - (double)ch);
+        const int a0 = g * kDfRows;
+        float sh[kDfRows], sl[kDfRows];
+#pragma unroll
+        for (int j = 0; j < kDfRows; ++j) sh[j] = sl[j] = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < NLOC; ++q) {
+            const float2 v = xs[loc[q * ne + e]];
+#pragma unroll
+            for (int j = 0; j < kDfRows; ++j) {
+                const int a = a0 + j;
+                if (a < NLOC) {
+                    const float2 m = Ms[a * NLOC + q];
+                    df_term(m.x, m.y, v.x, v.y, sh[j], sl[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kDfRows; ++j) {
+            const int a = a0 + j;
+            if (a < NLOC) {
+                float zh = 0.f, zl = 0.f;   // (sh + sl) (ch + cl)
+                df_term(ch, cl, sh[j], sl[j], zh, zl);
+                zs[pos[a * ne + e]] = make_float2(zh, zl);
+            }
+        }
+    }
+    __syncthreads();
+
+    for (int u = tid; u < nu; u += blockDim.x) {
+        const int s0 = incoff[u], s1 = incoff[u + 1];
+        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
+        float ah = 0.f, al = 0.f;
+        for (int s = s0; s < s1; ++s) {
+            const float2 z = zs[s];
+            df_merge(ah, al, z.x, z.y);
+        }
+        const double acc = (double)ah + (double)al;
+        if (u < nint) y[(size_t)ids[u] * nrhs + r] = acc;
+        else part[p0 + (u - nint)] = acc;
+    }
+}
+
+template <int NLOC>
+size_t df_smem_bytes(const BlockArgs& A) {
+    return 128 + ((A.max_pkt + 127u) & ~127u) +
+           sizeof(float2) * ((((size_t)A.max_u + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) +
+                             (size_t)NLOC * NLOC);
+}
+
+template <int NLOC>
+cudaError_t launch_block_df(const BlockArgs& A, int nblk, const double* x, double* y, double* part, int nrhs,
+                            int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
+                            cudaStream_t st) {
+    const size_t smem = df_smem_bytes<NLOC>(A);
+    auto kern = k_block_df<NLOC>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (err != cudaSuccess) return err;
+    // cells per row group: whole warps, every cell of the largest block if 1024 threads allow
+    const int cw = std::min((A.max_ne + 31) / 32 * 32, 1024 / DfShape<NLOC>::TPC / 32 * 32);
+    const int threads = cw * DfShape<NLOC>::TPC;
+    kern<<<dim3(nblk * nrhs), threads, smem, st>>>(A, x, y, part, nrhs);
+    count_launch(1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    return launch_combine<double, OP_MASS>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, nullptr, y, nrhs, false, st);
+}
+
+}  // namespace bras

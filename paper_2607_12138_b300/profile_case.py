@@ -23,7 +23,7 @@ def main() -> None:
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--cells", type=int, default=48)
     ap.add_argument("--op", default="bras", choices=["bras", "mass", "jacobi"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "fp64x"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--block-elems", type=int, default=0)
@@ -34,8 +34,8 @@ def main() -> None:
     n, l2g, s = mg.dof_map(mesh, a.space, a.order)
     ctx = B.Context(mesh.coords, mesh.cells, a.space, a.order, n, l2g, s, max_nrhs=a.nrhs,
                     block_elems=a.block_elems, precisions=a.precisions)
-    prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16}[a.prec]
-    dt = torch.float64 if prec == B.FP64 else torch.float32
+    prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16, "fp64x": B.FP64X}[a.prec]
+    dt = torch.float64 if prec in (B.FP64, B.FP64X) else torch.float32
     x = torch.as_tensor(mg.rhs(n, a.nrhs, seed=1), device="cuda").to(dt)
     y = torch.empty_like(x)
     fn = {"bras": ctx.bras_apply, "mass": ctx.mass_apply, "jacobi": ctx.jacobi_apply}[a.op]
