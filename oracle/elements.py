@@ -13,6 +13,10 @@ keeps the oracle's inverses accurate to cond(M_ref) * 1e-16).
 Spaces (reference tetrahedron / triangle with vertices 0, e_1, .., e_d):
   * Lagrange P_p: all monomials of degree <= p; dofs = values at the equispaced nodes
     ``sum alpha_i v_i / p`` (multi-indices in ascending lexicographic order).
+  * Bernstein P_p (space "h1b", the H1 "Bernstein" family of Table 1): not dualised -- the
+    basis is the Bernstein polynomials B_alpha = p!/alpha! prod_i lambda_i^alpha_i themselves
+    (barycentric lambda_0 = 1 - sum_c x_c, lambda_c = x_c), over the same multi-indices as
+    the Lagrange nodes, expanded into monomial coefficients by the multinomial theorem.
   * Nedelec first kind N1curl_k (3D): P_{k-1}^3 + x cross (homogeneous P_{k-1})^3.
   * Raviart-Thomas RT_k (3D): P_{k-1}^3 + x (homogeneous P_{k-1}).
 Dof functionals (this project's convention; the paper names Firedrake's families only):
@@ -33,6 +37,7 @@ G / |T| = L L^T.  Edge and face tuples are lexicographic in the local vertex num
 from __future__ import annotations
 
 import functools
+import math
 import itertools
 from dataclasses import dataclass
 from fractions import Fraction
@@ -149,6 +154,26 @@ def lagrange(dim: int, p: int) -> RefElement:
             F[r, j] = to_mpf(val)
     eye = [[Fraction(int(i == j)) for i in range(len(ms))] for j in range(len(ms))]
     phi = _dualise(eye, F, len(ms))
+    return RefElement("h1", dim, p, p, phi, 1)
+
+
+@functools.lru_cache(maxsize=None)
+def bernstein(dim: int, p: int) -> RefElement:
+    ms = monomials(dim, p)
+    col = {m: i for i, m in enumerate(ms)}
+    nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
+    phi = mpmath.matrix(len(ms), len(nodes))
+    for j, a in enumerate(nodes):
+        lead = Fraction(math.factorial(p), math.prod(math.factorial(x) for x in a))
+        # lambda_0^{a_0} = (1 - x_1 - .. - x_d)^{a_0}: multinomial terms with exponents k_1..k_d
+        for k in itertools.product(range(a[0] + 1), repeat=dim):
+            if sum(k) > a[0]:
+                continue
+            k0 = a[0] - sum(k)
+            c = Fraction(math.factorial(a[0]), math.factorial(k0) * math.prod(math.factorial(x) for x in k))
+            c *= (-1) ** sum(k)
+            m = tuple(k[i] + a[i + 1] for i in range(dim))
+            phi[col[m], j] += to_mpf(lead * c)
     return RefElement("h1", dim, p, p, phi, 1)
 
 
@@ -309,6 +334,8 @@ def raviart_thomas(k: int) -> RefElement:
 def reference_element(space: str, dim: int, order: int) -> RefElement:
     if space == "h1":
         return lagrange(dim, order)
+    if space == "h1b":
+        return bernstein(dim, order)
     if dim != 3:
         raise ValueError("H(curl)/H(div) elements are built on tetrahedra")
     if space == "hcurl":

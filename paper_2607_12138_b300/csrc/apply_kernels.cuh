@@ -517,7 +517,7 @@ __global__ void k_combine(int64_t nsh, const int32_t* __restrict__ sh_ids, const
                           const T* __restrict__ dinv, T* __restrict__ y, int nrhs, int slot_major) {
     const int64_t total = nsh * nrhs;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / nrhs;
+        const int64_t j = nrhs == 1 ? i : i / nrhs;
         const int r = (int)(i - j * nrhs);
         T acc = T(0);
         if (slot_major) {

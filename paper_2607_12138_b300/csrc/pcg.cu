@@ -467,25 +467,25 @@ __global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict_
 template <typename T>
 __global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fma((T)beta[i % R], p[i], z[i]);
+        p[i] = fma((T)beta[R == 1 ? 0 : i % R], p[i], z[i]);
 }
 
 template <typename T>
 __global__ void k_jacobi(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ diag, int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = x[i] / diag[i / R];
+        y[i] = x[i] / diag[R == 1 ? i : i / R];
 }
 
 // r32 = (float)(r64 * s_r)   and   x64 += (double)d32 / s_r   and   r = b - q
 __global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ s,
                                int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-        r32[i] = (float)(r[i] * s[i % R]);
+        r32[i] = (float)(r[i] * s[R == 1 ? 0 : i % R]);
 }
 __global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ f,
                             int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const double sr = f[i % R];
+        const double sr = f[R == 1 ? 0 : i % R];
         if (sr > 0.0) x[i] = fma((double)d[i], sr, x[i]);
     }
 }
@@ -502,7 +502,7 @@ __global__ void k_update_d(double* __restrict__ d, const double* __restrict__ z,
     const double* c1 = coef + (size_t)k * R;
     const double* c2 = coef + (size_t)(kmax + 1 + k) * R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i % R);
+        const int r = R == 1 ? 0 : (int)(i % R);
         d[i] = fma(c1[r], d[i], c2[r] * z[i]);
     }
 }
@@ -520,7 +520,7 @@ __global__ void k_seg_update_d(double* __restrict__ d, const double* __restrict_
 __global__ void k_scale_cols(double* __restrict__ v, const double* __restrict__ z, const double* __restrict__ s,
                              int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const double sr = s[i % R];
+        const double sr = s[R == 1 ? 0 : i % R];
         v[i] = sr > 0.0 ? z[i] / sqrt(sr) : 0.0;
     }
 }

@@ -143,7 +143,7 @@ def h1_local_nodes(dim: int, p: int) -> list[tuple[int, ...]]:
 
 
 def n_local_dofs(space: str, dim: int, order: int) -> int:
-    if space == "h1":
+    if space in ("h1", "h1b"):
         return math.comb(order + dim, dim)
     if dim != 3:
         raise ValueError("H(curl)/H(div) are built on tetrahedra")
@@ -275,8 +275,10 @@ def _hcurl_hdiv_dof_map(mesh: Mesh, space: str, k: int):
 
 
 def dof_map(mesh: Mesh, space: str, order: int):
-    """Returns (n_dof, l2g [E, n_loc] int32, signs [E, n_loc] int8 or None)."""
-    if space == "h1":
+    """Returns (n_dof, l2g [E, n_loc] int32, signs [E, n_loc] int8 or None).  "h1b"
+    (Bernstein) shares the Lagrange map: B_alpha sits on the same multi-index lattice, and
+    its trace on an entity depends only on that entity's components of alpha."""
+    if space in ("h1", "h1b"):
         return _h1_dof_map(mesh, order)
     if space in ("hcurl", "hdiv"):
         return _hcurl_hdiv_dof_map(mesh, space, order)

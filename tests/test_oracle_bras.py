@@ -7,7 +7,8 @@
 * lambda_min = 1 when n_br < 2n (RT) and for P1 on a uniform mesh (Sec. 2.3);
 * Corollary bras_piola_metric_contrast (metric-contrast bound) for H1 and H(div);
 * covariance under global dof sign flips (P' = P S, D' = D);
-* kappa_hat of Tables 1-3 at lowest order (tests/golden/paper_tables.json).
+* kappa_hat of Tables 1-3 at lowest order, and of the Bernstein column of Table 1 at every
+  order (tests/golden/paper_tables.json).
 """
 import json
 import os
@@ -161,6 +162,12 @@ KAPPA_MESHES = {
     "h1_3d_p2": (lambda: mg.unit_cube_mesh(6), "h1", 2),
     "hcurl_3d_k1": (lambda: mg.unit_cube_mesh(6), "hcurl", 1),
     "hdiv_3d_k1": (lambda: mg.unit_cube_mesh(5), "hdiv", 1),
+    "h1b_2d_p2": (lambda: mg.unit_square_mesh(16), "h1b", 2),
+    "h1b_2d_p3": (lambda: mg.unit_square_mesh(12), "h1b", 3),
+    "h1b_2d_p4": (lambda: mg.unit_square_mesh(9), "h1b", 4),
+    "h1b_3d_p2": (lambda: mg.unit_cube_mesh(6), "h1b", 2),
+    "h1b_3d_p3": (lambda: mg.unit_cube_mesh(4), "h1b", 3),
+    "h1b_3d_p4": (lambda: mg.unit_cube_mesh(4), "h1b", 4),
 }
 
 

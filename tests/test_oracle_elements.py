@@ -5,6 +5,9 @@
 * N1curl_1 = Whitney edge forms, RT_1 = Whitney face forms: element mass matrices from
   the closed form int_K lambda_i lambda_j = |K| (1 + delta_ij) / 20, on a random tetrahedron
   (this also pins the covariant / contravariant Piola metrics, Eq. piola_mass_pullbacks).
+* Bernstein: reference mass = (p!)^2 (alpha + beta)! / (alpha! beta! (2p + d)!) (the integral
+  of a barycentric monomial over the simplex), partition of unity sum_alpha B_alpha = 1, and
+  B_alpha = p!/alpha! lambda^alpha at random points.
 * Conformity: on two tetrahedra sharing a face, a random global coefficient vector gives
   a field whose value (H1), tangential part (H(curl)) or normal part (H(div)) agrees from
   both sides of the shared face -- this pins the dof functionals, the signs and the
@@ -124,8 +127,26 @@ def _field(mesh, space, order, l2g, signs, coef, k, x):
     return u
 
 
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 4), (3, 1), (3, 3), (3, 4)])
+def test_bernstein_closed_forms(dim, p):
+    ref = elements.reference_element("h1b", dim, p)
+    nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
+    f = math.factorial
+    fac = lambda a: math.prod(f(x) for x in a)
+    C = np.array([[f(p) ** 2 * math.prod(f(x + y) for x, y in zip(a, b)) / (fac(a) * fac(b) * f(2 * p + dim))
+                   for b in nodes] for a in nodes])
+    np.testing.assert_allclose(ref.mass_blocks()[0, 0], C, rtol=1e-14, atol=0)
+    rng = np.random.default_rng(dim * 10 + p)
+    pts = rng.dirichlet(np.ones(dim + 1), size=12)[:, 1:]          # reference points
+    vals = ref.evaluate(pts)[:, :, 0]
+    np.testing.assert_allclose(vals.sum(axis=1), 1.0, atol=1e-13)   # partition of unity
+    lam = np.concatenate([1 - pts.sum(1, keepdims=True), pts], axis=1)
+    expect = np.stack([f(p) / fac(a) * np.prod(lam ** np.array(a), axis=1) for a in nodes], axis=1)
+    np.testing.assert_allclose(vals, expect, atol=1e-13)
+
+
 @pytest.mark.parametrize("space,order,sort", [
-    ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False),
+    ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False), ("h1b", 3, False), ("h1b", 4, False),
     ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True),
     ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True),
     ("hcurl", 2, False)])
@@ -147,7 +168,7 @@ def test_conformity_across_shared_face(space, order, sort):
         coef = rng.standard_normal(n)
         u0 = _field(mesh, space, order, l2g, signs, coef, 0, x)
         u1 = _field(mesh, space, order, l2g, signs, coef, 1, x)
-        if space == "h1":
+        if space in ("h1", "h1b"):
             np.testing.assert_allclose(u0, u1, atol=1e-10)
         elif space == "hcurl":
             t0 = u0 - np.outer(u0 @ nrm, nrm)
