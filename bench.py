@@ -342,6 +342,30 @@ def run_ours(a):
             stat[f"p{pr['p']}"] = row
         compare["fp64_stationary"] = stat
 
+    # Bernstein basis (Table 1's second H1 family) on the same mesh: mixed BRAS-PCG against
+    # mixed Jacobi-PCG, p = 2..4
+    if not a.no_compare:
+        bern = {}
+        for pr in probs:
+            if pr["p"] < 2:
+                continue
+            cb = B.Context(mesh.coords, mesh.cells, "h1b", pr["p"], pr["n"], pr["l2g"], None)
+            row = {}
+            for name, pc in (("mixed_bras", B.PC_BRAS), ("mixed_jacobi", B.PC_JACOBI)):
+                cb.pcg_solve(pr["b"], pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=pr["x"])
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                _, its_b, rel_b, st_b = cb.pcg_solve(pr["b"], pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=pr["x"])
+                e1.record(st)
+                torch.cuda.synchronize()
+                row[name] = {"its": int(its_b[0]), "relres": float(rel_b[0]), "status": int(st_b),
+                             "ms": e0.elapsed_time(e1)}
+            bern[f"p{pr['p']}"] = row
+            del cb
+        compare["bernstein"] = bern
+
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

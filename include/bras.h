@@ -89,6 +89,9 @@ typedef struct {
     int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
     int simt_only;       /* 1: H1 FP32 applies on the FP32 units instead of the tensor-core
                             (3xTF32 tcgen05) local GEMM; 0 = tensor cores where supported  */
+    int h1_basis;        /* BRAS_H1 only: 0 = Lagrange (values at the equispaced nodes),
+                            1 = Bernstein (B_alpha = p!/alpha! prod lambda_i^alpha_i, the
+                            "Bernstein" family of Table 1); same multi-indices, same l2g */
 } bras_options;
 
 /*

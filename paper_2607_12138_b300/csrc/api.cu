@@ -129,6 +129,8 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     c->E = n_cell;
     c->n = n_dof;
     c->nvert = n_vert;
+    const int h1_basis = opt ? opt->h1_basis : 0;
+    if (h1_basis < 0 || h1_basis > 1 || (h1_basis != 0 && space != BRAS_H1)) return BRAS_ERR_INVALID;
     c->precisions = (opt && opt->precisions) ? opt->precisions : 7;
     c->max_nrhs = (opt && opt->max_nrhs > 0) ? opt->max_nrhs : 1;
     int BE = (opt && opt->block_elems) ? opt->block_elems : 256;
@@ -210,7 +212,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
 
     // reference tables (library construction, host)
     RefTables ref;
-    if (build_reference(dim, space, order, &ref) != 0) return BRAS_ERR_INVALID;
+    if (build_reference(dim, space, order, &ref, h1_basis) != 0) return BRAS_ERR_INVALID;
 
     // device copies of the geometry inputs
     const double* d_coords = coords;

@@ -401,12 +401,42 @@ int n_local(int dim, int space, int order) {
     return -1;
 }
 
-int build_reference(int dim, int space, int order, RefTables* out) {
+// ---- Bernstein ------------------------------------------------------------------------
+// B_a = p!/a! prod_i lambda_i^{a_i} over the same multi-indices as the Lagrange nodes.  The
+// reference mass is exact in closed form: the integral of lambda^g over the reference simplex
+// (volume 1/d!) is g! / (|g| + d)!, so int B_a B_b = (p!)^2 / (a! b!) (a + b)! / (2p + d)!.
+// All factorials are integers below 2^53 for p <= 4, d <= 3; one rounding at the end.
+int build_bernstein(int dim, int p, RefTables* out) {
+    std::vector<std::vector<int>> nodes;
+    compositions(dim + 1, p, nodes);
+    const int n = (int)nodes.size();
+    auto fact = [](int k) {
+        double f = 1;
+        for (int i = 2; i <= k; ++i) f *= i;
+        return f;
+    };
+    out->nloc = n;
+    out->ncomp = 1;
+    out->R.assign((size_t)n * n, 0.0);
+    const double den = fact(2 * p + dim);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double num = fact(p) * fact(p), dab = 1;
+            for (int k = 0; k <= dim; ++k) {
+                num *= fact(nodes[i][k] + nodes[j][k]);
+                dab *= fact(nodes[i][k]) * fact(nodes[j][k]);
+            }
+            out->R[(size_t)i * n + j] = num / (dab * den);
+        }
+    return 0;
+}
+
+int build_reference(int dim, int space, int order, RefTables* out, int h1_basis) {
     if (n_local(dim, space, order) < 0) return -1;
     out->dim = dim;
     out->space = space;
     out->order = order;
-    if (space == 0) return build_lagrange(dim, order, out);
+    if (space == 0) return h1_basis == 1 ? build_bernstein(dim, order, out) : build_lagrange(dim, order, out);
     return build_vector(space == 1, order, out);
 }
 

@@ -12,6 +12,7 @@ struct RefTables {
 };
 
 int n_local(int dim, int space, int order);
-int build_reference(int dim, int space, int order, RefTables* out);
+// h1_basis (H1 only): 0 = Lagrange, equispaced nodes; 1 = Bernstein.
+int build_reference(int dim, int space, int order, RefTables* out, int h1_basis = 0);
 
 }  // namespace bras
