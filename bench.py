@@ -10,9 +10,12 @@ dot products and scalars) inside FP64 iterative refinement, the TRUE FP64 residu
 The metric is conforming dofs solved per second (sum of n over the step / step time).
 Setup (tables, element inverses) is excluded, as in the paper.
 
-Comparison rows on the same GPU (plain FP64 BRAS-PCG, FP64 Jacobi-PCG, mixed Jacobi-PCG),
-the end-to-end number through host buffers, the live roofline of the dominant kernel and
-the FP64 CPU oracle baseline are reported in the same JSON line.
+Also in the same JSON line: comparison rows on the same GPU (plain FP64 BRAS-PCG, FP64
+Jacobi-PCG, mixed Jacobi-PCG; 32 right-hand sides at p = 2, 4; the FP64 damped fixed point and
+Chebyshev iterations of Sec. 3; the Bernstein basis with BRAS vs Jacobi), the end-to-end
+number through host buffers, live CUDA-event timings of the apply kernels (H1 p = 1..4 and
+the streamed N1curl k = 3 inverses on 40^3 x 6 tets), the roofline of the dominant kernel and
+of the streamed path, and the FP64 CPU oracle baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -30,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "BRAS-PCG mass-solve DOF/s to 1e-10 rel. residual (H1 p=1..4, 48^3x6 jittered tets)"
+METRIC = "BRAS-PCG mass-solve DOF/s to 1e-10 rel. residual vs Jacobi-PCG; bras_apply GB/s vs HBM peak"
 WORKLOAD = "H1 Lagrange p=1,2,3,4 on 48^3x6 Kuhn tets (663,552), jitter 0.15h, 1 RHS N(0,1), rtol 1e-10"
 N_CELLS = 48
 JITTER = 0.15
