@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--orders", default="1,2,3,4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-mesh rows")
     return ap.parse_args()
 
 
@@ -368,6 +369,43 @@ def run_ours(a):
             bern[f"p{pr['p']}"] = row
             del cb
         compare["bernstein"] = bern
+
+    # Batched multi-mesh solve (the H(div) batch configuration): jittered boxes with target tet
+    # counts log-uniform in [2e3, 2e5], one N(0,1) right-hand side each, all meshes in one
+    # context and one solve (per-mesh scalars and stopping tests).  RT k=1 on the whole batch of
+    # 256 meshes; RT k=3 on its first 32 meshes (the whole batch would need ~140 GB of FP64
+    # per-cell inverses).
+    if not a.no_compare and not a.no_batch:
+        sizes = mg.batch_mesh_sizes(256, seed=0)
+        batch = {}
+        for k, count in ((1, 256), (3, 32)):
+            t0 = time.perf_counter()
+            meshes, rhs = [], []
+            for i, (nx, nz) in enumerate(sizes[:count]):
+                m = mg.unit_cube_mesh(nx, jitter=JITTER, seed=100 + i, nz=nz)
+                nk, lk, sk = mg.dof_map(m, "hdiv", k)
+                meshes.append((m.coords, m.cells, nk, lk, sk))
+                rhs.append(mg.rhs(nk, 1, seed=1000 + i))
+            cb = B.Context.batched(meshes, "hdiv", k)
+            t_setup = time.perf_counter() - t0
+            bt = torch.as_tensor(np.concatenate(rhs), device="cuda")
+            xb = torch.empty_like(bt)
+            row = {"meshes": count, "cells": int(cb.n_cell), "dofs": int(cb.n_dof), "setup_s": t_setup}
+            for name, pc in (("mixed_bras", B.PC_BRAS), ("mixed_jacobi", B.PC_JACOBI)):
+                cb.pcg_solve(bt, pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=xb)
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                _, its_b, rel_b, st_b = cb.pcg_solve(bt, pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=xb)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                row[name] = {"ms": ms, "dof_per_s": cb.n_dof / (ms / 1e3), "its_min": int(its_b.min()),
+                             "its_max": int(its_b.max()), "relres_max": float(rel_b.max()), "status": int(st_b)}
+            batch[f"rt{k}"] = row
+            del cb, bt, xb
+        compare["batched_hdiv"] = batch
 
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
