@@ -92,6 +92,11 @@ typedef struct {
     int h1_basis;        /* BRAS_H1 only: 0 = Lagrange (values at the equispaced nodes),
                             1 = Bernstein (B_alpha = p!/alpha! prod lambda_i^alpha_i, the
                             "Bernstein" family of Table 1); same multi-indices, same l2g */
+    int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for every cell
+                            block size (multiples of 32 up to 256) whose kernels fit shared
+                            memory and keep the fastest (one table build and four applies per
+                            candidate; ignored if block_elems is set); 0 = the rule: the largest
+                            size whose FP32 kernel fits twice per SM                          */
 } bras_options;
 
 /*
@@ -262,6 +267,11 @@ int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream);
 
 /* Sizes of a context: n_dof, n_cell, n_loc, number of scatter blocks. */
 int bras_info(const bras_ctx* ctx, int64_t* n_dof, int64_t* n_cell, int* n_loc, int* n_blocks);
+
+/* The cell block size in use and, after an autotuned setup, the sizes timed and their BRAS
+ * apply times in microseconds (host arrays of at least 8 entries, or NULL; *count = 0 if the
+ * setup was not tuned). */
+int bras_block_tuning(const bras_ctx* ctx, int* block_elems, int* count, int* sizes, float* apply_us);
 
 /* Bytes one apply moves by the algorithmic count: l2g map (4 B per local dof), the
  * per-element factor (H1) or packed local inverse (H(curl)/H(div)), x read and y written,

@@ -45,7 +45,7 @@ class BrasError(RuntimeError):
 
 class bras_options(ctypes.Structure):
     _fields_ = [("precisions", ctypes.c_int), ("block_elems", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("simt_only", ctypes.c_int), ("h1_basis", ctypes.c_int)]
+                ("simt_only", ctypes.c_int), ("h1_basis", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -69,6 +69,8 @@ _lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.bras_grad_rho.restype = _int
 _lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
 _lib.bras_update_rho.restype = _int
+_lib.bras_block_tuning.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), _vp, _vp]
+_lib.bras_block_tuning.restype = _int
 _lib.bras_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int), ctypes.POINTER(_int)]
 _lib.bras_info.restype = _int
 _lib.bras_algorithmic_bytes.argtypes = [_vp, _int, _int, _int]
@@ -215,6 +217,16 @@ def bras_info(ctx):
     return n.value, e.value, nl.value, nb.value
 
 
+def bras_block_tuning(ctx):
+    """(block size in use, [(size, BRAS apply us), ...] timed by the autotuner)."""
+    be, cnt = _int(), _int()
+    sizes = np.zeros(8, dtype=np.int32)
+    us = np.zeros(8, dtype=np.float32)
+    _check(_lib.bras_block_tuning(ctx, ctypes.byref(be), ctypes.byref(cnt), sizes.ctypes.data, us.ctypes.data),
+           "bras_block_tuning")
+    return be.value, [(int(sizes[i]), float(us[i])) for i in range(cnt.value)]
+
+
 def bras_algorithmic_bytes(ctx, precision, nrhs, bras):
     return int(_lib.bras_algorithmic_bytes(ctx, precision, nrhs, int(bras)))
 
@@ -233,7 +245,7 @@ class Context:
 
     def __init__(self, coords, cells, space: str, order: int, n_dof: int, l2g, signs=None, rho=None,
                  precisions: int = 0, block_elems: int = 0, max_nrhs: int = 1, simt_only: bool = False,
-                 stream=None):
+                 autotune: bool = False, stream=None):
         dev = torch.device("cuda")
         self.dim = coords.shape[1]
         self.space = SPACES[space]
@@ -246,13 +258,14 @@ class Context:
         self._signs = t(signs, torch.int8)
         self._rho = t(rho, torch.float64)
         self.n_cell = int(self._cells.shape[0])
-        opt = bras_options(precisions, block_elems, max_nrhs, int(simt_only), H1_BASIS.get(space, 0))
+        opt = bras_options(precisions, block_elems, max_nrhs, int(simt_only), H1_BASIS.get(space, 0), int(autotune))
         self.ctx = bras_setup(self.dim, self.space, order, self._coords, self._cells, self.n_dof, self._l2g,
                               self._signs, self._rho, opt, stream)
         _, _, self.n_loc, self.n_blocks = bras_info(self.ctx)
 
     @classmethod
-    def batched(cls, meshes, space: str, order: int, precisions: int = 0, block_elems: int = 0, stream=None):
+    def batched(cls, meshes, space: str, order: int, precisions: int = 0, block_elems: int = 0, autotune: bool = False,
+                stream=None):
         """One context over several independent meshes: ``meshes`` is a list of
         (coords, cells, n_dof, l2g, signs) tuples (numpy); vectors are concatenated per mesh."""
         self = cls.__new__(cls)
@@ -268,12 +281,17 @@ class Context:
         self.dim = meshes[0][0].shape[1]
         self.space = SPACES[space]
         self.order = order
-        opt = bras_options(precisions, block_elems, 1, 0, H1_BASIS.get(space, 0))
+        opt = bras_options(precisions, block_elems, 1, 0, H1_BASIS.get(space, 0), int(autotune))
         self.ctx = bras_setup_batched(self.dim, self.space, order, descs, opt, stream)
         self.offsets = bras_batch_offsets(self.ctx)
         self.n_dof, self.n_cell, self.n_loc, self.n_blocks = bras_info(self.ctx)
         self.n_mesh = len(meshes)
         return self
+
+    @property
+    def block_tuning(self):
+        """(block size in use, [(size, BRAS apply us), ...] timed by the autotuner)."""
+        return bras_block_tuning(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

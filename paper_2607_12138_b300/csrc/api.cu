@@ -117,6 +117,36 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Replace the context's block tables (cell order, multiplicities and per-cell data do not
+// depend on the block size, so only these change).
+int install_tables(bras_ctx* c, const HostTables& t) {
+    for (void* p : {(void*)c->blk_e0, (void*)c->blk_u0, (void*)c->blk_nint, (void*)c->blk_p0, (void*)c->blk_pkt,
+                    (void*)c->pkt, (void*)c->sh_ids, (void*)c->sh_off, (void*)c->sh_slots})
+        if (p) dfree(c, p);
+    c->blk_e0 = c->blk_u0 = c->blk_nint = c->blk_p0 = c->sh_ids = c->sh_off = c->sh_slots = nullptr;
+    c->blk_pkt = nullptr;
+    c->pkt = nullptr;
+    c->BE = t.BE;
+    c->nblk = t.nblk;
+    c->max_u = t.max_u;
+    c->max_ne = t.max_ne;
+    c->U_tot = t.U_tot;
+    c->npart = t.npart;
+    c->nsh = (int64_t)t.sh_ids.size();
+    c->max_pkt = t.max_pkt;
+    int rc;
+    if ((rc = upload(c, &c->blk_e0, t.blk_e0.data(), t.blk_e0.size()))) return rc;
+    if ((rc = upload(c, &c->blk_u0, t.blk_u0.data(), t.blk_u0.size()))) return rc;
+    if ((rc = upload(c, &c->blk_nint, t.blk_nint.data(), t.blk_nint.size()))) return rc;
+    if ((rc = upload(c, &c->blk_p0, t.blk_p0.data(), t.blk_p0.size()))) return rc;
+    if ((rc = upload(c, &c->blk_pkt, t.blk_pkt.data(), t.blk_pkt.size()))) return rc;
+    if ((rc = upload(c, &c->pkt, t.pkt.data(), t.pkt.size()))) return rc;
+    if ((rc = upload(c, &c->sh_ids, t.sh_ids.data(), t.sh_ids.size()))) return rc;
+    if ((rc = upload(c, &c->sh_off, t.sh_off.data(), t.sh_off.size()))) return rc;
+    if ((rc = upload(c, &c->sh_slots, t.sh_slots.data(), t.sh_slots.size()))) return rc;
+    return BRAS_OK;
+}
+
 int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const double* coords,
                int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
                const double* rho, const bras_options* opt, cudaStream_t st, const int32_t* cell_group = nullptr) {
@@ -186,26 +216,11 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         }
         BE = std::max(32, (BE - 32) & ~31);
     }
-    c->BE = BE;
-    c->nblk = t.nblk;
-    c->max_u = t.max_u;
-    c->max_ne = t.max_ne;
-    c->U_tot = t.U_tot;
-    c->npart = t.npart;
-    c->nsh = (int64_t)t.sh_ids.size();
-    c->max_pkt = t.max_pkt;
+    t.BE = BE;
     if ((rc = upload(c, &c->perm, t.perm.data(), t.perm.size()))) return rc;
-    if ((rc = upload(c, &c->blk_e0, t.blk_e0.data(), t.blk_e0.size()))) return rc;
-    if ((rc = upload(c, &c->blk_u0, t.blk_u0.data(), t.blk_u0.size()))) return rc;
-    if ((rc = upload(c, &c->blk_nint, t.blk_nint.data(), t.blk_nint.size()))) return rc;
-    if ((rc = upload(c, &c->blk_p0, t.blk_p0.data(), t.blk_p0.size()))) return rc;
-    if ((rc = upload(c, &c->blk_pkt, t.blk_pkt.data(), t.blk_pkt.size()))) return rc;
-    if ((rc = upload(c, &c->pkt, t.pkt.data(), t.pkt.size()))) return rc;
+    if ((rc = install_tables(c, t))) return rc;
     if (!(c->status = dalloc<int>(c, 1))) return BRAS_ERR_OOM;
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return BRAS_ERR_CUDA;
-    if ((rc = upload(c, &c->sh_ids, t.sh_ids.data(), t.sh_ids.size()))) return rc;
-    if ((rc = upload(c, &c->sh_off, t.sh_off.data(), t.sh_off.size()))) return rc;
-    if ((rc = upload(c, &c->sh_slots, t.sh_slots.data(), t.sh_slots.size()))) return rc;
     if ((rc = upload(c, &c->dinv64, t.dinv.data(), t.dinv.size()))) return rc;
     if (!(c->dinv32 = dalloc<float>(c, n_dof))) return BRAS_ERR_OOM;
     if (to_float(c->dinv64, c->dinv32, n_dof, st) != cudaSuccess) return BRAS_ERR_CUDA;
@@ -305,8 +320,86 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     }
     (void)want64;
 
-    // partial-sum workspace and diag(M) (Jacobi, Sec. 2.1) through the same deterministic scatter
+    // Block-size autotuner (opt-in): time the FP32 (else FP64) BRAS apply with the block tables
+    // of every admissible size -- multiples of 32 up to 256 whose FP64 and FP32 / tensor-core
+    // kernels fit the opt-in shared memory -- and keep the fastest.
     if (ensure_part(c, c->max_nrhs) != BRAS_OK) return BRAS_ERR_OOM;
+    if (opt && opt->autotune && !fixed_be) {
+        const int prec = has_precision(c, BRAS_FP32) ? BRAS_FP32 : BRAS_FP64;
+        const size_t w = prec == BRAS_FP64 ? 8 : 4;
+        void* xv = dalloc_bytes(c, w * (size_t)n_dof);
+        void* yv = dalloc_bytes(c, w * (size_t)n_dof);
+        if (!xv || !yv) return BRAS_ERR_OOM;
+        {   // a fixed pseudo-random input (the timing does not depend on the values)
+            std::vector<double> hx((size_t)n_dof);
+            uint64_t z = 0x9E3779B97F4A7C15ull;
+            for (auto& v : hx) {
+                z ^= z << 13;
+                z ^= z >> 7;
+                z ^= z << 17;
+                v = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+            }
+            if (prec == BRAS_FP64) {
+                if (cudaMemcpy(xv, hx.data(), 8 * hx.size(), cudaMemcpyHostToDevice) != cudaSuccess) return BRAS_ERR_CUDA;
+            } else {
+                std::vector<float> hf(hx.begin(), hx.end());
+                if (cudaMemcpy(xv, hf.data(), 4 * hf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return BRAS_ERR_CUDA;
+            }
+        }
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BRAS_ERR_CUDA;
+        HostTables best;
+        float best_us = 1e30f;
+        c->tune_count = 0;
+        for (int be = 256; be >= 32; be -= 32) {
+            HostTables tt;
+            if ((rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
+                                   h_cells.data(), dim, be, &tt, &detail, cell_group)))
+                break;
+            tt.BE = be;
+            const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, tt.max_pkt, tt.max_u, tt.max_ne);
+            size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, tt.max_pkt, tt.max_u, tt.max_ne);
+            if (c->use_tc) {
+                BlockArgs tmp{};
+                tmp.max_pkt = tt.max_pkt;
+                tmp.max_u = tt.max_u;
+                tmp.max_ne = tt.max_ne;
+                s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
+            }
+            if (s64 > (size_t)smem_optin || s32 > (size_t)smem_optin) continue;
+            if ((rc = install_tables(c, tt)) || (rc = ensure_part(c, c->max_nrhs))) break;
+            float ms = 0.f;
+            bool okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;   // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && okr; ++r) okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;
+            cudaEventRecord(e1, st);
+            if (!okr || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = BRAS_ERR_CUDA;
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float us = 1e3f * ms / 3;
+            if (c->tune_count < (int)(sizeof(c->tune_be) / sizeof(c->tune_be[0]))) {
+                c->tune_be[c->tune_count] = be;
+                c->tune_us[c->tune_count] = us;
+                c->tune_count++;
+            }
+            if (us < best_us) {
+                best_us = us;
+                best = std::move(tt);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dfree(c, xv);
+        dfree(c, yv);
+        if (rc) return rc;
+        if (best_us < 1e30f) {
+            if ((rc = install_tables(c, best)) || (rc = ensure_part(c, c->max_nrhs))) return rc;
+        }
+    }
+
+    // diag(M) (Jacobi, Sec. 2.1) through the same deterministic scatter as the final tables
     if (!(c->diag64 = dalloc<double>(c, n_dof)) || !(c->diag32 = dalloc<float>(c, n_dof))) return BRAS_ERR_OOM;
     if (run_op(c, BRAS_FP64, OP_DIAG, nullptr, c->diag64, 1, st) != BRAS_OK) return BRAS_ERR_CUDA;
     if (to_float(c->diag64, c->diag32, n_dof, st) != cudaSuccess) return BRAS_ERR_CUDA;
@@ -649,6 +742,18 @@ int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream) {
     if (update_rho_launch(ctx, rho, st) != cudaSuccess) return BRAS_ERR_CUDA;
     if (run_op(ctx, BRAS_FP64, OP_DIAG, nullptr, ctx->diag64, 1, st) != BRAS_OK) return BRAS_ERR_CUDA;
     if (to_float(ctx->diag64, ctx->diag32, ctx->n, st) != cudaSuccess) return BRAS_ERR_CUDA;
+    return BRAS_OK;
+}
+
+int bras_block_tuning(const bras_ctx* ctx, int* block_elems, int* count, int* sizes, float* apply_us) {
+    set_detail(-1);
+    if (!ctx) return BRAS_ERR_INVALID;
+    if (block_elems) *block_elems = ctx->BE;
+    if (count) *count = ctx->tune_count;
+    for (int i = 0; i < ctx->tune_count; ++i) {
+        if (sizes) sizes[i] = ctx->tune_be[i];
+        if (apply_us) apply_us[i] = ctx->tune_us[i];
+    }
     return BRAS_OK;
 }
 

@@ -51,6 +51,9 @@ struct bras_ctx {
     int64_t Epad = 0;   // padded cell count of the packed (SoA) per-cell matrices
     int npk = 0;        // nloc (nloc + 1) / 2
     int bf16_fixed = 0; // cells whose bf16-rounded inverse needed a diagonal shift
+    int tune_count = 0; // block sizes the autotuner timed, and their BRAS apply times
+    int tune_be[8] = {0};
+    float tune_us[8] = {0};
 
     // scatter tables (device)
     int32_t *blk_e0 = nullptr, *blk_u0 = nullptr, *blk_nint = nullptr, *blk_p0 = nullptr;

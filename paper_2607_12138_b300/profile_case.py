@@ -27,13 +27,14 @@ def main() -> None:
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--block-elems", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="let setup time the cell block sizes")
     ap.add_argument("--precisions", type=int, default=0,
                     help="bit mask of precisions the context builds (1 << FP64 | 1 << FP32 | 1 << BF16); 0 = all")
     a = ap.parse_args()
     mesh = mg.unit_cube_mesh(a.cells, jitter=0.15, seed=0)
     n, l2g, s = mg.dof_map(mesh, a.space, a.order)
     ctx = B.Context(mesh.coords, mesh.cells, a.space, a.order, n, l2g, s, max_nrhs=a.nrhs,
-                    block_elems=a.block_elems, precisions=a.precisions)
+                    block_elems=a.block_elems, precisions=a.precisions, autotune=a.autotune)
     prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16, "fp64x": B.FP64X}[a.prec]
     dt = torch.float64 if prec in (B.FP64, B.FP64X) else torch.float32
     x = torch.as_tensor(mg.rhs(n, a.nrhs, seed=1), device="cuda").to(dt)
@@ -49,7 +50,7 @@ def main() -> None:
     torch.cuda.synchronize()
     dt_s = e0.elapsed_time(e1) / 1e3 / a.reps
     print(f"{a.space} p={a.order} cells={mesh.n_cell} dofs={n} op={a.op} prec={a.prec} nrhs={a.nrhs} "
-          f"blocks={ctx.n_blocks} avg_event_us={dt_s * 1e6:.1f} alg_bytes={ctx.algorithmic_bytes(prec, a.nrhs, a.op == 'bras')}")
+          f"blocks={ctx.n_blocks} tuning={ctx.block_tuning} avg_event_us={dt_s * 1e6:.1f} alg_bytes={ctx.algorithmic_bytes(prec, a.nrhs, a.op == 'bras')}")
 
 
 if __name__ == "__main__":

@@ -400,3 +400,25 @@ def test_stationary_multi_rhs_and_batched():
         _, its_o = fixed_point(p.mass_apply, bb[seg], p.bras_apply, 2.0 / (1.0 + lam[i]))
         assert abs(int(its[i]) - its_o) <= 1
         assert np.linalg.norm(bb[seg] - p.M @ xg[seg]) <= 1.05e-10 * np.linalg.norm(bb[seg])
+
+
+@pytest.mark.parametrize("case", ["3d_p3", "hcurl2", "c1_2d_p2"])
+def test_autotuned_block_size(case):
+    """A setup that times the admissible cell-block sizes keeps one of them, and the context
+    it leaves behind (re-installed tables, diag(M) recomputed) matches the oracle like any other."""
+    mesh, space, order, n, l2g, signs = build(case)
+    pr = Problem(mesh, space, order, l2g, signs, n)
+    ctx = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs, autotune=True)
+    be, timed = ctx.block_tuning
+    assert len(timed) >= 1 and be in [s for s, _ in timed] and all(us > 0 for _, us in timed)
+    x, xt = _vec(n)
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
+    assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr.diag) <= 1e-12
+    assert rel_err(ctx.bras_apply(xt.float(), B.FP32).cpu(), pr.B @ x) <= TOL32[space]
+    b, bt = _vec(n, 1, seed=1)
+    xs, its, rel, st = ctx.pcg_solve(bt, pc=B.PC_BRAS, rtol=1e-10)
+    _, its_o, _ = pcg(pr.mass_apply, b, pr.bras_apply, rtol=1e-10)
+    assert st == B.OK and abs(int(its[0]) - its_o) <= 1
+    plain = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs)
+    assert plain.block_tuning[1] == []
