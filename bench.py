@@ -199,7 +199,7 @@ def run_ours(a):
     probs = []
     for p in orders:
         n, l2g, s = mg.dof_map(mesh, "h1", p)
-        ctx = B.Context(mesh.coords, mesh.cells, "h1", p, n, l2g, s)
+        ctx = B.Context(mesh.coords, mesh.cells, "h1", p, n, l2g, s, autotune=True)   # setup: untimed
         b = torch.as_tensor(mg.rhs(n, 1, seed=1), device="cuda")
         x = torch.empty_like(b)
         bh = b.cpu().pin_memory()
@@ -280,7 +280,8 @@ def run_ours(a):
     last_ms = order_ms.get((B.SOLVE_MIXED, B.PC_BRAS, False), [None] * len(probs))
     for i, pr in enumerate(probs):
         its, rel, _ = res[i]
-        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel, "solve_ms": last_ms[i]})
+        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel, "solve_ms": last_ms[i],
+                       "block_elems": pr["ctx"].block_tuning[0]})
     if not a.no_compare:
         for name, mode, pc in (("fp64_bras", B.SOLVE_FP64, B.PC_BRAS), ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI),
                                ("mixed_jacobi", B.SOLVE_MIXED, B.PC_JACOBI)):
@@ -386,11 +387,12 @@ def run_ours(a):
                 nk, lk, sk = mg.dof_map(m, "hdiv", k)
                 meshes.append((m.coords, m.cells, nk, lk, sk))
                 rhs.append(mg.rhs(nk, 1, seed=1000 + i))
-            cb = B.Context.batched(meshes, "hdiv", k)
+            cb = B.Context.batched(meshes, "hdiv", k, autotune=(k == 3))
             t_setup = time.perf_counter() - t0
             bt = torch.as_tensor(np.concatenate(rhs), device="cuda")
             xb = torch.empty_like(bt)
-            row = {"meshes": count, "cells": int(cb.n_cell), "dofs": int(cb.n_dof), "setup_s": t_setup}
+            row = {"meshes": count, "cells": int(cb.n_cell), "dofs": int(cb.n_dof), "setup_s": t_setup,
+                   "block_elems": cb.block_tuning[0], "autotuned": k == 3}
             for name, pc in (("mixed_bras", B.PC_BRAS), ("mixed_jacobi", B.PC_JACOBI)):
                 cb.pcg_solve(bt, pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=xb)
                 flush.zero_()
