@@ -19,6 +19,13 @@ Spaces (reference tetrahedron / triangle with vertices 0, e_1, .., e_d):
     the Lagrange nodes, expanded into monomial coefficients by the multinomial theorem.
   * Nedelec first kind N1curl_k (3D): P_{k-1}^3 + x cross (homogeneous P_{k-1})^3.
   * Raviart-Thomas RT_k (3D): P_{k-1}^3 + x (homogeneous P_{k-1}).
+  * On triangles: N1curl_k = P_{k-1}^2 + (-y, x) (homogeneous P_{k-1}) and RT_k =
+    P_{k-1}^2 + x (homogeneous P_{k-1}); edge moments of the tangential component (N1curl) or
+    of the normal component n = (t_y, -t_x) (RT, t = v_b - v_a) against L_j, j = 0..k-1, then
+    interior moments of the two components against polynomials of degree <= k-2 orthonormal
+    for the mean inner product on the reference triangle (the face convention below), q outer,
+    component inner.  With this normal, RT_k on triangles is N1curl_k rotated by (v_y, -v_x)
+    (interior dofs: the pair of components swapped, one negated).
 Dof functionals (this project's convention; the paper names Firedrake's families only):
   * edge (a, b), x(u) = v_a + u (v_b - v_a):  int_0^1 phi(x(u)) . (v_b - v_a) L_j(u) du,
     L_j the shifted Legendre polynomial, j = 0..k-1;
@@ -331,13 +338,72 @@ def raviart_thomas(k: int) -> RefElement:
     return RefElement("hdiv", 3, k, k, phi, 3)
 
 
+EDGES_2D = [(0, 1), (0, 2), (1, 2)]
+
+
+def _functional_matrix_2d(space: str, k: int) -> mpmath.matrix:
+    ms = monomials(2, k)
+    nm = len(ms)
+    V = _ref_vertices(2)
+    rows = []
+    for a, b in EDGES_2D:
+        tau = [V[b][c] - V[a][c] for c in range(2)]
+        w = tau if space == "hcurl" else [tau[1], -tau[0]]
+        restricted = [restrict_to_param(m, V[a], [tau]) for m in ms]
+        for j in range(k):
+            L = shifted_legendre(j)
+            row = [mpmath.mpf(0)] * (2 * nm)
+            for mi, P in enumerate(restricted):
+                prod = {}
+                for (i, _), cf in P.items():
+                    for l, cl in enumerate(L):
+                        prod[(i + l, 0)] = prod.get((i + l, 0), 0) + cf * cl
+                val = to_mpf(integrate_segment(prod))
+                for c in range(2):
+                    row[c * nm + mi] = w[c] * val
+            rows.append(row)
+    qdeg = k - 2
+    if qdeg >= 0:
+        tm = _face_test_monomials(qdeg)                   # (x, y) = (s, t) on the reference triangle
+        C = _orthonormal_coeffs_triangle(qdeg)
+        mono_int = [[to_mpf(integrate_triangle({(m[0] + qi, m[1] + qj): Fraction(1)})) for m in ms]
+                    for (qi, qj) in tm]
+        for r in range(len(tm)):
+            vals = [mpmath.fsum(C[r, i] * mono_int[i][mi] for i in range(len(tm))) for mi in range(nm)]
+            for comp in range(2):
+                row = [mpmath.mpf(0)] * (2 * nm)
+                row[comp * nm:(comp + 1) * nm] = vals
+                rows.append(row)
+    return mpmath.matrix(rows)
+
+
+@functools.lru_cache(maxsize=None)
+def vector_2d(space: str, k: int) -> RefElement:
+    ms = monomials(2, k)
+    nm = len(ms)
+    idx = {m: i for i, m in enumerate(ms)}
+    span = [[Fraction(int(c * nm + idx[m] == t)) for t in range(2 * nm)]
+            for c in range(2) for m in monomials(2, k - 1)]
+    for m in (m for m in monomials(2, k - 1) if sum(m) == k - 1):
+        v = [Fraction(0)] * (2 * nm)
+        if space == "hcurl":            # (-y m, x m)
+            v[0 * nm + idx[(m[0], m[1] + 1)]] = Fraction(-1)
+            v[1 * nm + idx[(m[0] + 1, m[1])]] = Fraction(1)
+        else:                           # (x m, y m)
+            v[0 * nm + idx[(m[0] + 1, m[1])]] = Fraction(1)
+            v[1 * nm + idx[(m[0], m[1] + 1)]] = Fraction(1)
+        span.append(v)
+    phi = _dualise(span, _functional_matrix_2d(space, k), k * (k + 2))
+    return RefElement(space, 2, k, k, phi, 2)
+
+
 def reference_element(space: str, dim: int, order: int) -> RefElement:
     if space == "h1":
         return lagrange(dim, order)
     if space == "h1b":
         return bernstein(dim, order)
-    if dim != 3:
-        raise ValueError("H(curl)/H(div) elements are built on tetrahedra")
+    if dim == 2 and space in ("hcurl", "hdiv"):
+        return vector_2d(space, order)
     if space == "hcurl":
         return nedelec1(order)
     if space == "hdiv":

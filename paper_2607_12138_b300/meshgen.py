@@ -145,8 +145,8 @@ def h1_local_nodes(dim: int, p: int) -> list[tuple[int, ...]]:
 def n_local_dofs(space: str, dim: int, order: int) -> int:
     if space in ("h1", "h1b"):
         return math.comb(order + dim, dim)
-    if dim != 3:
-        raise ValueError("H(curl)/H(div) are built on tetrahedra")
+    if dim == 2:
+        return order * (order + 2)                       # N1curl_k and RT_k on triangles
     k = order
     if space == "hcurl":
         return k * (k + 2) * (k + 3) // 2
@@ -228,9 +228,36 @@ def _perm_parity(g: np.ndarray) -> np.ndarray:
     return s
 
 
+def _hcurl_hdiv_dof_map_2d(mesh: Mesh, k: int):
+    """Triangles (N1curl and RT share it): k moments per edge, oriented from the lower to the
+    higher global vertex id (moment j flips by (-1)^(j+1) on reversal), then k(k-1) interior
+    dofs per cell."""
+    cells, nv = mesh.cells.astype(np.int64), mesh.n_vert
+    E = cells.shape[0]
+    n_i = k * (k - 1)
+    cols, sgns = [], []
+    g = cells[:, EDGES_2D]                               # [E, 3, 2]
+    gs = np.sort(g, axis=2)
+    uniq, inv = _entity_index(gs[:, :, 0] * nv + gs[:, :, 1])
+    rev = g[:, :, 0] > g[:, :, 1]
+    for e in range(3):
+        for j in range(k):
+            cols.append(inv[:, e] * k + j)
+            flip = -1 if (j % 2 == 0) else 1             # (-1)^(j+1)
+            sgns.append(np.where(rev[:, e], flip, 1))
+    base = uniq.size * k
+    for j in range(n_i):
+        cols.append(base + np.arange(E) * n_i + j)
+        sgns.append(np.ones(E, dtype=np.int64))
+    base += E * n_i
+    l2g = np.stack(cols, axis=1).astype(np.int32)
+    signs = np.stack(sgns, axis=1).astype(np.int8)
+    return base, l2g, signs
+
+
 def _hcurl_hdiv_dof_map(mesh: Mesh, space: str, k: int):
-    if mesh.dim != 3:
-        raise ValueError("H(curl)/H(div) dof maps are built on tetrahedra")
+    if mesh.dim == 2:
+        return _hcurl_hdiv_dof_map_2d(mesh, k)
     cells, nv = mesh.cells.astype(np.int64), mesh.n_vert
     E = cells.shape[0]
     if space == "hcurl":

@@ -36,12 +36,20 @@ def test_one_element_is_exact_inverse(space, order):
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
 
 
+@pytest.mark.parametrize("space,order", [("hcurl", 1), ("hcurl", 3), ("hdiv", 2)])
+def test_one_triangle_is_exact_inverse(space, order):
+    pr = _problem(mg.single_simplex_mesh(2, seed=2), space, order)
+    np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
+
+
 CASES = [(mg.unit_square_mesh(5, jitter=0.2, seed=4), "h1", 2),
          (mg.unit_cube_mesh(2, jitter=0.15), "h1", 1),
          (mg.relabel_mesh(mg.unit_cube_mesh(2), seed=3), "hcurl", 1),
          (mg.unit_cube_mesh(2), "hcurl", 2),
          (mg.relabel_mesh(mg.unit_cube_mesh(2), seed=5), "hdiv", 1),
-         (mg.unit_cube_mesh(2), "hdiv", 2)]
+         (mg.unit_cube_mesh(2), "hdiv", 2),
+         (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=6), seed=7), "hcurl", 2),
+         (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=8), seed=9), "hdiv", 3)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -162,6 +170,8 @@ KAPPA_MESHES = {
     "h1_3d_p2": (lambda: mg.unit_cube_mesh(6), "h1", 2),
     "hcurl_3d_k1": (lambda: mg.unit_cube_mesh(6), "hcurl", 1),
     "hdiv_3d_k1": (lambda: mg.unit_cube_mesh(5), "hdiv", 1),
+    "hcurl_2d_k1": (lambda: mg.unit_square_mesh(24), "hcurl", 1),
+    "hdiv_2d_k1": (lambda: mg.unit_square_mesh(24), "hdiv", 1),
     "h1b_2d_p2": (lambda: mg.unit_square_mesh(16), "h1b", 2),
     "h1b_2d_p3": (lambda: mg.unit_square_mesh(12), "h1b", 3),
     "h1b_2d_p4": (lambda: mg.unit_square_mesh(9), "h1b", 4),

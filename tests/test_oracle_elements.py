@@ -8,6 +8,8 @@
 * Bernstein: reference mass = (p!)^2 (alpha + beta)! / (alpha! beta! (2p + d)!) (the integral
   of a barycentric monomial over the simplex), partition of unity sum_alpha B_alpha = 1, and
   B_alpha = p!/alpha! lambda^alpha at random points.
+* 2D N1curl / RT: on two triangles sharing an edge the tangential / normal trace agrees, and
+  RT_k on triangles is N1curl_k rotated by (v_y, -v_x) (interior pairs swapped with a sign).
 * Conformity: on two tetrahedra sharing a face, a random global coefficient vector gives
   a field whose value (H1), tangential part (H(curl)) or normal part (H(div)) agrees from
   both sides of the shared face -- this pins the dof functionals, the signs and the
@@ -177,3 +179,60 @@ def test_conformity_across_shared_face(space, order, sort):
             assert np.abs(u0 - u1).max() > 1e-6        # normal part is free to jump
         else:
             np.testing.assert_allclose(u0 @ nrm, u1 @ nrm, atol=1e-10)
+
+
+def _two_triangles(seed, sort=True):
+    rng = np.random.default_rng(seed)
+    coords = np.array([[0, 0], [1, 0], [0, 1], [1, 1.0]]) + rng.uniform(-0.15, 0.15, (4, 2))
+    cells = np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32)
+    if not sort:
+        cells = np.array([[2, 0, 1], [3, 1, 2]], dtype=np.int32)
+    return mg.Mesh(coords, cells, 2)
+
+
+@pytest.mark.parametrize("space", ["hcurl", "hdiv"])
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("sort", [True, False])
+def test_conformity_across_shared_edge_2d(space, order, sort):
+    mesh = _two_triangles(3, sort)
+    n, l2g, signs = mg.dof_map(mesh, space, order)
+    ref = elements.reference_element(space, 2, order)
+    shared = sorted(set(mesh.cells[0]) & set(mesh.cells[1]))
+    V = mesh.coords[shared]
+    t = V[1] - V[0]
+    nrm = np.array([t[1], -t[0]]) / np.linalg.norm(t)
+    x = V[0] + np.outer(np.random.default_rng(1).uniform(0, 1, 15), t)
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        coef = rng.standard_normal(n)
+        u = []
+        for k in range(2):
+            X = mesh.coords[mesh.cells[k]]
+            J = (X[1:] - X[0]).T
+            xh = np.linalg.solve(J, (x - X[0]).T).T
+            loc = signs[k].astype(float) * coef[l2g[k]]
+            v = np.einsum("pnc,n->pc", ref.evaluate(xh), loc)
+            u.append(v @ np.linalg.inv(J) if space == "hcurl" else v @ J.T / np.linalg.det(J))
+        if space == "hcurl":
+            np.testing.assert_allclose(u[0] @ t, u[1] @ t, atol=1e-10)
+            assert np.abs(u[0] - u[1]).max() > 1e-6
+        else:
+            np.testing.assert_allclose(u[0] @ nrm, u[1] @ nrm, atol=1e-10)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_rt_is_rotated_nedelec_2d(order):
+    """With n = R t, R v = (v_y, -v_x), the RT edge moments of R psi equal the N1curl edge moments
+    of psi, and the RT interior moments of components (0, 1) are the N1curl ones of (1, -0): so
+    the RT basis is R of the N1curl basis, with the interior pairs (q, 0), (q, 1) swapped and the
+    second negated."""
+    pts = np.random.default_rng(order).dirichlet(np.ones(3), size=10)[:, 1:]
+    vc = elements.reference_element("hcurl", 2, order).evaluate(pts)
+    vd = elements.reference_element("hdiv", 2, order).evaluate(pts)
+    rot = np.stack([vc[:, :, 1], -vc[:, :, 0]], axis=2)           # R applied to every N1curl function
+    k = order
+    expect = rot.copy()
+    for r in range((k - 1) * k // 2):
+        i0, i1 = 3 * k + 2 * r, 3 * k + 2 * r + 1
+        expect[:, i0], expect[:, i1] = rot[:, i1], -rot[:, i0]
+    np.testing.assert_allclose(vd, expect, atol=1e-12)

@@ -53,6 +53,8 @@ ITS_MESHES = {
     "h1_3d_p2": (lambda: mg.unit_cube_mesh(12), "h1", 2),
     "hcurl_3d_k1": (lambda: mg.unit_cube_mesh(14), "hcurl", 1),
     "hdiv_3d_k1": (lambda: mg.unit_cube_mesh(16), "hdiv", 1),
+    "hcurl_2d_k1": (lambda: mg.unit_square_mesh(160), "hcurl", 1),
+    "hdiv_2d_k1": (lambda: mg.unit_square_mesh(160), "hdiv", 1),
     "h1b_2d_p2": (lambda: mg.unit_square_mesh(96), "h1b", 2),
     "h1b_2d_p3": (lambda: mg.unit_square_mesh(64), "h1b", 3),
     "h1b_2d_p4": (lambda: mg.unit_square_mesh(48), "h1b", 4),
