@@ -20,13 +20,13 @@
  *    bras_pcg_solve synchronise the stream before they return.
  *  * Vectors with nrhs > 1 right-hand sides are RHS-interleaved: entry (i, r) is at
  *    i * nrhs + r.  Dof i is the global dof number used in `l2g`.
- *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange P_p on triangles (dim 2) or tetrahedra
- *    (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind of order k = 1..3 and BRAS_HDIV =
- *    Raviart-Thomas of order k = 1..3, on tetrahedra, mapped by the covariant /
- *    contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with |det J|.
- *    Local dof order and dof functionals are the ones documented with the mesh
- *    generator and the reference elements (vertices of each cell listed in ascending
- *    global id for face moments of order >= 2).
+ *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.h1_basis) P_p
+ *    on triangles (dim 2) or tetrahedra (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind
+ *    and BRAS_HDIV = Raviart-Thomas, order k = 1..3, on triangles or tetrahedra, mapped by
+ *    the covariant / contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with
+ *    |det J|.  Local dof order and dof functionals are the ones documented with the mesh
+ *    generator and the reference elements (vertices of each tetrahedron listed in
+ *    ascending global id for face moments of order >= 2).
  *  * Return codes: 0 = success, > 0 = non-fatal status, < 0 = error (nothing written
  *    to the outputs except where stated).  No call prints, throws or exits.
  *    bras_status_string() names a code; bras_last_error_detail() gives the element or
@@ -110,7 +110,7 @@ typedef struct {
  * deterministic scatter tables.  Not timed in solves (Sec. 3).
  *
  *   out      receives the new context (set to NULL on error).
- *   dim      2 or 3 (2 only with BRAS_H1).
+ *   dim      2 (triangles) or 3 (tetrahedra).
  *   space    BRAS_H1, BRAS_HCURL or BRAS_HDIV;  order p or k (see above).
  *   coords   [n_vert * dim] double, vertex coordinates.
  *   cells    [n_cell * (dim+1)] int32, vertex ids of each simplex.

@@ -525,7 +525,7 @@ int bras_setup(bras_ctx** out, int dim, int space, int order, int64_t n_vert, co
     set_detail(-1);
     if (!out) return BRAS_ERR_INVALID;
     *out = nullptr;
-    if ((dim != 2 && dim != 3) || space < 0 || space > 2 || (space != BRAS_H1 && dim != 3)) return BRAS_ERR_INVALID;
+    if ((dim != 2 && dim != 3) || space < 0 || space > 2) return BRAS_ERR_INVALID;
     const int nloc = n_local(dim, space, order);
     if (nloc < 0) return BRAS_ERR_INVALID;
     if (!coords || !cells || !l2g || n_vert <= dim || n_cell <= 0 || n_dof <= 0) return BRAS_ERR_INVALID;
@@ -584,8 +584,7 @@ int bras_setup_batched(bras_ctx** out, int dim, int space, int order, int n_mesh
     set_detail(-1);
     if (!out) return BRAS_ERR_INVALID;
     *out = nullptr;
-    if (!meshes || n_mesh < 1 || (dim != 2 && dim != 3) || space < 0 || space > 2 || (space != BRAS_H1 && dim != 3))
-        return BRAS_ERR_INVALID;
+    if (!meshes || n_mesh < 1 || (dim != 2 && dim != 3) || space < 0 || space > 2) return BRAS_ERR_INVALID;
     const int nloc = n_local(dim, space, order);
     if (nloc < 0) return BRAS_ERR_INVALID;
     int64_t V = 0, E = 0, N = 0;

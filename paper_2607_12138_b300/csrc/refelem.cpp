@@ -387,6 +387,105 @@ int build_vector(bool curl, int k, RefTables* out) {
     return 0;
 }
 
+// ---- vector elements on triangles ----------------------------------------------------------
+// N1curl_k: the geometric basis lambda^alpha (lambda_a grad lambda_b - lambda_b grad lambda_a),
+// alpha of size k - 1 with alpha_m = 0 below the first vertex a of the edge; RT_k: the same
+// functions rotated by R v = (v_y, -v_x).  Dofs: edge moments of v . t (N1curl) or v . R t (RT)
+// against L_j, j < k, t = v_b - v_a; interior moments of the two components against the
+// mean-orthonormal polynomials of degree <= k - 2 (q outer, component inner).  Tables are in the
+// three-component layout of the tetrahedral families with a zero third component.
+struct Span2 {
+    std::array<int, 3> alpha;
+    int a, b;
+};
+
+Vec3 eval_span2(bool curl, const Span2& f, const double* x) {
+    double lam[3];
+    bary(2, x, lam);
+    double pw = 1;
+    for (int i = 0; i < 3; ++i)
+        for (int m = 0; m < f.alpha[i]; ++m) pw *= lam[i];
+    const double g[3][2] = {{-1, -1}, {1, 0}, {0, 1}};
+    const double w0 = lam[f.a] * g[f.b][0] - lam[f.b] * g[f.a][0];
+    const double w1 = lam[f.a] * g[f.b][1] - lam[f.b] * g[f.a][1];
+    if (curl) return {w0 * pw, w1 * pw, 0.0};
+    return {w1 * pw, -w0 * pw, 0.0};
+}
+
+int build_vector_2d(bool curl, int k, RefTables* out) {
+    const int kE[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    const double kV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+    std::vector<Span2> span;
+    std::vector<std::vector<int>> al;
+    compositions(3, k - 1, al);
+    for (auto& e : kE)
+        for (auto& m : al) {
+            bool ok = true;
+            for (int i = 0; i < e[0]; ++i) ok &= (m[i] == 0);
+            if (ok) span.push_back({{m[0], m[1], m[2]}, e[0], e[1]});
+        }
+    const int n = (int)span.size();
+    if (n != k * (k + 2)) return -1;
+    const auto seg = segment_rule();
+    const auto tri = triangle_rule();
+    std::vector<long double> A;
+    A.reserve((size_t)n * n);
+    for (auto& e : kE) {
+        const double t[2] = {kV[e[1]][0] - kV[e[0]][0], kV[e[1]][1] - kV[e[0]][1]};
+        const double d[2] = {curl ? t[0] : t[1], curl ? t[1] : -t[0]};
+        for (int jm = 0; jm < k; ++jm)
+            for (int j = 0; j < n; ++j) {
+                double acc = 0;
+                for (const QP& q : seg) {
+                    const double x[3] = {kV[e[0]][0] + q.x[0] * t[0], kV[e[0]][1] + q.x[0] * t[1], 0};
+                    const Vec3 v = eval_span2(curl, span[j], x);
+                    acc += q.w * (v[0] * d[0] + v[1] * d[1]) * shifted_legendre(jm, q.x[0]);
+                }
+                A.push_back(acc);
+            }
+    }
+    if (k >= 2) {
+        auto iq = orthonormal_values(tri, 0.5, triangle_monos(k - 2));
+        for (size_t r = 0; r < iq.size(); ++r)
+            for (int comp = 0; comp < 2; ++comp)
+                for (int j = 0; j < n; ++j) {
+                    double acc = 0;
+                    for (size_t qi = 0; qi < tri.size(); ++qi)
+                        acc += tri[qi].w * eval_span2(curl, span[j], tri[qi].x)[comp] * iq[r][qi];
+                    A.push_back(acc);
+                }
+    }
+    if ((int)A.size() != n * n) return -2;
+    std::vector<long double> C;
+    if (!lu_inverse(A, n, C)) return -3;
+    out->nloc = n;
+    out->ncomp = 3;
+    out->R.assign((size_t)9 * n * n, 0.0);
+    std::vector<double> sv((size_t)n * 2), ph((size_t)n * 2);
+    for (const QP& q : tri) {
+        for (int j = 0; j < n; ++j) {
+            const Vec3 v = eval_span2(curl, span[j], q.x);
+            sv[(size_t)j * 2] = v[0];
+            sv[(size_t)j * 2 + 1] = v[1];
+        }
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 2; ++c) {
+                long double acc = 0;
+                for (int j = 0; j < n; ++j) acc += (long double)sv[(size_t)j * 2 + c] * C[(size_t)j * n + i];
+                ph[(size_t)i * 2 + c] = (double)acc;
+            }
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double* R = &out->R[(size_t)(a * 3 + b) * n * n];
+                for (int i = 0; i < n; ++i) {
+                    const double wa = q.w * ph[(size_t)i * 2 + a];
+                    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] += wa * ph[(size_t)j * 2 + b];
+                }
+            }
+    }
+    return 0;
+}
+
 }  // namespace
 
 int n_local(int dim, int space, int order) {
@@ -395,7 +494,9 @@ int n_local(int dim, int space, int order) {
         if (dim == 3 && order >= 1 && order <= 4) return (order + 1) * (order + 2) * (order + 3) / 6;
         return -1;
     }
-    if (dim != 3 || order < 1 || order > 3) return -1;
+    if (order < 1 || order > 3) return -1;
+    if (dim == 2 && (space == 1 || space == 2)) return order * (order + 2);
+    if (dim != 3) return -1;
     if (space == 1) return order * (order + 2) * (order + 3) / 2;
     if (space == 2) return order * (order + 1) * (order + 3) / 2;
     return -1;
@@ -437,6 +538,7 @@ int build_reference(int dim, int space, int order, RefTables* out, int h1_basis)
     out->space = space;
     out->order = order;
     if (space == 0) return h1_basis == 1 ? build_bernstein(dim, order, out) : build_lagrange(dim, order, out);
+    if (dim == 2) return build_vector_2d(space == 1, order, out);
     return build_vector(space == 1, order, out);
 }
 

@@ -30,6 +30,9 @@ SMALL_CASES = {
     "hdiv1_signed": (lambda: mg.relabel_mesh(cube(5), seed=8), "hdiv", 1),
     "hdiv2": (lambda: cube(4), "hdiv", 2),
     "hdiv3": (lambda: cube(4), "hdiv", 3),
+    "hcurl2d_1_signed": (lambda: mg.relabel_mesh(square(16), seed=11), "hcurl", 1),   # triangles
+    "hdiv2d_2_signed": (lambda: mg.relabel_mesh(square(12), seed=12), "hdiv", 2),
+    "hcurl2d_3": (lambda: square(12), "hcurl", 3),
     "2d_p4_bern": (lambda: square(13), "h1b", 4),        # Bernstein basis (Table 1)
     "3d_p3_bern": (lambda: cube(5), "h1b", 3),
     "3d_p4_bern": (lambda: cube(5), "h1b", 4),

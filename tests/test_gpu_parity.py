@@ -120,7 +120,7 @@ def test_small_blocks_and_single_cell(block_elems):
 
 @pytest.mark.parametrize("case,pc", [("c1_2d_p2", 2),
                                      ("c1_2d_p2", 1), ("3d_p2", 2), ("hcurl2", 2), ("hdiv2", 2), ("hcurl1_signed", 1),
-                                     ("3d_p3_bern", 2), ("3d_p3_bern", 1)])
+                                     ("3d_p3_bern", 2), ("3d_p3_bern", 1), ("hcurl2d_3", 2), ("hdiv2d_2_signed", 1)])
 def test_pcg_fp64_iterations_and_residual(case, pc):
     mesh, pr, ctx = _setup(case)
     b, bt = _vec(pr.n_dof, seed=1)
