@@ -9,6 +9,9 @@
   (Sec. 3).
 * ``chebyshev``: Chebyshev semi-iteration on a spectral interval [lmin, lmax] of
   Mt^{-1} M (Sec. 3: linear, no inner products in the update).
+* ``cg_lanczos``: the extreme eigenvalues of the Lanczos tridiagonal matrix that preconditioned
+  CG builds implicitly from its coefficients -- estimates of lambda_min, lambda_max of
+  Mt^{-1} M and so of kappa_hat (Eq. spectral-kappa) on meshes too large for a dense solve.
 * ``kappa_hat``: spectral condition number lambda_max / lambda_min of the pencil
   (M, Mt) (Eq. spectral-kappa), from eigenvalues of L^T X L where M = L L^T and
   X = Mt^{-1} (similar to X M).
@@ -19,10 +22,13 @@ import numpy as np
 import scipy.linalg as sla
 
 
-def pcg(A, b, precond=None, rtol: float = 1e-10, maxit: int = 5000, max_its: int | None = None):
+def pcg(A, b, precond=None, rtol: float = 1e-10, maxit: int = 5000, max_its: int | None = None,
+        coeffs: list | None = None):
     """Returns (x, iterations, history of ||r_k||/||r_0||).
 
     ``max_its`` (if given) runs exactly that many iterations with no stopping test.
+    ``coeffs`` (if a list) receives (alpha_k, beta_k) per iteration, beta_k the coefficient of
+    p_k = z_k + beta_k p_{k-1} (beta_0 = 0).
     """
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b)
@@ -34,11 +40,14 @@ def pcg(A, b, precond=None, rtol: float = 1e-10, maxit: int = 5000, max_its: int
     hist = [1.0]
     its = 0
     limit = max_its if max_its is not None else maxit
+    beta = 0.0
     while its < limit:
         if max_its is None and hist[-1] <= rtol:
             break
         q = A(p)
         alpha = rz / float(p @ q)
+        if coeffs is not None:
+            coeffs.append((alpha, beta))
         x += alpha * p
         r -= alpha * q
         its += 1
@@ -47,9 +56,32 @@ def pcg(A, b, precond=None, rtol: float = 1e-10, maxit: int = 5000, max_its: int
             break
         z = precond(r) if precond is not None else r.copy()
         rz_new = float(r @ z)
-        p = z + (rz_new / rz) * p
+        beta = rz_new / rz
+        p = z + beta * p
         rz = rz_new
     return x, its, np.array(hist)
+
+
+def lanczos_tridiagonal(coeffs) -> np.ndarray:
+    """T_k of the Lanczos process that CG on the preconditioned operator performs implicitly:
+    T[j, j] = 1/alpha_j + beta_j/alpha_{j-1} (second term from j = 1), T[j, j+1] = T[j+1, j]
+    = sqrt(beta_{j+1})/alpha_j."""
+    k = len(coeffs)
+    T = np.zeros((k, k))
+    for j, (a, bta) in enumerate(coeffs):
+        T[j, j] = 1.0 / a + (bta / coeffs[j - 1][0] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(coeffs[j + 1][1]) / a
+    return T
+
+
+def cg_lanczos(A, b, precond, steps: int):
+    """(lambda_min, lambda_max, steps taken) of T_k after ``steps`` CG iterations (fewer if the
+    residual vanishes); the Ritz values bracket-in towards the spectrum's ends."""
+    coeffs: list = []
+    pcg(A, b, precond, rtol=0.0, max_its=steps, coeffs=coeffs)
+    ev = np.linalg.eigvalsh(lanczos_tridiagonal(coeffs))
+    return float(ev[0]), float(ev[-1]), len(coeffs)
 
 
 def fixed_point(A, b, precond, omega: float, rtol: float = 1e-10, maxit: int = 5000, max_its: int | None = None):

@@ -8,6 +8,8 @@
   counts against the fixed-point columns of Tables 1-3 (omega from the power iteration, as in
   Sec. 3), and its error against the closed form (I - omega Mt^{-1} M)^k e_0;
 * the power iteration against the dense pencil eigensolve (and the Rayleigh lower bound);
+* CG-Lanczos extreme Ritz values: inside the spectrum at every step (interlacing), converging
+  to the dense pencil extremes, and kappa_hat of Table 1 on a uniform mesh;
 * the Chebyshev semi-iteration against its closed form T_k((theta - T)/delta)/T_k(sigma) e_0
   (eigendecomposition of the pencil), its error bound 1/T_k(sigma), and the observation of
   Sec. 3 that it converges like CG;
@@ -24,7 +26,7 @@ import scipy.sparse.linalg as spla
 
 from oracle import gradient, sampled
 from oracle.assembly import Problem, element_matrices
-from oracle.solvers import chebyshev, fixed_point, kappa_hat, pcg, pencil_eigs, power_lambda_max
+from oracle.solvers import cg_lanczos, chebyshev, fixed_point, kappa_hat, pcg, pencil_eigs, power_lambda_max
 from paper_2607_12138_b300 import meshgen as mg
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
@@ -204,3 +206,29 @@ def test_chebyshev_error_closed_form_and_bound():
         assert np.abs((u - xs) - ek).max() <= 1e-10 * np.abs(xs).max()
         e = u - xs
         assert np.sqrt(e @ M @ e) <= np.sqrt(e0 @ M @ e0) / Tk(theta / delta) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("space,order", [("h1", 2), ("hcurl", 2), ("hdiv", 1)])
+def test_cg_lanczos_against_dense(space, order):
+    mesh = mg.unit_square_mesh(8, jitter=0.2) if space == "h1" else mg.unit_cube_mesh(3)
+    pr = _problem(mesh, space, order)
+    M, X = pr.M.toarray(), pr.B.toarray()
+    ev = pencil_eigs(M, X)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    prev_lo, prev_hi = np.inf, 0.0
+    for steps in (5, 15, 40, 120):
+        lo, hi, k = cg_lanczos(pr.mass_apply, b, pr.bras_apply, steps)
+        assert ev[0] * (1 - 1e-12) <= lo <= prev_lo * (1 + 1e-12)      # Ritz values move outwards,
+        assert prev_hi * (1 - 1e-12) <= hi <= ev[-1] * (1 + 1e-12)     # staying inside the spectrum
+        prev_lo, prev_hi = lo, hi
+    assert abs(hi - ev[-1]) <= 1e-10 * ev[-1] and abs(lo - ev[0]) <= 1e-4 * ev[0]
+
+
+def test_cg_lanczos_kappa_matches_paper():
+    """Table 1, three dimensions, p = 2 (uniform 8^3 x 6 mesh, 4,913 dofs): 17 / 3.0."""
+    pr = _problem(mg.unit_cube_mesh(8), "h1", 2)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    for pre, printed in ((pr.jacobi_apply, GOLD["kappa_hat"]["h1_3d_p2"]["diag"]),
+                         (pr.bras_apply, GOLD["kappa_hat"]["h1_3d_p2"]["bras"])):
+        lo, hi, _ = cg_lanczos(pr.mass_apply, b, pre, 150)
+        assert abs(hi / lo - printed) <= 0.5 * 10 ** (np.floor(np.log10(printed)) - 1) + 0.02 * printed
