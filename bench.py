@@ -409,6 +409,40 @@ def run_ours(a):
             del cb, bt, xb
         compare["batched_hdiv"] = batch
 
+    # kappa_hat = lambda_max / lambda_min of Mt^{-1} M by CG-Lanczos (FP64) on ~1e6-dof meshes:
+    # uniform meshes beside the values the paper prints (Tables 1-3, diagonal / BRAS, ~5e3 dofs;
+    # kappa_hat of a mass matrix barely depends on the mesh size), and the jittered bench mesh
+    if not a.no_compare:
+        kap = {}
+        def lanczos_pair(ctx, n):
+            b0 = torch.as_tensor(mg.rhs(n, 1, seed=1), device="cuda")
+            out = {}
+            for name, pc, steps in (("diag", B.PC_JACOBI, 400), ("bras", B.PC_BRAS, 150)):
+                lo, hi, k = ctx.cg_lanczos(b0, pc, steps=steps)
+                out[name] = {"kappa": hi / lo, "lambda_min": lo, "lambda_max": hi, "steps": k}
+            return out
+        cases = (("h1_3d_p1", "h1", 1, 96, (5.0, 1.8), "Table 1, 3D, p=1, Lagrange"),
+                 ("h1_3d_p2", "h1", 2, 48, (17, 3.0), "Table 1, 3D, p=2, Lagrange"),
+                 ("h1b_3d_p2", "h1b", 2, 48, (24, 4.9), "Table 1, 3D, p=2, Bernstein"),
+                 ("h1b_3d_p3", "h1b", 3, 32, (98, 7.8), "Table 1, 3D, p=3, Bernstein"),
+                 ("h1b_3d_p4", "h1b", 4, 24, (420, 11), "Table 1, 3D, p=4, Bernstein"),
+                 ("hcurl_3d_k1", "hcurl", 1, 56, (6.0, 1.8), "Table 2, 3D, p=1, N1curl"),
+                 ("hdiv_3d_k1", "hdiv", 1, 64, (4.0, 1.6), "Table 3, 3D, p=1, RT"))
+        for key, space, order, cells, printed, where in cases:
+            mu = mg.unit_cube_mesh(cells, jitter=0.0, seed=0)
+            nk, lk, sk = mg.dof_map(mu, space, order)
+            cu = B.Context(mu.coords, mu.cells, space, order, nk, lk, sk)
+            row = lanczos_pair(cu, nk)
+            row.update({"mesh": f"uniform {cells}^3x6", "dofs": nk, "paper": {"diag": printed[0], "bras": printed[1]},
+                        "paper_where": where})
+            kap[key] = row
+            del cu
+        for pr in probs:
+            row = lanczos_pair(pr["ctx"], pr["n"])
+            row.update({"mesh": "jittered 48^3x6 (bench workload)", "dofs": pr["n"]})
+            kap[f"h1_bench_p{pr['p']}"] = row
+        compare["kappa_cg_lanczos"] = kap
+
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

@@ -254,6 +254,25 @@ int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const 
                          double* x, int nrhs, double rtol, int maxit, int* iters, double* relres,
                          void* stream);
 
+/*
+ * bras_cg_lanczos -- estimates of lambda_min and lambda_max of Mt^{-1} M (Mt = diag(M) for
+ * BRAS_PC_JACOBI, BRAS for BRAS_PC_BRAS, Mt = I for BRAS_PC_NONE), whose ratio is the spectral
+ * condition number kappa_hat of Eq. spectral-kappa, on meshes too large for a dense
+ * eigensolve: `steps` FP64 PCG iterations on M x = b (u_0 = 0, no stopping test) record their
+ * coefficients alpha_k, beta_k, which define the tridiagonal matrix of the Lanczos process on
+ * Mt^{-1} M (T[j][j] = 1/alpha_j + beta_j/alpha_{j-1}, T[j][j+1] = sqrt(beta_{j+1})/alpha_j);
+ * its extreme eigenvalues (bisection on Sturm sequences) approach the extreme eigenvalues of
+ * Mt^{-1} M from inside, lambda_max quickly, lambda_min more slowly.
+ *   b          [n_dof] double, host or device, a start vector with components along the whole
+ *              spectrum (e.g. N(0, 1) entries); one right-hand side; not on a batched context.
+ *   steps      >= 1 iterations (fewer once ||r|| <= 1e-14 ||b||: beyond that the coefficients
+ *              carry only rounding).
+ *   lambda_min, lambda_max  host doubles (output); steps_done host int (output) or NULL.
+ * Returns BRAS_OK, BRAS_ERR_BREAKDOWN, or an error.  Synchronises `stream`.
+ */
+int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, double* lambda_min,
+                    double* lambda_max, int* steps_done, void* stream);
+
 /* bras_grad_rho -- rho_bar_K = -lambda_K^T M_K^1 x_K for the weighted mass M(rho) =
  * sum_K rho_K P_K^T M_K^1 P_K (M_K^1 = unit-density element matrix): the element part of
  * the adjoint gradient of x = M(rho)^{-1} b, with lambda = M^{-1} xbar (H1 only).

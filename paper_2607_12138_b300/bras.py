@@ -65,6 +65,8 @@ _lib.bras_fixed_point_solve.argtypes = [_vp, _int, _vp, _vp, _vp, _int, _dbl, _i
 _lib.bras_fixed_point_solve.restype = _int
 _lib.bras_chebyshev_solve.argtypes = [_vp, _int, _vp, _vp, _vp, _vp, _int, _dbl, _int, _vp, _vp, _vp]
 _lib.bras_chebyshev_solve.restype = _int
+_lib.bras_cg_lanczos.argtypes = [_vp, _int, _vp, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_int), _vp]
+_lib.bras_cg_lanczos.restype = _int
 _lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.bras_grad_rho.restype = _int
 _lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
@@ -203,6 +205,14 @@ def bras_chebyshev_solve(ctx, pc, lmin, lmax, b, x, nrhs, rtol, maxit, iters, re
     return _check(rc, "bras_chebyshev_solve")
 
 
+def bras_cg_lanczos(ctx, pc, b, steps, stream=None):
+    """(lambda_min, lambda_max, steps done) of Mt^{-1} M from CG-Lanczos."""
+    lo, hi, k = _dbl(), _dbl(), _int()
+    _check(_lib.bras_cg_lanczos(ctx, pc, _ptr(b), steps, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(k),
+                                _stream(stream)), "bras_cg_lanczos")
+    return lo.value, hi.value, k.value
+
+
 def bras_grad_rho(ctx, x, lam, rho_bar, stream=None):
     return _check(_lib.bras_grad_rho(ctx, _ptr(x), _ptr(lam), _ptr(rho_bar), _stream(stream)), "bras_grad_rho")
 
@@ -334,6 +344,10 @@ class Context:
         lam = np.zeros(max(nrhs, getattr(self, "n_mesh", 1)), dtype=np.float64)
         bras_lambda_max(self.ctx, pc, v0, nrhs, iters, lam, stream)
         return lam
+
+    def cg_lanczos(self, b, pc=PC_BRAS, steps=100, stream=None):
+        """(lambda_min, lambda_max, steps done) estimates of Mt^{-1} M; kappa_hat = ratio."""
+        return bras_cg_lanczos(self.ctx, pc, b, steps, stream)
 
     def fixed_point_solve(self, b, omega, pc=PC_BRAS, rtol=1e-10, maxit=5000, out=None, stream=None):
         """Damped fixed point; omega scalar or per rhs.  Returns (x, iters, relres, status)."""

@@ -703,6 +703,14 @@ int bras_lambda_max(const bras_ctx* ctx, int pc, const double* v0, int nrhs, int
     return lambda_max_impl(const_cast<bras_ctx*>(ctx), pc, v0, nrhs, iters, lambda, static_cast<cudaStream_t>(stream));
 }
 
+int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, double* lambda_min, double* lambda_max,
+                    int* steps_done, void* stream) {
+    set_detail(-1);
+    if (!ctx || !b || !lambda_min || !lambda_max || steps < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
+    return cg_lanczos_impl(const_cast<bras_ctx*>(ctx), pc, b, steps, lambda_min, lambda_max, steps_done,
+                           static_cast<cudaStream_t>(stream));
+}
+
 int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, const double* b, double* x, int nrhs,
                            double rtol, int maxit, int* iters, double* relres, void* stream) {
     set_detail(-1);

@@ -24,6 +24,8 @@ int stationary_solve_impl(bras_ctx* c, int solver, int pc, const double* step, c
                           const double* b, double* x, int nrhs, double rtol, int maxit, int* iters, double* relres,
                           cudaStream_t st);
 int lambda_max_impl(bras_ctx* c, int pc, const double* v0, int nrhs, int iters, double* lambda, cudaStream_t st);
+int cg_lanczos_impl(bras_ctx* c, int pc, const double* b, int steps, double* lmin, double* lmax, int* done,
+                    cudaStream_t st);
 
 cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* lam, double* rho_bar, cudaStream_t st);
 cudaError_t update_rho_launch(bras_ctx* c, const double* rho, cudaStream_t st);

@@ -53,6 +53,8 @@ struct PcgWork {
     double* h_sc = nullptr;       // pinned
     double* coef = nullptr;       // Chebyshev direction coefficients [2][kmax + 1][slots]
     int coef_k = 0;               // kmax of the allocation
+    double* hist = nullptr;       // CG-Lanczos: alpha_k, beta_k of rhs 0 ([2][hist_cap]); null otherwise
+    int hist_cap = 0;
 };
 
 void free_pcg(bras_ctx* c) {
@@ -135,6 +137,8 @@ struct FinArgs {
     int* iparam;                   // [0] = maxit, [1] = iterations done
     cudaGraphConditionalHandle cond;
     int in_graph;                  // the loop condition exists (solve graph)
+    double* hist;                  // if set: alpha_k -> hist[k], beta_k -> hist[cap + k] (slot 0)
+    int hist_cap;
 };
 
 __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
@@ -164,6 +168,7 @@ __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
                 }
             }
             sc[S_ALPHA * R + r] = a;
+            if (F.hist && r == 0 && active[r] && its[r] < F.hist_cap) F.hist[its[r]] = a;
             break;
         }
         case FIN_RR:
@@ -178,6 +183,7 @@ __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
             if (active[r]) {
                 bta = its[r] == 0 ? 0.0 : s / sc[S_RZ * R + r];
                 sc[S_RZ * R + r] = s;
+                if (F.hist && r == 0 && its[r] < F.hist_cap) F.hist[F.hist_cap + its[r]] = bta;
             }
             sc[S_BETA * R + r] = bta;
             break;
@@ -540,6 +546,8 @@ static FinArgs fin_args(PcgWork* w, int kind, int* iparam = nullptr, cudaGraphCo
                         bool in_graph = false) {
     FinArgs F;
     F.in_graph = in_graph ? 1 : 0;
+    F.hist = w->hist;
+    F.hist_cap = w->hist_cap;
     F.kind = kind;
     F.partial = w->partial;
     F.ticket = w->ticket;
@@ -1002,6 +1010,89 @@ int stationary_solve_impl(bras_ctx* c, int solver, int pc, const double* step, c
     }
     if (w->h_flags[2 * S + 1] != 0) return w->h_flags[2 * S + 1];
     return w->h_flags[2 * S] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm sequence of the
+// LDL^T pivots).
+static int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+        q = d[i] - x - (i ? off / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// CG-Lanczos: `steps` FP64 PCG iterations on M x = b record alpha_k, beta_k; the tridiagonal
+// T[j][j] = 1/alpha_j + beta_j/alpha_{j-1}, T[j][j+1] = sqrt(beta_{j+1})/alpha_j of the Lanczos
+// process on Mt^{-1} M has extreme eigenvalues (found by bisection) that approach
+// lambda_min, lambda_max of Mt^{-1} M from inside.
+int cg_lanczos_impl(bras_ctx* c, int pc, const double* b, int steps, double* lmin, double* lmax, int* done,
+                    cudaStream_t st) {
+    if (batched(c)) return BRAS_ERR_INVALID;
+    RC(ensure_pcg(c, 1, false));
+    RC(ensure_part(c, 1));
+    PcgWork* w = c->pcg;
+    const int64_t n = c->n;
+    double* hist = (double*)dalloc_bytes(c, sizeof(double) * 2 * (size_t)steps);
+    if (!hist) return BRAS_ERR_OOM;
+    CK(cudaMemsetAsync(hist, 0, sizeof(double) * 2 * (size_t)steps, st));
+    CK(cudaMemcpyAsync(w->r, b, sizeof(double) * n, host_ptr(b) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w->xs, 0, sizeof(double) * n, st));
+    CK(cudaMemsetAsync(w->p, 0, sizeof(double) * n, st));
+    w->h_param[0] = 1e-28;   // stop below 1e-14 ||b||: beyond it the coefficients carry only rounding
+    int* hp = reinterpret_cast<int*>(w->h_param + 1);
+    hp[0] = steps;
+    hp[1] = 0;
+    CK(cudaMemcpyAsync(w->dparam, w->h_param, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->iparam, hp, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w->flags + 3, 0, sizeof(int), st));
+    w->hist = hist;
+    w->hist_cap = steps;
+    int rc = BRAS_OK;
+    if (vdot(c, w->r, w->r, 1, FIN_INIT_RR, st) != cudaSuccess) rc = BRAS_ERR_CUDA;
+    for (int it = 0; it < steps && rc == BRAS_OK; ++it)
+        rc = enqueue_iteration<double>(c, BRAS_FP64, pc, w->xs, w->r, w->z, w->p, w->q, 1, 0, st, false);
+    w->hist = nullptr;     // solve graphs never see the history buffer
+    w->hist_cap = 0;
+    std::vector<double> h(2 * (size_t)steps);
+    if (rc == BRAS_OK &&
+        (cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaMemcpyAsync(h.data(), hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        rc = BRAS_ERR_CUDA;
+    dfree(c, hist);
+    if (rc != BRAS_OK) return rc;
+    if (w->h_flags[3] != 0) return w->h_flags[3];
+    const int k = std::min(steps, w->h_flags[1]);   // iterations done
+    if (done) *done = k;
+    if (k < 1) return BRAS_ERR_BREAKDOWN;
+    std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+    for (int j = 0; j < k; ++j) {
+        d[j] = 1.0 / h[j] + (j ? h[steps + j] / h[j - 1] : 0.0);
+        if (j + 1 < k) e[j] = std::sqrt(h[steps + j + 1]) / h[j];
+    }
+    double lo = d[0], hi = d[0];   // Gershgorin bracket
+    for (int j = 0; j < k; ++j) {
+        const double rad = (j ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < k ? std::fabs(e[j]) : 0.0);
+        lo = std::min(lo, d[j] - rad);
+        hi = std::max(hi, d[j] + rad);
+    }
+    auto bisect = [&](int index) {   // the eigenvalue with `index` eigenvalues below it
+        double a = lo, bb = hi;
+        for (int it = 0; it < 200 && bb - a > 1e-15 * std::max(std::fabs(a), std::fabs(bb)); ++it) {
+            const double m = 0.5 * (a + bb);
+            if (sturm_count(d, e, m) <= index) a = m;
+            else bb = m;
+        }
+        return 0.5 * (a + bb);
+    };
+    *lmin = bisect(0);
+    *lmax = bisect(k - 1);
+    return BRAS_OK;
 }
 
 // lambda_max of Mt^{-1} M by the power iteration (Sec. 3): w = M v; z = Mt^{-1} w;

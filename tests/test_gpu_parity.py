@@ -16,7 +16,7 @@ import torch
 from oracle import gradient as ograd
 from oracle import sampled
 from oracle.assembly import Problem, element_matrices
-from oracle.solvers import chebyshev, fixed_point, pcg, power_lambda_max
+from oracle.solvers import cg_lanczos, chebyshev, fixed_point, pcg, power_lambda_max
 from paper_2607_12138_b300 import meshgen as mg
 
 from _cases import SMALL_CASES, build, cube, rel_err
@@ -422,3 +422,18 @@ def test_autotuned_block_size(case):
     assert st == B.OK and abs(int(its[0]) - its_o) <= 1
     plain = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs)
     assert plain.block_tuning[1] == []
+
+
+@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "c1_2d_p2", "hdiv2d_2_signed", "3d_p4_bern"])
+def test_cg_lanczos_kappa(case):
+    """Extreme Ritz values of the CG-Lanczos tridiagonal: the GPU's (FP64 PCG coefficients,
+    bisection) against the oracle's (same start vector and step count, dense eigvalsh)."""
+    mesh, pr, ctx = _setup(case)
+    b, bt = _vec(pr.n_dof, 1, seed=1)
+    for pc, P in ((B.PC_BRAS, pr.bras_apply), (B.PC_JACOBI, pr.jacobi_apply)):
+        lo, hi, k = ctx.cg_lanczos(bt, pc, steps=15)
+        lo_o, hi_o, k_o = cg_lanczos(pr.mass_apply, b, P, 15)
+        assert k == k_o == 15
+        assert abs(lo - lo_o) <= 1e-8 * lo_o and abs(hi - hi_o) <= 1e-8 * hi_o
+    lo, hi, k = ctx.cg_lanczos(bt.cpu(), B.PC_BRAS, steps=400)    # host start vector; early stop
+    assert k < 400 and lo >= 1.0 - 1e-9                             # lambda_min >= 1 for BRAS
