@@ -1,0 +1,81 @@
+"""Pins of the oracle's mixed Poisson Schur complement (Sec. 4, Sec. 5.1):
+
+* the lowest-order divergence block in closed form: with chi = 1 and the RT_1 flux dofs
+  (normal t1 x t2 of each sorted face), int_K div phi_f = +-1, the sign saying whether t1 x t2
+  points out of the reference tetrahedron: (-1, +1, -1, +1) for faces 012, 013, 023, 123;
+* B annihilates the RT interpolant of a constant field (div of a constant is 0; the pullback
+  of c is det J J^{-1} c, and the
+  interpolant's face moments are c . (t1 x t2) / 2 for the lowest face polynomial, 0 for the
+  others);
+* on one cell BRAS = M^{-1}, so -S~ = -S;
+* the bound of Sec. 4: if the mass pencil's eigenvalues lie in [a, b] then those of
+  S~^{-1} S lie in [1/b, 1/a] (for BRAS, a >= 1, so S~^{-1} S <= 1).
+"""
+import numpy as np
+import pytest
+
+from oracle.assembly import Problem, jacobians
+from oracle.elements import FACES_3D
+from oracle.schur import divergence_matrix, n_dg, reference_divergence, schur_bras, schur_exact_dense
+from oracle.solvers import pencil_eigs
+from paper_2607_12138_b300 import meshgen as mg
+
+
+def _problem(mesh, k):
+    n, l2g, s = mg.dof_map(mesh, "hdiv", k)
+    return Problem(mesh, "hdiv", k, l2g, s, n), l2g, s, n
+
+
+def test_lowest_order_divergence_closed_form():
+    np.testing.assert_allclose(reference_divergence(1), [[-1.0, 1.0, -1.0, 1.0]], atol=1e-14)
+    for k in (2, 3):
+        assert reference_divergence(k).shape == (n_dg(k), k * (k + 1) * (k + 3) // 2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_divergence_annihilates_constant_fields(k):
+    mesh = mg.unit_cube_mesh(2, jitter=0.15)
+    pr, l2g, s, n = _problem(mesh, k)
+    B = divergence_matrix(mesh, l2g, s, n, k)
+    J = jacobians(mesh.coords, mesh.cells)
+    c = np.array([0.3, -1.1, 0.7])
+    nf = k * (k + 1) // 2                                  # face dofs per face
+    x = np.zeros(n)
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    for K in range(mesh.n_cell):
+        ch = np.linalg.det(J[K]) * np.linalg.solve(J[K], c)           # contravariant pullback of c
+        for f, (a, b, cc) in enumerate(FACES_3D):
+            nrm = np.cross(V[b] - V[a], V[cc] - V[a])
+            g = l2g[K, f * nf]
+            x[g] = s[K, f * nf] * (ch @ nrm) / 2.0        # q_0 = 1 on the face (area 1/2)
+        # interior moments: component integrals against q_r; only q_0 = 1 survives (volume 1/6)
+        if k >= 2:
+            ni = k * (k - 1) * (k + 1) // 2
+            base = 4 * nf
+            for comp in range(3):
+                x[l2g[K, base + comp]] = ch[comp] / 6.0
+            for r in range(3, ni):
+                x[l2g[K, base + r]] = 0.0
+    assert np.abs(B @ x).max() <= 1e-12 * np.abs(x).max()
+    assert np.abs(B @ np.random.default_rng(0).standard_normal(n)).max() > 1e-3   # not identically zero
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_one_cell_schur_is_exact(k):
+    mesh = mg.single_simplex_mesh(3, seed=5)
+    pr, l2g, s, n = _problem(mesh, k)
+    B = divergence_matrix(mesh, l2g, s, n, k)
+    np.testing.assert_allclose(schur_bras(B, pr.B).toarray(), schur_exact_dense(B, pr.M), rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("k,cells", [(1, 3), (2, 2), (3, 2)])
+def test_schur_spectrum_within_mass_bounds(k, cells):
+    mesh = mg.unit_cube_mesh(cells, jitter=0.15, seed=k)
+    pr, l2g, s, n = _problem(mesh, k)
+    B = divergence_matrix(mesh, l2g, s, n, k)
+    mass_ev = pencil_eigs(pr.M.toarray(), pr.B.toarray())
+    St = schur_bras(B, pr.B).toarray()
+    S = schur_exact_dense(B, pr.M)
+    ev = pencil_eigs(St, np.linalg.inv(S))               # eigenvalues of (-S)^{-1}(-S~) = 1 / those of S~^{-1} S
+    assert ev[0] >= mass_ev[0] * (1 - 1e-9) and ev[-1] <= mass_ev[-1] * (1 + 1e-9)
+    assert ev[0] >= 1 - 1e-9                             # S~^{-1} S <= 1 for BRAS
