@@ -443,6 +443,36 @@ def run_ours(a):
             kap[f"h1_bench_p{pr['p']}"] = row
         compare["kappa_cg_lanczos"] = kap
 
+    # mixed Poisson Schur complement apply -S~ x = B M_bras^{-1} B^T x (RT_k / DG_{k-1}, FP32) on
+    # 40^3 x 6 tets, beside the BRAS apply it contains
+    if not a.no_compare:
+        sch = {}
+        m40s = mg.unit_cube_mesh(40, jitter=JITTER, seed=0)
+        for k in (1, 2, 3):
+            nk, lk, sk = mg.dof_map(m40s, "hdiv", k)
+            cs = B.Context(m40s.coords, m40s.cells, "hdiv", k, nk, lk, sk, precisions=2)
+            nq = k * (k + 1) * (k + 2) // 6
+            xq = torch.as_tensor(mg.rhs(m40s.n_cell * nq, 1, seed=1), device="cuda").float()
+            yq = torch.empty_like(xq)
+            xb = torch.as_tensor(mg.rhs(nk, 1, seed=1), device="cuda").float()
+            yb = torch.empty_like(xb)
+            row = {"cells": m40s.n_cell, "rt_dofs": nk, "dg_dofs": m40s.n_cell * nq}
+            for name, fn in (("schur_apply_us", lambda: cs.schur_apply(xq, B.FP32, out=yq)),
+                             ("bras_apply_us", lambda: cs.bras_apply(xb, B.FP32, out=yb))):
+                for _ in range(3):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                for _ in range(10):
+                    fn()
+                e1.record(st)
+                torch.cuda.synchronize()
+                row[name] = e0.elapsed_time(e1) * 1e3 / 10
+            sch[f"rt{k}"] = row
+            del cs
+        compare["schur_mixed_poisson"] = sch
+
     # live per-kernel timings on the launching stream: FP32 BRAS / mass apply and FP64 mass apply
     kern = {}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

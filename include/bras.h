@@ -273,6 +273,24 @@ int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const 
 int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, double* lambda_min,
                     double* lambda_max, int* steps_done, void* stream);
 
+/*
+ * bras_schur_apply -- y = -S~ x = B M_bras^{-1} B^T x, the BRAS approximation of the positive
+ * Schur complement of the mixed Poisson saddle point [[M, B^T], [B, 0]] (Sec. 4,
+ * Eq. approx_positive_schur_general with C = 0; Sec. 5.1), matrix-free: the divergence and its
+ * transpose element by element, the BRAS apply in between.  Pair: RT_k (this context, H(div) on
+ * tetrahedra) with DG_{k-1}; B_ij = (div phi_j, chi_i), chi_i = chi^_i o F_K^{-1}, chi^_i the
+ * polynomials of degree <= k - 1 orthonormal for the mean inner product on the reference
+ * tetrahedron (Gram-Schmidt of the monomials by degree, then descending lexicographic
+ * exponents), so cell K's block is sign(det J_K) B^.  (The paper's experiments pair BDM with DG;
+ * the spectrum of S~^{-1} S does not depend on the DG basis.)
+ *   x, y   [n_cell * n_q] of double (BRAS_FP64) or float (BRAS_FP32 / BRAS_BF16), cell K's
+ *          n_q = k (k + 1) (k + 2) / 6 values at K * n_q, cells in the caller's order; one
+ *          right-hand side; not on a batched context.
+ * Returns BRAS_ERR_INVALID for other spaces.  The first call allocates its workspace
+ * (8 bytes x (n_cell n_loc + 2 n_dof)).
+ */
+int bras_schur_apply(const bras_ctx* ctx, int precision, const void* x, void* y, void* stream);
+
 /* bras_grad_rho -- rho_bar_K = -lambda_K^T M_K^1 x_K for the weighted mass M(rho) =
  * sum_K rho_K P_K^T M_K^1 P_K (M_K^1 = unit-density element matrix): the element part of
  * the adjoint gradient of x = M(rho)^{-1} b, with lambda = M^{-1} xbar (H1 only).

@@ -67,6 +67,8 @@ _lib.bras_chebyshev_solve.argtypes = [_vp, _int, _vp, _vp, _vp, _vp, _int, _dbl,
 _lib.bras_chebyshev_solve.restype = _int
 _lib.bras_cg_lanczos.argtypes = [_vp, _int, _vp, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_int), _vp]
 _lib.bras_cg_lanczos.restype = _int
+_lib.bras_schur_apply.argtypes = [_vp, _int, _vp, _vp, _vp]
+_lib.bras_schur_apply.restype = _int
 _lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.bras_grad_rho.restype = _int
 _lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
@@ -213,6 +215,10 @@ def bras_cg_lanczos(ctx, pc, b, steps, stream=None):
     return lo.value, hi.value, k.value
 
 
+def bras_schur_apply(ctx, precision, x, y, stream=None):
+    return _check(_lib.bras_schur_apply(ctx, precision, _ptr(x), _ptr(y), _stream(stream)), "bras_schur_apply")
+
+
 def bras_grad_rho(ctx, x, lam, rho_bar, stream=None):
     return _check(_lib.bras_grad_rho(ctx, _ptr(x), _ptr(lam), _ptr(rho_bar), _stream(stream)), "bras_grad_rho")
 
@@ -344,6 +350,12 @@ class Context:
         lam = np.zeros(max(nrhs, getattr(self, "n_mesh", 1)), dtype=np.float64)
         bras_lambda_max(self.ctx, pc, v0, nrhs, iters, lam, stream)
         return lam
+
+    def schur_apply(self, x, precision=FP64, out=None, stream=None):
+        """y = B M_bras^{-1} B^T x for RT_k / DG_{k-1} (x: n_cell * k(k+1)(k+2)/6 values)."""
+        y = out if out is not None else torch.empty_like(x)
+        bras_schur_apply(self.ctx, precision, x, y, stream)
+        return y
 
     def cg_lanczos(self, b, pc=PC_BRAS, steps=100, stream=None):
         """(lambda_min, lambda_max, steps done) estimates of Mt^{-1} M; kappa_hat = ratio."""

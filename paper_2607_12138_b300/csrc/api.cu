@@ -229,6 +229,37 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     RefTables ref;
     if (build_reference(dim, space, order, &ref, h1_basis) != 0) return BRAS_ERR_INVALID;
 
+    // mixed Poisson Schur complement tables (RT on tetrahedra): divergence block, the caller's
+    // l2g with P's signs times sign(det J_K), and the dof-sorted order of the broken copies
+    if (space == BRAS_HDIV && dim == 3 && ref.nq > 0) {
+        c->nq = ref.nq;
+        std::vector<float> b32(ref.Bdiv.begin(), ref.Bdiv.end());
+        if ((rc = upload(c, &c->Bdiv64, ref.Bdiv.data(), ref.Bdiv.size()))) return rc;
+        if ((rc = upload(c, &c->Bdiv32, b32.data(), b32.size()))) return rc;
+        std::vector<int8_t> sg((size_t)n_cell * nloc);
+        for (int64_t K = 0; K < n_cell; ++K) {
+            const double* x0 = &h_coords[(size_t)h_cells[K * 4] * 3];
+            double J[3][3];
+            for (int j = 0; j < 3; ++j)
+                for (int r = 0; r < 3; ++r) J[r][j] = h_coords[(size_t)h_cells[K * 4 + j + 1] * 3 + r] - x0[r];
+            const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            for (int a = 0; a < nloc; ++a)
+                sg[(size_t)K * nloc + a] = (int8_t)((signs ? h_signs[(size_t)K * nloc + a] : 1) * (det < 0 ? -1 : 1));
+        }
+        std::vector<int64_t> off((size_t)n_dof + 1, 0);
+        for (size_t i = 0; i < h_l2g.size(); ++i) off[(size_t)h_l2g[i] + 1]++;
+        for (int64_t i = 0; i < n_dof; ++i) off[i + 1] += off[i];
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        std::vector<int32_t> pos(h_l2g.size());
+        for (size_t i = 0; i < h_l2g.size(); ++i) pos[i] = (int32_t)fill[h_l2g[i]]++;
+        if ((rc = upload(c, &c->l2g_user, h_l2g.data(), h_l2g.size()))) return rc;
+        if ((rc = upload(c, &c->sgn_user, sg.data(), sg.size()))) return rc;
+        if ((rc = upload(c, &c->cpos, pos.data(), pos.size()))) return rc;
+        if ((rc = upload(c, &c->coff, off.data(), off.size()))) return rc;
+    }
+
     // device copies of the geometry inputs
     const double* d_coords = coords;
     const int32_t* d_cells = cells;
@@ -709,6 +740,15 @@ int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, dou
     if (!ctx || !b || !lambda_min || !lambda_max || steps < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
     return cg_lanczos_impl(const_cast<bras_ctx*>(ctx), pc, b, steps, lambda_min, lambda_max, steps_done,
                            static_cast<cudaStream_t>(stream));
+}
+
+int bras_schur_apply(const bras_ctx* ctx, int precision, const void* x, void* y, void* stream) {
+    set_detail(-1);
+    if (!ctx || !x || !y || (precision != BRAS_FP64 && precision != BRAS_FP32 && precision != BRAS_BF16))
+        return BRAS_ERR_INVALID;
+    if (ctx->nq == 0 || (ctx->n_mesh > 1 && ctx->nseg > 0)) return BRAS_ERR_INVALID;
+    if (!has_precision(ctx, precision)) return BRAS_ERR_PRECISION;
+    return schur_apply_impl(const_cast<bras_ctx*>(ctx), precision, x, y, static_cast<cudaStream_t>(stream));
 }
 
 int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, const double* b, double* x, int nrhs,

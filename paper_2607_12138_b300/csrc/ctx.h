@@ -91,6 +91,17 @@ struct bras_ctx {
     bool use_tc = false;
     unsigned char *btile_mass = nullptr, *btile_bras = nullptr;
 
+    // mixed Poisson Schur complement (RT_k / DG_{k-1} on tetrahedra), caller's cell order
+    int nq = 0;                  // DG_{k-1} dofs per cell
+    double* Bdiv64 = nullptr;    // [nq][nloc] reference divergence block
+    float* Bdiv32 = nullptr;
+    int32_t* l2g_user = nullptr; // [E][nloc]
+    int8_t* sgn_user = nullptr;  // [E][nloc] sign of P times sign(det J_K)
+    int32_t* cpos = nullptr;     // [E][nloc] slot of each copy in dof-sorted order (cell, local index ascending)
+    int64_t* coff = nullptr;     // [n + 1] first slot of each dof
+    void* schur_ws = nullptr;    // copies [E * nloc], then two dof vectors (8-byte entries)
+    size_t schur_ws_bytes = 0;
+
     // workspace
     void* part = nullptr;        // partial sums of shared dofs [npart * nrhs] (double)
     size_t part_bytes = 0;

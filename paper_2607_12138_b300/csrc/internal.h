@@ -27,6 +27,7 @@ int lambda_max_impl(bras_ctx* c, int pc, const double* v0, int nrhs, int iters, 
 int cg_lanczos_impl(bras_ctx* c, int pc, const double* b, int steps, double* lmin, double* lmax, int* done,
                     cudaStream_t st);
 
+int schur_apply_impl(bras_ctx* c, int prec, const void* x, void* y, cudaStream_t st);
 cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* lam, double* rho_bar, cudaStream_t st);
 cudaError_t update_rho_launch(bras_ctx* c, const double* rho, cudaStream_t st);
 

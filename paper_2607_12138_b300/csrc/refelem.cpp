@@ -384,6 +384,52 @@ int build_vector(bool curl, int k, RefTables* out) {
                 }
             }
     }
+    if (!curl) {
+        // divergence block of the mixed Poisson pair RT_k / DG_{k-1}: the span's divergence in
+        // closed form, div(lambda^alpha W_abc) = grad(lambda^alpha) . W_abc + 3 lambda^alpha
+        // grad lambda_a . (grad lambda_b x grad lambda_c), against the mean-orthonormal
+        // polynomials of degree <= k - 1, by the tetrahedral rule
+        const auto chi = orthonormal_values(tet, 1.0 / 6.0, tet_monos(k - 1));
+        const int nq = (int)chi.size();
+        out->nq = nq;
+        out->Bdiv.assign((size_t)nq * n, 0.0);
+        Vec3 g[4];
+        for (int i = 0; i < 4; ++i) {
+            double t[3];
+            bary_grad(i, t);
+            g[i] = {t[0], t[1], t[2]};
+        }
+        std::vector<double> dv(n);
+        for (size_t qi = 0; qi < tet.size(); ++qi) {
+            double lam[4];
+            bary(3, tet[qi].x, lam);
+            for (int j = 0; j < n; ++j) {
+                const SpanFn& f = span[j];
+                const int a = f.v[0], b = f.v[1], c = f.v[2];
+                double pw = 1;
+                for (int m = 0; m < 4; ++m)
+                    for (int e = 0; e < f.alpha[m]; ++e) pw *= lam[m];
+                Vec3 grad_pw{0, 0, 0};
+                for (int m = 0; m < 4; ++m) {
+                    if (f.alpha[m] == 0) continue;
+                    double t = f.alpha[m];
+                    for (int mm = 0; mm < 4; ++mm)
+                        for (int e = 0; e < f.alpha[mm] - (mm == m ? 1 : 0); ++e) t *= lam[mm];
+                    for (int d = 0; d < 3; ++d) grad_pw[d] += t * g[m][d];
+                }
+                Vec3 W{0, 0, 0};
+                const Vec3 bc = cross(g[b], g[c]), ac = cross(g[a], g[c]), ab = cross(g[a], g[b]);
+                for (int d = 0; d < 3; ++d) W[d] = lam[a] * bc[d] - lam[b] * ac[d] + lam[c] * ab[d];
+                const double divW = 3.0 * (g[a][0] * bc[0] + g[a][1] * bc[1] + g[a][2] * bc[2]);
+                dv[j] = grad_pw[0] * W[0] + grad_pw[1] * W[1] + grad_pw[2] * W[2] + pw * divW;
+            }
+            for (int jj = 0; jj < n; ++jj) {   // divergence of the nodal function jj
+                long double d = 0;
+                for (int j = 0; j < n; ++j) d += (long double)dv[j] * C[(size_t)j * n + jj];
+                for (int i = 0; i < nq; ++i) out->Bdiv[(size_t)i * n + jj] += tet[qi].w * (double)d * chi[i][qi];
+            }
+        }
+    }
     return 0;
 }
 

@@ -9,6 +9,10 @@ struct RefTables {
     int dim = 0, space = 0, order = 0, nloc = 0, ncomp = 0;
     // R[(a * ncomp + b) * nloc * nloc + i * nloc + j] = int_ref phi_i^a phi_j^b
     std::vector<double> R;
+    // RT_k on tetrahedra only: Bdiv[i * nloc + j] = int_ref div phi_j chi_i, chi_i the
+    // mean-orthonormal polynomials of degree <= k - 1 (nq of them; DG_{k-1})
+    int nq = 0;
+    std::vector<double> Bdiv;
 };
 
 int n_local(int dim, int space, int order);

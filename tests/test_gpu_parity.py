@@ -437,3 +437,24 @@ def test_cg_lanczos_kappa(case):
         assert abs(lo - lo_o) <= 1e-8 * lo_o and abs(hi - hi_o) <= 1e-8 * hi_o
     lo, hi, k = ctx.cg_lanczos(bt.cpu(), B.PC_BRAS, steps=400)    # host start vector; early stop
     assert k < 400 and lo >= 1.0 - 1e-9                             # lambda_min >= 1 for BRAS
+
+
+@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3"])
+def test_schur_complement_apply(case):
+    """-S~ x = B M_bras^{-1} B^T x (mixed Poisson, RT_k / DG_{k-1}) against the oracle's
+    assembled B and BRAS, in FP64 and FP32; other spaces are rejected."""
+    from oracle.schur import divergence_matrix, n_dg, schur_bras
+    mesh, pr, ctx = _setup(case)
+    k = SMALL_CASES[case][2]
+    n, l2g, signs = mg.dof_map(mesh, "hdiv", k)
+    St = schur_bras(divergence_matrix(mesh, l2g, signs, n, k), pr.B)
+    x = np.random.default_rng(7).standard_normal(mesh.n_cell * n_dg(k))
+    xt = torch.as_tensor(x, device="cuda")
+    ref = St @ x
+    assert rel_err(ctx.schur_apply(xt).cpu(), ref) <= 1e-12
+    assert rel_err(ctx.schur_apply(xt).cpu(), ctx.schur_apply(xt).cpu()) == 0.0
+    assert rel_err(ctx.schur_apply(xt.float(), B.FP32).cpu(), ref) <= 1e-4
+    _, pr2, c2 = _setup("hcurl2")
+    with pytest.raises(B.BrasError) as e:
+        c2.schur_apply(torch.zeros(10, dtype=torch.float64, device="cuda"))
+    assert e.value.code == -1
