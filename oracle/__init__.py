@@ -10,12 +10,17 @@ Modules
 -------
 ``polynomials``  dense monomial polynomials and exact simplex integrals.
 ``elements``     reference Lagrange / Nedelec (first kind) / Raviart-Thomas elements by
-                 monomial spans dualised against the documented dof functionals.
+                 monomial spans dualised against the documented dof functionals (tetrahedra,
+                 and N1curl / RT on triangles); the Bernstein basis (space "h1b") by
+                 multinomial expansion.
 ``assembly``     Piola metrics (Sec. 2.4, Eq. piola_mass_pullbacks), element matrices,
                  assembled M (Eq. M_PMbrP), multiplicity D, explicit BRAS
                  (Eq. mhatinvbras_def), Jacobi diag(M).
-``solvers``      textbook PCG with the paper's stopping rule (Sec. 3), damped
-                 fixed point, dense spectral tools (Eq. spectral-kappa).
+``solvers``      textbook PCG with the paper's stopping rule (Sec. 3), damped fixed point,
+                 Chebyshev semi-iteration, power iteration, CG-Lanczos, dense spectral tools
+                 (Eq. spectral-kappa).
+``schur``        mixed Poisson divergence matrix and Schur complements -S = B M^{-1} B^T,
+                 -S~ = B M_bras^{-1} B^T (Sec. 4, Sec. 5.1) for RT_k / DG_{k-1}.
 ``gradient``     adjoint gradient of the density-weighted mass solve.
 ``sampled``      one-dof-at-a-time BRAS / mass outputs for meshes too large to assemble.
 
@@ -25,5 +30,6 @@ The Lagrange elements of order 3-4 and the Nedelec / Raviart-Thomas elements of 
 2-3 use this project's documented node / moment convention, which differs from the
 paper's (GLL nodes, Firedrake moments): their kappa values are unpinned against the
 paper's tables, while the theorems (SPD, lambda_min >= 1, one-element exactness,
-Lemma bras_exact_inverse_correction, Theorem bras_lambda_max_projector) pin them.
+Lemma bras_exact_inverse_correction, Theorem bras_lambda_max_projector) pin them.  The
+Bernstein basis is canonical and is pinned to Table 1 at every order.
 """
