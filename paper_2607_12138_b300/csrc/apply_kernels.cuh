@@ -179,10 +179,11 @@ __device__ __forceinline__ void df_merge(float& ah, float& al, float bh, float b
     al = __fadd_rn(__fadd_rn(al, bl), err);
 }
 
-// Streamed FP32/bf16 cell matrices: ask for two resident blocks per SM (at most 128 registers a
-// thread), so that twice as many matrix loads are in flight.
-template <int KIND, typename T, int NLOC> struct MinBlocks {
-    static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4) ? 2 : 1;
+// Streamed FP32/bf16 cell matrices, one right-hand side: ask for two resident blocks per SM (at
+// most 128 registers a thread), so that twice as many matrix loads are in flight.  Multi-RHS CTAs
+// are shared-memory bound to one per SM and keep each item's local vector in registers.
+template <int KIND, typename T, int NLOC, bool MR = false> struct MinBlocks {
+    static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4 && !MR) ? 2 : 1;
 };
 
 // ---- multi-RHS row segments --------------------------------------------------------------
@@ -238,7 +239,7 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 // out [npart][nrhs].  The block's tables (and streamed cell matrices, re-read from L2) serve
 // every chunk.
 template <int NLOC, typename T, typename S, int KIND, int OP, bool MR = false>
-__global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC>::value))
+__global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC, MR>::value))
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs, int vec_ok) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
     constexpr int CW = MR ? Chunk<T>::CW : 1;
@@ -253,7 +254,6 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW]
     T* zs = xs + ((A.max_u * CW + 3) & ~3);                               // [slot][CW]
     T* Ms = zs + ((NLOC * A.max_ne * CW + 3) & ~3);                       // [NLOC][NPAD] (H1), 16-B aligned
-    T* xt_mr = Ms + (KIND == KIND_H1 ? NLOC * NPAD : 0);                  // [NLOC][blockDim] (MR, XS)
 
     const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
@@ -387,28 +387,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 const int e = MR ? it / CW : it;
                 const int rr = MR ? it % CW : 0;
                 const uint16_t* L = loc + e;
-                if constexpr (XS) {   // MR: the local vector in a private column of xt_mr
-                    T* xt = xt_mr + tid;
-                    const int ld = blockDim.x;
-                    uint64_t neg = 0;
-                    T zl[NLOC];
-#pragma unroll
-                    for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-#pragma unroll
-                    for (int a = 0; a < NLOC; ++a) {
-                        const uint16_t c = L[a * ne];
-                        const T v = xs[(c & 0x7fff) * CW + rr];
-                        const bool s = (c & 0x8000) != 0;
-                        neg |= (uint64_t)s << a;
-                        xt[a * ld] = s ? -v : v;
-                    }
-                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
-                        zl[a] = fma(m, xt[q * ld], zl[a]);
-                        if (q < a) zl[q] = fma(m, xt[a * ld], zl[q]);
-                    });
-#pragma unroll
-                    for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e] * CW + rr] = ((neg >> a) & 1) ? -zl[a] : zl[a];
-                } else {
+                {
                     uint64_t neg = 0;
                     T xl[NPAD];
 #pragma unroll
@@ -546,10 +525,9 @@ template <int NLOC, typename T, int KIND>
 size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
     const int cw = mr ? Chunk<T>::CW : 1;
-    const bool xs_mr = mr && KIND == KIND_PACKED && NLOC >= 36;
     return 128 + ((A.max_pkt + 127u) & ~127u) +
            sizeof(T) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) +
-                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0) + (xs_mr ? (size_t)NLOC * 256 : 0));
+                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
 }
 
 // Largest dynamic shared memory one CTA may opt into on the current device.
