@@ -209,7 +209,11 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
             tmp.max_ne = t.max_ne;
             s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
         }
-        const bool fits = s64 <= (size_t)smem_optin && (fixed_be || 2 * (s32 + 1024) <= (size_t)smem_sm);
+        // a context for several right-hand sides also wants its multi-RHS kernel (16-byte
+        // chunks of every dof's row) to fit one CTA
+        const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, want_tc, t.max_pkt, t.max_u, t.max_ne);
+        const bool fits = s64 <= (size_t)smem_optin &&
+                          (fixed_be || (2 * (s32 + 1024) <= (size_t)smem_sm && smr <= (size_t)smem_optin));
         if (fits || BE <= 32) {
             if (s64 > (size_t)smem_optin) return BRAS_ERR_TOO_LARGE;
             break;
@@ -398,6 +402,8 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
                 s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
             }
             if (s64 > (size_t)smem_optin || s32 > (size_t)smem_optin) continue;
+            const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, c->use_tc, tt.max_pkt, tt.max_u, tt.max_ne);
+            if (smr > (size_t)smem_optin && be > 32) continue;   // keep the multi-RHS kernel usable
             if ((rc = install_tables(c, tt)) || (rc = ensure_part(c, c->max_nrhs))) break;
             float ms = 0.f;
             bool okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;   // warm-up
@@ -440,11 +446,40 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
 
 }  // namespace
 
-size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int max_u, int max_ne) {
+size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int max_u, int max_ne, int cw) {
     const int w = tsize == 4 ? 4 : 2;
     const size_t npad = (size_t)((nloc + w - 1) / w * w);
     return 128 + ((max_pkt + 127u) & ~127u) +
-           (size_t)tsize * (((size_t)max_u + 3) / 4 * 4 + ((size_t)nloc * max_ne + 3) / 4 * 4 + (h1 ? nloc * npad : 0));
+           (size_t)tsize * (((size_t)max_u * cw + 3) / 4 * 4 + ((size_t)nloc * max_ne * cw + 3) / 4 * 4 +
+                            (h1 ? nloc * npad : 0));
+}
+
+// Shared memory of the FP32 multi-RHS block kernel (16-byte chunks: 4 values a dof), 0 for a
+// context built for one right-hand side.
+size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, uint32_t max_pkt, int max_u, int max_ne) {
+    if (c->max_nrhs <= 1) return 0;
+    size_t s = block_smem_estimate(nloc, 4, h1, max_pkt, max_u, max_ne, 4);
+    if (tc) {
+        BlockArgs tmp{};
+        tmp.max_pkt = max_pkt;
+        tmp.max_u = max_u;
+        tmp.max_ne = max_ne;
+        s = std::max(s, h1_tc_smem_bytes(nloc, tmp, true));
+    }
+    return s;
+}
+
+int smem_per_sm_bytes() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cached[dev] = v;
+    }
+    return cached[dev];
 }
 
 int smem_optin_bytes() {

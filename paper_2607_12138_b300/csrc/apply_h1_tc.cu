@@ -19,12 +19,12 @@ uint32_t h1_tc_btile_bytes(int nloc) {
     }
 }
 
-size_t h1_tc_smem_bytes(int nloc, const BlockArgs& A) {
+size_t h1_tc_smem_bytes(int nloc, const BlockArgs& A, bool mr) {
     switch (nloc) {
-        case 10: return tc_smem_bytes<10>(A);
-        case 15: return tc_smem_bytes<15>(A);
-        case 20: return tc_smem_bytes<20>(A);
-        case 35: return tc_smem_bytes<35>(A);
+        case 10: return tc_smem_bytes<10>(A, mr);
+        case 15: return tc_smem_bytes<15>(A, mr);
+        case 20: return tc_smem_bytes<20>(A, mr);
+        case 35: return tc_smem_bytes<35>(A, mr);
         default: return 0;
     }
 }

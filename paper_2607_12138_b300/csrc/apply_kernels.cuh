@@ -146,6 +146,42 @@ __device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t
 __device__ __forceinline__ double div_by_count(double v, uint16_t d) { return v / (double)d; }
 __device__ __forceinline__ float div_by_count(float v, uint16_t d) { return v * __frcp_rn((float)d); }
 
+// Stage 3 for one right-hand side: each block-local dof u sums its copies zs[incoff[u],
+// incoff[u+1]) in that order (Eq. mhatinvbras_def, the D^{-1} P^T half), BRAS divides by the
+// multiplicity, interior dofs store to y and shared ones to the partials.  A thread takes four
+// dofs at a time so that their shared-memory chains overlap; every dof's order is unchanged.
+template <typename T, int OP>
+__device__ __forceinline__ void block_dof_sums(int nu, int nint, const uint16_t* incoff, const T* zs,
+                                               const uint16_t* dmul, const int32_t* ids, T* __restrict__ y,
+                                               int nrhs, int r0, T* __restrict__ part, int64_t p0) {
+    constexpr int U = 4;
+    for (int u = threadIdx.x; u < nu; u += U * blockDim.x) {
+        int s0[U], cnt[U];
+        T acc[U];
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * (int)blockDim.x;
+            s0[k] = uu < nu ? incoff[uu] : 0;
+            cnt[k] = uu < nu ? incoff[uu + 1] - s0[k] : 0;
+            acc[k] = T(0);
+            m = max(m, cnt[k]);
+        }
+        for (int j = 0; j < m; ++j) {
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (j < cnt[k]) acc[k] += zs[s0[k] + j];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * (int)blockDim.x;
+            if (uu >= nu) break;
+            if (uu < nint) y[(size_t)ids[uu] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc[k], dmul[uu]) : acc[k];
+            else part[p0 + (uu - nint)] = acc[k];
+        }
+    }
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec4<double> { using type = double2; static constexpr int W = 2; };
@@ -473,17 +509,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 }
             }
         } else {
-            for (int u = tid; u < nu; u += blockDim.x) {
-                const int s0 = incoff[u], s1 = incoff[u + 1];
-                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-                T acc = T(0);
-                for (int s = s0; s < s1; ++s) acc += zs[s];
-                if (u < nint) {
-                    y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
-                } else {
-                    part[p0 + (u - nint)] = acc;
-                }
-            }
+            block_dof_sums<T, OP>(nu, nint, incoff, zs, dmul, ids, y, nrhs, r0, part, p0);
         }
     }
 }
@@ -532,6 +558,8 @@ size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
 
 // Largest dynamic shared memory one CTA may opt into on the current device.
 int smem_optin_bytes();
+// Shared memory of one SM of the current device.
+int smem_per_sm_bytes();
 
 // Rows of nrhs values 16-byte aligned, so that full chunks load and store as one vector.
 template <typename T>

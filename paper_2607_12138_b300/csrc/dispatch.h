@@ -27,7 +27,7 @@ cudaError_t launch_pk_f64(const LaunchCommon& L, int nloc, int op, const double*
 cudaError_t launch_pk_f32(const LaunchCommon& L, int nloc, int op, const float* x, float* y, float* part, int nrhs, cudaStream_t st);
 bool h1_tc_supported(int nloc);
 uint32_t h1_tc_btile_bytes(int nloc);
-size_t h1_tc_smem_bytes(int nloc, const BlockArgs& A);
+size_t h1_tc_smem_bytes(int nloc, const BlockArgs& A, bool mr = false);
 cudaError_t launch_h1_tc(const LaunchCommon& L, const unsigned char* btile, int nloc, int op, const float* x,
                          float* y, float* part, int nrhs, cudaStream_t st);
 void h1_tc_build_btile(const double* ref, int nloc, std::vector<unsigned char>& out);

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "apply_kernels.cuh"
 
 namespace bras {
@@ -96,6 +98,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Ties registers written by tcgen05.ld to a point after tcgen05.wait::ld, so that no use of
+// them is scheduled before the wait.
+template <int N> __device__ __forceinline__ void reg_fence(uint32_t (&v)[N]) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) asm volatile("" : "+r"(v[j]));
+}
 
 // D[tmem] (+)= A[tmem] * B[smem desc]^T, kind::tf32, one thread.
 __device__ __forceinline__ void umma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
@@ -116,18 +124,27 @@ struct TcArgs {
     const unsigned char* btile;   // [Abig | Asmall] pre-arranged, 2 * N * K * 4 bytes
 };
 
-// MR = false: one cell per thread, one right-hand side per CTA (as k_block).  MR = true: one
-// CTA per cell block walks the right-hand sides in chunks of 4; the block's ne * 4 items
-// (cell, rhs) fill the tensor-memory lanes in passes of blockDim items (two 128-lane tiles),
-// each pass one GEMM (the E*R rows of the local product on the M side).
-template <int NLOC, int OP, bool MR = false>
-__global__ void __launch_bounds__(256, 1)
+// MR = false: one cell per TMEM lane, one right-hand side per CTA (as k_block).  TPC = 1: one
+// thread per cell, blockDim / 128 tiles.  TPC = 2 (blocks of at most 128 cells): one tile, two
+// threads per cell, warps 0-3 taking the even and warps 4-7 the odd 8-column groups of the
+// tensor-memory rows, so that a CTA needs 128 TMEM columns and more CTAs share an SM.
+// ALIAS (one right-hand side): the dof-sorted products overwrite the block's loc/pos tables
+// (both dead by then) instead of a buffer of their own; chosen when it is what lets two CTAs
+// share an SM, or with TPC = 2.
+// MR = true (TPC = 1): one CTA per cell block walks the right-hand sides in chunks of 4; the
+// block's ne * 4 items (cell, rhs) fill the tensor-memory lanes in passes of blockDim items
+// (two 128-lane tiles), each pass one GEMM (the E*R rows of the local product on the M side).
+template <int NLOC, int OP, bool MR = false, int TPC = 1, bool ALIAS = false>
+__global__ void __launch_bounds__(256, TPC == 2 ? 3 : 1)
 k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs,
            int vec_ok) {
+    static_assert(TPC == 1 || (TPC == 2 && !MR), "two threads per cell only for one right-hand side a CTA");
+    static_assert(!(ALIAS && MR), "multi-RHS passes keep reading pos");
     using Sh = TcShape<NLOC>;
     constexpr int K = Sh::K, N = Sh::N;
     constexpr int CW = MR ? Chunk<float>::CW : 1;
-    const int tiles = blockDim.x / 128;                       // 128 items (TMEM lanes) per tile
+    const int lanes = blockDim.x / TPC;                       // items (TMEM lanes) per pass
+    const int tiles = lanes / 128;                            // 128 lanes per tile
     const uint32_t TMEM_COLS = (uint32_t)tiles * Sh::TILE_COLS;   // 128 or 256
     const BlockArgs& A = TA.A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -136,16 +153,20 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     unsigned char* btile = smem_raw + 128;                           // 2 * B_BYTES, 128-B aligned
     unsigned char* tab = btile + 2 * Sh::B_BYTES;
     float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u][CW]
-    float* zs = xs + ((A.max_u * CW + 3) & ~3);                                  // [slot][CW]
 
-    const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int lt = TPC == 2 ? (tid & 127) : tid;              // this thread's lane in the pass
+    const int half = TPC == 2 ? (warp >> 2) : 0;              // its column groups (TPC = 2)
+    // one work item per CTA: a block (MR), or a (block, rhs) pair
+    const int b = MR ? blockIdx.x : blockIdx.x / nrhs;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
-    // this thread's cell factor (one cell per thread), fetched now so that its latency hides
-    // behind the copies
-    const float cfac = (!MR && tid < ne) ? static_cast<const float*>(A.scale)[e0 + tid] : 0.f;
+    // [slot][CW]: after the staged vector, or over the block's loc/pos tables
+    float* zs = !ALIAS ? xs + ((A.max_u * CW + 3) & ~3) : reinterpret_cast<float*>(tab + sa);
+    // this thread's cell factor, fetched now so that its latency hides behind the copies
+    const float cfac = (!MR && lt < ne) ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -162,15 +183,14 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tile_col = TPC == 2 ? 0u : (uint32_t)(warp >> 2) * Sh::TILE_COLS;
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
     const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
     const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
 
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t tile_col = (uint32_t)(warp >> 2) * Sh::TILE_COLS;
     bool ok = cta_wait(&bars[0], 0, A.status, true);
     int pending = -1;        // (thread 0) parity of a committed GEMM whose completion was not seen
     uint32_t commits = 0;    // GEMMs committed on bars[3] so far (its phase parity)
@@ -225,23 +245,27 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         }
 
         const int nitem = ne * CW;
-        const int npass = (nitem + blockDim.x - 1) / blockDim.x;   // block-uniform (1 without MR)
+        const int npass = (nitem + lanes - 1) / lanes;   // block-uniform (1 without MR)
         for (int pass = 0; pass < npass; ++pass) {
             // stage 2a: this thread's item row -> tensor memory (big TF32 part, exact remainder)
-            const int it = pass * blockDim.x + tid;   // item of this thread (tile tid / 128, lane tid % 128)
+            const int it = pass * lanes + lt;   // item of this thread (tile lt / 128, lane lt % 128)
             const bool valid = it < nitem;
             const int e = valid ? it / CW : 0;
             const int rr = it % CW;
-            {
+            // (TPC = 2: the column groups of this thread's half, fixed at compile time per branch)
+            auto stage2a = [&](auto hc) {
+                constexpr int H = decltype(hc)::value;
                 float xl[K];
 #pragma unroll
                 for (int a = 0; a < K; ++a) xl[a] = 0.f;
                 if (valid) {
 #pragma unroll
-                    for (int a = 0; a < NLOC; ++a) xl[a] = xs[loc[a * ne + e] * CW + rr];
+                    for (int a = 0; a < NLOC; ++a)
+                        if (TPC == 1 || ((a >> 3) & 1) == H) xl[a] = xs[loc[a * ne + e] * CW + rr];
                 }
 #pragma unroll
                 for (int k0 = 0; k0 < K; k0 += 8) {
+                    if (TPC == 2 && ((k0 >> 3) & 1) != H) continue;
                     uint32_t hi[8], lo[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -252,7 +276,9 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                     tmem_st8(tmem + lane_base + tile_col + K + k0, lo);
                 }
                 tmem_wait_st();
-            }
+            };
+            if (half == 0) stage2a(std::integral_constant<int, 0>{});
+            else stage2a(std::integral_constant<int, 1>{});
             tc_fence_before();
             __syncthreads();
 
@@ -266,7 +292,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                     const uint32_t bb = smem_addr(btile), bs = bb + Sh::B_BYTES;
                     constexpr uint32_t LBO = 128, SBO = (K / 4) * 128;
                     const uint32_t idesc = umma_idesc_tf32_m128<N>();
-                    const int ptiles = min(tiles, (nitem - pass * (int)blockDim.x + 127) / 128);
+                    const int ptiles = min(tiles, (nitem - pass * lanes + 127) / 128);
                     for (int t = 0; t < ptiles; ++t) {
                         const uint32_t base = tmem + (uint32_t)t * Sh::TILE_COLS;
                         const uint32_t d = base + 2 * K;
@@ -294,19 +320,56 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 
             // stage 2c: read this item's row of Z, scale, stage for the incidence sums
             const float c = MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac;
+            auto stage2c = [&](auto hc) {
+                constexpr int H = decltype(hc)::value;
+                constexpr int G = N / 16;
+                auto mine = [](int g) { return TPC == 1 || (g & 1) == H; };
+                // all of this thread's column groups in flight, one wait
+                uint32_t v[G][16];
 #pragma unroll
-            for (int n0 = 0; n0 < N; n0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + lane_base + tile_col + 2 * K + n0, v);
+                for (int g = 0; g < G; ++g)
+                    if (mine(g)) tmem_ld16(tmem + lane_base + tile_col + 2 * K + 16 * g, v[g]);
                 tmem_wait_ld();
-                if (valid) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int a = n0 + j;
-                        if (a < NLOC) zs[pos[a * ne + e] * CW + rr] = __uint_as_float(v[j]) * c;
+                for (int g = 0; g < G; ++g)
+                    if (mine(g)) reg_fence(v[g]);
+                if constexpr (!ALIAS) {
+                    if (valid) {
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int a = 16 * g + j;
+                                if (a < NLOC) zs[pos[a * ne + e] * CW + rr] = __uint_as_float(v[g][j]) * c;
+                            }
+                    }
+                } else {
+                    // zs overwrites loc/pos: every thread takes its positions first
+                    uint32_t pv[G][16];
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int a = 16 * g + j;
+                            if (mine(g) && a < NLOC) pv[g][j] = valid ? pos[a * ne + e] : 0u;
+                        }
+                    // every warp passes exactly one of the two call sites (barrier 1, all threads)
+                    asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x) : "memory");
+                    if (valid) {
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            if (!mine(g)) continue;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int a = 16 * g + j;
+                                if (a < NLOC) zs[pv[g][j]] = __uint_as_float(v[g][j]) * c;
+                            }
+                        }
                     }
                 }
-            }
+            };
+            if (half == 0) stage2c(std::integral_constant<int, 0>{});
+            else stage2c(std::integral_constant<int, 1>{});
             tc_fence_before();
             __syncthreads();   // zs complete; the next pass may overwrite tensor memory
         }
@@ -331,17 +394,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                 }
             }
         } else {
-            for (int u = tid; u < nu; u += blockDim.x) {
-                const int s0 = incoff[u], s1 = incoff[u + 1];
-                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-                float acc = 0.f;
-                for (int s = s0; s < s1; ++s) acc += zs[s];
-                if (u < nint) {
-                    y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc, dmul[u]) : acc;
-                } else {
-                    part[p0 + (u - nint)] = acc;
-                }
-            }
+            block_dof_sums<float, OP>(nu, nint, incoff, zs, dmul, ids, y, nrhs, r0, part, p0);
         }
     }
     // a GEMM committed but not seen complete: drain it before the columns are released
@@ -352,20 +405,25 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (!ok && tid == 0) {
-        // leave after the copies that may still be in flight have landed
-        mbar_wait_bounded(&bars[0], A.status);
-        mbar_wait_bounded(&bars[1], A.status);
+    if (tid == 0) {
+        // leave after the copies that may still be in flight have landed (the B tile's phase
+        // has completed already unless no item got that far)
+        if (!ok) {
+            mbar_wait_bounded(&bars[0], A.status);
+            mbar_wait_bounded(&bars[1], A.status);
+        }
         mbar_wait_bounded(&bars[2], A.status);
     }
 }
 
+// alias: the products reuse the loc/pos bytes of the packet (4 per copy; one right-hand side)
 template <int NLOC>
-size_t tc_smem_bytes(const BlockArgs& A, bool mr = false) {
+size_t tc_smem_bytes(const BlockArgs& A, bool mr = false, bool alias = true) {
     using Sh = TcShape<NLOC>;
     const size_t cw = mr ? Chunk<float>::CW : 1;
     return 128 + 2 * (size_t)Sh::B_BYTES + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(float) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3));
+           sizeof(float) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) +
+                            ((mr || !alias) ? (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) : 0));
 }
 
 template <int NLOC, int OP>
@@ -373,15 +431,24 @@ cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y
                             const float* dinv, int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off,
                             const int32_t* sh_slots, cudaStream_t st) {
     const bool mr = nrhs > 1 && tc_smem_bytes<NLOC>(TA.A, true) <= (size_t)smem_optin_bytes();
-    const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr);
-    auto kern = mr ? k_block_tc<NLOC, OP, true> : k_block_tc<NLOC, OP, false>;
+    // blocks of at most 128 cells: one tile, two threads per cell
+    const bool two = !mr && TA.A.max_ne <= 128;
+    // the products get a buffer of their own unless sharing the tables' bytes is what fits
+    // two CTAs per SM (measured: the own buffer is faster at equal occupancy)
+    const bool alias = !mr && (two || 2 * (tc_smem_bytes<NLOC>(TA.A, false, false) + 1024) >
+                                           (size_t)smem_per_sm_bytes());
+    const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr, alias);
+    auto kern = mr ? k_block_tc<NLOC, OP, true, 1, false>
+                   : (two ? k_block_tc<NLOC, OP, false, 2, true>
+                          : (alias ? k_block_tc<NLOC, OP, false, 1, true> : k_block_tc<NLOC, OP, false, 1, false>));
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
+    // one or two 128-cell tensor tiles (two threads per cell with one); multi-RHS: two tiles of
+    // items per pass
+    const int threads = 256;
     dim3 grid(mr ? nblk : nblk * nrhs);
-    // one or two 128-cell tensor tiles; multi-RHS: two tiles of items per pass
-    const int threads = (mr || TA.A.max_ne > 128) ? 256 : 128;
     const int vec = rows_vectorisable<float>(nrhs, x, y, part) ? 1 : 0;
     kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs, vec);
     count_launch(1);
