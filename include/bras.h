@@ -22,7 +22,7 @@
  *    i * nrhs + r.  Dof i is the global dof number used in `l2g`.
  *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.h1_basis) P_p
  *    on triangles (dim 2) or tetrahedra (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind
- *    and BRAS_HDIV = Raviart-Thomas, order k = 1..3, on triangles or tetrahedra, mapped by
+ *    and BRAS_HDIV = Raviart-Thomas, order k = 1..4, on triangles or tetrahedra, mapped by
  *    the covariant / contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with
  *    |det J|.  Local dof order and dof functionals are the ones documented with the mesh
  *    generator and the reference elements (vertices of each tetrahedron listed in

@@ -215,11 +215,12 @@ __device__ __forceinline__ void df_merge(float& ah, float& al, float bh, float b
     al = __fadd_rn(__fadd_rn(al, bl), err);
 }
 
-// Streamed FP32/bf16 cell matrices, one right-hand side: ask for two resident blocks per SM (at
-// most 128 registers a thread), so that twice as many matrix loads are in flight.  Multi-RHS CTAs
-// are shared-memory bound to one per SM and keep each item's local vector in registers.
+// Streamed FP32/bf16 cell matrices, one right-hand side, n_loc <= 48: ask for two resident
+// blocks per SM (at most 128 registers a thread), so that twice as many matrix loads are in
+// flight.  Multi-RHS CTAs are shared-memory bound to one per SM and keep each item's local
+// vector in registers; n_loc = 70, 84 need the full register file for their accumulators.
 template <int KIND, typename T, int NLOC, bool MR = false> struct MinBlocks {
-    static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4 && !MR) ? 2 : 1;
+    static constexpr int value = (KIND == KIND_PACKED && sizeof(T) == 4 && !MR && NLOC <= 48) ? 2 : 1;
 };
 
 // ---- multi-RHS row segments --------------------------------------------------------------
@@ -405,7 +406,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     const uint16_t c = L[a * ne];
                     const T v = xs[c & 0x7fff];
                     const bool s = (c & 0x8000) != 0;
-                    neg |= (uint64_t)s << a;
+                    if (a < 64) neg |= (uint64_t)s << (a & 63);
                     xt[a * ne + e] = s ? -v : v;
                 }
                 for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
@@ -416,7 +417,11 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             __syncthreads();
             if (e < ne) {
 #pragma unroll
-                for (int a = 0; a < NLOC; ++a) zs[pos[a * ne + e]] = ((neg >> a) & 1) ? -zl[a] : zl[a];
+                for (int a = 0; a < NLOC; ++a) {
+                    // signs of the first 64 local dofs kept as bits, the rest re-read from loc
+                    const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (loc[a * ne + e] & 0x8000) != 0;
+                    zs[pos[a * ne + e]] = s ? -zl[a] : zl[a];
+                }
             }
         } else {
             for (int it = tid; it < nitem; it += blockDim.x) {
@@ -432,7 +437,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                         if constexpr (SIGNED) {
                             const T v = (OP == OP_DIAG) ? T(0) : xs[(c & 0x7fff) * CW + rr];
                             const bool s = (c & 0x8000) != 0;
-                            neg |= (uint64_t)s << a;
+                            if (a < 64) neg |= (uint64_t)s << (a & 63);
                             xl[a] = s ? -v : v;
                         } else {
                             xl[a] = (OP == OP_DIAG) ? T(0) : xs[c * CW + rr];
@@ -441,7 +446,8 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
                     for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
                     auto out = [&](int a, T v) {
-                        const bool s = SIGNED && OP != OP_DIAG && ((neg >> a) & 1);
+                        const bool s = SIGNED && OP != OP_DIAG &&
+                                       (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (L[a * ne] & 0x8000) != 0);
                         zs[pos[a * ne + e] * CW + rr] = s ? -v : v;
                     };
                     if constexpr (KIND == KIND_H1) {
@@ -576,10 +582,15 @@ template <int NLOC, typename T, typename S, int KIND, int OP>
 cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
                          int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
                          cudaStream_t st) {
-    const bool mr = nrhs > 1 && OP != OP_DIAG &&
+    // multi-RHS items hold their local vector and accumulators in registers: n_loc <= 48
+    constexpr bool kMR = NLOC <= 48;
+    const bool mr = kMR && nrhs > 1 && OP != OP_DIAG &&
                     block_smem_bytes<NLOC, T, KIND>(A, true) <= (size_t)smem_optin_bytes();
     const size_t smem = block_smem_bytes<NLOC, T, KIND>(A, mr);
-    auto kern = mr ? k_block<NLOC, T, S, KIND, OP, true> : k_block<NLOC, T, S, KIND, OP, false>;
+    auto kern = k_block<NLOC, T, S, KIND, OP, false>;
+    if constexpr (kMR) {
+        if (mr) kern = k_block<NLOC, T, S, KIND, OP, true>;
+    }
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

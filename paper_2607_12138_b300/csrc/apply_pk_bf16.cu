@@ -17,6 +17,12 @@ cudaError_t launch_pk_bf16(const LaunchCommon& L, int nloc, int op, const float*
     BRAS_CASE(20, OP_BRAS)
     BRAS_CASE(36, OP_BRAS)
     BRAS_CASE(45, OP_BRAS)
+    BRAS_CASE(24, OP_MASS)
+    BRAS_CASE(24, OP_BRAS)
+    BRAS_CASE(70, OP_MASS)
+    BRAS_CASE(70, OP_BRAS)
+    BRAS_CASE(84, OP_MASS)
+    BRAS_CASE(84, OP_BRAS)
 #undef BRAS_CASE
     return cudaErrorInvalidValue;
 }

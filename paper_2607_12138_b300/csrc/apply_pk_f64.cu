@@ -33,6 +33,15 @@ cudaError_t launch_pk_f64(const LaunchCommon& L, int nloc, int op, const double*
     BRAS_CASE(45, OP_MASS)
     BRAS_CASE(45, OP_BRAS)
     BRAS_CASE(45, OP_DIAG)
+    BRAS_CASE(24, OP_MASS)
+    BRAS_CASE(24, OP_BRAS)
+    BRAS_CASE(24, OP_DIAG)
+    BRAS_CASE(70, OP_MASS)
+    BRAS_CASE(70, OP_BRAS)
+    BRAS_CASE(70, OP_DIAG)
+    BRAS_CASE(84, OP_MASS)
+    BRAS_CASE(84, OP_BRAS)
+    BRAS_CASE(84, OP_DIAG)
 #undef BRAS_CASE
     return cudaErrorInvalidValue;
 }

@@ -540,7 +540,7 @@ int n_local(int dim, int space, int order) {
         if (dim == 3 && order >= 1 && order <= 4) return (order + 1) * (order + 2) * (order + 3) / 6;
         return -1;
     }
-    if (order < 1 || order > 3) return -1;
+    if (order < 1 || order > 4) return -1;
     if (dim == 2 && (space == 1 || space == 2)) return order * (order + 2);
     if (dim != 3) return -1;
     if (space == 1) return order * (order + 2) * (order + 3) / 2;

@@ -113,6 +113,7 @@ int schur_order(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
         case 1: return schur_typed<1, T>(c, prec, x, y, st);
         case 2: return schur_typed<2, T>(c, prec, x, y, st);
         case 3: return schur_typed<3, T>(c, prec, x, y, st);
+        case 4: return schur_typed<4, T>(c, prec, x, y, st);
         default: return BRAS_ERR_INVALID;
     }
 }

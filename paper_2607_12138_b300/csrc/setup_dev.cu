@@ -208,8 +208,15 @@ cudaError_t run_element_inverse(int n, int64_t E, int64_t Epad, const double* Rr
                                 double* Mpk64, float* Mpk32, double* Minv64, float* Minv32,
                                 __nv_bfloat16* Minvbf, unsigned long long* bad, int* nfixed,
                                 const int32_t* perm, cudaStream_t st) {
-    const int warps = 4;
-    size_t smem = (size_t)warps * 2 * n * n * sizeof(double);
+    // one warp per cell, two n x n FP64 work arrays each: four warps a CTA while they fit the
+    // opt-in shared memory (n_loc = 84 takes 113 KB a warp)
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t per_warp = (size_t)2 * n * n * sizeof(double);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)optin / per_warp));
+    size_t smem = (size_t)warps * per_warp;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
     cudaError_t err = cudaFuncSetAttribute(k_element_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int nb = (int)std::min<int64_t>((E + warps - 1) / warps, 148 * 16);

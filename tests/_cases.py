@@ -33,6 +33,9 @@ SMALL_CASES = {
     "hcurl2d_1_signed": (lambda: mg.relabel_mesh(square(16), seed=11), "hcurl", 1),   # triangles
     "hdiv2d_2_signed": (lambda: mg.relabel_mesh(square(12), seed=12), "hdiv", 2),
     "hcurl2d_3": (lambda: square(12), "hcurl", 3),
+    "hcurl4": (lambda: cube(3), "hcurl", 4),             # order 4: n_loc 84 / 70 / 24
+    "hdiv4": (lambda: cube(3), "hdiv", 4),
+    "hdiv2d_4_signed": (lambda: mg.relabel_mesh(square(8), seed=13), "hdiv", 4),
     "2d_p4_bern": (lambda: square(13), "h1b", 4),        # Bernstein basis (Table 1)
     "3d_p3_bern": (lambda: cube(5), "h1b", 3),
     "3d_p4_bern": (lambda: cube(5), "h1b", 4),

@@ -29,11 +29,11 @@ def test_host_only_entry_points():
     lib.bras_n_local.restype = ctypes.c_int
     assert [lib.bras_n_local(3, 0, p) for p in (1, 2, 3, 4)] == [4, 10, 20, 35]
     assert [lib.bras_n_local(2, 0, p) for p in (1, 2, 3, 4)] == [3, 6, 10, 15]
-    assert [lib.bras_n_local(3, 1, k) for k in (1, 2, 3)] == [6, 20, 45]
-    assert [lib.bras_n_local(3, 2, k) for k in (1, 2, 3)] == [4, 15, 36]
-    assert [lib.bras_n_local(2, 1, k) for k in (1, 2, 3)] == [3, 8, 15]
-    assert [lib.bras_n_local(2, 2, k) for k in (1, 2, 3)] == [3, 8, 15]
-    assert lib.bras_n_local(2, 1, 4) == -1 and lib.bras_n_local(3, 0, 5) == -1
+    assert [lib.bras_n_local(3, 1, k) for k in (1, 2, 3, 4)] == [6, 20, 45, 84]
+    assert [lib.bras_n_local(3, 2, k) for k in (1, 2, 3, 4)] == [4, 15, 36, 70]
+    assert [lib.bras_n_local(2, 1, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
+    assert [lib.bras_n_local(2, 2, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
+    assert lib.bras_n_local(2, 1, 5) == -1 and lib.bras_n_local(3, 2, 5) == -1 and lib.bras_n_local(3, 0, 5) == -1
     lib.bras_status_string.restype = ctypes.c_char_p
     assert lib.bras_status_string(-5) == b"local mass matrix not SPD"
     out = ctypes.c_void_p(1)

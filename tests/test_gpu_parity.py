@@ -69,7 +69,8 @@ def test_fp32_and_bf16_applies(case):
     assert rel_err(ctx.bras_apply(xt, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space not in ("h1", "h1b") else TOL32[space])
 
 
-@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2", "3d_p3", "3d_p4", "hcurl3", "hdiv3"])
+@pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2", "3d_p3", "3d_p4", "hcurl3", "hdiv3",
+                                  "hcurl4"])
 @pytest.mark.parametrize("nrhs", [2, 3, 5, 8])
 def test_multi_rhs_interleaved(case, nrhs):
     """[n][R] vectors: chunks of up to 4 right-hand sides per CTA (ragged last chunk for R = 3, 5),
@@ -340,6 +341,24 @@ def test_tensor_core_vs_simt_fp32(case):
         assert rel_err(a, s) <= 2e-5
 
 
+@pytest.mark.parametrize("case", ["3d_p3", "3d_p4"])
+@pytest.mark.parametrize("block_elems", [64, 128, 160, 256])
+def test_tensor_core_block_variants(case, block_elems):
+    """The tensor-core kernel's launch variants on 750 tets: blocks of <= 128 cells (two threads
+    per cell, one TMEM tile, products over the block tables), 160 (one thread per cell, own
+    product buffer) and 256 (at p = 4 the products overwrite the tables); one and four
+    right-hand sides."""
+    mesh, space, order, n, l2g, signs = build(case)
+    pr = Problem(mesh, space, order, l2g, signs, n)
+    ctx = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs, block_elems=block_elems, max_nrhs=4)
+    x, xt = _vec(n, dtype=torch.float32)
+    for op, ref in (("bras_apply", pr.B @ x), ("mass_apply", pr.M @ x)):
+        assert rel_err(getattr(ctx, op)(xt, B.FP32).cpu(), ref) <= 2e-5
+    x4, xt4 = _vec(n, nrhs=4, seed=9, dtype=torch.float32)
+    y4 = ctx.bras_apply(xt4, B.FP32).cpu().numpy().reshape(n, 4)
+    assert rel_err(y4, pr.B @ x4.reshape(n, 4)) <= 2e-5
+
+
 @pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "c1_2d_p2", "3d_p4", "hdiv1_signed"])
 def test_stationary_iterations(case):
     """Power iteration, damped fixed point and Chebyshev semi-iteration (Sec. 3) against the
@@ -439,7 +458,7 @@ def test_cg_lanczos_kappa(case):
     assert k < 400 and lo >= 1.0 - 1e-9                             # lambda_min >= 1 for BRAS
 
 
-@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3"])
+@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3", "hdiv4"])
 def test_schur_complement_apply(case):
     """-S~ x = B M_bras^{-1} B^T x (mixed Poisson, RT_k / DG_{k-1}) against the oracle's
     assembled B and BRAS, in FP64 and FP32; other spaces are rejected."""

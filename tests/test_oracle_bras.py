@@ -30,13 +30,14 @@ def _problem(mesh, space, order, rho=None):
     return Problem(mesh, space, order, l2g, s, n, rho)
 
 
-@pytest.mark.parametrize("space,order", [("h1", 2), ("h1", 4), ("hcurl", 2), ("hcurl", 3), ("hdiv", 3)])
+@pytest.mark.parametrize("space,order", [("h1", 2), ("h1", 4), ("hcurl", 2), ("hcurl", 3), ("hcurl", 4), ("hdiv", 3),
+                                         ("hdiv", 4)])
 def test_one_element_is_exact_inverse(space, order):
     pr = _problem(mg.single_simplex_mesh(3, seed=2), space, order)
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
 
 
-@pytest.mark.parametrize("space,order", [("hcurl", 1), ("hcurl", 3), ("hdiv", 2)])
+@pytest.mark.parametrize("space,order", [("hcurl", 1), ("hcurl", 3), ("hdiv", 2), ("hcurl", 4), ("hdiv", 4)])
 def test_one_triangle_is_exact_inverse(space, order):
     pr = _problem(mg.single_simplex_mesh(2, seed=2), space, order)
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
@@ -49,7 +50,9 @@ CASES = [(mg.unit_square_mesh(5, jitter=0.2, seed=4), "h1", 2),
          (mg.relabel_mesh(mg.unit_cube_mesh(2), seed=5), "hdiv", 1),
          (mg.unit_cube_mesh(2), "hdiv", 2),
          (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=6), seed=7), "hcurl", 2),
-         (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=8), seed=9), "hdiv", 3)]
+         (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=8), seed=9), "hdiv", 3),
+         (mg.unit_cube_mesh(2, jitter=0.1, seed=10), "hcurl", 4),
+         (mg.unit_cube_mesh(2, jitter=0.1, seed=11), "hdiv", 4)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))

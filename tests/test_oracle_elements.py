@@ -149,8 +149,8 @@ def test_bernstein_closed_forms(dim, p):
 
 @pytest.mark.parametrize("space,order,sort", [
     ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False), ("h1b", 3, False), ("h1b", 4, False),
-    ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True),
-    ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True),
+    ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True), ("hcurl", 4, True),
+    ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True), ("hdiv", 4, True),
     ("hcurl", 2, False)])
 def test_conformity_across_shared_face(space, order, sort):
     if space == "hcurl" and order == 2 and not sort:
@@ -191,7 +191,7 @@ def _two_triangles(seed, sort=True):
 
 
 @pytest.mark.parametrize("space", ["hcurl", "hdiv"])
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 @pytest.mark.parametrize("sort", [True, False])
 def test_conformity_across_shared_edge_2d(space, order, sort):
     mesh = _two_triangles(3, sort)
@@ -220,7 +220,7 @@ def test_conformity_across_shared_edge_2d(space, order, sort):
             np.testing.assert_allclose(u[0] @ nrm, u[1] @ nrm, atol=1e-10)
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_rt_is_rotated_nedelec_2d(order):
     """With n = R t, R v = (v_y, -v_x), the RT edge moments of R psi equal the N1curl edge moments
     of psi, and the RT interior moments of components (0, 1) are the N1curl ones of (1, -0): so

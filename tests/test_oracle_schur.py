@@ -28,11 +28,11 @@ def _problem(mesh, k):
 
 def test_lowest_order_divergence_closed_form():
     np.testing.assert_allclose(reference_divergence(1), [[-1.0, 1.0, -1.0, 1.0]], atol=1e-14)
-    for k in (2, 3):
+    for k in (2, 3, 4):
         assert reference_divergence(k).shape == (n_dg(k), k * (k + 1) * (k + 3) // 2)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_divergence_annihilates_constant_fields(k):
     mesh = mg.unit_cube_mesh(2, jitter=0.15)
     pr, l2g, s, n = _problem(mesh, k)
