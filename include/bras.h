@@ -20,9 +20,11 @@
  *    bras_pcg_solve synchronise the stream before they return.
  *  * Vectors with nrhs > 1 right-hand sides are RHS-interleaved: entry (i, r) is at
  *    i * nrhs + r.  Dof i is the global dof number used in `l2g`.
- *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.h1_basis) P_p
+ *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.basis) P_p
  *    on triangles (dim 2) or tetrahedra (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind
- *    and BRAS_HDIV = Raviart-Thomas, order k = 1..4, on triangles or tetrahedra, mapped by
+ *    and BRAS_HDIV = Raviart-Thomas, order k = 1..4, or with bras_options.basis = 1 the
+ *    second kinds N2curl and BDM (the full P_k^dim, k = 1..3; Tables 2-3), on triangles or
+ *    tetrahedra, mapped by
  *    the covariant / contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with
  *    |det J|.  Local dof order and dof functionals are the ones documented with the mesh
  *    generator and the reference elements (vertices of each tetrahedron listed in
@@ -89,9 +91,11 @@ typedef struct {
     int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
     int simt_only;       /* 1: H1 FP32 applies on the FP32 units instead of the tensor-core
                             (3xTF32 tcgen05) local GEMM; 0 = tensor cores where supported  */
-    int h1_basis;        /* BRAS_H1 only: 0 = Lagrange (values at the equispaced nodes),
+    int basis;           /* BRAS_H1: 0 = Lagrange (values at the equispaced nodes),
                             1 = Bernstein (B_alpha = p!/alpha! prod lambda_i^alpha_i, the
-                            "Bernstein" family of Table 1); same multi-indices, same l2g */
+                            "Bernstein" family of Table 1); same multi-indices, same l2g.
+                            BRAS_HCURL / BRAS_HDIV: 0 = first kind (N1curl_k / RT_k),
+                            1 = second kind (N2curl_k / BDM_k, k = 1..3)                  */
     int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for every cell
                             block size (multiples of 32 up to 256) whose kernels fit shared
                             memory and keep the fastest (one table build and four applies per
@@ -156,8 +160,9 @@ int bras_setup_batched(bras_ctx** out, int dim, int space, int order, int n_mesh
  * n_mesh + 1 dof offsets (host array). */
 int bras_batch_offsets(const bras_ctx* ctx, int* n_mesh, int64_t* dof_offsets);
 
-/* Number of local dofs per cell for (dim, space, order), or -1 if unsupported. */
-int bras_n_local(int dim, int space, int order);
+/* Number of local dofs per cell for (dim, space, order, basis as in bras_options.basis), or
+ * -1 if unsupported. */
+int bras_n_local(int dim, int space, int order, int basis);
 
 /* bras_mass_apply -- y = M x  (Eq. M_PMbrP, element by element).
  * x, y: [n_dof * nrhs] of double (BRAS_FP64) or float (BRAS_FP32 / BRAS_BF16); x and y

@@ -30,10 +30,10 @@ def metrics(space: str, J: np.ndarray) -> np.ndarray:
     det = np.abs(np.linalg.det(J))
     if space in ("h1", "h1b"):   # Lagrange or Bernstein basis: scalar pullback
         return det[:, None, None]
-    if space == "hcurl":
+    if space in ("hcurl", "n2curl"):
         Jinv = np.linalg.inv(J)
         return det[:, None, None] * Jinv @ np.transpose(Jinv, (0, 2, 1))
-    if space == "hdiv":
+    if space in ("hdiv", "bdm"):
         return np.transpose(J, (0, 2, 1)) @ J / det[:, None, None]
     raise ValueError(space)
 

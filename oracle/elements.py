@@ -26,6 +26,14 @@ Spaces (reference tetrahedron / triangle with vertices 0, e_1, .., e_d):
     for the mean inner product on the reference triangle (the face convention below), q outer,
     component inner.  With this normal, RT_k on triangles is N1curl_k rotated by (v_y, -v_x)
     (interior dofs: the pair of components swapped, one negated).
+  * Second kind (N2curl_k: space "n2curl", BDM_k: space "bdm", Tables 2-3): the full vector
+    polynomial space P_k^d.  Dofs, in this order: edge moments of the tangential (N2curl) or,
+    on triangles, normal (BDM) component against L_j, j = 0..k; BDM face moments of the normal
+    component against the orthonormal P_k(face); N2curl face moments int_T phi . (J_f psi)
+    over the nodal basis psi of RT_{k-1} on the reference triangle (J_f = [t1 t2], the face
+    parametrisation below), face outer; interior moments int phi . psi over the nodal basis
+    of RT_{k-1} (N2curl, triangles), RT_{k-2} (N2curl, tetrahedra) or N1curl_{k-1} (BDM).
+    The lower-order nodal bases are this module's own.
 Dof functionals (this project's convention; the paper names Firedrake's families only):
   * edge (a, b), x(u) = v_a + u (v_b - v_a):  int_0^1 phi(x(u)) . (v_b - v_a) L_j(u) du,
     L_j the shifted Legendre polynomial, j = 0..k-1;
@@ -397,11 +405,139 @@ def vector_2d(space: str, k: int) -> RefElement:
     return RefElement(space, 2, k, k, phi, 2)
 
 
+def _mono_vec_integrals_2d(ms2, psi: RefElement, comp_dirs) -> list[list]:
+    """Rows r: the functional int_T v(x) . (sum_c comp_dirs[c] psi_r^c(x)) dx over the reference
+    triangle, evaluated on the monomial vectors x^m e_d of ms2 (2 components, coefficient
+    layout [d * nm + m])."""
+    nm = len(ms2)
+    pm = monomials(2, psi.degree)
+    rows = []
+    for r in range(psi.n_loc):
+        row = [mpmath.mpf(0)] * (2 * nm)
+        for d in range(2):
+            for mi, m in enumerate(ms2):
+                acc = mpmath.mpf(0)
+                for c in range(2):
+                    w = comp_dirs[c][d]
+                    if w == 0:
+                        continue
+                    for qi, q in enumerate(pm):
+                        cf = psi.phi_mp[c * len(pm) + qi, r]
+                        if cf != 0:
+                            acc += w * cf * to_mpf(integrate_triangle({(m[0] + q[0], m[1] + q[1]): Fraction(1)}))
+                row[d * nm + mi] = acc
+        rows.append(row)
+    return rows
+
+
+def _second_kind_functionals_2d(space: str, k: int) -> mpmath.matrix:
+    ms = monomials(2, k)
+    nm = len(ms)
+    V = _ref_vertices(2)
+    rows = []
+    for a, b in EDGES_2D:
+        tau = [V[b][c] - V[a][c] for c in range(2)]
+        w = tau if space == "n2curl" else [tau[1], -tau[0]]
+        restricted = [restrict_to_param(m, V[a], [tau]) for m in ms]
+        for j in range(k + 1):
+            L = shifted_legendre(j)
+            row = [mpmath.mpf(0)] * (2 * nm)
+            for mi, P in enumerate(restricted):
+                prod = {}
+                for (i, _), cf in P.items():
+                    for l, cl in enumerate(L):
+                        prod[(i + l, 0)] = prod.get((i + l, 0), 0) + cf * cl
+                val = to_mpf(integrate_segment(prod))
+                for c in range(2):
+                    row[c * nm + mi] = w[c] * val
+            rows.append(row)
+    if k >= 2:
+        psi = vector_2d("hdiv" if space == "n2curl" else "hcurl", k - 1)
+        rows += _mono_vec_integrals_2d(ms, psi, [[1, 0], [0, 1]])
+    return mpmath.matrix(rows)
+
+
+def _interior_against_basis_3d(ms, psi: RefElement) -> list[list]:
+    """Rows r: int_K v . psi_r over the reference tetrahedron on the monomial vectors of ms."""
+    nm = len(ms)
+    pm = monomials(3, psi.degree)
+    rows = []
+    for r in range(psi.n_loc):
+        row = [mpmath.mpf(0)] * (3 * nm)
+        for c in range(3):
+            for qi, q in enumerate(pm):
+                cf = psi.phi_mp[c * len(pm) + qi, r]
+                if cf == 0:
+                    continue
+                for mi, m in enumerate(ms):
+                    row[c * nm + mi] += cf * to_mpf(simplex_monomial_integral(tuple(x + y for x, y in zip(m, q))))
+        rows.append(row)
+    return rows
+
+
+def _n2curl_face_functionals(k: int, nm: int, ms) -> list[list]:
+    """int_T phi(x(s, t)) . (psi_r^s t1 + psi_r^t t2) ds dt, psi the RT_{k-1} triangle basis."""
+    V = _ref_vertices(3)
+    psi = vector_2d("hdiv", k - 1)
+    pm = monomials(2, psi.degree)
+    rows = []
+    for a, b, c in FACES_3D:
+        t1 = [V[b][i] - V[a][i] for i in range(3)]
+        t2 = [V[c][i] - V[a][i] for i in range(3)]
+        restricted = [restrict_to_param(m, V[a], [t1, t2]) for m in ms]
+        for r in range(psi.n_loc):
+            # the face field psi_r as a polynomial per Cartesian component
+            field = [{} for _ in range(3)]
+            for comp, tv in ((0, t1), (1, t2)):
+                for qi, q in enumerate(pm):
+                    cf = psi.phi_mp[comp * len(pm) + qi, r]
+                    if cf == 0:
+                        continue
+                    for d in range(3):
+                        if tv[d] != 0:
+                            field[d][q] = field[d].get(q, mpmath.mpf(0)) + cf * tv[d]
+            row = [mpmath.mpf(0)] * (3 * nm)
+            for mi, P in enumerate(restricted):
+                for d in range(3):
+                    acc = mpmath.mpf(0)
+                    for q, cf in field[d].items():
+                        acc += cf * to_mpf(integrate_triangle({(i + q[0], j + q[1]): c0 for (i, j), c0 in P.items()}))
+                    row[d * nm + mi] = acc
+            rows.append(row)
+    return rows
+
+
+@functools.lru_cache(maxsize=None)
+def second_kind(space: str, dim: int, k: int) -> RefElement:
+    """N2curl_k ("n2curl") or BDM_k ("bdm"): P_k^dim dualised against the functionals above."""
+    ms = monomials(dim, k)
+    nm = len(ms)
+    span = [[Fraction(int(t == c * nm + j)) for t in range(dim * nm)] for c in range(dim) for j in range(nm)]
+    if dim == 2:
+        F = _second_kind_functionals_2d(space, k)
+    elif space == "n2curl":
+        rows = _edge_functionals(k + 1, nm, ms)
+        if k >= 2:
+            rows += _n2curl_face_functionals(k, nm, ms)
+        if k >= 3:
+            rows += _interior_against_basis_3d(ms, raviart_thomas(k - 2))
+        F = mpmath.matrix(rows)
+    else:
+        rows = _face_functionals("hdiv", k + 1, nm, ms)
+        if k >= 2:
+            rows += _interior_against_basis_3d(ms, nedelec1(k - 1))
+        F = mpmath.matrix(rows)
+    phi = _dualise(span, F, dim * nm)
+    return RefElement(space, dim, k, k, phi, dim)
+
+
 def reference_element(space: str, dim: int, order: int) -> RefElement:
     if space == "h1":
         return lagrange(dim, order)
     if space == "h1b":
         return bernstein(dim, order)
+    if space in ("n2curl", "bdm"):
+        return second_kind(space, dim, order)
     if dim == 2 and space in ("hcurl", "hdiv"):
         return vector_2d(space, order)
     if space == "hcurl":

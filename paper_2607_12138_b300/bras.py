@@ -28,8 +28,9 @@ H1, HCURL, HDIV = 0, 1, 2
 FP64, FP32, BF16, FP64X = 0, 1, 2, 3
 PC_NONE, PC_JACOBI, PC_BRAS = 0, 1, 2
 SOLVE_FP64, SOLVE_MIXED = 0, 1
-SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV, "h1b": H1}   # h1b: H1 with the Bernstein basis
-H1_BASIS = {"h1b": 1}
+# h1b: H1 with the Bernstein basis; n2curl / bdm: the second-kind H(curl) / H(div) families
+SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV, "h1b": H1, "n2curl": HCURL, "bdm": HDIV}
+BASIS = {"h1b": 1, "n2curl": 1, "bdm": 1}
 
 OK, NOT_CONVERGED = 0, 1
 ERR = {-1: "INVALID", -2: "L2G_RANGE", -3: "NO_COPY", -4: "DEGENERATE", -5: "NOT_SPD", -6: "CUDA",
@@ -45,14 +46,14 @@ class BrasError(RuntimeError):
 
 class bras_options(ctypes.Structure):
     _fields_ = [("precisions", ctypes.c_int), ("block_elems", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("simt_only", ctypes.c_int), ("h1_basis", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("simt_only", ctypes.c_int), ("basis", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 _lib.bras_setup.argtypes = [ctypes.POINTER(_vp), _int, _int, _int, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp,
                             ctypes.POINTER(bras_options), _vp]
 _lib.bras_setup.restype = _int
-_lib.bras_n_local.argtypes = [_int, _int, _int]
+_lib.bras_n_local.argtypes = [_int, _int, _int, _int]
 _lib.bras_n_local.restype = _int
 for _name in ("bras_mass_apply", "bras_apply", "bras_apply_noalloc", "bras_jacobi_apply"):
     getattr(_lib, _name).argtypes = [_vp, _int, _vp, _vp, _int, _vp]
@@ -131,8 +132,8 @@ def bras_status_string(code: int) -> str:
     return _lib.bras_status_string(code).decode()
 
 
-def bras_n_local(dim: int, space: int, order: int) -> int:
-    return _lib.bras_n_local(dim, space, order)
+def bras_n_local(dim: int, space: int, order: int, basis: int = 0) -> int:
+    return _lib.bras_n_local(dim, space, order, basis)
 
 
 def bras_setup(dim, space, order, coords, cells, n_dof, l2g, signs=None, rho=None, options=None, stream=None):
@@ -274,7 +275,7 @@ class Context:
         self._signs = t(signs, torch.int8)
         self._rho = t(rho, torch.float64)
         self.n_cell = int(self._cells.shape[0])
-        opt = bras_options(precisions, block_elems, max_nrhs, int(simt_only), H1_BASIS.get(space, 0), int(autotune))
+        opt = bras_options(precisions, block_elems, max_nrhs, int(simt_only), BASIS.get(space, 0), int(autotune))
         self.ctx = bras_setup(self.dim, self.space, order, self._coords, self._cells, self.n_dof, self._l2g,
                               self._signs, self._rho, opt, stream)
         _, _, self.n_loc, self.n_blocks = bras_info(self.ctx)
@@ -297,7 +298,7 @@ class Context:
         self.dim = meshes[0][0].shape[1]
         self.space = SPACES[space]
         self.order = order
-        opt = bras_options(precisions, block_elems, 1, 0, H1_BASIS.get(space, 0), int(autotune))
+        opt = bras_options(precisions, block_elems, 1, 0, BASIS.get(space, 0), int(autotune))
         self.ctx = bras_setup_batched(self.dim, self.space, order, descs, opt, stream)
         self.offsets = bras_batch_offsets(self.ctx)
         self.n_dof, self.n_cell, self.n_loc, self.n_blocks = bras_info(self.ctx)

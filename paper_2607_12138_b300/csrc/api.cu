@@ -150,7 +150,9 @@ int install_tables(bras_ctx* c, const HostTables& t) {
 int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const double* coords,
                int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
                const double* rho, const bras_options* opt, cudaStream_t st, const int32_t* cell_group = nullptr) {
-    const int nloc = n_local(dim, space, order);
+    const int basis = opt ? opt->basis : 0;
+    if (basis < 0 || basis > 1) return BRAS_ERR_INVALID;
+    const int nloc = n_local(dim, space, order, basis);
     c->dim = dim;
     c->space = space;
     c->order = order;
@@ -159,8 +161,6 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     c->E = n_cell;
     c->n = n_dof;
     c->nvert = n_vert;
-    const int h1_basis = opt ? opt->h1_basis : 0;
-    if (h1_basis < 0 || h1_basis > 1 || (h1_basis != 0 && space != BRAS_H1)) return BRAS_ERR_INVALID;
     c->precisions = (opt && opt->precisions) ? opt->precisions : 7;
     c->max_nrhs = (opt && opt->max_nrhs > 0) ? opt->max_nrhs : 1;
     int BE = (opt && opt->block_elems) ? opt->block_elems : 256;
@@ -231,7 +231,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
 
     // reference tables (library construction, host)
     RefTables ref;
-    if (build_reference(dim, space, order, &ref, h1_basis) != 0) return BRAS_ERR_INVALID;
+    if (build_reference(dim, space, order, &ref, basis) != 0) return BRAS_ERR_INVALID;
 
     // mixed Poisson Schur complement tables (RT on tetrahedra): divergence block, the caller's
     // l2g with P's signs times sign(det J_K), and the dof-sorted order of the broken copies
@@ -583,7 +583,7 @@ using namespace bras;
 
 extern "C" {
 
-int bras_n_local(int dim, int space, int order) { return n_local(dim, space, order); }
+int bras_n_local(int dim, int space, int order, int basis) { return n_local(dim, space, order, basis); }
 
 int bras_setup(bras_ctx** out, int dim, int space, int order, int64_t n_vert, const double* coords,
                int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
@@ -592,7 +592,7 @@ int bras_setup(bras_ctx** out, int dim, int space, int order, int64_t n_vert, co
     if (!out) return BRAS_ERR_INVALID;
     *out = nullptr;
     if ((dim != 2 && dim != 3) || space < 0 || space > 2) return BRAS_ERR_INVALID;
-    const int nloc = n_local(dim, space, order);
+    const int nloc = n_local(dim, space, order, opt ? opt->basis : 0);
     if (nloc < 0) return BRAS_ERR_INVALID;
     if (!coords || !cells || !l2g || n_vert <= dim || n_cell <= 0 || n_dof <= 0) return BRAS_ERR_INVALID;
     if (n_cell >= (1ll << 31) || n_dof >= (1ll << 31) || n_cell * nloc >= (1ll << 31)) return BRAS_ERR_TOO_LARGE;
@@ -651,7 +651,7 @@ int bras_setup_batched(bras_ctx** out, int dim, int space, int order, int n_mesh
     if (!out) return BRAS_ERR_INVALID;
     *out = nullptr;
     if (!meshes || n_mesh < 1 || (dim != 2 && dim != 3) || space < 0 || space > 2) return BRAS_ERR_INVALID;
-    const int nloc = n_local(dim, space, order);
+    const int nloc = n_local(dim, space, order, opt ? opt->basis : 0);
     if (nloc < 0) return BRAS_ERR_INVALID;
     int64_t V = 0, E = 0, N = 0;
     bool any_signs = false, any_rho = false;

@@ -42,6 +42,15 @@ cudaError_t launch_pk_f64(const LaunchCommon& L, int nloc, int op, const double*
     BRAS_CASE(84, OP_MASS)
     BRAS_CASE(84, OP_BRAS)
     BRAS_CASE(84, OP_DIAG)
+    BRAS_CASE(12, OP_MASS)
+    BRAS_CASE(12, OP_BRAS)
+    BRAS_CASE(12, OP_DIAG)
+    BRAS_CASE(30, OP_MASS)
+    BRAS_CASE(30, OP_BRAS)
+    BRAS_CASE(30, OP_DIAG)
+    BRAS_CASE(60, OP_MASS)
+    BRAS_CASE(60, OP_BRAS)
+    BRAS_CASE(60, OP_DIAG)
 #undef BRAS_CASE
     return cudaErrorInvalidValue;
 }

@@ -15,12 +15,16 @@
 //     and P_k^- Lambda^2 (lambda^alpha times Whitney forms, alpha_m = 0 below the first
 //     vertex of the form) as a spanning basis, dualised against the documented dof
 //     functionals (edge Legendre moments, face moments against mean-orthonormal
-//     polynomials, interior moments) by an LU solve in long double.
+//     polynomials, interior moments) by an LU solve in long double;
+//   * second kind (N2curl_k / BDM_k): the monomial vectors of P_k^d dualised the same way, with
+//     edge moments up to L_k, BDM face moments against P_k and the remaining face / interior
+//     moments taken against the nodal bases of the lower-order first-kind elements above.
 #include "refelem.h"
 
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <functional>
 #include <vector>
 
 namespace bras {
@@ -136,6 +140,9 @@ int build_lagrange(int dim, int p, RefTables* out) {
 
 // ---- vector elements ------------------------------------------------------------------
 using Vec3 = std::array<double, 3>;
+// Values of every nodal basis function of an element at a reference point (3 components; the
+// third is zero on triangles).
+using BasisEval = std::function<void(const double* x, std::vector<Vec3>& vals)>;
 
 struct SpanFn {            // lambda^alpha * form(vertices)
     std::array<int, 4> alpha;
@@ -288,7 +295,7 @@ const int kEdges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 const int kFaces[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
 const double kVert[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 
-int build_vector(bool curl, int k, RefTables* out) {
+int build_vector(bool curl, int k, RefTables* out, BasisEval* ev = nullptr) {
     const auto span = afw_span(curl, k);
     const int n = (int)span.size();
     const int expect = curl ? k * (k + 2) * (k + 3) / 2 : k * (k + 1) * (k + 3) / 2;
@@ -359,6 +366,18 @@ int build_vector(bool curl, int k, RefTables* out) {
     if ((int)A.size() != n * n) return -2;
     std::vector<long double> C;
     if (!lu_inverse(A, n, C)) return -3;
+    if (ev)
+        *ev = [span, C, n, curl](const double* x, std::vector<Vec3>& vals) {
+            std::vector<Vec3> sv(n);
+            for (int j = 0; j < n; ++j) sv[j] = eval_span(curl, span[j], x);
+            vals.assign(n, Vec3{0, 0, 0});
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    long double acc = 0;
+                    for (int j = 0; j < n; ++j) acc += (long double)sv[j][c] * C[(size_t)j * n + i];
+                    vals[i][c] = (double)acc;
+                }
+        };
     // nodal basis phi_i = sum_j span_j C[j][i]; R_ab = int phi^a phi^b
     out->nloc = n;
     out->ncomp = 3;
@@ -458,7 +477,7 @@ Vec3 eval_span2(bool curl, const Span2& f, const double* x) {
     return {w1 * pw, -w0 * pw, 0.0};
 }
 
-int build_vector_2d(bool curl, int k, RefTables* out) {
+int build_vector_2d(bool curl, int k, RefTables* out, BasisEval* ev = nullptr) {
     const int kE[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     const double kV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
     std::vector<Span2> span;
@@ -504,6 +523,18 @@ int build_vector_2d(bool curl, int k, RefTables* out) {
     if ((int)A.size() != n * n) return -2;
     std::vector<long double> C;
     if (!lu_inverse(A, n, C)) return -3;
+    if (ev)
+        *ev = [span, C, n, curl](const double* x, std::vector<Vec3>& vals) {
+            std::vector<Vec3> sv(n);
+            for (int j = 0; j < n; ++j) sv[j] = eval_span2(curl, span[j], x);
+            vals.assign(n, Vec3{0, 0, 0});
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 2; ++c) {
+                    long double acc = 0;
+                    for (int j = 0; j < n; ++j) acc += (long double)sv[j][c] * C[(size_t)j * n + i];
+                    vals[i][c] = (double)acc;
+                }
+        };
     out->nloc = n;
     out->ncomp = 3;
     out->R.assign((size_t)9 * n * n, 0.0);
@@ -532,9 +563,189 @@ int build_vector_2d(bool curl, int k, RefTables* out) {
     return 0;
 }
 
+// ---- second-kind vector elements: N2curl_k (curl) and BDM_k (div), the full P_k^d -----------
+// Spanning basis: the monomial vectors x^m e_c (c outer, monomials inner), dualised against
+//   * edge moments of v . t (N2curl) or, on triangles, of v . (t_y, -t_x) (BDM) against L_j,
+//     j = 0..k (one more than the first kind);
+//   * BDM faces: moments of v . (t1 x t2) against the mean-orthonormal P_k of the face;
+//   * N2curl faces (k >= 2): int_T v(x(s, t)) . (psi^s t1 + psi^t t2) ds dt over the nodal basis
+//     psi of RT_{k-1} on the reference triangle, face outer;
+//   * interior: int v . psi over the nodal basis psi of RT_{k-1} (N2curl, triangles), RT_{k-2}
+//     (N2curl, tetrahedra, k >= 3) or N1curl_{k-1} (BDM, k >= 2), those bases built above.
+int build_second_kind(int dim, bool curl, int k, RefTables* out) {
+    const auto monos = dim == 3 ? tet_monos(k) : triangle_monos(k);
+    const int nm = (int)monos.size(), n = dim * nm;
+    auto span_val = [&](int j, const double* x) {   // x^m e_c
+        const auto& m = monos[j % nm];
+        double v = 1;
+        for (int c = 0; c < dim; ++c)
+            for (int e = 0; e < m[c]; ++e) v *= x[c];
+        Vec3 r{0, 0, 0};
+        r[j / nm] = v;
+        return r;
+    };
+    const auto seg = segment_rule();
+    const auto tri = triangle_rule();
+    const auto tet = tet_rule();
+    std::vector<long double> A;
+    A.reserve((size_t)n * n);
+    auto push_row = [&](auto&& fn) {
+        for (int j = 0; j < n; ++j) A.push_back((long double)fn(j));
+    };
+    // interior moments against the nodal basis given by ev (reference cell quadrature)
+    auto push_interior = [&](const BasisEval& ev, int npsi) {
+        const auto& rule = dim == 3 ? tet : tri;
+        std::vector<std::vector<Vec3>> pv(rule.size());
+        for (size_t qi = 0; qi < rule.size(); ++qi) ev(rule[qi].x, pv[qi]);
+        for (int r = 0; r < npsi; ++r)
+            push_row([&](int j) {
+                double s = 0;
+                for (size_t qi = 0; qi < rule.size(); ++qi) {
+                    const Vec3 v = span_val(j, rule[qi].x);
+                    s += rule[qi].w * (v[0] * pv[qi][r][0] + v[1] * pv[qi][r][1] + v[2] * pv[qi][r][2]);
+                }
+                return s;
+            });
+    };
+    if (dim == 2) {
+        const int kE[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        const double kV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+        for (auto& e : kE) {
+            const double t[2] = {kV[e[1]][0] - kV[e[0]][0], kV[e[1]][1] - kV[e[0]][1]};
+            const double d[2] = {curl ? t[0] : t[1], curl ? t[1] : -t[0]};
+            for (int jm = 0; jm <= k; ++jm)
+                push_row([&](int j) {
+                    double acc = 0;
+                    for (const QP& q : seg) {
+                        const double x[3] = {kV[e[0]][0] + q.x[0] * t[0], kV[e[0]][1] + q.x[0] * t[1], 0};
+                        const Vec3 v = span_val(j, x);
+                        acc += q.w * (v[0] * d[0] + v[1] * d[1]) * shifted_legendre(jm, q.x[0]);
+                    }
+                    return acc;
+                });
+        }
+        if (k >= 2) {
+            RefTables tmp;
+            BasisEval ev;
+            if (build_vector_2d(!curl, k - 1, &tmp, &ev) != 0) return -4;   // RT_{k-1} / N1curl_{k-1}
+            push_interior(ev, tmp.nloc);
+        }
+    } else {
+        if (curl) {
+            for (auto& e : kEdges) {
+                Vec3 tau;
+                for (int c = 0; c < 3; ++c) tau[c] = kVert[e[1]][c] - kVert[e[0]][c];
+                for (int jm = 0; jm <= k; ++jm)
+                    push_row([&](int j) {
+                        double s = 0;
+                        for (const QP& q : seg) {
+                            double x[3];
+                            for (int c = 0; c < 3; ++c) x[c] = kVert[e[0]][c] + q.x[0] * tau[c];
+                            const Vec3 v = span_val(j, x);
+                            s += q.w * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2]) * shifted_legendre(jm, q.x[0]);
+                        }
+                        return s;
+                    });
+            }
+            if (k >= 2) {
+                RefTables tmp;
+                BasisEval ev;
+                if (build_vector_2d(false, k - 1, &tmp, &ev) != 0) return -4;   // RT_{k-1}, triangle
+                std::vector<std::vector<Vec3>> pv(tri.size());
+                for (size_t qi = 0; qi < tri.size(); ++qi) ev(tri[qi].x, pv[qi]);
+                for (auto& f : kFaces) {
+                    Vec3 t1, t2;
+                    for (int c = 0; c < 3; ++c) {
+                        t1[c] = kVert[f[1]][c] - kVert[f[0]][c];
+                        t2[c] = kVert[f[2]][c] - kVert[f[0]][c];
+                    }
+                    for (int r = 0; r < tmp.nloc; ++r)
+                        push_row([&](int j) {
+                            double s = 0;
+                            for (size_t qi = 0; qi < tri.size(); ++qi) {
+                                double x[3];
+                                for (int c = 0; c < 3; ++c)
+                                    x[c] = kVert[f[0]][c] + tri[qi].x[0] * t1[c] + tri[qi].x[1] * t2[c];
+                                const Vec3 v = span_val(j, x);
+                                double w = 0;
+                                for (int c = 0; c < 3; ++c) w += v[c] * (pv[qi][r][0] * t1[c] + pv[qi][r][1] * t2[c]);
+                                s += tri[qi].w * w;
+                            }
+                            return s;
+                        });
+                }
+            }
+            if (k >= 3) {
+                RefTables tmp;
+                BasisEval ev;
+                if (build_vector(false, k - 2, &tmp, &ev) != 0) return -4;   // RT_{k-2}
+                push_interior(ev, tmp.nloc);
+            }
+        } else {
+            auto fq = orthonormal_values(tri, 0.5, triangle_monos(k));
+            for (auto& f : kFaces) {
+                Vec3 t1, t2;
+                for (int c = 0; c < 3; ++c) {
+                    t1[c] = kVert[f[1]][c] - kVert[f[0]][c];
+                    t2[c] = kVert[f[2]][c] - kVert[f[0]][c];
+                }
+                const Vec3 nrm = cross(t1, t2);
+                for (size_t r = 0; r < fq.size(); ++r)
+                    push_row([&](int j) {
+                        double s = 0;
+                        for (size_t qi = 0; qi < tri.size(); ++qi) {
+                            double x[3];
+                            for (int c = 0; c < 3; ++c)
+                                x[c] = kVert[f[0]][c] + tri[qi].x[0] * t1[c] + tri[qi].x[1] * t2[c];
+                            const Vec3 v = span_val(j, x);
+                            s += tri[qi].w * (v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2]) * fq[r][qi];
+                        }
+                        return s;
+                    });
+            }
+            if (k >= 2) {
+                RefTables tmp;
+                BasisEval ev;
+                if (build_vector(true, k - 1, &tmp, &ev) != 0) return -4;   // N1curl_{k-1}
+                push_interior(ev, tmp.nloc);
+            }
+        }
+    }
+    if ((int)A.size() != n * n) return -2;
+    std::vector<long double> C;
+    if (!lu_inverse(A, n, C)) return -3;
+    out->nloc = n;
+    out->ncomp = 3;
+    out->R.assign((size_t)9 * n * n, 0.0);
+    const auto& rule = dim == 3 ? tet : tri;
+    std::vector<Vec3> sv(n), ph(n);
+    for (const QP& q : rule) {
+        for (int j = 0; j < n; ++j) sv[j] = span_val(j, q.x);
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) {
+                long double acc = 0;
+                for (int j = 0; j < n; ++j) acc += (long double)sv[j][c] * C[(size_t)j * n + i];
+                ph[i][c] = (double)acc;
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double* R = &out->R[(size_t)(a * 3 + b) * n * n];
+                for (int i = 0; i < n; ++i) {
+                    const double wa = q.w * ph[i][a];
+                    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] += wa * ph[j][b];
+                }
+            }
+    }
+    return 0;
+}
+
 }  // namespace
 
-int n_local(int dim, int space, int order) {
+int n_local(int dim, int space, int order, int basis) {
+    if (space != 0 && basis == 1) {   // N2curl_k / BDM_k: the full P_k^dim, k = 1..3
+        if (order < 1 || order > 3 || (dim != 2 && dim != 3)) return -1;
+        return dim == 2 ? (order + 1) * (order + 2) : (order + 1) * (order + 2) * (order + 3) / 2;
+    }
     if (space == 0) {
         if (dim == 2 && order >= 1 && order <= 4) return (order + 1) * (order + 2) / 2;
         if (dim == 3 && order >= 1 && order <= 4) return (order + 1) * (order + 2) * (order + 3) / 6;
@@ -578,12 +789,13 @@ int build_bernstein(int dim, int p, RefTables* out) {
     return 0;
 }
 
-int build_reference(int dim, int space, int order, RefTables* out, int h1_basis) {
-    if (n_local(dim, space, order) < 0) return -1;
+int build_reference(int dim, int space, int order, RefTables* out, int basis) {
+    if (n_local(dim, space, order, basis) < 0) return -1;
     out->dim = dim;
     out->space = space;
     out->order = order;
-    if (space == 0) return h1_basis == 1 ? build_bernstein(dim, order, out) : build_lagrange(dim, order, out);
+    if (space == 0) return basis == 1 ? build_bernstein(dim, order, out) : build_lagrange(dim, order, out);
+    if (basis == 1) return build_second_kind(dim, space == 1, order, out);
     if (dim == 2) return build_vector_2d(space == 1, order, out);
     return build_vector(space == 1, order, out);
 }

@@ -15,8 +15,9 @@ struct RefTables {
     std::vector<double> Bdiv;
 };
 
-int n_local(int dim, int space, int order);
-// h1_basis (H1 only): 0 = Lagrange, equispaced nodes; 1 = Bernstein.
-int build_reference(int dim, int space, int order, RefTables* out, int h1_basis = 0);
+// basis: H1 0 = Lagrange (equispaced nodes), 1 = Bernstein; H(curl) / H(div) 0 = first kind
+// (N1curl_k / RT_k), 1 = second kind (N2curl_k / BDM_k).
+int n_local(int dim, int space, int order, int basis = 0);
+int build_reference(int dim, int space, int order, RefTables* out, int basis = 0);
 
 }  // namespace bras

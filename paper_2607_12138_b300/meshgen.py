@@ -21,8 +21,11 @@ Conventions (shared by every consumer; stated once here):
   faces (0,1,2),(0,1,3),(0,2,3),(1,2,3) with k(k-1) dofs each (test polynomial outer,
   tangent m = 1,2 inner), then k(k-1)(k-2)/2 interior dofs (test polynomial outer,
   component inner).  RT_k (3D): faces in the same order with k(k+1)/2 dofs each (test
-  polynomial), then interior dofs (test polynomial outer, component inner).  The dof
-  functionals themselves are defined where the elements are built.
+  polynomial), then interior dofs (test polynomial outer, component inner).  Second kind
+  (N2curl_k "n2curl", BDM_k "bdm"): the same entity order with k+1 dofs per edge
+  (N2curl; BDM on triangles), (k-1)(k+1) tangential (N2curl) or (k+1)(k+2)/2 normal (BDM)
+  dofs per face, then the interior dofs.  The dof functionals themselves are defined where
+  the elements are built.
 * Signs.  An edge moment j seen with the reversed orientation (local a->b runs from the
   higher to the lower global id) changes by ``(-1)^(j+1)``; a lowest-order face flux
   changes by the parity of the permutation that sorts the face's global ids.  Face
@@ -145,6 +148,8 @@ def h1_local_nodes(dim: int, p: int) -> list[tuple[int, ...]]:
 def n_local_dofs(space: str, dim: int, order: int) -> int:
     if space in ("h1", "h1b"):
         return math.comb(order + dim, dim)
+    if space in ("n2curl", "bdm"):                       # the full P_k^dim
+        return dim * math.comb(order + dim, dim)
     if dim == 2:
         return order * (order + 2)                       # N1curl_k and RT_k on triangles
     k = order
@@ -228,24 +233,26 @@ def _perm_parity(g: np.ndarray) -> np.ndarray:
     return s
 
 
-def _hcurl_hdiv_dof_map_2d(mesh: Mesh, k: int):
+def _hcurl_hdiv_dof_map_2d(mesh: Mesh, k: int, second: bool = False):
     """Triangles (N1curl and RT share it): k moments per edge, oriented from the lower to the
     higher global vertex id (moment j flips by (-1)^(j+1) on reversal), then k(k-1) interior
-    dofs per cell."""
+    dofs per cell.  Second kind (N2curl and BDM share it): k+1 moments per edge, then
+    (k-1)(k+1) interior dofs."""
     cells, nv = mesh.cells.astype(np.int64), mesh.n_vert
     E = cells.shape[0]
-    n_i = k * (k - 1)
+    n_i = (k - 1) * (k + 1) if second else k * (k - 1)
+    n_e = k + 1 if second else k
     cols, sgns = [], []
     g = cells[:, EDGES_2D]                               # [E, 3, 2]
     gs = np.sort(g, axis=2)
     uniq, inv = _entity_index(gs[:, :, 0] * nv + gs[:, :, 1])
     rev = g[:, :, 0] > g[:, :, 1]
     for e in range(3):
-        for j in range(k):
-            cols.append(inv[:, e] * k + j)
+        for j in range(n_e):
+            cols.append(inv[:, e] * n_e + j)
             flip = -1 if (j % 2 == 0) else 1             # (-1)^(j+1)
             sgns.append(np.where(rev[:, e], flip, 1))
-    base = uniq.size * k
+    base = uniq.size * n_e
     for j in range(n_i):
         cols.append(base + np.arange(E) * n_i + j)
         sgns.append(np.ones(E, dtype=np.int64))
@@ -257,13 +264,17 @@ def _hcurl_hdiv_dof_map_2d(mesh: Mesh, k: int):
 
 def _hcurl_hdiv_dof_map(mesh: Mesh, space: str, k: int):
     if mesh.dim == 2:
-        return _hcurl_hdiv_dof_map_2d(mesh, k)
+        return _hcurl_hdiv_dof_map_2d(mesh, k, second=space in ("n2curl", "bdm"))
     cells, nv = mesh.cells.astype(np.int64), mesh.n_vert
     E = cells.shape[0]
     if space == "hcurl":
         n_e, n_f, n_i = k, k * (k - 1), k * (k - 1) * (k - 2) // 2
-    else:
+    elif space == "hdiv":
         n_e, n_f, n_i = 0, k * (k + 1) // 2, k * (k - 1) * (k + 1) // 2
+    elif space == "n2curl":
+        n_e, n_f, n_i = k + 1, (k - 1) * (k + 1), (k - 2) * (k - 1) * (k + 1) // 2
+    else:                                                 # bdm
+        n_e, n_f, n_i = 0, (k + 1) * (k + 2) // 2, (k - 1) * (k + 1) * (k + 2) // 2
     cols, sgns = [], []
     base = 0
     if n_e:
@@ -307,7 +318,7 @@ def dof_map(mesh: Mesh, space: str, order: int):
     its trace on an entity depends only on that entity's components of alpha."""
     if space in ("h1", "h1b"):
         return _h1_dof_map(mesh, order)
-    if space in ("hcurl", "hdiv"):
+    if space in ("hcurl", "hdiv", "n2curl", "bdm"):
         return _hcurl_hdiv_dof_map(mesh, space, order)
     raise ValueError(space)
 

@@ -36,6 +36,11 @@ SMALL_CASES = {
     "hcurl4": (lambda: cube(3), "hcurl", 4),             # order 4: n_loc 84 / 70 / 24
     "hdiv4": (lambda: cube(3), "hdiv", 4),
     "hdiv2d_4_signed": (lambda: mg.relabel_mesh(square(8), seed=13), "hdiv", 4),
+    "n2curl1_signed": (lambda: mg.relabel_mesh(cube(4), seed=14), "n2curl", 1),   # second kind: n_loc 12
+    "n2curl3": (lambda: cube(3), "n2curl", 3),           # n_loc 60
+    "bdm2": (lambda: cube(3), "bdm", 2),                 # n_loc 30
+    "n2curl2d_2": (lambda: square(10), "n2curl", 2),     # n_loc 12 (triangles)
+    "bdm2d_3_signed": (lambda: mg.relabel_mesh(square(8), seed=15), "bdm", 3),   # n_loc 20
     "2d_p4_bern": (lambda: square(13), "h1b", 4),        # Bernstein basis (Table 1)
     "3d_p3_bern": (lambda: cube(5), "h1b", 3),
     "3d_p4_bern": (lambda: cube(5), "h1b", 4),

@@ -27,13 +27,19 @@ def test_library_exports_header_symbols():
 def test_host_only_entry_points():
     lib = ctypes.CDLL(LIB)
     lib.bras_n_local.restype = ctypes.c_int
-    assert [lib.bras_n_local(3, 0, p) for p in (1, 2, 3, 4)] == [4, 10, 20, 35]
-    assert [lib.bras_n_local(2, 0, p) for p in (1, 2, 3, 4)] == [3, 6, 10, 15]
-    assert [lib.bras_n_local(3, 1, k) for k in (1, 2, 3, 4)] == [6, 20, 45, 84]
-    assert [lib.bras_n_local(3, 2, k) for k in (1, 2, 3, 4)] == [4, 15, 36, 70]
-    assert [lib.bras_n_local(2, 1, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
-    assert [lib.bras_n_local(2, 2, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
-    assert lib.bras_n_local(2, 1, 5) == -1 and lib.bras_n_local(3, 2, 5) == -1 and lib.bras_n_local(3, 0, 5) == -1
+    nl = lambda d, s, k, b=0: lib.bras_n_local(d, s, k, b)
+    assert [nl(3, 0, p) for p in (1, 2, 3, 4)] == [4, 10, 20, 35]
+    assert [nl(2, 0, p) for p in (1, 2, 3, 4)] == [3, 6, 10, 15]
+    assert [nl(3, 0, p, 1) for p in (1, 2, 3, 4)] == [4, 10, 20, 35]          # Bernstein
+    assert [nl(3, 1, k) for k in (1, 2, 3, 4)] == [6, 20, 45, 84]
+    assert [nl(3, 2, k) for k in (1, 2, 3, 4)] == [4, 15, 36, 70]
+    assert [nl(2, 1, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
+    assert [nl(2, 2, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
+    for s in (1, 2):                                                             # N2curl, BDM
+        assert [nl(3, s, k, 1) for k in (1, 2, 3)] == [12, 30, 60]
+        assert [nl(2, s, k, 1) for k in (1, 2, 3)] == [6, 12, 20]
+        assert nl(3, s, 4, 1) == -1
+    assert nl(2, 1, 5) == -1 and nl(3, 2, 5) == -1 and nl(3, 0, 5) == -1
     lib.bras_status_string.restype = ctypes.c_char_p
     assert lib.bras_status_string(-5) == b"local mass matrix not SPD"
     out = ctypes.c_void_p(1)

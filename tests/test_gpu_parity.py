@@ -44,7 +44,7 @@ def _vec(n, nrhs=1, seed=5, dtype=torch.float64):
     return x, torch.as_tensor(x, dtype=dtype, device="cuda")
 
 
-TOL32 = {"h1": 2e-5, "h1b": 2e-5, "hcurl": 1e-4, "hdiv": 1e-4}
+TOL32 = {"h1": 2e-5, "h1b": 2e-5, "hcurl": 1e-4, "hdiv": 1e-4, "n2curl": 1e-4, "bdm": 1e-4}
 
 
 @pytest.mark.parametrize("case", sorted(SMALL_CASES))
@@ -70,7 +70,7 @@ def test_fp32_and_bf16_applies(case):
 
 
 @pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2", "3d_p3", "3d_p4", "hcurl3", "hdiv3",
-                                  "hcurl4"])
+                                  "hcurl4", "bdm2", "n2curl3"])
 @pytest.mark.parametrize("nrhs", [2, 3, 5, 8])
 def test_multi_rhs_interleaved(case, nrhs):
     """[n][R] vectors: chunks of up to 4 right-hand sides per CTA (ragged last chunk for R = 3, 5),
@@ -297,7 +297,7 @@ def _batch(space, order, sizes, seed0=10):
     return meshes, probs
 
 
-@pytest.mark.parametrize("space,order", [("hdiv", 1), ("hdiv", 2), ("h1", 2)])
+@pytest.mark.parametrize("space,order", [("hdiv", 1), ("hdiv", 2), ("h1", 2), ("n2curl", 1)])
 def test_batched_multi_mesh(space, order):
     """Several uneven meshes in one context: applies equal the per-mesh oracle operators and
     one solve reaches each mesh's own tolerance with the oracle's iteration count."""

@@ -31,13 +31,14 @@ def _problem(mesh, space, order, rho=None):
 
 
 @pytest.mark.parametrize("space,order", [("h1", 2), ("h1", 4), ("hcurl", 2), ("hcurl", 3), ("hcurl", 4), ("hdiv", 3),
-                                         ("hdiv", 4)])
+                                         ("hdiv", 4), ("n2curl", 3), ("bdm", 3)])
 def test_one_element_is_exact_inverse(space, order):
     pr = _problem(mg.single_simplex_mesh(3, seed=2), space, order)
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
 
 
-@pytest.mark.parametrize("space,order", [("hcurl", 1), ("hcurl", 3), ("hdiv", 2), ("hcurl", 4), ("hdiv", 4)])
+@pytest.mark.parametrize("space,order", [("hcurl", 1), ("hcurl", 3), ("hdiv", 2), ("hcurl", 4), ("hdiv", 4),
+                                         ("n2curl", 2), ("bdm", 3)])
 def test_one_triangle_is_exact_inverse(space, order):
     pr = _problem(mg.single_simplex_mesh(2, seed=2), space, order)
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())
@@ -52,7 +53,10 @@ CASES = [(mg.unit_square_mesh(5, jitter=0.2, seed=4), "h1", 2),
          (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=6), seed=7), "hcurl", 2),
          (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=8), seed=9), "hdiv", 3),
          (mg.unit_cube_mesh(2, jitter=0.1, seed=10), "hcurl", 4),
-         (mg.unit_cube_mesh(2, jitter=0.1, seed=11), "hdiv", 4)]
+         (mg.unit_cube_mesh(2, jitter=0.1, seed=11), "hdiv", 4),
+         (mg.relabel_mesh(mg.unit_cube_mesh(2, jitter=0.1), seed=12), "n2curl", 1),
+         (mg.unit_cube_mesh(2, jitter=0.1, seed=13), "bdm", 2),
+         (mg.relabel_mesh(mg.unit_square_mesh(4, jitter=0.2, seed=14), seed=15), "bdm", 3)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -181,6 +185,14 @@ KAPPA_MESHES = {
     "h1b_3d_p2": (lambda: mg.unit_cube_mesh(6), "h1b", 2),
     "h1b_3d_p3": (lambda: mg.unit_cube_mesh(4), "h1b", 3),
     "h1b_3d_p4": (lambda: mg.unit_cube_mesh(4), "h1b", 4),
+    "n2curl_2d_k1": (lambda: mg.unit_square_mesh(24), "n2curl", 1),
+    "n2curl_2d_k2": (lambda: mg.unit_square_mesh(16), "n2curl", 2),
+    "n2curl_3d_k1": (lambda: mg.unit_cube_mesh(5), "n2curl", 1),
+    "n2curl_3d_k2": (lambda: mg.unit_cube_mesh(3), "n2curl", 2),
+    "bdm_2d_k1": (lambda: mg.unit_square_mesh(24), "bdm", 1),
+    "bdm_2d_k2": (lambda: mg.unit_square_mesh(16), "bdm", 2),
+    "bdm_3d_k1": (lambda: mg.unit_cube_mesh(5), "bdm", 1),
+    "bdm_3d_k2": (lambda: mg.unit_cube_mesh(3), "bdm", 2),
 }
 
 

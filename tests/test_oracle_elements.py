@@ -122,9 +122,9 @@ def _field(mesh, space, order, l2g, signs, coef, k, x):
     vals = ref.evaluate(xh)                             # [pts, n_loc, comp]
     loc = s * coef[l2g[k]]
     u = np.einsum("pnc,n->pc", vals, loc)
-    if space == "hcurl":
+    if space in ("hcurl", "n2curl"):
         return u @ np.linalg.inv(J)                     # J^{-T} u (row vectors)
-    if space == "hdiv":
+    if space in ("hdiv", "bdm"):
         return u @ J.T / np.linalg.det(J)
     return u
 
@@ -151,7 +151,9 @@ def test_bernstein_closed_forms(dim, p):
     ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False), ("h1b", 3, False), ("h1b", 4, False),
     ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True), ("hcurl", 4, True),
     ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True), ("hdiv", 4, True),
-    ("hcurl", 2, False)])
+    ("hcurl", 2, False),
+    ("n2curl", 1, False), ("n2curl", 2, True), ("n2curl", 3, True), ("bdm", 1, True), ("bdm", 2, True),
+    ("bdm", 3, True)])
 def test_conformity_across_shared_face(space, order, sort):
     if space == "hcurl" and order == 2 and not sort:
         with pytest.raises(ValueError):
@@ -172,7 +174,7 @@ def test_conformity_across_shared_face(space, order, sort):
         u1 = _field(mesh, space, order, l2g, signs, coef, 1, x)
         if space in ("h1", "h1b"):
             np.testing.assert_allclose(u0, u1, atol=1e-10)
-        elif space == "hcurl":
+        elif space in ("hcurl", "n2curl"):
             t0 = u0 - np.outer(u0 @ nrm, nrm)
             t1 = u1 - np.outer(u1 @ nrm, nrm)
             np.testing.assert_allclose(t0, t1, atol=1e-10)
@@ -190,8 +192,8 @@ def _two_triangles(seed, sort=True):
     return mg.Mesh(coords, cells, 2)
 
 
-@pytest.mark.parametrize("space", ["hcurl", "hdiv"])
-@pytest.mark.parametrize("order", [1, 2, 3, 4])
+@pytest.mark.parametrize("space,order", [(s, k) for s in ("hcurl", "hdiv") for k in (1, 2, 3, 4)]
+                         + [(s, k) for s in ("n2curl", "bdm") for k in (1, 2, 3)])
 @pytest.mark.parametrize("sort", [True, False])
 def test_conformity_across_shared_edge_2d(space, order, sort):
     mesh = _two_triangles(3, sort)
@@ -212,8 +214,8 @@ def test_conformity_across_shared_edge_2d(space, order, sort):
             xh = np.linalg.solve(J, (x - X[0]).T).T
             loc = signs[k].astype(float) * coef[l2g[k]]
             v = np.einsum("pnc,n->pc", ref.evaluate(xh), loc)
-            u.append(v @ np.linalg.inv(J) if space == "hcurl" else v @ J.T / np.linalg.det(J))
-        if space == "hcurl":
+            u.append(v @ np.linalg.inv(J) if space in ("hcurl", "n2curl") else v @ J.T / np.linalg.det(J))
+        if space in ("hcurl", "n2curl"):
             np.testing.assert_allclose(u[0] @ t, u[1] @ t, atol=1e-10)
             assert np.abs(u[0] - u[1]).max() > 1e-6
         else:
@@ -236,3 +238,67 @@ def test_rt_is_rotated_nedelec_2d(order):
         i0, i1 = 3 * k + 2 * r, 3 * k + 2 * r + 1
         expect[:, i0], expect[:, i1] = rot[:, i1], -rot[:, i0]
     np.testing.assert_allclose(vd, expect, atol=1e-12)
+
+
+def _simplex_rule(dim, n=6):
+    """Collapsed Gauss-Legendre rule on the reference simplex (exact to degree 2n - 2 - dim)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = (x + 1) / 2, w / 2
+    if dim == 2:
+        u, v = np.meshgrid(x, x, indexing="ij")
+        W = np.outer(w, w) * (1 - u)
+        return np.stack([u.ravel(), (v * (1 - u)).ravel()], 1), W.ravel()
+    u, v, t = np.meshgrid(x, x, x, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :] * (1 - u) ** 2 * (1 - v)
+    return np.stack([u.ravel(), (v * (1 - u)).ravel(), (t * (1 - u) * (1 - v)).ravel()], 1), W.ravel()
+
+
+@pytest.mark.parametrize("space", ["n2curl", "bdm", "hcurl", "hdiv"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_second_kind_reproduces_full_polynomials(space, dim):
+    """N2curl_k and BDM_k contain the whole P_k^d: the L2 projection (M c = int phi . f) of a
+    random vector field of degree k = 2 onto the assembled space on a jittered mesh gives f back
+    at random points.  The first kinds (N1curl_2, RT_2) contain only part of P_2^d, so the same
+    projection misses f by a visible amount."""
+    k = 2
+    mesh = mg.unit_square_mesh(2, jitter=0.2, seed=3) if dim == 2 else mg.unit_cube_mesh(1, jitter=0.15, seed=3)
+    n, l2g, signs = mg.dof_map(mesh, space, k)
+    ref = elements.reference_element(space, dim, k)
+    rng = np.random.default_rng(4)
+    from oracle.polynomials import monomials
+    ms = monomials(dim, k)
+    coef_f = rng.standard_normal((dim, len(ms)))
+    f = lambda x: np.stack([np.prod(x[:, None, :] ** np.array(ms)[None], axis=2) @ coef_f[c] for c in range(dim)], 1)
+    qx, qw = _simplex_rule(dim)
+    vals = ref.evaluate(qx)                                # [q, n_loc, dim]
+    M = np.zeros((n, n))
+    b = np.zeros(n)
+    maps = []
+    for K in range(mesh.n_cell):
+        X = mesh.coords[mesh.cells[K]]
+        J = (X[1:] - X[0]).T
+        dJ = np.linalg.det(J)
+        s = np.ones(l2g.shape[1]) if signs is None else signs[K].astype(float)
+        phys = vals @ np.linalg.inv(J) if space in ("hcurl", "n2curl") else vals @ J.T / dJ
+        phys = phys * s[None, :, None]
+        xq = qx @ J.T + X[0]
+        w = qw * abs(dJ)
+        Mk = np.einsum("q,qic,qjc->ij", w, phys, phys)
+        bk = np.einsum("q,qic,qc->i", w, phys, f(xq))
+        idx = l2g[K]
+        M[np.ix_(idx, idx)] += Mk
+        np.add.at(b, idx, bk)
+        maps.append((X, J, phys, idx, s))
+    c = np.linalg.solve(M, b)
+    err = 0.0
+    for K, (X, J, _, idx, s) in enumerate(maps):
+        xh = rng.dirichlet(np.ones(dim + 1), size=10)[:, 1:]
+        v = ref.evaluate(xh)
+        phys = v @ np.linalg.inv(J) if space in ("hcurl", "n2curl") else v @ J.T / np.linalg.det(J)
+        u = np.einsum("pnc,n->pc", phys, s * c[idx])
+        err = max(err, np.abs(u - f(xh @ J.T + X[0])).max())
+    scale = np.abs(coef_f).max()
+    if space in ("n2curl", "bdm"):
+        assert err <= 1e-9 * scale
+    else:
+        assert err >= 1e-3 * scale
