@@ -282,12 +282,13 @@ int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, dou
  * bras_schur_apply -- y = -S~ x = B M_bras^{-1} B^T x, the BRAS approximation of the positive
  * Schur complement of the mixed Poisson saddle point [[M, B^T], [B, 0]] (Sec. 4,
  * Eq. approx_positive_schur_general with C = 0; Sec. 5.1), matrix-free: the divergence and its
- * transpose element by element, the BRAS apply in between.  Pair: RT_k (this context, H(div) on
- * tetrahedra) with DG_{k-1}; B_ij = (div phi_j, chi_i), chi_i = chi^_i o F_K^{-1}, chi^_i the
+ * transpose element by element, the BRAS apply in between.  Pair: RT_k (k = 1..4) or BDM_k
+ * (k = 1..3, bras_options.basis = 1; the pair of Sec. 5.1) -- this context, H(div) on
+ * tetrahedra -- with DG_{k-1}; B_ij = (div phi_j, chi_i), chi_i = chi^_i o F_K^{-1}, chi^_i the
  * polynomials of degree <= k - 1 orthonormal for the mean inner product on the reference
  * tetrahedron (Gram-Schmidt of the monomials by degree, then descending lexicographic
- * exponents), so cell K's block is sign(det J_K) B^.  (The paper's experiments pair BDM with DG;
- * the spectrum of S~^{-1} S does not depend on the DG basis.)
+ * exponents), so cell K's block is sign(det J_K) B^.  (The spectrum of S~^{-1} S does not
+ * depend on the DG basis.)
  *   x, y   [n_cell * n_q] of double (BRAS_FP64) or float (BRAS_FP32 / BRAS_BF16), cell K's
  *          n_q = k (k + 1) (k + 2) / 6 values at K * n_q, cells in the caller's order; one
  *          right-hand side; not on a batched context.

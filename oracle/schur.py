@@ -5,8 +5,8 @@ B_ij = (div phi_j, chi_i) (Sec. 5.1).  Eliminating sigma gives the positive Schu
 -S = B M^{-1} B^T (Eq. positive_schur_general with C = 0), and replacing M^{-1} by the BRAS
 approximation gives -S~ = B M_bras^{-1} B^T (Eq. approx_positive_schur_general).
 
-Pair (a reading: the paper's experiments use BDM_p / DG_{p-1}, which this project does not
-build): RT_k / DG_{k-1} on tetrahedra.  Q basis: on the reference tetrahedron the polynomials of
+Pairs: BDM_k / DG_{k-1} (the pair of Sec. 5.1) and RT_k / DG_{k-1} on tetrahedra (div maps
+both onto P_{k-1}).  Q basis: on the reference tetrahedron the polynomials of
 degree <= k-1 orthonormal for the mean inner product (Gram-Schmidt of the monomials in the
 order of ``monomials(3, .)``), mapped without a Piola transform (chi = chi^ o F^{-1}).  The
 conforming H(div) space is the contravariant Piola one, phi = J phi^ / det J (the mass matrices
@@ -33,10 +33,10 @@ def n_dg(order_rt: int) -> int:
     return k * (k + 1) * (k + 2) // 6
 
 
-def reference_divergence(k: int) -> np.ndarray:
-    """B^ [n_dg, n_loc]: exact divergence of the RT_k basis (monomial coefficients) against the
-    orthonormal Q basis, integrated exactly."""
-    ref = reference_element("hdiv", 3, k)
+def reference_divergence(k: int, space: str = "hdiv") -> np.ndarray:
+    """B^ [n_dg, n_loc]: exact divergence of the RT_k ("hdiv") or BDM_k ("bdm") basis (monomial
+    coefficients) against the orthonormal Q basis, integrated exactly."""
+    ref = reference_element(space, 3, k)
     ms = monomials(3, k)
     idx = {m: i for i, m in enumerate(ms)}
     nm = len(ms)
@@ -62,9 +62,9 @@ def reference_divergence(k: int) -> np.ndarray:
     return B
 
 
-def divergence_matrix(mesh, l2g, signs, n_dof: int, k: int) -> sp.csr_matrix:
+def divergence_matrix(mesh, l2g, signs, n_dof: int, k: int, space: str = "hdiv") -> sp.csr_matrix:
     """Global B [n_cell * n_dg, n_dof]: cell K's DG dofs are rows K * n_dg .. K * n_dg + n_dg - 1."""
-    Bh = reference_divergence(k)
+    Bh = reference_divergence(k, space)
     E, nloc = l2g.shape
     nq = Bh.shape[0]
     sdet = np.sign(np.linalg.det(jacobians(mesh.coords, mesh.cells)))

@@ -717,6 +717,34 @@ int build_second_kind(int dim, bool curl, int k, RefTables* out) {
     out->nloc = n;
     out->ncomp = 3;
     out->R.assign((size_t)9 * n * n, 0.0);
+    if (!curl && dim == 3) {
+        // divergence block of the mixed Poisson pair BDM_k / DG_{k-1}: div(x^m e_c) =
+        // m_c x^(m - e_c), against the mean-orthonormal polynomials of degree <= k - 1
+        const auto chi = orthonormal_values(tet, 1.0 / 6.0, tet_monos(k - 1));
+        const int nq = (int)chi.size();
+        out->nq = nq;
+        out->Bdiv.assign((size_t)nq * n, 0.0);
+        std::vector<double> dv(n);
+        for (size_t qi = 0; qi < tet.size(); ++qi) {
+            const double* x = tet[qi].x;
+            for (int j = 0; j < n; ++j) {
+                const int c = j / nm;
+                const auto& m = monos[j % nm];
+                double v = 0;
+                if (m[c] > 0) {
+                    v = m[c];
+                    for (int d = 0; d < 3; ++d)
+                        for (int e = 0; e < m[d] - (d == c ? 1 : 0); ++e) v *= x[d];
+                }
+                dv[j] = v;
+            }
+            for (int jj = 0; jj < n; ++jj) {   // divergence of the nodal function jj
+                long double d = 0;
+                for (int j = 0; j < n; ++j) d += (long double)dv[j] * C[(size_t)j * n + jj];
+                for (int i = 0; i < nq; ++i) out->Bdiv[(size_t)i * n + jj] += tet[qi].w * (double)d * chi[i][qi];
+            }
+        }
+    }
     const auto& rule = dim == 3 ? tet : tri;
     std::vector<Vec3> sv(n), ph(n);
     for (const QP& q : rule) {

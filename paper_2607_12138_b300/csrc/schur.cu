@@ -1,6 +1,6 @@
 // Matrix-free Schur complement of the mixed Poisson saddle point (Sec. 4, Sec. 5.1):
 //   -S~ x = B M_bras^{-1} B^T x   (Eq. approx_positive_schur_general with C = 0)
-// for the pair RT_k / DG_{k-1} on tetrahedra.  B's block of cell K is sign(det J_K) B^ with
+// for the pairs RT_k / DG_{k-1} and BDM_k / DG_{k-1} (the pair of Sec. 5.1) on tetrahedra.  B's block of cell K is sign(det J_K) B^ with
 // B^_ij = int_ref div phi_j chi_i (the contravariant Piola map makes div phi = div^ phi^ / det J),
 // chi_i the mean-orthonormal polynomials of degree <= k - 1 on the reference tetrahedron.
 //   1. copies w_(K,a) = s_(K,a) (B^T x_K)_a, written to their slots in dof-sorted order;
@@ -17,16 +17,11 @@
 namespace bras {
 namespace {
 
-template <int K> struct RtShape {
-    static constexpr int NLOC = K * (K + 1) * (K + 3) / 2;
-    static constexpr int NQ = K * (K + 1) * (K + 2) / 6;
-};
-
-template <int K, typename T>
+// NLOC: local H(div) dofs (RT_k or BDM_k), NQ: local DG_{k-1} dofs
+template <int NLOC, int NQ, typename T>
 __global__ void __launch_bounds__(256) k_schur_bt(int64_t E, const T* __restrict__ Bd, const T* __restrict__ x,
                                                   const int8_t* __restrict__ sgn, const int32_t* __restrict__ pos,
                                                   T* __restrict__ wb) {
-    constexpr int NLOC = RtShape<K>::NLOC, NQ = RtShape<K>::NQ;
     __shared__ T Bs[NQ * NLOC];
     for (int i = threadIdx.x; i < NQ * NLOC; i += blockDim.x) Bs[i] = Bd[i];
     __syncthreads();
@@ -54,11 +49,10 @@ __global__ void k_copy_sums(int64_t n, const int64_t* __restrict__ off, const T*
     }
 }
 
-template <int K, typename T>
+template <int NLOC, int NQ, typename T>
 __global__ void __launch_bounds__(256) k_schur_b(int64_t E, const T* __restrict__ Bd, const T* __restrict__ z,
                                                  const int32_t* __restrict__ l2g, const int8_t* __restrict__ sgn,
                                                  T* __restrict__ y) {
-    constexpr int NLOC = RtShape<K>::NLOC, NQ = RtShape<K>::NQ;
     __shared__ T Bs[NQ * NLOC];
     for (int i = threadIdx.x; i < NQ * NLOC; i += blockDim.x) Bs[i] = Bd[i];
     __syncthreads();
@@ -81,9 +75,8 @@ __global__ void __launch_bounds__(256) k_schur_b(int64_t E, const T* __restrict_
 
 int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16)); }
 
-template <int K, typename T>
+template <int NLOC, int NQ, typename T>
 int schur_typed(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
-    constexpr int NLOC = RtShape<K>::NLOC;
     const size_t copies = (size_t)c->E * NLOC;
     const size_t need = 8 * (copies + 2 * (size_t)c->n);
     if (c->schur_ws_bytes < need) {
@@ -96,24 +89,28 @@ int schur_typed(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
     T* t = wb + copies;
     T* z = t + c->n;
     const T* Bd = sizeof(T) == 8 ? reinterpret_cast<const T*>(c->Bdiv64) : reinterpret_cast<const T*>(c->Bdiv32);
-    k_schur_bt<K, T><<<grid_of(c->E), 256, 0, st>>>(c->E, Bd, x, c->sgn_user, c->cpos, wb);
+    k_schur_bt<NLOC, NQ, T><<<grid_of(c->E), 256, 0, st>>>(c->E, Bd, x, c->sgn_user, c->cpos, wb);
     k_copy_sums<T><<<grid_of(c->n), 256, 0, st>>>(c->n, c->coff, wb, t);
     count_launch(2);
     if (cudaGetLastError() != cudaSuccess) return BRAS_ERR_CUDA;
     int rc = run_op(c, prec, OP_BRAS, t, z, 1, st);
     if (rc != BRAS_OK) return rc;
-    k_schur_b<K, T><<<grid_of(c->E), 256, 0, st>>>(c->E, Bd, z, c->l2g_user, c->sgn_user, y);
+    k_schur_b<NLOC, NQ, T><<<grid_of(c->E), 256, 0, st>>>(c->E, Bd, z, c->l2g_user, c->sgn_user, y);
     count_launch(1);
     return cudaGetLastError() == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
 }
 
+// n_loc names the family and order on tetrahedra: RT_k 4 / 15 / 36 / 70, BDM_k 12 / 30 / 60
 template <typename T>
 int schur_order(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
-    switch (c->order) {
-        case 1: return schur_typed<1, T>(c, prec, x, y, st);
-        case 2: return schur_typed<2, T>(c, prec, x, y, st);
-        case 3: return schur_typed<3, T>(c, prec, x, y, st);
-        case 4: return schur_typed<4, T>(c, prec, x, y, st);
+    switch (c->nloc) {
+        case 4: return schur_typed<4, 1, T>(c, prec, x, y, st);
+        case 15: return schur_typed<15, 4, T>(c, prec, x, y, st);
+        case 36: return schur_typed<36, 10, T>(c, prec, x, y, st);
+        case 70: return schur_typed<70, 20, T>(c, prec, x, y, st);
+        case 12: return schur_typed<12, 1, T>(c, prec, x, y, st);
+        case 30: return schur_typed<30, 4, T>(c, prec, x, y, st);
+        case 60: return schur_typed<60, 10, T>(c, prec, x, y, st);
         default: return BRAS_ERR_INVALID;
     }
 }

@@ -458,15 +458,15 @@ def test_cg_lanczos_kappa(case):
     assert k < 400 and lo >= 1.0 - 1e-9                             # lambda_min >= 1 for BRAS
 
 
-@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3", "hdiv4"])
+@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3", "hdiv4", "bdm2"])
 def test_schur_complement_apply(case):
-    """-S~ x = B M_bras^{-1} B^T x (mixed Poisson, RT_k / DG_{k-1}) against the oracle's
+    """-S~ x = B M_bras^{-1} B^T x (mixed Poisson, RT_k or BDM_k / DG_{k-1}) against the oracle's
     assembled B and BRAS, in FP64 and FP32; other spaces are rejected."""
     from oracle.schur import divergence_matrix, n_dg, schur_bras
     mesh, pr, ctx = _setup(case)
-    k = SMALL_CASES[case][2]
-    n, l2g, signs = mg.dof_map(mesh, "hdiv", k)
-    St = schur_bras(divergence_matrix(mesh, l2g, signs, n, k), pr.B)
+    space, k = SMALL_CASES[case][1], SMALL_CASES[case][2]
+    n, l2g, signs = mg.dof_map(mesh, space, k)
+    St = schur_bras(divergence_matrix(mesh, l2g, signs, n, k, space), pr.B)
     x = np.random.default_rng(7).standard_normal(mesh.n_cell * n_dg(k))
     xt = torch.as_tensor(x, device="cuda")
     ref = St @ x

@@ -7,6 +7,9 @@
   of c is det J J^{-1} c, and the
   interpolant's face moments are c . (t1 x t2) / 2 for the lowest face polynomial, 0 for the
   others);
+* BDM_k / DG_{k-1} (the pair of Sec. 5.1): the L2 projection of a constant field onto BDM_k
+  reproduces it (BDM_k holds all of P_k^3), so B annihilates it, and B is onto DG_{k-1} on a
+  mesh (div maps BDM_k onto P_{k-1} cell by cell);
 * on one cell BRAS = M^{-1}, so -S~ = -S;
 * the bound of Sec. 4: if the mass pencil's eigenvalues lie in [a, b] then those of
   S~^{-1} S lie in [1/b, 1/a] (for BRAS, a >= 1, so S~^{-1} S <= 1).
@@ -21,9 +24,9 @@ from oracle.solvers import pencil_eigs
 from paper_2607_12138_b300 import meshgen as mg
 
 
-def _problem(mesh, k):
-    n, l2g, s = mg.dof_map(mesh, "hdiv", k)
-    return Problem(mesh, "hdiv", k, l2g, s, n), l2g, s, n
+def _problem(mesh, k, space="hdiv"):
+    n, l2g, s = mg.dof_map(mesh, space, k)
+    return Problem(mesh, space, k, l2g, s, n), l2g, s, n
 
 
 def test_lowest_order_divergence_closed_form():
@@ -79,3 +82,47 @@ def test_schur_spectrum_within_mass_bounds(k, cells):
     ev = pencil_eigs(St, np.linalg.inv(S))               # eigenvalues of (-S)^{-1}(-S~) = 1 / those of S~^{-1} S
     assert ev[0] >= mass_ev[0] * (1 - 1e-9) and ev[-1] <= mass_ev[-1] * (1 + 1e-9)
     assert ev[0] >= 1 - 1e-9                             # S~^{-1} S <= 1 for BRAS
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_bdm_divergence_kernel_and_range(k):
+    mesh = mg.unit_cube_mesh(2, jitter=0.15, seed=k)
+    pr, l2g, s, n = _problem(mesh, k, "bdm")
+    B = divergence_matrix(mesh, l2g, s, n, k, "bdm")
+    assert B.shape == (mesh.n_cell * n_dg(k), n)
+    # L2 projection of the constant field c: M x = int phi . c, cell by cell with the reference
+    # mass blocks (phi . c is linear in phi, so int_K phi_i . c = c . (pulled-back moments))
+    from oracle.elements import reference_element
+    from oracle.polynomials import monomials, simplex_monomial_integral
+    ref = reference_element("bdm", 3, k)
+    ms = monomials(3, k)
+    mom = ref.phi.reshape(3, len(ms), ref.n_loc)
+    ints = np.array([float(simplex_monomial_integral(m)) for m in ms])
+    phi_int = np.einsum("cij,i->jc", mom, ints)            # int_ref phi^_j, [n_loc, 3]
+    J = jacobians(mesh.coords, mesh.cells)
+    c = np.array([0.4, -1.3, 0.9])
+    b = np.zeros(n)
+    for K in range(mesh.n_cell):
+        # phi = J phi^ / det J, dx = |det J| dx^  ->  int_K phi . c = sign(det J) (J phi^_int) . c
+        v = np.sign(np.linalg.det(J[K])) * (phi_int @ J[K].T) @ c
+        np.add.at(b, l2g[K], s[K] * v)
+    x = np.linalg.solve(pr.M.toarray(), b)
+    assert np.abs(B @ x).max() <= 1e-10 * np.abs(x).max()
+    assert np.linalg.matrix_rank(B.toarray()) == B.shape[0]
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_bdm_one_cell_schur_is_exact(k):
+    mesh = mg.single_simplex_mesh(3, seed=6)
+    pr, l2g, s, n = _problem(mesh, k, "bdm")
+    B = divergence_matrix(mesh, l2g, s, n, k, "bdm")
+    np.testing.assert_allclose(schur_bras(B, pr.B).toarray(), schur_exact_dense(B, pr.M), rtol=1e-9, atol=1e-12)
+
+
+def test_bdm_schur_spectrum_within_mass_bounds():
+    mesh = mg.unit_cube_mesh(2, jitter=0.15, seed=9)
+    pr, l2g, s, n = _problem(mesh, 2, "bdm")
+    B = divergence_matrix(mesh, l2g, s, n, 2, "bdm")
+    mass_ev = pencil_eigs(pr.M.toarray(), pr.B.toarray())
+    ev = pencil_eigs(schur_bras(B, pr.B).toarray(), np.linalg.inv(schur_exact_dense(B, pr.M)))
+    assert ev[0] >= mass_ev[0] * (1 - 1e-9) and ev[-1] <= mass_ev[-1] * (1 + 1e-9)
