@@ -23,7 +23,7 @@
  *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.basis) P_p
  *    on triangles (dim 2) or tetrahedra (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind
  *    and BRAS_HDIV = Raviart-Thomas, order k = 1..4, or with bras_options.basis = 1 the
- *    second kinds N2curl and BDM (the full P_k^dim, k = 1..3; Tables 2-3), on triangles or
+ *    second kinds N2curl and BDM (the full P_k^dim, k = 1..4; Tables 2-3), on triangles or
  *    tetrahedra, mapped by
  *    the covariant / contravariant Piola maps (Sec. 2.4, Eq. piola_mass_pullbacks) with
  *    |det J|.  Local dof order and dof functionals are the ones documented with the mesh
@@ -95,7 +95,7 @@ typedef struct {
                             1 = Bernstein (B_alpha = p!/alpha! prod lambda_i^alpha_i, the
                             "Bernstein" family of Table 1); same multi-indices, same l2g.
                             BRAS_HCURL / BRAS_HDIV: 0 = first kind (N1curl_k / RT_k),
-                            1 = second kind (N2curl_k / BDM_k, k = 1..3)                  */
+                            1 = second kind (N2curl_k / BDM_k, k = 1..4)                  */
     int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for every cell
                             block size (multiples of 32 up to 256) whose kernels fit shared
                             memory and keep the fastest (one table build and four applies per
@@ -282,8 +282,8 @@ int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, dou
  * bras_schur_apply -- y = -S~ x = B M_bras^{-1} B^T x, the BRAS approximation of the positive
  * Schur complement of the mixed Poisson saddle point [[M, B^T], [B, 0]] (Sec. 4,
  * Eq. approx_positive_schur_general with C = 0; Sec. 5.1), matrix-free: the divergence and its
- * transpose element by element, the BRAS apply in between.  Pair: RT_k (k = 1..4) or BDM_k
- * (k = 1..3, bras_options.basis = 1; the pair of Sec. 5.1) -- this context, H(div) on
+ * transpose element by element, the BRAS apply in between.  Pair: RT_k or BDM_k (k = 1..4,
+ * BDM with bras_options.basis = 1; the pair of Sec. 5.1) -- this context, H(div) on
  * tetrahedra -- with DG_{k-1}; B_ij = (div phi_j, chi_i), chi_i = chi^_i o F_K^{-1}, chi^_i the
  * polynomials of degree <= k - 1 orthonormal for the mean inner product on the reference
  * tetrahedron (Gram-Schmidt of the monomials by degree, then descending lexicographic

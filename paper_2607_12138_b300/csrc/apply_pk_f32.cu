@@ -37,6 +37,8 @@ cudaError_t launch_pk_f32(const LaunchCommon& L, int nloc, int op, const float* 
     BRAS_CASE(30, OP_BRAS)
     BRAS_CASE(60, OP_MASS)
     BRAS_CASE(60, OP_BRAS)
+    BRAS_CASE(105, OP_MASS)
+    BRAS_CASE(105, OP_BRAS)
 #undef BRAS_CASE
     return cudaErrorInvalidValue;
 }

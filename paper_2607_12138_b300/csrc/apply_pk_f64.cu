@@ -51,6 +51,9 @@ cudaError_t launch_pk_f64(const LaunchCommon& L, int nloc, int op, const double*
     BRAS_CASE(60, OP_MASS)
     BRAS_CASE(60, OP_BRAS)
     BRAS_CASE(60, OP_DIAG)
+    BRAS_CASE(105, OP_MASS)
+    BRAS_CASE(105, OP_BRAS)
+    BRAS_CASE(105, OP_DIAG)
 #undef BRAS_CASE
     return cudaErrorInvalidValue;
 }

@@ -770,8 +770,8 @@ int build_second_kind(int dim, bool curl, int k, RefTables* out) {
 }  // namespace
 
 int n_local(int dim, int space, int order, int basis) {
-    if (space != 0 && basis == 1) {   // N2curl_k / BDM_k: the full P_k^dim, k = 1..3
-        if (order < 1 || order > 3 || (dim != 2 && dim != 3)) return -1;
+    if (space != 0 && basis == 1) {   // N2curl_k / BDM_k: the full P_k^dim, k = 1..4
+        if (order < 1 || order > 4 || (dim != 2 && dim != 3)) return -1;
         return dim == 2 ? (order + 1) * (order + 2) : (order + 1) * (order + 2) * (order + 3) / 2;
     }
     if (space == 0) {

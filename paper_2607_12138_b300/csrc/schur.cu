@@ -100,7 +100,7 @@ int schur_typed(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
 }
 
-// n_loc names the family and order on tetrahedra: RT_k 4 / 15 / 36 / 70, BDM_k 12 / 30 / 60
+// n_loc names the family and order on tetrahedra: RT_k 4 / 15 / 36 / 70, BDM_k 12 / 30 / 60 / 105
 template <typename T>
 int schur_order(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
     switch (c->nloc) {
@@ -111,6 +111,7 @@ int schur_order(bras_ctx* c, int prec, const T* x, T* y, cudaStream_t st) {
         case 12: return schur_typed<12, 1, T>(c, prec, x, y, st);
         case 30: return schur_typed<30, 4, T>(c, prec, x, y, st);
         case 60: return schur_typed<60, 10, T>(c, prec, x, y, st);
+        case 105: return schur_typed<105, 20, T>(c, prec, x, y, st);
         default: return BRAS_ERR_INVALID;
     }
 }

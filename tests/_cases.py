@@ -41,6 +41,9 @@ SMALL_CASES = {
     "bdm2": (lambda: cube(3), "bdm", 2),                 # n_loc 30
     "n2curl2d_2": (lambda: square(10), "n2curl", 2),     # n_loc 12 (triangles)
     "bdm2d_3_signed": (lambda: mg.relabel_mesh(square(8), seed=15), "bdm", 3),   # n_loc 20
+    "bdm4": (lambda: cube(2), "bdm", 4),                 # n_loc 105
+    "n2curl4": (lambda: cube(2), "n2curl", 4),
+    "n2curl2d_4": (lambda: square(6), "n2curl", 4),      # n_loc 30
     "2d_p4_bern": (lambda: square(13), "h1b", 4),        # Bernstein basis (Table 1)
     "3d_p3_bern": (lambda: cube(5), "h1b", 3),
     "3d_p4_bern": (lambda: cube(5), "h1b", 4),

@@ -36,9 +36,9 @@ def test_host_only_entry_points():
     assert [nl(2, 1, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
     assert [nl(2, 2, k) for k in (1, 2, 3, 4)] == [3, 8, 15, 24]
     for s in (1, 2):                                                             # N2curl, BDM
-        assert [nl(3, s, k, 1) for k in (1, 2, 3)] == [12, 30, 60]
-        assert [nl(2, s, k, 1) for k in (1, 2, 3)] == [6, 12, 20]
-        assert nl(3, s, 4, 1) == -1
+        assert [nl(3, s, k, 1) for k in (1, 2, 3, 4)] == [12, 30, 60, 105]
+        assert [nl(2, s, k, 1) for k in (1, 2, 3, 4)] == [6, 12, 20, 30]
+        assert nl(3, s, 5, 1) == -1
     assert nl(2, 1, 5) == -1 and nl(3, 2, 5) == -1 and nl(3, 0, 5) == -1
     lib.bras_status_string.restype = ctypes.c_char_p
     assert lib.bras_status_string(-5) == b"local mass matrix not SPD"

@@ -458,7 +458,7 @@ def test_cg_lanczos_kappa(case):
     assert k < 400 and lo >= 1.0 - 1e-9                             # lambda_min >= 1 for BRAS
 
 
-@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3", "hdiv4", "bdm2"])
+@pytest.mark.parametrize("case", ["hdiv1_signed", "hdiv2", "hdiv3", "hdiv4", "bdm2", "bdm4"])
 def test_schur_complement_apply(case):
     """-S~ x = B M_bras^{-1} B^T x (mixed Poisson, RT_k or BDM_k / DG_{k-1}) against the oracle's
     assembled B and BRAS, in FP64 and FP32; other spaces are rejected."""

@@ -31,7 +31,7 @@ def _problem(mesh, space, order, rho=None):
 
 
 @pytest.mark.parametrize("space,order", [("h1", 2), ("h1", 4), ("hcurl", 2), ("hcurl", 3), ("hcurl", 4), ("hdiv", 3),
-                                         ("hdiv", 4), ("n2curl", 3), ("bdm", 3)])
+                                         ("hdiv", 4), ("n2curl", 3), ("bdm", 3), ("n2curl", 4), ("bdm", 4)])
 def test_one_element_is_exact_inverse(space, order):
     pr = _problem(mg.single_simplex_mesh(3, seed=2), space, order)
     np.testing.assert_allclose(pr.B.toarray(), np.linalg.inv(pr.M.toarray()), rtol=1e-10, atol=1e-9 * np.abs(pr.B).max())

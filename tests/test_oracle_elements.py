@@ -152,8 +152,8 @@ def test_bernstein_closed_forms(dim, p):
     ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True), ("hcurl", 4, True),
     ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True), ("hdiv", 4, True),
     ("hcurl", 2, False),
-    ("n2curl", 1, False), ("n2curl", 2, True), ("n2curl", 3, True), ("bdm", 1, True), ("bdm", 2, True),
-    ("bdm", 3, True)])
+    ("n2curl", 1, False), ("n2curl", 2, True), ("n2curl", 3, True), ("n2curl", 4, True), ("bdm", 1, True),
+    ("bdm", 2, True), ("bdm", 3, True), ("bdm", 4, True)])
 def test_conformity_across_shared_face(space, order, sort):
     if space == "hcurl" and order == 2 and not sort:
         with pytest.raises(ValueError):
@@ -193,7 +193,7 @@ def _two_triangles(seed, sort=True):
 
 
 @pytest.mark.parametrize("space,order", [(s, k) for s in ("hcurl", "hdiv") for k in (1, 2, 3, 4)]
-                         + [(s, k) for s in ("n2curl", "bdm") for k in (1, 2, 3)])
+                         + [(s, k) for s in ("n2curl", "bdm") for k in (1, 2, 3, 4)])
 @pytest.mark.parametrize("sort", [True, False])
 def test_conformity_across_shared_edge_2d(space, order, sort):
     mesh = _two_triangles(3, sort)

@@ -84,7 +84,7 @@ def test_schur_spectrum_within_mass_bounds(k, cells):
     assert ev[0] >= 1 - 1e-9                             # S~^{-1} S <= 1 for BRAS
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_bdm_divergence_kernel_and_range(k):
     mesh = mg.unit_cube_mesh(2, jitter=0.15, seed=k)
     pr, l2g, s, n = _problem(mesh, k, "bdm")
