@@ -427,7 +427,11 @@ def run_ours(a):
                  ("h1b_3d_p3", "h1b", 3, 32, (98, 7.8), "Table 1, 3D, p=3, Bernstein"),
                  ("h1b_3d_p4", "h1b", 4, 24, (420, 11), "Table 1, 3D, p=4, Bernstein"),
                  ("hcurl_3d_k1", "hcurl", 1, 56, (6.0, 1.8), "Table 2, 3D, p=1, N1curl"),
-                 ("hdiv_3d_k1", "hdiv", 1, 64, (4.0, 1.6), "Table 3, 3D, p=1, RT"))
+                 ("hdiv_3d_k1", "hdiv", 1, 64, (4.0, 1.6), "Table 3, 3D, p=1, RT"),
+                 ("n2curl_3d_k1", "n2curl", 1, 40, (36, 7.4), "Table 2, 3D, p=1, N2curl"),
+                 ("n2curl_3d_k2", "n2curl", 2, 26, (170, 10), "Table 2, 3D, p=2, N2curl"),
+                 ("bdm_3d_k1", "bdm", 1, 28, (39, 7.1), "Table 3, 3D, p=1, BDM"),
+                 ("bdm_3d_k2", "bdm", 2, 21, (32, 5.4), "Table 3, 3D, p=2, BDM"))
         for key, space, order, cells, printed, where in cases:
             mu = mg.unit_cube_mesh(cells, jitter=0.0, seed=0)
             nk, lk, sk = mg.dof_map(mu, space, order)
@@ -443,20 +447,20 @@ def run_ours(a):
             kap[f"h1_bench_p{pr['p']}"] = row
         compare["kappa_cg_lanczos"] = kap
 
-    # mixed Poisson Schur complement apply -S~ x = B M_bras^{-1} B^T x (RT_k / DG_{k-1}, FP32) on
-    # 40^3 x 6 tets, beside the BRAS apply it contains
+    # mixed Poisson Schur complement apply -S~ x = B M_bras^{-1} B^T x (RT_k or BDM_k / DG_{k-1},
+    # FP32) on 40^3 x 6 tets, beside the BRAS apply it contains
     if not a.no_compare:
         sch = {}
         m40s = mg.unit_cube_mesh(40, jitter=JITTER, seed=0)
-        for k in (1, 2, 3):
-            nk, lk, sk = mg.dof_map(m40s, "hdiv", k)
-            cs = B.Context(m40s.coords, m40s.cells, "hdiv", k, nk, lk, sk, precisions=2)
+        for fam, k in (("hdiv", 1), ("hdiv", 2), ("hdiv", 3), ("bdm", 1), ("bdm", 2), ("bdm", 3)):
+            nk, lk, sk = mg.dof_map(m40s, fam, k)
+            cs = B.Context(m40s.coords, m40s.cells, fam, k, nk, lk, sk, precisions=2)
             nq = k * (k + 1) * (k + 2) // 6
             xq = torch.as_tensor(mg.rhs(m40s.n_cell * nq, 1, seed=1), device="cuda").float()
             yq = torch.empty_like(xq)
             xb = torch.as_tensor(mg.rhs(nk, 1, seed=1), device="cuda").float()
             yb = torch.empty_like(xb)
-            row = {"cells": m40s.n_cell, "rt_dofs": nk, "dg_dofs": m40s.n_cell * nq}
+            row = {"cells": m40s.n_cell, "hdiv_dofs": nk, "dg_dofs": m40s.n_cell * nq}
             for name, fn in (("schur_apply_us", lambda: cs.schur_apply(xq, B.FP32, out=yq)),
                              ("bras_apply_us", lambda: cs.bras_apply(xb, B.FP32, out=yb))):
                 for _ in range(3):
@@ -469,7 +473,7 @@ def run_ours(a):
                 e1.record(st)
                 torch.cuda.synchronize()
                 row[name] = e0.elapsed_time(e1) * 1e3 / 10
-            sch[f"rt{k}"] = row
+            sch[f"{'rt' if fam == 'hdiv' else 'bdm'}{k}"] = row
             del cs
         compare["schur_mixed_poisson"] = sch
 
