@@ -59,6 +59,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(t: float, ws: int, device="cpu") -> float:
+    """The slowest rank's time: every rank gets the same value (identity on one rank)."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: float, t_max: float, ws: int) -> float:
+    """Replicas: every rank solves the same fixed workload, so the job rate is the units of all
+    ranks over the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank / t_max
+
+
 # ---- CPU oracle timing (the baseline leg; the only place bench.py runs the oracle) ----------
 def oracle_solve_rate(orders=(1, 2), repeats=3):
     """FP64 oracle BRAS-PCG (assembled CSR M and BRAS, scipy) on the same inputs; setup
@@ -223,20 +240,24 @@ def run_ours(a):
         order_ms[(mode, pc, host)] = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(probs))]
         return out
 
-    def timed(fn, steps):
+    def timed(fn, steps, collective=True):
+        # collective: every rank runs this loop (barriers around each step); rank 0's comparison
+        # rows run after the other ranks have left and time locally
         ts = []
         res = None
         for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
-            barrier()
+            if collective:
+                barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
             res = fn()
             e1.record(st)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) / 1e3)
-        barrier()
+        if collective:
+            barrier()
         return ts, res
 
     for _ in range(a.warmup):
@@ -248,12 +269,8 @@ def run_ours(a):
     launches = B._lib.bras_kernel_launches() - launches0
     clk = clocks.stop()
     t_step = float(np.mean(ts))
-    t_max = t_step
-    if ws > 1:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * total_n / t_max
+    t_max = max_over_ranks(t_step, ws, "cuda")
+    value = whole_job_rate(total_n, t_max, ws)
     for its, rel, status in res:
         if status != 0 or rel > 1e-10:
             raise RuntimeError(f"solve did not reach 1e-10: {res}")
@@ -268,9 +285,13 @@ def run_ours(a):
         t0 = time.perf_counter()
         step(host=True)
         ts_e2e.append(time.perf_counter() - t0)
-    e2e = {"value": ws * total_n / float(np.mean(ts_e2e)), "unit": "DOF/s",
+    t_e2e = max_over_ranks(float(np.mean(ts_e2e)), ws, "cuda")
+    e2e = {"value": whole_job_rate(total_n, t_e2e, ws), "unit": "DOF/s",
            "h2d_bytes_per_step": 8 * total_n, "d2h_bytes_per_step": 8 * total_n}
 
+    if ws > 1:
+        barrier()
+        torch.distributed.destroy_process_group()   # no collective follows: rank 0 reports alone
     if rank != 0:
         return 0
 
@@ -286,7 +307,7 @@ def run_ours(a):
         for name, mode, pc in (("fp64_bras", B.SOLVE_FP64, B.PC_BRAS), ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI),
                                ("mixed_jacobi", B.SOLVE_MIXED, B.PC_JACOBI)):
             step(mode, pc)
-            tsc, rc = timed(lambda: step(mode, pc), 1)
+            tsc, rc = timed(lambda: step(mode, pc), 1, collective=False)
             compare[name] = {"dof_per_s": total_n / tsc[0], "ms": 1e3 * tsc[0], "its": [r[0] for r in rc],
                              "solve_ms": order_ms.get((mode, pc, False))}
         compare["mixed_bras"] = {"dof_per_s": value / ws, "ms": 1e3 * t_step, "its": [r[0] for r in res]}
@@ -557,8 +578,6 @@ def run_ours(a):
             "gpu_launches": int(launches),
             "clocks": clk, "compare": compare, "kernels": kern}
     print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
     return 0
 
 
