@@ -76,6 +76,38 @@ def test_cg_iterations_match_paper(key):
     assert abs(itd - gold["diag"]) <= 1 and abs(itb - gold["bras"]) <= 1, (key, itd, itb, gold)
 
 
+# second kinds (Tables 2-3): ~3e4-1.5e5 dofs against the paper's ~1e6
+SECOND_KIND_ITS = {
+    "n2curl_2d_k1": (lambda: mg.unit_square_mesh(100), "n2curl", 1),
+    "bdm_2d_k1": (lambda: mg.unit_square_mesh(100), "bdm", 1),
+    "n2curl_2d_k2": (lambda: mg.unit_square_mesh(64), "n2curl", 2),
+    "n2curl_3d_k1": (lambda: mg.unit_cube_mesh(20), "n2curl", 1),
+    "bdm_3d_k1": (lambda: mg.unit_cube_mesh(16), "bdm", 1),
+    "bdm_3d_k2": (lambda: mg.unit_cube_mesh(7), "bdm", 2),
+}
+
+
+@pytest.mark.parametrize("key", sorted(SECOND_KIND_ITS))
+def test_second_kind_iterations_match_paper(key):
+    """CG (diagonal and BRAS) and the BRAS fixed point within one iteration of Tables 2-3; the
+    diagonal fixed point within 5 %: its count still grows by a few per cent between these meshes
+    and the paper's (N2curl_1 in 3D: 690 at 2.7e4 dofs, 667 at 1.2e5, 638 printed)."""
+    make, space, order = SECOND_KIND_ITS[key]
+    pr = _problem(make(), space, order)
+    b = mg.rhs(pr.n_dof, 1, seed=1)
+    v0 = mg.rhs(pr.n_dof, 1, seed=4)
+    _, itd, _ = pcg(pr.mass_apply, b, pr.jacobi_apply, rtol=1e-10)
+    _, itb, _ = pcg(pr.mass_apply, b, pr.bras_apply, rtol=1e-10)
+    cg, fp = GOLD["cg_iterations"][key], GOLD["fixed_point_iterations"][key]
+    assert abs(itd - cg["diag"]) <= 1 and abs(itb - cg["bras"]) <= 1, (key, itd, itb, cg)
+    lam_d = power_lambda_max(pr.mass_apply, pr.jacobi_apply, v0, 100)
+    lam_b = power_lambda_max(pr.mass_apply, pr.bras_apply, v0, 100)
+    _, fd = fixed_point(pr.mass_apply, b, pr.jacobi_apply, 1.0 / lam_d)
+    _, fb = fixed_point(pr.mass_apply, b, pr.bras_apply, 2.0 / (1.0 + lam_b))
+    assert abs(fb - fp["bras"]) <= 1, (key, fb, fp)
+    assert abs(fd - fp["diag"]) <= 0.05 * fp["diag"], (key, fd, fp)
+
+
 def test_chebyshev_bound_and_fixed_point():
     pr = _problem(mg.unit_square_mesh(12, jitter=0.2), "h1", 2)
     M = pr.M.toarray()
