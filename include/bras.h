@@ -176,7 +176,7 @@ int bras_mass_apply(const bras_ctx* ctx, int precision, const void* x, void* y, 
 int bras_apply(const bras_ctx* ctx, int precision, const void* x, void* y, int nrhs,
                void* stream);
 
-/* bras_apply_noalloc -- the same y = M_bras^{-1} x as bras_apply (the paper has no
+/* bras_apply_noalloc -- the same y = M_bras^{-1} x as bras_apply, bit for bit (the paper has no
  * counterpart: this is a memory-management variant of this library), for callers that must
  * not have the library allocate device memory: code that owns all device memory through its
  * own pool or caching allocator, loops where the implicit synchronisation of cudaMalloc is not

@@ -121,9 +121,13 @@ bool is_device_ptr(const void* p) {
 // depend on the block size, so only these change).
 int install_tables(bras_ctx* c, const HostTables& t) {
     for (void* p : {(void*)c->blk_e0, (void*)c->blk_u0, (void*)c->blk_nint, (void*)c->blk_p0, (void*)c->blk_pkt,
-                    (void*)c->pkt, (void*)c->sh_ids, (void*)c->sh_off, (void*)c->sh_slots})
+                    (void*)c->pkt, (void*)c->sh_items, (void*)c->sh_d, (void*)c->grp_rec, (void*)c->grp_slots})
         if (p) dfree(c, p);
-    c->blk_e0 = c->blk_u0 = c->blk_nint = c->blk_p0 = c->sh_ids = c->sh_off = c->sh_slots = nullptr;
+    c->blk_e0 = c->blk_u0 = c->blk_nint = c->blk_p0 = nullptr;
+    c->sh_items = nullptr;
+    c->sh_d = nullptr;
+    c->grp_rec = nullptr;
+    c->grp_slots = nullptr;
     c->blk_pkt = nullptr;
     c->pkt = nullptr;
     c->BE = t.BE;
@@ -132,7 +136,8 @@ int install_tables(bras_ctx* c, const HostTables& t) {
     c->max_ne = t.max_ne;
     c->U_tot = t.U_tot;
     c->npart = t.npart;
-    c->nsh = (int64_t)t.sh_ids.size();
+    c->nsh = t.nsh;
+    c->ngrp = (int64_t)t.grp_size.size();
     c->max_pkt = t.max_pkt;
     int rc;
     if ((rc = upload(c, &c->blk_e0, t.blk_e0.data(), t.blk_e0.size()))) return rc;
@@ -141,9 +146,20 @@ int install_tables(bras_ctx* c, const HostTables& t) {
     if ((rc = upload(c, &c->blk_p0, t.blk_p0.data(), t.blk_p0.size()))) return rc;
     if ((rc = upload(c, &c->blk_pkt, t.blk_pkt.data(), t.blk_pkt.size()))) return rc;
     if ((rc = upload(c, &c->pkt, t.pkt.data(), t.pkt.size()))) return rc;
-    if ((rc = upload(c, &c->sh_ids, t.sh_ids.data(), t.sh_ids.size()))) return rc;
-    if ((rc = upload(c, &c->sh_off, t.sh_off.data(), t.sh_off.size()))) return rc;
-    if ((rc = upload(c, &c->sh_slots, t.sh_slots.data(), t.sh_slots.size()))) return rc;
+    {   // the combine pass's records: items (dof, group) in group order, groups (first item,
+        // block count, first slot entry)
+        const size_t ng = t.grp_size.size();
+        std::vector<int2> items(t.sh_ids.size());
+        std::vector<int4> rec(ng);
+        for (size_t g = 0; g < ng; ++g) {
+            rec[g] = make_int4(t.grp_item0[g], t.grp_cnt[g], t.grp_slot0[g], 0);
+            for (int32_t j = t.grp_item0[g]; j < t.grp_item0[g + 1]; ++j) items[j] = make_int2(t.sh_ids[j], (int)g);
+        }
+        if ((rc = upload(c, &c->sh_items, items.data(), items.size()))) return rc;
+        if ((rc = upload(c, &c->grp_rec, rec.data(), rec.size()))) return rc;
+    }
+    if ((rc = upload(c, &c->grp_slots, t.grp_slots.data(), t.grp_slots.size()))) return rc;
+    if ((rc = upload(c, &c->sh_d, t.sh_d.data(), t.sh_d.size()))) return rc;
     return BRAS_OK;
 }
 
@@ -200,18 +216,13 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
                           h_cells.data(), dim, BE, &t, &detail, cell_group);
         if (rc) { set_detail(detail); return rc; }
-        const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
-        size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t.max_pkt, t.max_u, t.max_ne);
-        if (want_tc) {   // the FP32 tensor-core kernel: B tiles instead of the SIMT reference copy
-            BlockArgs tmp{};
-            tmp.max_pkt = t.max_pkt;
-            tmp.max_u = t.max_u;
-            tmp.max_ne = t.max_ne;
-            s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
-        }
+        const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t);
+        size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t);
+        // the FP32 tensor-core kernel: B tiles instead of the SIMT reference copy
+        if (want_tc) s32 = std::max(s32, h1_tc_smem_bytes(nloc, shape_args(t)));
         // a context for several right-hand sides also wants its multi-RHS kernel (16-byte
         // chunks of every dof's row) to fit one CTA
-        const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, want_tc, t.max_pkt, t.max_u, t.max_ne);
+        const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, want_tc, t);
         const bool fits = s64 <= (size_t)smem_optin &&
                           (fixed_be || (2 * (s32 + 1024) <= (size_t)smem_sm && smr <= (size_t)smem_optin));
         if (fits || BE <= 32) {
@@ -392,17 +403,11 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
                                    h_cells.data(), dim, be, &tt, &detail, cell_group)))
                 break;
             tt.BE = be;
-            const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, tt.max_pkt, tt.max_u, tt.max_ne);
-            size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, tt.max_pkt, tt.max_u, tt.max_ne);
-            if (c->use_tc) {
-                BlockArgs tmp{};
-                tmp.max_pkt = tt.max_pkt;
-                tmp.max_u = tt.max_u;
-                tmp.max_ne = tt.max_ne;
-                s32 = std::max(s32, h1_tc_smem_bytes(nloc, tmp));
-            }
+            const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, tt);
+            size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, tt);
+            if (c->use_tc) s32 = std::max(s32, h1_tc_smem_bytes(nloc, shape_args(tt)));
             if (s64 > (size_t)smem_optin || s32 > (size_t)smem_optin) continue;
-            const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, c->use_tc, tt.max_pkt, tt.max_u, tt.max_ne);
+            const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, c->use_tc, tt);
             if (smr > (size_t)smem_optin && be > 32) continue;   // keep the multi-RHS kernel usable
             if ((rc = install_tables(c, tt)) || (rc = ensure_part(c, c->max_nrhs))) break;
             float ms = 0.f;
@@ -446,26 +451,29 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
 
 }  // namespace
 
-size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int max_u, int max_ne, int cw) {
+BlockArgs shape_args(const HostTables& t) {
+    BlockArgs A{};
+    A.max_pkt = t.max_pkt;
+    A.max_u = t.max_u;
+    A.max_ne = t.max_ne;
+    return A;
+}
+
+size_t block_smem_estimate(int nloc, int tsize, bool h1, const HostTables& t, int cw) {
     const int w = tsize == 4 ? 4 : 2;
     const size_t npad = (size_t)((nloc + w - 1) / w * w);
-    return 128 + ((max_pkt + 127u) & ~127u) +
-           (size_t)tsize * (((size_t)max_u * cw + 3) / 4 * 4 + ((size_t)nloc * max_ne * cw + 3) / 4 * 4 +
-                            (h1 ? nloc * npad : 0));
+    return 128 + ((t.max_pkt + 127u) & ~127u) +
+           (size_t)tsize * (((size_t)t.max_u * cw + 3) / 4 * 4 + ((size_t)nloc * t.max_ne * cw + 3) / 4 * 4 +
+                            (h1 ? nloc * npad : 0)) +
+           128;
 }
 
 // Shared memory of the FP32 multi-RHS block kernel (16-byte chunks: 4 values a dof), 0 for a
 // context built for one right-hand side.
-size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, uint32_t max_pkt, int max_u, int max_ne) {
+size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, const HostTables& t) {
     if (c->max_nrhs <= 1) return 0;
-    size_t s = block_smem_estimate(nloc, 4, h1, max_pkt, max_u, max_ne, 4);
-    if (tc) {
-        BlockArgs tmp{};
-        tmp.max_pkt = max_pkt;
-        tmp.max_u = max_u;
-        tmp.max_ne = max_ne;
-        s = std::max(s, h1_tc_smem_bytes(nloc, tmp, true));
-    }
+    size_t s = block_smem_estimate(nloc, 4, h1, t, 4);
+    if (tc) s = std::max(s, h1_tc_smem_bytes(nloc, shape_args(t), true));
     return s;
 }
 
@@ -522,7 +530,6 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.max_ne = c->max_ne;
     A.max_pkt = c->max_pkt;
     const bool f64 = prec == BRAS_FP64;
-    L.dinv = f64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
     if (c->space == BRAS_H1) {
         if (op == OP_BRAS) {
             A.refmat = f64 ? (const void*)c->Minvref64 : (const void*)c->Minvref32;
@@ -538,28 +545,30 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
             A.pk = f64 ? (const void*)c->Mpk64 : (const void*)c->Mpk32;
     }
     L.nblk = c->nblk;
-    L.nsh = c->nsh;
-    L.sh_ids = c->sh_ids;
-    L.sh_off = c->sh_off;
-    L.sh_slots = c->sh_slots;
+    L.G.nsh = c->nsh;
+    L.G.items = c->sh_items;
+    L.G.sh_d = c->sh_d;
+    L.G.grp = c->grp_rec;
+    L.G.grp_slots = c->grp_slots;
     return L;
 }
 
-int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st) {
-    if (ensure_part(c, nrhs) != BRAS_OK) return BRAS_ERR_OOM;
+// The one precision / kernel dispatch of every apply; `part` holds the partial sums of the
+// block-boundary dofs (npart * nrhs values of the apply's type).
+int dispatch_op(const bras_ctx* c, int prec, int op, const void* x, void* y, void* part, int nrhs, cudaStream_t st) {
     LaunchCommon L = make_launch(c, prec, op);
     cudaError_t err;
     const bool h1 = c->space == BRAS_H1;
     if (prec == BRAS_FP64 || prec == BRAS_FP64X) {
         auto* xx = static_cast<const double*>(x);
         auto* yy = static_cast<double*>(y);
-        auto* pp = static_cast<double*>(c->part);
+        auto* pp = static_cast<double*>(part);
         if (h1 && prec == BRAS_FP64X && op == OP_MASS) err = launch_h1_df(L, c->nloc, xx, yy, pp, nrhs, st);
         else err = h1 ? launch_h1_f64(L, c->nloc, op, xx, yy, pp, nrhs, st) : launch_pk_f64(L, c->nloc, op, xx, yy, pp, nrhs, st);
     } else {
         auto* xx = static_cast<const float*>(x);
         auto* yy = static_cast<float*>(y);
-        auto* pp = static_cast<float*>(c->part);
+        auto* pp = static_cast<float*>(part);
         if (h1 && c->use_tc && (op == OP_MASS || op == OP_BRAS))
             err = launch_h1_tc(L, op == OP_MASS ? c->btile_mass : c->btile_bras, c->nloc, op, xx, yy, pp, nrhs, st);
         else if (h1) err = launch_h1_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
@@ -567,6 +576,11 @@ int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cuda
         else err = launch_pk_f32(L, c->nloc, op, xx, yy, pp, nrhs, st);
     }
     return err == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
+}
+
+int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st) {
+    if (ensure_part(c, nrhs) != BRAS_OK) return BRAS_ERR_OOM;
+    return dispatch_op(c, prec, op, x, y, c->part, nrhs, st);
 }
 
 bool has_precision(const bras_ctx* c, int prec) {

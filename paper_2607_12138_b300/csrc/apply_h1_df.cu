@@ -11,7 +11,7 @@ cudaError_t launch_h1_df(const LaunchCommon& L, int nloc, const double* x, doubl
                          cudaStream_t st) {
 #define BRAS_CASE(N)                                                                                    \
     if (nloc == N)                                                                                      \
-        return launch_block_df<N>(L.A, L.nblk, x, y, part, nrhs, L.nsh, L.sh_ids, L.sh_off, L.sh_slots, st);
+        return launch_block_df<N>(L.A, L.G, L.nblk, x, y, part, nrhs, st);
     BRAS_CASE(3)
     BRAS_CASE(4)
     BRAS_CASE(6)

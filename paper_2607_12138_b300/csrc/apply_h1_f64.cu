@@ -8,7 +8,7 @@ namespace bras {
 cudaError_t launch_h1_f64(const LaunchCommon& L, int nloc, int op, const double* x, double* y, double* part, int nrhs, cudaStream_t st) {
 #define BRAS_CASE(N, OPV) \
     if (nloc == N && op == OPV) \
-        return launch_block<N, double, double, KIND_H1, OPV>(L.A, L.nblk, x, y, part, nrhs, static_cast<const double*>(L.dinv), L.nsh, L.sh_ids, L.sh_off, L.sh_slots, st);
+        return launch_block<N, double, double, KIND_H1, OPV>(L.A, L.G, L.nblk, x, y, part, nrhs, st);
     BRAS_CASE(3, OP_MASS)
     BRAS_CASE(3, OP_BRAS)
     BRAS_CASE(3, OP_DIAG)

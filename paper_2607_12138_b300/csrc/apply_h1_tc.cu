@@ -34,11 +34,9 @@ cudaError_t launch_h1_tc(const LaunchCommon& L, const unsigned char* btile, int 
     TcArgs TA;
     TA.A = L.A;
     TA.btile = btile;
-    const float* dinv = static_cast<const float*>(L.dinv);
 #define BRAS_CASE(N, OPV)                                                                                   \
     if (nloc == N && op == OPV)                                                                             \
-        return launch_block_tc<N, OPV>(TA, L.nblk, x, y, part, nrhs, dinv, L.nsh, L.sh_ids, L.sh_off,     \
-                                       L.sh_slots, st);
+        return launch_block_tc<N, OPV>(TA, L.G, L.nblk, x, y, part, nrhs, st);
     BRAS_CASE(10, OP_MASS)
     BRAS_CASE(10, OP_BRAS)
     BRAS_CASE(15, OP_MASS)

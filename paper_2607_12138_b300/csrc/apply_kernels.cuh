@@ -15,10 +15,14 @@
 //                       broadcasts;
 //        H(curl)/H(div): z_K = A_K x_K with A_K = M_K or M_K^{-1} streamed per cell as a
 //                       packed symmetric matrix in a cell-interleaved layout (coalesced);
-//   3. the signed local results go to shared memory, and every block-local dof sums its
-//      copies in a fixed order (the P^T of Eq. M_PMbrP / mhatinvbras_def); dofs with all
-//      copies in the block are final (times 1/d for BRAS, the left D^{-1}), the others
-//      leave a partial sum that k_combine adds up in ascending block order.
+//   3. the signed local results go to shared memory in dof-sorted order (the start of every
+//      dof's run is read off the end bits of the packet), and every block-local dof sums its
+//      run of copies in a fixed order (the P^T of Eq. M_PMbrP / mhatinvbras_def); dofs with
+//      all copies in the block are final (times 1/d for BRAS, the left D^{-1}), the others
+//      leave a partial sum;
+//   4. k_group_combine walks the groups of shared dofs (dofs whose copies lie in the same set
+//      of blocks), one warp per group, and adds each dof's partials up in ascending block
+//      order (times 1/d for BRAS).
 // No floating-point atomics anywhere: results are bit-reproducible.
 #pragma once
 #include <cuda_bf16.h>
@@ -49,6 +53,18 @@ struct BlockArgs {
     int max_u;
     int max_ne;
     uint32_t max_pkt;          // largest packet (bytes)
+};
+
+// Shared dofs for the combine pass (tables.cpp), in group order: item j = (global dof, group g)
+// with multiplicity sh_d[j]; group g = (first item, block count, first slot entry): the
+// partials of its i-th dof sit at grp_slots[first slot entry + k] + i for its k-th block
+// (ascending block order).
+struct CombineArgs {
+    int64_t nsh;
+    const int2* items;
+    const uint16_t* sh_d;
+    const int4* grp;
+    const int32_t* grp_slots;
 };
 
 // 16-byte groups of a cell's packed matrix (layout: pk_index in packet.h)
@@ -146,42 +162,6 @@ __device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t
 __device__ __forceinline__ double div_by_count(double v, uint16_t d) { return v / (double)d; }
 __device__ __forceinline__ float div_by_count(float v, uint16_t d) { return v * __frcp_rn((float)d); }
 
-// Stage 3 for one right-hand side: each block-local dof u sums its copies zs[incoff[u],
-// incoff[u+1]) in that order (Eq. mhatinvbras_def, the D^{-1} P^T half), BRAS divides by the
-// multiplicity, interior dofs store to y and shared ones to the partials.  A thread takes four
-// dofs at a time so that their shared-memory chains overlap; every dof's order is unchanged.
-template <typename T, int OP>
-__device__ __forceinline__ void block_dof_sums(int nu, int nint, const uint16_t* incoff, const T* zs,
-                                               const uint16_t* dmul, const int32_t* ids, T* __restrict__ y,
-                                               int nrhs, int r0, T* __restrict__ part, int64_t p0) {
-    constexpr int U = 4;
-    for (int u = threadIdx.x; u < nu; u += U * blockDim.x) {
-        int s0[U], cnt[U];
-        T acc[U];
-        int m = 0;
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int uu = u + k * (int)blockDim.x;
-            s0[k] = uu < nu ? incoff[uu] : 0;
-            cnt[k] = uu < nu ? incoff[uu + 1] - s0[k] : 0;
-            acc[k] = T(0);
-            m = max(m, cnt[k]);
-        }
-        for (int j = 0; j < m; ++j) {
-#pragma unroll
-            for (int k = 0; k < U; ++k)
-                if (j < cnt[k]) acc[k] += zs[s0[k] + j];
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int uu = u + k * (int)blockDim.x;
-            if (uu >= nu) break;
-            if (uu < nint) y[(size_t)ids[uu] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(acc[k], dmul[uu]) : acc[k];
-            else part[p0 + (uu - nint)] = acc[k];
-        }
-    }
-}
-
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec4<double> { using type = double2; static constexpr int W = 2; };
@@ -269,6 +249,142 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
     return __syncthreads_and(ok) != 0;
 }
 
+// ---- stage 3: per-dof sums over the dof-sorted copies ------------------------------------
+// Start of every block-local dof's run of copies in the dof-sorted order, from the end bits:
+// incoff[0] = 0, incoff[u + 1] = 1 + the position of the u-th end.  Thread t scans a
+// contiguous chunk of end-bit words; a block-wide scan of their popcounts numbers the ends.
+// Requires blockDim.x a multiple of 32; incoff is complete after the call and a CTA barrier.
+__device__ __forceinline__ void run_starts(int m, const uint32_t* __restrict__ ends, uint16_t* incoff, int* wsum) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int nw = (m + 31) >> 5, W = (nw + T - 1) / T;
+    const int w0 = min(tid * W, nw), w1 = min(w0 + W, nw);
+    int cnt = 0;
+    for (int k = w0; k < w1; ++k) cnt += __popc(ends[k]);
+    int v = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += x;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    int u = v - cnt;
+    for (int j = 0; j < w; ++j) u += wsum[j];
+    for (int k = w0; k < w1; ++k) {
+        uint32_t bits = ends[k];
+        while (bits) {
+            const int bpos = __ffs(bits) - 1;
+            incoff[++u] = (uint16_t)((k << 5) + bpos + 1);
+            bits &= bits - 1u;
+        }
+    }
+    if (tid == 0) incoff[0] = 0;
+}
+
+// Every block-local dof u sums its run zs[incoff[u], incoff[u+1]) in order and hands the total
+// to out(u, v).  A thread takes four dofs (u, u + T, u + 2T, u + 3T) so that their shared-memory
+// chains overlap; interior dofs are sorted by copy count, so the lanes of a warp run alike.
+template <typename V, typename Add, typename Out>
+__device__ __forceinline__ void dof_run_sums(int nu, const uint16_t* incoff, const V* zs, V zero, Add add, Out out) {
+    constexpr int U = 4;
+    const int T = blockDim.x;
+    for (int u = threadIdx.x; u < nu; u += U * T) {
+        int s0[U], cnt[U];
+        V acc[U];
+        int mx = 0;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * T;
+            s0[k] = uu < nu ? incoff[uu] : 0;
+            cnt[k] = uu < nu ? incoff[uu + 1] - s0[k] : 0;
+            acc[k] = zero;
+            mx = max(mx, cnt[k]);
+        }
+        for (int j = 0; j < mx; ++j) {
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (j < cnt[k]) acc[k] = add(acc[k], zs[s0[k] + j]);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * T;
+            if (uu < nu) out(uu, acc[k]);
+        }
+    }
+}
+
+// Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
+// their partial slot.  MR: V = 16-byte chunk of rc right-hand sides starting at r0, partials
+// slot-major; else V = T, partials [nrhs][npart] from p0.
+template <typename T, int OP, bool MR, typename V>
+__device__ __forceinline__ void store_dof(int u, V v, int nint, const int32_t* ids, const uint16_t* dmul,
+                                          T* __restrict__ y, T* __restrict__ part, int nrhs, int r0, int rc, bool vec,
+                                          int64_t p0) {
+    if constexpr (MR) {
+        if (u < nint) {
+            if (OP == OP_BRAS) {
+#pragma unroll
+                for (int j = 0; j < Chunk<T>::CW; ++j) vget(v, j) = div_by_count(vget(v, j), dmul[u]);
+            }
+            st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, v);
+        } else {
+            st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, v);
+        }
+    } else {
+        if (u < nint) y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(v, dmul[u]) : v;
+        else part[p0 + (u - nint)] = v;
+    }
+}
+
+// Stage 4: one thread per (shared dof, rhs); every dof adds its partials in ascending block
+// order (0 + p_0 + p_1 + ...) and stores the total to y (times 1/d for BRAS).  Consecutive
+// threads take consecutive dofs of a group, so the partial reads coalesce and the group's
+// record and slots are shared through L1.  slot_major: partials laid out [npart][nrhs], else
+// [nrhs][npart].
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_group_combine(const CombineArgs G, const T* __restrict__ part, int64_t npart,
+                                                       T* __restrict__ y, int nrhs, int slot_major) {
+    const int64_t total = G.nsh * nrhs;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = nrhs == 1 ? q : q / nrhs;
+        const int r = (int)(q - j * nrhs);
+        const int2 it = __ldg(G.items + j);
+        const int4 gr = __ldg(G.grp + it.y);
+        const int i = (int)(j - gr.x), cnt = gr.y;
+        const int32_t* sl = G.grp_slots + gr.z;
+        T acc = T(0);
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k0 + k < cnt) {
+                    const int64_t slot = (int64_t)__ldg(sl + k0 + k) + i;
+                    v[k] = __ldg(part + (slot_major ? slot * nrhs + r : (int64_t)r * npart + slot));
+                } else {
+                    v[k] = T(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k0 + k < cnt) acc += v[k];
+        }
+        y[(size_t)it.x * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, __ldg(G.sh_d + j)) : acc;
+    }
+}
+
+template <typename T, int OP>
+cudaError_t launch_group_combine(const CombineArgs& G, const T* part, int64_t npart, T* y, int nrhs, bool slot_major,
+                                 cudaStream_t st) {
+    if (G.nsh <= 0) return cudaSuccess;
+    const int nb = (int)std::min<int64_t>((G.nsh * nrhs + 255) / 256, 148 * 16);
+    k_group_combine<T, OP><<<nb, 256, 0, st>>>(G, part, npart, y, nrhs, slot_major ? 1 : 0);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float4 vsum(float4 a, const float4& b) { vadd(a, b); return a; }
+__device__ __forceinline__ double2 vsum(double2 a, const double2& b) { vadd(a, b); return a; }
+
 // Kernel modes.  MR = false: one right-hand side per CTA (grid = blocks x nrhs), vectors read
 // with stride nrhs, partial sums laid out [nrhs][npart].  MR = true (multi-RHS): one CTA per
 // cell block (grid = blocks) walks the right-hand sides in chunks of CW; each cell of the block
@@ -291,6 +407,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW]
     T* zs = xs + ((A.max_u * CW + 3) & ~3);                               // [slot][CW]
     T* Ms = zs + ((NLOC * A.max_ne * CW + 3) & ~3);                       // [NLOC][NPAD] (H1), 16-B aligned
+    int* wsum = reinterpret_cast<int*>(Ms + (KIND == KIND_H1 ? NLOC * NPAD : 0));   // [32] scan scratch
 
     const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
@@ -321,9 +438,10 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     __syncthreads();   // barriers initialised before anyone polls them
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
-    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
+    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
     const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
@@ -497,60 +615,20 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
         __syncthreads();
 
+        // the start of every dof's run (over the staged x, dead by now), then the per-dof sums
+        uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
+        run_starts((int)m, ends, incoff, wsum);
+        __syncthreads();
         if constexpr (MR) {
-            const V* zv = reinterpret_cast<const V*>(zs);
-            for (int u = tid; u < nu; u += blockDim.x) {
-                const int s0 = incoff[u], s1 = incoff[u + 1];
-                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-                V acc = vzero(V{});
-                for (int s = s0; s < s1; ++s) vadd(acc, zv[s]);
-                if (u < nint) {
-                    if (OP == OP_BRAS) {
-#pragma unroll
-                        for (int j = 0; j < CW; ++j) vget(acc, j) = div_by_count(vget(acc, j), dmul[u]);
-                    }
-                    st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, acc);
-                } else {
-                    st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, acc);
-                }
-            }
+            dof_run_sums<V>(nu, incoff, reinterpret_cast<const V*>(zs), vzero(V{}),
+                            [](V a, const V& c) { return vsum(a, c); },
+                            [&](int u, V v) { store_dof<T, OP, true, V>(u, v, nint, ids, dmul, y, part, nrhs, r0, rc, vec, p0); });
+            __syncthreads();   // incoff (over xs) read before the next chunk stages x
         } else {
-            block_dof_sums<T, OP>(nu, nint, incoff, zs, dmul, ids, y, nrhs, r0, part, p0);
+            dof_run_sums<T>(nu, incoff, zs, T(0), [](T a, T c) { return a + c; },
+                            [&](int u, T v) { store_dof<T, OP, false, T>(u, v, nint, ids, dmul, y, part, nrhs, r0, 1, false, p0); });
         }
     }
-}
-
-// Fixed-order sums of the partials of dofs shared between blocks; slot_major: partials laid
-// out [npart][nrhs] (multi-RHS kernels), else [nrhs][npart].
-template <typename T, int OP>
-__global__ void k_combine(int64_t nsh, const int32_t* __restrict__ sh_ids, const int32_t* __restrict__ sh_off,
-                          const int32_t* __restrict__ sh_slots, const T* __restrict__ part, int64_t npart,
-                          const T* __restrict__ dinv, T* __restrict__ y, int nrhs, int slot_major) {
-    const int64_t total = nsh * nrhs;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = nrhs == 1 ? i : i / nrhs;
-        const int r = (int)(i - j * nrhs);
-        T acc = T(0);
-        if (slot_major) {
-            for (int s = sh_off[j]; s < sh_off[j + 1]; ++s) acc += part[(size_t)sh_slots[s] * nrhs + r];
-        } else {
-            for (int s = sh_off[j]; s < sh_off[j + 1]; ++s) acc += part[(size_t)r * npart + sh_slots[s]];
-        }
-        const int g = sh_ids[j];
-        y[(size_t)g * nrhs + r] = (OP == OP_BRAS) ? acc * dinv[g] : acc;
-    }
-}
-
-template <typename T, int OP>
-cudaError_t launch_combine(int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
-                           const T* part, int64_t npart, const T* dinv, T* y, int nrhs, bool slot_major,
-                           cudaStream_t st) {
-    if (nsh <= 0) return cudaSuccess;
-    const int64_t total = nsh * nrhs;
-    const int nb = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
-    k_combine<T, OP><<<nb, 256, 0, st>>>(nsh, sh_ids, sh_off, sh_slots, part, npart, dinv, y, nrhs, slot_major ? 1 : 0);
-    count_launch(1);
-    return cudaGetLastError();
 }
 
 template <int NLOC, typename T, int KIND>
@@ -559,7 +637,8 @@ size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     const int cw = mr ? Chunk<T>::CW : 1;
     return 128 + ((A.max_pkt + 127u) & ~127u) +
            sizeof(T) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) +
-                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
+                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0)) +
+           128;
 }
 
 // Largest dynamic shared memory one CTA may opt into on the current device.
@@ -575,12 +654,11 @@ inline bool rows_vectorisable(int nrhs, const void* x, const void* y, const void
     return nrhs % per16 == 0 && al(x) && al(y) && al(part);
 }
 
-// Launch one block apply (block kernel + combine).  Returns a cudaError_t.  Several right-hand
-// sides go to the multi-RHS kernel when its chunk buffers fit shared memory, else to one CTA
-// per (block, rhs).
+// Launch one block apply (block kernel + combine pass).  Returns a cudaError_t.  Several right-hand sides go
+// to the multi-RHS kernel when its chunk buffers fit shared memory, else to one CTA per
+// (block, rhs).
 template <int NLOC, typename T, typename S, int KIND, int OP>
-cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part, int nrhs, const T* dinv,
-                         int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
+cudaError_t launch_block(const BlockArgs& A, const CombineArgs& G, int nblk, const T* x, T* y, T* part, int nrhs,
                          cudaStream_t st) {
     // multi-RHS items hold their local vector and accumulators in registers: n_loc <= 48
     constexpr bool kMR = NLOC <= 48;
@@ -603,7 +681,7 @@ cudaError_t launch_block(const BlockArgs& A, int nblk, const T* x, T* y, T* part
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    return launch_combine<T, OP>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, dinv, y, nrhs, mr, st);
+    return launch_group_combine<T, OP>(G, part, A.npart, y, nrhs, mr, st);
 }
 
 }  // namespace bras

@@ -8,7 +8,7 @@ namespace bras {
 cudaError_t launch_pk_f32(const LaunchCommon& L, int nloc, int op, const float* x, float* y, float* part, int nrhs, cudaStream_t st) {
 #define BRAS_CASE(N, OPV) \
     if (nloc == N && op == OPV) \
-        return launch_block<N, float, float, KIND_PACKED, OPV>(L.A, L.nblk, x, y, part, nrhs, static_cast<const float*>(L.dinv), L.nsh, L.sh_ids, L.sh_off, L.sh_slots, st);
+        return launch_block<N, float, float, KIND_PACKED, OPV>(L.A, L.G, L.nblk, x, y, part, nrhs, st);
     BRAS_CASE(3, OP_MASS)
     BRAS_CASE(3, OP_BRAS)
     BRAS_CASE(8, OP_MASS)

@@ -16,24 +16,31 @@ struct PcgWork;
 // Cells are reordered along a Morton curve of their centroids and cut into blocks of at
 // most BE consecutive cells.  Block b owns cells [blk_e0[b], blk_e0[b+1]) and nu_b =
 // blk_u0[b+1] - blk_u0[b] block-local dofs: first the dofs all of whose broken copies lie
-// inside the block ("interior", blk_nint[b] of them), then the others ("shared").  Its table
-// packet (byte offset blk_pkt[b], layout in apply_kernels.cuh) holds
-//   ids[u]      global dof of block-local dof u
-//   d[u]        multiplicity of that dof (D = P^T P)
-//   incoff[u]   dof u's copies occupy positions [incoff[u], incoff[u+1]) of the dof-sorted order
-//   loc[a*ne+e] block-local dof of (cell e, local a); bit 15 = sign -1 of P
-//   pos[a*ne+e] position of copy (cell e, local a) in the dof-sorted order (copies of one dof
-//               by ascending slot a*ne + e: the fixed summation order)
-// Shared dof j of block b writes partial slot blk_p0[b] + j; sh_off / sh_slots list, per
-// globally shared dof sh_ids[i], its partial slots in ascending block order.
+// inside the block ("interior", blk_nint[b] of them, ascending global id), then the others
+// ("shared"), grouped.  Its table packet (byte offset blk_pkt[b], layout in packet.h) holds
+// the dof ids, multiplicities, local indices with signs, dof-sorted positions and the end
+// bits of the dof runs.
+// A group is the set of shared dofs whose copies lie in one and the same set of blocks
+// (grp_cnt[g] blocks, grp_size[g] dofs); every member block lists the group's dofs
+// contiguously, by ascending global id.  Shared dof u of block b leaves its partial sum in
+// slot blk_p0[b] + u - nint_b; grp_slots[grp_slot0[g] + k] is the slot of the group's first
+// dof in its k-th block (ascending block order), so the partials of the group's dof i sit at
+// grp_slots[...] + i.  Block b's groups are bg_gid[blk_g0[b] .. blk_g0[b+1]) with their first
+// block-local dof bg_u[...].  The combine pass walks the groups (grp_item0, sh_ids, sh_d:
+// the group's dofs in order, with their multiplicities) and sums each dof's partials in the
+// fixed block order.
 struct HostTables {
     int BE = 256, nblk = 0, max_u = 0, max_ne = 0;
     uint32_t max_pkt = 0;
-    std::vector<int32_t> perm, blk_e0, blk_u0, blk_nint, blk_p0, sh_ids, sh_off, sh_slots;
+    std::vector<int32_t> perm, blk_e0, blk_u0, blk_nint, blk_p0;
+    std::vector<int32_t> grp_size, grp_cnt, grp_slot0, grp_slots, blk_g0, bg_gid, bg_u;
+    std::vector<int32_t> grp_item0, sh_ids;   // combine pass: group g's dofs are sh_ids[grp_item0[g] ..]
+    std::vector<uint16_t> sh_d;               // and their multiplicities
     std::vector<int64_t> blk_pkt;
     std::vector<unsigned char> pkt;
     std::vector<double> dinv;
-    int64_t npart = 0, U_tot = 0;
+    int64_t npart = 0, U_tot = 0, nsh = 0;
+    int max_bg = 0;   // most groups of one block
 };
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
@@ -57,7 +64,12 @@ struct bras_ctx {
 
     // scatter tables (device)
     int32_t *blk_e0 = nullptr, *blk_u0 = nullptr, *blk_nint = nullptr, *blk_p0 = nullptr;
-    int32_t *sh_ids = nullptr, *sh_off = nullptr, *sh_slots = nullptr;
+    // shared dofs by group, for the combine pass
+    int2* sh_items = nullptr;    // (global dof, group)
+    uint16_t* sh_d = nullptr;    // multiplicity
+    int4* grp_rec = nullptr;     // (first item, block count, first slot entry, 0)
+    int32_t* grp_slots = nullptr;
+    int64_t ngrp = 0;
     int32_t *perm = nullptr;
     int64_t* blk_pkt = nullptr;
     unsigned char* pkt = nullptr;

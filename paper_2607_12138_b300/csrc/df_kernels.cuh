@@ -2,7 +2,8 @@
 // b - M x of the FP64 refinement loop around the FP32 inner solve.
 //
 // Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async copies,
-// x staged in shared memory, fixed-order in-block incidence sums, partials of boundary dofs.
+// x staged in shared memory, fixed-order in-block dof sums, partials of boundary dofs added up
+// by the combine pass.
 // All arithmetic runs on the FP32 units as float-float pairs (about 2^-48 relative, the
 // accuracy of FP64 sums) -- B300 issues FP64, and conversions to and from it, at 1/64 of the
 // FP32 rate:
@@ -41,6 +42,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     float2* xs = reinterpret_cast<float2*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u] (hi, lo)
     float2* zs = xs + ((A.max_u + 3) & ~3);                                          // [slot] (hi, lo)
     float2* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                                  // [NLOC][NLOC] (hi, lo)
+    int* wsum = reinterpret_cast<int*>(Ms + NLOC * NLOC);                             // [32] scan scratch
 
     const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x;
     const int cw = blockDim.x / DfShape<NLOC>::TPC;   // cells per row group
@@ -68,9 +70,10 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     }
     __syncthreads();   // barriers initialised before anyone polls them
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
-    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
+    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
     if (okA) {
@@ -130,45 +133,48 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     }
     __syncthreads();
 
-    for (int u = tid; u < nu; u += blockDim.x) {
-        const int s0 = incoff[u], s1 = incoff[u + 1];
-        // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-        float ah = 0.f, al = 0.f;
-        for (int s = s0; s < s1; ++s) {
-            const float2 z = zs[s];
-            df_merge(ah, al, z.x, z.y);
-        }
-        const double acc = (double)ah + (double)al;
-        if (u < nint) y[(size_t)ids[u] * nrhs + r] = acc;
-        else part[p0 + (u - nint)] = acc;
-    }
+    // per-dof sums of the float pairs (two-sums, fixed order), converted to FP64 once per dof;
+    // the runs' starts go over the staged x, dead by now
+    uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
+    run_starts((int)m, ends, incoff, wsum);
+    __syncthreads();
+    dof_run_sums<float2>(nu, incoff, zs, make_float2(0.f, 0.f),
+                         [](float2 a, const float2& c) {
+                             df_merge(a.x, a.y, c.x, c.y);
+                             return a;
+                         },
+                         [&](int u, float2 z) {
+                             const double acc = (double)z.x + (double)z.y;
+                             if (u < nint) y[(size_t)ids[u] * nrhs + r] = acc;
+                             else part[p0 + (u - nint)] = acc;
+                         });
 }
 
 template <int NLOC>
-size_t df_smem_bytes(const BlockArgs& A) {
+size_t df_smem_bytes(const BlockArgs& A, int threads) {
     return 128 + ((A.max_pkt + 127u) & ~127u) +
            sizeof(float2) * ((((size_t)A.max_u + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) +
-                             (size_t)NLOC * NLOC);
+                             (size_t)NLOC * NLOC) +
+           128;
 }
 
 template <int NLOC>
-cudaError_t launch_block_df(const BlockArgs& A, int nblk, const double* x, double* y, double* part, int nrhs,
-                            int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off, const int32_t* sh_slots,
-                            cudaStream_t st) {
-    const size_t smem = df_smem_bytes<NLOC>(A);
+cudaError_t launch_block_df(const BlockArgs& A, const CombineArgs& G, int nblk, const double* x, double* y,
+                            double* part, int nrhs, cudaStream_t st) {
+    // cells per row group: whole warps, every cell of the largest block if 1024 threads allow
+    const int cw = std::min((A.max_ne + 31) / 32 * 32, 1024 / DfShape<NLOC>::TPC / 32 * 32);
+    const int threads = cw * DfShape<NLOC>::TPC;
+    const size_t smem = df_smem_bytes<NLOC>(A, threads);
     auto kern = k_block_df<NLOC>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    // cells per row group: whole warps, every cell of the largest block if 1024 threads allow
-    const int cw = std::min((A.max_ne + 31) / 32 * 32, 1024 / DfShape<NLOC>::TPC / 32 * 32);
-    const int threads = cw * DfShape<NLOC>::TPC;
     kern<<<dim3(nblk * nrhs), threads, smem, st>>>(A, x, y, part, nrhs);
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    return launch_combine<double, OP_MASS>(nsh, sh_ids, sh_off, sh_slots, part, A.npart, nullptr, y, nrhs, false, st);
+    return launch_group_combine<double, OP_MASS>(G, part, A.npart, y, nrhs, false, st);
 }
 
 }  // namespace bras

@@ -15,10 +15,8 @@ int64_t launches_so_far();
 
 struct LaunchCommon {
     BlockArgs A;
-    const void* dinv;   // T[n] 1/d for the combine pass
+    CombineArgs G;
     int nblk;
-    int64_t nsh;
-    const int32_t *sh_ids, *sh_off, *sh_slots;
 };
 
 cudaError_t launch_h1_f64(const LaunchCommon& L, int nloc, int op, const double* x, double* y, double* part, int nrhs, cudaStream_t st);

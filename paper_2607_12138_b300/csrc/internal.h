@@ -11,9 +11,11 @@ void set_detail(int64_t d);
 void* dalloc_bytes(bras_ctx* c, size_t bytes);
 void dfree(bras_ctx* c, void* p);
 int ensure_part(bras_ctx* c, int nrhs);
-size_t block_smem_estimate(int nloc, int tsize, bool h1, uint32_t max_pkt, int max_u, int max_ne, int cw = 1);
-size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, uint32_t max_pkt, int max_u, int max_ne);
+BlockArgs shape_args(const HostTables& t);
+size_t block_smem_estimate(int nloc, int tsize, bool h1, const HostTables& t, int cw = 1);
+size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, const HostTables& t);
 LaunchCommon make_launch(const bras_ctx* c, int prec, int op);
+int dispatch_op(const bras_ctx* c, int prec, int op, const void* x, void* y, void* part, int nrhs, cudaStream_t st);
 int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st);
 bool has_precision(const bras_ctx* c, int prec);
 

@@ -59,25 +59,8 @@ extern "C" int bras_apply_noalloc(const bras_ctx* ctx, int precision, const void
     void* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != BRAS_OK) return rc;
-    // Every slot the combine pass reads is written by exactly one block earlier in the same
-    // call, so nothing in the shared array needs clearing between calls.
-    LaunchCommon L = make_launch(ctx, precision, OP_BRAS);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t err;
-    const bool h1 = ctx->space == BRAS_H1;
-    if (precision == BRAS_FP64) {
-        auto* xx = static_cast<const double*>(x);
-        auto* yy = static_cast<double*>(y);
-        auto* pp = static_cast<double*>(scratch);
-        err = h1 ? launch_h1_f64(L, ctx->nloc, OP_BRAS, xx, yy, pp, nrhs, st)
-                 : launch_pk_f64(L, ctx->nloc, OP_BRAS, xx, yy, pp, nrhs, st);
-    } else {
-        auto* xx = static_cast<const float*>(x);
-        auto* yy = static_cast<float*>(y);
-        auto* pp = static_cast<float*>(scratch);
-        if (h1) err = launch_h1_f32(L, ctx->nloc, OP_BRAS, xx, yy, pp, nrhs, st);
-        else if (precision == BRAS_BF16) err = launch_pk_bf16(L, ctx->nloc, OP_BRAS, xx, yy, pp, nrhs, st);
-        else err = launch_pk_f32(L, ctx->nloc, OP_BRAS, xx, yy, pp, nrhs, st);
-    }
-    return err == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA;
+    // Every partial slot the combine pass reads is written by exactly one block earlier in the
+    // same call, so nothing in the shared array needs clearing between calls.  The dispatch is bras_apply's
+    // own, so both calls run the same kernel and return the same bits.
+    return dispatch_op(ctx, precision, OP_BRAS, x, y, scratch, nrhs, static_cast<cudaStream_t>(stream));
 }

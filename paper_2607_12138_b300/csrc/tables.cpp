@@ -3,8 +3,9 @@
 // The BRAS apply D^{-1} P^T M_br^{-1} P D^{-1} (Eq. mhatinvbras_def) and the mass apply
 // P^T M_br P (Eq. M_PMbrP) both end in the transpose of the signed gather P: every conforming
 // dof sums the contributions of its broken copies.  These tables let one thread block do
-// that sum in on-chip memory for the dofs whose copies all live in its cells, and hand the
-// few dofs on block boundaries to a second, fixed-order pass -- no floating-point atomics.
+// that sum in on-chip memory for the dofs whose copies all live in its cells; a dof on a
+// block boundary gets one partial sum per block, and the last of its blocks to finish adds
+// them up in ascending block order -- no floating-point atomics.
 #include <omp.h>
 
 #include <algorithm>
@@ -81,129 +82,212 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
     t->blk_e0.resize(nblk + 1);
     for (int b = 0; b <= nblk; ++b) t->blk_e0[b] = (int32_t)std::min<int64_t>((int64_t)b * BE, E);
 
+    // pass 1, per block: its distinct dofs (ascending) with their copies, by ascending slot
     struct Blk {
-        std::vector<int32_t> ids;
-        std::vector<uint16_t> incoff, inc, loc;
+        std::vector<std::pair<int32_t, int32_t>> srt;   // (dof, slot a * ne + e), sorted
+        std::vector<int32_t> uq, first;                   // distinct dofs, start of each run in srt
+        std::vector<int32_t> order;                       // block-local order: indices into uq
+        std::vector<int32_t> ids, gid_of;                 // final ids; group of each shared dof
         int nint = 0;
     };
+    if ((int64_t)std::min<int64_t>(BE, E) * nloc > 65535) { *detail = (int64_t)BE * nloc; return BRAS_ERR_TOO_LARGE; }
     std::vector<Blk> blk(nblk);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int b = 0; b < nblk; ++b) {
+        const int e0 = t->blk_e0[b], ne = t->blk_e0[b + 1] - e0;
+        Blk& B = blk[b];
+        B.srt.resize((size_t)ne * nloc);
+        for (int e = 0; e < ne; ++e) {
+            const int64_t K = t->perm[e0 + e];
+            for (int a = 0; a < nloc; ++a) B.srt[(size_t)a * ne + e] = {l2g[K * nloc + a], a * ne + e};
+        }
+        std::sort(B.srt.begin(), B.srt.end());
+        // (block sizes are chosen so that m = ne * nloc < 65536 and nu < 32768 hold: the
+        // positions and local indices are 16-bit, bit 15 of a local index being the sign)
+        for (size_t i = 0; i < B.srt.size(); ++i)
+            if (i == 0 || B.srt[i].first != B.srt[i - 1].first) {
+                B.uq.push_back(B.srt[i].first);
+                B.first.push_back((int32_t)i);
+            }
+        B.first.push_back((int32_t)B.srt.size());
+    }
+    // pass 2: the blocks of every shared dof, ascending (CSR over dofs, filled in block order)
+    std::vector<int32_t> nb_of((size_t)n + 1, 0);
+    for (int b = 0; b < nblk; ++b) {
+        const Blk& B = blk[b];
+        for (size_t i = 0; i < B.uq.size(); ++i)
+            if (B.first[i + 1] - B.first[i] != d[B.uq[i]]) nb_of[(size_t)B.uq[i] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) nb_of[i + 1] += nb_of[i];
+    std::vector<int32_t> blist((size_t)nb_of[n]);
+    {
+        std::vector<int32_t> fill(nb_of.begin(), nb_of.end() - 1);
+        for (int b = 0; b < nblk; ++b) {
+            const Blk& B = blk[b];
+            for (size_t i = 0; i < B.uq.size(); ++i)
+                if (B.first[i + 1] - B.first[i] != d[B.uq[i]]) blist[fill[B.uq[i]]++] = b;
+        }
+    }
+    // pass 3: groups = runs of shared dofs with equal block lists (dofs sorted by (list, id))
+    std::vector<int32_t> shd;
+    for (int64_t i = 0; i < n; ++i)
+        if (nb_of[i + 1] > nb_of[i]) shd.push_back((int32_t)i);
+    auto lst_less = [&](int32_t a, int32_t b) {
+        const int32_t *pa = &blist[nb_of[a]], *ea = &blist[nb_of[a + 1]];
+        const int32_t *pb = &blist[nb_of[b]], *eb = &blist[nb_of[b + 1]];
+        if (std::lexicographical_compare(pa, ea, pb, eb)) return true;
+        if (std::lexicographical_compare(pb, eb, pa, ea)) return false;
+        return a < b;
+    };
+    std::sort(shd.begin(), shd.end(), lst_less);
+    std::vector<int32_t> gid((size_t)n, -1);
+    t->grp_size.clear();
+    t->grp_cnt.clear();
+    for (size_t j = 0; j < shd.size(); ++j) {
+        const int32_t a = shd[j];
+        const bool same = j > 0 && std::equal(&blist[nb_of[shd[j - 1]]], &blist[nb_of[shd[j - 1] + 1]],
+                                              &blist[nb_of[a]], &blist[nb_of[a + 1]]);
+        if (!same) {
+            t->grp_size.push_back(0);
+            t->grp_cnt.push_back(nb_of[a + 1] - nb_of[a]);
+        }
+        gid[a] = (int32_t)t->grp_size.size() - 1;
+        t->grp_size.back()++;
+    }
+    const int64_t ngrp = (int64_t)t->grp_size.size();
+    t->nsh = (int64_t)shd.size();
+
+    // pass 4, per block: interior dofs by ascending id, then the shared ones by (group, id)
     int max_u = 0, max_ne = 0;
 #pragma omp parallel for schedule(dynamic, 4) reduction(max : max_u, max_ne)
     for (int b = 0; b < nblk; ++b) {
-        const int e0 = t->blk_e0[b], ne = t->blk_e0[b + 1] - e0;
-        std::vector<std::pair<int32_t, int32_t>> pr((size_t)ne * nloc);   // (dof, slot)
-        for (int e = 0; e < ne; ++e) {
-            const int64_t K = t->perm[e0 + e];
-            for (int a = 0; a < nloc; ++a) pr[(size_t)a * ne + e] = {l2g[K * nloc + a], a * ne + e};
-        }
-        std::vector<std::pair<int32_t, int32_t>> srt(pr);
-        std::sort(srt.begin(), srt.end());
-        // unique dofs with in-block copy counts
-        std::vector<int32_t> uq, first;
-        for (size_t i = 0; i < srt.size(); ++i)
-            if (i == 0 || srt[i].first != srt[i - 1].first) { uq.push_back(srt[i].first); first.push_back((int32_t)i); }
-        first.push_back((int32_t)srt.size());
-        const int nu = (int)uq.size();
-        // interior first, then shared, each in ascending dof id (neighbouring threads touch
-        // neighbouring entries of x and y)
-        std::vector<int32_t> order;
-        order.reserve(nu);
-        for (int i = 0; i < nu; ++i) if (first[i + 1] - first[i] == d[uq[i]]) order.push_back(i);
-        const int nint = (int)order.size();
-        for (int i = 0; i < nu; ++i) if (first[i + 1] - first[i] != d[uq[i]]) order.push_back(i);
-        std::vector<int32_t> uidx(nu);
+        const int ne = t->blk_e0[b + 1] - t->blk_e0[b];
         Blk& B = blk[b];
-        B.nint = nint;
-        B.ids.resize(nu);
-        B.incoff.resize(nu + 1);
-        B.inc.resize((size_t)ne * nloc);
-        int off = 0;
-        for (int u = 0; u < nu; ++u) {
-            const int i = order[u];
-            uidx[i] = u;
-            B.ids[u] = uq[i];
-            B.incoff[u] = (uint16_t)off;
-            for (int s = first[i]; s < first[i + 1]; ++s) B.inc[off++] = (uint16_t)srt[s].second;
-        }
-        B.incoff[nu] = (uint16_t)off;
-        // loc: block-local index of each broken copy, sign in bit 15
-        B.loc.resize((size_t)ne * nloc);
+        const int nu = (int)B.uq.size();
         for (int i = 0; i < nu; ++i)
-            for (int s = first[i]; s < first[i + 1]; ++s) {
-                const int slot = srt[s].second, a = slot / ne, e = slot % ne;
-                const int64_t K = t->perm[e0 + e];
-                const bool neg = signs && signs[K * nloc + a] < 0;
-                B.loc[slot] = (uint16_t)(uidx[i] | (neg ? 0x8000 : 0));
-            }
+            if (B.first[i + 1] - B.first[i] == d[B.uq[i]]) B.order.push_back(i);
+        B.nint = (int)B.order.size();
+        // interior dofs by (copy count, id): the lanes of a warp then sum runs of one length
+        std::stable_sort(B.order.begin(), B.order.end(), [&](int32_t i, int32_t j) {
+            return B.first[i + 1] - B.first[i] < B.first[j + 1] - B.first[j];
+        });
+        std::vector<int32_t> sh;
+        for (int i = 0; i < nu; ++i)
+            if (B.first[i + 1] - B.first[i] != d[B.uq[i]]) sh.push_back(i);
+        std::sort(sh.begin(), sh.end(), [&](int32_t i, int32_t j) {
+            const int32_t gi = gid[B.uq[i]], gj = gid[B.uq[j]];
+            return gi != gj ? gi < gj : B.uq[i] < B.uq[j];
+        });
+        B.order.insert(B.order.end(), sh.begin(), sh.end());
+        B.ids.resize(nu);
+        B.gid_of.resize(nu - B.nint);
+        for (int u = 0; u < nu; ++u) {
+            B.ids[u] = B.uq[B.order[u]];
+            if (u >= B.nint) B.gid_of[u - B.nint] = gid[B.ids[u]];
+        }
         max_u = std::max(max_u, nu);
         max_ne = std::max(max_ne, ne);
     }
     t->max_u = max_u;
     t->max_ne = max_ne;
-    // packets: part A = ids | d | incoff, part B = loc | inc, 16-byte aligned sections
+    // packets: part A = ids | d, part B = loc | pos | ends, 16-byte aligned sections
     t->blk_u0.resize(nblk + 1);
     t->blk_nint.resize(nblk);
     t->blk_p0.resize(nblk);
     t->blk_pkt.resize(nblk + 1);
+    t->blk_g0.assign(nblk + 1, 0);
     int64_t U = 0, P = 0, bytes = 0;
     uint32_t max_pkt = 0;
+    int max_bg = 0;
     for (int b = 0; b < nblk; ++b) {
-        const uint32_t nu = (uint32_t)blk[b].ids.size();
+        const Blk& B = blk[b];
+        const uint32_t nu = (uint32_t)B.ids.size();
         const uint32_t m = (uint32_t)(t->blk_e0[b + 1] - t->blk_e0[b]) * (uint32_t)nloc;
+        uint32_t ng = 0;
+        for (size_t j = 0; j < B.gid_of.size(); ++j)
+            if (j == 0 || B.gid_of[j] != B.gid_of[j - 1]) ++ng;
         const uint32_t sz = pkt_size_a(nu) + pkt_size_b(m);
         t->blk_u0[b] = (int32_t)U;
-        t->blk_nint[b] = blk[b].nint;
+        t->blk_nint[b] = B.nint;
         t->blk_p0[b] = (int32_t)P;
         t->blk_pkt[b] = bytes;
         U += nu;
-        P += (int64_t)nu - blk[b].nint;
+        P += (int64_t)nu - B.nint;
         bytes += sz;
         max_pkt = std::max(max_pkt, sz);
+        t->blk_g0[b + 1] = t->blk_g0[b] + (int32_t)ng;
+        max_bg = std::max(max_bg, (int)ng);
     }
     t->blk_u0[nblk] = (int32_t)U;
     t->blk_pkt[nblk] = bytes;
     t->npart = P;
     t->U_tot = U;
     t->max_pkt = max_pkt;
+    t->max_bg = max_bg;
+    // the groups of each block, and the partial slots of each group in ascending block order
+    t->bg_gid.resize(t->blk_g0[nblk]);
+    t->bg_u.resize(t->blk_g0[nblk]);
+    t->grp_slot0.assign(ngrp + 1, 0);
+    for (int64_t g = 0; g < ngrp; ++g) t->grp_slot0[g + 1] = t->grp_slot0[g] + t->grp_cnt[g];
+    t->grp_slots.assign(t->grp_slot0[ngrp], 0);
+    {
+        std::vector<int32_t> fill(t->grp_slot0.begin(), t->grp_slot0.end() - 1);
+        for (int b = 0; b < nblk; ++b) {
+            const Blk& B = blk[b];
+            int k = t->blk_g0[b];
+            for (size_t j = 0; j < B.gid_of.size(); ++j)
+                if (j == 0 || B.gid_of[j] != B.gid_of[j - 1]) {
+                    const int32_t g = B.gid_of[j];
+                    t->bg_gid[k] = g;
+                    t->bg_u[k] = B.nint + (int32_t)j;
+                    t->grp_slots[fill[g]++] = t->blk_p0[b] + (int32_t)j;
+                    ++k;
+                }
+        }
+    }
+    // the combine pass walks the groups: their dofs (ids, multiplicities) in group order
+    t->grp_item0.assign(ngrp + 1, 0);
+    for (int64_t g = 0; g < ngrp; ++g) t->grp_item0[g + 1] = t->grp_item0[g] + t->grp_size[g];
+    t->sh_ids.assign(t->grp_item0[ngrp], 0);
+    t->sh_d.assign(t->grp_item0[ngrp], 0);
+    {
+        std::vector<int32_t> fill(t->grp_item0.begin(), t->grp_item0.end() - 1);
+        for (size_t j = 0; j < shd.size(); ++j) {
+            const int32_t a = shd[j], g = gid[a];
+            t->sh_ids[fill[g]] = a;
+            t->sh_d[fill[g]++] = (uint16_t)std::min<int32_t>(d[a], 65535);
+        }
+    }
     t->pkt.assign((size_t)bytes, 0);
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < nblk; ++b) {
         const Blk& B = blk[b];
+        const int ne = t->blk_e0[b + 1] - t->blk_e0[b];
         const uint32_t nu = (uint32_t)B.ids.size();
-        const uint32_t m = (uint32_t)B.loc.size();
+        const uint32_t m = (uint32_t)ne * (uint32_t)nloc;
+        const int e0 = t->blk_e0[b];
         unsigned char* p = t->pkt.data() + t->blk_pkt[b];
         std::memcpy(p, B.ids.data(), 4 * (size_t)nu);
         uint16_t* dm = reinterpret_cast<uint16_t*>(p + pkt_off_d(nu));
         for (uint32_t u = 0; u < nu; ++u) dm[u] = (uint16_t)std::min<int32_t>(d[B.ids[u]], 65535);
-        std::memcpy(p + pkt_off_incoff(nu), B.incoff.data(), 2 * (size_t)(nu + 1));
-        const uint32_t sa = pkt_size_a(nu);
-        std::memcpy(p + sa, B.loc.data(), 2 * (size_t)m);
-        // position of every broken copy in the dof-sorted order (the inverse of the incidence
-        // list): a cell writes its result for copy (a, e) there, and each dof then sums one
-        // contiguous run
-        uint16_t* pos = reinterpret_cast<uint16_t*>(p + sa + pad16(2u * m));
-        for (uint32_t s = 0; s < m; ++s) pos[B.inc[s]] = (uint16_t)s;
-    }
-    // shared dofs: partial slots in ascending block order per dof
-    std::vector<std::pair<int32_t, int32_t>> sh;   // (dof, slot)
-    sh.reserve(P);
-    for (int b = 0; b < nblk; ++b) {
-        const Blk& B = blk[b];
-        for (size_t u = B.nint; u < B.ids.size(); ++u)
-            sh.push_back({B.ids[u], t->blk_p0[b] + (int32_t)(u - B.nint)});
-    }
-    std::stable_sort(sh.begin(), sh.end(), [](auto& x, auto& y) { return x.first < y.first; });
-    t->sh_ids.clear();
-    t->sh_off.clear();
-    t->sh_slots.resize(sh.size());
-    for (size_t i = 0; i < sh.size(); ++i) {
-        if (i == 0 || sh[i].first != sh[i - 1].first) {
-            t->sh_ids.push_back(sh[i].first);
-            t->sh_off.push_back((int32_t)i);
+        unsigned char* pb = p + pkt_size_a(nu);
+        uint16_t* loc = reinterpret_cast<uint16_t*>(pb);
+        uint16_t* pos = reinterpret_cast<uint16_t*>(pb + pkt_off_pos(m));
+        uint32_t* ends = reinterpret_cast<uint32_t*>(pb + pkt_off_ends(m));
+        // dof-sorted order: the dofs in block-local order u, each dof's copies by ascending slot
+        uint32_t off = 0;
+        for (uint32_t u = 0; u < nu; ++u) {
+            const int i = B.order[u];
+            for (int s = B.first[i]; s < B.first[i + 1]; ++s) {
+                const int slot = B.srt[s].second, a = slot / ne, e = slot % ne;
+                const int64_t K = t->perm[e0 + e];
+                const bool neg = signs && signs[K * nloc + a] < 0;
+                loc[slot] = (uint16_t)(u | (neg ? 0x8000u : 0u));
+                pos[slot] = (uint16_t)off++;
+            }
+            ends[(off - 1) >> 5] |= 1u << ((off - 1) & 31);
         }
-        t->sh_slots[i] = sh[i].second;
     }
-    t->sh_off.push_back((int32_t)sh.size());
     return BRAS_OK;
 }
 

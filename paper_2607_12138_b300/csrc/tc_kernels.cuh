@@ -1,8 +1,8 @@
 // H1 block kernel with the local multiply on the 5th-generation tensor cores (tcgen05).
 //
 // Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async
-// copies, x staged in shared memory, fixed-order in-block incidence sums, partials of
-// boundary dofs.  The difference is stage 2: for an affine H1 cell the local operator is
+// copies, x staged in shared memory, fixed-order in-block dof sums, partials of boundary dofs
+// added up by the combine pass.  The difference is stage 2: for an affine H1 cell the local operator is
 // c_K * A_ref with one reference matrix shared by all cells (A_ref = M_ref or M_ref^{-1},
 // Eq. piola_mass_pullbacks), so a block's local products form one GEMM
 //      Z[cells x n] = Xt[cells x k] * A_ref^T,
@@ -119,6 +119,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// Bytes reserved for the B tiles, a multiple of 128 (one right-hand side: the scan scratch of
+// stage 3 takes the region over once the GEMM is done).
+template <int NLOC>
+__host__ __device__ constexpr uint32_t tc_btile_region() {
+    return (2 * TcShape<NLOC>::B_BYTES + 127u) & ~127u;
+}
+
 struct TcArgs {
     BlockArgs A;
     const unsigned char* btile;   // [Abig | Asmall] pre-arranged, 2 * N * K * 4 bytes
@@ -148,11 +155,15 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const uint32_t TMEM_COLS = (uint32_t)tiles * Sh::TILE_COLS;   // 128 or 256
     const BlockArgs& A = TA.A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);         // [0] tab A, [1] tab B, [2] B tile, [3] MMA
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);   // [0] tab A, [1] tab B, [2] B tile, [3] MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + 64);
     unsigned char* btile = smem_raw + 128;                           // 2 * B_BYTES, 128-B aligned
-    unsigned char* tab = btile + 2 * Sh::B_BYTES;
+    unsigned char* tab = btile + tc_btile_region<NLOC>();
     float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u][CW]
+    // stage 3's scan scratch (32 ints): over the B tiles (dead once the last GEMM has completed)
+    // for one right-hand side, after the products for the multi-RHS passes
+    int* wsum = MR ? reinterpret_cast<int*>(xs + ((A.max_u * CW + 3) & ~3) + (((size_t)NLOC * A.max_ne * CW + 3) & ~(size_t)3))
+                   : reinterpret_cast<int*>(btile);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int lt = TPC == 2 ? (tid & 127) : tid;              // this thread's lane in the pass
@@ -187,11 +198,13 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const uint32_t tile_col = TPC == 2 ? 0u : (uint32_t)(warp >> 2) * Sh::TILE_COLS;
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
-    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
+    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pad16(2u * ne * NLOC));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
+    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     bool ok = cta_wait(&bars[0], 0, A.status, true);
+    bool tmem_live = true;   // block-uniform
     int pending = -1;        // (thread 0) parity of a committed GEMM whose completion was not seen
     uint32_t commits = 0;    // GEMMs committed on bars[3] so far (its phase parity)
     const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
@@ -375,33 +388,35 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         }
         if (!ok) break;
 
+        if constexpr (!MR) {
+            // every product is in shared memory: release the tensor memory now, so that the next
+            // CTA on this SM can allocate it while this one sums and stores
+            if (warp == 0) {
+                tc_fence_after();
+                tmem_dealloc(tmem, TMEM_COLS);
+            }
+            tmem_live = false;
+        }
+        // the start of every dof's run (over the staged x, dead by now), then the per-dof sums
+        uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
+        run_starts((int)m, ends, incoff, wsum);
+        __syncthreads();
         if constexpr (MR) {
             using V = Chunk<float>::V;
-            const V* zv = reinterpret_cast<const V*>(zs);
-            for (int u = tid; u < nu; u += blockDim.x) {
-                const int s0 = incoff[u], s1 = incoff[u + 1];
-                // the copies of dof u sit contiguously in zs[s0, s1); fixed summation order
-                V acc = vzero(V{});
-                for (int s = s0; s < s1; ++s) vadd(acc, zv[s]);
-                if (u < nint) {
-                    if (OP == OP_BRAS) {
-#pragma unroll
-                        for (int j = 0; j < CW; ++j) vget(acc, j) = div_by_count(vget(acc, j), dmul[u]);
-                    }
-                    st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, acc);
-                } else {
-                    st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, acc);
-                }
-            }
+            dof_run_sums<V>(nu, incoff, reinterpret_cast<const V*>(zs), vzero(V{}),
+                            [](V a, const V& c) { return vsum(a, c); },
+                            [&](int u, V v) { store_dof<float, OP, true, V>(u, v, nint, ids, dmul, y, part, nrhs, r0, rc, vec, p0); });
+            __syncthreads();   // incoff (over xs) read before the next chunk stages x
         } else {
-            block_dof_sums<float, OP>(nu, nint, incoff, zs, dmul, ids, y, nrhs, r0, part, p0);
+            dof_run_sums<float>(nu, incoff, zs, 0.f, [](float a, float c) { return a + c; },
+                                [&](int u, float v) { store_dof<float, OP, false, float>(u, v, nint, ids, dmul, y, part, nrhs, r0, 1, false, p0); });
         }
     }
     // a GEMM committed but not seen complete: drain it before the columns are released
     if (pending >= 0 && tid == 0) mbar_wait_parity_bounded(&bars[3], (uint32_t)pending, A.status);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (tmem_live && warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
@@ -416,20 +431,20 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     }
 }
 
-// alias: the products reuse the loc/pos bytes of the packet (4 per copy; one right-hand side)
+// alias: the products reuse the loc/pos bytes of the packet (4 per copy; one right-hand side).
+// One right-hand side: the scan scratch of stage 3 sits over the B tiles.
 template <int NLOC>
 size_t tc_smem_bytes(const BlockArgs& A, bool mr = false, bool alias = true) {
-    using Sh = TcShape<NLOC>;
     const size_t cw = mr ? Chunk<float>::CW : 1;
-    return 128 + 2 * (size_t)Sh::B_BYTES + ((A.max_pkt + 127u) & ~127u) +
+    return 128 + (size_t)tc_btile_region<NLOC>() + ((A.max_pkt + 127u) & ~127u) +
            sizeof(float) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) +
-                            ((mr || !alias) ? (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) : 0));
+                            ((mr || !alias) ? (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) : 0)) +
+           (mr ? 128 : 0);
 }
 
 template <int NLOC, int OP>
-cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y, float* part, int nrhs,
-                            const float* dinv, int64_t nsh, const int32_t* sh_ids, const int32_t* sh_off,
-                            const int32_t* sh_slots, cudaStream_t st) {
+cudaError_t launch_block_tc(const TcArgs& TA, const CombineArgs& G, int nblk, const float* x, float* y, float* part,
+                            int nrhs, cudaStream_t st) {
     const bool mr = nrhs > 1 && tc_smem_bytes<NLOC>(TA.A, true) <= (size_t)smem_optin_bytes();
     // blocks of at most 128 cells: one tile, two threads per cell
     const bool two = !mr && TA.A.max_ne <= 128;
@@ -454,7 +469,7 @@ cudaError_t launch_block_tc(const TcArgs& TA, int nblk, const float* x, float* y
     count_launch(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    return launch_combine<float, OP>(nsh, sh_ids, sh_off, sh_slots, part, TA.A.npart, dinv, y, nrhs, mr, st);
+    return launch_group_combine<float, OP>(G, part, TA.A.npart, y, nrhs, mr, st);
 }
 
 }  // namespace bras

@@ -4,10 +4,11 @@
 // Input (little endian): int64 E, int32 nloc, int64 n, int32 dim, int32 BE, int64 nvert,
 //   int32 has_signs, int32 has_groups, int32 l2g[E*nloc], [int8 signs[E*nloc]],
 //   double coords[nvert*dim], int32 cells[E*(dim+1)], [int32 groups[E]].
-// Output: int32 rc, int64 detail, and for rc == 0: int32 BE, nblk, max_u, max_ne,
-//   uint32 max_pkt, int64 npart, U_tot, then the arrays perm, blk_e0, blk_u0, blk_nint, blk_p0,
-//   sh_ids, sh_off, sh_slots (int32), blk_pkt (int64), pkt (uint8), dinv (double), each
-//   preceded by its int64 length.
+// Output: int32 rc, int64 detail, and for rc == 0: int32 BE, nblk, max_u, max_ne, max_bg,
+//   uint32 max_pkt, int64 npart, U_tot, nsh, then the arrays perm, blk_e0, blk_u0, blk_nint,
+//   blk_p0, grp_size, grp_cnt, grp_slot0, grp_slots, blk_g0, bg_gid, bg_u, grp_item0, sh_ids
+//   (int32), sh_d (uint16), blk_pkt (int64), pkt (uint8), dinv (double), each preceded by its
+//   int64 length.
 #include <cstdio>
 #include <vector>
 
@@ -62,11 +63,15 @@ int main(int argc, char** argv) {
         wr(out, (int32_t)t.nblk);
         wr(out, (int32_t)t.max_u);
         wr(out, (int32_t)t.max_ne);
+        wr(out, (int32_t)t.max_bg);
         wr(out, (uint32_t)t.max_pkt);
         wr(out, (int64_t)t.npart);
         wr(out, (int64_t)t.U_tot);
-        for (const auto* v : {&t.perm, &t.blk_e0, &t.blk_u0, &t.blk_nint, &t.blk_p0, &t.sh_ids, &t.sh_off, &t.sh_slots})
+        wr(out, (int64_t)t.nsh);
+        for (const auto* v : {&t.perm, &t.blk_e0, &t.blk_u0, &t.blk_nint, &t.blk_p0, &t.grp_size, &t.grp_cnt,
+                              &t.grp_slot0, &t.grp_slots, &t.blk_g0, &t.bg_gid, &t.bg_u, &t.grp_item0, &t.sh_ids})
             wr_vec(out, *v);
+        wr_vec(out, t.sh_d);
         wr_vec(out, t.blk_pkt);
         wr_vec(out, t.pkt);
         wr_vec(out, t.dinv);

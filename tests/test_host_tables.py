@@ -5,12 +5,14 @@ table; the tests below read the table packets back and
 
 * check their invariants: the cell order is a permutation, each block's copies are listed
   once, the dof-sorted order keeps the copies of a dof by ascending slot (the fixed
-  summation order), interior dofs have all their copies in the block, the partial slots of
-  each shared dof come in ascending block order, d = the copy counts;
+  summation order) and its end bits close every dof's run, interior dofs have all their
+  copies in the block, a group's dofs are exactly the shared dofs with one block set, listed
+  contiguously by ascending id in each of its blocks, its partial slots in ascending block
+  order, d = the copy counts;
 * replay the block apply from the packets alone -- gather with the sign bits and 1/d, local
-  products, dof-sorted sums, interior stores and the combine pass over the partials -- with
-  the oracle's element matrices, and compare with the oracle's assembled M and
-  M_bras^{-1} (Eq. M_PMbrP, Eq. mhatinvbras_def);
+  products, per-dof sums over the runs the end bits delimit, interior stores, partials, and
+  the group sums of the last block -- with the oracle's element matrices, and compare with
+  the oracle's assembled M and M_bras^{-1} (Eq. M_PMbrP, Eq. mhatinvbras_def);
 * check the error codes of a bad map (an l2g entry out of range, a dof with no copy).
 """
 import os
@@ -62,14 +64,16 @@ def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
     if rc != 0:
         return rc, detail, None
     o = 12
-    BE_, nblk, max_u, max_ne, max_pkt = struct.unpack_from("<iiiiI", buf, o)
-    o += 20
-    npart, U_tot = struct.unpack_from("<qq", buf, o)
-    o += 16
-    t = {"BE": BE_, "nblk": nblk, "max_u": max_u, "max_ne": max_ne, "max_pkt": max_pkt, "npart": npart,
-         "U_tot": U_tot}
+    BE_, nblk, max_u, max_ne, max_bg, max_pkt = struct.unpack_from("<iiiiiI", buf, o)
+    o += 24
+    npart, U_tot, nsh = struct.unpack_from("<qqq", buf, o)
+    o += 24
+    t = {"BE": BE_, "nblk": nblk, "max_u": max_u, "max_ne": max_ne, "max_bg": max_bg, "max_pkt": max_pkt,
+         "npart": npart, "U_tot": U_tot, "nsh": nsh}
     for name, dt in (("perm", np.int32), ("blk_e0", np.int32), ("blk_u0", np.int32), ("blk_nint", np.int32),
-                     ("blk_p0", np.int32), ("sh_ids", np.int32), ("sh_off", np.int32), ("sh_slots", np.int32),
+                     ("blk_p0", np.int32), ("grp_size", np.int32), ("grp_cnt", np.int32), ("grp_slot0", np.int32),
+                     ("grp_slots", np.int32), ("blk_g0", np.int32), ("bg_gid", np.int32), ("bg_u", np.int32),
+                     ("grp_item0", np.int32), ("sh_ids", np.int32), ("sh_d", np.uint16),
                      ("blk_pkt", np.int64), ("pkt", np.uint8), ("dinv", np.float64)):
         (cnt,) = struct.unpack_from("<q", buf, o)
         o += 8
@@ -81,21 +85,28 @@ def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
 
 
 def packet(t, b, nloc):
-    """The sections of block b's packet (layout of csrc/packet.h)."""
+    """The sections of block b's packet (layout of csrc/packet.h); incoff[u] = start of dof u's
+    run in the dof-sorted order, read off the end bits."""
     ne = int(t["blk_e0"][b + 1] - t["blk_e0"][b])
     nu = int(t["blk_u0"][b + 1] - t["blk_u0"][b])
     p = t["pkt"][t["blk_pkt"][b]:t["blk_pkt"][b + 1]]
     off_d = _pad16(4 * nu)
-    off_inc = off_d + _pad16(2 * nu)
-    sa = off_inc + _pad16(2 * nu + 2)
+    sa = off_d + _pad16(2 * nu)
     m = ne * nloc
-    sb = 2 * _pad16(2 * m)
+    off_ends = 2 * _pad16(2 * m)
+    nw = (m + 31) // 32
+    sb = off_ends + _pad16(4 * nw)
     assert p.size == sa + sb
     ids = p[:4 * nu].view(np.int32)
     d = p[off_d:off_d + 2 * nu].view(np.uint16)
-    incoff = p[off_inc:off_inc + 2 * (nu + 1)].view(np.uint16)
     loc = p[sa:sa + 2 * m].view(np.uint16)
     pos = p[sa + _pad16(2 * m):sa + _pad16(2 * m) + 2 * m].view(np.uint16)
+    words = p[sa + off_ends:sa + off_ends + 4 * nw].view(np.uint32)
+    bits = ((words[:, None] >> np.arange(32, dtype=np.uint32)[None, :]) & 1).ravel()
+    assert not bits[m:].any()                                   # no end bit past the copies
+    ends = np.nonzero(bits[:m])[0]
+    assert ends.size == nu and (nu == 0 or ends[-1] == m - 1)
+    incoff = np.concatenate([[0], ends + 1]).astype(np.int64)
     return ne, nu, ids, d, incoff, loc, pos
 
 
@@ -109,6 +120,7 @@ def check_invariants(t, l2g, signs, n, groups=None):
     np.testing.assert_allclose(t["dinv"], 1.0 / d, rtol=0, atol=0)
     seen_interior = []
     shared_slots = {}
+    groups_seen = {}
     for b in range(t["nblk"]):
         ne, nu, ids, dm, incoff, loc, pos = packet(t, b, nloc)
         e0, nint = int(t["blk_e0"][b]), int(t["blk_nint"][b])
@@ -133,16 +145,51 @@ def check_invariants(t, l2g, signs, n, groups=None):
         counts = np.diff(incoff.astype(np.int64))
         assert np.array_equal(counts[:nint], d[ids[:nint]])   # interior: every copy in the block
         assert np.all(counts[nint:] < d[ids[nint:]])
-        assert np.all(np.diff(ids[:nint]) > 0) and np.all(np.diff(ids[nint:]) > 0)
         seen_interior += ids[:nint].tolist()
         for j, g in enumerate(ids[nint:]):
-            shared_slots.setdefault(int(g), []).append(int(t["blk_p0"][b]) + j)
+            shared_slots.setdefault(int(g), []).append((b, int(t["blk_p0"][b]) + j))
+        # interior dofs by ascending copy count (then id)
+        counts_int = counts[:nint]
+        assert np.all(np.diff(counts_int) >= 0)
+        for c_ in np.unique(counts_int):
+            assert np.all(np.diff(ids[:nint][counts_int == c_]) > 0)
+        # the block's groups cover its shared dofs in order, each a contiguous run
+        g0, g1 = int(t["blk_g0"][b]), int(t["blk_g0"][b + 1])
+        assert g1 - g0 <= t["max_bg"]
+        u = nint
+        for k in range(g0, g1):
+            g = int(t["bg_gid"][k])
+            assert int(t["bg_u"][k]) == u
+            size = int(t["grp_size"][g])
+            assert np.all(np.diff(ids[u:u + size]) > 0)           # ascending ids inside a group
+            groups_seen.setdefault(g, []).append((b, ids[u:u + size].tolist(), int(t["blk_p0"][b]) + u - nint))
+            u += size
+        assert u == nu
     assert sorted(seen_interior + list(shared_slots)) == list(range(n))   # each dof ends somewhere once
-    assert t["sh_ids"].tolist() == sorted(shared_slots)
-    for j, g in enumerate(t["sh_ids"]):
-        sl = t["sh_slots"][t["sh_off"][j]:t["sh_off"][j + 1]].tolist()
-        assert sl == shared_slots[int(g)] and sl == sorted(sl)          # ascending block order
+    assert t["nsh"] == len(shared_slots)
     assert t["npart"] == sum(len(v) for v in shared_slots.values())
+    ngrp = t["grp_size"].size
+    assert sorted(groups_seen) == list(range(ngrp))
+    block_set = {}
+    for g, members in groups_seen.items():
+        blocks = [mb for mb, _, _ in members]
+        assert blocks == sorted(blocks) and len(blocks) == int(t["grp_cnt"][g])    # ascending block order
+        assert all(lst == members[0][1] for _, lst, _ in members)             # same dofs, same order
+        sl = t["grp_slots"][t["grp_slot0"][g]:t["grp_slot0"][g + 1]].tolist()
+        assert sl == [s0 for _, _, s0 in members]
+        # the combine pass's group-major items: the group's dofs in order, with their d
+        items = t["sh_ids"][t["grp_item0"][g]:t["grp_item0"][g + 1]].tolist()
+        assert items == members[0][1]
+        assert t["sh_d"][t["grp_item0"][g]:t["grp_item0"][g + 1]].tolist() == [int(d[v]) for v in items]
+        for dof in members[0][1]:
+            assert [bb for bb, _ in shared_slots[dof]] == blocks               # the dof's blocks = the group's
+            block_set[dof] = tuple(blocks)
+    # a group holds every shared dof of its block set: no two groups share one
+    sets = {}
+    for g, members in groups_seen.items():
+        key = tuple(mb for mb, _, _ in members)
+        assert key not in sets
+        sets[key] = g
 
 
 def replay(t, A, x, nloc, bras):
@@ -169,11 +216,15 @@ def replay(t, A, x, nloc, bras):
                 y[ids[u]] = acc / dm[u] if bras else acc
             else:
                 part[t["blk_p0"][b] + u - nint] = acc
-    for j, g in enumerate(t["sh_ids"]):
-        acc = 0.0
-        for s in range(t["sh_off"][j], t["sh_off"][j + 1]):
-            acc += part[t["sh_slots"][s]]
-        y[g] = acc * t["dinv"][g] if bras else acc
+    # the combine pass: every group's dofs, partials in ascending block order
+    for g in range(t["grp_item0"].size - 1):
+        i0, i1 = t["grp_item0"][g], t["grp_item0"][g + 1]
+        slots = t["grp_slots"][t["grp_slot0"][g]:t["grp_slot0"][g + 1]]
+        for i in range(i1 - i0):
+            acc = 0.0
+            for sl in slots:
+                acc += part[sl + i]
+            y[t["sh_ids"][i0 + i]] = acc / t["sh_d"][i0 + i] if bras else acc
     return y
 
 
