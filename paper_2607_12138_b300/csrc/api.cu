@@ -137,6 +137,14 @@ int install_tables(bras_ctx* c, const HostTables& t) {
     c->U_tot = t.U_tot;
     c->npart = t.npart;
     c->nsh = t.nsh;
+    {   // at most 2^h copies of a dof in a block: low words of fx_lo = 31 - h bits (sums below
+        // 2^31), products below 2^fx_top with fx_top = 60 - 2h (high-word sums below 2^29 + 2^h)
+        int h = 0;
+        while ((1 << h) < t.max_copies) ++h;
+        c->fx_lo = 31 - h;
+        c->fx_top = 60 - 2 * h;
+        c->fx_top64 = 61 - h;
+    }
     c->ngrp = (int64_t)t.grp_size.size();
     c->max_pkt = t.max_pkt;
     int rc;
@@ -309,6 +317,21 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         const int n = nloc;
         std::vector<double> inv;
         if (!spd_inverse(ref.R, n, inv)) return BRAS_ERR_NOT_SPD;
+        // exponent bounds of the row abs-sums of M_ref and M_ref^{-1}, plus one for the rounding
+        // of the FP32 / TF32 copies
+        auto row_exp = [n](const std::vector<double>& A) {
+            double best = 0.0;
+            for (int r = 0; r < n; ++r) {
+                double s = 0.0;
+                for (int q = 0; q < n; ++q) s += std::fabs(A[(size_t)r * n + q]);
+                best = std::max(best, s);
+            }
+            int ex = 0;
+            std::frexp(best, &ex);
+            return ex + 1;
+        };
+        c->er_mass = row_exp(ref.R);
+        c->er_bras = row_exp(inv);
         std::vector<float> R32(ref.R.begin(), ref.R.end()), I32(inv.begin(), inv.end());
         if ((rc = upload(c, &c->Mref64, ref.R.data(), ref.R.size()))) return rc;
         if ((rc = upload(c, &c->Minvref64, inv.data(), inv.size()))) return rc;
@@ -363,6 +386,19 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
             cudaStreamSynchronize(st) != cudaSuccess)
             return BRAS_ERR_CUDA;
         if (hbad != none) { set_detail((int64_t)hbad); return BRAS_ERR_NOT_SPD; }
+        // exponent bounds of the cells' row abs-sums (plus one for the FP32 / bf16 roundings)
+        int* eb = dalloc<int>(c, 2);
+        if (!eb) return BRAS_ERR_OOM;
+        const int lo[2] = {-100000, -100000};
+        int he[2] = {0, 0};
+        if (cudaMemcpy(eb, lo, sizeof(lo), cudaMemcpyHostToDevice) != cudaSuccess ||
+            run_row_bound(nloc, n_cell, c->Epad, c->Mpk64, eb, st) != cudaSuccess ||
+            run_row_bound(nloc, n_cell, c->Epad, c->Minvpk64, eb + 1, st) != cudaSuccess ||
+            cudaMemcpyAsync(he, eb, sizeof(he), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return BRAS_ERR_CUDA;
+        c->er_mass = he[0] + 1;
+        c->er_bras = he[1] + 1;
     }
     (void)want64;
 
@@ -462,10 +498,10 @@ BlockArgs shape_args(const HostTables& t) {
 size_t block_smem_estimate(int nloc, int tsize, bool h1, const HostTables& t, int cw) {
     const int w = tsize == 4 ? 4 : 2;
     const size_t npad = (size_t)((nloc + w - 1) / w * w);
-    return 128 + ((t.max_pkt + 127u) & ~127u) +
-           (size_t)tsize * (((size_t)t.max_u * cw + 3) / 4 * 4 + ((size_t)nloc * t.max_ne * cw + 3) / 4 * 4 +
-                            (h1 ? nloc * npad : 0)) +
-           128;
+    const bool xs_cells = !h1 && nloc >= 36;   // local vectors of streamed matrices in shared memory
+    return 128 + ((t.max_pkt + 127u) & ~127u) + (size_t)tsize * (((size_t)t.max_u * cw + 3) / 4 * 4) +
+           8 * (((size_t)t.max_u * cw + 1) / 2 * 2) +
+           (size_t)tsize * ((xs_cells ? ((size_t)nloc * t.max_ne + 3) / 4 * 4 : 0) + (h1 ? nloc * npad : 0));
 }
 
 // Shared memory of the FP32 multi-RHS block kernel (16-byte chunks: 4 values a dof), 0 for a
@@ -514,6 +550,9 @@ int ensure_part(bras_ctx* c, int nrhs) {
 }
 
 LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
+    // FP64 kernels accumulate in one 64-bit word per dof; FP32, bf16 and the H1 float-float mass
+    // apply (BRAS_FP64X) in two 32-bit words
+    const bool acc64 = prec == BRAS_FP64 || (prec == BRAS_FP64X && !(c->space == BRAS_H1 && op == OP_MASS));
     if (prec == BRAS_FP64X) prec = BRAS_FP64;
     LaunchCommon L{};
     BlockArgs& A = L.A;
@@ -529,6 +568,9 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.max_u = c->max_u;
     A.max_ne = c->max_ne;
     A.max_pkt = c->max_pkt;
+    A.fx_top = acc64 ? c->fx_top64 : c->fx_top;
+    A.fx_lo = acc64 ? 0 : c->fx_lo;
+    A.fx_er = op == OP_BRAS ? c->er_bras : c->er_mass;
     const bool f64 = prec == BRAS_FP64;
     if (c->space == BRAS_H1) {
         if (op == OP_BRAS) {

@@ -15,9 +15,9 @@
 //                       broadcasts;
 //        H(curl)/H(div): z_K = A_K x_K with A_K = M_K or M_K^{-1} streamed per cell as a
 //                       packed symmetric matrix in a cell-interleaved layout (coalesced);
-//   3. the signed local results go to shared memory in dof-sorted order (the start of every
-//      dof's run is read off the end bits of the packet), and every block-local dof sums its
-//      run of copies in a fixed order (the P^T of Eq. M_PMbrP / mhatinvbras_def); dofs with
+//   3. every signed local result is added to its block-local dof's 64-bit fixed-point
+//      accumulator in shared memory (the P^T of Eq. M_PMbrP / mhatinvbras_def): integer sums
+//      are exact, so the total does not depend on the order in which copies arrive; dofs with
 //      all copies in the block are final (times 1/d for BRAS, the left D^{-1}), the others
 //      leave a partial sum;
 //   4. k_group_combine walks the groups of shared dofs (dofs whose copies lie in the same set
@@ -53,6 +53,13 @@ struct BlockArgs {
     int max_u;
     int max_ne;
     uint32_t max_pkt;          // largest packet (bytes)
+    // fixed-point dof sums (stage 3): the bound of a block's products is placed at 2^fx_top;
+    // each product's integer splits into fx_lo low bits and the rest, accumulated in two 32-bit
+    // words that cannot overflow for the copies one dof has in a block; fx_er bounds the row
+    // abs-sums of the local operator: < 2^fx_er (H1: of A_ref; vector spaces: of every A_K)
+    int fx_top;
+    int fx_lo;
+    int fx_er;
 };
 
 // Shared dofs for the combine pass (tables.cpp), in group order: item j = (global dof, group g)
@@ -157,10 +164,15 @@ __device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t
     return false;
 }
 
-// v / d for the multiplicity d: FP64 divides; FP32 multiplies by the correctly rounded
-// reciprocal (within one unit in the last place of the quotient, no division subroutine).
+// v / d for the multiplicity d: FP64 divides; FP32 multiplies by the hardware reciprocal
+// approximation of 1/d (one instruction, within one unit in the last place).
 __device__ __forceinline__ double div_by_count(double v, uint16_t d) { return v / (double)d; }
-__device__ __forceinline__ float div_by_count(float v, uint16_t d) { return v * __frcp_rn((float)d); }
+__device__ __forceinline__ float rcp_approx(float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
+}
+__device__ __forceinline__ float div_by_count(float v, uint16_t d) { return v * rcp_approx((float)d); }
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; static constexpr int W = 4; };
@@ -249,91 +261,91 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
     return __syncthreads_and(ok) != 0;
 }
 
-// ---- stage 3: per-dof sums over the dof-sorted copies ------------------------------------
-// Start of every block-local dof's run of copies in the dof-sorted order, from the end bits:
-// incoff[0] = 0, incoff[u + 1] = 1 + the position of the u-th end.  Thread t scans a
-// contiguous chunk of end-bit words; a block-wide scan of their popcounts numbers the ends.
-// Requires blockDim.x a multiple of 32; incoff is complete after the call and a CTA barrier.
-__device__ __forceinline__ void run_starts(int m, const uint32_t* __restrict__ ends, uint16_t* incoff, int* wsum) {
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int nw = (m + 31) >> 5, W = (nw + T - 1) / T;
-    const int w0 = min(tid * W, nw), w1 = min(w0 + W, nw);
-    int cnt = 0;
-    for (int k = w0; k < w1; ++k) cnt += __popc(ends[k]);
-    int v = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int x = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += x;
-    }
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    int u = v - cnt;
-    for (int j = 0; j < w; ++j) u += wsum[j];
-    for (int k = w0; k < w1; ++k) {
-        uint32_t bits = ends[k];
-        while (bits) {
-            const int bpos = __ffs(bits) - 1;
-            incoff[++u] = (uint16_t)((k << 5) + bpos + 1);
-            bits &= bits - 1u;
-        }
-    }
-    if (tid == 0) incoff[0] = 0;
+// ---- stage 3: exact fixed-point dof sums -------------------------------------------------
+// Every signed local product v of a block is added to its block-local dof's integer
+// accumulator as q = rint(v * 2^k) with shared-memory integer atomics: FP32 applies split q
+// into its low fx_lo bits and the rest, each added to a 32-bit word (with at most 2^h copies of
+// a dof in a block, fx_lo = 31 - h and fx_top = 60 - 2h, neither word can overflow); FP64
+// applies add q to one 64-bit word (fx_lo = 0, fx_top = 61 - h).  The integer sums are exact,
+// so a dof's total does not depend on the order in which its copies arrive: every apply gives
+// the same bits (no floating-point atomics).  The scale comes from an a-priori bound of the
+// block's products, |v| < 2^(ex + ec + fx_er) with ex, ec the block's largest exponents of the
+// staged x and of the cell factors (H1; 0 for the vector spaces) and fx_er that of the local
+// operator's row abs-sums, placed at 2^fx_top: k = fx_top - ex - ec - fx_er.  The total is
+// converted back once, rounded to nearest.  Products well below the bound keep an absolute
+// resolution of 2^-k, about 2^-fx_top (~1e-16) of the bound.
+constexpr int kExpZero = -100000;   // exponent bound of zero
+constexpr int kExpBad = 100000;     // of an infinity or a NaN
+
+// E with |v| < 2^E, read off the IEEE exponent field
+__device__ __forceinline__ int exp_bound(float v) {
+    const uint32_t bits = __float_as_uint(v) & 0x7fffffffu;
+    if (bits == 0) return kExpZero;
+    const int f = (int)(bits >> 23);
+    return f == 255 ? kExpBad : (f == 0 ? -126 : f - 126);
+}
+__device__ __forceinline__ int exp_bound(double v) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    if (bits == 0) return kExpZero;
+    const int f = (int)(bits >> 52);
+    return f == 2047 ? kExpBad : (f == 0 ? -1022 : f - 1022);
 }
 
-// Every block-local dof u sums its run zs[incoff[u], incoff[u+1]) in order and hands the total
-// to out(u, v).  A thread takes four dofs (u, u + T, u + 2T, u + 3T) so that their shared-memory
-// chains overlap; interior dofs are sorted by copy count, so the lanes of a warp run alike.
-template <typename V, typename Add, typename Out>
-__device__ __forceinline__ void dof_run_sums(int nu, const uint16_t* incoff, const V* zs, V zero, Add add, Out out) {
-    constexpr int U = 4;
-    const int T = blockDim.x;
-    for (int u = threadIdx.x; u < nu; u += U * T) {
-        int s0[U], cnt[U];
-        V acc[U];
-        int mx = 0;
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int uu = u + k * T;
-            s0[k] = uu < nu ? incoff[uu] : 0;
-            cnt[k] = uu < nu ? incoff[uu + 1] - s0[k] : 0;
-            acc[k] = zero;
-            mx = max(mx, cnt[k]);
-        }
-        for (int j = 0; j < mx; ++j) {
-#pragma unroll
-            for (int k = 0; k < U; ++k)
-                if (j < cnt[k]) acc[k] = add(acc[k], zs[s0[k] + j]);
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int uu = u + k * T;
-            if (uu < nu) out(uu, acc[k]);
-        }
+// Scale exponent k of a block from its exponent bounds; bad = the products are not finite (or
+// beyond what the accumulators can hold), and the block then stores NaN.
+template <typename T>
+__device__ __forceinline__ int fx_scale(int ex, int ec, int er, int top, bool& bad) {
+    constexpr int kmin = sizeof(T) == 4 ? -126 : -1022, kmax = sizeof(T) == 4 ? 126 : 1022;
+    bad = ex >= kExpBad || ec >= kExpBad;
+    if (ex <= kExpZero || ec <= kExpZero) return 0;   // every product is zero
+    const int k = top - (ex + ec + er);
+    if (k < kmin) bad = true;
+    return max(kmin, min(kmax, k));
+}
+
+// 2^k as T, k within the normal range of T
+template <typename T> __device__ __forceinline__ T pow2(int k);
+template <> __device__ __forceinline__ float pow2<float>(int k) { return __int_as_float((k + 127) << 23); }
+template <> __device__ __forceinline__ double pow2<double>(int k) {
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__device__ __forceinline__ long long fx_round(float v) { return __float2ll_rn(v); }
+__device__ __forceinline__ long long fx_round(double v) { return __double2ll_rn(v); }
+// acc = [low word | high word] of one dof (lo_bits > 0), or one 64-bit word (lo_bits = 0: the
+// FP64 applies, whose extra bits of resolution the FP64 tolerance needs)
+__device__ __forceinline__ void fx_add(long long* acc, long long q, int lo_bits) {
+    if (lo_bits == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)q);
+        return;
     }
+    int* w = reinterpret_cast<int*>(acc);
+    atomicAdd(w, (int)(q & ((1ll << lo_bits) - 1)));
+    atomicAdd(w + 1, (int)(q >> lo_bits));
+}
+__device__ __forceinline__ long long fx_total(long long acc, int lo_bits) {
+    if (lo_bits == 0) return acc;
+    const int* w = reinterpret_cast<const int*>(&acc);
+    return ((long long)w[1] << lo_bits) + (long long)w[0];
+}
+// accumulator -> value: one rounding of the exact integer sum, then the exact power-of-two scale
+template <typename T>
+__device__ __forceinline__ T fx_value(long long acc, int lo_bits, int k);
+template <> __device__ __forceinline__ float fx_value<float>(long long acc, int lo_bits, int k) {
+    return __ll2float_rn(fx_total(acc, lo_bits)) * pow2<float>(-k);
+}
+template <> __device__ __forceinline__ double fx_value<double>(long long acc, int lo_bits, int k) {
+    return __ll2double_rn(fx_total(acc, lo_bits)) * pow2<double>(-k);
 }
 
 // Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
-// their partial slot.  MR: V = 16-byte chunk of rc right-hand sides starting at r0, partials
-// slot-major; else V = T, partials [nrhs][npart] from p0.
-template <typename T, int OP, bool MR, typename V>
-__device__ __forceinline__ void store_dof(int u, V v, int nint, const int32_t* ids, const uint16_t* dmul,
-                                          T* __restrict__ y, T* __restrict__ part, int nrhs, int r0, int rc, bool vec,
-                                          int64_t p0) {
-    if constexpr (MR) {
-        if (u < nint) {
-            if (OP == OP_BRAS) {
-#pragma unroll
-                for (int j = 0; j < Chunk<T>::CW; ++j) vget(v, j) = div_by_count(vget(v, j), dmul[u]);
-            }
-            st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, v);
-        } else {
-            st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, v);
-        }
-    } else {
-        if (u < nint) y[(size_t)ids[u] * nrhs + r0] = (OP == OP_BRAS) ? div_by_count(v, dmul[u]) : v;
-        else part[p0 + (u - nint)] = v;
-    }
+// their partial slot ([nrhs][npart] from p0; MR: slot-major rows, right-hand side r).
+template <typename T, int OP, bool MR>
+__device__ __forceinline__ void store_dof(int u, T v, int nint, const int32_t* ids, const uint16_t* dmul,
+                                          T* __restrict__ y, T* __restrict__ part, int nrhs, int r, int64_t p0) {
+    if (u < nint) y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(v, dmul[u]) : v;
+    else if (MR) part[(size_t)(p0 + (u - nint)) * nrhs + r] = v;
+    else part[p0 + (u - nint)] = v;
 }
 
 // Stage 4: one thread per (shared dof, rhs); every dof adds its partials in ascending block
@@ -402,21 +414,22 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     constexpr bool SIGNED = KIND == KIND_PACKED;
     constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36 && OP != OP_DIAG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // 2 mbarriers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // [0, 1] mbarriers
+    int* fx = reinterpret_cast<int*>(smem_raw + 64);                    // [0, 1] ex per chunk parity, [2] ec
     unsigned char* tab = smem_raw + 128;                                 // table packet
-    T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW]
-    T* zs = xs + ((A.max_u * CW + 3) & ~3);                               // [slot][CW]
-    T* Ms = zs + ((NLOC * A.max_ne * CW + 3) & ~3);                       // [NLOC][NPAD] (H1), 16-B aligned
-    int* wsum = reinterpret_cast<int*>(Ms + (KIND == KIND_H1 ? NLOC * NPAD : 0));   // [32] scan scratch
+    T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW] staged x
+    long long* ys = reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3));   // [u][CW] accumulators
+    T* xt = reinterpret_cast<T*>(ys + (((size_t)A.max_u * CW + 1) & ~(size_t)1));  // [NLOC][ne] (XS)
+    T* Ms = xt + (XS ? ((NLOC * A.max_ne + 3) & ~3) : 0);                 // [NLOC][NPAD] (H1), 16-B aligned
 
     const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
-    // this thread's cell factor (H1, one cell per thread), fetched now so that its latency
-    // hides behind the copies
-    const T cfac = (!MR && KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
+    // this thread's cell factor (H1, one cell per thread; multi-RHS items read theirs again),
+    // fetched now so that its latency hides behind the copies
+    const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -426,6 +439,8 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         bulk_copy_g2s(tab, src, sa, &bars[0]);
         mbar_expect_tx(&bars[1], sb);
         bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
+        fx[0] = fx[1] = kExpZero;
+        fx[2] = KIND == KIND_H1 ? kExpZero : 0;
     }
     if (KIND == KIND_H1) {
         const T* ref = static_cast<const T*>(A.refmat);
@@ -435,13 +450,11 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             Ms[i] = v;
         }
     }
-    __syncthreads();   // barriers initialised before anyone polls them
+    __syncthreads();   // barriers and bounds initialised before anyone uses them
+    if (KIND == KIND_H1 && tid < ne) atomicMax(&fx[2], exp_bound(cfac));
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
-    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
-    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
     const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
@@ -451,7 +464,11 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         const bool vec = MR && vec_ok && rc == CW;
         // first partial slot of this block (MR: row of [npart][nrhs])
         const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
+        int* fxe = &fx[ch & 1];
+        if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
+        for (int i = tid; i < nu * CW; i += blockDim.x) ys[i] = 0;
 
+        int emax = OP == OP_DIAG ? 1 : kExpZero;   // DIAG: the products are matrix entries (x = 1)
         if (OP != OP_DIAG && okA) {
             if constexpr (MR) {
                 // one 16-byte row segment per dof, four in flight per thread
@@ -466,9 +483,10 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     for (int k = 0; k < 4; ++k) {
                         const int uu = u + k * blockDim.x;
                         if (uu < nu) {
-                            if (OP == OP_BRAS) {
 #pragma unroll
-                                for (int j = 0; j < CW; ++j) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                            for (int j = 0; j < CW; ++j) {
+                                if (OP == OP_BRAS) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                                emax = max(emax, exp_bound(vget(v[k], j)));
                             }
                             reinterpret_cast<V*>(xs)[uu] = v[k];
                         }
@@ -486,11 +504,16 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int uu = u + k * blockDim.x;
-                        if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                        if (uu < nu) {
+                            const T w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                            emax = max(emax, exp_bound(w));
+                            xs[uu] = w;
+                        }
                     }
                 }
             }
         }
+        if (emax > kExpZero) atomicMax(fxe, emax);
         if (ch == 0) {
             if (!cta_wait(&bars[1], 0, A.status, okA)) {   // block-uniform decision
                 // let any copy still in flight land before the block's shared memory is released
@@ -503,16 +526,18 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         } else {
             __syncthreads();
         }
+        // the block's fixed-point scale (the bounds and the zeroed accumulators are complete)
+        bool bad;
+        const int kx = fx_scale<T>(*fxe, fx[2], A.fx_er, A.fx_top, bad);
+        const T sc = pow2<T>(kx);
 
         // Work items: (cell e, rhs rr) -> item e * CW + rr.  One item per thread without MR.
         const int nitem = ne * CW;
         if constexpr (XS && !MR) {
             // Large streamed cell matrices (n_loc >= 36): the signed local vector waits in shared
             // memory, column e of a [a][cell] array (only this thread touches it), so that
-            // registers hold just the accumulators and the matrix loads in flight; the results go
-            // out after a barrier, over the same array.
+            // registers hold just the accumulators and the matrix loads in flight.
             const int e = tid;
-            T* xt = zs;
             uint64_t neg = 0;
             T zl[NLOC];
 #pragma unroll
@@ -531,14 +556,12 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     zl[a] = fma(m, xt[q * ne + e], zl[a]);
                     if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
                 });
-            }
-            __syncthreads();
-            if (e < ne) {
 #pragma unroll
                 for (int a = 0; a < NLOC; ++a) {
                     // signs of the first 64 local dofs kept as bits, the rest re-read from loc
-                    const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (loc[a * ne + e] & 0x8000) != 0;
-                    zs[pos[a * ne + e]] = s ? -zl[a] : zl[a];
+                    const uint16_t c = L[a * ne];
+                    const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0;
+                    fx_add(&ys[c & 0x7fff], fx_round((s ? -zl[a] : zl[a]) * sc), A.fx_lo);
                 }
             }
         } else {
@@ -546,99 +569,92 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 const int e = MR ? it / CW : it;
                 const int rr = MR ? it % CW : 0;
                 const uint16_t* L = loc + e;
-                {
-                    uint64_t neg = 0;
-                    T xl[NPAD];
+                uint64_t neg = 0;
+                T xl[NPAD];
+#pragma unroll
+                for (int a = 0; a < NLOC; ++a) {
+                    const uint16_t c = L[a * ne];
+                    if constexpr (SIGNED) {
+                        const T v = (OP == OP_DIAG) ? T(0) : xs[(c & 0x7fff) * CW + rr];
+                        const bool s = (c & 0x8000) != 0;
+                        if (a < 64) neg |= (uint64_t)s << (a & 63);
+                        xl[a] = s ? -v : v;
+                    } else {
+                        xl[a] = (OP == OP_DIAG) ? T(0) : xs[c * CW + rr];
+                    }
+                }
+#pragma unroll
+                for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
+                // the signed product v of copy (e, a) into its dof's accumulator
+                auto out = [&](int a, T v) {
+                    const uint16_t c = L[a * ne];
+                    const bool s = SIGNED && OP != OP_DIAG && (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0);
+                    fx_add(&ys[(c & 0x7fff) * CW + rr], fx_round((s ? -v : v) * sc), A.fx_lo);
+                };
+                if constexpr (KIND == KIND_H1) {
+                    using VM = typename Vec4<T>::type;
+                    constexpr int W = Vec4<T>::W;
+                    const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
 #pragma unroll
                     for (int a = 0; a < NLOC; ++a) {
-                        const uint16_t c = L[a * ne];
-                        if constexpr (SIGNED) {
-                            const T v = (OP == OP_DIAG) ? T(0) : xs[(c & 0x7fff) * CW + rr];
-                            const bool s = (c & 0x8000) != 0;
-                            if (a < 64) neg |= (uint64_t)s << (a & 63);
-                            xl[a] = s ? -v : v;
+                        T acc = T(0);
+                        if (OP == OP_DIAG) {
+                            acc = Ms[a * NPAD + a];
                         } else {
-                            xl[a] = (OP == OP_DIAG) ? T(0) : xs[c * CW + rr];
-                        }
-                    }
+                            const VM* row = reinterpret_cast<const VM*>(Ms + a * NPAD);
 #pragma unroll
-                    for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
-                    auto out = [&](int a, T v) {
-                        const bool s = SIGNED && OP != OP_DIAG &&
-                                       (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (L[a * ne] & 0x8000) != 0);
-                        zs[pos[a * ne + e] * CW + rr] = s ? -v : v;
-                    };
-                    if constexpr (KIND == KIND_H1) {
-                        using VM = typename Vec4<T>::type;
-                        constexpr int W = Vec4<T>::W;
-                        const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
-#pragma unroll
-                        for (int a = 0; a < NLOC; ++a) {
-                            T acc = T(0);
-                            if (OP == OP_DIAG) {
-                                acc = Ms[a * NPAD + a];
-                            } else {
-                                const VM* row = reinterpret_cast<const VM*>(Ms + a * NPAD);
-#pragma unroll
-                                for (int q = 0; q < NPAD / W; ++q) {
-                                    const VM m = row[q];
-                                    if constexpr (W == 4) {
-                                        acc = fma(m.x, xl[4 * q + 0], acc);
-                                        acc = fma(m.y, xl[4 * q + 1], acc);
-                                        acc = fma(m.z, xl[4 * q + 2], acc);
-                                        acc = fma(m.w, xl[4 * q + 3], acc);
-                                    } else {
-                                        acc = fma(m.x, xl[2 * q + 0], acc);
-                                        acc = fma(m.y, xl[2 * q + 1], acc);
-                                    }
+                            for (int q = 0; q < NPAD / W; ++q) {
+                                const VM m = row[q];
+                                if constexpr (W == 4) {
+                                    acc = fma(m.x, xl[4 * q + 0], acc);
+                                    acc = fma(m.y, xl[4 * q + 1], acc);
+                                    acc = fma(m.z, xl[4 * q + 2], acc);
+                                    acc = fma(m.w, xl[4 * q + 3], acc);
+                                } else {
+                                    acc = fma(m.x, xl[2 * q + 0], acc);
+                                    acc = fma(m.y, xl[2 * q + 1], acc);
                                 }
                             }
-                            out(a, acc * c);
                         }
-                    } else {
-                        T zl[NLOC];
-#pragma unroll
-                        for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-                        for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
-                            if (OP == OP_DIAG) {
-                                if (q == a) zl[a] = m;
-                            } else {
-                                zl[a] = fma(m, xl[q], zl[a]);
-                                if (q < a) zl[q] = fma(m, xl[a], zl[q]);
-                            }
-                        });
-#pragma unroll
-                        for (int a = 0; a < NLOC; ++a) out(a, zl[a]);
+                        out(a, acc * c);
                     }
+                } else {
+                    T zl[NLOC];
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
+                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                        if (OP == OP_DIAG) {
+                            if (q == a) zl[a] = m;
+                        } else {
+                            zl[a] = fma(m, xl[q], zl[a]);
+                            if (q < a) zl[q] = fma(m, xl[a], zl[q]);
+                        }
+                    });
+#pragma unroll
+                    for (int a = 0; a < NLOC; ++a) out(a, zl[a]);
                 }
             }
         }
         __syncthreads();
 
-        // the start of every dof's run (over the staged x, dead by now), then the per-dof sums
-        uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
-        run_starts((int)m, ends, incoff, wsum);
-        __syncthreads();
-        if constexpr (MR) {
-            dof_run_sums<V>(nu, incoff, reinterpret_cast<const V*>(zs), vzero(V{}),
-                            [](V a, const V& c) { return vsum(a, c); },
-                            [&](int u, V v) { store_dof<T, OP, true, V>(u, v, nint, ids, dmul, y, part, nrhs, r0, rc, vec, p0); });
-            __syncthreads();   // incoff (over xs) read before the next chunk stages x
-        } else {
-            dof_run_sums<T>(nu, incoff, zs, T(0), [](T a, T c) { return a + c; },
-                            [&](int u, T v) { store_dof<T, OP, false, T>(u, v, nint, ids, dmul, y, part, nrhs, r0, 1, false, p0); });
+        // totals: interior dofs to y, shared ones to their partial slots
+        for (int i = tid; i < nu * rc; i += blockDim.x) {
+            const int u = i / rc, rr = i - u * rc;
+            const T v = bad ? T(NAN) : fx_value<T>(ys[u * CW + rr], A.fx_lo, kx);
+            store_dof<T, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
         }
+        if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
     }
 }
 
 template <int NLOC, typename T, int KIND>
 size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
-    const int cw = mr ? Chunk<T>::CW : 1;
-    return 128 + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(T) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) +
-                        (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0)) +
-           128;
+    constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36;
+    const size_t cw = mr ? Chunk<T>::CW : 1;
+    return 128 + ((A.max_pkt + 127u) & ~127u) + sizeof(T) * (((size_t)A.max_u * cw + 3) & ~(size_t)3) +
+           8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1) +
+           sizeof(T) * ((XS ? (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) : 0) + (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
 }
 
 // Largest dynamic shared memory one CTA may opt into on the current device.

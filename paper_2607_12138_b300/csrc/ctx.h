@@ -18,8 +18,7 @@ struct PcgWork;
 // blk_u0[b+1] - blk_u0[b] block-local dofs: first the dofs all of whose broken copies lie
 // inside the block ("interior", blk_nint[b] of them, ascending global id), then the others
 // ("shared"), grouped.  Its table packet (byte offset blk_pkt[b], layout in packet.h) holds
-// the dof ids, multiplicities, local indices with signs, dof-sorted positions and the end
-// bits of the dof runs.
+// the dof ids, multiplicities and local indices with signs.
 // A group is the set of shared dofs whose copies lie in one and the same set of blocks
 // (grp_cnt[g] blocks, grp_size[g] dofs); every member block lists the group's dofs
 // contiguously, by ascending global id.  Shared dof u of block b leaves its partial sum in
@@ -40,7 +39,8 @@ struct HostTables {
     std::vector<unsigned char> pkt;
     std::vector<double> dinv;
     int64_t npart = 0, U_tot = 0, nsh = 0;
-    int max_bg = 0;   // most groups of one block
+    int max_bg = 0;       // most groups of one block
+    int max_copies = 1;   // most copies of one dof inside one block
 };
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
@@ -54,6 +54,9 @@ struct bras_ctx {
     int64_t E = 0, n = 0, nvert = 0;
     int BE = 256, nblk = 0, max_u = 0, max_ne = 0;
     int precisions = 0, max_nrhs = 1;
+    // fixed-point dof sums: product bound placed at 2^fx_top; exponent bounds of the local
+    // operators' row abs-sums (mass, BRAS)
+    int fx_top = 50, fx_lo = 24, fx_top64 = 56, er_mass = 0, er_bras = 0;
     int64_t U_tot = 0, npart = 0, nsh = 0;
     int64_t Epad = 0;   // padded cell count of the packed (SoA) per-cell matrices
     int npk = 0;        // nloc (nloc + 1) / 2

@@ -2,8 +2,8 @@
 // b - M x of the FP64 refinement loop around the FP32 inner solve.
 //
 // Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async copies,
-// x staged in shared memory, fixed-order in-block dof sums, partials of boundary dofs added up
-// by the combine pass.
+// x staged in shared memory, exact fixed-point in-block dof sums, partials of boundary dofs
+// added up by the combine pass.
 // All arithmetic runs on the FP32 units as float-float pairs (about 2^-48 relative, the
 // accuracy of FP64 sums) -- B300 issues FP64, and conversions to and from it, at 1/64 of the
 // FP32 rate:
@@ -12,8 +12,8 @@
 //     [8g, 8g + 8) of z_K = c_K M_ref x_K (Eq. piola_mass_pullbacks); each row is one
 //     compensated chain (leading product exact by an FMA, cross terms into the low part,
 //     running sum by a two-sum), and c_K multiplies it as a float pair;
-//   * the staged copies are float pairs, summed per dof by two-sums in a fixed order, and
-//     converted to FP64 once per dof.
+//   * both halves of each product pair go into the dof's exact 64-bit fixed-point accumulator
+//     (apply_kernels.cuh), converted to FP64 once per dof.
 // Eight independent rows per thread and ~60 registers keep many warps in flight; lanes of a
 // warp hold different cells of the same row group, so the rows of M_ref are broadcast reads.
 #pragma once
@@ -39,10 +39,10 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     unsigned char* tab = smem_raw + 128;
+    int* fx = reinterpret_cast<int*>(smem_raw + 64);                                 // [0] ex, [1] ec
     float2* xs = reinterpret_cast<float2*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u] (hi, lo)
-    float2* zs = xs + ((A.max_u + 3) & ~3);                                          // [slot] (hi, lo)
-    float2* Ms = zs + ((NLOC * A.max_ne + 3) & ~3);                                  // [NLOC][NLOC] (hi, lo)
-    int* wsum = reinterpret_cast<int*>(Ms + NLOC * NLOC);                             // [32] scan scratch
+    long long* ys = reinterpret_cast<long long*>(xs + ((A.max_u + 1) & ~1));       // [u] accumulators
+    float2* Ms = reinterpret_cast<float2*>(ys + ((A.max_u + 1) & ~1));              // [NLOC][NLOC] (hi, lo)
 
     const int b = blockIdx.x / nrhs, r = blockIdx.x % nrhs, tid = threadIdx.x;
     const int cw = blockDim.x / DfShape<NLOC>::TPC;   // cells per row group
@@ -61,21 +61,23 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
         bulk_copy_g2s(tab, src, sa, &bars[0]);
         mbar_expect_tx(&bars[1], sb);
         bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
+        fx[0] = fx[1] = kExpZero;
     }
+    for (int i = tid; i < nu; i += blockDim.x) ys[i] = 0;
     const double* ref = static_cast<const double*>(A.refmat);
     for (int i = tid; i < NLOC * NLOC; i += blockDim.x) {
         const double v = ref[i];
         const float hi = (float)v;
         Ms[i] = make_float2(hi, (float)(v - (double)hi));
     }
-    __syncthreads();   // barriers initialised before anyone polls them
+    __syncthreads();   // barriers and bounds initialised before anyone uses them
+    for (int e = tid; e < ne; e += blockDim.x)
+        atomicMax(&fx[1], exp_bound(static_cast<const double*>(A.scale)[e0 + e]));
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
-    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
-    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
+    int emax = kExpZero;
     if (okA) {
         for (int u = tid; u < nu; u += 8 * blockDim.x) {
             double v[8];
@@ -90,10 +92,12 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
                 if (uu < nu) {
                     const float hi = (float)v[k];
                     xs[uu] = make_float2(hi, (float)(v[k] - (double)hi));
+                    emax = max(emax, exp_bound(v[k]));
                 }
             }
         }
     }
+    if (emax > kExpZero) atomicMax(&fx[0], emax);
     if (!cta_wait(&bars[1], 0, A.status, okA)) {
         if (tid == 0) {
             mbar_wait_bounded(&bars[0], A.status);
@@ -102,6 +106,10 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
         return;
     }
 
+    // the block's fixed-point scale (2^k as a float: the products arrive as float pairs)
+    bool bad;
+    const int kx = fx_scale<float>(fx[0], fx[1], A.fx_er, A.fx_top, bad);
+    const float sc = pow2<float>(kx);
     for (int e = tid % cw; e < ne; e += cw) {
         const double c = static_cast<const double*>(A.scale)[e0 + e];
         const float ch = (float)c, cl = (float)(c - (double)ch);
@@ -127,35 +135,25 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
             if (a < NLOC) {
                 float zh = 0.f, zl = 0.f;   // (sh + sl) (ch + cl)
                 df_term(ch, cl, sh[j], sl[j], zh, zl);
-                zs[pos[a * ne + e]] = make_float2(zh, zl);
+                // both halves of the pair into the dof's fixed-point accumulator
+                fx_add(&ys[loc[a * ne + e]], fx_round(zh * sc) + fx_round(zl * sc), A.fx_lo);
             }
         }
     }
     __syncthreads();
 
-    // per-dof sums of the float pairs (two-sums, fixed order), converted to FP64 once per dof;
-    // the runs' starts go over the staged x, dead by now
-    uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
-    run_starts((int)m, ends, incoff, wsum);
-    __syncthreads();
-    dof_run_sums<float2>(nu, incoff, zs, make_float2(0.f, 0.f),
-                         [](float2 a, const float2& c) {
-                             df_merge(a.x, a.y, c.x, c.y);
-                             return a;
-                         },
-                         [&](int u, float2 z) {
-                             const double acc = (double)z.x + (double)z.y;
-                             if (u < nint) y[(size_t)ids[u] * nrhs + r] = acc;
-                             else part[p0 + (u - nint)] = acc;
-                         });
+    // totals in FP64: interior dofs to y, shared ones to their partial slots
+    for (int u = tid; u < nu; u += blockDim.x) {
+        const double v = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_value<double>(ys[u], A.fx_lo, kx);
+        if (u < nint) y[(size_t)ids[u] * nrhs + r] = v;
+        else part[p0 + (u - nint)] = v;
+    }
 }
 
 template <int NLOC>
 size_t df_smem_bytes(const BlockArgs& A, int threads) {
-    return 128 + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(float2) * ((((size_t)A.max_u + 3) & ~(size_t)3) + (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) +
-                             (size_t)NLOC * NLOC) +
-           128;
+    return 128 + ((A.max_pkt + 127u) & ~127u) + 2 * 8 * (((size_t)A.max_u + 1) & ~(size_t)1) +
+           sizeof(float2) * (size_t)NLOC * NLOC;
 }
 
 template <int NLOC>

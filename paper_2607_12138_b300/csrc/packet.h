@@ -1,14 +1,11 @@
 // Byte layout of one cell block's table packet (host and device share it).
 //   part A: ids int32[nu] | d uint16[nu]
-//   part B: loc uint16[m] | pos uint16[m] | ends uint32[ceil(m / 32)]      (m = ne * nloc)
+//   part B: loc uint16[m]                                                (m = ne * nloc)
 // Every section starts on a 16-byte boundary so that each part is one bulk copy.
-//   ids[u]   global dof of block-local dof u (interior dofs first, by copy count, then the
+//   ids[u]   global dof of block-local dof u (interior dofs first, by ascending id, then the
 //            shared ones grouped by their set of blocks)
 //   d[u]     its multiplicity (D = P^T P)
 //   loc[s]   block-local dof of copy s = a * ne + e (cell e, local index a); bit 15 = sign -1
-//   pos[s]   position of copy s in the dof-sorted order (dof u's copies are one contiguous run,
-//            by ascending s: the fixed summation order)
-//   ends     bit j set iff position j of the dof-sorted order is the last copy of its dof
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
@@ -23,10 +20,7 @@ namespace bras {
 BRAS_HD inline uint32_t pad16(uint32_t b) { return (b + 15u) & ~15u; }
 BRAS_HD inline uint32_t pkt_off_d(uint32_t nu) { return pad16(4u * nu); }
 BRAS_HD inline uint32_t pkt_size_a(uint32_t nu) { return pkt_off_d(nu) + pad16(2u * nu); }
-BRAS_HD inline uint32_t pkt_off_pos(uint32_t m) { return pad16(2u * m); }
-BRAS_HD inline uint32_t pkt_off_ends(uint32_t m) { return 2u * pad16(2u * m); }
-BRAS_HD inline uint32_t pkt_ends_words(uint32_t m) { return (m + 31u) / 32u; }
-BRAS_HD inline uint32_t pkt_size_b(uint32_t m) { return pkt_off_ends(m) + pad16(4u * pkt_ends_words(m)); }
+BRAS_HD inline uint32_t pkt_size_b(uint32_t m) { return pad16(2u * m); }
 
 // Per-cell packed symmetric matrices (lower triangle by rows, entry idx = a (a + 1) / 2 + q)
 // are stored vector-interleaved: groups of G consecutive entries of one cell are contiguous

@@ -226,4 +226,34 @@ cudaError_t run_element_inverse(int n, int64_t E, int64_t Epad, const double* Rr
     return cudaGetLastError();
 }
 
+// Exponent bound of the largest row abs-sum of every packed symmetric cell matrix: one thread
+// per cell; *out = max over cells of E with sum_q |A_aq| < 2^E (atomicMax, *out preset).
+__global__ void k_row_bound(int n, int64_t E, int64_t Epad, const double* __restrict__ pk, int* out) {
+    int emax = -100000;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        double best = 0.0;
+        for (int a = 0; a < n; ++a) {
+            double sum = 0.0;
+            for (int q = 0; q < n; ++q) {
+                const int i = a >= q ? a * (a + 1) / 2 + q : q * (q + 1) / 2 + a;
+                sum += fabs(pk[pk_index(i, e, Epad, 2)]);
+            }
+            best = fmax(best, sum);
+        }
+        if (best > 0.0) {
+            int ex;
+            frexp(best, &ex);   // best < 2^ex
+            emax = max(emax, ex);
+        }
+    }
+    atomicMax(out, emax);
+}
+
+cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const double* pk, int* out, cudaStream_t st) {
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((E + 255) / 256, 148 * 8));
+    k_row_bound<<<nb, 256, 0, st>>>(n, E, Epad, pk, out);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 }  // namespace bras

@@ -88,7 +88,7 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         std::vector<int32_t> uq, first;                   // distinct dofs, start of each run in srt
         std::vector<int32_t> order;                       // block-local order: indices into uq
         std::vector<int32_t> ids, gid_of;                 // final ids; group of each shared dof
-        int nint = 0;
+        int nint = 0, max_cnt = 0;
     };
     if ((int64_t)std::min<int64_t>(BE, E) * nloc > 65535) { *detail = (int64_t)BE * nloc; return BRAS_ERR_TOO_LARGE; }
     std::vector<Blk> blk(nblk);
@@ -167,10 +167,6 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         for (int i = 0; i < nu; ++i)
             if (B.first[i + 1] - B.first[i] == d[B.uq[i]]) B.order.push_back(i);
         B.nint = (int)B.order.size();
-        // interior dofs by (copy count, id): the lanes of a warp then sum runs of one length
-        std::stable_sort(B.order.begin(), B.order.end(), [&](int32_t i, int32_t j) {
-            return B.first[i + 1] - B.first[i] < B.first[j + 1] - B.first[j];
-        });
         std::vector<int32_t> sh;
         for (int i = 0; i < nu; ++i)
             if (B.first[i + 1] - B.first[i] != d[B.uq[i]]) sh.push_back(i);
@@ -185,12 +181,15 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
             B.ids[u] = B.uq[B.order[u]];
             if (u >= B.nint) B.gid_of[u - B.nint] = gid[B.ids[u]];
         }
+        for (int i = 0; i < nu; ++i) B.max_cnt = std::max(B.max_cnt, B.first[i + 1] - B.first[i]);
         max_u = std::max(max_u, nu);
         max_ne = std::max(max_ne, ne);
     }
     t->max_u = max_u;
     t->max_ne = max_ne;
-    // packets: part A = ids | d, part B = loc | pos | ends, 16-byte aligned sections
+    t->max_copies = 1;
+    for (int b = 0; b < nblk; ++b) t->max_copies = std::max(t->max_copies, blk[b].max_cnt);
+    // packets: part A = ids | d, part B = loc, 16-byte aligned sections
     t->blk_u0.resize(nblk + 1);
     t->blk_nint.resize(nblk);
     t->blk_p0.resize(nblk);
@@ -270,12 +269,7 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         std::memcpy(p, B.ids.data(), 4 * (size_t)nu);
         uint16_t* dm = reinterpret_cast<uint16_t*>(p + pkt_off_d(nu));
         for (uint32_t u = 0; u < nu; ++u) dm[u] = (uint16_t)std::min<int32_t>(d[B.ids[u]], 65535);
-        unsigned char* pb = p + pkt_size_a(nu);
-        uint16_t* loc = reinterpret_cast<uint16_t*>(pb);
-        uint16_t* pos = reinterpret_cast<uint16_t*>(pb + pkt_off_pos(m));
-        uint32_t* ends = reinterpret_cast<uint32_t*>(pb + pkt_off_ends(m));
-        // dof-sorted order: the dofs in block-local order u, each dof's copies by ascending slot
-        uint32_t off = 0;
+        uint16_t* loc = reinterpret_cast<uint16_t*>(p + pkt_size_a(nu));
         for (uint32_t u = 0; u < nu; ++u) {
             const int i = B.order[u];
             for (int s = B.first[i]; s < B.first[i + 1]; ++s) {
@@ -283,10 +277,9 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
                 const int64_t K = t->perm[e0 + e];
                 const bool neg = signs && signs[K * nloc + a] < 0;
                 loc[slot] = (uint16_t)(u | (neg ? 0x8000u : 0u));
-                pos[slot] = (uint16_t)off++;
             }
-            ends[(off - 1) >> 5] |= 1u << ((off - 1) & 31);
         }
+        (void)m;
     }
     return BRAS_OK;
 }

@@ -1,8 +1,8 @@
 // H1 block kernel with the local multiply on the 5th-generation tensor cores (tcgen05).
 //
 // Same block structure as k_block (apply_kernels.cuh): table packet staged by bulk async
-// copies, x staged in shared memory, fixed-order in-block dof sums, partials of boundary dofs
-// added up by the combine pass.  The difference is stage 2: for an affine H1 cell the local operator is
+// copies, x staged in shared memory, exact fixed-point in-block dof sums, partials of boundary
+// dofs added up by the combine pass.  The difference is stage 2: for an affine H1 cell the local operator is
 // c_K * A_ref with one reference matrix shared by all cells (A_ref = M_ref or M_ref^{-1},
 // Eq. piola_mass_pullbacks), so a block's local products form one GEMM
 //      Z[cells x n] = Xt[cells x k] * A_ref^T,
@@ -135,18 +135,17 @@ struct TcArgs {
 // thread per cell, blockDim / 128 tiles.  TPC = 2 (blocks of at most 128 cells): one tile, two
 // threads per cell, warps 0-3 taking the even and warps 4-7 the odd 8-column groups of the
 // tensor-memory rows, so that a CTA needs 128 TMEM columns and more CTAs share an SM.
-// ALIAS (one right-hand side): the dof-sorted products overwrite the block's loc/pos tables
-// (both dead by then) instead of a buffer of their own; chosen when it is what lets two CTAs
-// share an SM, or with TPC = 2.
 // MR = true (TPC = 1): one CTA per cell block walks the right-hand sides in chunks of 4; the
 // block's ne * 4 items (cell, rhs) fill the tensor-memory lanes in passes of blockDim items
 // (two 128-lane tiles), each pass one GEMM (the E*R rows of the local product on the M side).
-template <int NLOC, int OP, bool MR = false, int TPC = 1, bool ALIAS = false>
-__global__ void __launch_bounds__(256, TPC == 2 ? 3 : 1)
+// Stage 3 adds every product to its dof's 64-bit fixed-point accumulator (apply_kernels.cuh);
+// with one right-hand side the accumulators take the staged vector's bytes over (dead once the
+// local vectors are in tensor memory) and are cleared while the GEMM runs.
+template <int NLOC, int OP, bool MR = false, int TPC = 1>
+__global__ void __launch_bounds__(256, TPC == 2 ? 4 : (MR ? 1 : 2))
 k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs,
            int vec_ok) {
     static_assert(TPC == 1 || (TPC == 2 && !MR), "two threads per cell only for one right-hand side a CTA");
-    static_assert(!(ALIAS && MR), "multi-RHS passes keep reading pos");
     using Sh = TcShape<NLOC>;
     constexpr int K = Sh::K, N = Sh::N;
     constexpr int CW = MR ? Chunk<float>::CW : 1;
@@ -157,13 +156,12 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);   // [0] tab A, [1] tab B, [2] B tile, [3] MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + 64);
-    unsigned char* btile = smem_raw + 128;                           // 2 * B_BYTES, 128-B aligned
+    int* fx = reinterpret_cast<int*>(smem_raw + 80);             // [0, 1] ex per chunk parity, [2] ec
+    unsigned char* btile = smem_raw + 128;                       // 2 * B_BYTES, 128-B aligned
     unsigned char* tab = btile + tc_btile_region<NLOC>();
-    float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u][CW]
-    // stage 3's scan scratch (32 ints): over the B tiles (dead once the last GEMM has completed)
-    // for one right-hand side, after the products for the multi-RHS passes
-    int* wsum = MR ? reinterpret_cast<int*>(xs + ((A.max_u * CW + 3) & ~3) + (((size_t)NLOC * A.max_ne * CW + 3) & ~(size_t)3))
-                   : reinterpret_cast<int*>(btile);
+    float* xs = reinterpret_cast<float*>(tab + ((A.max_pkt + 127u) & ~127u));   // [u][CW] staged x
+    // [u][CW] accumulators: over the staged vector (one right-hand side), after it (MR)
+    long long* ys = MR ? reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3)) : reinterpret_cast<long long*>(xs);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int lt = TPC == 2 ? (tid & 127) : tid;              // this thread's lane in the pass
@@ -174,10 +172,8 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
     const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
-    // [slot][CW]: after the staged vector, or over the block's loc/pos tables
-    float* zs = !ALIAS ? xs + ((A.max_u * CW + 3) & ~3) : reinterpret_cast<float*>(tab + sa);
     // this thread's cell factor, fetched now so that its latency hides behind the copies
-    const float cfac = (!MR && lt < ne) ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;
+    const float cfac = lt < ne ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -188,20 +184,19 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
         mbar_expect_tx(&bars[2], 2 * Sh::B_BYTES);
         bulk_copy_g2s(btile, TA.btile, 2 * Sh::B_BYTES, &bars[2]);
+        fx[0] = fx[1] = fx[2] = kExpZero;
     }
     if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (lt < ne && (TPC == 1 || half == 0)) atomicMax(&fx[2], exp_bound(cfac));
     const uint32_t tmem = *tmem_slot;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t tile_col = TPC == 2 ? 0u : (uint32_t)(warp >> 2) * Sh::TILE_COLS;
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
-    const uint32_t m = (uint32_t)(ne * NLOC);
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
-    const uint32_t* ends = reinterpret_cast<const uint32_t*>(tab + sa + pkt_off_ends(m));
 
     bool ok = cta_wait(&bars[0], 0, A.status, true);
     bool tmem_live = true;   // block-uniform
@@ -213,6 +208,11 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         const int rc = MR ? min(CW, nrhs - r0) : 1;
         const bool vec = MR && vec_ok && rc == CW;
         const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
+        int* fxe = &fx[ch & 1];
+        if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
+        if constexpr (MR)
+            for (int i = tid; i < nu * CW; i += blockDim.x) ys[i] = 0;
+        int emax = kExpZero;
         if constexpr (MR) {
             using V = Chunk<float>::V;
             for (int u = tid; u < nu; u += 4 * blockDim.x) {
@@ -226,9 +226,10 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                 for (int k = 0; k < 4; ++k) {
                     const int uu = u + k * blockDim.x;
                     if (uu < nu) {
-                        if (OP == OP_BRAS) {
 #pragma unroll
-                            for (int j = 0; j < CW; ++j) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                        for (int j = 0; j < CW; ++j) {
+                            if (OP == OP_BRAS) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
+                            emax = max(emax, exp_bound(vget(v[k], j)));
                         }
                         reinterpret_cast<V*>(xs)[uu] = v[k];
                     }
@@ -246,16 +247,25 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int uu = u + k * blockDim.x;
-                    if (uu < nu) xs[uu] = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                    if (uu < nu) {
+                        const float w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
+                        emax = max(emax, exp_bound(w));
+                        xs[uu] = w;
+                    }
                 }
             }
         }
+        if (emax > kExpZero) atomicMax(fxe, emax);
         if (ch == 0) {
             ok = cta_wait(&bars[1], 0, A.status, ok);
             if (!ok) break;
         } else {
             __syncthreads();
         }
+        // the block's fixed-point scale
+        bool bad;
+        const int kx = fx_scale<float>(*fxe, fx[2], A.fx_er, A.fx_top, bad);
+        const float sc = pow2<float>(kx);
 
         const int nitem = ne * CW;
         const int npass = (nitem + lanes - 1) / lanes;   // block-uniform (1 without MR)
@@ -296,7 +306,10 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
             __syncthreads();
 
             // stage 2b: one thread issues the 3xTF32 GEMM for the pass's tiles and waits for it;
-            // the rest of the CTA sleeps in the barrier
+            // with one right-hand side the others clear the accumulators (over the staged x,
+            // read by now) meanwhile
+            if constexpr (!MR)
+                for (int i = tid; i < nu; i += blockDim.x) ys[i] = 0;
             bool done = true;
             if (tid == 0) {
                 if (ch == 0 && pass == 0) done = mbar_wait_bounded(&bars[2], A.status);
@@ -331,8 +344,9 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
             tc_fence_after();
             if (!ok) break;
 
-            // stage 2c: read this item's row of Z, scale, stage for the incidence sums
-            const float c = MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac;
+            // stage 2c: read this item's row of Z, scale, and add each product to its dof's
+            // fixed-point accumulator
+            const float cs = (MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac) * sc;
             auto stage2c = [&](auto hc) {
                 constexpr int H = decltype(hc)::value;
                 constexpr int G = N / 16;
@@ -346,37 +360,15 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                 for (int g = 0; g < G; ++g)
                     if (mine(g)) reg_fence(v[g]);
-                if constexpr (!ALIAS) {
-                    if (valid) {
+                if (valid) {
 #pragma unroll
-                        for (int g = 0; g < G; ++g)
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int a = 16 * g + j;
-                                if (a < NLOC) zs[pos[a * ne + e] * CW + rr] = __uint_as_float(v[g][j]) * c;
-                            }
-                    }
-                } else {
-                    // zs overwrites loc/pos: every thread takes its positions first
-                    uint32_t pv[G][16];
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
+                    for (int g = 0; g < G; ++g) {
+                        if (!mine(g)) continue;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int a = 16 * g + j;
-                            if (mine(g) && a < NLOC) pv[g][j] = valid ? pos[a * ne + e] : 0u;
-                        }
-                    // every warp passes exactly one of the two call sites (barrier 1, all threads)
-                    asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x) : "memory");
-                    if (valid) {
-#pragma unroll
-                        for (int g = 0; g < G; ++g) {
-                            if (!mine(g)) continue;
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int a = 16 * g + j;
-                                if (a < NLOC) zs[pv[g][j]] = __uint_as_float(v[g][j]) * c;
-                            }
+                            if (a < NLOC)
+                                fx_add(&ys[loc[a * ne + e] * CW + rr], fx_round(__uint_as_float(v[g][j]) * cs), A.fx_lo);
                         }
                     }
                 }
@@ -384,33 +376,25 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
             if (half == 0) stage2c(std::integral_constant<int, 0>{});
             else stage2c(std::integral_constant<int, 1>{});
             tc_fence_before();
-            __syncthreads();   // zs complete; the next pass may overwrite tensor memory
+            __syncthreads();   // every product added; the next pass may overwrite tensor memory
         }
         if (!ok) break;
-
         if constexpr (!MR) {
-            // every product is in shared memory: release the tensor memory now, so that the next
-            // CTA on this SM can allocate it while this one sums and stores
+            // every product is accumulated: release the tensor memory now, so that the next CTA on
+            // this SM can allocate it while this one stores
             if (warp == 0) {
                 tc_fence_after();
                 tmem_dealloc(tmem, TMEM_COLS);
             }
             tmem_live = false;
         }
-        // the start of every dof's run (over the staged x, dead by now), then the per-dof sums
-        uint16_t* incoff = reinterpret_cast<uint16_t*>(xs);
-        run_starts((int)m, ends, incoff, wsum);
-        __syncthreads();
-        if constexpr (MR) {
-            using V = Chunk<float>::V;
-            dof_run_sums<V>(nu, incoff, reinterpret_cast<const V*>(zs), vzero(V{}),
-                            [](V a, const V& c) { return vsum(a, c); },
-                            [&](int u, V v) { store_dof<float, OP, true, V>(u, v, nint, ids, dmul, y, part, nrhs, r0, rc, vec, p0); });
-            __syncthreads();   // incoff (over xs) read before the next chunk stages x
-        } else {
-            dof_run_sums<float>(nu, incoff, zs, 0.f, [](float a, float c) { return a + c; },
-                                [&](int u, float v) { store_dof<float, OP, false, float>(u, v, nint, ids, dmul, y, part, nrhs, r0, 1, false, p0); });
+        // totals: interior dofs to y, shared ones to their partial slots
+        for (int i = tid; i < nu * rc; i += blockDim.x) {
+            const int u = i / rc, rr = i - u * rc;
+            const float v = bad ? __int_as_float(0x7fc00000) : fx_value<float>(ys[u * CW + rr], A.fx_lo, kx);
+            store_dof<float, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
         }
+        if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
     }
     // a GEMM committed but not seen complete: drain it before the columns are released
     if (pending >= 0 && tid == 0) mbar_wait_parity_bounded(&bars[3], (uint32_t)pending, A.status);
@@ -431,15 +415,14 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     }
 }
 
-// alias: the products reuse the loc/pos bytes of the packet (4 per copy; one right-hand side).
-// One right-hand side: the scan scratch of stage 3 sits over the B tiles.
+// Shared memory of the tensor-core block kernel: B tiles, the packet, the staged x (one
+// right-hand side: also the 8-byte accumulators over it), the multi-RHS accumulators.
 template <int NLOC>
-size_t tc_smem_bytes(const BlockArgs& A, bool mr = false, bool alias = true) {
+size_t tc_smem_bytes(const BlockArgs& A, bool mr = false) {
     const size_t cw = mr ? Chunk<float>::CW : 1;
-    return 128 + (size_t)tc_btile_region<NLOC>() + ((A.max_pkt + 127u) & ~127u) +
-           sizeof(float) * ((((size_t)A.max_u * cw + 3) & ~(size_t)3) +
-                            ((mr || !alias) ? (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3) : 0)) +
-           (mr ? 128 : 0);
+    const size_t xsb = sizeof(float) * (((size_t)A.max_u * cw + 3) & ~(size_t)3);
+    const size_t ysb = 8 * (size_t)A.max_u * cw;
+    return 128 + (size_t)tc_btile_region<NLOC>() + ((A.max_pkt + 127u) & ~127u) + (mr ? xsb + ysb : std::max(xsb, ysb));
 }
 
 template <int NLOC, int OP>
@@ -448,14 +431,8 @@ cudaError_t launch_block_tc(const TcArgs& TA, const CombineArgs& G, int nblk, co
     const bool mr = nrhs > 1 && tc_smem_bytes<NLOC>(TA.A, true) <= (size_t)smem_optin_bytes();
     // blocks of at most 128 cells: one tile, two threads per cell
     const bool two = !mr && TA.A.max_ne <= 128;
-    // the products get a buffer of their own unless sharing the tables' bytes is what fits
-    // two CTAs per SM (measured: the own buffer is faster at equal occupancy)
-    const bool alias = !mr && (two || 2 * (tc_smem_bytes<NLOC>(TA.A, false, false) + 1024) >
-                                           (size_t)smem_per_sm_bytes());
-    const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr, alias);
-    auto kern = mr ? k_block_tc<NLOC, OP, true, 1, false>
-                   : (two ? k_block_tc<NLOC, OP, false, 2, true>
-                          : (alias ? k_block_tc<NLOC, OP, false, 1, true> : k_block_tc<NLOC, OP, false, 1, false>));
+    const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr);
+    auto kern = mr ? k_block_tc<NLOC, OP, true, 1> : (two ? k_block_tc<NLOC, OP, false, 2> : k_block_tc<NLOC, OP, false, 1>);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -4,7 +4,7 @@
 // Input (little endian): int64 E, int32 nloc, int64 n, int32 dim, int32 BE, int64 nvert,
 //   int32 has_signs, int32 has_groups, int32 l2g[E*nloc], [int8 signs[E*nloc]],
 //   double coords[nvert*dim], int32 cells[E*(dim+1)], [int32 groups[E]].
-// Output: int32 rc, int64 detail, and for rc == 0: int32 BE, nblk, max_u, max_ne, max_bg,
+// Output: int32 rc, int64 detail, and for rc == 0: int32 BE, nblk, max_u, max_ne, max_bg, max_copies,
 //   uint32 max_pkt, int64 npart, U_tot, nsh, then the arrays perm, blk_e0, blk_u0, blk_nint,
 //   blk_p0, grp_size, grp_cnt, grp_slot0, grp_slots, blk_g0, bg_gid, bg_u, grp_item0, sh_ids
 //   (int32), sh_d (uint16), blk_pkt (int64), pkt (uint8), dinv (double), each preceded by its
@@ -64,6 +64,7 @@ int main(int argc, char** argv) {
         wr(out, (int32_t)t.max_u);
         wr(out, (int32_t)t.max_ne);
         wr(out, (int32_t)t.max_bg);
+        wr(out, (int32_t)t.max_copies);
         wr(out, (uint32_t)t.max_pkt);
         wr(out, (int64_t)t.npart);
         wr(out, (int64_t)t.U_tot);

@@ -4,13 +4,11 @@
 table; the tests below read the table packets back and
 
 * check their invariants: the cell order is a permutation, each block's copies are listed
-  once, the dof-sorted order keeps the copies of a dof by ascending slot (the fixed
-  summation order) and its end bits close every dof's run, interior dofs have all their
-  copies in the block, a group's dofs are exactly the shared dofs with one block set, listed
+  once, interior dofs have all their copies in the block (and come by ascending id), a group's dofs are exactly the shared dofs with one block set, listed
   contiguously by ascending id in each of its blocks, its partial slots in ascending block
   order, d = the copy counts;
 * replay the block apply from the packets alone -- gather with the sign bits and 1/d, local
-  products, per-dof sums over the runs the end bits delimit, interior stores, partials, and
+  products, per-dof sums through the local indices, interior stores, partials, and
   the group sums of the last block -- with the oracle's element matrices, and compare with
   the oracle's assembled M and M_bras^{-1} (Eq. M_PMbrP, Eq. mhatinvbras_def);
 * check the error codes of a bad map (an l2g entry out of range, a dof with no copy).
@@ -64,11 +62,12 @@ def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
     if rc != 0:
         return rc, detail, None
     o = 12
-    BE_, nblk, max_u, max_ne, max_bg, max_pkt = struct.unpack_from("<iiiiiI", buf, o)
-    o += 24
+    BE_, nblk, max_u, max_ne, max_bg, max_copies, max_pkt = struct.unpack_from("<iiiiiiI", buf, o)
+    o += 28
     npart, U_tot, nsh = struct.unpack_from("<qqq", buf, o)
     o += 24
-    t = {"BE": BE_, "nblk": nblk, "max_u": max_u, "max_ne": max_ne, "max_bg": max_bg, "max_pkt": max_pkt,
+    t = {"BE": BE_, "nblk": nblk, "max_u": max_u, "max_ne": max_ne, "max_bg": max_bg, "max_copies": max_copies,
+         "max_pkt": max_pkt,
          "npart": npart, "U_tot": U_tot, "nsh": nsh}
     for name, dt in (("perm", np.int32), ("blk_e0", np.int32), ("blk_u0", np.int32), ("blk_nint", np.int32),
                      ("blk_p0", np.int32), ("grp_size", np.int32), ("grp_cnt", np.int32), ("grp_slot0", np.int32),
@@ -85,29 +84,18 @@ def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
 
 
 def packet(t, b, nloc):
-    """The sections of block b's packet (layout of csrc/packet.h); incoff[u] = start of dof u's
-    run in the dof-sorted order, read off the end bits."""
+    """The sections of block b's packet (layout of csrc/packet.h)."""
     ne = int(t["blk_e0"][b + 1] - t["blk_e0"][b])
     nu = int(t["blk_u0"][b + 1] - t["blk_u0"][b])
     p = t["pkt"][t["blk_pkt"][b]:t["blk_pkt"][b + 1]]
     off_d = _pad16(4 * nu)
     sa = off_d + _pad16(2 * nu)
     m = ne * nloc
-    off_ends = 2 * _pad16(2 * m)
-    nw = (m + 31) // 32
-    sb = off_ends + _pad16(4 * nw)
-    assert p.size == sa + sb
+    assert p.size == sa + _pad16(2 * m)
     ids = p[:4 * nu].view(np.int32)
     d = p[off_d:off_d + 2 * nu].view(np.uint16)
     loc = p[sa:sa + 2 * m].view(np.uint16)
-    pos = p[sa + _pad16(2 * m):sa + _pad16(2 * m) + 2 * m].view(np.uint16)
-    words = p[sa + off_ends:sa + off_ends + 4 * nw].view(np.uint32)
-    bits = ((words[:, None] >> np.arange(32, dtype=np.uint32)[None, :]) & 1).ravel()
-    assert not bits[m:].any()                                   # no end bit past the copies
-    ends = np.nonzero(bits[:m])[0]
-    assert ends.size == nu and (nu == 0 or ends[-1] == m - 1)
-    incoff = np.concatenate([[0], ends + 1]).astype(np.int64)
-    return ne, nu, ids, d, incoff, loc, pos
+    return ne, nu, ids, d, loc
 
 
 def check_invariants(t, l2g, signs, n, groups=None):
@@ -122,7 +110,7 @@ def check_invariants(t, l2g, signs, n, groups=None):
     shared_slots = {}
     groups_seen = {}
     for b in range(t["nblk"]):
-        ne, nu, ids, dm, incoff, loc, pos = packet(t, b, nloc)
+        ne, nu, ids, dm, loc = packet(t, b, nloc)
         e0, nint = int(t["blk_e0"][b]), int(t["blk_nint"][b])
         assert 0 < ne <= t["BE"] and nu <= t["max_u"] and ne <= t["max_ne"]
         cells = perm[e0:e0 + ne]
@@ -136,23 +124,14 @@ def check_invariants(t, l2g, signs, n, groups=None):
             assert np.array_equal(ids[u_of[a * ne:(a + 1) * ne]], g)
             s = np.ones(ne, bool) if signs is None else signs[cells, a] < 0
             assert np.array_equal(neg[a * ne:(a + 1) * ne], s if signs is not None else np.zeros(ne, bool))
-        # pos: a permutation of the slots; dof u's copies fill [incoff[u], incoff[u+1]) by ascending slot
-        assert np.array_equal(np.sort(pos), np.arange(ne * nloc))
-        assert incoff[0] == 0 and incoff[nu] == ne * nloc
-        for u in range(nu):
-            slots = np.nonzero(u_of == u)[0]                   # ascending slot a * ne + e
-            assert np.array_equal(pos[slots], np.arange(incoff[u], incoff[u + 1]))
-        counts = np.diff(incoff.astype(np.int64))
+        counts = np.bincount(u_of, minlength=nu)
+        assert counts.max() <= t["max_copies"]
         assert np.array_equal(counts[:nint], d[ids[:nint]])   # interior: every copy in the block
         assert np.all(counts[nint:] < d[ids[nint:]])
+        assert np.all(np.diff(ids[:nint]) > 0)                 # interior dofs by ascending id
         seen_interior += ids[:nint].tolist()
         for j, g in enumerate(ids[nint:]):
             shared_slots.setdefault(int(g), []).append((b, int(t["blk_p0"][b]) + j))
-        # interior dofs by ascending copy count (then id)
-        counts_int = counts[:nint]
-        assert np.all(np.diff(counts_int) >= 0)
-        for c_ in np.unique(counts_int):
-            assert np.all(np.diff(ids[:nint][counts_int == c_]) > 0)
         # the block's groups cover its shared dofs in order, each a contiguous run
         g0, g1 = int(t["blk_g0"][b]), int(t["blk_g0"][b + 1])
         assert g1 - g0 <= t["max_bg"]
@@ -198,20 +177,18 @@ def replay(t, A, x, nloc, bras):
     y = np.zeros_like(x)
     part = np.zeros(t["npart"])
     for b in range(t["nblk"]):
-        ne, nu, ids, dm, incoff, loc, pos = packet(t, b, nloc)
+        ne, nu, ids, dm, loc = packet(t, b, nloc)
         e0, nint = int(t["blk_e0"][b]), int(t["blk_nint"][b])
         xs = x[ids] / dm if bras else x[ids]
-        zs = np.zeros(ne * nloc)
+        ys = np.zeros(nu)
         sign = np.where(loc & 0x8000, -1.0, 1.0)
         u_of = (loc & 0x7FFF).astype(np.int64)
         for e in range(ne):
             sl = np.arange(nloc) * ne + e
             xl = sign[sl] * xs[u_of[sl]]
-            zs[pos[sl]] = sign[sl] * (A[perm[e0 + e]] @ xl)
+            np.add.at(ys, u_of[sl], sign[sl] * (A[perm[e0 + e]] @ xl))
         for u in range(nu):
-            acc = 0.0
-            for s in range(incoff[u], incoff[u + 1]):
-                acc += zs[s]
+            acc = ys[u]
             if u < nint:
                 y[ids[u]] = acc / dm[u] if bras else acc
             else:
