@@ -87,7 +87,8 @@ enum {
 typedef struct {
     int precisions;      /* bit mask of (1 << BRAS_FP64 | 1 << BRAS_FP32 | 1 << BRAS_BF16);
                             0 means all three                                           */
-    int block_elems;     /* elements per scatter block, 32..256; 0 = 256                 */
+    int block_elems;     /* elements per scatter block, 32..256 (H1 contexts without the
+                            tensor-core kernel: 32..1024); 0 = 256                          */
     int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
     int simt_only;       /* 1: H1 FP32 applies on the FP32 units instead of the tensor-core
                             (3xTF32 tcgen05) local GEMM; 0 = tensor cores where supported  */
@@ -96,11 +97,12 @@ typedef struct {
                             "Bernstein" family of Table 1); same multi-indices, same l2g.
                             BRAS_HCURL / BRAS_HDIV: 0 = first kind (N1curl_k / RT_k),
                             1 = second kind (N2curl_k / BDM_k, k = 1..4)                  */
-    int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for every cell
-                            block size (multiples of 32 up to 256) whose kernels fit shared
+    int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for eight cell
+                            block sizes (H1 on the FP32 units: 64..1024; H1 with tensor
+                            cores: 64..256; H(curl)/H(div): 32..256) whose kernels fit shared
                             memory and keep the fastest (one table build and four applies per
                             candidate; ignored if block_elems is set); 0 = the rule: the largest
-                            size whose FP32 kernel fits twice per SM                          */
+                            size up to 256 whose FP32 kernel fits twice per SM              */
 } bras_options;
 
 /*

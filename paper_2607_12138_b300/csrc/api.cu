@@ -188,7 +188,10 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     c->precisions = (opt && opt->precisions) ? opt->precisions : 7;
     c->max_nrhs = (opt && opt->max_nrhs > 0) ? opt->max_nrhs : 1;
     int BE = (opt && opt->block_elems) ? opt->block_elems : 256;
-    if (BE < 32 || BE > 256) return BRAS_ERR_INVALID;
+    // H1 contexts on the FP32 units (no tensor-core kernel) take blocks of up to 1024 cells,
+    // the block kernels looping over the cells of a block; the others up to 256
+    const bool simt_h1 = space == BRAS_H1 && !(h1_tc_supported(nloc) && !(opt && opt->simt_only));
+    if (BE < 32 || BE > (simt_h1 ? 1024 : 256)) return BRAS_ERR_INVALID;
     c->BE = BE;
     const bool want64 = c->precisions & 1, want32 = c->precisions & 2, wantbf = c->precisions & 4;
 
@@ -433,7 +436,14 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         HostTables best;
         float best_us = 1e30f;
         c->tune_count = 0;
-        for (int be = 256; be >= 32; be -= 32) {
+        // candidates: larger blocks for H1 on the FP32 units (fewer shared dofs), finer steps
+        // around the tensor-core kernel's two-threads-per-cell limit of 128 cells
+        static const int kSimtH1[8] = {1024, 768, 512, 384, 256, 192, 128, 64};
+        static const int kTc[8] = {256, 192, 160, 128, 112, 96, 80, 64};
+        static const int kOther[8] = {256, 224, 192, 160, 128, 96, 64, 32};
+        const int* cand = simt_h1 ? kSimtH1 : (c->use_tc ? kTc : kOther);
+        for (int ci = 0; ci < 8; ++ci) {
+            const int be = cand[ci];
             HostTables tt;
             if ((rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
                                    h_cells.data(), dim, be, &tt, &detail, cell_group)))

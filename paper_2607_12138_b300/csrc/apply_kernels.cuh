@@ -312,31 +312,36 @@ template <> __device__ __forceinline__ double pow2<double>(int k) {
 
 __device__ __forceinline__ long long fx_round(float v) { return __float2ll_rn(v); }
 __device__ __forceinline__ long long fx_round(double v) { return __double2ll_rn(v); }
-// acc = [low word | high word] of one dof (lo_bits > 0), or one 64-bit word (lo_bits = 0: the
-// FP64 applies, whose extra bits of resolution the FP64 tolerance needs)
-__device__ __forceinline__ void fx_add(long long* acc, long long q, int lo_bits) {
-    if (lo_bits == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)q);
-        return;
+// The accumulators of a block: FP32 (lo_bits > 0) two 32-bit words per dof, the low words of
+// every dof first and the high words after them (so that the lanes of a warp spread over all
+// banks), FP64 (lo_bits = 0) one 64-bit word per dof.  `count` dofs (times right-hand sides).
+struct FxAcc {
+    long long* base;
+    int count;
+    int lo_bits;
+    // zero the first n 8-byte words (n = count covers both halves, or every 64-bit word)
+    __device__ __forceinline__ void clear(int n) const {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) base[i] = 0;
     }
-    int* w = reinterpret_cast<int*>(acc);
-    atomicAdd(w, (int)(q & ((1ll << lo_bits) - 1)));
-    atomicAdd(w + 1, (int)(q >> lo_bits));
-}
-__device__ __forceinline__ long long fx_total(long long acc, int lo_bits) {
-    if (lo_bits == 0) return acc;
-    const int* w = reinterpret_cast<const int*>(&acc);
-    return ((long long)w[1] << lo_bits) + (long long)w[0];
-}
+    __device__ __forceinline__ void add(int i, long long q) const {
+        if (lo_bits == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(base) + i, (unsigned long long)q);
+            return;
+        }
+        int* w = reinterpret_cast<int*>(base);
+        atomicAdd(w + i, (int)(q & ((1ll << lo_bits) - 1)));
+        atomicAdd(w + count + i, (int)(q >> lo_bits));
+    }
+    __device__ __forceinline__ long long total(int i) const {
+        if (lo_bits == 0) return base[i];
+        const int* w = reinterpret_cast<const int*>(base);
+        return ((long long)w[count + i] << lo_bits) + (long long)w[i];
+    }
+};
+
 // accumulator -> value: one rounding of the exact integer sum, then the exact power-of-two scale
-template <typename T>
-__device__ __forceinline__ T fx_value(long long acc, int lo_bits, int k);
-template <> __device__ __forceinline__ float fx_value<float>(long long acc, int lo_bits, int k) {
-    return __ll2float_rn(fx_total(acc, lo_bits)) * pow2<float>(-k);
-}
-template <> __device__ __forceinline__ double fx_value<double>(long long acc, int lo_bits, int k) {
-    return __ll2double_rn(fx_total(acc, lo_bits)) * pow2<double>(-k);
-}
+__device__ __forceinline__ float fx_value(long long q, int k, float) { return __ll2float_rn(q) * pow2<float>(-k); }
+__device__ __forceinline__ double fx_value(long long q, int k, double) { return __ll2double_rn(q) * pow2<double>(-k); }
 
 // Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
 // their partial slot ([nrhs][npart] from p0; MR: slot-major rows, right-hand side r).
@@ -418,7 +423,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     int* fx = reinterpret_cast<int*>(smem_raw + 64);                    // [0, 1] ex per chunk parity, [2] ec
     unsigned char* tab = smem_raw + 128;                                 // table packet
     T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW] staged x
-    long long* ys = reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3));   // [u][CW] accumulators
+    long long* ys = reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3));   // accumulators
     T* xt = reinterpret_cast<T*>(ys + (((size_t)A.max_u * CW + 1) & ~(size_t)1));  // [NLOC][ne] (XS)
     T* Ms = xt + (XS ? ((NLOC * A.max_ne + 3) & ~3) : 0);                 // [NLOC][NPAD] (H1), 16-B aligned
 
@@ -451,7 +456,12 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
     }
     __syncthreads();   // barriers and bounds initialised before anyone uses them
-    if (KIND == KIND_H1 && tid < ne) atomicMax(&fx[2], exp_bound(cfac));
+    if (KIND == KIND_H1) {
+        int ec = tid < ne ? exp_bound(cfac) : kExpZero;
+        for (int e = tid + blockDim.x; e < ne; e += blockDim.x)   // blocks of more cells than threads
+            ec = max(ec, exp_bound(static_cast<const T*>(A.scale)[e0 + e]));
+        if (ec > kExpZero) atomicMax(&fx[2], ec);
+    }
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
@@ -466,7 +476,8 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
         int* fxe = &fx[ch & 1];
         if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
-        for (int i = tid; i < nu * CW; i += blockDim.x) ys[i] = 0;
+        const FxAcc acc{ys, (nu * CW + 1) & ~1, A.fx_lo};
+        acc.clear(acc.count);
 
         int emax = OP == OP_DIAG ? 1 : kExpZero;   // DIAG: the products are matrix entries (x = 1)
         if (OP != OP_DIAG && okA) {
@@ -561,7 +572,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     // signs of the first 64 local dofs kept as bits, the rest re-read from loc
                     const uint16_t c = L[a * ne];
                     const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0;
-                    fx_add(&ys[c & 0x7fff], fx_round((s ? -zl[a] : zl[a]) * sc), A.fx_lo);
+                    acc.add(c & 0x7fff, fx_round((s ? -zl[a] : zl[a]) * sc));
                 }
             }
         } else {
@@ -589,12 +600,12 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 auto out = [&](int a, T v) {
                     const uint16_t c = L[a * ne];
                     const bool s = SIGNED && OP != OP_DIAG && (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0);
-                    fx_add(&ys[(c & 0x7fff) * CW + rr], fx_round((s ? -v : v) * sc), A.fx_lo);
+                    acc.add((c & 0x7fff) * CW + rr, fx_round((s ? -v : v) * sc));
                 };
                 if constexpr (KIND == KIND_H1) {
                     using VM = typename Vec4<T>::type;
                     constexpr int W = Vec4<T>::W;
-                    const T c = MR ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
+                    const T c = (MR || e != tid) ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
 #pragma unroll
                     for (int a = 0; a < NLOC; ++a) {
                         T acc = T(0);
@@ -640,7 +651,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         // totals: interior dofs to y, shared ones to their partial slots
         for (int i = tid; i < nu * rc; i += blockDim.x) {
             const int u = i / rc, rr = i - u * rc;
-            const T v = bad ? T(NAN) : fx_value<T>(ys[u * CW + rr], A.fx_lo, kx);
+            const T v = bad ? T(NAN) : fx_value(acc.total(u * CW + rr), kx, T(0));
             store_dof<T, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
         }
         if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
@@ -653,7 +664,7 @@ size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36;
     const size_t cw = mr ? Chunk<T>::CW : 1;
     return 128 + ((A.max_pkt + 127u) & ~127u) + sizeof(T) * (((size_t)A.max_u * cw + 3) & ~(size_t)3) +
-           8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1) +
+           8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1) +   // accumulators
            sizeof(T) * ((XS ? (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) : 0) + (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
 }
 
@@ -690,8 +701,9 @@ cudaError_t launch_block(const BlockArgs& A, const CombineArgs& G, int nblk, con
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
     dim3 grid(mr ? nblk : nblk * nrhs);
-    // one thread per cell of the largest block; multi-RHS: 256 threads over the block's items
-    const int threads = mr ? 256 : (A.max_ne + 31) / 32 * 32;
+    // one thread per cell of the largest block (at most 256: larger H1 blocks loop over their
+    // cells); multi-RHS: 256 threads over the block's items
+    const int threads = mr ? 256 : std::min(256, (A.max_ne + 31) / 32 * 32);
     const int vec = rows_vectorisable<T>(nrhs, x, y, part) ? 1 : 0;
     kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs, vec);
     count_launch(1);

@@ -63,7 +63,8 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
         bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
         fx[0] = fx[1] = kExpZero;
     }
-    for (int i = tid; i < nu; i += blockDim.x) ys[i] = 0;
+    const FxAcc acc{ys, (nu + 1) & ~1, A.fx_lo};
+    acc.clear(acc.count);
     const double* ref = static_cast<const double*>(A.refmat);
     for (int i = tid; i < NLOC * NLOC; i += blockDim.x) {
         const double v = ref[i];
@@ -136,7 +137,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
                 float zh = 0.f, zl = 0.f;   // (sh + sl) (ch + cl)
                 df_term(ch, cl, sh[j], sl[j], zh, zl);
                 // both halves of the pair into the dof's fixed-point accumulator
-                fx_add(&ys[loc[a * ne + e]], fx_round(zh * sc) + fx_round(zl * sc), A.fx_lo);
+                acc.add(loc[a * ne + e], fx_round(zh * sc) + fx_round(zl * sc));
             }
         }
     }
@@ -144,7 +145,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
 
     // totals in FP64: interior dofs to y, shared ones to their partial slots
     for (int u = tid; u < nu; u += blockDim.x) {
-        const double v = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_value<double>(ys[u], A.fx_lo, kx);
+        const double v = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_value(acc.total(u), kx, 0.0);
         if (u < nint) y[(size_t)ids[u] * nrhs + r] = v;
         else part[p0 + (u - nint)] = v;
     }

@@ -132,9 +132,10 @@ struct TcArgs {
 };
 
 // MR = false: one cell per TMEM lane, one right-hand side per CTA (as k_block).  TPC = 1: one
-// thread per cell, blockDim / 128 tiles.  TPC = 2 (blocks of at most 128 cells): one tile, two
-// threads per cell, warps 0-3 taking the even and warps 4-7 the odd 8-column groups of the
-// tensor-memory rows, so that a CTA needs 128 TMEM columns and more CTAs share an SM.
+// thread per cell, blockDim / 128 tiles.  TPC = 2: two threads per cell, 256 threads per
+// 128-cell tile; in each group of eight warps, warps 0-3 take the even and warps 4-7 the odd
+// 8-column groups of the tile's tensor-memory rows (64 registers a thread: four 256-thread or
+// two 512-thread CTAs share an SM).
 // MR = true (TPC = 1): one CTA per cell block walks the right-hand sides in chunks of 4; the
 // block's ne * 4 items (cell, rhs) fill the tensor-memory lanes in passes of blockDim items
 // (two 128-lane tiles), each pass one GEMM (the E*R rows of the local product on the M side).
@@ -142,7 +143,7 @@ struct TcArgs {
 // with one right-hand side the accumulators take the staged vector's bytes over (dead once the
 // local vectors are in tensor memory) and are cleared while the GEMM runs.
 template <int NLOC, int OP, bool MR = false, int TPC = 1>
-__global__ void __launch_bounds__(256, TPC == 2 ? 4 : (MR ? 1 : 2))
+__global__ void __launch_bounds__(TPC == 2 ? 512 : 256, TPC == 2 ? 2 : (MR ? 1 : 2))
 k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, float* __restrict__ part, int nrhs,
            int vec_ok) {
     static_assert(TPC == 1 || (TPC == 2 && !MR), "two threads per cell only for one right-hand side a CTA");
@@ -164,8 +165,8 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     long long* ys = MR ? reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3)) : reinterpret_cast<long long*>(xs);
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int lt = TPC == 2 ? (tid & 127) : tid;              // this thread's lane in the pass
-    const int half = TPC == 2 ? (warp >> 2) : 0;              // its column groups (TPC = 2)
+    const int lt = TPC == 2 ? (warp >> 3) * 128 + (tid & 127) : tid;   // this thread's lane in the pass
+    const int half = TPC == 2 ? ((warp >> 2) & 1) : 0;                  // its column groups (TPC = 2)
     // one work item per CTA: a block (MR), or a (block, rhs) pair
     const int b = MR ? blockIdx.x : blockIdx.x / nrhs;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
@@ -193,7 +194,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     if (lt < ne && (TPC == 1 || half == 0)) atomicMax(&fx[2], exp_bound(cfac));
     const uint32_t tmem = *tmem_slot;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t tile_col = TPC == 2 ? 0u : (uint32_t)(warp >> 2) * Sh::TILE_COLS;
+    const uint32_t tile_col = (uint32_t)(TPC == 2 ? (warp >> 3) : (warp >> 2)) * Sh::TILE_COLS;
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
@@ -210,8 +211,8 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
         int* fxe = &fx[ch & 1];
         if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
-        if constexpr (MR)
-            for (int i = tid; i < nu * CW; i += blockDim.x) ys[i] = 0;
+        const FxAcc acc{ys, (nu * CW + 1) & ~1, A.fx_lo};
+        if constexpr (MR) acc.clear(acc.count);
         int emax = kExpZero;
         if constexpr (MR) {
             using V = Chunk<float>::V;
@@ -308,8 +309,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
             // stage 2b: one thread issues the 3xTF32 GEMM for the pass's tiles and waits for it;
             // with one right-hand side the others clear the accumulators (over the staged x,
             // read by now) meanwhile
-            if constexpr (!MR)
-                for (int i = tid; i < nu; i += blockDim.x) ys[i] = 0;
+            if constexpr (!MR) acc.clear(acc.count);
             bool done = true;
             if (tid == 0) {
                 if (ch == 0 && pass == 0) done = mbar_wait_bounded(&bars[2], A.status);
@@ -367,8 +367,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int a = 16 * g + j;
-                            if (a < NLOC)
-                                fx_add(&ys[loc[a * ne + e] * CW + rr], fx_round(__uint_as_float(v[g][j]) * cs), A.fx_lo);
+                            if (a < NLOC) acc.add(loc[a * ne + e] * CW + rr, fx_round(__uint_as_float(v[g][j]) * cs));
                         }
                     }
                 }
@@ -391,7 +390,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         // totals: interior dofs to y, shared ones to their partial slots
         for (int i = tid; i < nu * rc; i += blockDim.x) {
             const int u = i / rc, rr = i - u * rc;
-            const float v = bad ? __int_as_float(0x7fc00000) : fx_value<float>(ys[u * CW + rr], A.fx_lo, kx);
+            const float v = bad ? __int_as_float(0x7fc00000) : fx_value(acc.total(u * CW + rr), kx, 0.f);
             store_dof<float, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
         }
         if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
@@ -421,7 +420,7 @@ template <int NLOC>
 size_t tc_smem_bytes(const BlockArgs& A, bool mr = false) {
     const size_t cw = mr ? Chunk<float>::CW : 1;
     const size_t xsb = sizeof(float) * (((size_t)A.max_u * cw + 3) & ~(size_t)3);
-    const size_t ysb = 8 * (size_t)A.max_u * cw;
+    const size_t ysb = 8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1);
     return 128 + (size_t)tc_btile_region<NLOC>() + ((A.max_pkt + 127u) & ~127u) + (mr ? xsb + ysb : std::max(xsb, ysb));
 }
 
@@ -429,7 +428,8 @@ template <int NLOC, int OP>
 cudaError_t launch_block_tc(const TcArgs& TA, const CombineArgs& G, int nblk, const float* x, float* y, float* part,
                             int nrhs, cudaStream_t st) {
     const bool mr = nrhs > 1 && tc_smem_bytes<NLOC>(TA.A, true) <= (size_t)smem_optin_bytes();
-    // blocks of at most 128 cells: one tile, two threads per cell
+    // one right-hand side: blocks of at most 128 cells take two threads per cell (four CTAs per
+    // SM), larger ones one thread per cell over two tiles (measured faster at 256 cells)
     const bool two = !mr && TA.A.max_ne <= 128;
     const size_t smem = tc_smem_bytes<NLOC>(TA.A, mr);
     auto kern = mr ? k_block_tc<NLOC, OP, true, 1> : (two ? k_block_tc<NLOC, OP, false, 2> : k_block_tc<NLOC, OP, false, 1>);
@@ -437,8 +437,8 @@ cudaError_t launch_block_tc(const TcArgs& TA, const CombineArgs& G, int nblk, co
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err != cudaSuccess) return err;
-    // one or two 128-cell tensor tiles (two threads per cell with one); multi-RHS: two tiles of
-    // items per pass
+    // one or two 128-cell tensor tiles (two threads per cell); multi-RHS: two tiles of items
+    // per pass
     const int threads = 256;
     dim3 grid(mr ? nblk : nblk * nrhs);
     const int vec = rows_vectorisable<float>(nrhs, x, y, part) ? 1 : 0;
