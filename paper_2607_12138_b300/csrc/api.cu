@@ -225,7 +225,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     int64_t detail = -1;
     for (;;) {
         rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
-                          h_cells.data(), dim, BE, &t, &detail, cell_group);
+                          h_cells.data(), dim, BE, &t, &detail, cell_group, space != BRAS_H1);
         if (rc) { set_detail(detail); return rc; }
         const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, t);
         size_t s32 = block_smem_estimate(nloc, 4, space == BRAS_H1, t);
@@ -446,7 +446,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
             const int be = cand[ci];
             HostTables tt;
             if ((rc = build_tables(h_l2g.data(), signs ? h_signs.data() : nullptr, n_cell, nloc, n_dof, h_coords.data(),
-                                   h_cells.data(), dim, be, &tt, &detail, cell_group)))
+                                   h_cells.data(), dim, be, &tt, &detail, cell_group, space != BRAS_H1)))
                 break;
             tt.BE = be;
             const size_t s64 = block_smem_estimate(nloc, 8, space == BRAS_H1, tt);
@@ -508,10 +508,12 @@ BlockArgs shape_args(const HostTables& t) {
 size_t block_smem_estimate(int nloc, int tsize, bool h1, const HostTables& t, int cw) {
     const int w = tsize == 4 ? 4 : 2;
     const size_t npad = (size_t)((nloc + w - 1) / w * w);
-    const bool xs_cells = !h1 && nloc >= 36;   // local vectors of streamed matrices in shared memory
-    return 128 + ((t.max_pkt + 127u) & ~127u) + (size_t)tsize * (((size_t)t.max_u * cw + 3) / 4 * 4) +
-           8 * (((size_t)t.max_u * cw + 1) / 2 * 2) +
-           (size_t)tsize * ((xs_cells ? ((size_t)nloc * t.max_ne + 3) / 4 * 4 : 0) + (h1 ? nloc * npad : 0));
+    const size_t xsb = (size_t)tsize * (((size_t)t.max_u * cw + 3) / 4 * 4);
+    if (h1)   // staged x, fixed-point accumulators, reference matrix
+        return 128 + ((t.max_pkt + 127u) & ~127u) + xsb + 8 * (((size_t)t.max_u * cw + 1) / 2 * 2) +
+               (size_t)tsize * nloc * npad;
+    // staged x, dof-sorted products
+    return 128 + ((t.max_pkt + 127u) & ~127u) + xsb + (size_t)tsize * (((size_t)nloc * t.max_ne * cw + 3) / 4 * 4);
 }
 
 // Shared memory of the FP32 multi-RHS block kernel (16-byte chunks: 4 values a dof), 0 for a

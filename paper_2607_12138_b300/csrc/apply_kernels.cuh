@@ -353,6 +353,39 @@ __device__ __forceinline__ void store_dof(int u, T v, int nint, const int32_t* i
     else part[p0 + (u - nint)] = v;
 }
 
+// Stage 3 of the scatter path (streamed cell matrices): every block-local dof u sums its copies
+// zs[incoff[u], incoff[u+1]) in that order (Eq. mhatinvbras_def, the D^{-1} P^T half) and hands
+// the total to out(u, v).  A thread takes four dofs at a time so that their shared-memory chains
+// overlap; every dof's order is unchanged.
+template <typename V, typename Add, typename Out>
+__device__ __forceinline__ void dof_run_sums(int nu, const uint16_t* incoff, const V* zs, V zero, Add add, Out out) {
+    constexpr int U = 4;
+    const int T = blockDim.x;
+    for (int u = threadIdx.x; u < nu; u += U * T) {
+        int s0[U], cnt[U];
+        V acc[U];
+        int mx = 0;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * T;
+            s0[k] = uu < nu ? incoff[uu] : 0;
+            cnt[k] = uu < nu ? incoff[uu + 1] - s0[k] : 0;
+            acc[k] = zero;
+            mx = max(mx, cnt[k]);
+        }
+        for (int j = 0; j < mx; ++j) {
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (j < cnt[k]) acc[k] = add(acc[k], zs[s0[k] + j]);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int uu = u + k * T;
+            if (uu < nu) out(uu, acc[k]);
+        }
+    }
+}
+
 // Stage 4: one thread per (shared dof, rhs); every dof adds its partials in ascending block
 // order (0 + p_0 + p_1 + ...) and stores the total to y (times 1/d for BRAS).  Consecutive
 // threads take consecutive dofs of a group, so the partial reads coalesce and the group's
@@ -408,12 +441,17 @@ __device__ __forceinline__ double2 vsum(double2 a, const double2& b) { vadd(a, b
 // is CW work items (cell, rhs), rows of x and y move as 16-byte vectors, partial sums are laid
 // out [npart][nrhs].  The block's tables (and streamed cell matrices, re-read from L2) serve
 // every chunk.
+// Stage 3 by kind: H1 blocks add their products into fixed-point accumulators (ys); blocks of
+// streamed cell matrices (KIND_PACKED: up to 4 KB of matrix per cell, so the products leave a
+// thread in a long stream of loads) write each product to its dof-sorted slot (zs) and sum the
+// dofs' runs afterwards, which costs fewer shared-memory operations per copy than the atomics.
 template <int NLOC, typename T, typename S, int KIND, int OP, bool MR = false>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, T, NLOC, MR>::value))
 k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __restrict__ part, int nrhs, int vec_ok) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
     constexpr int CW = MR ? Chunk<T>::CW : 1;
     using V = typename Chunk<T>::V;
+    constexpr bool FX = KIND == KIND_H1;   // fixed-point accumulators (else dof-sorted scatter)
     // Lagrange (H1) dofs carry no orientation: the sign bit of a local index is only read for
     // H(curl)/H(div)
     constexpr bool SIGNED = KIND == KIND_PACKED;
@@ -423,15 +461,20 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     int* fx = reinterpret_cast<int*>(smem_raw + 64);                    // [0, 1] ex per chunk parity, [2] ec
     unsigned char* tab = smem_raw + 128;                                 // table packet
     T* xs = reinterpret_cast<T*>(tab + ((A.max_pkt + 127u) & ~127u));  // [u][CW] staged x
-    long long* ys = reinterpret_cast<long long*>(xs + ((A.max_u * CW + 3) & ~3));   // accumulators
-    T* xt = reinterpret_cast<T*>(ys + (((size_t)A.max_u * CW + 1) & ~(size_t)1));  // [NLOC][ne] (XS)
-    T* Ms = xt + (XS ? ((NLOC * A.max_ne + 3) & ~3) : 0);                 // [NLOC][NPAD] (H1), 16-B aligned
+    // H1: [u][CW] accumulators; vector spaces: [slot][CW] dof-sorted products (the signed local
+    // vectors of n_loc >= 36 wait there first, column e of a [a][cell] array)
+    T* after_xs = xs + ((A.max_u * CW + 3) & ~3);
+    long long* ys = reinterpret_cast<long long*>(after_xs);
+    T* zs = after_xs;
+    T* Ms = FX ? reinterpret_cast<T*>(ys + (((size_t)A.max_u * CW + 1) & ~(size_t)1))
+               : zs + ((NLOC * A.max_ne * CW + 3) & ~3);                  // [NLOC][NPAD] (H1), 16-B aligned
 
     const int b = MR ? blockIdx.x : blockIdx.x / nrhs, tid = threadIdx.x;
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
-    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    const uint32_t m = (uint32_t)(ne * NLOC);
+    const uint32_t sa = pkt_size_a(nu, !FX), sb = pkt_size_b(m, !FX);
     // this thread's cell factor (H1, one cell per thread; multi-RHS items read theirs again),
     // fetched now so that its latency hides behind the copies
     const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
@@ -444,8 +487,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         bulk_copy_g2s(tab, src, sa, &bars[0]);
         mbar_expect_tx(&bars[1], sb);
         bulk_copy_g2s(tab + sa, src + sa, sb, &bars[1]);
-        fx[0] = fx[1] = kExpZero;
-        fx[2] = KIND == KIND_H1 ? kExpZero : 0;
+        fx[0] = fx[1] = fx[2] = kExpZero;
     }
     if (KIND == KIND_H1) {
         const T* ref = static_cast<const T*>(A.refmat);
@@ -456,7 +498,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
     }
     __syncthreads();   // barriers and bounds initialised before anyone uses them
-    if (KIND == KIND_H1) {
+    if (FX) {
         int ec = tid < ne ? exp_bound(cfac) : kExpZero;
         for (int e = tid + blockDim.x; e < ne; e += blockDim.x)   // blocks of more cells than threads
             ec = max(ec, exp_bound(static_cast<const T*>(A.scale)[e0 + e]));
@@ -464,7 +506,9 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     }
     const int32_t* ids = reinterpret_cast<const int32_t*>(tab);
     const uint16_t* dmul = reinterpret_cast<const uint16_t*>(tab + pkt_off_d(nu));
+    const uint16_t* incoff = reinterpret_cast<const uint16_t*>(tab + pkt_off_incoff(nu));
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(tab + sa + pkt_off_pos(m));
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
     const int nchunk = MR ? (nrhs + CW - 1) / CW : 1;
@@ -475,9 +519,11 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         // first partial slot of this block (MR: row of [npart][nrhs])
         const int64_t p0 = MR ? (int64_t)A.blk_p0[b] : (int64_t)r0 * A.npart + A.blk_p0[b];
         int* fxe = &fx[ch & 1];
-        if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
         const FxAcc acc{ys, (nu * CW + 1) & ~1, A.fx_lo};
-        acc.clear(acc.count);
+        if (FX) {
+            if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
+            acc.clear(acc.count);
+        }
 
         int emax = OP == OP_DIAG ? 1 : kExpZero;   // DIAG: the products are matrix entries (x = 1)
         if (OP != OP_DIAG && okA) {
@@ -497,7 +543,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
                             for (int j = 0; j < CW; ++j) {
                                 if (OP == OP_BRAS) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
-                                emax = max(emax, exp_bound(vget(v[k], j)));
+                                if (FX) emax = max(emax, exp_bound(vget(v[k], j)));
                             }
                             reinterpret_cast<V*>(xs)[uu] = v[k];
                         }
@@ -517,14 +563,14 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                         const int uu = u + k * blockDim.x;
                         if (uu < nu) {
                             const T w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
-                            emax = max(emax, exp_bound(w));
+                            if (FX) emax = max(emax, exp_bound(w));
                             xs[uu] = w;
                         }
                     }
                 }
             }
         }
-        if (emax > kExpZero) atomicMax(fxe, emax);
+        if (FX && emax > kExpZero) atomicMax(fxe, emax);
         if (ch == 0) {
             if (!cta_wait(&bars[1], 0, A.status, okA)) {   // block-uniform decision
                 // let any copy still in flight land before the block's shared memory is released
@@ -537,9 +583,9 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         } else {
             __syncthreads();
         }
-        // the block's fixed-point scale (the bounds and the zeroed accumulators are complete)
-        bool bad;
-        const int kx = fx_scale<T>(*fxe, fx[2], A.fx_er, A.fx_top, bad);
+        // H1: the block's fixed-point scale (the bounds and the zeroed accumulators are complete)
+        bool bad = false;
+        const int kx = FX ? fx_scale<T>(*fxe, fx[2], A.fx_er, A.fx_top, bad) : 0;
         const T sc = pow2<T>(kx);
 
         // Work items: (cell e, rhs rr) -> item e * CW + rr.  One item per thread without MR.
@@ -547,8 +593,10 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         if constexpr (XS && !MR) {
             // Large streamed cell matrices (n_loc >= 36): the signed local vector waits in shared
             // memory, column e of a [a][cell] array (only this thread touches it), so that
-            // registers hold just the accumulators and the matrix loads in flight.
+            // registers hold just the accumulators and the matrix loads in flight; the results go
+            // out after a barrier, over the same array.
             const int e = tid;
+            T* xt = zs;
             uint64_t neg = 0;
             T zl[NLOC];
 #pragma unroll
@@ -567,12 +615,14 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     zl[a] = fma(m, xt[q * ne + e], zl[a]);
                     if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
                 });
+            }
+            __syncthreads();
+            if (e < ne) {
 #pragma unroll
                 for (int a = 0; a < NLOC; ++a) {
                     // signs of the first 64 local dofs kept as bits, the rest re-read from loc
-                    const uint16_t c = L[a * ne];
-                    const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0;
-                    acc.add(c & 0x7fff, fx_round((s ? -zl[a] : zl[a]) * sc));
+                    const bool s = a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (loc[a * ne + e] & 0x8000) != 0;
+                    zs[pos[a * ne + e]] = s ? -zl[a] : zl[a];
                 }
             }
         } else {
@@ -596,11 +646,16 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 }
 #pragma unroll
                 for (int a = NLOC; a < NPAD; ++a) xl[a] = T(0);
-                // the signed product v of copy (e, a) into its dof's accumulator
+                // the signed product v of copy (e, a): into its dof's accumulator (H1) or its
+                // dof-sorted slot
                 auto out = [&](int a, T v) {
-                    const uint16_t c = L[a * ne];
-                    const bool s = SIGNED && OP != OP_DIAG && (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (c & 0x8000) != 0);
-                    acc.add((c & 0x7fff) * CW + rr, fx_round((s ? -v : v) * sc));
+                    if constexpr (FX) {
+                        acc.add(L[a * ne] * CW + rr, fx_round(v * sc));
+                    } else {
+                        const bool s = SIGNED && OP != OP_DIAG &&
+                                       (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (L[a * ne] & 0x8000) != 0);
+                        zs[pos[a * ne + e] * CW + rr] = s ? -v : v;
+                    }
                 };
                 if constexpr (KIND == KIND_H1) {
                     using VM = typename Vec4<T>::type;
@@ -608,37 +663,37 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     const T c = (MR || e != tid) ? static_cast<const T*>(A.scale)[e0 + e] : cfac;
 #pragma unroll
                     for (int a = 0; a < NLOC; ++a) {
-                        T acc = T(0);
+                        T accv = T(0);
                         if (OP == OP_DIAG) {
-                            acc = Ms[a * NPAD + a];
+                            accv = Ms[a * NPAD + a];
                         } else {
                             const VM* row = reinterpret_cast<const VM*>(Ms + a * NPAD);
 #pragma unroll
                             for (int q = 0; q < NPAD / W; ++q) {
-                                const VM m = row[q];
+                                const VM mm = row[q];
                                 if constexpr (W == 4) {
-                                    acc = fma(m.x, xl[4 * q + 0], acc);
-                                    acc = fma(m.y, xl[4 * q + 1], acc);
-                                    acc = fma(m.z, xl[4 * q + 2], acc);
-                                    acc = fma(m.w, xl[4 * q + 3], acc);
+                                    accv = fma(mm.x, xl[4 * q + 0], accv);
+                                    accv = fma(mm.y, xl[4 * q + 1], accv);
+                                    accv = fma(mm.z, xl[4 * q + 2], accv);
+                                    accv = fma(mm.w, xl[4 * q + 3], accv);
                                 } else {
-                                    acc = fma(m.x, xl[2 * q + 0], acc);
-                                    acc = fma(m.y, xl[2 * q + 1], acc);
+                                    accv = fma(mm.x, xl[2 * q + 0], accv);
+                                    accv = fma(mm.y, xl[2 * q + 1], accv);
                                 }
                             }
                         }
-                        out(a, acc * c);
+                        out(a, accv * c);
                     }
                 } else {
                     T zl[NLOC];
 #pragma unroll
                     for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T mm) {
                         if (OP == OP_DIAG) {
-                            if (q == a) zl[a] = m;
+                            if (q == a) zl[a] = mm;
                         } else {
-                            zl[a] = fma(m, xl[q], zl[a]);
-                            if (q < a) zl[q] = fma(m, xl[a], zl[q]);
+                            zl[a] = fma(mm, xl[q], zl[a]);
+                            if (q < a) zl[q] = fma(mm, xl[a], zl[q]);
                         }
                     });
 #pragma unroll
@@ -648,24 +703,44 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
         __syncthreads();
 
-        // totals: interior dofs to y, shared ones to their partial slots
-        for (int i = tid; i < nu * rc; i += blockDim.x) {
-            const int u = i / rc, rr = i - u * rc;
-            const T v = bad ? T(NAN) : fx_value(acc.total(u * CW + rr), kx, T(0));
-            store_dof<T, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
+        if constexpr (FX) {
+            // totals: interior dofs to y, shared ones to their partial slots
+            for (int i = tid; i < nu * rc; i += blockDim.x) {
+                const int u = i / rc, rr = i - u * rc;
+                const T v = bad ? T(NAN) : fx_value(acc.total(u * CW + rr), kx, T(0));
+                store_dof<T, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
+            }
+        } else if constexpr (MR) {
+            dof_run_sums<V>(nu, incoff, reinterpret_cast<const V*>(zs), vzero(V{}),
+                            [](V a, const V& c) { return vsum(a, c); }, [&](int u, V v) {
+                                if (u < nint) {
+                                    if (OP == OP_BRAS) {
+#pragma unroll
+                                        for (int j = 0; j < CW; ++j) vget(v, j) = div_by_count(vget(v, j), dmul[u]);
+                                    }
+                                    st_seg(y + (size_t)ids[u] * nrhs + r0, rc, vec, v);
+                                } else {
+                                    st_seg(part + (size_t)(p0 + (u - nint)) * nrhs + r0, rc, vec, v);
+                                }
+                            });
+        } else {
+            dof_run_sums<T>(nu, incoff, zs, T(0), [](T a, T c) { return a + c; },
+                            [&](int u, T v) { store_dof<T, OP, false>(u, v, nint, ids, dmul, y, part, nrhs, r0, p0); });
         }
-        if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
+        if (MR) __syncthreads();   // the sums are read before the next chunk stages x and clears
     }
 }
 
 template <int NLOC, typename T, int KIND>
 size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     constexpr int NPAD = PadTo<NLOC, T>::value;
-    constexpr bool XS = KIND == KIND_PACKED && NLOC >= 36;
     const size_t cw = mr ? Chunk<T>::CW : 1;
-    return 128 + ((A.max_pkt + 127u) & ~127u) + sizeof(T) * (((size_t)A.max_u * cw + 3) & ~(size_t)3) +
-           8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1) +   // accumulators
-           sizeof(T) * ((XS ? (((size_t)NLOC * A.max_ne + 3) & ~(size_t)3) : 0) + (KIND == KIND_H1 ? (size_t)NLOC * NPAD : 0));
+    const size_t xsb = sizeof(T) * (((size_t)A.max_u * cw + 3) & ~(size_t)3);
+    if (KIND == KIND_H1)   // staged x, fixed-point accumulators, reference matrix
+        return 128 + ((A.max_pkt + 127u) & ~127u) + xsb + 8 * (((size_t)A.max_u * cw + 1) & ~(size_t)1) +
+               sizeof(T) * (size_t)NLOC * NPAD;
+    // staged x, dof-sorted products
+    return 128 + ((A.max_pkt + 127u) & ~127u) + xsb + sizeof(T) * (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3);
 }
 
 // Largest dynamic shared memory one CTA may opt into on the current device.

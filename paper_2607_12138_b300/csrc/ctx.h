@@ -43,9 +43,11 @@ struct HostTables {
     int max_copies = 1;   // most copies of one dof inside one block
 };
 
+// scatter = true: the packets also carry the dof-sorted positions and run offsets (blocks of
+// streamed cell matrices); false: local indices only (H1, fixed-point sums)
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
                  const double* coords, const int32_t* cells, int dim, int BE, HostTables* t,
-                 int64_t* detail, const int32_t* cell_group = nullptr);
+                 int64_t* detail, const int32_t* cell_group = nullptr, bool scatter = false);
 
 }  // namespace bras
 

@@ -51,7 +51,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
     const int64_t p0 = (int64_t)r * A.npart + A.blk_p0[b];
-    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    const uint32_t sa = pkt_size_a(nu, false), sb = pkt_size_b((uint32_t)(ne * NLOC), false);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);

@@ -28,7 +28,7 @@ __global__ void k_grad_rho(int64_t E, int BE, const int32_t* __restrict__ blk_e0
         const uint32_t nu = (uint32_t)(blk_u0[b + 1] - blk_u0[b]);
         const unsigned char* P = pkt + blk_pkt[b];
         const int32_t* ids = reinterpret_cast<const int32_t*>(P);
-        const uint16_t* L = reinterpret_cast<const uint16_t*>(P + pkt_size_a(nu)) + el;
+        const uint16_t* L = reinterpret_cast<const uint16_t*>(P + pkt_size_a(nu, false)) + el;
         double xl[NLOC], ll[NLOC];
 #pragma unroll
         for (int a = 0; a < NLOC; ++a) {

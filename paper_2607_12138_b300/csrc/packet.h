@@ -1,11 +1,17 @@
 // Byte layout of one cell block's table packet (host and device share it).
-//   part A: ids int32[nu] | d uint16[nu]
-//   part B: loc uint16[m]                                                (m = ne * nloc)
+//   part A: ids int32[nu] | d uint16[nu] | (scatter) incoff uint16[nu + 1]
+//   part B: loc uint16[m] | (scatter) pos uint16[m]                          (m = ne * nloc)
+// H1 blocks sum their copies in fixed-point accumulators indexed by loc; blocks of streamed
+// cell matrices (H(curl), H(div)) scatter their products to the dof-sorted order (pos) and sum
+// each dof's run [incoff[u], incoff[u + 1]) -- the "scatter" sections.
 // Every section starts on a 16-byte boundary so that each part is one bulk copy.
 //   ids[u]   global dof of block-local dof u (interior dofs first, by ascending id, then the
 //            shared ones grouped by their set of blocks)
 //   d[u]     its multiplicity (D = P^T P)
 //   loc[s]   block-local dof of copy s = a * ne + e (cell e, local index a); bit 15 = sign -1
+//   pos[s]   position of copy s in the dof-sorted order (dof u's copies are one contiguous run,
+//            by ascending s: the fixed summation order)
+//   incoff   dof u's copies occupy positions [incoff[u], incoff[u + 1]) of that order
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
@@ -19,8 +25,12 @@
 namespace bras {
 BRAS_HD inline uint32_t pad16(uint32_t b) { return (b + 15u) & ~15u; }
 BRAS_HD inline uint32_t pkt_off_d(uint32_t nu) { return pad16(4u * nu); }
-BRAS_HD inline uint32_t pkt_size_a(uint32_t nu) { return pkt_off_d(nu) + pad16(2u * nu); }
-BRAS_HD inline uint32_t pkt_size_b(uint32_t m) { return pad16(2u * m); }
+BRAS_HD inline uint32_t pkt_off_incoff(uint32_t nu) { return pkt_off_d(nu) + pad16(2u * nu); }
+BRAS_HD inline uint32_t pkt_size_a(uint32_t nu, bool scatter) {
+    return pkt_off_incoff(nu) + (scatter ? pad16(2u * nu + 2u) : 0u);
+}
+BRAS_HD inline uint32_t pkt_off_pos(uint32_t m) { return pad16(2u * m); }
+BRAS_HD inline uint32_t pkt_size_b(uint32_t m, bool scatter) { return (scatter ? 2u : 1u) * pad16(2u * m); }
 
 // Per-cell packed symmetric matrices (lower triangle by rows, entry idx = a (a + 1) / 2 + q)
 // are stored vector-interleaved: groups of G consecutive entries of one cell are contiguous

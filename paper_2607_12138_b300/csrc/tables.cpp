@@ -33,7 +33,7 @@ uint64_t spread3(uint64_t v) {          // 21 bits -> every third bit
 
 int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, int64_t n,
                  const double* coords, const int32_t* cells, int dim, int BE, HostTables* t,
-                 int64_t* detail, const int32_t* cell_group) {
+                 int64_t* detail, const int32_t* cell_group, bool scatter) {
     // multiplicities d_i = #{(K, a) : l2g[K, a] = i}  (D = P^T P)
     std::vector<int32_t> d(n, 0);
     for (int64_t i = 0; i < E * nloc; ++i) {
@@ -205,7 +205,7 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         uint32_t ng = 0;
         for (size_t j = 0; j < B.gid_of.size(); ++j)
             if (j == 0 || B.gid_of[j] != B.gid_of[j - 1]) ++ng;
-        const uint32_t sz = pkt_size_a(nu) + pkt_size_b(m);
+        const uint32_t sz = pkt_size_a(nu, scatter) + pkt_size_b(m, scatter);
         t->blk_u0[b] = (int32_t)U;
         t->blk_nint[b] = B.nint;
         t->blk_p0[b] = (int32_t)P;
@@ -269,17 +269,25 @@ int build_tables(const int32_t* l2g, const int8_t* signs, int64_t E, int nloc, i
         std::memcpy(p, B.ids.data(), 4 * (size_t)nu);
         uint16_t* dm = reinterpret_cast<uint16_t*>(p + pkt_off_d(nu));
         for (uint32_t u = 0; u < nu; ++u) dm[u] = (uint16_t)std::min<int32_t>(d[B.ids[u]], 65535);
-        uint16_t* loc = reinterpret_cast<uint16_t*>(p + pkt_size_a(nu));
+        uint16_t* incoff = reinterpret_cast<uint16_t*>(p + pkt_off_incoff(nu));
+        uint16_t* loc = reinterpret_cast<uint16_t*>(p + pkt_size_a(nu, scatter));
+        uint16_t* pos = loc + pkt_off_pos(m) / 2;
+        // dof-sorted order (scatter tables): the dofs in block-local order u, each dof's copies
+        // by ascending slot
+        uint32_t off = 0;
         for (uint32_t u = 0; u < nu; ++u) {
             const int i = B.order[u];
+            if (scatter) incoff[u] = (uint16_t)off;
             for (int s = B.first[i]; s < B.first[i + 1]; ++s) {
                 const int slot = B.srt[s].second, a = slot / ne, e = slot % ne;
                 const int64_t K = t->perm[e0 + e];
                 const bool neg = signs && signs[K * nloc + a] < 0;
                 loc[slot] = (uint16_t)(u | (neg ? 0x8000u : 0u));
+                if (scatter) pos[slot] = (uint16_t)off;
+                ++off;
             }
         }
-        (void)m;
+        if (scatter) incoff[nu] = (uint16_t)off;
     }
     return BRAS_OK;
 }

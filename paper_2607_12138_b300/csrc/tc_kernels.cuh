@@ -172,7 +172,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const int e0 = A.blk_e0[b], ne = A.blk_e0[b + 1] - e0;
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
-    const uint32_t sa = pkt_size_a(nu), sb = pkt_size_b((uint32_t)(ne * NLOC));
+    const uint32_t sa = pkt_size_a(nu, false), sb = pkt_size_b((uint32_t)(ne * NLOC), false);
     // this thread's cell factor, fetched now so that its latency hides behind the copies
     const float cfac = lt < ne ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;
     if (tid == 0) {

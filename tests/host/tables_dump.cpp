@@ -2,7 +2,7 @@
 // read from a binary file and writes every table it produced, for the CPU tests to check.
 //
 // Input (little endian): int64 E, int32 nloc, int64 n, int32 dim, int32 BE, int64 nvert,
-//   int32 has_signs, int32 has_groups, int32 l2g[E*nloc], [int8 signs[E*nloc]],
+//   int32 has_signs, int32 has_groups, int32 scatter, int32 l2g[E*nloc], [int8 signs[E*nloc]],
 //   double coords[nvert*dim], int32 cells[E*(dim+1)], [int32 groups[E]].
 // Output: int32 rc, int64 detail, and for rc == 0: int32 BE, nblk, max_u, max_ne, max_bg, max_copies,
 //   uint32 max_pkt, int64 npart, U_tot, nsh, then the arrays perm, blk_e0, blk_u0, blk_nint,
@@ -31,9 +31,9 @@ int main(int argc, char** argv) {
     FILE* in = fopen(argv[1], "rb");
     if (!in) return 2;
     int64_t E = 0, n = 0, nvert = 0;
-    int32_t nloc = 0, dim = 0, BE = 0, has_signs = 0, has_groups = 0;
+    int32_t nloc = 0, dim = 0, BE = 0, has_signs = 0, has_groups = 0, scatter = 0;
     bool ok = rd(in, &E, 1) && rd(in, &nloc, 1) && rd(in, &n, 1) && rd(in, &dim, 1) && rd(in, &BE, 1) &&
-              rd(in, &nvert, 1) && rd(in, &has_signs, 1) && rd(in, &has_groups, 1);
+              rd(in, &nvert, 1) && rd(in, &has_signs, 1) && rd(in, &has_groups, 1) && rd(in, &scatter, 1);
     std::vector<int32_t> l2g(ok ? E * nloc : 0), cells(ok ? E * (dim + 1) : 0), groups;
     std::vector<int8_t> signs;
     std::vector<double> coords(ok ? nvert * dim : 0);
@@ -53,7 +53,8 @@ int main(int argc, char** argv) {
     bras::HostTables t;
     int64_t detail = -1;
     const int rc = bras::build_tables(l2g.data(), has_signs ? signs.data() : nullptr, E, nloc, n, coords.data(),
-                                      cells.data(), dim, BE, &t, &detail, has_groups ? groups.data() : nullptr);
+                                      cells.data(), dim, BE, &t, &detail, has_groups ? groups.data() : nullptr,
+                                      scatter != 0);
     FILE* out = fopen(argv[2], "wb");
     if (!out) return 2;
     wr(out, (int32_t)rc);

@@ -42,12 +42,13 @@ def _pad16(b):
     return (b + 15) & ~15
 
 
-def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
+def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None, scatter=False):
     E, nloc = l2g.shape
     dim = mesh.dim
     inp, out = str(tmp / "in.bin"), str(tmp / "out.bin")
     with open(inp, "wb") as f:
-        f.write(struct.pack("<qiqiiqii", E, nloc, n, dim, BE, mesh.n_vert, signs is not None, groups is not None))
+        f.write(struct.pack("<qiqiiqiii", E, nloc, n, dim, BE, mesh.n_vert, signs is not None, groups is not None,
+                            scatter))
         f.write(np.ascontiguousarray(l2g, dtype=np.int32).tobytes())
         if signs is not None:
             f.write(np.ascontiguousarray(signs, dtype=np.int8).tobytes())
@@ -80,22 +81,28 @@ def build_tables(exe, tmp, mesh, l2g, signs, n, BE, groups=None):
         t[name] = np.frombuffer(buf, dtype=dt, count=cnt, offset=o).copy()
         o += size
     assert o == len(buf)
+    t["scatter"] = scatter
     return rc, detail, t
 
 
 def packet(t, b, nloc):
-    """The sections of block b's packet (layout of csrc/packet.h)."""
+    """The sections of block b's packet (layout of csrc/packet.h): ids, d, loc, and with the
+    scatter sections also incoff and pos (None otherwise)."""
     ne = int(t["blk_e0"][b + 1] - t["blk_e0"][b])
     nu = int(t["blk_u0"][b + 1] - t["blk_u0"][b])
     p = t["pkt"][t["blk_pkt"][b]:t["blk_pkt"][b + 1]]
+    sc = t["scatter"]
     off_d = _pad16(4 * nu)
-    sa = off_d + _pad16(2 * nu)
+    off_inc = off_d + _pad16(2 * nu)
+    sa = off_inc + (_pad16(2 * nu + 2) if sc else 0)
     m = ne * nloc
-    assert p.size == sa + _pad16(2 * m)
+    assert p.size == sa + (2 if sc else 1) * _pad16(2 * m)
     ids = p[:4 * nu].view(np.int32)
     d = p[off_d:off_d + 2 * nu].view(np.uint16)
     loc = p[sa:sa + 2 * m].view(np.uint16)
-    return ne, nu, ids, d, loc
+    incoff = p[off_inc:off_inc + 2 * (nu + 1)].view(np.uint16) if sc else None
+    pos = p[sa + _pad16(2 * m):sa + _pad16(2 * m) + 2 * m].view(np.uint16) if sc else None
+    return ne, nu, ids, d, loc, incoff, pos
 
 
 def check_invariants(t, l2g, signs, n, groups=None):
@@ -110,7 +117,7 @@ def check_invariants(t, l2g, signs, n, groups=None):
     shared_slots = {}
     groups_seen = {}
     for b in range(t["nblk"]):
-        ne, nu, ids, dm, loc = packet(t, b, nloc)
+        ne, nu, ids, dm, loc, incoff, pos = packet(t, b, nloc)
         e0, nint = int(t["blk_e0"][b]), int(t["blk_nint"][b])
         assert 0 < ne <= t["BE"] and nu <= t["max_u"] and ne <= t["max_ne"]
         cells = perm[e0:e0 + ne]
@@ -126,6 +133,14 @@ def check_invariants(t, l2g, signs, n, groups=None):
             assert np.array_equal(neg[a * ne:(a + 1) * ne], s if signs is not None else np.zeros(ne, bool))
         counts = np.bincount(u_of, minlength=nu)
         assert counts.max() <= t["max_copies"]
+        if pos is not None:
+            # pos: a permutation of the slots; dof u's copies fill [incoff[u], incoff[u+1]) by ascending slot
+            assert np.array_equal(np.sort(pos), np.arange(ne * nloc))
+            assert incoff[0] == 0 and incoff[nu] == ne * nloc
+            assert np.array_equal(np.diff(incoff.astype(np.int64)), counts)
+            for u in range(nu):
+                slots = np.nonzero(u_of == u)[0]               # ascending slot a * ne + e
+                assert np.array_equal(pos[slots], np.arange(incoff[u], incoff[u + 1]))
         assert np.array_equal(counts[:nint], d[ids[:nint]])   # interior: every copy in the block
         assert np.all(counts[nint:] < d[ids[nint:]])
         assert np.all(np.diff(ids[:nint]) > 0)                 # interior dofs by ascending id
@@ -177,16 +192,25 @@ def replay(t, A, x, nloc, bras):
     y = np.zeros_like(x)
     part = np.zeros(t["npart"])
     for b in range(t["nblk"]):
-        ne, nu, ids, dm, loc = packet(t, b, nloc)
+        ne, nu, ids, dm, loc, incoff, pos = packet(t, b, nloc)
         e0, nint = int(t["blk_e0"][b]), int(t["blk_nint"][b])
         xs = x[ids] / dm if bras else x[ids]
         ys = np.zeros(nu)
         sign = np.where(loc & 0x8000, -1.0, 1.0)
         u_of = (loc & 0x7FFF).astype(np.int64)
-        for e in range(ne):
-            sl = np.arange(nloc) * ne + e
-            xl = sign[sl] * xs[u_of[sl]]
-            np.add.at(ys, u_of[sl], sign[sl] * (A[perm[e0 + e]] @ xl))
+        if pos is None:     # fixed-point path: products straight into the dofs' accumulators
+            for e in range(ne):
+                sl = np.arange(nloc) * ne + e
+                xl = sign[sl] * xs[u_of[sl]]
+                np.add.at(ys, u_of[sl], sign[sl] * (A[perm[e0 + e]] @ xl))
+        else:               # scatter path: products to the dof-sorted slots, then each dof's run
+            zs = np.zeros(ne * nloc)
+            for e in range(ne):
+                sl = np.arange(nloc) * ne + e
+                xl = sign[sl] * xs[u_of[sl]]
+                zs[pos[sl]] = sign[sl] * (A[perm[e0 + e]] @ xl)
+            for u in range(nu):
+                ys[u] = zs[incoff[u]:incoff[u + 1]].sum()
         for u in range(nu):
             acc = ys[u]
             if u < nint:
@@ -220,7 +244,7 @@ def test_tables_replay_the_oracle_operators(dump_exe, tmp_path, case):
     make, space, order, BE = CASES[case]
     mesh = make()
     n, l2g, signs = mg.dof_map(mesh, space, order)
-    rc, _, t = build_tables(dump_exe, tmp_path, mesh, l2g, signs, n, BE)
+    rc, _, t = build_tables(dump_exe, tmp_path, mesh, l2g, signs, n, BE, scatter=space != "h1")
     assert rc == 0
     assert t["nblk"] == -(-mesh.n_cell // BE)
     check_invariants(t, l2g, signs, n)
