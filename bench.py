@@ -10,12 +10,17 @@ dot products and scalars) inside FP64 iterative refinement, the TRUE FP64 residu
 The metric is conforming dofs solved per second (sum of n over the step / step time).
 Setup (tables, element inverses) is excluded, as in the paper.
 
-Also in the same JSON line: comparison rows on the same GPU (plain FP64 BRAS-PCG, FP64
-Jacobi-PCG, mixed Jacobi-PCG; 32 right-hand sides at p = 2, 4; the FP64 damped fixed point and
-Chebyshev iterations of Sec. 3; the Bernstein basis with BRAS vs Jacobi), the end-to-end
-number through host buffers, live CUDA-event timings of the apply kernels (H1 p = 1..4 and
-the streamed N1curl k = 3 inverses on 40^3 x 6 tets), the roofline of the dominant kernel and
-of the streamed path, and the FP64 CPU oracle baseline.
+Every timed answer is checked afterwards by its true FP64 residual from the FP64 mass apply
+(`true_relres_fp64`, must be <= 1e-10).  Also in the same JSON line: plain FP64 BRAS-PCG and
+FP64 Jacobi-PCG on the same GPU (top level, `fp64_bras_pcg`, `fp64_jacobi_pcg`); comparison
+rows (mixed Jacobi-PCG; 32 right-hand sides at p = 2, 4; 64 right-hand sides on H(curl) k = 1..3,
+mixed vs FP64 BRAS vs FP64 Jacobi; the FP64 damped fixed point and Chebyshev iterations of Sec. 3;
+the Bernstein basis with BRAS vs Jacobi; the batched H(div) solves RT k = 1..3 over 256 meshes;
+the differentiable weighted solve, forward and backward; kappa_hat by CG-Lanczos; the mixed
+Poisson Schur apply), the end-to-end number through host buffers, live CUDA-event timings of
+the apply kernels (H1 p = 1..4 and the streamed N1curl k = 3 inverses on 40^3 x 6 tets), the
+roofline of the dominant kernel and of the streamed path, and the FP64 CPU oracle baselines
+(one thread, and one independent solve per host core).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -50,6 +55,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-mesh rows")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 64-RHS H(curl) rows")
     return ap.parse_args()
 
 
@@ -100,6 +106,39 @@ def oracle_solve_rate(orders=(1, 2), repeats=3):
         tot_t += t
         detail.append({"p": p, "n": n, "its": its, "s": round(t, 4)})
     return tot_n / tot_t, detail
+
+
+def _oracle_worker(args):
+    """One process of the all-cores leg: build the oracle problem of order p (its own RHS
+    seed), wait for the others, then time one solve."""
+    p, seed, barrier = args
+    from oracle.assembly import Problem
+    from oracle.solvers import pcg
+    from paper_2607_12138_b300 import meshgen as mg
+    mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
+    n, l2g, s = mg.dof_map(mesh, "h1", p)
+    pr = Problem(mesh, "h1", p, l2g, s, n)
+    b = mg.rhs(n, 1, seed=seed)
+    barrier.wait()
+    t0 = time.perf_counter()
+    pcg(pr.mass_apply, b, pr.bras_apply, rtol=1e-10)
+    return n, time.perf_counter() - t0
+
+
+def oracle_all_cores_rate(p=2, max_procs=16):
+    """Throughput of the FP64 oracle on all host cores: one independent single-threaded
+    BRAS-PCG solve per process (order p, one right-hand side each, started together after
+    their setups); rate = all processes' dofs / the slowest solve."""
+    import multiprocessing as mp
+    procs = max(1, min(os.cpu_count() or 1, max_procs))
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(p, 1 + i, barrier) for i in range(procs)])
+    tot_n = sum(r[0] for r in res)
+    t_max = max(r[1] for r in res)
+    return tot_n / t_max, procs, t_max
 
 
 def run_reference(a):
@@ -274,6 +313,15 @@ def run_ours(a):
     for its, rel, status in res:
         if status != 0 or rel > 1e-10:
             raise RuntimeError(f"solve did not reach 1e-10: {res}")
+    # independent check of the 1e-10 target: the true residual ||b - M x|| / ||b|| of every
+    # answer of the last timed step from the FP64 mass apply (the FP64 block kernel, parity-
+    # tested at full size; not the float-float apply the refinement loop itself uses), untimed
+    true_relres = []
+    for pr in probs:
+        r = pr["b"] - pr["ctx"].mass_apply(pr["x"], B.FP64)
+        true_relres.append(float(torch.linalg.norm(r) / torch.linalg.norm(pr["b"])))
+    if max(true_relres) > 1e-10:
+        raise RuntimeError(f"true FP64 residual above 1e-10: {true_relres}")
 
     # end to end through host buffers (H2D of b and D2H of x inside the call)
     for _ in range(1):
@@ -301,7 +349,8 @@ def run_ours(a):
     last_ms = order_ms.get((B.SOLVE_MIXED, B.PC_BRAS, False), [None] * len(probs))
     for i, pr in enumerate(probs):
         its, rel, _ = res[i]
-        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel, "solve_ms": last_ms[i],
+        detail.append({"p": pr["p"], "n": pr["n"], "mixed_bras_its": its, "relres": rel,
+                       "true_relres_fp64": true_relres[i], "solve_ms": last_ms[i],
                        "block_elems": pr["ctx"].block_tuning[0]})
     if not a.no_compare:
         for name, mode, pc in (("fp64_bras", B.SOLVE_FP64, B.PC_BRAS), ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI),
@@ -394,13 +443,13 @@ def run_ours(a):
 
     # Batched multi-mesh solve (the H(div) batch configuration): jittered boxes with target tet
     # counts log-uniform in [2e3, 2e5], one N(0,1) right-hand side each, all meshes in one
-    # context and one solve (per-mesh scalars and stopping tests).  RT k=1 on the whole batch of
-    # 256 meshes; RT k=3 on its first 32 meshes (the whole batch would need ~140 GB of FP64
-    # per-cell inverses).
+    # context and one solve (per-mesh scalars and stopping tests).  RT k = 1, 2, 3 on the whole
+    # batch of 256 meshes; the contexts keep FP32 inverses only (the mixed solve's inner
+    # precision; FP64 cell mass matrices for the refinement residual are always kept).
     if not a.no_compare and not a.no_batch:
         sizes = mg.batch_mesh_sizes(256, seed=0)
         batch = {}
-        for k, count in ((1, 256), (3, 32)):
+        for k, count in ((1, 256), (2, 256), (3, 256)):
             t0 = time.perf_counter()
             meshes, rhs = [], []
             for i, (nx, nz) in enumerate(sizes[:count]):
@@ -408,7 +457,7 @@ def run_ours(a):
                 nk, lk, sk = mg.dof_map(m, "hdiv", k)
                 meshes.append((m.coords, m.cells, nk, lk, sk))
                 rhs.append(mg.rhs(nk, 1, seed=1000 + i))
-            cb = B.Context.batched(meshes, "hdiv", k, autotune=(k == 3))
+            cb = B.Context.batched(meshes, "hdiv", k, autotune=(k == 3), precisions=2)
             t_setup = time.perf_counter() - t0
             bt = torch.as_tensor(np.concatenate(rhs), device="cuda")
             xb = torch.empty_like(bt)
@@ -428,7 +477,72 @@ def run_ours(a):
                              "its_max": int(its_b.max()), "relres_max": float(rel_b.max()), "status": int(st_b)}
             batch[f"rt{k}"] = row
             del cb, bt, xb
+            torch.cuda.empty_cache()
         compare["batched_hdiv"] = batch
+
+    # 64 right-hand sides, H(curl) Nedelec k = 1..3 on 40^3 x 6 tets: mixed BRAS-PCG (FP32 inner,
+    # FP64 refinement) against plain FP64 BRAS-PCG and FP64 Jacobi-PCG, one solve each
+    if not a.no_compare and not a.no_c3:
+        c3rows = {}
+        m40c = mg.unit_cube_mesh(40, jitter=JITTER, seed=0)
+        R = 64
+        for k in (1, 2, 3):
+            nk, lk, sk = mg.dof_map(m40c, "hcurl", k)
+            cc = B.Context(m40c.coords, m40c.cells, "hcurl", k, nk, lk, sk, max_nrhs=R, precisions=3)
+            bR = torch.as_tensor(mg.rhs(nk, R, seed=1), device="cuda")
+            xR = torch.empty_like(bR)
+            row = {"dofs": nk, "nrhs": R}
+            for name, mode, pc in (("mixed_bras", B.SOLVE_MIXED, B.PC_BRAS), ("fp64_bras", B.SOLVE_FP64, B.PC_BRAS),
+                                   ("fp64_jacobi", B.SOLVE_FP64, B.PC_JACOBI)):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                _, itsR, relR, stR = cc.pcg_solve(bR, pc=pc, mode=mode, rtol=1e-10, out=xR)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                r = bR - cc.mass_apply(xR, B.FP64)
+                true_rel = float((torch.linalg.norm(r, dim=0) / torch.linalg.norm(bR, dim=0)).max())
+                row[name] = {"ms": ms, "dof_per_s": nk * R / (ms / 1e3), "its_max": int(max(itsR)),
+                             "relres_max": float(max(relR)), "true_relres_fp64_max": true_rel, "status": int(stR)}
+            c3rows[f"n1curl_k{k}"] = row
+            del cc, bR, xR
+            torch.cuda.empty_cache()
+        compare["hcurl_64rhs"] = c3rows
+
+    # differentiable weighted mass solve (H1 p = 3 on 32^3 x 6 tets, rho = exp(z), z ~ N(0, 0.5^2)):
+    # forward x = M(rho)^{-1} b and backward (second solve, fused element gradient) timed
+    if not a.no_compare:
+        from paper_2607_12138_b300.autograd import WeightedMassSolver
+        m32 = mg.unit_cube_mesh(32, jitter=JITTER, seed=0)
+        n5, l5, _ = mg.dof_map(m32, "h1", 3)
+        zt = torch.as_tensor(np.random.default_rng(2).normal(0, 0.5, m32.n_cell), device="cuda")
+        b5 = torch.as_tensor(mg.rhs(n5, 1, seed=1), device="cuda")
+        xs5 = torch.as_tensor(mg.rhs(n5, 1, seed=3), device="cuda")
+        grad_rows = {"dofs": n5, "cells": int(m32.n_cell)}
+        for name, mode, rtol in (("mixed_rtol1e-10", B.SOLVE_MIXED, 1e-10), ("fp64_rtol1e-12", B.SOLVE_FP64, 1e-12)):
+            solver = WeightedMassSolver(m32.coords, m32.cells, 3, n5, l5, rtol=rtol, mode=mode)
+            fwd, bwd = [], []
+            for rep in range(3):
+                z = zt.clone().requires_grad_(True)
+                bb = b5.clone().requires_grad_(True)
+                torch.cuda.synchronize()
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(st)
+                x5 = solver(z, bb)
+                loss = 0.5 * torch.sum((x5 - xs5) ** 2)
+                e1.record(st)
+                loss.backward()
+                e2.record(st)
+                torch.cuda.synchronize()
+                if rep:
+                    fwd.append(e0.elapsed_time(e1))
+                    bwd.append(e1.elapsed_time(e2))
+            grad_rows[name] = {"forward_ms": float(np.mean(fwd)), "backward_ms": float(np.mean(bwd)),
+                               "its_last_solve": solver.last[0]}
+            del solver
+        compare["weighted_solve_grad"] = grad_rows
 
     # kappa_hat = lambda_max / lambda_min of Mt^{-1} M by CG-Lanczos (FP64) on ~1e6-dof meshes:
     # uniform meshes beside the values the paper prints (Tables 1-3, diagonal / BRAS, ~5e3 dofs;
@@ -528,7 +642,7 @@ def run_ours(a):
     kb = kern[f"bras_f32_p{top['p']}"]
     roofline = {"bound": "hbm", "achieved": kb["gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": kb["gbs"] / hbm_peak, "traffic": _traffic("h1_p4_bras_f32", kb["alg_bytes"]),
-                "kernel": f"bras_apply FP32 (tcgen05 block kernel + combine), H1 p={top['p']}",
+                "kernel": f"bras_apply FP32 (tcgen05 block kernel + group combine), H1 p={top['p']}",
                 "alg_bytes_per_launch": kb["alg_bytes"], "launch_us": kb["us"], "peak_source": "measured"}
 
     # streamed path: H(curl) Nedelec k=3 on 40^3 x 6 tets, per-cell inverses FP32 / bf16
@@ -561,11 +675,19 @@ def run_ours(a):
         del c3
 
     cpu = None
+    cpu_all = None
     if not a.no_cpu_baseline:
         rate, cdetail = oracle_solve_rate((1, 2), repeats=3)
         cpu = {"value": rate, "unit": "DOF/s", "cores": 1, "kind": "oracle",
                "sample": "FP64 oracle BRAS-PCG (scipy CSR, single thread) on the same mesh at p=1,2, mean of 3",
                "detail": cdetail}
+        try:
+            rate_all, procs, t_all = oracle_all_cores_rate(2)
+            cpu_all = {"value": rate_all, "unit": "DOF/s", "cores": procs, "nproc": os.cpu_count(), "kind": "oracle",
+                       "sample": f"{procs} concurrent single-threaded FP64 oracle BRAS-PCG solves of the p=2 problem "
+                                 f"(one process per core, own RHS seeds), dofs of all / slowest solve ({t_all:.2f} s)"}
+        except Exception as ex:   # a host without spawn support: report why, keep the line
+            cpu_all = {"unavailable": str(ex)[:200]}
 
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -574,7 +696,10 @@ def run_ours(a):
                        "solver": "mixed: FP32 BRAS-PCG (FP64 dots) in FP64 refinement",
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}",
                        "detail": detail},
-            "roofline": roofline, "roofline_streamed": streamed, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_streamed": streamed, "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "true_relres_fp64": true_relres,
+            "fp64_bras_pcg": compare.get("fp64_bras"), "fp64_jacobi_pcg": compare.get("fp64_jacobi"),
             "gpu_launches": int(launches),
             "clocks": clk, "compare": compare, "kernels": kern}
     print(json.dumps(line), flush=True)

@@ -86,7 +86,11 @@ enum {
 /* Options of bras_setup.  Zero-initialise, then set what you need. */
 typedef struct {
     int precisions;      /* bit mask of (1 << BRAS_FP64 | 1 << BRAS_FP32 | 1 << BRAS_BF16);
-                            0 means all three                                           */
+                            0 means all three.  H(curl)/H(div) always keep the FP64 cell mass
+                            matrices (refinement residual, diag); their FP64 inverses only with
+                            the FP64 bit -- without it, FP64 BRAS applies and FP64 solves with
+                            BRAS return BRAS_ERR_PRECISION (the mixed solve needs only FP32 or
+                            bf16 inverses)                                                    */
     int block_elems;     /* elements per scatter block, 32..256 (H1 contexts without the
                             tensor-core kernel: 32..1024); 0 = 256                          */
     int max_nrhs;        /* largest nrhs the solve workspace is sized for; 0 = 1          */
@@ -306,9 +310,20 @@ int bras_schur_apply(const bras_ctx* ctx, int precision, const void* x, void* y,
 int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar,
                   void* stream);
 
+/* bras_grad_log_rho -- the same element gradient with respect to log-densities: for rho_K =
+ * exp(z_K) (the weights last set by bras_update_log_rho or bras_update_rho),
+ * z_bar_K = rho_bar_K * rho_K = -rho_K lambda_K^T M_K^1 x_K, in one fused element kernel.
+ * x, lam: [n_dof] double; z_bar: [n_cell] double in the caller's cell order (H1 only). */
+int bras_grad_log_rho(const bras_ctx* ctx, const double* x, const double* lam, double* z_bar,
+                      void* stream);
+
 /* bras_update_rho -- replace the element weights (H1 only): rescales the per-element
  * factors and diag(M) without rebuilding the scatter tables.  rho: [n_cell] double > 0. */
 int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream);
+
+/* bras_update_log_rho -- the same from log-densities: rho_K = exp(z_K), computed on the
+ * device.  z: [n_cell] double, finite. */
+int bras_update_log_rho(bras_ctx* ctx, const double* z, void* stream);
 
 /* Sizes of a context: n_dof, n_cell, n_loc, number of scatter blocks. */
 int bras_info(const bras_ctx* ctx, int64_t* n_dof, int64_t* n_cell, int* n_loc, int* n_blocks);

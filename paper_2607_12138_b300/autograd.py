@@ -1,10 +1,11 @@
 """Differentiable density-weighted mass solve x = M(rho)^{-1} b, rho = exp(z).
 
 M(rho) = sum_K rho_K P_K^T M_K^1 P_K (H1; the weight enters the pullback of
-Eq. piola_mass_pullbacks like det J).  Forward: one BRAS-PCG solve.  Backward, for
-xbar = dL/dx: lambda = M^{-1} xbar by a second BRAS-PCG solve (M is symmetric), so
-bbar = lambda, and rhobar_K = -lambda_K^T M_K^1 x_K from the fused element kernel of the
-library; zbar = rhobar * rho.  All numerical work runs in libbras.
+Eq. piola_mass_pullbacks like det J).  Forward: the library sets rho = exp(z) on the device
+and runs one BRAS-PCG solve.  Backward, for xbar = dL/dx: lambda = M^{-1} xbar by a second
+BRAS-PCG solve (M is symmetric), so bbar = lambda, and zbar_K = rho_K rhobar_K =
+-rho_K lambda_K^T M_K^1 x_K from the library's fused element kernel.  All numerical work runs
+in libbras; this module only marshals tensors.
 """
 from __future__ import annotations
 
@@ -26,8 +27,7 @@ class BrasMassSolve(torch.autograd.Function):
         z, x = ctx.saved_tensors
         solver = ctx.solver
         lam = solver._solve(z, xbar.contiguous().to(torch.float64))
-        rho_bar = solver.context.grad_rho(x, lam)
-        return rho_bar * torch.exp(z), lam, None
+        return solver.context.grad_log_rho(x, lam), lam, None
 
 
 class WeightedMassSolver:
@@ -39,7 +39,7 @@ class WeightedMassSolver:
         self.last = None
 
     def _solve(self, z, b):
-        self.context.update_rho(torch.exp(z.to(torch.float64)))
+        self.context.update_log_rho(z.to(torch.float64))
         x, its, rel, st = self.context.pcg_solve(b.contiguous(), pc=B.PC_BRAS, mode=self.mode, rtol=self.rtol,
                                                  maxit=self.maxit)
         if st != B.OK:

@@ -74,6 +74,10 @@ _lib.bras_grad_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.bras_grad_rho.restype = _int
 _lib.bras_update_rho.argtypes = [_vp, _vp, _vp]
 _lib.bras_update_rho.restype = _int
+_lib.bras_grad_log_rho.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.bras_grad_log_rho.restype = _int
+_lib.bras_update_log_rho.argtypes = [_vp, _vp, _vp]
+_lib.bras_update_log_rho.restype = _int
 _lib.bras_block_tuning.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), _vp, _vp]
 _lib.bras_block_tuning.restype = _int
 _lib.bras_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int), ctypes.POINTER(_int)]
@@ -226,6 +230,14 @@ def bras_grad_rho(ctx, x, lam, rho_bar, stream=None):
 
 def bras_update_rho(ctx, rho, stream=None):
     return _check(_lib.bras_update_rho(ctx, _ptr(rho), _stream(stream)), "bras_update_rho")
+
+
+def bras_grad_log_rho(ctx, x, lam, z_bar, stream=None):
+    return _check(_lib.bras_grad_log_rho(ctx, _ptr(x), _ptr(lam), _ptr(z_bar), _stream(stream)), "bras_grad_log_rho")
+
+
+def bras_update_log_rho(ctx, z, stream=None):
+    return _check(_lib.bras_update_log_rho(ctx, _ptr(z), _stream(stream)), "bras_update_log_rho")
 
 
 def bras_info(ctx):
@@ -401,6 +413,17 @@ class Context:
     def update_rho(self, rho, stream=None):
         self._rho = torch.as_tensor(rho, dtype=torch.float64, device="cuda").contiguous()
         bras_update_rho(self.ctx, self._rho, stream)
+
+    def grad_log_rho(self, x, lam, stream=None):
+        """z_bar = rho_bar * rho for the log-densities z (rho = exp(z)), computed in the library."""
+        out = torch.empty(self.n_cell, dtype=torch.float64, device=x.device)
+        bras_grad_log_rho(self.ctx, x.contiguous(), lam.contiguous(), out, stream)
+        return out
+
+    def update_log_rho(self, z, stream=None):
+        """Element weights rho = exp(z), exponentiated on the device by the library."""
+        self._rho = torch.as_tensor(z, dtype=torch.float64, device="cuda").contiguous()
+        bras_update_log_rho(self.ctx, self._rho, stream)
 
     def algorithmic_bytes(self, precision, nrhs=1, bras=True):
         return bras_algorithmic_bytes(self.ctx, precision, nrhs, bras)

@@ -369,14 +369,18 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         c->Epad = (n_cell + 31) / 32 * 32;
         const size_t cnt = (size_t)pk_groups(c->npk, 8) * 8 * c->Epad;   // whole 16-byte groups
         // FP64 tables are always built (outer residual, diag); FP32 / bf16 on request
-        if (!(c->Mpk64 = dalloc<double>(c, cnt)) || !(c->Minvpk64 = dalloc<double>(c, cnt))) return BRAS_ERR_OOM;
+        // FP64 cell matrices always (refinement residual, diag); FP64 inverses only when the FP64
+        // precision is asked for (the FP64 BRAS apply)
+        if (!(c->Mpk64 = dalloc<double>(c, cnt))) return BRAS_ERR_OOM;
+        if (want64 && !(c->Minvpk64 = dalloc<double>(c, cnt))) return BRAS_ERR_OOM;
         if (want32 || wantbf) {
             if (!(c->Mpk32 = dalloc<float>(c, cnt))) return BRAS_ERR_OOM;
         }
         if (want32 && !(c->Minvpk32 = dalloc<float>(c, cnt))) return BRAS_ERR_OOM;
         if (wantbf && !(c->Minvpkbf = dalloc<__nv_bfloat16>(c, cnt))) return BRAS_ERR_OOM;
         // zero the padding entries of the last 16-byte groups
-        if (cudaMemsetAsync(c->Mpk64, 0, cnt * 8, st) != cudaSuccess || cudaMemsetAsync(c->Minvpk64, 0, cnt * 8, st) != cudaSuccess ||
+        if (cudaMemsetAsync(c->Mpk64, 0, cnt * 8, st) != cudaSuccess ||
+            (c->Minvpk64 && cudaMemsetAsync(c->Minvpk64, 0, cnt * 8, st) != cudaSuccess) ||
             (c->Mpk32 && cudaMemsetAsync(c->Mpk32, 0, cnt * 4, st) != cudaSuccess) ||
             (c->Minvpk32 && cudaMemsetAsync(c->Minvpk32, 0, cnt * 4, st) != cudaSuccess) ||
             (c->Minvpkbf && cudaMemsetAsync(c->Minvpkbf, 0, cnt * 2, st) != cudaSuccess))
@@ -396,14 +400,15 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
         int he[2] = {0, 0};
         if (cudaMemcpy(eb, lo, sizeof(lo), cudaMemcpyHostToDevice) != cudaSuccess ||
             run_row_bound(nloc, n_cell, c->Epad, c->Mpk64, eb, st) != cudaSuccess ||
-            run_row_bound(nloc, n_cell, c->Epad, c->Minvpk64, eb + 1, st) != cudaSuccess ||
+            (c->Minvpk64 ? run_row_bound(nloc, n_cell, c->Epad, c->Minvpk64, eb + 1, st)
+                         : c->Minvpk32 ? run_row_bound(nloc, n_cell, c->Epad, c->Minvpk32, eb + 1, st)
+                                       : run_row_bound(nloc, n_cell, c->Epad, c->Minvpkbf, eb + 1, st)) != cudaSuccess ||
             cudaMemcpyAsync(he, eb, sizeof(he), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return BRAS_ERR_CUDA;
         c->er_mass = he[0] + 1;
         c->er_bras = he[1] + 1;
     }
-    (void)want64;
 
     // Block-size autotuner (opt-in): time the FP32 (else FP64) BRAS apply with the block tables
     // of every admissible size -- multiples of 32 up to 256 whose FP64 and FP32 / tensor-core
@@ -637,6 +642,9 @@ int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cuda
     return dispatch_op(c, prec, op, x, y, c->part, nrhs, st);
 }
 
+// FP64 BRAS apply available (H1 always; vector spaces built with the FP64 precision)
+bool has_fp64_bras(const bras_ctx* c) { return c->space == BRAS_H1 || c->Minvpk64 != nullptr; }
+
 bool has_precision(const bras_ctx* c, int prec) {
     if (prec == BRAS_FP64 || prec == BRAS_FP64X) return true;
     if (c->space == BRAS_H1) return prec == BRAS_FP32 || prec == BRAS_BF16;
@@ -709,7 +717,8 @@ static int apply_common(const bras_ctx* cc, int prec, int op, const void* x, voi
     set_detail(-1);
     if (!cc || !x || !y || nrhs < 1 || prec < 0 || prec > 3) return BRAS_ERR_INVALID;
     if (prec == BRAS_FP64X && op != OP_MASS) return BRAS_ERR_INVALID;
-    if (!has_precision(cc, prec)) return BRAS_ERR_PRECISION;
+    if (!has_precision(cc, prec) || (prec == BRAS_FP64 && op == OP_BRAS && !has_fp64_bras(cc)))
+        return BRAS_ERR_PRECISION;
     return run_op(const_cast<bras_ctx*>(cc), prec, op, x, y, nrhs, static_cast<cudaStream_t>(stream));
 }
 
@@ -824,6 +833,7 @@ int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision, c
     if (mode == BRAS_SOLVE_MIXED && inner_precision != BRAS_FP32 && inner_precision != BRAS_BF16)
         return BRAS_ERR_INVALID;
     if (mode == BRAS_SOLVE_MIXED && !has_precision(ctx, inner_precision)) return BRAS_ERR_PRECISION;
+    if (mode == BRAS_SOLVE_FP64 && pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
     return pcg_solve_impl(const_cast<bras_ctx*>(ctx), pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters,
                           relres, static_cast<cudaStream_t>(stream));
 }
@@ -834,6 +844,7 @@ int bras_lambda_max(const bras_ctx* ctx, int pc, const double* v0, int nrhs, int
                     void* stream) {
     set_detail(-1);
     if (!ctx || !v0 || !lambda || nrhs < 1 || iters < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
+    if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
     return lambda_max_impl(const_cast<bras_ctx*>(ctx), pc, v0, nrhs, iters, lambda, static_cast<cudaStream_t>(stream));
 }
 
@@ -841,6 +852,7 @@ int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, dou
                     int* steps_done, void* stream) {
     set_detail(-1);
     if (!ctx || !b || !lambda_min || !lambda_max || steps < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
+    if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
     return cg_lanczos_impl(const_cast<bras_ctx*>(ctx), pc, b, steps, lambda_min, lambda_max, steps_done,
                            static_cast<cudaStream_t>(stream));
 }
@@ -850,7 +862,7 @@ int bras_schur_apply(const bras_ctx* ctx, int precision, const void* x, void* y,
     if (!ctx || !x || !y || (precision != BRAS_FP64 && precision != BRAS_FP32 && precision != BRAS_BF16))
         return BRAS_ERR_INVALID;
     if (ctx->nq == 0 || (ctx->n_mesh > 1 && ctx->nseg > 0)) return BRAS_ERR_INVALID;
-    if (!has_precision(ctx, precision)) return BRAS_ERR_PRECISION;
+    if (!has_precision(ctx, precision) || (precision == BRAS_FP64 && !has_fp64_bras(ctx))) return BRAS_ERR_PRECISION;
     return schur_apply_impl(const_cast<bras_ctx*>(ctx), precision, x, y, static_cast<cudaStream_t>(stream));
 }
 
@@ -859,6 +871,7 @@ int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, con
     set_detail(-1);
     if (!ctx || !omega || !b || !x || nrhs < 1 || pc < 0 || pc > 2 || !(rtol >= 0) || maxit < 0)
         return BRAS_ERR_INVALID;
+    if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
     const int S = slots_of(ctx, nrhs);
     for (int s = 0; s < S; ++s)
         if (!(omega[s] > 0) || !std::isfinite(omega[s])) { set_detail(s); return BRAS_ERR_INVALID; }
@@ -871,6 +884,7 @@ int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const 
     set_detail(-1);
     if (!ctx || !lmin || !lmax || !b || !x || nrhs < 1 || pc < 0 || pc > 2 || !(rtol >= 0) || maxit < 0)
         return BRAS_ERR_INVALID;
+    if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
     const int S = slots_of(ctx, nrhs);
     for (int s = 0; s < S; ++s)
         if (!(lmin[s] > 0) || !(lmax[s] > lmin[s]) || !std::isfinite(lmax[s])) { set_detail(s); return BRAS_ERR_INVALID; }
@@ -881,19 +895,32 @@ int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const 
 int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar, void* stream) {
     set_detail(-1);
     if (!ctx || !x || !lam || !rho_bar || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
-    return grad_rho_launch(ctx, x, lam, rho_bar, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BRAS_OK
-                                                                                                     : BRAS_ERR_CUDA;
+    return grad_rho_launch(ctx, x, lam, rho_bar, false, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? BRAS_OK
+               : BRAS_ERR_CUDA;
 }
 
-int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream) {
+int bras_grad_log_rho(const bras_ctx* ctx, const double* x, const double* lam, double* z_bar, void* stream) {
     set_detail(-1);
-    if (!ctx || !rho || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
+    if (!ctx || !x || !lam || !z_bar || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
+    return grad_rho_launch(ctx, x, lam, z_bar, true, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? BRAS_OK
+               : BRAS_ERR_CUDA;
+}
+
+static int update_weights(bras_ctx* ctx, const double* w, bool from_log, void* stream) {
+    set_detail(-1);
+    if (!ctx || !w || ctx->space != BRAS_H1) return BRAS_ERR_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (update_rho_launch(ctx, rho, st) != cudaSuccess) return BRAS_ERR_CUDA;
+    if (update_rho_launch(ctx, w, from_log, st) != cudaSuccess) return BRAS_ERR_CUDA;
     if (run_op(ctx, BRAS_FP64, OP_DIAG, nullptr, ctx->diag64, 1, st) != BRAS_OK) return BRAS_ERR_CUDA;
     if (to_float(ctx->diag64, ctx->diag32, ctx->n, st) != cudaSuccess) return BRAS_ERR_CUDA;
     return BRAS_OK;
 }
+
+int bras_update_rho(bras_ctx* ctx, const double* rho, void* stream) { return update_weights(ctx, rho, false, stream); }
+
+int bras_update_log_rho(bras_ctx* ctx, const double* z, void* stream) { return update_weights(ctx, z, true, stream); }
 
 int bras_block_tuning(const bras_ctx* ctx, int* block_elems, int* count, int* sizes, float* apply_us) {
     set_detail(-1);

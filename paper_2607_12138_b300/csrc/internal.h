@@ -18,6 +18,7 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op);
 int dispatch_op(const bras_ctx* c, int prec, int op, const void* x, void* y, void* part, int nrhs, cudaStream_t st);
 int run_op(bras_ctx* c, int prec, int op, const void* x, void* y, int nrhs, cudaStream_t st);
 bool has_precision(const bras_ctx* c, int prec);
+bool has_fp64_bras(const bras_ctx* c);
 
 cudaError_t jacobi_launch(const bras_ctx* c, int prec, const void* x, void* y, int nrhs, cudaStream_t st);
 int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* b, double* x, int nrhs,
@@ -31,7 +32,8 @@ int cg_lanczos_impl(bras_ctx* c, int pc, const double* b, int steps, double* lmi
                     cudaStream_t st);
 
 int schur_apply_impl(bras_ctx* c, int prec, const void* x, void* y, cudaStream_t st);
-cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* lam, double* rho_bar, cudaStream_t st);
-cudaError_t update_rho_launch(bras_ctx* c, const double* rho, cudaStream_t st);
+cudaError_t grad_rho_launch(const bras_ctx* c, const double* x, const double* lam, double* rho_bar, bool wrt_log,
+                            cudaStream_t st);
+cudaError_t update_rho_launch(bras_ctx* c, const double* rho, bool from_log, cudaStream_t st);
 
 }  // namespace bras

@@ -49,7 +49,7 @@ extern "C" int bras_apply_noalloc(const bras_ctx* ctx, int precision, const void
                                   void* stream) {
     set_detail(-1);
     if (!ctx || !x || !y || nrhs < 1 || precision < 0 || precision > 2) return BRAS_ERR_INVALID;
-    if (!has_precision(ctx, precision)) return BRAS_ERR_PRECISION;
+    if (!has_precision(ctx, precision) || (precision == BRAS_FP64 && !has_fp64_bras(ctx))) return BRAS_ERR_PRECISION;
     const size_t w = precision == BRAS_FP64 ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)ctx->npart * (size_t)nrhs * w;
     if (need > kScratchBytes) {

@@ -228,7 +228,13 @@ cudaError_t run_element_inverse(int n, int64_t E, int64_t Epad, const double* Rr
 
 // Exponent bound of the largest row abs-sum of every packed symmetric cell matrix: one thread
 // per cell; *out = max over cells of E with sum_q |A_aq| < 2^E (atomicMax, *out preset).
-__global__ void k_row_bound(int n, int64_t E, int64_t Epad, const double* __restrict__ pk, int* out) {
+__device__ __forceinline__ double pk_abs(const double* pk, size_t i) { return fabs(pk[i]); }
+__device__ __forceinline__ double pk_abs(const float* pk, size_t i) { return fabs((double)pk[i]); }
+__device__ __forceinline__ double pk_abs(const __nv_bfloat16* pk, size_t i) { return fabs((double)__bfloat162float(pk[i])); }
+
+template <typename S>
+__global__ void k_row_bound(int n, int64_t E, int64_t Epad, const S* __restrict__ pk, int* out) {
+    constexpr int G = 16 / (int)sizeof(S);
     int emax = -100000;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         double best = 0.0;
@@ -236,7 +242,7 @@ __global__ void k_row_bound(int n, int64_t E, int64_t Epad, const double* __rest
             double sum = 0.0;
             for (int q = 0; q < n; ++q) {
                 const int i = a >= q ? a * (a + 1) / 2 + q : q * (q + 1) / 2 + a;
-                sum += fabs(pk[pk_index(i, e, Epad, 2)]);
+                sum += pk_abs(pk, pk_index(i, e, Epad, G));
             }
             best = fmax(best, sum);
         }
@@ -249,11 +255,15 @@ __global__ void k_row_bound(int n, int64_t E, int64_t Epad, const double* __rest
     atomicMax(out, emax);
 }
 
-cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const double* pk, int* out, cudaStream_t st) {
+template <typename S>
+cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const S* pk, int* out, cudaStream_t st) {
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((E + 255) / 256, 148 * 8));
-    k_row_bound<<<nb, 256, 0, st>>>(n, E, Epad, pk, out);
+    k_row_bound<S><<<nb, 256, 0, st>>>(n, E, Epad, pk, out);
     count_launch(1);
     return cudaGetLastError();
 }
+template cudaError_t run_row_bound<double>(int, int64_t, int64_t, const double*, int*, cudaStream_t);
+template cudaError_t run_row_bound<float>(int, int64_t, int64_t, const float*, int*, cudaStream_t);
+template cudaError_t run_row_bound<__nv_bfloat16>(int, int64_t, int64_t, const __nv_bfloat16*, int*, cudaStream_t);
 
 }  // namespace bras

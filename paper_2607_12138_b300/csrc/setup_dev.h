@@ -16,7 +16,8 @@ cudaError_t run_element_inverse(int n, int64_t E, int64_t Epad, const double* Rr
                                 __nv_bfloat16* Minvbf, unsigned long long* bad, int* nfixed,
                                 const int32_t* perm, cudaStream_t st);
 
-// *out = max(*out, exponent bound of the largest row abs-sum of the packed FP64 cell matrices)
-cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const double* pk, int* out, cudaStream_t st);
+// *out = max(*out, exponent bound of the largest row abs-sum of the packed cell matrices)
+template <typename S>
+cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const S* pk, int* out, cudaStream_t st);
 
 }  // namespace bras

@@ -193,6 +193,26 @@ def test_gradient_and_weight_update():
     assert rel_err(ctx.jacobi_apply(xt).cpu(), x / pr2.diag) <= 1e-12
 
 
+def test_log_density_weights_and_gradient():
+    """rho = exp(z) set from z on the device, and zbar = rhobar * rho from the fused element
+    kernel, against the oracle's weighted operators and adjoint gradient."""
+    mesh = cube(3, 0.1)
+    n, l2g, s = mg.dof_map(mesh, "h1", 3)
+    z = np.random.default_rng(5).normal(0, 0.5, mesh.n_cell)
+    ctx = B.Context(mesh.coords, mesh.cells, "h1", 3, n, l2g, s)
+    ctx.update_log_rho(torch.as_tensor(z, device="cuda"))
+    rho = np.exp(z)
+    pr = Problem(mesh, "h1", 3, l2g, s, n, rho)
+    x = mg.rhs(n, 1, seed=3)
+    lam = mg.rhs(n, 1, seed=4)
+    xt, lt = torch.as_tensor(x, device="cuda"), torch.as_tensor(lam, device="cuda")
+    assert rel_err(ctx.mass_apply(xt).cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.bras_apply(xt).cpu(), pr.B @ x) <= 1e-12
+    Me1 = element_matrices(mesh.coords, mesh.cells, "h1", 3)
+    zbar = ctx.grad_log_rho(xt, lt).cpu().numpy()
+    assert rel_err(zbar, ograd.rho_bar(Me1, l2g, s, x, lam) * rho) <= 1e-12
+
+
 def test_error_codes():
     mesh = cube(2)
     n, l2g, s = mg.dof_map(mesh, "h1", 2)
