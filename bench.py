@@ -457,12 +457,12 @@ def run_ours(a):
                 nk, lk, sk = mg.dof_map(m, "hdiv", k)
                 meshes.append((m.coords, m.cells, nk, lk, sk))
                 rhs.append(mg.rhs(nk, 1, seed=1000 + i))
-            cb = B.Context.batched(meshes, "hdiv", k, autotune=(k == 3), precisions=2)
+            cb = B.Context.batched(meshes, "hdiv", k, precisions=2)
             t_setup = time.perf_counter() - t0
             bt = torch.as_tensor(np.concatenate(rhs), device="cuda")
             xb = torch.empty_like(bt)
             row = {"meshes": count, "cells": int(cb.n_cell), "dofs": int(cb.n_dof), "setup_s": t_setup,
-                   "block_elems": cb.block_tuning[0], "autotuned": k == 3}
+                   "block_elems": cb.block_tuning[0]}
             for name, pc in (("mixed_bras", B.PC_BRAS), ("mixed_jacobi", B.PC_JACOBI)):
                 cb.pcg_solve(bt, pc=pc, mode=B.SOLVE_MIXED, rtol=1e-10, out=xb)
                 flush.zero_()
