@@ -28,7 +28,7 @@ def jacobians(coords: np.ndarray, cells: np.ndarray) -> np.ndarray:
 def metrics(space: str, J: np.ndarray) -> np.ndarray:
     """Pulled-back mass coefficient G_K of Eq. piola_mass_pullbacks, with |det J|."""
     det = np.abs(np.linalg.det(J))
-    if space in ("h1", "h1b"):   # Lagrange or Bernstein basis: scalar pullback
+    if space in ("h1", "h1b", "h1g"):   # Lagrange (equispaced or GLL nodes) or Bernstein: scalar pullback
         return det[:, None, None]
     if space in ("hcurl", "n2curl"):
         Jinv = np.linalg.inv(J)

@@ -13,6 +13,15 @@ keeps the oracle's inverses accurate to cond(M_ref) * 1e-16).
 Spaces (reference tetrahedron / triangle with vertices 0, e_1, .., e_d):
   * Lagrange P_p: all monomials of degree <= p; dofs = values at the equispaced nodes
     ``sum alpha_i v_i / p`` (multi-indices in ascending lexicographic order).
+  * Lagrange P_p at GLL-based nodes (space "h1g", the "spectral" nodal variant of Sec. 3):
+    dofs = values at the recursive nodes of Isaac (2020, "Recursive, parameter-free, explicitly
+    defined interpolation nodes for simplices") built on the Gauss-Lobatto-Legendre points
+    x_{n,0} < .. < x_{n,n} of [0, 1] (0, 1 and the roots of P_n'): in barycentric coordinates
+    b(alpha) = sum_i w_i E_i b(alpha without alpha_i) / sum_i w_i with w_i = x_{n, n - alpha_i},
+    n = |alpha|, E_i inserting a zero barycentric coordinate at position i, and b((n)) = (1).
+    On every edge and face the nodes are the lower-dimensional ones (so the basis is
+    conforming with the same dof map), on an edge the GLL points themselves; for p <= 2
+    they coincide with the equispaced nodes.
   * Bernstein P_p (space "h1b", the H1 "Bernstein" family of Table 1): not dualised -- the
     basis is the Bernstein polynomials B_alpha = p!/alpha! prod_i lambda_i^alpha_i themselves
     (barycentric lambda_0 = 1 - sum_c x_c, lambda_c = x_c), over the same multi-indices as
@@ -170,6 +179,70 @@ def lagrange(dim: int, p: int) -> RefElement:
     eye = [[Fraction(int(i == j)) for i in range(len(ms))] for j in range(len(ms))]
     phi = _dualise(eye, F, len(ms))
     return RefElement("h1", dim, p, p, phi, 1)
+
+
+@functools.lru_cache(maxsize=None)
+def gll_points_01(n: int) -> tuple:
+    """The n + 1 Gauss-Lobatto-Legendre points of [0, 1], ascending (40 digits): the end
+    points and the roots of the derivative of the Legendre polynomial P_n (mapped from
+    [-1, 1])."""
+    if n == 1:
+        return (mpmath.mpf(0), mpmath.mpf(1))
+    # Legendre coefficients by (k + 1) P_{k+1} = (2k + 1) x P_k - k P_{k-1}, exact rationals
+    P = [[Fraction(1)], [Fraction(0), Fraction(1)]]
+    for k in range(1, n):
+        nxt = [Fraction(0)] * (k + 2)
+        for i, c in enumerate(P[k]):
+            nxt[i + 1] += Fraction(2 * k + 1, k + 1) * c
+        for i, c in enumerate(P[k - 1]):
+            nxt[i] -= Fraction(k, k + 1) * c
+        P.append(nxt)
+    dP = [i * c for i, c in enumerate(P[n])][1:]           # ascending powers
+    with mpmath.workdps(60):
+        roots = mpmath.polyroots([to_mpf(c) for c in reversed(dP)], maxsteps=200, extraprec=200)
+        inner = sorted(mpmath.re(r) for r in roots)
+        pts = [mpmath.mpf(0)] + [(t + 1) / 2 for t in inner] + [mpmath.mpf(1)]
+    return tuple(+x for x in pts)
+
+
+def _recursive_node(alpha: tuple) -> tuple:
+    """Barycentric coordinates of the recursive GLL node of multi-index alpha (Isaac 2020)."""
+    d = len(alpha) - 1
+    n = sum(alpha)
+    if d == 0:
+        return (mpmath.mpf(1),)
+    if n == 0:                      # a degree-0 facet: its weight below is x_{n,0} = 0
+        return tuple(mpmath.mpf(1) / (d + 1) for _ in range(d + 1))
+    x = gll_points_01(n)
+    acc = [mpmath.mpf(0)] * (d + 1)
+    wsum = mpmath.mpf(0)
+    for i in range(d + 1):
+        w = x[n - alpha[i]]
+        sub = _recursive_node(alpha[:i] + alpha[i + 1:])
+        emb = sub[:i] + (mpmath.mpf(0),) + sub[i:]
+        for j in range(d + 1):
+            acc[j] += w * emb[j]
+        wsum += w
+    return tuple(a / wsum for a in acc)
+
+
+@functools.lru_cache(maxsize=None)
+def lagrange_gll(dim: int, p: int) -> RefElement:
+    ms = monomials(dim, p)
+    nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
+    V = _ref_vertices(dim)
+    F = mpmath.matrix(len(nodes), len(ms))                  # point evaluations at the GLL nodes
+    for r, a in enumerate(nodes):
+        lam = _recursive_node(a)
+        pt = [sum(lam[i] * V[i][c] for i in range(dim + 1)) for c in range(dim)]
+        for j, m in enumerate(ms):
+            val = mpmath.mpf(1)
+            for c in range(dim):
+                val *= pt[c] ** m[c]
+            F[r, j] = val
+    eye = [[Fraction(int(i == j)) for i in range(len(ms))] for j in range(len(ms))]
+    phi = _dualise(eye, F, len(ms))
+    return RefElement("h1g", dim, p, p, phi, 1)
 
 
 @functools.lru_cache(maxsize=None)
@@ -536,6 +609,8 @@ def reference_element(space: str, dim: int, order: int) -> RefElement:
         return lagrange(dim, order)
     if space == "h1b":
         return bernstein(dim, order)
+    if space == "h1g":
+        return lagrange_gll(dim, order)
     if space in ("n2curl", "bdm"):
         return second_kind(space, dim, order)
     if dim == 2 and space in ("hcurl", "hdiv"):

@@ -146,7 +146,7 @@ def h1_local_nodes(dim: int, p: int) -> list[tuple[int, ...]]:
 
 
 def n_local_dofs(space: str, dim: int, order: int) -> int:
-    if space in ("h1", "h1b"):
+    if space in ("h1", "h1b", "h1g"):
         return math.comb(order + dim, dim)
     if space in ("n2curl", "bdm"):                       # the full P_k^dim
         return dim * math.comb(order + dim, dim)
@@ -313,10 +313,11 @@ def _hcurl_hdiv_dof_map(mesh: Mesh, space: str, k: int):
 
 
 def dof_map(mesh: Mesh, space: str, order: int):
-    """Returns (n_dof, l2g [E, n_loc] int32, signs [E, n_loc] int8 or None).  "h1b"
-    (Bernstein) shares the Lagrange map: B_alpha sits on the same multi-index lattice, and
-    its trace on an entity depends only on that entity's components of alpha."""
-    if space in ("h1", "h1b"):
+    """Returns (n_dof, l2g [E, n_loc] int32, signs [E, n_loc] int8 or None).  "h1g" (Lagrange
+    at GLL-based nodes) and "h1b" (Bernstein) share the Lagrange map: their nodes / B_alpha sit
+    on the same multi-index lattice, and the trace on an entity depends only on that entity's
+    components of alpha."""
+    if space in ("h1", "h1b", "h1g"):
         return _h1_dof_map(mesh, order)
     if space in ("hcurl", "hdiv", "n2curl", "bdm"):
         return _hcurl_hdiv_dof_map(mesh, space, order)

@@ -185,6 +185,10 @@ KAPPA_MESHES = {
     "h1b_3d_p2": (lambda: mg.unit_cube_mesh(6), "h1b", 2),
     "h1b_3d_p3": (lambda: mg.unit_cube_mesh(4), "h1b", 3),
     "h1b_3d_p4": (lambda: mg.unit_cube_mesh(4), "h1b", 4),
+    "h1g_2d_p3": (lambda: mg.unit_square_mesh(12), "h1g", 3),
+    "h1g_2d_p4": (lambda: mg.unit_square_mesh(9), "h1g", 4),
+    "h1g_3d_p3": (lambda: mg.unit_cube_mesh(4), "h1g", 3),
+    "h1g_3d_p4": (lambda: mg.unit_cube_mesh(3), "h1g", 4),
     "n2curl_2d_k1": (lambda: mg.unit_square_mesh(24), "n2curl", 1),
     "n2curl_2d_k2": (lambda: mg.unit_square_mesh(16), "n2curl", 2),
     "n2curl_3d_k1": (lambda: mg.unit_cube_mesh(5), "n2curl", 1),

@@ -59,6 +59,60 @@ def test_lagrange_partition_of_unity_and_reproduction(dim, p):
     assert abs(e.mass_blocks()[0, 0].sum() - 1 / math.factorial(dim)) < 1e-12
 
 
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_gll_points_are_legendre_derivative_roots(n):
+    """The 1D family of the GLL-based nodes: end points and the roots of P_n' (numpy's Legendre
+    routines, mapped to [0, 1])."""
+    from numpy.polynomial import legendre as L
+    c = np.zeros(n + 1)
+    c[n] = 1
+    inner = np.sort(np.real(L.legroots(L.legder(c))))
+    expect = np.concatenate([[0.0], (inner + 1) / 2, [1.0]])
+    got = np.array([float(v) for v in elements.gll_points_01(n)])
+    np.testing.assert_allclose(got, expect, atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4), (3, 3), (3, 4)])
+def test_recursive_gll_nodes_restrict_to_facets(dim, p):
+    """A node with a zero barycentric index is the lower-dimensional node of its facet (the
+    property that makes the basis conforming); on an edge it is the GLL point; nodes permute
+    with their multi-indices."""
+    x = [float(v) for v in elements.gll_points_01(p)]
+    for a in itertools.product(range(p + 1), repeat=dim + 1):
+        if sum(a) != p:
+            continue
+        b = np.array([float(v) for v in elements._recursive_node(a)])
+        assert abs(b.sum() - 1) < 1e-14 and np.all(b >= -1e-15)
+        for i in range(dim + 1):
+            if a[i] == 0 and dim > 1:
+                sub = np.array([float(v) for v in elements._recursive_node(a[:i] + a[i + 1:])])
+                np.testing.assert_allclose(np.delete(b, i), sub, atol=1e-14)
+                assert abs(b[i]) < 1e-15
+        if dim == 1:
+            np.testing.assert_allclose(b, [x[a[0]], x[a[1]]], atol=1e-14)
+        for perm in itertools.permutations(range(dim + 1)):
+            bp = np.array([float(v) for v in elements._recursive_node(tuple(a[j] for j in perm))])
+            np.testing.assert_allclose(bp, b[list(perm)], atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 3), (2, 4), (3, 3), (3, 4)])
+def test_gll_lagrange_interpolates_at_its_nodes(dim, p):
+    """phi_i(node_j) = delta_ij, partition of unity, and exact interpolation of P_p."""
+    e = elements.reference_element("h1g", dim, p)
+    nodes = sorted(a for a in itertools.product(range(p + 1), repeat=dim + 1) if sum(a) == p)
+    V = np.vstack([np.zeros(dim), np.eye(dim)])
+    npts = np.array([np.array([float(v) for v in elements._recursive_node(a)]) @ V for a in nodes])
+    np.testing.assert_allclose(e.evaluate(npts)[:, :, 0], np.eye(len(nodes)), atol=1e-12)
+    rng = np.random.default_rng(3)
+    pts = rng.dirichlet(np.ones(dim + 1), size=40)[:, 1:]
+    vals = e.evaluate(pts)[:, :, 0]
+    np.testing.assert_allclose(vals.sum(axis=1), 1.0, atol=1e-12)
+    coef = rng.standard_normal(len(monomials(dim, p)))
+    np.testing.assert_allclose(vals @ (eval_monomials(dim, p, npts) @ coef), eval_monomials(dim, p, pts) @ coef,
+                               atol=1e-11)
+    assert abs(e.mass_blocks()[0, 0].sum() - 1 / math.factorial(dim)) < 1e-12
+
+
 def _bary_grads(J):
     Jinv = np.linalg.inv(J)
     return np.vstack([-Jinv.sum(axis=0), Jinv])          # row i = grad lambda_i
@@ -149,6 +203,7 @@ def test_bernstein_closed_forms(dim, p):
 
 @pytest.mark.parametrize("space,order,sort", [
     ("h1", 1, False), ("h1", 2, False), ("h1", 3, False), ("h1", 4, False), ("h1b", 3, False), ("h1b", 4, False),
+    ("h1g", 3, False), ("h1g", 4, False),
     ("hcurl", 1, False), ("hcurl", 1, True), ("hcurl", 2, True), ("hcurl", 3, True), ("hcurl", 4, True),
     ("hdiv", 1, False), ("hdiv", 1, True), ("hdiv", 2, True), ("hdiv", 3, True), ("hdiv", 4, True),
     ("hcurl", 2, False),
@@ -173,7 +228,7 @@ def test_conformity_across_shared_face(space, order, sort):
         coef = rng.standard_normal(n)
         u0 = _field(mesh, space, order, l2g, signs, coef, 0, x)
         u1 = _field(mesh, space, order, l2g, signs, coef, 1, x)
-        if space in ("h1", "h1b"):
+        if space in ("h1", "h1b", "h1g"):
             np.testing.assert_allclose(u0, u1, atol=1e-10)
         elif space in ("hcurl", "n2curl"):
             t0 = u0 - np.outer(u0 @ nrm, nrm)

@@ -62,6 +62,10 @@ ITS_MESHES = {
     "h1b_2d_p4": (lambda: mg.unit_square_mesh(48), "h1b", 4),
     "h1b_3d_p2": (lambda: mg.unit_cube_mesh(12), "h1b", 2),
     "h1b_3d_p3": (lambda: mg.unit_cube_mesh(8), "h1b", 3),
+    "h1g_2d_p3": (lambda: mg.unit_square_mesh(64), "h1g", 3),
+    "h1g_2d_p4": (lambda: mg.unit_square_mesh(48), "h1g", 4),
+    "h1g_3d_p3": (lambda: mg.unit_cube_mesh(8), "h1g", 3),
+    "h1g_3d_p4": (lambda: mg.unit_cube_mesh(6), "h1g", 4),
 }
 
 
