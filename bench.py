@@ -3,7 +3,8 @@
 
 Workload (the H1 configuration of the headline metric): unit cube, 48^3 cells x 6 Kuhn
 tetrahedra = 663,552 cells, interior vertices jittered by U(-0.15h, 0.15h) (seed 0), H1
-Lagrange p = 1, 2, 3, 4 (117,649 / 912,673 / 3,048,625 / 7,189,057 dofs), right-hand side
+Lagrange p = 1, 2, 3, 4 at the GLL-based nodes of the paper's nodal variant (117,649 / 912,673
+/ 3,048,625 / 7,189,057 dofs), right-hand side
 N(0, 1) (seed 1), u_0 = 0, stop at ||r||/||b|| <= 1e-10 (Sec. 3).  One step = one solve for
 each of the four orders with the library's fast path: BRAS-preconditioned CG in FP32 (FP64
 dot products and scalars) inside FP64 iterative refinement, the TRUE FP64 residual tested.
@@ -40,7 +41,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BRAS-PCG mass-solve DOF/s to 1e-10 rel. residual vs Jacobi-PCG; bras_apply GB/s vs HBM peak"
-WORKLOAD = "H1 Lagrange p=1,2,3,4 on 48^3x6 Kuhn tets (663,552), jitter 0.15h, 1 RHS N(0,1), rtol 1e-10"
+WORKLOAD = ("H1 Lagrange (GLL-based nodes) p=1,2,3,4 on 48^3x6 Kuhn tets (663,552), jitter 0.15h, 1 RHS N(0,1), "
+            "rtol 1e-10")
+SPACE = "h1g"   # Lagrange at the GLL-based nodes of Sec. 3 (equal to the equispaced basis for p <= 2)
 N_CELLS = 48
 JITTER = 0.15
 
@@ -93,8 +96,8 @@ def oracle_solve_rate(orders=(1, 2), repeats=3):
     mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
     tot_n, tot_t, detail = 0, 0.0, []
     for p in orders:
-        n, l2g, s = mg.dof_map(mesh, "h1", p)
-        pr = Problem(mesh, "h1", p, l2g, s, n)
+        n, l2g, s = mg.dof_map(mesh, SPACE, p)
+        pr = Problem(mesh, SPACE, p, l2g, s, n)
         b = mg.rhs(n, 1, seed=1)
         ts = []
         for _ in range(repeats):
@@ -116,8 +119,8 @@ def _oracle_worker(args):
     from oracle.solvers import pcg
     from paper_2607_12138_b300 import meshgen as mg
     mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
-    n, l2g, s = mg.dof_map(mesh, "h1", p)
-    pr = Problem(mesh, "h1", p, l2g, s, n)
+    n, l2g, s = mg.dof_map(mesh, SPACE, p)
+    pr = Problem(mesh, SPACE, p, l2g, s, n)
     b = mg.rhs(n, 1, seed=seed)
     barrier.wait()
     t0 = time.perf_counter()
@@ -254,8 +257,8 @@ def run_ours(a):
     mesh = mg.unit_cube_mesh(N_CELLS, jitter=JITTER, seed=0)
     probs = []
     for p in orders:
-        n, l2g, s = mg.dof_map(mesh, "h1", p)
-        ctx = B.Context(mesh.coords, mesh.cells, "h1", p, n, l2g, s, autotune=True)   # setup: untimed
+        n, l2g, s = mg.dof_map(mesh, SPACE, p)
+        ctx = B.Context(mesh.coords, mesh.cells, SPACE, p, n, l2g, s, autotune=True)   # setup: untimed
         b = torch.as_tensor(mg.rhs(n, 1, seed=1), device="cuda")
         x = torch.empty_like(b)
         bh = b.cpu().pin_memory()
@@ -368,7 +371,7 @@ def run_ours(a):
                 continue
             R = 32
             n = pr["n"]
-            ctxR = B.Context(mesh.coords, mesh.cells, "h1", pr["p"], n, pr["l2g"], None, max_nrhs=R)
+            ctxR = B.Context(mesh.coords, mesh.cells, SPACE, pr["p"], n, pr["l2g"], None, max_nrhs=R)
             bR = torch.as_tensor(mg.rhs(n, R, seed=1), device="cuda")
             xR = torch.empty_like(bR)
             ctxR.pcg_solve(bR, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10, out=xR)
@@ -516,13 +519,13 @@ def run_ours(a):
     if not a.no_compare:
         from paper_2607_12138_b300.autograd import WeightedMassSolver
         m32 = mg.unit_cube_mesh(32, jitter=JITTER, seed=0)
-        n5, l5, _ = mg.dof_map(m32, "h1", 3)
+        n5, l5, _ = mg.dof_map(m32, SPACE, 3)
         zt = torch.as_tensor(np.random.default_rng(2).normal(0, 0.5, m32.n_cell), device="cuda")
         b5 = torch.as_tensor(mg.rhs(n5, 1, seed=1), device="cuda")
         xs5 = torch.as_tensor(mg.rhs(n5, 1, seed=3), device="cuda")
         grad_rows = {"dofs": n5, "cells": int(m32.n_cell)}
         for name, mode, rtol in (("mixed_rtol1e-10", B.SOLVE_MIXED, 1e-10), ("fp64_rtol1e-12", B.SOLVE_FP64, 1e-12)):
-            solver = WeightedMassSolver(m32.coords, m32.cells, 3, n5, l5, rtol=rtol, mode=mode)
+            solver = WeightedMassSolver(m32.coords, m32.cells, 3, n5, l5, rtol=rtol, mode=mode, space=SPACE)
             fwd, bwd = [], []
             for rep in range(3):
                 z = zt.clone().requires_grad_(True)
@@ -558,6 +561,8 @@ def run_ours(a):
             return out
         cases = (("h1_3d_p1", "h1", 1, 96, (5.0, 1.8), "Table 1, 3D, p=1, Lagrange"),
                  ("h1_3d_p2", "h1", 2, 48, (17, 3.0), "Table 1, 3D, p=2, Lagrange"),
+                 ("h1g_3d_p3", "h1g", 3, 32, (13, 2.9), "Table 1, 3D, p=3, Lagrange (GLL-based nodes)"),
+                 ("h1g_3d_p4", "h1g", 4, 24, (22, 3.5), "Table 1, 3D, p=4, Lagrange (GLL-based nodes)"),
                  ("h1b_3d_p2", "h1b", 2, 48, (24, 4.9), "Table 1, 3D, p=2, Bernstein"),
                  ("h1b_3d_p3", "h1b", 3, 32, (98, 7.8), "Table 1, 3D, p=3, Bernstein"),
                  ("h1b_3d_p4", "h1b", 4, 24, (420, 11), "Table 1, 3D, p=4, Bernstein"),

@@ -20,7 +20,8 @@
  *    bras_pcg_solve synchronise the stream before they return.
  *  * Vectors with nrhs > 1 right-hand sides are RHS-interleaved: entry (i, r) is at
  *    i * nrhs + r.  Dof i is the global dof number used in `l2g`.
- *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (or Bernstein, bras_options.basis) P_p
+ *  * Element kinds (Sec. 3): BRAS_H1 = Lagrange (equispaced or GLL-based nodes, or Bernstein;
+ *    bras_options.basis) P_p
  *    on triangles (dim 2) or tetrahedra (dim 3), p = 1..4; BRAS_HCURL = Nedelec first kind
  *    and BRAS_HDIV = Raviart-Thomas, order k = 1..4, or with bras_options.basis = 1 the
  *    second kinds N2curl and BDM (the full P_k^dim, k = 1..4; Tables 2-3), on triangles or
@@ -98,7 +99,10 @@ typedef struct {
                             (3xTF32 tcgen05) local GEMM; 0 = tensor cores where supported  */
     int basis;           /* BRAS_H1: 0 = Lagrange (values at the equispaced nodes),
                             1 = Bernstein (B_alpha = p!/alpha! prod lambda_i^alpha_i, the
-                            "Bernstein" family of Table 1); same multi-indices, same l2g.
+                            "Bernstein" family of Table 1), 2 = Lagrange at GLL-based nodes
+                            (the recursive nodes of Isaac (2020) on the Gauss-Lobatto-Legendre
+                            points: the "spectral" nodal variant of Sec. 3, Table 1's Lagrange
+                            column; equal to 0 for p <= 2); same multi-indices, same l2g.
                             BRAS_HCURL / BRAS_HDIV: 0 = first kind (N1curl_k / RT_k),
                             1 = second kind (N2curl_k / BDM_k, k = 1..4)                  */
     int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for eight cell

@@ -33,8 +33,8 @@ class BrasMassSolve(torch.autograd.Function):
 class WeightedMassSolver:
     """Holds one H1 context; ``__call__(z, b)`` is differentiable in z and b."""
 
-    def __init__(self, coords, cells, order, n_dof, l2g, rtol=1e-12, mode=B.SOLVE_FP64, maxit=5000):
-        self.context = B.Context(coords, cells, "h1", order, n_dof, l2g)
+    def __init__(self, coords, cells, order, n_dof, l2g, rtol=1e-12, mode=B.SOLVE_FP64, maxit=5000, space="h1"):
+        self.context = B.Context(coords, cells, space, order, n_dof, l2g)
         self.rtol, self.mode, self.maxit = rtol, mode, maxit
         self.last = None
 

@@ -28,9 +28,10 @@ H1, HCURL, HDIV = 0, 1, 2
 FP64, FP32, BF16, FP64X = 0, 1, 2, 3
 PC_NONE, PC_JACOBI, PC_BRAS = 0, 1, 2
 SOLVE_FP64, SOLVE_MIXED = 0, 1
-# h1b: H1 with the Bernstein basis; n2curl / bdm: the second-kind H(curl) / H(div) families
-SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV, "h1b": H1, "n2curl": HCURL, "bdm": HDIV}
-BASIS = {"h1b": 1, "n2curl": 1, "bdm": 1}
+# h1b: H1 with the Bernstein basis; h1g: H1 Lagrange at GLL-based nodes (the paper's nodal
+# variant); n2curl / bdm: the second-kind H(curl) / H(div) families
+SPACES = {"h1": H1, "hcurl": HCURL, "hdiv": HDIV, "h1b": H1, "h1g": H1, "n2curl": HCURL, "bdm": HDIV}
+BASIS = {"h1b": 1, "n2curl": 1, "bdm": 1, "h1g": 2}
 
 OK, NOT_CONVERGED = 0, 1
 ERR = {-1: "INVALID", -2: "L2G_RANGE", -3: "NO_COPY", -4: "DEGENERATE", -5: "NOT_SPD", -6: "CUDA",

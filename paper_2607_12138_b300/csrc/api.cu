@@ -175,7 +175,7 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
                int64_t n_cell, const int32_t* cells, int64_t n_dof, const int32_t* l2g, const int8_t* signs,
                const double* rho, const bras_options* opt, cudaStream_t st, const int32_t* cell_group = nullptr) {
     const int basis = opt ? opt->basis : 0;
-    if (basis < 0 || basis > 1) return BRAS_ERR_INVALID;
+    if (basis < 0 || basis > 2) return BRAS_ERR_INVALID;   // n_local rejects the pairs that do not exist
     const int nloc = n_local(dim, space, order, basis);
     c->dim = dim;
     c->space = space;

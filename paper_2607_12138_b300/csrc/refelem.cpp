@@ -11,6 +11,9 @@
 //   * integrals by collapsed (Duffy) tensor Gauss-Legendre rules, exact for the degrees used;
 //   * Lagrange: Silvester's product form of the nodal basis in barycentric coordinates,
 //     phi_alpha = prod_i prod_{m < alpha_i} (p lambda_i - m) / (m + 1);
+//   * Lagrange at GLL-based nodes (the spectral nodal variant of Sec. 3): the recursive nodes
+//     of Isaac (2020) on the Gauss-Lobatto-Legendre points of [0, 1] (Newton iterations on
+//     P_n'), the nodal basis by a long-double inverse of the monomial Vandermonde matrix;
 //   * Nedelec / Raviart-Thomas: the Arnold-Falk-Winther geometric bases of P_k^- Lambda^1
 //     and P_k^- Lambda^2 (lambda^alpha times Whitney forms, alpha_m = 0 below the first
 //     vertex of the form) as a spanning basis, dualised against the documented dof
@@ -135,6 +138,112 @@ int build_lagrange(int dim, int p, RefTables* out) {
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) out->R[(size_t)i * n + j] += q.w * phi[i] * phi[j];
     }
+    return 0;
+}
+
+// ---- Lagrange at GLL-based nodes --------------------------------------------------------
+// n + 1 Gauss-Lobatto-Legendre points of [0, 1], ascending: the end points and the roots of
+// P_n', found by Newton's method from the Chebyshev-Gauss-Lobatto points, with P_n and P_n'
+// from the three-term recurrence and P_n'' from Legendre's equation.
+std::vector<long double> gll_points01(int n) {
+    std::vector<long double> x(n + 1);
+    x[0] = 0;
+    x[n] = 1;
+    for (int j = 1; j < n; ++j) {
+        long double t = -std::cos(M_PI * (long double)j / n);
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = t;   // P_{k-1}, P_k
+            for (int k = 1; k < n; ++k) {
+                const long double p2 = ((2 * k + 1) * t * p1 - k * p0) / (k + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            const long double dp = n * (t * p1 - p0) / (t * t - 1);              // P_n'
+            const long double d2p = (2 * t * dp - n * (n + 1) * p1) / (1 - t * t);  // P_n''
+            const long double step = dp / d2p;
+            t -= step;
+            if (std::fabs(step) < 1e-19L) break;
+        }
+        x[j] = (t + 1) / 2;
+    }
+    return x;
+}
+
+// Barycentric coordinates of the recursive node of multi-index a: the weighted mean of the
+// facet nodes b(a without a_i) embedded with a zero at position i, weights x_{n, n - a_i}
+// (n = |a|); one coordinate 1 for a single index.
+std::vector<long double> recursive_node(const std::vector<int>& a) {
+    const int d = (int)a.size() - 1;
+    int n = 0;
+    for (int v : a) n += v;
+    if (d == 0) return {1.0L};
+    if (n == 0) return std::vector<long double>(d + 1, 1.0L / (d + 1));   // weight 0 below
+    const std::vector<long double> x = gll_points01(n);
+    std::vector<long double> acc(d + 1, 0.0L);
+    long double wsum = 0;
+    for (int i = 0; i <= d; ++i) {
+        std::vector<int> sub;
+        for (int j = 0; j <= d; ++j)
+            if (j != i) sub.push_back(a[j]);
+        const std::vector<long double> bs = recursive_node(sub);
+        const long double w = x[n - a[i]];
+        for (int j = 0, k = 0; j <= d; ++j) acc[j] += w * (j == i ? 0.0L : bs[k++]);
+        wsum += w;
+    }
+    for (auto& v : acc) v /= wsum;
+    return acc;
+}
+
+bool lu_inverse(std::vector<long double> A, int n, std::vector<long double>& inv);
+
+int build_lagrange_gll(int dim, int p, RefTables* out) {
+    std::vector<std::vector<int>> nodes;
+    compositions(dim + 1, p, nodes);             // ascending lexicographic, as the equispaced nodes
+    const int n = (int)nodes.size();
+    // monomials x^a y^b z^c of total degree <= p
+    std::vector<std::array<int, 3>> mono;
+    for (int a = 0; a <= p; ++a)
+        for (int b = 0; b + a <= p; ++b)
+            for (int c = 0; c + a + b <= p; ++c)
+                if (dim == 3 || c == 0) mono.push_back({a, b, c});
+    if ((int)mono.size() != n) return -1;
+    auto eval_mono = [&](const long double* x, std::vector<long double>& m) {
+        m.resize(n);
+        for (int j = 0; j < n; ++j) {
+            long double v = 1;
+            for (int c = 0; c < dim; ++c)
+                for (int e = 0; e < mono[j][c]; ++e) v *= x[c];
+            m[j] = v;
+        }
+    };
+    // Vandermonde V[i][j] = m_j(node_i); the nodal basis phi_i = sum_j m_j C[j][i], C = V^{-1}
+    std::vector<long double> V((size_t)n * n), C, m;
+    for (int i = 0; i < n; ++i) {
+        const std::vector<long double> lam = recursive_node(nodes[i]);
+        long double x[3] = {0, 0, 0};
+        for (int c = 0; c < dim; ++c) x[c] = lam[c + 1];   // vertices 0, e_1, .., e_d
+        eval_mono(x, m);
+        for (int j = 0; j < n; ++j) V[(size_t)i * n + j] = m[j];
+    }
+    if (!lu_inverse(V, n, C)) return -1;
+    auto rule = dim == 3 ? tet_rule() : triangle_rule();
+    out->nloc = n;
+    out->ncomp = 1;
+    out->R.assign((size_t)n * n, 0.0);
+    std::vector<long double> phi(n);
+    std::vector<long double> acc((size_t)n * n, 0.0L);
+    for (const QP& q : rule) {
+        const long double x[3] = {q.x[0], q.x[1], q.x[2]};
+        eval_mono(x, m);
+        for (int i = 0; i < n; ++i) {
+            long double v = 0;
+            for (int j = 0; j < n; ++j) v += m[j] * C[(size_t)j * n + i];
+            phi[i] = v;
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) acc[(size_t)i * n + j] += (long double)q.w * phi[i] * phi[j];
+    }
+    for (size_t i = 0; i < acc.size(); ++i) out->R[i] = (double)acc[i];
     return 0;
 }
 
@@ -770,6 +879,7 @@ int build_second_kind(int dim, bool curl, int k, RefTables* out) {
 }  // namespace
 
 int n_local(int dim, int space, int order, int basis) {
+    if (basis < 0 || basis > 2 || (space != 0 && basis == 2)) return -1;
     if (space != 0 && basis == 1) {   // N2curl_k / BDM_k: the full P_k^dim, k = 1..4
         if (order < 1 || order > 4 || (dim != 2 && dim != 3)) return -1;
         return dim == 2 ? (order + 1) * (order + 2) : (order + 1) * (order + 2) * (order + 3) / 2;
@@ -822,7 +932,11 @@ int build_reference(int dim, int space, int order, RefTables* out, int basis) {
     out->dim = dim;
     out->space = space;
     out->order = order;
-    if (space == 0) return basis == 1 ? build_bernstein(dim, order, out) : build_lagrange(dim, order, out);
+    if (space == 0) {
+        if (basis == 1) return build_bernstein(dim, order, out);
+        if (basis == 2) return build_lagrange_gll(dim, order, out);
+        return build_lagrange(dim, order, out);
+    }
     if (basis == 1) return build_second_kind(dim, space == 1, order, out);
     if (dim == 2) return build_vector_2d(space == 1, order, out);
     return build_vector(space == 1, order, out);

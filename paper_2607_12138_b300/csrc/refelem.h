@@ -15,8 +15,8 @@ struct RefTables {
     std::vector<double> Bdiv;
 };
 
-// basis: H1 0 = Lagrange (equispaced nodes), 1 = Bernstein; H(curl) / H(div) 0 = first kind
-// (N1curl_k / RT_k), 1 = second kind (N2curl_k / BDM_k).
+// basis: H1 0 = Lagrange (equispaced nodes), 1 = Bernstein, 2 = Lagrange at GLL-based nodes;
+// H(curl) / H(div) 0 = first kind (N1curl_k / RT_k), 1 = second kind (N2curl_k / BDM_k).
 int n_local(int dim, int space, int order, int basis = 0);
 int build_reference(int dim, int space, int order, RefTables* out, int basis = 0);
 

@@ -47,6 +47,9 @@ SMALL_CASES = {
     "2d_p4_bern": (lambda: square(13), "h1b", 4),        # Bernstein basis (Table 1)
     "3d_p3_bern": (lambda: cube(5), "h1b", 3),
     "3d_p4_bern": (lambda: cube(5), "h1b", 4),
+    "2d_p4_gll": (lambda: square(13), "h1g", 4),         # Lagrange at GLL-based nodes (Table 1)
+    "3d_p3_gll": (lambda: cube(5), "h1g", 3),
+    "3d_p4_gll": (lambda: cube(5), "h1g", 4),
 }
 
 

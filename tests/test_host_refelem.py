@@ -18,7 +18,8 @@ from oracle.schur import reference_divergence
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2607_12138_b300", "csrc")
-SPACE = {"h1": (0, 0), "h1b": (0, 1), "hcurl": (1, 0), "hdiv": (2, 0), "n2curl": (1, 1), "bdm": (2, 1)}
+SPACE = {"h1": (0, 0), "h1b": (0, 1), "h1g": (0, 2), "hcurl": (1, 0), "hdiv": (2, 0), "n2curl": (1, 1),
+         "bdm": (2, 1)}
 
 
 @pytest.fixture(scope="module")
@@ -48,6 +49,7 @@ def library_tables(exe, tmp, dim, space, order):
 
 
 FAMILIES = ([("h1", d, p) for d in (2, 3) for p in (1, 2, 3, 4)] + [("h1b", d, p) for d in (2, 3) for p in (2, 4)]
+            + [("h1g", d, p) for d in (2, 3) for p in (3, 4)]
             + [(s, d, k) for s in ("hcurl", "hdiv") for d in (2, 3) for k in (1, 2, 3, 4)]
             + [(s, d, k) for s in ("n2curl", "bdm") for d in (2, 3) for k in (1, 2, 3, 4)])
 
