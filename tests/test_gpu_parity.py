@@ -3,9 +3,11 @@
 Tolerances (max-abs error / max-abs of the oracle result):
   * FP64 applies: 1e-12 (the FP64 target); both sides round the same exact operator, so
     they differ by about cond(M_K) * 1e-16.
-  * FP32 applies: 2e-5 for H1, 1e-4 for H(curl)/H(div) (FP32 storage of local inverses
-    with cond up to ~1e4 and sums of up to 45 terms, each rounded at 6e-8).
-  * bf16-stored inverses: 2e-2 (8-bit mantissa, 4e-3 per entry, plus the SPD repair shift).
+  * FP32 applies: 2e-6 for every family (measured at most 5.7e-7 over every case of the
+    suite, max-abs over max-abs: FP32 local matrices and products, ~6e-8 per rounding, over
+    up to 105 terms; the in-block dof sums are exact, see the block kernels).
+  * bf16-stored inverses: 1e-2 (measured at most 3.2e-3; per entry the median is ~1e-3 and
+    the 99th percentile ~3e-2 on small entries: an 8-bit mantissa, 4e-3 per stored entry).
 Solves are checked by iteration count (oracle +-1) and by the oracle's own FP64 residual of
 the GPU solution (<= the requested 1e-10).
 """
@@ -44,7 +46,8 @@ def _vec(n, nrhs=1, seed=5, dtype=torch.float64):
     return x, torch.as_tensor(x, dtype=dtype, device="cuda")
 
 
-TOL32 = {"h1": 2e-5, "h1b": 2e-5, "h1g": 2e-5, "hcurl": 1e-4, "hdiv": 1e-4, "n2curl": 1e-4, "bdm": 1e-4}
+TOL32 = {"h1": 2e-6, "h1b": 2e-6, "h1g": 2e-6, "hcurl": 2e-6, "hdiv": 2e-6, "n2curl": 2e-6, "bdm": 2e-6}
+TOL16 = 1e-2   # bf16-stored inverses of H(curl) / H(div)
 
 
 @pytest.mark.parametrize("case", sorted(SMALL_CASES))
@@ -66,7 +69,7 @@ def test_fp32_and_bf16_applies(case):
     assert rel_err(ctx.mass_apply(xt, B.FP32).cpu(), pr.M @ x) <= TOL32[space]
     assert rel_err(ctx.bras_apply(xt, B.FP32).cpu(), pr.B @ x) <= TOL32[space]
     assert rel_err(ctx.jacobi_apply(xt, B.FP32).cpu(), x / pr.diag) <= 1e-6
-    assert rel_err(ctx.bras_apply(xt, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space not in ("h1", "h1b", "h1g") else TOL32[space])
+    assert rel_err(ctx.bras_apply(xt, B.BF16).cpu(), pr.B @ x) <= (TOL16 if space not in ("h1", "h1b", "h1g") else TOL32[space])
 
 
 @pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "hdiv1_signed", "c1_2d_p2", "3d_p3", "3d_p4", "hcurl3", "hdiv3",
@@ -87,7 +90,7 @@ def test_multi_rhs_interleaved(case, nrhs):
     yb32, ym32 = ctx.bras_apply(x32, B.FP32), ctx.mass_apply(x32, B.FP32)
     assert rel_err(yb32.cpu(), pr.B @ x) <= TOL32[space]
     assert rel_err(ym32.cpu(), pr.M @ x) <= TOL32[space]
-    assert rel_err(ctx.bras_apply(x32, B.BF16).cpu(), pr.B @ x) <= (2e-2 if space not in ("h1", "h1b", "h1g") else TOL32[space])
+    assert rel_err(ctx.bras_apply(x32, B.BF16).cpu(), pr.B @ x) <= (TOL16 if space not in ("h1", "h1b", "h1g") else TOL32[space])
     for r in (0, nrhs - 1):
         col = xt[:, r].contiguous()
         assert rel_err(yb[:, r].cpu(), ctx.bras_apply(col).cpu()) <= 1e-15
@@ -278,7 +281,7 @@ def test_full_size_sampled_parity(key):
     assert rel_err(y32, ob) <= TOL32[space]
     if space not in ("h1", "h1g"):   # bf16-stored inverses of the streamed spaces
         y16 = ctx.bras_apply(xt.float(), B.BF16).cpu().numpy()[dofs]
-        assert rel_err(y16, ob) <= 2e-2
+        assert rel_err(y16, ob) <= TOL16
 
 
 def test_full_size_multi_rhs_sampled_parity():
@@ -403,26 +406,25 @@ def test_tensor_core_vs_simt_fp32(case):
     for op, ref in (("bras_apply", pr.B @ x), ("mass_apply", pr.M @ x)):
         a = getattr(tc, op)(xt, B.FP32).cpu()
         s = getattr(simt, op)(xt, B.FP32).cpu()
-        assert rel_err(a, ref) <= 2e-5 and rel_err(s, ref) <= 2e-5
-        assert rel_err(a, s) <= 2e-5
+        assert rel_err(a, ref) <= TOL32[space] and rel_err(s, ref) <= TOL32[space]
+        assert rel_err(a, s) <= 2 * TOL32[space]
 
 
 @pytest.mark.parametrize("case", ["3d_p3", "3d_p4"])
 @pytest.mark.parametrize("block_elems", [64, 128, 160, 256])
 def test_tensor_core_block_variants(case, block_elems):
     """The tensor-core kernel's launch variants on 750 tets: blocks of <= 128 cells (two threads
-    per cell, one TMEM tile, products over the block tables), 160 (one thread per cell, own
-    product buffer) and 256 (at p = 4 the products overwrite the tables); one and four
-    right-hand sides."""
+    per cell, one TMEM tile, four CTAs per SM), 160 and 256 (one thread per cell, two tiles);
+    one and four (multi-RHS kernel) right-hand sides."""
     mesh, space, order, n, l2g, signs = build(case)
     pr = Problem(mesh, space, order, l2g, signs, n)
     ctx = B.Context(mesh.coords, mesh.cells, space, order, n, l2g, signs, block_elems=block_elems, max_nrhs=4)
     x, xt = _vec(n, dtype=torch.float32)
     for op, ref in (("bras_apply", pr.B @ x), ("mass_apply", pr.M @ x)):
-        assert rel_err(getattr(ctx, op)(xt, B.FP32).cpu(), ref) <= 2e-5
+        assert rel_err(getattr(ctx, op)(xt, B.FP32).cpu(), ref) <= TOL32[space]
     x4, xt4 = _vec(n, nrhs=4, seed=9, dtype=torch.float32)
     y4 = ctx.bras_apply(xt4, B.FP32).cpu().numpy().reshape(n, 4)
-    assert rel_err(y4, pr.B @ x4.reshape(n, 4)) <= 2e-5
+    assert rel_err(y4, pr.B @ x4.reshape(n, 4)) <= TOL32[space]
 
 
 @pytest.mark.parametrize("case", ["3d_p2", "hcurl2", "c1_2d_p2", "3d_p4", "hdiv1_signed"])
