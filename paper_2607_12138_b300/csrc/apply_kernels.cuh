@@ -550,16 +550,18 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     }
                 }
             } else {
-                // all of this thread's loads in flight at once (up to 16 per pass)
-                for (int u = tid; u < nu; u += 16 * blockDim.x) {
-                    T v[16];
+                // several loads in flight per thread and pass: 16 for the streamed spaces (many
+                // dofs a thread), 4 for H1 (about one to four dofs a thread)
+                constexpr int UX = KIND == KIND_H1 ? 4 : 16;
+                for (int u = tid; u < nu; u += UX * blockDim.x) {
+                    T v[UX];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
+                    for (int k = 0; k < UX; ++k) {
                         const int uu = u + k * blockDim.x;
                         v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : T(0);
                     }
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
+                    for (int k = 0; k < UX; ++k) {
                         const int uu = u + k * blockDim.x;
                         if (uu < nu) {
                             const T w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];

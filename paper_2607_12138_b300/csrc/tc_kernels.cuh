@@ -237,16 +237,17 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
                 }
             }
         } else {
-            // all of this thread's loads in flight at once (up to 16 per pass)
-            for (int u = tid; u < nu; u += 16 * blockDim.x) {
-                float v[16];
+            // up to 8 loads in flight per thread and pass (blocks of <= 256 cells stage ~8 dofs a
+            // thread: a deeper unroll only adds predicated-off slots)
+            for (int u = tid; u < nu; u += 8 * blockDim.x) {
+                float v[8];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     const int uu = u + k * blockDim.x;
                     v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : 0.f;
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     const int uu = u + k * blockDim.x;
                     if (uu < nu) {
                         const float w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
