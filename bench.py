@@ -306,9 +306,10 @@ def run_ours(a):
         step()
     total_n = sum(pr["n"] for pr in probs)
     clocks = Clocks(local)
-    launches0 = B._lib.bras_kernel_launches()
+    launches0, graphs0 = B.kernel_launches(), B.graph_launches()
     ts, res = timed(step, a.steps)
-    launches = B._lib.bras_kernel_launches() - launches0
+    launches = B.kernel_launches() - launches0
+    graphs = B.graph_launches() - graphs0
     clk = clocks.stop()
     t_step = float(np.mean(ts))
     t_max = max_over_ranks(t_step, ws, "cuda")
@@ -706,6 +707,8 @@ def run_ours(a):
             "true_relres_fp64": true_relres,
             "fp64_bras_pcg": compare.get("fp64_bras"), "fp64_jacobi_pcg": compare.get("fp64_jacobi"),
             "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / a.steps,
+            "solve_graph_launches_per_step": graphs / a.steps, "solves_per_step": len(probs),
             "clocks": clk, "compare": compare, "kernels": kern}
     print(json.dumps(line), flush=True)
     return 0

@@ -350,6 +350,11 @@ int64_t bras_last_error_detail(void);
  * threads); a host-side counter for launch accounting. */
 int64_t bras_kernel_launches(void);
 
+/* Number of CUDA graph launches this library has made since it was loaded (one per solve
+ * that runs as a graph: bras_pcg_solve in either mode, the stationary solvers); the kernels
+ * such a graph runs are counted by bras_kernel_launches. */
+int64_t bras_graph_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,20 @@ _lib.bras_status_string.argtypes = [_int]
 _lib.bras_status_string.restype = ctypes.c_char_p
 _lib.bras_last_error_detail.argtypes = []
 _lib.bras_last_error_detail.restype = _i64
+_lib.bras_kernel_launches.argtypes = []
+_lib.bras_kernel_launches.restype = _i64
+_lib.bras_graph_launches.argtypes = []
+_lib.bras_graph_launches.restype = _i64
+
+
+def kernel_launches() -> int:
+    """CUDA kernels the library has launched since it was loaded (graph-run kernels included)."""
+    return int(_lib.bras_kernel_launches())
+
+
+def graph_launches() -> int:
+    """CUDA graph launches the library has made since it was loaded (one per graph-run solve)."""
+    return int(_lib.bras_graph_launches())
 
 
 def header_functions() -> list[str]:

@@ -19,9 +19,11 @@ namespace bras {
 
 thread_local int64_t g_detail = -1;
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_graph_launches{0};
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void count_graph_launch() { g_graph_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_detail(int64_t d) { g_detail = d; }
 
@@ -137,12 +139,17 @@ int install_tables(bras_ctx* c, const HostTables& t) {
     c->U_tot = t.U_tot;
     c->npart = t.npart;
     c->nsh = t.nsh;
-    {   // at most 2^h copies of a dof in a block: low words of fx_lo = 31 - h bits (sums below
-        // 2^31), products below 2^fx_top with fx_top = 60 - 2h (high-word sums below 2^29 + 2^h)
+    {   // at most 2^h copies of a dof in a block.  FP32 / bf16: parts of L = min(22, 30 - h)
+        // bits (|ql| <= 2^(L-1): sums below 2^29), products below 2^fx_top with fx_top =
+        // min(L + 21, 31 + L - h) (|qh| < 2^21 for the FP32 rounding, high sums below 2^31).
+        // Float-float mass: low words of 31 - h bits, fx_top = 60 - 2h.  FP64: 61 - h.
         int h = 0;
         while ((1 << h) < t.max_copies) ++h;
-        c->fx_lo = 31 - h;
-        c->fx_top = 60 - 2 * h;
+        if (h > 20) return BRAS_ERR_TOO_LARGE;
+        c->fx_lo = std::min(22, 30 - h);
+        c->fx_top = std::min(c->fx_lo + 21, 31 + c->fx_lo - h);
+        c->fx_lo_df = 31 - h;
+        c->fx_top_df = 60 - 2 * h;
         c->fx_top64 = 61 - h;
     }
     c->ngrp = (int64_t)t.grp_size.size();
@@ -568,8 +575,9 @@ int ensure_part(bras_ctx* c, int nrhs) {
 
 LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     // FP64 kernels accumulate in one 64-bit word per dof; FP32, bf16 and the H1 float-float mass
-    // apply (BRAS_FP64X) in two 32-bit words
-    const bool acc64 = prec == BRAS_FP64 || (prec == BRAS_FP64X && !(c->space == BRAS_H1 && op == OP_MASS));
+    // apply (BRAS_FP64X) in two 32-bit words, with their own splits
+    const bool df = prec == BRAS_FP64X && c->space == BRAS_H1 && op == OP_MASS;
+    const bool acc64 = prec == BRAS_FP64 || (prec == BRAS_FP64X && !df);
     if (prec == BRAS_FP64X) prec = BRAS_FP64;
     LaunchCommon L{};
     BlockArgs& A = L.A;
@@ -585,8 +593,8 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.max_u = c->max_u;
     A.max_ne = c->max_ne;
     A.max_pkt = c->max_pkt;
-    A.fx_top = acc64 ? c->fx_top64 : c->fx_top;
-    A.fx_lo = acc64 ? 0 : c->fx_lo;
+    A.fx_top = acc64 ? c->fx_top64 : df ? c->fx_top_df : c->fx_top;
+    A.fx_lo = acc64 ? 0 : df ? c->fx_lo_df : c->fx_lo;
     A.fx_er = op == OP_BRAS ? c->er_bras : c->er_mass;
     const bool f64 = prec == BRAS_FP64;
     if (c->space == BRAS_H1) {
@@ -986,5 +994,6 @@ const char* bras_status_string(int code) {
 int64_t bras_last_error_detail(void) { return g_detail; }
 
 int64_t bras_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+int64_t bras_graph_launches(void) { return g_graph_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -20,9 +20,9 @@
 //      are exact, so the total does not depend on the order in which copies arrive; dofs with
 //      all copies in the block are final (times 1/d for BRAS, the left D^{-1}), the others
 //      leave a partial sum;
-//   4. k_group_combine walks the groups of shared dofs (dofs whose copies lie in the same set
-//      of blocks), one warp per group, and adds each dof's partials up in ascending block
-//      order (times 1/d for BRAS).
+//   4. k_group_combine finishes the shared dofs, grouped by the set of blocks that hold their
+//      copies: one thread per (shared dof, right-hand side) adds the dof's partials up in the
+//      group's ascending block order (times 1/d for BRAS).
 // No floating-point atomics anywhere: results are bit-reproducible.
 #pragma once
 #include <cuda_bf16.h>
@@ -54,9 +54,10 @@ struct BlockArgs {
     int max_ne;
     uint32_t max_pkt;          // largest packet (bytes)
     // fixed-point dof sums (stage 3): the bound of a block's products is placed at 2^fx_top;
-    // each product's integer splits into fx_lo low bits and the rest, accumulated in two 32-bit
-    // words that cannot overflow for the copies one dof has in a block; fx_er bounds the row
-    // abs-sums of the local operator: < 2^fx_er (H1: of A_ref; vector spaces: of every A_K)
+    // each product's integer splits at bit fx_lo into two parts accumulated in two 32-bit
+    // words that cannot overflow for the copies one dof has in a block (fx_lo = 0: one 64-bit
+    // word); fx_er bounds the row abs-sums of the local operator: < 2^fx_er (H1: of A_ref;
+    // vector spaces: of every A_K)
     int fx_top;
     int fx_lo;
     int fx_er;
@@ -263,17 +264,23 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 
 // ---- stage 3: exact fixed-point dof sums -------------------------------------------------
 // Every signed local product v of a block is added to its block-local dof's integer
-// accumulator as q = rint(v * 2^k) with shared-memory integer atomics: FP32 applies split q
-// into its low fx_lo bits and the rest, each added to a 32-bit word (with at most 2^h copies of
-// a dof in a block, fx_lo = 31 - h and fx_top = 60 - 2h, neither word can overflow); FP64
-// applies add q to one 64-bit word (fx_lo = 0, fx_top = 61 - h).  The integer sums are exact,
-// so a dof's total does not depend on the order in which its copies arrive: every apply gives
-// the same bits (no floating-point atomics).  The scale comes from an a-priori bound of the
-// block's products, |v| < 2^(ex + ec + fx_er) with ex, ec the block's largest exponents of the
-// staged x and of the cell factors (H1; 0 for the vector spaces) and fx_er that of the local
-// operator's row abs-sums, placed at 2^fx_top: k = fx_top - ex - ec - fx_er.  The total is
-// converted back once, rounded to nearest.  Products well below the bound keep an absolute
-// resolution of 2^-k, about 2^-fx_top (~1e-16) of the bound.
+// accumulator as q = rint(v * 2^k) with shared-memory integer atomics.  The integer sums are
+// exact, so a dof's total does not depend on the order in which its copies arrive: every apply
+// gives the same bits (no floating-point atomics).  The scale comes from an a-priori bound of
+// the block's products, |v| < 2^(ex + ec + fx_er) with ex, ec the block's largest exponents of
+// the staged x and of the cell factors (H1; 0 for the vector spaces) and fx_er that of the
+// local operator's row abs-sums, placed at 2^fx_top: k = fx_top - ex - ec - fx_er.  The total
+// is converted back once, rounded to nearest; products well below the bound keep an absolute
+// resolution of 2^-k = 2^-fx_top of the bound.  With at most 2^h copies of a dof in a block:
+//   FP32 and bf16 applies: q = qh 2^L + ql with |ql| <= 2^(L-1), each part summed in a 32-bit
+//     word; L = min(22, 30 - h), fx_top = min(L + 21, 31 + L - h) (43 bits for h <= 8, about
+//     1e-13 of the bound, far below FP32 rounding).  Both parts come out of FP32 additions
+//     with the round-to-integer constant 1.5 * 2^23 (exact for magnitudes below 2^22), so no
+//     64-bit float-integer conversion is needed: B300 runs those on its FP64 pipe, at 1/64 of
+//     the FP32 rate.
+//   FP64 applies: one 64-bit word (fx_lo = 0, fx_top = 61 - h), rounded by the FP64 conversion.
+//   The float-float H1 mass apply: q of each half of a product pair split into fx_lo = 31 - h
+//     low bits and the rest (fx_top = 60 - 2h, about 2^-48 of the bound for the FP64 result).
 constexpr int kExpZero = -100000;   // exponent bound of zero
 constexpr int kExpBad = 100000;     // of an infinity or a NaN
 
@@ -312,6 +319,29 @@ template <> __device__ __forceinline__ double pow2<double>(int k) {
 
 __device__ __forceinline__ long long fx_round(float v) { return __float2ll_rn(v); }
 __device__ __forceinline__ long long fx_round(double v) { return __double2ll_rn(v); }
+
+// rint(t) for |t| < 2^22 on the FP32 adder: t + 1.5 * 2^23 lands in [2^23, 2^24), where the
+// spacing is 1, so the sum is rounded to an integer (ties to even) and its low mantissa bits
+// hold that integer plus 2^22.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;  // its IEEE bits
+__device__ __forceinline__ int magic_int(float rounded) { return __float_as_int(rounded) - kRoundMagicBits; }
+
+// Correctly rounded int64 -> float on the integer units (normalise, round to nearest even on
+// the dropped bits; a mantissa carry moves into the exponent field by itself).
+__device__ __forceinline__ float ll_to_float_rn(long long q) {
+    if (q == 0) return 0.f;
+    const uint32_t sgn = q < 0 ? 0x80000000u : 0u;
+    unsigned long long m = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    const int lz = __clzll((long long)m);
+    m <<= lz;                                          // leading one at bit 63
+    uint32_t mant = (uint32_t)(m >> 40);               // 24 bits, bit 23 set
+    const unsigned long long rest = m << 24;           // the 40 dropped bits, left-aligned
+    const unsigned long long half = 0x8000000000000000ull;
+    if (rest > half || (rest == half && (mant & 1u))) ++mant;
+    return __uint_as_float(sgn | ((uint32_t)(63 - lz + 126) << 23) + mant);
+}
+
 // The accumulators of a block: FP32 (lo_bits > 0) two 32-bit words per dof, the low words of
 // every dof first and the high words after them (so that the lanes of a warp spread over all
 // banks), FP64 (lo_bits = 0) one 64-bit word per dof.  `count` dofs (times right-hand sides).
@@ -322,6 +352,22 @@ struct FxAcc {
     // zero the first n 8-byte words (n = count covers both halves, or every 64-bit word)
     __device__ __forceinline__ void clear(int n) const {
         for (int i = threadIdx.x; i < n; i += blockDim.x) base[i] = 0;
+    }
+    // FP32 product already scaled, s = v 2^k with |s| < 2^(lo_bits + 22), lo_bits <= 22:
+    // rint(s) = qh 2^L + ql, qh = rint(s 2^-L) and ql = rint(s - qh 2^L) (the FMA forms that
+    // difference exactly; |ql| <= 2^(L-1)), each part by the round-to-integer constant.
+    __device__ __forceinline__ void add_scaled(int i, float s) const {
+        const float t = __fmul_rn(s, __int_as_float((127 - lo_bits) << 23));
+        const float th = __fadd_rn(t, kRoundMagic);
+        const float hf = __fsub_rn(th, kRoundMagic);
+        const float r = __fmaf_rn(-hf, __int_as_float((127 + lo_bits) << 23), s);
+        int* w = reinterpret_cast<int*>(base);
+        atomicAdd(w + i, magic_int(__fadd_rn(r, kRoundMagic)));
+        atomicAdd(w + count + i, magic_int(th));
+    }
+    // FP64 product (one 64-bit word, lo_bits = 0)
+    __device__ __forceinline__ void add_scaled(int i, double s) const {
+        atomicAdd(reinterpret_cast<unsigned long long*>(base) + i, (unsigned long long)fx_round(s));
     }
     __device__ __forceinline__ void add(int i, long long q) const {
         if (lo_bits == 0) {
@@ -340,7 +386,7 @@ struct FxAcc {
 };
 
 // accumulator -> value: one rounding of the exact integer sum, then the exact power-of-two scale
-__device__ __forceinline__ float fx_value(long long q, int k, float) { return __ll2float_rn(q) * pow2<float>(-k); }
+__device__ __forceinline__ float fx_value(long long q, int k, float) { return ll_to_float_rn(q) * pow2<float>(-k); }
 __device__ __forceinline__ double fx_value(long long q, int k, double) { return __ll2double_rn(q) * pow2<double>(-k); }
 
 // Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
@@ -652,7 +698,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 // dof-sorted slot
                 auto out = [&](int a, T v) {
                     if constexpr (FX) {
-                        acc.add(L[a * ne] * CW + rr, fx_round(v * sc));
+                        acc.add_scaled(L[a * ne] * CW + rr, v * sc);
                     } else {
                         const bool s = SIGNED && OP != OP_DIAG &&
                                        (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (L[a * ne] & 0x8000) != 0);

@@ -58,7 +58,7 @@ struct bras_ctx {
     int precisions = 0, max_nrhs = 1;
     // fixed-point dof sums: product bound placed at 2^fx_top; exponent bounds of the local
     // operators' row abs-sums (mass, BRAS)
-    int fx_top = 50, fx_lo = 24, fx_top64 = 56, er_mass = 0, er_bras = 0;
+    int fx_top = 43, fx_lo = 22, fx_top_df = 50, fx_lo_df = 24, fx_top64 = 56, er_mass = 0, er_bras = 0;
     int64_t U_tot = 0, npart = 0, nsh = 0;
     int64_t Epad = 0;   // padded cell count of the packed (SoA) per-cell matrices
     int npk = 0;        // nloc (nloc + 1) / 2

@@ -12,6 +12,7 @@ namespace bras {
 // Kernels launched by this library since load (host counter, for launch accounting).
 void count_launch(int k);
 int64_t launches_so_far();
+void count_graph_launch();
 
 struct LaunchCommon {
     BlockArgs A;

@@ -15,14 +15,23 @@ namespace bras {
 constexpr int kDotBlocks = 1184;   // 8 per SM on a 148-SM B300 (fixed: it fixes the summation order)
 constexpr int kMaxRhs = 256;
 
-enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_ISCALE, S_SCALE, S_COUNT };
+// per-slot scalars; S_BN, S_RN = ||b||, ||b - M x|| of the refinement loop
+enum { S_RZ = 0, S_PQ, S_RR, S_RR0, S_ALPHA, S_BETA, S_ISCALE, S_SCALE, S_BN, S_RN, S_COUNT };
 enum { FIN_INIT_RR = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_NORM,
        // stationary iterations: as FIN_INIT_RR / FIN_RR, then the step of the next update is
        // sc[S_SCALE] for an active rhs and 0 for a converged one
        FIN_INIT_STAT, FIN_RR_STAT,
        // power iteration: store the dot product in S_RZ / S_PQ
-       FIN_STORE_A, FIN_STORE_B };
-enum { SOLVER_CG = 0, SOLVER_FIXED_POINT = 1, SOLVER_CHEBYSHEV = 2 };
+       FIN_STORE_A, FIN_STORE_B,
+       // refinement loop: (b, b) and (r, r) of the true residual -> scales, inner tolerance,
+       // outer loop condition; FIN_INIT_INNER = FIN_INIT_RR + the inner loop condition
+       FIN_OUTER_INIT, FIN_OUTER, FIN_INIT_INNER };
+enum { SOLVER_CG = 0, SOLVER_FIXED_POINT = 1, SOLVER_CHEBYSHEV = 2, SOLVER_MIXED = 3 };
+constexpr int kMaxOuter = 60;      // refinement steps of a mixed solve at most
+// iparam: [0] inner maxit, [1] inner iterations done, [2] maxit of the whole mixed solve,
+// [3] inner iterations charged so far (at least 1 per refinement step), [4] refinement steps
+// done, [5] outer loop condition, [6] inner loop condition, [7] inner iterations done in all
+enum { IP_MAXIT = 0, IP_DONE, IP_MAXIT_ALL, IP_CHARGED, IP_OUTER, IP_GO_OUTER, IP_GO_INNER, IP_DONE_ALL, IP_COUNT };
 
 struct SolveGraph {
     int solver = SOLVER_CG, prec = 0, pc = 0, R = 0, tsize = 0;
@@ -30,6 +39,7 @@ struct SolveGraph {
     const void* coef = nullptr;   // Chebyshev coefficient table captured in the body
     int coef_k = 0;
     int kernels_per_iter = 0;
+    int mixed_init = 0, mixed_start = 0, mixed_post = 0;   // mixed solve: kernels of its other parts
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -37,8 +47,8 @@ struct SolveGraph {
 struct PcgWork {
     cudaStream_t cap = nullptr;   // private stream used only to capture solve graphs
     std::vector<SolveGraph> graphs;
-    double* dparam = nullptr;     // [0] = rtol^2
-    int* iparam = nullptr;        // [0] = maxit, [1] = iterations done
+    double* dparam = nullptr;     // [0] = rtol^2 of the CG loop, [1] = rtol of a mixed solve
+    int* iparam = nullptr;        // [IP_COUNT], see IP_*
     double* h_param = nullptr;    // pinned staging of dparam/iparam
     int nrhs = 0;
     int slots = 0;                // scalar slots: max(nrhs, meshes of a batch)
@@ -48,7 +58,8 @@ struct PcgWork {
     double* partial = nullptr;    // [kDotBlocks][nrhs]
     unsigned int* ticket = nullptr;  // arrival counter of the fused reductions
     double* sc = nullptr;         // [S_COUNT][nrhs]
-    int* flags = nullptr;         // [0..nrhs): active, [nrhs..2nrhs): its, [2nrhs]: n active, [2nrhs+1]: status
+    int* flags = nullptr;         // [0..S): active, [S..2S): its, [2S]: n active, [2S+1]: status,
+                                  // [2S+2..3S+2): inner iterations of a mixed solve (S = slots)
     int* h_flags = nullptr;       // pinned
     double* h_sc = nullptr;       // pinned
     double* coef = nullptr;       // Chebyshev direction coefficients [2][kmax + 1][slots]
@@ -99,14 +110,14 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
     w->slots = (int)slots;
     w->partial = (double*)d(std::max((size_t)kDotBlocks * w->nrhs, (size_t)c->nseg) * 8);
     w->sc = (double*)d((size_t)S_COUNT * slots * 8);
-    w->flags = (int*)d((2 * slots + 2) * 4);
+    w->flags = (int*)d((3 * slots + 2) * 4);
     w->dparam = (double*)d(8 * 2);
     w->ticket = (unsigned int*)d(16);
     if (!w->ticket || cudaMemset(w->ticket, 0, 16) != cudaSuccess) return BRAS_ERR_OOM;
-    w->iparam = (int*)d(4 * 4);
+    w->iparam = (int*)d(4 * IP_COUNT);
     if (!w->dparam || !w->iparam) return BRAS_ERR_OOM;
     if (cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess) return BRAS_ERR_CUDA;
-    if (cudaMallocHost(&w->h_param, 64) != cudaSuccess) return BRAS_ERR_OOM;
+    if (cudaMallocHost(&w->h_param, 16 + 4 * IP_COUNT) != cudaSuccess) return BRAS_ERR_OOM;
     if (!w->r || !w->z || !w->p || !w->q || !w->xs || !w->bs || !w->partial || !w->sc || !w->flags) return BRAS_ERR_OOM;
     if (mixed) {
         w->r32 = (float*)d(nv * 4);
@@ -116,7 +127,7 @@ static int ensure_pcg(bras_ctx* c, int R, bool mixed) {
         w->x32 = (float*)d(nv * 4);
         if (!w->r32 || !w->z32 || !w->p32 || !w->q32 || !w->x32) return BRAS_ERR_OOM;
     }
-    if (cudaMallocHost(&w->h_flags, (2 * slots + 2) * sizeof(int)) != cudaSuccess) return BRAS_ERR_OOM;
+    if (cudaMallocHost(&w->h_flags, (3 * slots + 2) * sizeof(int)) != cudaSuccess) return BRAS_ERR_OOM;
     if (cudaMallocHost(&w->h_sc, S_COUNT * slots * sizeof(double)) != cudaSuccess) return BRAS_ERR_OOM;
     return BRAS_OK;
 }
@@ -133,7 +144,7 @@ struct FinArgs {
     unsigned int* ticket;          // arrival counter, returned to 0 by the last block
     double* sc;                    // per-rhs scalars [S_COUNT][R]
     int* flags;                    // active[R], its[R], n_active, status
-    const double* dparam;          // [0] = rtol^2
+    double* dparam;                // [0] = rtol^2 of the CG loop, [1] = rtol of a mixed solve
     int* iparam;                   // [0] = maxit, [1] = iterations done
     cudaGraphConditionalHandle cond;
     int in_graph;                  // the loop condition exists (solve graph)
@@ -217,10 +228,84 @@ __device__ void apply_fin(const FinArgs& F, int R, int r, double s) {
         case FIN_STORE_B:
             sc[S_PQ * R + r] = s;
             break;
+        case FIN_INIT_INNER:
+            sc[S_RR0 * R + r] = s;
+            sc[S_RR * R + r] = s;
+            active[r] = s > 0.0 ? 1 : 0;
+            its[r] = 0;
+            break;
+        case FIN_OUTER_INIT:
+        case FIN_OUTER: {
+            // s = ||b||^2 (init) or ||b - M x||^2; a slot is refined while ||r|| / ||b|| > rtol,
+            // its inner right-hand side is r / ||r|| and the inner solution is added times ||r||
+            int* its_all = F.flags + 2 * R + 2;
+            const double rn = sqrt(s);
+            double bn;
+            if (F.kind == FIN_OUTER_INIT) {
+                bn = rn;
+                sc[S_BN * R + r] = bn;
+                its_all[r] = 0;
+            } else {
+                bn = sc[S_BN * R + r];
+                its_all[r] += its[r];
+            }
+            sc[S_RN * R + r] = rn;
+            const double rel = bn > 0.0 ? rn / bn : 0.0;
+            const bool refine = bn > 0.0 && rel > F.dparam[1];
+            sc[S_SCALE * R + r] = refine ? 1.0 / rn : 0.0;
+            sc[S_ISCALE * R + r] = refine ? rn : 0.0;
+            break;
+        }
     }
 }
 
 __device__ __forceinline__ bool fin_counts_iteration(int kind) { return kind == FIN_RR || kind == FIN_RR_STAT; }
+
+// Scalar tail of a fused reduction, run by one thread after every slot's apply_fin: the
+// count of active slots `cnt`, iteration counting and the loop conditions.
+__device__ void fin_tail(const FinArgs& F, int R, int cnt) {
+    F.flags[2 * R] = cnt;
+    int* ip = F.iparam;
+    if (fin_counts_iteration(F.kind) && ip) {
+        const int done = ++ip[IP_DONE];
+        const unsigned go = (cnt > 0 && done < ip[IP_MAXIT]) ? 1u : 0u;
+        ip[IP_GO_INNER] = (int)go;
+        if (F.in_graph) cudaGraphSetConditional(F.cond, go);
+    }
+    if (F.kind == FIN_INIT_INNER && ip) {
+        ip[IP_DONE] = 0;
+        const unsigned go = (cnt > 0 && ip[IP_MAXIT] > 0) ? 1u : 0u;
+        ip[IP_GO_INNER] = (int)go;
+        if (F.in_graph) cudaGraphSetConditional(F.cond, go);
+    }
+    if ((F.kind == FIN_OUTER_INIT || F.kind == FIN_OUTER) && ip) {
+        double worst = 0.0;
+        for (int k = 0; k < R; ++k) {
+            const double bn = F.sc[S_BN * R + k];
+            const double rel = bn > 0.0 ? F.sc[S_RN * R + k] / bn : 0.0;
+            if (rel > worst) worst = rel;
+        }
+        int charged = 0, outer = 0;
+        if (F.kind == FIN_OUTER) {
+            charged = ip[IP_CHARGED] + max(ip[IP_DONE], 1);
+            outer = ip[IP_OUTER] + 1;
+            ip[IP_DONE_ALL] += ip[IP_DONE];
+        } else {
+            ip[IP_DONE_ALL] = 0;
+        }
+        ip[IP_CHARGED] = charged;
+        ip[IP_OUTER] = outer;
+        const double rtol = F.dparam[1];
+        const unsigned go =
+            (worst > rtol && charged < ip[IP_MAXIT_ALL] && outer < kMaxOuter && F.flags[2 * R + 1] == 0) ? 1u : 0u;
+        // inner tolerance: as deep as FP32 allows, no deeper than the outer test needs
+        const double tin = fmax(1e-6, fmin(1e-2, 0.5 * rtol / worst));
+        F.dparam[0] = tin * tin;
+        ip[IP_MAXIT] = ip[IP_MAXIT_ALL] - charged;
+        ip[IP_GO_OUTER] = (int)go;
+        if (F.in_graph) cudaGraphSetConditional(F.cond, go);
+    }
+}
 
 // `red` holds this block's 256 per-thread sums (thread t: rhs t % R, group t / R).
 __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
@@ -254,11 +339,7 @@ __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
     if (tid == 0) {
         int cnt = 0;
         for (int k = 0; k < R; ++k) cnt += F.flags[k];
-        F.flags[2 * R] = cnt;
-        if (fin_counts_iteration(F.kind) && F.iparam) {
-            const int done = ++F.iparam[1];
-            if (F.in_graph) cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
-        }
+        fin_tail(F, R, cnt);
         *F.ticket = 0u;
     }
 }
@@ -361,6 +442,120 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
     block_partial_and_finish(F, R, red);
 }
 
+// ---- refinement loop of the mixed solve (one graph: the outer loop and the inner CG loop are
+// conditional WHILE nodes; these kernels end in the fused reductions that decide them) ------
+// x = 0; r = b; (b, b) -> FIN_OUTER_INIT
+__global__ void __launch_bounds__(256) k_outer_init(double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ b, int64_t n, int R, FinArgs F) {
+    __shared__ double red[256];
+    const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
+    double acc = 0.0;
+    if (lr < rows) {
+        const int64_t stride = (int64_t)gridDim.x * rows;
+        DotAcc<double> c[4];
+        int64_t i = (int64_t)blockIdx.x * rows + lr;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            double bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) bv[u] = b[(i + u * stride) * R + rr];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = (i + u * stride) * R + rr;
+                r[k] = bv[u];
+                x[k] = 0.0;
+                c[u].add(bv[u], bv[u]);
+            }
+        }
+        for (; i < n; i += stride) {
+            const int64_t k = i * R + rr;
+            const double v = b[k];
+            r[k] = v;
+            x[k] = 0.0;
+            c[0].add(v, v);
+        }
+        acc = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+    }
+    red[tid] = acc;
+    block_partial_and_finish(F, R, red);
+}
+
+// inner start: r32 = (float)(r s) (s = 1/||r|| or 0), x32 = p32 = 0; (r32, r32) -> FIN_INIT_INNER
+__global__ void __launch_bounds__(256) k_inner_start(const double* __restrict__ r, const double* __restrict__ s,
+                                                    float* __restrict__ r32, float* __restrict__ x32,
+                                                    float* __restrict__ p32, int64_t n, int R, FinArgs F) {
+    __shared__ double red[256];
+    const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
+    double acc = 0.0;
+    if (lr < rows) {
+        const double sc = s[rr];
+        const int64_t stride = (int64_t)gridDim.x * rows;
+        DotAcc<float> c[4];
+        int64_t i = (int64_t)blockIdx.x * rows + lr;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            double rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rv[u] = r[(i + u * stride) * R + rr];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = (i + u * stride) * R + rr;
+                const float v = (float)(rv[u] * sc);
+                r32[k] = v;
+                x32[k] = 0.f;
+                p32[k] = 0.f;
+                c[u].add(v, v);
+            }
+        }
+        for (; i < n; i += stride) {
+            const int64_t k = i * R + rr;
+            const float v = (float)(r[k] * sc);
+            r32[k] = v;
+            x32[k] = 0.f;
+            p32[k] = 0.f;
+            c[0].add(v, v);
+        }
+        acc = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+    }
+    red[tid] = acc;
+    block_partial_and_finish(F, R, red);
+}
+
+// true residual r = b - q (q = M x in FP64); (r, r) -> FIN_OUTER
+__global__ void __launch_bounds__(256) k_residual_rr(double* __restrict__ r, const double* __restrict__ b,
+                                                    const double* __restrict__ q, int64_t n, int R, FinArgs F) {
+    __shared__ double red[256];
+    const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
+    double acc = 0.0;
+    if (lr < rows) {
+        const int64_t stride = (int64_t)gridDim.x * rows;
+        DotAcc<double> c[4];
+        int64_t i = (int64_t)blockIdx.x * rows + lr;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            double bv[4], qv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = (i + u * stride) * R + rr;
+                bv[u] = b[k];
+                qv[u] = q[k];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double v = bv[u] - qv[u];
+                r[(i + u * stride) * R + rr] = v;
+                c[u].add(v, v);
+            }
+        }
+        for (; i < n; i += stride) {
+            const int64_t k = i * R + rr;
+            const double v = b[k] - q[k];
+            r[k] = v;
+            c[0].add(v, v);
+        }
+        acc = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+    }
+    red[tid] = acc;
+    block_partial_and_finish(F, R, red);
+}
+
 // ---- batched (segmented) variants: vectors are one rhs each of n_mesh independent systems;
 // thread block s works on the dofs [seg[2s], seg[2s+1]) of mesh seg_mesh[s] and the last block
 // reduces, mesh by mesh, the partials of that mesh's blocks in a fixed order (one warp per
@@ -406,12 +601,7 @@ __device__ void seg_partial_and_finish(const FinArgs& F, const SegArgs& G, doubl
     }
     __syncthreads();
     if (tid == 0) {
-        const int cnt = cnt_s[0];
-        F.flags[2 * G.M] = cnt;
-        if (fin_counts_iteration(F.kind) && F.iparam) {
-            const int done = ++F.iparam[1];
-            if (F.in_graph) cudaGraphSetConditional(F.cond, (cnt > 0 && done < F.iparam[0]) ? 1u : 0u);
-        }
+        fin_tail(F, G.M, cnt_s[0]);
         *F.ticket = 0u;
     }
 }
@@ -446,18 +636,58 @@ __global__ void __launch_bounds__(256) k_seg_update_xr(T* __restrict__ x, T* __r
     seg_partial_and_finish(F, G, red);
 }
 
+__global__ void __launch_bounds__(256) k_seg_outer_init(double* __restrict__ x, double* __restrict__ r,
+                                                       const double* __restrict__ b, SegArgs G, FinArgs F) {
+    __shared__ double red[256];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    DotAcc<double> acc;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) {
+        const double v = b[i];
+        r[i] = v;
+        x[i] = 0.0;
+        acc.add(v, v);
+    }
+    red[threadIdx.x] = acc.value();
+    seg_partial_and_finish(F, G, red);
+}
+
+__global__ void __launch_bounds__(256) k_seg_inner_start(const double* __restrict__ r, const double* __restrict__ s,
+                                                        float* __restrict__ r32, float* __restrict__ x32,
+                                                        float* __restrict__ p32, SegArgs G, FinArgs F) {
+    __shared__ double red[256];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    const double sc = s[G.seg_mesh[blockIdx.x]];
+    DotAcc<float> acc;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) {
+        const float v = (float)(r[i] * sc);
+        r32[i] = v;
+        x32[i] = 0.f;
+        p32[i] = 0.f;
+        acc.add(v, v);
+    }
+    red[threadIdx.x] = acc.value();
+    seg_partial_and_finish(F, G, red);
+}
+
+__global__ void __launch_bounds__(256) k_seg_residual_rr(double* __restrict__ r, const double* __restrict__ b,
+                                                        const double* __restrict__ q, SegArgs G, FinArgs F) {
+    __shared__ double red[256];
+    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
+    DotAcc<double> acc;
+    for (int64_t i = beg + threadIdx.x; i < end; i += 256) {
+        const double v = b[i] - q[i];
+        r[i] = v;
+        acc.add(v, v);
+    }
+    red[threadIdx.x] = acc.value();
+    seg_partial_and_finish(F, G, red);
+}
+
 template <typename T>
 __global__ void k_seg_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, SegArgs G) {
     const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
     const T bt = (T)beta[G.seg_mesh[blockIdx.x]];
     for (int64_t i = beg + threadIdx.x; i < end; i += 256) p[i] = fma(bt, p[i], z[i]);
-}
-
-__global__ void k_seg_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ s,
-                                   SegArgs G) {
-    const int64_t beg = G.seg[2 * blockIdx.x], end = G.seg[2 * blockIdx.x + 1];
-    const double sc = s[G.seg_mesh[blockIdx.x]];
-    for (int64_t i = beg + threadIdx.x; i < end; i += 256) r32[i] = (float)(r[i] * sc);
 }
 
 // x += d * f with f = ||r|| (the inverse of the scale that made the inner right-hand side;
@@ -482,12 +712,7 @@ __global__ void k_jacobi(const T* __restrict__ x, T* __restrict__ y, const T* __
         y[i] = x[i] / diag[R == 1 ? i : i / R];
 }
 
-// r32 = (float)(r64 * s_r)   and   x64 += (double)d32 / s_r   and   r = b - q
-__global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ s,
-                               int64_t nv, int R) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-        r32[i] = (float)(r[i] * s[R == 1 ? 0 : i % R]);
-}
+// x64 += (double)d32 * f_r  (f_r = ||r||: undoes the scaling of the inner right-hand side)
 __global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ f,
                             int64_t nv, int R) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
@@ -495,11 +720,6 @@ __global__ void k_accum_f32(double* __restrict__ x, const float* __restrict__ d,
         if (sr > 0.0) x[i] = fma((double)d[i], sr, x[i]);
     }
 }
-__global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q, int64_t nv) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-        r[i] = b[i] - q[i];
-}
-
 // Chebyshev direction update d = c1[k] d + c2[k] z, k = iterations done (read on the device,
 // so that one captured body serves every iteration); coefficients [2][kmax + 1][S].
 __global__ void k_update_d(double* __restrict__ d, const double* __restrict__ z, const double* __restrict__ coef,
@@ -582,14 +802,15 @@ static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, 
 }
 
 // x += alpha p; r -= alpha q; (r, r) -> `kind` (FIN_RR for CG, FIN_RR_STAT for the stationary
-// iterations).  CG counts iterations on the device only inside its solve graph; the stationary
-// iterations always do (Chebyshev indexes its coefficients by the count).
+// iterations).  Iterations are counted on the device (iparam[IP_DONE]); inside a solve graph
+// the count and the active slots set the loop condition (Chebyshev also indexes its
+// coefficients by the count).
 template <typename T>
 static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, int R, cudaGraphConditionalHandle cond,
                               cudaStream_t st, bool in_graph, int kind = FIN_RR) {
     PcgWork* w = c->pcg;
     const int S = batched(c) ? c->n_mesh : R;
-    int* ip = (in_graph || kind == FIN_RR_STAT) ? w->iparam : nullptr;
+    int* ip = w->iparam;
     if (batched(c))
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
                                                      fin_args(w, kind, ip, cond, in_graph));
@@ -808,6 +1029,7 @@ static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z,
         kpi = 0;
     } else if (maxit > 0) {
         CK(cudaGraphLaunch(exec, st));
+        count_graph_launch();
     }
     CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (2 * S + 2), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
@@ -816,6 +1038,171 @@ static int pcg_core(bras_ctx* c, int prec, int pc, const T* b, T* x, T* r, T* z,
     if (maxit > 0) count_launch(kpi * hp[1]);
     if (w->h_flags[2 * S + 1] != 0) return w->h_flags[2 * S + 1];
     return w->h_flags[2 * S] > 0 ? BRAS_NOT_CONVERGED : BRAS_OK;
+}
+
+// ---- mixed solve: FP64 iterative refinement around an FP32 (or BF16-inverse) inner PCG ----
+// Refinement step j (slot s refined while ||r_j|| / ||b|| > rtol):
+//   r32 = (float)(r_j / ||r_j||);  inner PCG on M d = r32 to the tolerance
+//   tin = clamp(0.5 rtol / max_s(||r_j|| / ||b||), 1e-6, 1e-2);  x += ||r_j|| d (FP64);
+//   r_{j+1} = b - M x (FP64 cell products, exact dof sums); stop when every slot passes, the
+// inner iterations charged (at least one per step) reach maxit, a step broke down, or after
+// kMaxOuter steps.  All of it runs from device scalars: one graph launch per solve.
+static cudaError_t enqueue_outer_init(bras_ctx* c, int R, cudaGraphConditionalHandle cond, cudaStream_t st,
+                                      bool in_graph) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    cudaError_t e = cudaMemsetAsync(w->flags + 2 * S + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const FinArgs F = fin_args(w, FIN_OUTER_INIT, w->iparam, cond, in_graph);
+    if (batched(c)) k_seg_outer_init<<<c->nseg, 256, 0, st>>>(w->xs, w->r, w->bs, seg_args(c), F);
+    else k_outer_init<<<kDotBlocks, 256, 0, st>>>(w->xs, w->r, w->bs, c->n, R, F);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t enqueue_inner_start(bras_ctx* c, int R, cudaGraphConditionalHandle cond, cudaStream_t st,
+                                       bool in_graph) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    const FinArgs F = fin_args(w, FIN_INIT_INNER, w->iparam, cond, in_graph);
+    if (batched(c))
+        k_seg_inner_start<<<c->nseg, 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, seg_args(c), F);
+    else
+        k_inner_start<<<kDotBlocks, 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, c->n, R, F);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// inner CG iteration on the FP32 buffers (q32 serves as the search direction's image M p)
+static int enqueue_inner_iteration(bras_ctx* c, int inner_prec, int pc, int R, cudaGraphConditionalHandle cond,
+                                   cudaStream_t st, bool in_graph) {
+    PcgWork* w = c->pcg;
+    return enqueue_iteration<float>(c, inner_prec, pc, w->x32, w->r32, w->z32, w->p32, w->q32, R, cond, st, in_graph);
+}
+
+// x += ||r|| d; q = M x (FP64); r = b - q; (r, r) -> FIN_OUTER
+static int enqueue_outer_post(bras_ctx* c, int R, cudaGraphConditionalHandle cond, cudaStream_t st, bool in_graph) {
+    PcgWork* w = c->pcg;
+    const int S = batched(c) ? c->n_mesh : R;
+    const int64_t nv = c->n * R;
+    if (batched(c)) k_seg_accum_f32<<<c->nseg, 256, 0, st>>>(w->xs, w->x32, w->sc + S_ISCALE * S, seg_args(c));
+    else k_accum_f32<<<grid_for(nv), 256, 0, st>>>(w->xs, w->x32, w->sc + S_ISCALE * S, nv, R);
+    count_launch(1);
+    CK(cudaGetLastError());
+    RC(run_op(c, BRAS_FP64X, OP_MASS, w->xs, w->q, R, st));
+    const FinArgs F = fin_args(w, FIN_OUTER, w->iparam, cond, in_graph);
+    if (batched(c)) k_seg_residual_rr<<<c->nseg, 256, 0, st>>>(w->r, w->bs, w->q, seg_args(c), F);
+    else k_residual_rr<<<kDotBlocks, 256, 0, st>>>(w->r, w->bs, w->q, c->n, R, F);
+    count_launch(1);
+    CK(cudaGetLastError());
+    return BRAS_OK;
+}
+
+// Append a conditional WHILE node (handle h) to the graph that `st` is capturing into, after
+// everything captured so far; later captures on `st` depend on it.  Returns its body graph.
+static int capture_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return BRAS_ERR_CUDA;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *body = np.conditional.phGraph_out[0];
+    return BRAS_OK;
+}
+
+struct MixedKernels {
+    int init = 0, start = 0, iter = 0, post = 0;   // kernels launched by each part
+};
+
+// The mixed solve as one graph:  init -> WHILE(outer) { inner start -> WHILE(inner) { CG
+// iteration } -> accumulate, true residual, test }.  Cached per (inner precision,
+// preconditioner, nrhs, partial buffer); every vector is a workspace buffer.
+static int get_mixed_graph(bras_ctx* c, int inner_prec, int pc, int R, cudaGraphExec_t* out, MixedKernels* kn) {
+    PcgWork* w = c->pcg;
+    for (auto& g : w->graphs)
+        if (g.solver == SOLVER_MIXED && g.prec == inner_prec && g.pc == pc && g.R == R && g.x == w->xs &&
+            g.part == c->part) {
+            *out = g.exec;
+            *kn = MixedKernels{g.mixed_init, g.mixed_start, g.kernels_per_iter, g.mixed_post};
+            return BRAS_OK;
+        }
+    SolveGraph g;
+    g.solver = SOLVER_MIXED;
+    g.prec = inner_prec;
+    g.pc = pc;
+    g.R = R;
+    g.x = w->xs;
+    g.part = c->part;
+    CK(cudaGraphCreate(&g.graph, 0));
+    MixedKernels k;
+    int rc = BRAS_OK;
+    auto counted = [&](int* cnt, auto&& fn) {
+        const int64_t before = launches_so_far();
+        const int r = fn();
+        *cnt = (int)(launches_so_far() - before);
+        count_launch(-*cnt);     // captured, not launched
+        return r;
+    };
+    auto fail = [&](int r) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(w->cap, &junk);
+        cudaGraphDestroy(g.graph);
+        cudaGetLastError();
+        return r;
+    };
+    cudaGraphConditionalHandle h_outer, h_inner;
+    CK(cudaGraphConditionalHandleCreate(&h_outer, g.graph, 0, cudaGraphCondAssignDefault));
+    // top level: init, then the outer loop
+    CK(cudaStreamBeginCaptureToGraph(w->cap, g.graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaGraph_t outer_body = nullptr, inner_body = nullptr;
+    rc = counted(&k.init, [&] { return enqueue_outer_init(c, R, h_outer, w->cap, true) == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA; });
+    if (rc == BRAS_OK) rc = capture_while(w->cap, h_outer, &outer_body);
+    if (rc != BRAS_OK) return fail(rc);
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(w->cap, &captured) != cudaSuccess) return fail(BRAS_ERR_CUDA);
+    // outer body: inner start, the inner loop, accumulate + true residual + test
+    if (cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0, 0) != cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(w->cap, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+            cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        return BRAS_ERR_CUDA;
+    }
+    rc = counted(&k.start, [&] { return enqueue_inner_start(c, R, h_inner, w->cap, true) == cudaSuccess ? BRAS_OK : BRAS_ERR_CUDA; });
+    if (rc == BRAS_OK) rc = capture_while(w->cap, h_inner, &inner_body);
+    if (rc == BRAS_OK) rc = counted(&k.post, [&] { return enqueue_outer_post(c, R, h_outer, w->cap, true); });
+    if (rc != BRAS_OK) return fail(rc);
+    if (cudaStreamEndCapture(w->cap, &captured) != cudaSuccess) return fail(BRAS_ERR_CUDA);
+    // inner body: one CG iteration
+    if (cudaStreamBeginCaptureToGraph(w->cap, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        return BRAS_ERR_CUDA;
+    }
+    rc = counted(&k.iter, [&] { return enqueue_inner_iteration(c, inner_prec, pc, R, h_inner, w->cap, true); });
+    if (rc != BRAS_OK) return fail(rc);
+    if (cudaStreamEndCapture(w->cap, &captured) != cudaSuccess) return fail(BRAS_ERR_CUDA);
+    if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        cudaGetLastError();
+        return BRAS_ERR_CUDA;
+    }
+    g.mixed_init = k.init;
+    g.mixed_start = k.start;
+    g.kernels_per_iter = k.iter;
+    g.mixed_post = k.post;
+    w->graphs.push_back(g);
+    *out = g.exec;
+    *kn = k;
+    return BRAS_OK;
 }
 
 static bool host_ptr(const void* p) {
@@ -858,61 +1245,55 @@ int pcg_solve_impl(bras_ctx* c, int pc, int mode, int inner_prec, const double* 
             rel[r] = rr0 > 0 ? std::sqrt(w->h_sc[S_RR * S + r] / rr0) : 0.0;
         }
     } else {
-        // x = 0, r = b; ||b|| per slot
-        CK(cudaMemsetAsync(dx, 0, sizeof(double) * nv, st));
-        CK(cudaMemcpyAsync(w->r, db, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-        CK(vdot(c, db, db, R, FIN_NORM, st));
-        CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * S, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::vector<double> bn(S), rn(S), scale(S), iscale(S);
-        for (int r = 0; r < S; ++r) { bn[r] = std::sqrt(w->h_sc[r]); rn[r] = bn[r]; }
-        int total_inner = 0;
-        bool done = false;
-        for (int outer = 0; outer < 60 && !done; ++outer) {
-            double worst = 0.0;
-            for (int r = 0; r < S; ++r) {
-                rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
-                worst = std::max(worst, rel[r]);
-                scale[r] = (bn[r] > 0 && rel[r] > rtol) ? 1.0 / rn[r] : 0.0;
+        // the whole refinement loop is one graph on workspace buffers: b -> bs, result from xs
+        if (!hb && b != w->bs) CK(cudaMemcpyAsync(w->bs, b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+        cudaGraphExec_t exec = nullptr;
+        MixedKernels kn;
+        RC(get_mixed_graph(c, inner_prec, pc, R, &exec, &kn));
+        w->h_param[1] = rtol;
+        int* hp = reinterpret_cast<int*>(w->h_param + 2);
+        for (int k = 0; k < IP_COUNT; ++k) hp[k] = 0;
+        hp[IP_MAXIT_ALL] = std::max(maxit, 0);
+        CK(cudaMemcpyAsync(w->dparam + 1, w->h_param + 1, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(w->iparam, hp, sizeof(int) * IP_COUNT, cudaMemcpyHostToDevice, st));
+        if (host_loop()) {
+            // profiling aid: the graph's kernels launched one by one, each loop condition read back
+            auto go = [&](int which) -> int {
+                if (cudaMemcpyAsync(hp, w->iparam, sizeof(int) * IP_COUNT, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return -1;
+                return hp[which];
+            };
+            CK(enqueue_outer_init(c, R, 0, st, false));
+            int g_out;
+            while ((g_out = go(IP_GO_OUTER)) == 1) {
+                CK(enqueue_inner_start(c, R, 0, st, false));
+                int g_in;
+                while ((g_in = go(IP_GO_INNER)) == 1) RC(enqueue_inner_iteration(c, inner_prec, pc, R, 0, st, false));
+                if (g_in < 0) return BRAS_ERR_CUDA;
+                RC(enqueue_outer_post(c, R, 0, st, false));
             }
-            if (worst <= rtol) { done = true; break; }
-            if (total_inner >= maxit) break;
-            // inner tolerance: as deep as FP32 allows, no deeper than needed
-            const double tin = std::max(1e-6, std::min(1e-2, 0.5 * rtol / worst));
-            for (int r = 0; r < S; ++r) iscale[r] = scale[r] > 0 ? rn[r] : 0.0;
-            CK(cudaMemcpyAsync(w->sc + S_SCALE * S, scale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(w->sc + S_ISCALE * S, iscale.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
-            if (batched(c))
-                k_seg_scale_to_f32<<<c->nseg, 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * S, seg_args(c));
-            else
-                k_scale_to_f32<<<grid_for(nv), 256, 0, st>>>(w->r, w->r32, w->sc + S_SCALE * S, nv, R);
-            count_launch(1);
-            CK(cudaGetLastError());
-            int s = pcg_core<float>(c, inner_prec, pc, w->r32, w->x32, w->q32 /*r*/, w->z32, w->p32,
-                                    reinterpret_cast<float*>(w->z) /*q*/, R, tin, maxit - total_inner, st);
-            if (s < 0) return s;
-            int mx = 0;
-            for (int r = 0; r < S; ++r) { its[r] += w->h_flags[S + r]; mx = std::max(mx, w->h_flags[S + r]); }
-            total_inner += std::max(mx, 1);
-            if (batched(c))
-                k_seg_accum_f32<<<c->nseg, 256, 0, st>>>(dx, w->x32, w->sc + S_ISCALE * S, seg_args(c));
-            else
-                k_accum_f32<<<grid_for(nv), 256, 0, st>>>(dx, w->x32, w->sc + S_ISCALE * S, nv, R);
-            count_launch(1);
-            RC(run_op(c, BRAS_FP64X, OP_MASS, dx, w->q, R, st));   // refinement residual b - M x
-            k_residual<<<grid_for(nv), 256, 0, st>>>(w->r, db, w->q, nv);
-            count_launch(1);
-            CK(vdot(c, w->r, w->r, R, FIN_NORM, st));
-            CK(cudaMemcpyAsync(w->h_sc, w->sc + S_RR * S, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            for (int r = 0; r < S; ++r) rn[r] = std::sqrt(w->h_sc[r]);
+            if (g_out < 0) return BRAS_ERR_CUDA;
+        } else {
+            CK(cudaGraphLaunch(exec, st));
+            count_graph_launch();
         }
-        double worst = 0.0;
+        CK(cudaMemcpyAsync(w->h_flags, w->flags, sizeof(int) * (3 * S + 2), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(double) * S_COUNT * S, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp, w->iparam, sizeof(int) * IP_COUNT, cudaMemcpyDeviceToHost, st));
+        if (dx != w->xs) CK(cudaMemcpyAsync(dx, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        if (!host_loop())
+            count_launch(kn.init + (int64_t)hp[IP_OUTER] * (kn.start + kn.post) + (int64_t)hp[IP_DONE_ALL] * kn.iter);
+        bool ok = true;
         for (int r = 0; r < S; ++r) {
-            rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
-            worst = std::max(worst, rel[r]);
+            const double bn = w->h_sc[S_BN * S + r];
+            its[r] = w->h_flags[2 * S + 2 + r];
+            rel[r] = bn > 0 ? w->h_sc[S_RN * S + r] / bn : 0.0;
+            if (!(rel[r] <= rtol)) ok = false;
         }
-        status = worst <= rtol ? BRAS_OK : BRAS_NOT_CONVERGED;
+        if (w->h_flags[2 * S + 1] != 0) return w->h_flags[2 * S + 1];
+        status = ok ? BRAS_OK : BRAS_NOT_CONVERGED;
     }
     if (hx) CK(cudaMemcpyAsync(x, dx, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -995,6 +1376,7 @@ int stationary_solve_impl(bras_ctx* c, int solver, int pc, const double* step, c
         kpi = 0;
     } else if (maxit > 0) {
         CK(cudaGraphLaunch(exec, st));
+        count_graph_launch();
     }
     if (hx) CK(cudaMemcpyAsync(x, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
     else if (x != w->xs) CK(cudaMemcpyAsync(x, w->xs, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));

@@ -368,7 +368,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int a = 16 * g + j;
-                            if (a < NLOC) acc.add(loc[a * ne + e] * CW + rr, fx_round(__uint_as_float(v[g][j]) * cs));
+                            if (a < NLOC) acc.add_scaled(loc[a * ne + e] * CW + rr, __uint_as_float(v[g][j]) * cs);
                         }
                     }
                 }

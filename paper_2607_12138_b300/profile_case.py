@@ -19,7 +19,7 @@ from . import meshgen as mg
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--space", default="h1", choices=["h1", "hcurl", "hdiv"])
+    ap.add_argument("--space", default="h1", choices=["h1", "h1g", "h1b", "hcurl", "hdiv"])
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--cells", type=int, default=48)
     ap.add_argument("--op", default="bras", choices=["bras", "mass", "jacobi"])

@@ -158,6 +158,35 @@ def test_pcg_mixed_refinement_reaches_fp64_residual(case, inner):
     assert true_rel <= 1e-10 and abs(true_rel - rel[0]) <= 1e-3 * 1e-10 + 1e-6 * true_rel
 
 
+@pytest.mark.parametrize("case", ["3d_p3", "hcurl3"])
+def test_mixed_solve_runs_as_one_graph(case):
+    """The refinement loop (scales, inner tolerance, stopping test) runs from device scalars:
+    one graph launch per mixed solve, bit-identical repeats, a zero column left at zero and
+    untouched by the inner loop, and the iteration budget honoured."""
+    mesh, pr, ctx = _setup(case)
+    b, _ = _vec(pr.n_dof, 3, seed=5)
+    b[:, 1] = 0.0
+    bt = torch.as_tensor(b, device="cuda")
+    g0, k0 = B.graph_launches(), B.kernel_launches()
+    x1, its1, rel1, st1 = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
+    assert B.graph_launches() - g0 == 1 and B.kernel_launches() - k0 > int(its1.max())
+    x2, its2, rel2, st2 = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
+    assert st1 == st2 == B.OK
+    assert torch.equal(x1, x2) and np.array_equal(its1, its2) and np.array_equal(rel1, rel2)
+    xg = x1.cpu().numpy()
+    assert its1[1] == 0 and rel1[1] == 0.0 and not np.any(xg[:, 1])
+    for r in (0, 2):
+        assert np.linalg.norm(b[:, r] - pr.M @ xg[:, r]) <= 1e-10 * np.linalg.norm(b[:, r])
+    # budget: at most maxit inner iterations in all (each refinement step charges at least one)
+    xb, itsb, relb, stb = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10, maxit=4)
+    assert stb == B.NOT_CONVERGED and int(itsb.max()) <= 4 and relb.max() > 1e-10
+    x0, its0, rel0, st0 = ctx.pcg_solve(bt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10, maxit=0)
+    assert st0 == B.NOT_CONVERGED and not torch.any(x0) and np.array_equal(rel0, [1.0, 0.0, 1.0])
+    z = torch.zeros_like(bt)
+    xz, itsz, relz, stz = ctx.pcg_solve(z, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
+    assert stz == B.OK and not torch.any(xz) and not np.any(itsz) and not np.any(relz)
+
+
 @pytest.mark.parametrize("case,nrhs", [("3d_p2", 4), ("3d_p4", 5), ("hcurl3", 3)])
 def test_pcg_multi_rhs_and_host_buffers(case, nrhs):
     mesh, pr, ctx = _setup(case)
