@@ -258,6 +258,29 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
     if (!(c->dinv32 = dalloc<float>(c, n_dof))) return BRAS_ERR_OOM;
     if (to_float(c->dinv64, c->dinv32, n_dof, st) != cudaSuccess) return BRAS_ERR_CUDA;
 
+    // many right-hand sides on streamed cell matrices: the cells' maps in internal order with
+    // P's sign in bit 31, and the dof-sorted slots of the copies (ascending (cell, local index))
+    if (space != BRAS_H1 && nloc <= kCellMrMaxLoc && c->max_nrhs >= kCellMrMinRhs) {
+        const size_t m = (size_t)n_cell * nloc;
+        std::vector<int32_t> ml(m), slot(m);
+        std::vector<int64_t> off((size_t)n_dof + 1, 0);
+        for (int64_t e = 0; e < n_cell; ++e) {
+            const int64_t K = t.perm[e];
+            for (int a = 0; a < nloc; ++a) {
+                const int32_t g = h_l2g[(size_t)K * nloc + a];
+                const bool neg = signs && h_signs[(size_t)K * nloc + a] < 0;
+                ml[(size_t)e * nloc + a] = neg ? (int32_t)((uint32_t)g | 0x80000000u) : g;
+                off[(size_t)g + 1]++;
+            }
+        }
+        for (int64_t u = 0; u < n_dof; ++u) off[u + 1] += off[u];
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        for (size_t i = 0; i < m; ++i) slot[i] = (int32_t)fill[ml[i] & 0x7fffffff]++;
+        if ((rc = upload(c, &c->mr_l2g, ml.data(), m))) return rc;
+        if ((rc = upload(c, &c->mr_slot, slot.data(), m))) return rc;
+        if ((rc = upload(c, &c->mr_off, off.data(), off.size()))) return rc;
+    }
+
     // reference tables (library construction, host)
     RefTables ref;
     if (build_reference(dim, space, order, &ref, basis) != 0) return BRAS_ERR_INVALID;
@@ -563,8 +586,15 @@ int smem_optin_bytes() {
     return cached[dev];
 }
 
+// Scratch entries (times element size) one apply of nrhs right-hand sides needs: the partial
+// sums of shared dofs, or, on the many-right-hand-side streamed path, every copy's row.
+size_t part_entries(const bras_ctx* c, int nrhs) {
+    const int64_t rows = (c->mr_l2g && nrhs >= kCellMrMinRhs) ? std::max<int64_t>(c->npart, c->E * c->nloc) : c->npart;
+    return (size_t)std::max<int64_t>(rows, 1) * (size_t)nrhs;
+}
+
 int ensure_part(bras_ctx* c, int nrhs) {
-    size_t need = (size_t)std::max<int64_t>(c->npart, 1) * nrhs * sizeof(double);
+    size_t need = part_entries(c, nrhs) * sizeof(double);
     if (need <= c->part_bytes) return BRAS_OK;
     dfree(c, c->part);
     c->part = dalloc_bytes(c, need);
@@ -596,6 +626,12 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.fx_top = acc64 ? c->fx_top64 : df ? c->fx_top_df : c->fx_top;
     A.fx_lo = acc64 ? 0 : df ? c->fx_lo_df : c->fx_lo;
     A.fx_er = op == OP_BRAS ? c->er_bras : c->er_mass;
+    A.mr_l2g = c->mr_l2g;
+    A.mr_slot = c->mr_slot;
+    A.mr_off = c->mr_off;
+    A.dinv = prec == BRAS_FP64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
+    A.n_dof = c->n;
+    A.n_cell = c->E;
     const bool f64 = prec == BRAS_FP64;
     if (c->space == BRAS_H1) {
         if (op == OP_BRAS) {

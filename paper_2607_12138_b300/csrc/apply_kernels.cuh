@@ -61,6 +61,16 @@ struct BlockArgs {
     int fx_top;
     int fx_lo;
     int fx_er;
+    // many right-hand sides, streamed cell matrices (k_cell_mr + k_dof_gather): the cells'
+    // local-to-global maps in internal cell order (bit 31 = sign of P), each copy's slot in
+    // dof-sorted order (copies of a dof by ascending (cell, local index)), the first slot of
+    // each dof, 1/d per dof; null when the context was built for fewer right-hand sides
+    const int32_t* mr_l2g;     // [E][nloc]
+    const int32_t* mr_slot;    // [E][nloc]
+    const int64_t* mr_off;     // [n + 1]
+    const void* dinv;          // T[n]
+    int64_t n_dof;
+    int64_t n_cell;
 };
 
 // Shared dofs for the combine pass (tables.cpp), in group order: item j = (global dof, group g)
@@ -94,16 +104,18 @@ template <typename T> __device__ __forceinline__ T vec_elem(const uint4& v, int 
 }
 
 // Visit the packed entries (a, q <= a) of this thread's cell in order, 16 bytes per load;
-// f(a, q, m) is inlined with compile-time a, q after unrolling.
+// f(a, q, m) is inlined with compile-time a, q after unrolling.  Layout pk_index (packet.h):
+// the groups of a cell sit 32 groups apart inside its tile of 32 cells, so a warp of 32
+// consecutive cells reads its tile as one contiguous stream of 512-byte rows.
 template <int NLOC, typename T, typename S, typename F>
-__device__ __forceinline__ void for_packed(const S* pk_base, int64_t cell, int64_t Epad, F&& f) {
+__device__ __forceinline__ void for_packed(const S* pk_base, int64_t cell, F&& f) {
     using V = typename PkVec<S>::V;
-    constexpr int G = PkVec<S>::G, NPK = NLOC * (NLOC + 1) / 2;
-    const V* base = reinterpret_cast<const V*>(pk_base) + cell;
+    constexpr int G = PkVec<S>::G, NPK = NLOC * (NLOC + 1) / 2, NG = (NPK + G - 1) / G;
+    const V* base = reinterpret_cast<const V*>(pk_base) + (((size_t)(cell >> 5) * NG) << 5) + (size_t)(cell & 31);
     int a = 0, q = 0;
 #pragma unroll
-    for (int g = 0; g < (NPK + G - 1) / G; ++g) {
-        const V v = ld_vec(base + (size_t)g * Epad);
+    for (int g = 0; g < NG; ++g) {
+        const V v = ld_vec(base + ((size_t)g << 5));
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             if (g * G + j < NPK) {
@@ -659,7 +671,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     if (a < 64) neg |= (uint64_t)s << (a & 63);
                     xt[a * ne + e] = s ? -v : v;
                 }
-                for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T m) {
+                for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, [&](int a, int q, T m) {
                     zl[a] = fma(m, xt[q * ne + e], zl[a]);
                     if (q < a) zl[q] = fma(m, xt[a * ne + e], zl[q]);
                 });
@@ -736,7 +748,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                     T zl[NLOC];
 #pragma unroll
                     for (int a = 0; a < NLOC; ++a) zl[a] = T(0);
-                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, A.Epad, [&](int a, int q, T mm) {
+                    for_packed<NLOC, T, S>(static_cast<const S*>(A.pk), e0 + e, [&](int a, int q, T mm) {
                         if (OP == OP_DIAG) {
                             if (q == a) zl[a] = mm;
                         } else {
@@ -791,6 +803,145 @@ size_t block_smem_bytes(const BlockArgs& A, bool mr = false) {
     return 128 + ((A.max_pkt + 127u) & ~127u) + xsb + sizeof(T) * (((size_t)NLOC * A.max_ne * cw + 3) & ~(size_t)3);
 }
 
+// ---- many right-hand sides, streamed cell matrices: cell products + dof gather -----------
+// From kCellMrMinRhs right-hand sides on (n_loc <= 48), the apply runs as two kernels around a
+// dof-sorted array of copies (the incidence-gather form of P^T):
+//   k_cell_mr: one CTA per half tile of 16 cells (packet.h layout): the 16 cells' packed
+//     matrices arrive in shared memory by bulk copies (one 256-byte run per 16-byte group), and
+//     each warp takes (cell, 32 right-hand sides) items, lane = right-hand side: the local
+//     vector and the accumulators stay in registers, every matrix group is one broadcast
+//     shared-memory read for the 32 lanes, so each matrix byte feeds 32 right-hand sides; the
+//     signed product a of cell e goes to its copy slot's row of R values;
+//   k_dof_gather: y[u][r] = sum of dof u's copy rows in slot order (times 1/d for BRAS).
+// Every sum has a fixed order: results are bit-reproducible.
+constexpr int kCellMrMinRhs = 16;
+constexpr int kCellMrMaxLoc = 48;  // local vector and accumulators in registers
+constexpr int kCellMrCells = 16;   // cells of one CTA (half of a 32-cell tile)
+
+template <int NLOC, typename S>
+__host__ __device__ constexpr int mr_groups() {
+    return (NLOC * (NLOC + 1) / 2 + PkVec<S>::G - 1) / PkVec<S>::G;
+}
+template <int NLOC, typename S>
+constexpr size_t cell_mr_smem_bytes() {
+    return 128 + (size_t)mr_groups<NLOC, S>() * kCellMrCells * 16;
+}
+
+template <int NLOC, typename T, typename S, int OP>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+k_cell_mr(const BlockArgs A, const T* __restrict__ x, T* __restrict__ cp, int R) {
+    using V = typename PkVec<S>::V;
+    constexpr int G = PkVec<S>::G, NG = mr_groups<NLOC, S>(), NC = kCellMrCells;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    const V* mat = reinterpret_cast<const V*>(smem_raw + 128);   // [g][cell] groups
+    const int ht = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t e0 = (int64_t)ht * NC;
+    const int ncell = (int)(A.n_cell - e0 < NC ? A.n_cell - e0 : NC);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // group g of this half tile: NC * 16 contiguous bytes (the tile's 512-byte row g)
+        const unsigned char* src = static_cast<const unsigned char*>(A.pk) +
+                                   ((((size_t)(ht >> 1) * NG) << 5) + (size_t)(ht & 1) * NC) * 16;
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)NG * NC * 16);
+        __syncwarp();
+        for (int g = lane; g < NG; g += 32)
+            bulk_copy_g2s(smem_raw + 128 + (size_t)g * NC * 16, src + ((size_t)g << 5) * 16, NC * 16, bar);
+    }
+    const bool ok = cta_wait(bar, 0, A.status, true);
+    if (!ok) {
+        if (tid == 0) mbar_wait_bounded(bar, A.status);   // let the copies land before exiting
+        return;
+    }
+    const T* dinv = static_cast<const T*>(A.dinv);
+    const int nch = (R + 31) >> 5;
+    for (int it = warp; it < ncell * nch; it += (int)(blockDim.x >> 5)) {
+        const int c = it / nch;
+        const int r = (it - c * nch) * 32 + lane;
+        const bool act = r < R;
+        const int64_t e = e0 + c;
+        const int32_t* lg = A.mr_l2g + e * NLOC;
+        T xl[NLOC], zl[NLOC];
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a) {
+            const int32_t gd = __ldg(lg + a);
+            const int64_t u = gd & 0x7fffffff;
+            T v = act ? __ldg(x + u * R + r) : T(0);
+            if (OP == OP_BRAS) v *= __ldg(dinv + u);
+            xl[a] = gd < 0 ? -v : v;
+            zl[a] = T(0);
+        }
+        const V* mv = mat + c;
+        int a = 0, q = 0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const V v = mv[g * NC];
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                if (g * G + j < NLOC * (NLOC + 1) / 2) {
+                    const T m = vec_elem<T>(v, j);
+                    zl[a] = fma(m, xl[q], zl[a]);
+                    if (q < a) zl[q] = fma(m, xl[a], zl[q]);
+                    if (++q > a) {
+                        ++a;
+                        q = 0;
+                    }
+                }
+            }
+        }
+        if (act) {
+            const int32_t* sl = A.mr_slot + e * NLOC;
+#pragma unroll
+            for (int b = 0; b < NLOC; ++b) {
+                const T v = __ldg(lg + b) < 0 ? -zl[b] : zl[b];
+                cp[(int64_t)__ldg(sl + b) * R + r] = v;
+            }
+        }
+    }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_dof_gather(const BlockArgs A, const T* __restrict__ cp, T* __restrict__ y,
+                                                    int R) {
+    const int64_t total = A.n_dof * R;
+    const T* dinv = static_cast<const T*>(A.dinv);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = i / R;
+        const int r = (int)(i - u * R);
+        const int64_t s0 = __ldg(A.mr_off + u), s1 = __ldg(A.mr_off + u + 1);
+        T acc = T(0);
+        for (int64_t s = s0; s < s1; ++s) acc += __ldg(cp + s * R + r);
+        y[i] = (OP == OP_BRAS) ? acc * __ldg(dinv + u) : acc;
+    }
+}
+
+template <int NLOC, typename T, typename S, int OP>
+cudaError_t launch_cell_mr(const BlockArgs& A, const T* x, T* y, T* cp, int nrhs, cudaStream_t st) {
+    auto kern = k_cell_mr<NLOC, T, S, OP>;
+    const size_t smem = cell_mr_smem_bytes<NLOC, S>();
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int nct = (int)((A.n_cell + kCellMrCells - 1) / kCellMrCells);
+    kern<<<nct, 256, smem, st>>>(A, x, cp, nrhs);
+    count_launch(1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int nb = (int)std::min<int64_t>((A.n_dof * nrhs + 255) / 256, 148 * 16);
+    k_dof_gather<T, OP><<<nb, 256, 0, st>>>(A, cp, y, nrhs);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// The many-right-hand-side path applies (kernel family, n_loc, call)
+template <int NLOC, int KIND, int OP>
+__host__ __device__ constexpr bool cell_mr_kind() {
+    return KIND == KIND_PACKED && NLOC <= kCellMrMaxLoc && OP != OP_DIAG;
+}
+inline bool cell_mr_call(const BlockArgs& A, int nrhs) { return A.mr_l2g != nullptr && nrhs >= kCellMrMinRhs; }
+
 // Largest dynamic shared memory one CTA may opt into on the current device.
 int smem_optin_bytes();
 // Shared memory of one SM of the current device.
@@ -811,6 +962,9 @@ template <int NLOC, typename T, typename S, int KIND, int OP>
 cudaError_t launch_block(const BlockArgs& A, const CombineArgs& G, int nblk, const T* x, T* y, T* part, int nrhs,
                          cudaStream_t st) {
     // multi-RHS items hold their local vector and accumulators in registers: n_loc <= 48
+    if constexpr (cell_mr_kind<NLOC, KIND, OP>()) {
+        if (cell_mr_call(A, nrhs)) return launch_cell_mr<NLOC, T, S, OP>(A, x, y, part, nrhs, st);
+    }
     constexpr bool kMR = NLOC <= 48;
     const bool mr = kMR && nrhs > 1 && OP != OP_DIAG &&
                     block_smem_bytes<NLOC, T, KIND>(A, true) <= (size_t)smem_optin_bytes();

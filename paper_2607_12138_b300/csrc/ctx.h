@@ -80,6 +80,12 @@ struct bras_ctx {
     unsigned char* pkt = nullptr;
     uint32_t max_pkt = 0;
 
+    // many right-hand sides on streamed cell matrices (max_nrhs >= 16, n_loc <= 48): maps in
+    // internal cell order (bit 31 = sign of P), dof-sorted copy slots, first slot of each dof
+    int32_t* mr_l2g = nullptr;
+    int32_t* mr_slot = nullptr;
+    int64_t* mr_off = nullptr;
+
     // per dof
     double* dinv64 = nullptr;
     float* dinv32 = nullptr;

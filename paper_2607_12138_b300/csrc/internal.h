@@ -11,6 +11,7 @@ void set_detail(int64_t d);
 void* dalloc_bytes(bras_ctx* c, size_t bytes);
 void dfree(bras_ctx* c, void* p);
 int ensure_part(bras_ctx* c, int nrhs);
+size_t part_entries(const bras_ctx* c, int nrhs);
 BlockArgs shape_args(const HostTables& t);
 size_t block_smem_estimate(int nloc, int tsize, bool h1, const HostTables& t, int cw = 1);
 size_t mr_smem_estimate(const bras_ctx* c, int nloc, bool h1, bool tc, const HostTables& t);

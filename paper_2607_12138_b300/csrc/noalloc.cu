@@ -51,7 +51,7 @@ extern "C" int bras_apply_noalloc(const bras_ctx* ctx, int precision, const void
     if (!ctx || !x || !y || nrhs < 1 || precision < 0 || precision > 2) return BRAS_ERR_INVALID;
     if (!has_precision(ctx, precision) || (precision == BRAS_FP64 && !has_fp64_bras(ctx))) return BRAS_ERR_PRECISION;
     const size_t w = precision == BRAS_FP64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)ctx->npart * (size_t)nrhs * w;
+    const size_t need = part_entries(ctx, nrhs) * w;
     if (need > kScratchBytes) {
         set_detail((int64_t)need);
         return BRAS_ERR_TOO_LARGE;

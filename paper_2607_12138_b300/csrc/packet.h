@@ -32,12 +32,16 @@ BRAS_HD inline uint32_t pkt_size_a(uint32_t nu, bool scatter) {
 BRAS_HD inline uint32_t pkt_off_pos(uint32_t m) { return pad16(2u * m); }
 BRAS_HD inline uint32_t pkt_size_b(uint32_t m, bool scatter) { return (scatter ? 2u : 1u) * pad16(2u * m); }
 
-// Per-cell packed symmetric matrices (lower triangle by rows, entry idx = a (a + 1) / 2 + q)
-// are stored vector-interleaved: groups of G consecutive entries of one cell are contiguous
-// (16 bytes: G = 4 floats, 8 bfloat16, 2 doubles), groups of consecutive cells follow, so that
-// each thread of a warp loads 16 bytes of its own cell and the warp reads whole sectors.
-BRAS_HD inline size_t pk_index(int idx, int64_t e, int64_t Epad, int G) {
-    return ((size_t)(idx / G) * (size_t)Epad + (size_t)e) * (size_t)G + (size_t)(idx % G);
-}
+// Per-cell packed symmetric matrices (lower triangle by rows, entry idx = a (a + 1) / 2 + q,
+// npk entries a cell) are stored in tiles of 32 consecutive cells: groups of G consecutive
+// entries of one cell are contiguous (16 bytes: G = 4 floats, 8 bfloat16, 2 doubles), group g
+// of the tile's 32 cells forms one 512-byte row, and the tile's rows follow in g order.  Each
+// thread of a warp loads 16 bytes of its own cell, the warp reads whole rows, and a warp of
+// 32 consecutive cells streams its tile front to back.  Cell counts are padded to a multiple
+// of 32.
 BRAS_HD inline int pk_groups(int npk, int G) { return (npk + G - 1) / G; }
+BRAS_HD inline size_t pk_index(int idx, int64_t e, int npk, int G) {
+    const size_t ng = (size_t)pk_groups(npk, G);
+    return (((((size_t)(e >> 5) * ng) + (size_t)(idx / G)) << 5) + (size_t)(e & 31)) * (size_t)G + (size_t)(idx % G);
+}
 }  // namespace bras

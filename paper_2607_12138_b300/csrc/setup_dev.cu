@@ -134,8 +134,8 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
         for (int i = 0; i < n; ++i)
             for (int j = lane; j <= i; j += 32) {
                 const int idx = i * (i + 1) / 2 + j;
-                if (Mpk64) Mpk64[pk_index(idx, e, Epad, 2)] = A[i * n + j];
-                if (Mpk32) Mpk32[pk_index(idx, e, Epad, 4)] = (float)A[i * n + j];
+                if (Mpk64) Mpk64[pk_index(idx, e, n * (n + 1) / 2, 2)] = A[i * n + j];
+                if (Mpk32) Mpk32[pk_index(idx, e, n * (n + 1) / 2, 4)] = (float)A[i * n + j];
             }
         __syncwarp();
         if (!warp_cholesky(A, n, lane)) {
@@ -160,8 +160,8 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
             double s = 0;
             for (int k = i; k < n; ++k) s += W[k * n + i] * W[k * n + j];
             const int idx = i * (i + 1) / 2 + j;
-            if (Minv64) Minv64[pk_index(idx, e, Epad, 2)] = s;
-            if (Minv32) Minv32[pk_index(idx, e, Epad, 4)] = (float)s;
+            if (Minv64) Minv64[pk_index(idx, e, n * (n + 1) / 2, 2)] = s;
+            if (Minv32) Minv32[pk_index(idx, e, n * (n + 1) / 2, 4)] = (float)s;
             A[i * n + j] = s;
             A[j * n + i] = s;
         }
@@ -186,7 +186,7 @@ __global__ void k_element_inverse(int n, int64_t E, int64_t Epad, const double* 
             for (int i = 0; i < n; ++i)
                 for (int j = lane; j <= i; j += 32) {
                     const double v = A[i * n + j] + (i == j ? shift : 0.0);
-                    Minvbf[pk_index(i * (i + 1) / 2 + j, e, Epad, 8)] = __float2bfloat16_rn((float)v);
+                    Minvbf[pk_index(i * (i + 1) / 2 + j, e, n * (n + 1) / 2, 8)] = __float2bfloat16_rn((float)v);
                 }
         }
         __syncwarp();
@@ -242,7 +242,7 @@ __global__ void k_row_bound(int n, int64_t E, int64_t Epad, const S* __restrict_
             double sum = 0.0;
             for (int q = 0; q < n; ++q) {
                 const int i = a >= q ? a * (a + 1) / 2 + q : q * (q + 1) / 2 + a;
-                sum += pk_abs(pk, pk_index(i, e, Epad, G));
+                sum += pk_abs(pk, pk_index(i, e, n * (n + 1) / 2, G));
             }
             best = fmax(best, sum);
         }

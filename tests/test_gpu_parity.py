@@ -97,6 +97,38 @@ def test_multi_rhs_interleaved(case, nrhs):
         assert rel_err(ym32[:, r].cpu(), ctx.mass_apply(col.float(), B.FP32).cpu()) <= 1e-6
 
 
+@pytest.mark.parametrize("case", ["hcurl3", "hdiv3", "hdiv1_signed", "hcurl2d_1_signed", "bdm2", "hcurl2"])
+@pytest.mark.parametrize("nrhs", [16, 20, 64])
+def test_many_rhs_cell_products(case, nrhs):
+    """A context built for many right-hand sides (max_nrhs >= 16, n_loc <= 48) applies the
+    streamed cell matrices to 32 right-hand sides per warp and sums each dof's copies in its
+    dof-sorted order: every precision against the oracle, every column against the one-RHS
+    apply (a different summation order: agreement to rounding), ragged last lane group
+    (R = 20), bit-identical repeats, and a mixed solve of all right-hand sides."""
+    mesh, pr, ctx = _setup(case, max_nrhs=64)
+    space = SMALL_CASES[case][1]
+    x, xt = _vec(pr.n_dof, nrhs, seed=7)
+    yb, ym = ctx.bras_apply(xt), ctx.mass_apply(xt)
+    assert rel_err(yb.cpu(), pr.B @ x) <= 1e-12
+    assert rel_err(ym.cpu(), pr.M @ x) <= 1e-12
+    assert rel_err(ctx.mass_apply(xt, B.FP64X).cpu(), pr.M @ x) <= 1e-12
+    x32 = xt.float()
+    yb32, ym32 = ctx.bras_apply(x32, B.FP32), ctx.mass_apply(x32, B.FP32)
+    assert rel_err(yb32.cpu(), pr.B @ x) <= TOL32[space]
+    assert rel_err(ym32.cpu(), pr.M @ x) <= TOL32[space]
+    assert rel_err(ctx.bras_apply(x32, B.BF16).cpu(), pr.B @ x) <= TOL16
+    for r in (0, 17 % nrhs, nrhs - 1):
+        col = xt[:, r].contiguous()
+        assert rel_err(yb[:, r].cpu(), ctx.bras_apply(col).cpu()) <= 1e-14
+        assert rel_err(yb32[:, r].cpu(), ctx.bras_apply(col.float(), B.FP32).cpu()) <= 1e-6
+    assert torch.equal(ctx.bras_apply(x32, B.FP32), yb32) and torch.equal(ctx.mass_apply(xt), ym)
+    xs, its, rel, st = ctx.pcg_solve(xt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
+    assert st == B.OK
+    xg = xs.cpu().numpy()
+    for r in (0, nrhs - 1):
+        assert np.linalg.norm(x[:, r] - pr.M @ xg[:, r]) <= 1e-10 * np.linalg.norm(x[:, r])
+
+
 @pytest.mark.parametrize("case", ["3d_p4", "hcurl3"])
 def test_bit_reproducible(case):
     mesh, pr, ctx = _setup(case)
