@@ -423,6 +423,12 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
             cudaStreamSynchronize(st) != cudaSuccess)
             return BRAS_ERR_CUDA;
         if (hbad != none) { set_detail((int64_t)hbad); return BRAS_ERR_NOT_SPD; }
+        // many right-hand sides: the FP64 cell matrices as float pairs for the float-float
+        // refinement residual
+        if (c->mr_l2g) {
+            if (!(c->Mpkdf = dalloc<float2>(c, cnt))) return BRAS_ERR_OOM;
+            if (run_split_pairs(c->Mpk64, c->Mpkdf, cnt, st) != cudaSuccess) return BRAS_ERR_CUDA;
+        }
         // exponent bounds of the cells' row abs-sums (plus one for the FP32 / bf16 roundings)
         int* eb = dalloc<int>(c, 2);
         if (!eb) return BRAS_ERR_OOM;
@@ -607,6 +613,7 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     // FP64 kernels accumulate in one 64-bit word per dof; FP32, bf16 and the H1 float-float mass
     // apply (BRAS_FP64X) in two 32-bit words, with their own splits
     const bool df = prec == BRAS_FP64X && c->space == BRAS_H1 && op == OP_MASS;
+    const bool pk_df = prec == BRAS_FP64X && c->space != BRAS_H1 && op == OP_MASS;
     const bool acc64 = prec == BRAS_FP64 || (prec == BRAS_FP64X && !df);
     if (prec == BRAS_FP64X) prec = BRAS_FP64;
     LaunchCommon L{};
@@ -632,6 +639,7 @@ LaunchCommon make_launch(const bras_ctx* c, int prec, int op) {
     A.dinv = prec == BRAS_FP64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
     A.n_dof = c->n;
     A.n_cell = c->E;
+    A.pk_df = pk_df ? c->Mpkdf : nullptr;
     const bool f64 = prec == BRAS_FP64;
     if (c->space == BRAS_H1) {
         if (op == OP_BRAS) {

@@ -71,6 +71,9 @@ struct BlockArgs {
     const void* dinv;          // T[n]
     int64_t n_dof;
     int64_t n_cell;
+    // float-float copy of the FP64 cell matrices (hi, lo per entry, FP64 layout): set for the
+    // float-float mass apply (BRAS_FP64X) of a many-right-hand-side context, else null
+    const float2* pk_df;
 };
 
 // Shared dofs for the combine pass (tables.cpp), in group order: item j = (global dof, group g)
@@ -904,17 +907,106 @@ k_cell_mr(const BlockArgs A, const T* __restrict__ x, T* __restrict__ cp, int R)
     }
 }
 
+// The same with FP64 vectors and float-float cell products (the refinement residual b - M x of
+// the mixed solve on many right-hand sides): M_K as (hi, lo) float pairs, x split once per
+// value, every product term compensated (df_term, about 2^-48), each result rounded to FP64
+// once.  B300 runs FP64 arithmetic at 1/64 of the FP32 rate; this runs on the FP32 units.
+template <int NLOC>
+__global__ void __launch_bounds__(256, 1)
+k_cell_mr_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__ cp, int R) {
+    constexpr int NPK = NLOC * (NLOC + 1) / 2, NG = (NPK + 1) / 2, NC = kCellMrCells;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    const float4* mat = reinterpret_cast<const float4*>(smem_raw + 128);   // [g][cell]: two (hi, lo) entries
+    const int ht = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t e0 = (int64_t)ht * NC;
+    const int ncell = (int)(A.n_cell - e0 < NC ? A.n_cell - e0 : NC);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.pk_df) +
+                                   ((((size_t)(ht >> 1) * NG) << 5) + (size_t)(ht & 1) * NC) * 16;
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)NG * NC * 16);
+        __syncwarp();
+        for (int g = lane; g < NG; g += 32)
+            bulk_copy_g2s(smem_raw + 128 + (size_t)g * NC * 16, src + ((size_t)g << 5) * 16, NC * 16, bar);
+    }
+    if (!cta_wait(bar, 0, A.status, true)) {
+        if (tid == 0) mbar_wait_bounded(bar, A.status);
+        return;
+    }
+    const int nch = (R + 31) >> 5;
+    for (int it = warp; it < ncell * nch; it += (int)(blockDim.x >> 5)) {
+        const int c = it / nch;
+        const int r = (it - c * nch) * 32 + lane;
+        const bool act = r < R;
+        const int64_t e = e0 + c;
+        const int32_t* lg = A.mr_l2g + e * NLOC;
+        float xh[NLOC], xl[NLOC], zh[NLOC], zl[NLOC];
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a) {
+            const int32_t gd = __ldg(lg + a);
+            double v = act ? __ldg(x + (int64_t)(gd & 0x7fffffff) * R + r) : 0.0;
+            if (gd < 0) v = -v;
+            xh[a] = (float)v;
+            xl[a] = (float)(v - (double)xh[a]);
+            zh[a] = zl[a] = 0.f;
+        }
+        const float4* mv = mat + c;
+        int a = 0, q = 0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const float4 v = mv[g * NC];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (2 * g + j < NPK) {
+                    const float mh = j ? v.z : v.x, ml = j ? v.w : v.y;
+                    df_term(mh, ml, xh[q], xl[q], zh[a], zl[a]);
+                    if (q < a) df_term(mh, ml, xh[a], xl[a], zh[q], zl[q]);
+                    if (++q > a) {
+                        ++a;
+                        q = 0;
+                    }
+                }
+            }
+        }
+        if (act) {
+            const int32_t* sl = A.mr_slot + e * NLOC;
+#pragma unroll
+            for (int b = 0; b < NLOC; ++b) {
+                const double v = (double)zh[b] + (double)zl[b];
+                cp[(int64_t)__ldg(sl + b) * R + r] = __ldg(lg + b) < 0 ? -v : v;
+            }
+        }
+    }
+}
+
+// One thread per (dof, rhs): consecutive threads take consecutive right-hand sides of a dof,
+// so every copy row is one coalesced read; a dof's first four copies are loaded together (more
+// bytes in flight per thread), and each dof adds its copies in slot order.
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_dof_gather(const BlockArgs A, const T* __restrict__ cp, T* __restrict__ y,
                                                     int R) {
+    constexpr int C = 4;
     const int64_t total = A.n_dof * R;
     const T* dinv = static_cast<const T*>(A.dinv);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = i / R;
         const int r = (int)(i - u * R);
         const int64_t s0 = __ldg(A.mr_off + u), s1 = __ldg(A.mr_off + u + 1);
+        const T* row = cp + s0 * R + r;
+        const int64_t cnt = s1 - s0;
+        T v[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = j < cnt ? __ldg(row + (int64_t)j * R) : T(0);
         T acc = T(0);
-        for (int64_t s = s0; s < s1; ++s) acc += __ldg(cp + s * R + r);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < cnt) acc += v[j];
+        for (int64_t j = C; j < cnt; ++j) acc += __ldg(row + j * R);
         y[i] = (OP == OP_BRAS) ? acc * __ldg(dinv + u) : acc;
     }
 }
@@ -931,6 +1023,22 @@ cudaError_t launch_cell_mr(const BlockArgs& A, const T* x, T* y, T* cp, int nrhs
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int nb = (int)std::min<int64_t>((A.n_dof * nrhs + 255) / 256, 148 * 16);
     k_dof_gather<T, OP><<<nb, 256, 0, st>>>(A, cp, y, nrhs);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <int NLOC>
+cudaError_t launch_cell_mr_df(const BlockArgs& A, const double* x, double* y, double* cp, int nrhs, cudaStream_t st) {
+    auto kern = k_cell_mr_df<NLOC>;
+    const size_t smem = 128 + (size_t)((NLOC * (NLOC + 1) / 2 + 1) / 2) * kCellMrCells * 16;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int nct = (int)((A.n_cell + kCellMrCells - 1) / kCellMrCells);
+    kern<<<nct, 256, smem, st>>>(A, x, cp, nrhs);
+    count_launch(1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int nb = (int)std::min<int64_t>((A.n_dof * nrhs + 255) / 256, 148 * 16);
+    k_dof_gather<double, OP_MASS><<<nb, 256, 0, st>>>(A, cp, y, nrhs);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -963,7 +1071,12 @@ cudaError_t launch_block(const BlockArgs& A, const CombineArgs& G, int nblk, con
                          cudaStream_t st) {
     // multi-RHS items hold their local vector and accumulators in registers: n_loc <= 48
     if constexpr (cell_mr_kind<NLOC, KIND, OP>()) {
-        if (cell_mr_call(A, nrhs)) return launch_cell_mr<NLOC, T, S, OP>(A, x, y, part, nrhs, st);
+        if (cell_mr_call(A, nrhs)) {
+            if constexpr (sizeof(T) == 8 && OP == OP_MASS) {
+                if (A.pk_df) return launch_cell_mr_df<NLOC>(A, x, y, part, nrhs, st);
+            }
+            return launch_cell_mr<NLOC, T, S, OP>(A, x, y, part, nrhs, st);
+        }
     }
     constexpr bool kMR = NLOC <= 48;
     const bool mr = kMR && nrhs > 1 && OP != OP_DIAG &&

@@ -108,6 +108,7 @@ struct bras_ctx {
     double *Mpk64 = nullptr, *Minvpk64 = nullptr;
     float *Mpk32 = nullptr, *Minvpk32 = nullptr;
     __nv_bfloat16* Minvpkbf = nullptr;
+    float2* Mpkdf = nullptr;     // Mpk64 as (hi, lo) float pairs (many-right-hand-side contexts)
 
     // H1 tensor-core path: reference matrices pre-split (TF32 big | remainder) and laid out
     // as the GEMM's shared-memory B operand

@@ -9,13 +9,15 @@
 // FP32 rate:
 //   * x is split once per block-local dof into (vh, vl) with vh + vl = x to 2^-48;
 //   * each cell is split over TPC = ceil(n_loc / 8) threads, thread g owning the output rows
-//     [8g, 8g + 8) of z_K = c_K M_ref x_K (Eq. piola_mass_pullbacks); each row is one
+//     [g R, g R + R) of z_K = c_K M_ref x_K, R = ceil(n_loc / TPC) (35 = 5 x 7, 20 = 3 x 7;
+//     Eq. piola_mass_pullbacks); each row is one
 //     compensated chain (leading product exact by an FMA, cross terms into the low part,
 //     running sum by a two-sum), and c_K multiplies it as a float pair;
 //   * both halves of each product pair go into the dof's exact 64-bit fixed-point accumulator
 //     (apply_kernels.cuh), converted to FP64 once per dof.
-// Eight independent rows per thread and ~60 registers keep many warps in flight; lanes of a
-// warp hold different cells of the same row group, so the rows of M_ref are broadcast reads.
+// Seven or eight independent rows per thread at 48 registers (two CTAs of up to 640 threads
+// per SM) keep many warps in flight; lanes of a warp hold different cells of the same row
+// group, so the rows of M_ref are broadcast reads.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,14 +28,15 @@
 
 namespace bras {
 
-constexpr int kDfRows = 8;   // output rows per thread
+constexpr int kDfRows = 8;   // at most this many output rows per thread
 
 template <int NLOC> struct DfShape {
     static constexpr int TPC = (NLOC + kDfRows - 1) / kDfRows;   // threads per cell
+    static constexpr int ROWS = (NLOC + TPC - 1) / TPC;          // rows per thread (35: 5 x 7)
 };
 
 template <int NLOC>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(640, 2)
 k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__ y, double* __restrict__ part,
            int nrhs) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -114,15 +117,16 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     for (int e = tid % cw; e < ne; e += cw) {
         const double c = static_cast<const double*>(A.scale)[e0 + e];
         const float ch = (float)c, cl = (float)(c - (double)ch);
-        const int a0 = g * kDfRows;
-        float sh[kDfRows], sl[kDfRows];
+        constexpr int RW = DfShape<NLOC>::ROWS;
+        const int a0 = g * RW;
+        float sh[RW], sl[RW];
 #pragma unroll
-        for (int j = 0; j < kDfRows; ++j) sh[j] = sl[j] = 0.f;
+        for (int j = 0; j < RW; ++j) sh[j] = sl[j] = 0.f;
 #pragma unroll 4
         for (int q = 0; q < NLOC; ++q) {
             const float2 v = xs[loc[q * ne + e]];
 #pragma unroll
-            for (int j = 0; j < kDfRows; ++j) {
+            for (int j = 0; j < RW; ++j) {
                 const int a = a0 + j;
                 if (a < NLOC) {
                     const float2 m = Ms[a * NLOC + q];
@@ -131,7 +135,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
             }
         }
 #pragma unroll
-        for (int j = 0; j < kDfRows; ++j) {
+        for (int j = 0; j < RW; ++j) {
             const int a = a0 + j;
             if (a < NLOC) {
                 float zh = 0.f, zl = 0.f;   // (sh + sl) (ch + cl)
@@ -160,8 +164,9 @@ size_t df_smem_bytes(const BlockArgs& A, int threads) {
 template <int NLOC>
 cudaError_t launch_block_df(const BlockArgs& A, const CombineArgs& G, int nblk, const double* x, double* y,
                             double* part, int nrhs, cudaStream_t st) {
-    // cells per row group: whole warps, every cell of the largest block if 1024 threads allow
-    const int cw = std::min((A.max_ne + 31) / 32 * 32, 1024 / DfShape<NLOC>::TPC / 32 * 32);
+    // cells per row group: whole warps, at most 128 (640 threads at n_loc = 35, two CTAs per
+    // SM at 48 registers; larger blocks loop over their cells)
+    const int cw = std::min((A.max_ne + 31) / 32 * 32, 128);
     const int threads = cw * DfShape<NLOC>::TPC;
     const size_t smem = df_smem_bytes<NLOC>(A, threads);
     auto kern = k_block_df<NLOC>;

@@ -266,4 +266,20 @@ template cudaError_t run_row_bound<double>(int, int64_t, int64_t, const double*,
 template cudaError_t run_row_bound<float>(int, int64_t, int64_t, const float*, int*, cudaStream_t);
 template cudaError_t run_row_bound<__nv_bfloat16>(int, int64_t, int64_t, const __nv_bfloat16*, int*, cudaStream_t);
 
+// v -> (hi, lo) = ((float)v, (float)(v - hi)): a float pair within ~2^-48 of v
+__global__ void k_split_pairs(const double* __restrict__ a, float2* __restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        const float h = (float)v;
+        b[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+
+cudaError_t run_split_pairs(const double* a, float2* b, size_t n, cudaStream_t st) {
+    const int nb = (int)std::min<size_t>((n + 255) / 256, 148 * 8);
+    k_split_pairs<<<nb, 256, 0, st>>>(a, b, n);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 }  // namespace bras

@@ -16,6 +16,9 @@ cudaError_t run_element_inverse(int n, int64_t E, int64_t Epad, const double* Rr
                                 __nv_bfloat16* Minvbf, unsigned long long* bad, int* nfixed,
                                 const int32_t* perm, cudaStream_t st);
 
+// b[i] = (hi, lo) float pair of a[i] (hi = a rounded to FP32, lo = the rest rounded)
+cudaError_t run_split_pairs(const double* a, float2* b, size_t n, cudaStream_t st);
+
 // *out = max(*out, exponent bound of the largest row abs-sum of the packed cell matrices)
 template <typename S>
 cudaError_t run_row_bound(int n, int64_t E, int64_t Epad, const S* pk, int* out, cudaStream_t st);
