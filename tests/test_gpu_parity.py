@@ -120,7 +120,8 @@ def test_many_rhs_cell_products(case, nrhs):
     for r in (0, 17 % nrhs, nrhs - 1):
         col = xt[:, r].contiguous()
         assert rel_err(yb[:, r].cpu(), ctx.bras_apply(col).cpu()) <= 1e-14
-        assert rel_err(yb32[:, r].cpu(), ctx.bras_apply(col.float(), B.FP32).cpu()) <= 1e-6
+        # two FP32 paths with different summation orders: each is within TOL32 of the oracle
+        assert rel_err(yb32[:, r].cpu(), ctx.bras_apply(col.float(), B.FP32).cpu()) <= 2 * TOL32[space]
     assert torch.equal(ctx.bras_apply(x32, B.FP32), yb32) and torch.equal(ctx.mass_apply(xt), ym)
     xs, its, rel, st = ctx.pcg_solve(xt, pc=B.PC_BRAS, mode=B.SOLVE_MIXED, rtol=1e-10)
     assert st == B.OK
