@@ -12,7 +12,7 @@
 
 namespace bras {
 
-constexpr int kDotBlocks = 1184;   // 8 per SM on a 148-SM B300 (fixed: it fixes the summation order)
+constexpr int kDotBlocks = 1184;   // at most 8 per SM on a 148-SM B300 (the partial-sum buffer)
 constexpr int kMaxRhs = 256;
 
 // per-slot scalars; S_BN, S_RN = ||b||, ||b - M x|| of the refinement loop
@@ -790,13 +790,23 @@ static SegArgs seg_args(const bras_ctx* c) {
 
 static bool batched(const bras_ctx* c) { return c->n_mesh > 1 && c->nseg > 0; }
 
+// Blocks of the fused reductions over n x R values: about 4,096 values a block (16 per thread),
+// a multiple of the 148 SMs, between 148 and kDotBlocks.  A function of the context's size and
+// R only, so every call of a context sums in the same order (bit-reproducible); small systems
+// get short reduction tails instead of mostly idle blocks.
+static int dot_blocks(const bras_ctx* c, int R) {
+    const int64_t want = (c->n * (int64_t)R + 4095) / 4096;
+    const int64_t b = (want + 147) / 148 * 148;
+    return (int)std::max<int64_t>(148, std::min<int64_t>(kDotBlocks, b));
+}
+
 // Dot products / fused updates on either layout: R interleaved rhs, or (batched) one rhs per
 // mesh with n_mesh scalar slots.
 template <typename TA, typename TB>
 static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, cudaStream_t st) {
     PcgWork* w = c->pcg;
     if (batched(c)) k_seg_dot<TA, TB><<<c->nseg, 256, 0, st>>>(a, b, seg_args(c), fin_args(w, kind));
-    else k_dot<TA, TB><<<kDotBlocks, 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
+    else k_dot<TA, TB><<<dot_blocks(c, R), 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
     count_launch(1);
     return cudaGetLastError();
 }
@@ -815,7 +825,7 @@ static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, i
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
                                                      fin_args(w, kind, ip, cond, in_graph));
     else
-        k_update_xr<T><<<kDotBlocks, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
+        k_update_xr<T><<<dot_blocks(c, R), 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
                                                     fin_args(w, kind, ip, cond, in_graph));
     count_launch(1);
     return cudaGetLastError();
@@ -1055,7 +1065,7 @@ static cudaError_t enqueue_outer_init(bras_ctx* c, int R, cudaGraphConditionalHa
     if (e != cudaSuccess) return e;
     const FinArgs F = fin_args(w, FIN_OUTER_INIT, w->iparam, cond, in_graph);
     if (batched(c)) k_seg_outer_init<<<c->nseg, 256, 0, st>>>(w->xs, w->r, w->bs, seg_args(c), F);
-    else k_outer_init<<<kDotBlocks, 256, 0, st>>>(w->xs, w->r, w->bs, c->n, R, F);
+    else k_outer_init<<<dot_blocks(c, R), 256, 0, st>>>(w->xs, w->r, w->bs, c->n, R, F);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1068,7 +1078,7 @@ static cudaError_t enqueue_inner_start(bras_ctx* c, int R, cudaGraphConditionalH
     if (batched(c))
         k_seg_inner_start<<<c->nseg, 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, seg_args(c), F);
     else
-        k_inner_start<<<kDotBlocks, 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, c->n, R, F);
+        k_inner_start<<<dot_blocks(c, R), 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, c->n, R, F);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1092,7 +1102,7 @@ static int enqueue_outer_post(bras_ctx* c, int R, cudaGraphConditionalHandle con
     RC(run_op(c, BRAS_FP64X, OP_MASS, w->xs, w->q, R, st));
     const FinArgs F = fin_args(w, FIN_OUTER, w->iparam, cond, in_graph);
     if (batched(c)) k_seg_residual_rr<<<c->nseg, 256, 0, st>>>(w->r, w->bs, w->q, seg_args(c), F);
-    else k_residual_rr<<<kDotBlocks, 256, 0, st>>>(w->r, w->bs, w->q, c->n, R, F);
+    else k_residual_rr<<<dot_blocks(c, R), 256, 0, st>>>(w->r, w->bs, w->q, c->n, R, F);
     count_launch(1);
     CK(cudaGetLastError());
     return BRAS_OK;
