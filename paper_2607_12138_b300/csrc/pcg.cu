@@ -6,6 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -790,14 +793,35 @@ static SegArgs seg_args(const bras_ctx* c) {
 
 static bool batched(const bras_ctx* c) { return c->n_mesh > 1 && c->nseg > 0; }
 
-// Blocks of the fused reductions over n x R values: about 4,096 values a block (16 per thread),
-// a multiple of the 148 SMs, between 148 and kDotBlocks.  A function of the context's size and
-// R only, so every call of a context sums in the same order (bit-reproducible); small systems
-// get short reduction tails instead of mostly idle blocks.
-static int dot_blocks(const bras_ctx* c, int R) {
+// Blocks of 256 threads of `kern` that the device keeps resident at once (all SMs), cached per
+// (kernel, device).
+static int resident_blocks(const void* kern) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kern, dev);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess) cudaGetLastError();
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int v = std::max(1, per_sm) * std::max(1, sms);
+    cache[key] = v;
+    return v;
+}
+
+// Blocks of a fused reduction over n x R values: about 4,096 values a block (16 per thread),
+// a multiple of the 148 SMs, between 148 and one wave of resident blocks (at most
+// kDotBlocks): the grid-stride loops then run in a single wave, without a partial second one.
+// A function of the context's size, R and the kernel only, so every call of a context sums in
+// the same order (bit-reproducible); small systems get short reduction tails.
+static int dot_blocks(const bras_ctx* c, int R, const void* kern) {
     const int64_t want = (c->n * (int64_t)R + 4095) / 4096;
     const int64_t b = (want + 147) / 148 * 148;
-    return (int)std::max<int64_t>(148, std::min<int64_t>(kDotBlocks, b));
+    const int64_t cap = std::min<int64_t>(kDotBlocks, resident_blocks(kern));
+    return (int)std::max<int64_t>(std::min<int64_t>(148, cap), std::min<int64_t>(cap, b));
 }
 
 // Dot products / fused updates on either layout: R interleaved rhs, or (batched) one rhs per
@@ -806,7 +830,7 @@ template <typename TA, typename TB>
 static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, cudaStream_t st) {
     PcgWork* w = c->pcg;
     if (batched(c)) k_seg_dot<TA, TB><<<c->nseg, 256, 0, st>>>(a, b, seg_args(c), fin_args(w, kind));
-    else k_dot<TA, TB><<<dot_blocks(c, R), 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
+    else k_dot<TA, TB><<<dot_blocks(c, R, (const void*)k_dot<TA, TB>), 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
     count_launch(1);
     return cudaGetLastError();
 }
@@ -825,7 +849,7 @@ static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, i
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
                                                      fin_args(w, kind, ip, cond, in_graph));
     else
-        k_update_xr<T><<<dot_blocks(c, R), 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
+        k_update_xr<T><<<dot_blocks(c, R, (const void*)k_update_xr<T>), 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
                                                     fin_args(w, kind, ip, cond, in_graph));
     count_launch(1);
     return cudaGetLastError();
@@ -1065,7 +1089,7 @@ static cudaError_t enqueue_outer_init(bras_ctx* c, int R, cudaGraphConditionalHa
     if (e != cudaSuccess) return e;
     const FinArgs F = fin_args(w, FIN_OUTER_INIT, w->iparam, cond, in_graph);
     if (batched(c)) k_seg_outer_init<<<c->nseg, 256, 0, st>>>(w->xs, w->r, w->bs, seg_args(c), F);
-    else k_outer_init<<<dot_blocks(c, R), 256, 0, st>>>(w->xs, w->r, w->bs, c->n, R, F);
+    else k_outer_init<<<dot_blocks(c, R, (const void*)k_outer_init), 256, 0, st>>>(w->xs, w->r, w->bs, c->n, R, F);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1078,7 +1102,8 @@ static cudaError_t enqueue_inner_start(bras_ctx* c, int R, cudaGraphConditionalH
     if (batched(c))
         k_seg_inner_start<<<c->nseg, 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, seg_args(c), F);
     else
-        k_inner_start<<<dot_blocks(c, R), 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32, w->p32, c->n, R, F);
+        k_inner_start<<<dot_blocks(c, R, (const void*)k_inner_start), 256, 0, st>>>(w->r, w->sc + S_SCALE * S, w->r32, w->x32,
+                                                                              w->p32, c->n, R, F);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1102,7 +1127,7 @@ static int enqueue_outer_post(bras_ctx* c, int R, cudaGraphConditionalHandle con
     RC(run_op(c, BRAS_FP64X, OP_MASS, w->xs, w->q, R, st));
     const FinArgs F = fin_args(w, FIN_OUTER, w->iparam, cond, in_graph);
     if (batched(c)) k_seg_residual_rr<<<c->nseg, 256, 0, st>>>(w->r, w->bs, w->q, seg_args(c), F);
-    else k_residual_rr<<<dot_blocks(c, R), 256, 0, st>>>(w->r, w->bs, w->q, c->n, R, F);
+    else k_residual_rr<<<dot_blocks(c, R, (const void*)k_residual_rr), 256, 0, st>>>(w->r, w->bs, w->q, c->n, R, F);
     count_launch(1);
     CK(cudaGetLastError());
     return BRAS_OK;
