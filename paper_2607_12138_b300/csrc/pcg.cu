@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -311,9 +312,44 @@ __device__ void fin_tail(const FinArgs& F, int R, int cnt) {
 }
 
 // `red` holds this block's 256 per-thread sums (thread t: rhs t % R, group t / R).
+// Fixed-order sum of a 256-thread block's values (one right-hand side): a shuffle tree within
+// each warp, then the eight warp sums in warp order.  Every thread gets the total.
+__device__ __forceinline__ double block_sum_fixed(double v, double* wsum) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += wsum[w];
+    return s;
+}
+
 __device__ void block_partial_and_finish(const FinArgs& F, int R, double* red) {
     const int tid = threadIdx.x, J = 256 / R, r = tid % R, j = tid / R;
     __shared__ unsigned int s_last;
+    if (R == 1) {
+        // one right-hand side: shuffle trees instead of the shared-memory tree
+        __shared__ double wsum[8];
+        const double bs = block_sum_fixed(red[tid], wsum);
+        if (tid == 0) {
+            F.partial[blockIdx.x] = bs;
+            __threadfence();
+            s_last = (atomicAdd(F.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        double v = 0.0;
+        for (int g = tid; g < (int)gridDim.x; g += 256) v += __ldcg(&F.partial[g]);
+        __syncthreads();   // wsum is reused
+        const double total = block_sum_fixed(v, wsum);
+        if (tid == 0) {
+            apply_fin(F, 1, 0, total);
+            fin_tail(F, 1, F.flags[0]);
+            *F.ticket = 0u;
+        }
+        return;
+    }
     // fixed tree over the J groups of this block
     for (int h = 1; h < J; h *= 2) {
         __syncthreads();
@@ -375,13 +411,48 @@ template <typename TA, typename TB> struct DotType { using type = double; };
 template <> struct DotType<float, float> { using type = float; };
 
 // Thread t of a block handles rhs t % R of rows t / R, so every thread sticks to one rhs.
+// One right-hand side with 16-byte aligned vectors (vec): 16-byte loads, four in flight per
+// array and thread, the n mod W last values taken one each by the first threads.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int64_t n, int R,
-                                             FinArgs F) {
+                                             int vec, FinArgs F) {
     using TD = typename DotType<TA, TB>::type;
     __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
     double acc = 0.0;
+    if constexpr (std::is_same<TA, TB>::value) {
+        if (vec) {
+            using V = typename Vec4<TA>::type;
+            constexpr int W = Vec4<TA>::W;
+            const V* av = reinterpret_cast<const V*>(a);
+            const V* bv = reinterpret_cast<const V*>(b);
+            const int64_t nvec = n / W, stride = (int64_t)gridDim.x * 256;
+            const int64_t gid = (int64_t)blockIdx.x * 256 + tid;
+            DotAcc<TD> c[4];
+            int64_t i = gid;
+            for (; i + 3 * stride < nvec; i += 4 * stride) {
+                V x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    x[u] = av[i + u * stride];
+                    y[u] = bv[i + u * stride];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int j = 0; j < W; ++j) c[u].add((TD)vget(x[u], j), (TD)vget(y[u], j));
+            }
+            for (; i < nvec; i += stride) {
+                V x = av[i], y = bv[i];
+#pragma unroll
+                for (int j = 0; j < W; ++j) c[0].add((TD)vget(x, j), (TD)vget(y, j));
+            }
+            if (gid < n - nvec * W) c[1].add((TD)a[nvec * W + gid], (TD)b[nvec * W + gid]);
+            red[tid] = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+            block_partial_and_finish(F, 1, red);
+            return;
+        }
+    }
     if (lr < rows) {
         // four independent accumulators (loads in flight), combined in a fixed order
         const int64_t stride = (int64_t)gridDim.x * rows;
@@ -400,14 +471,72 @@ __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB*
     block_partial_and_finish(F, R, red);
 }
 
-// x += alpha p; r -= alpha q; and r.r with the convergence test  (fused, one pass)
+// x += alpha p; r -= alpha q; and r.r with the convergence test  (fused, one pass; vec: one
+// right-hand side, 16-byte aligned vectors, 16-byte accesses as in k_dot)
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                    const T* __restrict__ q, const double* __restrict__ alpha,
-                                                   int64_t n, int R, FinArgs F) {
+                                                   int64_t n, int R, int vec, FinArgs F) {
     __shared__ double red[256];
     const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
     double acc = 0.0;
+    if (vec) {
+        using V = typename Vec4<T>::type;
+        constexpr int W = Vec4<T>::W;
+        const T a = (T)alpha[0];
+        V* xv = reinterpret_cast<V*>(x);
+        V* rv = reinterpret_cast<V*>(r);
+        const V* pv = reinterpret_cast<const V*>(p);
+        const V* qv = reinterpret_cast<const V*>(q);
+        const int64_t nvec = n / W, stride = (int64_t)gridDim.x * 256;
+        const int64_t gid = (int64_t)blockIdx.x * 256 + tid;
+        DotAcc<T> c[4];
+        int64_t i = gid;
+        for (; i + 3 * stride < nvec; i += 4 * stride) {
+            V pp[4], qq[4], xx[4], ro[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pp[u] = pv[i + u * stride];
+                qq[u] = qv[i + u * stride];
+                xx[u] = xv[i + u * stride];
+                ro[u] = rv[i + u * stride];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    vget(xx[u], j) = fma(a, vget(pp[u], j), vget(xx[u], j));
+                    const T v = fma(-a, vget(qq[u], j), vget(ro[u], j));
+                    vget(ro[u], j) = v;
+                    c[u].add(v, v);
+                }
+                xv[i + u * stride] = xx[u];
+                rv[i + u * stride] = ro[u];
+            }
+        }
+        for (; i < nvec; i += stride) {
+            V pp = pv[i], qq = qv[i], xx = xv[i], ro = rv[i];
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                vget(xx, j) = fma(a, vget(pp, j), vget(xx, j));
+                const T v = fma(-a, vget(qq, j), vget(ro, j));
+                vget(ro, j) = v;
+                c[0].add(v, v);
+            }
+            xv[i] = xx;
+            rv[i] = ro;
+        }
+        if (gid < n - nvec * W) {
+            const int64_t k = nvec * W + gid;
+            x[k] = fma(a, p[k], x[k]);
+            const T v = fma(-a, q[k], r[k]);
+            r[k] = v;
+            c[1].add(v, v);
+        }
+        red[tid] = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+        block_partial_and_finish(F, 1, red);
+        return;
+    }
     if (lr < rows) {
         const T a = (T)alpha[rr];
         const int64_t stride = (int64_t)gridDim.x * rows;
@@ -792,6 +921,7 @@ static SegArgs seg_args(const bras_ctx* c) {
 }
 
 static bool batched(const bras_ctx* c) { return c->n_mesh > 1 && c->nseg > 0; }
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Blocks of 256 threads of `kern` that the device keeps resident at once (all SMs), cached per
 // (kernel, device).
@@ -830,7 +960,11 @@ template <typename TA, typename TB>
 static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, cudaStream_t st) {
     PcgWork* w = c->pcg;
     if (batched(c)) k_seg_dot<TA, TB><<<c->nseg, 256, 0, st>>>(a, b, seg_args(c), fin_args(w, kind));
-    else k_dot<TA, TB><<<dot_blocks(c, R, (const void*)k_dot<TA, TB>), 256, 0, st>>>(a, b, c->n, R, fin_args(w, kind));
+    else {
+        const int vec = (R == 1 && std::is_same<TA, TB>::value && aligned16(a) && aligned16(b)) ? 1 : 0;
+        k_dot<TA, TB><<<dot_blocks(c, R, (const void*)k_dot<TA, TB>), 256, 0, st>>>(a, b, c->n, R, vec,
+                                                                                     fin_args(w, kind));
+    }
     count_launch(1);
     return cudaGetLastError();
 }
@@ -849,8 +983,10 @@ static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, i
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
                                                      fin_args(w, kind, ip, cond, in_graph));
     else
-        k_update_xr<T><<<dot_blocks(c, R, (const void*)k_update_xr<T>), 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
-                                                    fin_args(w, kind, ip, cond, in_graph));
+        k_update_xr<T><<<dot_blocks(c, R, (const void*)k_update_xr<T>), 256, 0, st>>>(
+            x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
+            (R == 1 && aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q)) ? 1 : 0,
+            fin_args(w, kind, ip, cond, in_graph));
     count_launch(1);
     return cudaGetLastError();
 }
