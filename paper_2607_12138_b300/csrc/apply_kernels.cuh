@@ -447,64 +447,39 @@ __device__ __forceinline__ void dof_run_sums(int nu, const uint16_t* incoff, con
     }
 }
 
-// Stage 4: every (shared dof, rhs) output adds the dof's partials in ascending block order
-// (0 + p_0 + p_1 + ...) and stores the total to y (times 1/d for BRAS).  Consecutive threads
-// take consecutive dofs of a group, so the partial reads coalesce and the group's record and
-// slots are shared through L1.  slot_major: partials laid out [npart][nrhs], else
+// Stage 4: one thread per (shared dof, rhs); every dof adds its partials in ascending block
+// order (0 + p_0 + p_1 + ...) and stores the total to y (times 1/d for BRAS).  Consecutive
+// threads take consecutive dofs of a group, so the partial reads coalesce and the group's
+// record and slots are shared through L1.  slot_major: partials laid out [npart][nrhs], else
 // [nrhs][npart].
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_group_combine(const CombineArgs G, const T* __restrict__ part, int64_t npart,
                                                        T* __restrict__ y, int nrhs, int slot_major) {
-    // two outputs a thread and pass, their dependent loads (item -> group record -> slot
-    // entries -> partials) interleaved so that both chains are in flight together
-    constexpr int U = 2, C = 4;
     const int64_t total = G.nsh * nrhs;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < total; q0 += U * stride) {
-        int64_t j[U];
-        int r[U];
-        bool ok[U];
-        int2 it[U];
-        int4 gr[U];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = nrhs == 1 ? q : q / nrhs;
+        const int r = (int)(q - j * nrhs);
+        const int2 it = __ldg(G.items + j);
+        const int4 gr = __ldg(G.grp + it.y);
+        const int i = (int)(j - gr.x), cnt = gr.y;
+        const int32_t* sl = G.grp_slots + gr.z;
+        T acc = T(0);
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+            T v[4];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int64_t q = q0 + k * stride;
-            ok[k] = q < total;
-            j[k] = ok[k] ? (nrhs == 1 ? q : q / nrhs) : 0;
-            r[k] = ok[k] ? (int)(q - j[k] * nrhs) : 0;
-            it[k] = __ldg(G.items + j[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) gr[k] = __ldg(G.grp + it[k].y);
-        int32_t s[U][C];
-#pragma unroll
-        for (int k = 0; k < U; ++k)
-#pragma unroll
-            for (int c = 0; c < C; ++c) s[k][c] = c < gr[k].y ? __ldg(G.grp_slots + gr[k].z + c) : 0;
-        T v[U][C];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int i = (int)(j[k] - gr[k].x);
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const int64_t slot = (int64_t)s[k][c] + i;
-                v[k][c] = c < gr[k].y ? __ldg(part + (slot_major ? slot * nrhs + r[k] : (int64_t)r[k] * npart + slot)) : T(0);
+            for (int k = 0; k < 4; ++k) {
+                if (k0 + k < cnt) {
+                    const int64_t slot = (int64_t)__ldg(sl + k0 + k) + i;
+                    v[k] = __ldg(part + (slot_major ? slot * nrhs + r : (int64_t)r * npart + slot));
+                } else {
+                    v[k] = T(0);
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            if (!ok[k]) continue;
-            const int i = (int)(j[k] - gr[k].x), cnt = gr[k].y;
-            T acc = T(0);
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                if (c < cnt) acc += v[k][c];
-            for (int c = C; c < cnt; ++c) {   // groups of more than four blocks: in order
-                const int64_t slot = (int64_t)__ldg(G.grp_slots + gr[k].z + c) + i;
-                acc += __ldg(part + (slot_major ? slot * nrhs + r[k] : (int64_t)r[k] * npart + slot));
-            }
-            y[(size_t)it[k].x * nrhs + r[k]] = (OP == OP_BRAS) ? div_by_count(acc, __ldg(G.sh_d + j[k])) : acc;
+            for (int k = 0; k < 4; ++k)
+                if (k0 + k < cnt) acc += v[k];
         }
+        y[(size_t)it.x * nrhs + r] = (OP == OP_BRAS) ? div_by_count(acc, __ldg(G.sh_d + j)) : acc;
     }
 }
 
@@ -512,8 +487,7 @@ template <typename T, int OP>
 cudaError_t launch_group_combine(const CombineArgs& G, const T* part, int64_t npart, T* y, int nrhs, bool slot_major,
                                  cudaStream_t st) {
     if (G.nsh <= 0) return cudaSuccess;
-    // one wave (eight 256-thread CTAs an SM at 32 registers), two outputs a thread and pass
-    const int nb = (int)std::min<int64_t>((G.nsh * nrhs + 511) / 512, 148 * 8);
+    const int nb = (int)std::min<int64_t>((G.nsh * nrhs + 255) / 256, 148 * 16);
     k_group_combine<T, OP><<<nb, 256, 0, st>>>(G, part, npart, y, nrhs, slot_major ? 1 : 0);
     count_launch(1);
     return cudaGetLastError();
