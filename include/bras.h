@@ -108,8 +108,9 @@ typedef struct {
     int autotune;        /* 1: at setup, time the FP32 (else FP64) BRAS apply for eight cell
                             block sizes (H1 on the FP32 units: 64..1024; H1 with tensor
                             cores: 64..256; H(curl)/H(div): 32..256) whose kernels fit shared
-                            memory and keep the fastest (one table build and four applies per
-                            candidate; ignored if block_elems is set); 0 = the rule: the largest
+                            memory and keep the fastest (one table build and twelve applies per
+                            candidate, the mean of the last ten kept; ignored if block_elems is
+                            set); 0 = the rule: the largest
                             size up to 256 whose FP32 kernel fits twice per SM              */
 } bras_options;
 

@@ -497,17 +497,21 @@ int setup_impl(bras_ctx* c, int dim, int space, int order, int64_t n_vert, const
             const size_t smr = mr_smem_estimate(c, nloc, space == BRAS_H1, c->use_tc, tt);
             if (smr > (size_t)smem_optin && be > 32) continue;   // keep the multi-RHS kernel usable
             if ((rc = install_tables(c, tt)) || (rc = ensure_part(c, c->max_nrhs))) break;
+            // two warm-up applies, then the mean of ten (candidates within a few percent of
+            // each other need that many to be told apart)
+            constexpr int kWarm = 2, kReps = 10;
             float ms = 0.f;
-            bool okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;   // warm-up
+            bool okr = true;
+            for (int r = 0; r < kWarm && okr; ++r) okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 3 && okr; ++r) okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;
+            for (int r = 0; r < kReps && okr; ++r) okr = run_op(c, prec, OP_BRAS, xv, yv, 1, st) == BRAS_OK;
             cudaEventRecord(e1, st);
             if (!okr || cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = BRAS_ERR_CUDA;
                 break;
             }
             cudaEventElapsedTime(&ms, e0, e1);
-            const float us = 1e3f * ms / 3;
+            const float us = 1e3f * ms / kReps;
             if (c->tune_count < (int)(sizeof(c->tune_be) / sizeof(c->tune_be[0]))) {
                 c->tune_be[c->tune_count] = be;
                 c->tune_us[c->tune_count] = us;
