@@ -28,6 +28,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "packet.h"
 
 namespace bras {
@@ -163,6 +165,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization
+// (launch_pdl) may start while its predecessor in the stream is still running: pdl_launch()
+// lets the successor start launching once every CTA of this kernel has called it, and
+// pdl_wait() blocks until the predecessor has completed with its memory visible.  Kernels call
+// pdl_wait() before their first read of data another kernel may write and before their first
+// global write; before it they only set up shared memory, barriers and copies of tables that
+// never change after setup.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Bounded wait on phase 0 of `bar`: gives up after ~2^22 polls (each try_wait itself
 // suspends for a hardware-chosen interval), records the failure and tells the caller.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
@@ -455,6 +467,8 @@ __device__ __forceinline__ void dof_run_sums(int nu, const uint16_t* incoff, con
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_group_combine(const CombineArgs G, const T* __restrict__ part, int64_t npart,
                                                        T* __restrict__ y, int nrhs, int slot_major) {
+    pdl_launch();
+    pdl_wait();
     const int64_t total = G.nsh * nrhs;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = nrhs == 1 ? q : q / nrhs;
@@ -483,14 +497,32 @@ __global__ void __launch_bounds__(256) k_group_combine(const CombineArgs G, cons
     }
 }
 
+// Launch with programmatic stream serialization (see pdl_wait): the kernel may begin while its
+// predecessor in the stream finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename T, int OP>
 cudaError_t launch_group_combine(const CombineArgs& G, const T* part, int64_t npart, T* y, int nrhs, bool slot_major,
                                  cudaStream_t st) {
     if (G.nsh <= 0) return cudaSuccess;
     const int nb = (int)std::min<int64_t>((G.nsh * nrhs + 255) / 256, 148 * 16);
-    k_group_combine<T, OP><<<nb, 256, 0, st>>>(G, part, npart, y, nrhs, slot_major ? 1 : 0);
+    const cudaError_t err = launch_pdl(k_group_combine<T, OP>, dim3(nb), dim3(256), 0, st, G, part, npart, y, nrhs,
+                                       slot_major ? 1 : 0);
     count_launch(1);
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 __device__ __forceinline__ float4 vsum(float4 a, const float4& b) { vadd(a, b); return a; }
@@ -536,9 +568,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
     const int nint = A.blk_nint[b];
     const uint32_t m = (uint32_t)(ne * NLOC);
     const uint32_t sa = pkt_size_a(nu, !FX), sb = pkt_size_b(m, !FX);
-    // this thread's cell factor (H1, one cell per thread; multi-RHS items read theirs again),
-    // fetched now so that its latency hides behind the copies
-    const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
+    pdl_launch();
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -558,6 +588,9 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             Ms[i] = v;
         }
     }
+    pdl_wait();   // x, the cell factors, y and the partials belong to the stream's order from here
+    // this thread's cell factor (H1, one cell per thread; multi-RHS items read theirs again)
+    const T cfac = (KIND == KIND_H1 && tid < ne) ? static_cast<const T*>(A.scale)[e0 + tid] : T(0);
     __syncthreads();   // barriers and bounds initialised before anyone uses them
     if (FX) {
         int ec = tid < ne ? exp_bound(cfac) : kExpZero;
@@ -1095,9 +1128,9 @@ cudaError_t launch_block(const BlockArgs& A, const CombineArgs& G, int nblk, con
     // cells); multi-RHS: 256 threads over the block's items
     const int threads = mr ? 256 : std::min(256, (A.max_ne + 31) / 32 * 32);
     const int vec = rows_vectorisable<T>(nrhs, x, y, part) ? 1 : 0;
-    kern<<<grid, threads, smem, st>>>(A, x, y, part, nrhs, vec);
+    err = launch_pdl(kern, grid, dim3(threads), smem, st, A, x, y, part, nrhs, vec);
     count_launch(1);
-    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_group_combine<T, OP>(G, part, A.npart, y, nrhs, mr, st);
 }

@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(256) k_dot(const TA* __restrict__ a, const TB*
                                              int vec, FinArgs F) {
     using TD = typename DotType<TA, TB>::type;
     __shared__ double red[256];
+    pdl_launch();
+    pdl_wait();
     const int rows = 256 / R, tid = threadIdx.x, r = tid % R, lr = tid / R;
     double acc = 0.0;
     if constexpr (std::is_same<TA, TB>::value) {
@@ -478,6 +480,8 @@ __global__ void __launch_bounds__(256) k_update_xr(T* __restrict__ x, T* __restr
                                                    const T* __restrict__ q, const double* __restrict__ alpha,
                                                    int64_t n, int R, int vec, FinArgs F) {
     __shared__ double red[256];
+    pdl_launch();
+    pdl_wait();
     const int rows = 256 / R, tid = threadIdx.x, rr = tid % R, lr = tid / R;
     double acc = 0.0;
     if (vec) {
@@ -834,12 +838,16 @@ __global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict_
 
 template <typename T>
 __global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R) {
+    pdl_launch();
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fma((T)beta[R == 1 ? 0 : i % R], p[i], z[i]);
 }
 
 template <typename T>
 __global__ void k_jacobi(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ diag, int64_t nv, int R) {
+    pdl_launch();
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = x[i] / diag[R == 1 ? i : i / R];
 }
@@ -962,8 +970,9 @@ static cudaError_t vdot(bras_ctx* c, const TA* a, const TB* b, int R, int kind, 
     if (batched(c)) k_seg_dot<TA, TB><<<c->nseg, 256, 0, st>>>(a, b, seg_args(c), fin_args(w, kind));
     else {
         const int vec = (R == 1 && std::is_same<TA, TB>::value && aligned16(a) && aligned16(b)) ? 1 : 0;
-        k_dot<TA, TB><<<dot_blocks(c, R, (const void*)k_dot<TA, TB>), 256, 0, st>>>(a, b, c->n, R, vec,
-                                                                                     fin_args(w, kind));
+        const cudaError_t e = launch_pdl(k_dot<TA, TB>, dim3(dot_blocks(c, R, (const void*)k_dot<TA, TB>)), dim3(256), 0,
+                                         st, a, b, c->n, R, vec, fin_args(w, kind));
+        if (e != cudaSuccess) return e;
     }
     count_launch(1);
     return cudaGetLastError();
@@ -982,11 +991,14 @@ static cudaError_t vupdate_xr(bras_ctx* c, T* x, T* r, const T* p, const T* q, i
     if (batched(c))
         k_seg_update_xr<T><<<c->nseg, 256, 0, st>>>(x, r, p, q, w->sc + S_ALPHA * S, seg_args(c),
                                                      fin_args(w, kind, ip, cond, in_graph));
-    else
-        k_update_xr<T><<<dot_blocks(c, R, (const void*)k_update_xr<T>), 256, 0, st>>>(
-            x, r, p, q, w->sc + S_ALPHA * S, c->n, R,
+    else {
+        const cudaError_t e = launch_pdl(
+            k_update_xr<T>, dim3(dot_blocks(c, R, (const void*)k_update_xr<T>)), dim3(256), 0, st, x, r, p, q,
+            (const double*)(w->sc + S_ALPHA * S), c->n, R,
             (R == 1 && aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q)) ? 1 : 0,
             fin_args(w, kind, ip, cond, in_graph));
+        if (e != cudaSuccess) return e;
+    }
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1017,19 +1029,25 @@ static cudaError_t vupdate_p(bras_ctx* c, T* p, const T* z, int R, cudaStream_t 
     PcgWork* w = c->pcg;
     const int S = batched(c) ? c->n_mesh : R;
     if (batched(c)) k_seg_update_p<T><<<c->nseg, 256, 0, st>>>(p, z, w->sc + S_BETA * S, seg_args(c));
-    else k_update_p<T><<<grid_for(c->n * R), 256, 0, st>>>(p, z, w->sc + S_BETA * S, c->n * R, R);
+    else {
+        const cudaError_t e = launch_pdl(k_update_p<T>, dim3(grid_for(c->n * R)), dim3(256), 0, st, p, z,
+                                         (const double*)(w->sc + S_BETA * S), c->n * R, R);
+        if (e != cudaSuccess) return e;
+    }
     count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t jacobi_launch(const bras_ctx* c, int prec, const void* x, void* y, int nrhs, cudaStream_t st) {
     const int64_t nv = c->n * nrhs;
-    if (prec == BRAS_FP64)
-        k_jacobi<double><<<grid_for(nv), 256, 0, st>>>((const double*)x, (double*)y, c->diag64, nv, nrhs);
-    else
-        k_jacobi<float><<<grid_for(nv), 256, 0, st>>>((const float*)x, (float*)y, c->diag32, nv, nrhs);
+    const cudaError_t e =
+        prec == BRAS_FP64
+            ? launch_pdl(k_jacobi<double>, dim3(grid_for(nv)), dim3(256), 0, st, (const double*)x, (double*)y,
+                         (const double*)c->diag64, nv, nrhs)
+            : launch_pdl(k_jacobi<float>, dim3(grid_for(nv)), dim3(256), 0, st, (const float*)x, (float*)y,
+                         (const float*)c->diag32, nv, nrhs);
     count_launch(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>

@@ -173,8 +173,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
     const int u0 = A.blk_u0[b], nu = A.blk_u0[b + 1] - u0;
     const int nint = A.blk_nint[b];
     const uint32_t sa = pkt_size_a(nu, false), sb = pkt_size_b((uint32_t)(ne * NLOC), false);
-    // this thread's cell factor, fetched now so that its latency hides behind the copies
-    const float cfac = lt < ne ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;
+    pdl_launch();
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -188,6 +187,8 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         fx[0] = fx[1] = fx[2] = kExpZero;
     }
     if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+    pdl_wait();   // x, the cell factors, y and the partials belong to the stream's order from here
+    const float cfac = lt < ne ? static_cast<const float*>(A.scale)[e0 + lt] : 0.f;   // this thread's cell factor
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -443,9 +444,9 @@ cudaError_t launch_block_tc(const TcArgs& TA, const CombineArgs& G, int nblk, co
     const int threads = 256;
     dim3 grid(mr ? nblk : nblk * nrhs);
     const int vec = rows_vectorisable<float>(nrhs, x, y, part) ? 1 : 0;
-    kern<<<grid, threads, smem, st>>>(TA, x, y, part, nrhs, vec);
+    err = launch_pdl(kern, grid, dim3(threads), smem, st, TA, x, y, part, nrhs, vec);
     count_launch(1);
-    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_group_combine<float, OP>(G, part, TA.A.npart, y, nrhs, mr, st);
 }
