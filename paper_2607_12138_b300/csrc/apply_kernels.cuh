@@ -297,7 +297,8 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 // the block's products, |v| < 2^(ex + ec + fx_er) with ex, ec the block's largest exponents of
 // the staged x and of the cell factors (H1; 0 for the vector spaces) and fx_er that of the
 // local operator's row abs-sums, placed at 2^fx_top: k = fx_top - ex - ec - fx_er.  The total
-// is converted back once, rounded to nearest; products well below the bound keep an absolute
+// is converted back rounded to nearest (FP32: from its two words, FxAcc::value_f32, within
+// 2^-38 of the bound besides that rounding); products well below the bound keep an absolute
 // resolution of 2^-k = 2^-fx_top of the bound.  With at most 2^h copies of a dof in a block:
 //   FP32 and bf16 applies: q = qh 2^L + ql with |ql| <= 2^(L-1), each part summed in a 32-bit
 //     word; L = min(22, 30 - h), fx_top = min(L + 21, 31 + L - h) (43 bits for h <= 8, about
@@ -410,11 +411,27 @@ struct FxAcc {
         const int* w = reinterpret_cast<const int*>(base);
         return ((long long)w[count + i] << lo_bits) + (long long)w[i];
     }
+    // FP32 total times 2^-k from the two words (lo_bits > 0): the high word is exact in FP32
+    // (|hi| < 2^22 since totals stay below 2^fx_top <= 2^(L + 21)), the low word is rounded
+    // only beyond 2^24 (|lo| <= 2^(L - 1 + h) <= 2^29), and hi 2^L + lo is rounded once by
+    // an FMA: within half a unit in the last place plus 2^5 units of 2^-k (below 2^-38 of the
+    // block's bound), and a function of the two exact integer sums alone, so every apply still
+    // gives the same bits.  Two conversions and an FMA instead of a 64-bit normalisation.
+    __device__ __forceinline__ float value_f32(int i, int k) const {
+        const int* w = reinterpret_cast<const int*>(base);
+        const float hi = __int2float_rn(w[count + i]), lo = __int2float_rn(w[i]);
+        return __fmul_rn(__fmaf_rn(hi, __int_as_float((127 + lo_bits) << 23), lo), __int_as_float((127 - k) << 23));
+    }
 };
 
 // accumulator -> value: one rounding of the exact integer sum, then the exact power-of-two scale
 __device__ __forceinline__ float fx_value(long long q, int k, float) { return ll_to_float_rn(q) * pow2<float>(-k); }
 __device__ __forceinline__ double fx_value(long long q, int k, double) { return __ll2double_rn(q) * pow2<double>(-k); }
+// accumulator i of a block -> value: FP32 from the two words, FP64 from the 64-bit word
+__device__ __forceinline__ float fx_total(const FxAcc& acc, int i, int k, float) { return acc.value_f32(i, k); }
+__device__ __forceinline__ double fx_total(const FxAcc& acc, int i, int k, double) {
+    return fx_value(acc.total(i), k, 0.0);
+}
 
 // Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
 // their partial slot ([nrhs][npart] from p0; MR: slot-major rows, right-hand side r).
@@ -803,7 +820,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
             // totals: interior dofs to y, shared ones to their partial slots
             for (int i = tid; i < nu * rc; i += blockDim.x) {
                 const int u = i / rc, rr = i - u * rc;
-                const T v = bad ? T(NAN) : fx_value(acc.total(u * CW + rr), kx, T(0));
+                const T v = bad ? T(NAN) : fx_total(acc, u * CW + rr, kx, T(0));
                 store_dof<T, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
             }
         } else if constexpr (MR) {

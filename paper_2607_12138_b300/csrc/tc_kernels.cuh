@@ -392,7 +392,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         // totals: interior dofs to y, shared ones to their partial slots
         for (int i = tid; i < nu * rc; i += blockDim.x) {
             const int u = i / rc, rr = i - u * rc;
-            const float v = bad ? __int_as_float(0x7fc00000) : fx_value(acc.total(u * CW + rr), kx, 0.f);
+            const float v = bad ? __int_as_float(0x7fc00000) : acc.value_f32(u * CW + rr, kx);
             store_dof<float, OP, MR>(u, v, nint, ids, dmul, y, part, nrhs, r0 + rr, p0);
         }
         if (MR) __syncthreads();   // the accumulators are read before the next chunk clears them
