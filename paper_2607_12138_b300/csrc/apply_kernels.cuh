@@ -156,14 +156,22 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+// Test the phase of `bar` with the given parity; if it is not complete the thread is suspended
+// until it completes or `hint_ns` nanoseconds pass (the suspend-time hint of try_wait), so a
+// waiting thread does not spin on the issue slots the other warps of the SM need.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 // Programmatic dependent launch.  A kernel launched with programmatic stream serialization
 // (launch_pdl) may start while its predecessor in the stream is still running: pdl_launch()
@@ -175,21 +183,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Bounded wait on phase 0 of `bar`: gives up after ~2^22 polls (each try_wait itself
-// suspends for a hardware-chosen interval), records the failure and tells the caller.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
-        if (mbar_try_wait(bar, 0)) return true;
+// Bounded wait on the phase of `bar` with the given parity (barriers reused across phases):
+// each try_wait suspends the thread for up to 20 us or until the phase completes; the wait
+// gives up after 0.5 s of the global timer (or 2^20 tries), records the failure in `status`
+// and tells the caller.
+__device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t parity, int* status) {
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        if (mbar_try_wait(bar, parity, 20000u)) return true;
+        if (global_ns() - t0 > 500000000ull) break;
+    }
     atomicOr(status, 1);
     return false;
 }
-
-// Bounded wait on the phase of `bar` with the given parity (barriers reused across phases).
-__device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t* bar, uint32_t parity, int* status) {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(status, 1);
-    return false;
+// Bounded wait on phase 0 of `bar`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, int* status) {
+    return mbar_wait_parity_bounded(bar, 0u, status);
 }
 
 // v / d for the multiplicity d: FP64 divides; FP32 multiplies by the hardware reciprocal
