@@ -322,19 +322,26 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 constexpr int kExpZero = -100000;   // exponent bound of zero
 constexpr int kExpBad = 100000;     // of an infinity or a NaN
 
-// E with |v| < 2^E, read off the IEEE exponent field
-__device__ __forceinline__ int exp_bound(float v) {
-    const uint32_t bits = __float_as_uint(v) & 0x7fffffffu;
+// IEEE bits of |v|.  exp_bound_bits is non-decreasing in them (zero, subnormals, normals by
+// exponent, infinities, NaNs), so the bound of a set of values is the bound of their largest
+// magnitude bits: staging loops keep an unsigned maximum and convert once.
+__device__ __forceinline__ uint32_t abs_bits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ __forceinline__ uint64_t abs_bits(double v) {
+    return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+// E with |v| < 2^E, read off the IEEE exponent field of |v|'s bits
+__device__ __forceinline__ int exp_bound_bits(uint32_t bits) {
     if (bits == 0) return kExpZero;
     const int f = (int)(bits >> 23);
     return f == 255 ? kExpBad : (f == 0 ? -126 : f - 126);
 }
-__device__ __forceinline__ int exp_bound(double v) {
-    const uint64_t bits = (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+__device__ __forceinline__ int exp_bound_bits(uint64_t bits) {
     if (bits == 0) return kExpZero;
     const int f = (int)(bits >> 52);
     return f == 2047 ? kExpBad : (f == 0 ? -1022 : f - 1022);
 }
+__device__ __forceinline__ int exp_bound(float v) { return exp_bound_bits(abs_bits(v)); }
+__device__ __forceinline__ int exp_bound(double v) { return exp_bound_bits(abs_bits(v)); }
 
 // Scale exponent k of a block from its exponent bounds; bad = the products are not finite (or
 // beyond what the accumulators can hold), and the block then stores NaN.
@@ -443,12 +450,15 @@ __device__ __forceinline__ double fx_total(const FxAcc& acc, int i, int k, doubl
     return fx_value(acc.total(i), k, 0.0);
 }
 
+// Element offset of dof `id` (>= 0) in a [n][nrhs] array: one 32 x 32 -> 64-bit multiply
+__device__ __forceinline__ size_t dof_offset(int32_t id, int nrhs) { return (size_t)(uint32_t)id * (uint32_t)nrhs; }
+
 // Stage 3's store of one dof's total: interior dofs to y (times 1/d for BRAS), shared ones to
 // their partial slot ([nrhs][npart] from p0; MR: slot-major rows, right-hand side r).
 template <typename T, int OP, bool MR>
 __device__ __forceinline__ void store_dof(int u, T v, int nint, const int32_t* ids, const uint16_t* dmul,
                                           T* __restrict__ y, T* __restrict__ part, int nrhs, int r, int64_t p0) {
-    if (u < nint) y[(size_t)ids[u] * nrhs + r] = (OP == OP_BRAS) ? div_by_count(v, dmul[u]) : v;
+    if (u < nint) (y + r)[dof_offset(ids[u], nrhs)] = (OP == OP_BRAS) ? div_by_count(v, dmul[u]) : v;
     else if (MR) part[(size_t)(p0 + (u - nint)) * nrhs + r] = v;
     else part[p0 + (u - nint)] = v;
 }
@@ -647,6 +657,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         }
 
         int emax = OP == OP_DIAG ? 1 : kExpZero;   // DIAG: the products are matrix entries (x = 1)
+        decltype(abs_bits(T(0))) amax = 0;         // largest |staged value| bits
         if (OP != OP_DIAG && okA) {
             if constexpr (MR) {
                 // one 16-byte row segment per dof, four in flight per thread
@@ -664,7 +675,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
                             for (int j = 0; j < CW; ++j) {
                                 if (OP == OP_BRAS) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
-                                if (FX) emax = max(emax, exp_bound(vget(v[k], j)));
+                                if (FX) amax = max(amax, abs_bits(vget(v[k], j)));
                             }
                             reinterpret_cast<V*>(xs)[uu] = v[k];
                         }
@@ -679,20 +690,21 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
 #pragma unroll
                     for (int k = 0; k < UX; ++k) {
                         const int uu = u + k * blockDim.x;
-                        v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : T(0);
+                        v[k] = uu < nu ? (x + r0)[dof_offset(ids[uu], nrhs)] : T(0);
                     }
 #pragma unroll
                     for (int k = 0; k < UX; ++k) {
                         const int uu = u + k * blockDim.x;
                         if (uu < nu) {
                             const T w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
-                            if (FX) emax = max(emax, exp_bound(w));
+                            if (FX) amax = max(amax, abs_bits(w));
                             xs[uu] = w;
                         }
                     }
                 }
             }
         }
+        if (FX && OP != OP_DIAG) emax = exp_bound_bits(amax);
         if (FX && emax > kExpZero) atomicMax(fxe, emax);
         if (ch == 0) {
             if (!cta_wait(&bars[1], 0, A.status, okA)) {   // block-uniform decision

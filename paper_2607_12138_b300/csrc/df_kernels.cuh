@@ -81,7 +81,7 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
     const uint16_t* loc = reinterpret_cast<const uint16_t*>(tab + sa);
 
     const bool okA = cta_wait(&bars[0], 0, A.status, true);
-    int emax = kExpZero;
+    uint64_t amax = 0;   // largest |staged value| bits
     if (okA) {
         for (int u = tid; u < nu; u += 8 * blockDim.x) {
             double v[8];
@@ -96,11 +96,12 @@ k_block_df(const BlockArgs A, const double* __restrict__ x, double* __restrict__
                 if (uu < nu) {
                     const float hi = (float)v[k];
                     xs[uu] = make_float2(hi, (float)(v[k] - (double)hi));
-                    emax = max(emax, exp_bound(v[k]));
+                    amax = max(amax, abs_bits(v[k]));
                 }
             }
         }
     }
+    const int emax = exp_bound_bits(amax);
     if (emax > kExpZero) atomicMax(&fx[0], emax);
     if (!cta_wait(&bars[1], 0, A.status, okA)) {
         if (tid == 0) {

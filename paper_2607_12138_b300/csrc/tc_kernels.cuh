@@ -214,7 +214,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
         if (tid == 0) fx[(ch + 1) & 1] = kExpZero;   // the next chunk's bound (its readers are done)
         const FxAcc acc{ys, (nu * CW + 1) & ~1, A.fx_lo};
         if constexpr (MR) acc.clear(acc.count);
-        int emax = kExpZero;
+        uint32_t amax = 0;   // largest |staged value| bits
         if constexpr (MR) {
             using V = Chunk<float>::V;
             for (int u = tid; u < nu; u += 4 * blockDim.x) {
@@ -231,7 +231,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                         for (int j = 0; j < CW; ++j) {
                             if (OP == OP_BRAS) vget(v[k], j) = div_by_count(vget(v[k], j), dmul[uu]);
-                            emax = max(emax, exp_bound(vget(v[k], j)));
+                            amax = max(amax, abs_bits(vget(v[k], j)));
                         }
                         reinterpret_cast<V*>(xs)[uu] = v[k];
                     }
@@ -245,19 +245,20 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int uu = u + k * blockDim.x;
-                    v[k] = uu < nu ? x[(size_t)ids[uu] * nrhs + r0] : 0.f;
+                    v[k] = uu < nu ? (x + r0)[dof_offset(ids[uu], nrhs)] : 0.f;
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int uu = u + k * blockDim.x;
                     if (uu < nu) {
                         const float w = (OP == OP_BRAS) ? div_by_count(v[k], dmul[uu]) : v[k];
-                        emax = max(emax, exp_bound(w));
+                        amax = max(amax, abs_bits(w));
                         xs[uu] = w;
                     }
                 }
             }
         }
+        const int emax = exp_bound_bits(amax);
         if (emax > kExpZero) atomicMax(fxe, emax);
         if (ch == 0) {
             ok = cta_wait(&bars[1], 0, A.status, ok);
