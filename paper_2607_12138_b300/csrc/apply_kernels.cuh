@@ -410,6 +410,21 @@ struct FxAcc {
         atomicAdd(w + i, magic_int(__fadd_rn(r, kRoundMagic)));
         atomicAdd(w + count + i, magic_int(th));
     }
+    // The same with the product given as t = s 2^-L (the caller folds 2^-L into its scale
+    // factor, one multiply less per product): qh = rint(t), t - qh is exact (the fraction of t,
+    // or Sterbenz for |t| < 1), and ql = rint((t - qh) 2^L) by one FMA with the round-to-integer
+    // constant -- the same two integers as add_scaled(i, t 2^L).  Only where the folded factor
+    // falls below FP32's normal range (cell factors 2^40 apart in one block) does it keep fewer
+    // bits: those products stay below 2^-29 of the block's bound, and the result is still a
+    // fixed function of the inputs.
+    __device__ __forceinline__ void add_prescaled(int i, float t) const {
+        const float th = __fadd_rn(t, kRoundMagic);
+        const float fr = __fsub_rn(t, __fsub_rn(th, kRoundMagic));
+        const float tl = __fmaf_rn(fr, __int_as_float((127 + lo_bits) << 23), kRoundMagic);
+        int* w = reinterpret_cast<int*>(base);
+        atomicAdd(w + i, magic_int(tl));
+        atomicAdd(w + count + i, magic_int(th));
+    }
     // FP64 product (one 64-bit word, lo_bits = 0)
     __device__ __forceinline__ void add_scaled(int i, double s) const {
         atomicAdd(reinterpret_cast<unsigned long long*>(base) + i, (unsigned long long)fx_round(s));
@@ -440,6 +455,9 @@ struct FxAcc {
         return __fmul_rn(__fmaf_rn(hi, __int_as_float((127 + lo_bits) << 23), lo), __int_as_float((127 - k) << 23));
     }
 };
+
+// 2^-L for the low-word split at bit L (lo_bits)
+__device__ __forceinline__ float acc_lo_scale(int lo_bits) { return __int_as_float((127 - lo_bits) << 23); }
 
 // accumulator -> value: one rounding of the exact integer sum, then the exact power-of-two scale
 __device__ __forceinline__ float fx_value(long long q, int k, float) { return ll_to_float_rn(q) * pow2<float>(-k); }
@@ -722,6 +740,7 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
         bool bad = false;
         const int kx = FX ? fx_scale<T>(*fxe, fx[2], A.fx_er, A.fx_top, bad) : 0;
         const T sc = pow2<T>(kx);
+        const T scl = sc * T(FX && sizeof(T) == 4 ? acc_lo_scale(A.fx_lo) : 1.f);   // FP32: sc 2^-L
 
         // Work items: (cell e, rhs rr) -> item e * CW + rr.  One item per thread without MR.
         const int nitem = ne * CW;
@@ -785,7 +804,8 @@ k_block(const BlockArgs A, const T* __restrict__ x, T* __restrict__ y, T* __rest
                 // dof-sorted slot
                 auto out = [&](int a, T v) {
                     if constexpr (FX) {
-                        acc.add_scaled(L[a * ne] * CW + rr, v * sc);
+                        if constexpr (sizeof(T) == 4) acc.add_prescaled(L[a * ne] * CW + rr, v * scl);
+                        else acc.add_scaled(L[a * ne] * CW + rr, v * sc);
                     } else {
                         const bool s = SIGNED && OP != OP_DIAG &&
                                        (a < 64 ? ((neg >> (a & 63)) & 1) != 0 : (L[a * ne] & 0x8000) != 0);

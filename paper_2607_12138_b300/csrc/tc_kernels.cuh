@@ -349,7 +349,9 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 
             // stage 2c: read this item's row of Z, scale, and add each product to its dof's
             // fixed-point accumulator
-            const float cs = (MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac) * sc;
+            // the cell factor times the block scale and 2^-L (add_prescaled)
+            const float cs = (MR ? (valid ? static_cast<const float*>(A.scale)[e0 + e] : 0.f) : cfac) * sc *
+                             acc_lo_scale(acc.lo_bits);
             auto stage2c = [&](auto hc) {
                 constexpr int H = decltype(hc)::value;
                 constexpr int G = N / 16;
@@ -370,7 +372,7 @@ k_block_tc(const TcArgs TA, const float* __restrict__ x, float* __restrict__ y, 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int a = 16 * g + j;
-                            if (a < NLOC) acc.add_scaled(loc[a * ne + e] * CW + rr, __uint_as_float(v[g][j]) * cs);
+                            if (a < NLOC) acc.add_prescaled(loc[a * ne + e] * CW + rr, __uint_as_float(v[g][j]) * cs);
                         }
                     }
                 }
