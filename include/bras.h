@@ -81,7 +81,8 @@ enum {
     BRAS_ERR_OOM = -7,            /* device or host allocation failed                    */
     BRAS_ERR_BREAKDOWN = -8,      /* CG breakdown: p^T M p <= 0 or not finite            */
     BRAS_ERR_PRECISION = -9,      /* the context holds no tables for this precision      */
-    BRAS_ERR_TOO_LARGE = -10      /* a size exceeds a documented library limit           */
+    BRAS_ERR_TOO_LARGE = -10,     /* a size exceeds a documented library limit           */
+    BRAS_ERR_DEVICE = -11         /* a kernel's bounded wait ran out (detail = status bits) */
 };
 
 /* Options of bras_setup.  Zero-initialise, then set what you need. */
@@ -342,6 +343,23 @@ int bras_block_tuning(const bras_ctx* ctx, int* block_elems, int* count, int* si
  * per-element factor (H1) or packed local inverse (H(curl)/H(div)), x read and y written,
  * and one multiplicity byte per dof (BRAS apply only).  For roofline reporting. */
 int64_t bras_algorithmic_bytes(const bras_ctx* ctx, int precision, int nrhs, int bras);
+
+/* Device status of a context.  Every wait of the library's kernels on an mbarrier (a table
+ * copy, a tensor-core GEMM) is bounded: it gives up after 0.5 s of the GPU's global timer,
+ * lets the copies it issued land, releases its tensor memory, records a bit in the context's
+ * status word (bit 0: a copy wait, bit 1: a GEMM or operand-tile wait) and leaves its outputs
+ * unwritten.  The solvers (bras_pcg_solve, bras_fixed_point_solve, bras_chebyshev_solve,
+ * bras_lambda_max, bras_cg_lanczos) read the word when they finish and return
+ * BRAS_ERR_DEVICE (detail = the bits, the word cleared) if any bit is set; the stream-ordered
+ * applies leave it to this call: it synchronises `stream`, returns BRAS_OK if the word is 0,
+ * else BRAS_ERR_DEVICE with the bits as detail, and clears the word if `clear` != 0. */
+int bras_device_status(bras_ctx* ctx, void* stream, int clear);
+
+/* Self-test of the bounded wait: one CTA waits on an mbarrier that nothing completes, on the
+ * legacy default stream, until the bound runs out.  *bits = the status bits it recorded
+ * (1 expected), *elapsed_ms = the wait's duration by CUDA events (about 500 expected).  The
+ * CUDA context stays usable.  Returns BRAS_OK, or BRAS_ERR_CUDA / BRAS_ERR_OOM. */
+int bras_wait_selftest(int* bits, double* elapsed_ms);
 
 void bras_destroy(bras_ctx* ctx);
 const char* bras_status_string(int code);

@@ -35,7 +35,7 @@ BASIS = {"h1b": 1, "n2curl": 1, "bdm": 1, "h1g": 2}
 
 OK, NOT_CONVERGED = 0, 1
 ERR = {-1: "INVALID", -2: "L2G_RANGE", -3: "NO_COPY", -4: "DEGENERATE", -5: "NOT_SPD", -6: "CUDA",
-       -7: "OOM", -8: "BREAKDOWN", -9: "PRECISION", -10: "TOO_LARGE"}
+       -7: "OOM", -8: "BREAKDOWN", -9: "PRECISION", -10: "TOO_LARGE", -11: "DEVICE"}
 
 
 class BrasError(RuntimeError):
@@ -105,6 +105,10 @@ _lib.bras_kernel_launches.argtypes = []
 _lib.bras_kernel_launches.restype = _i64
 _lib.bras_graph_launches.argtypes = []
 _lib.bras_graph_launches.restype = _i64
+_lib.bras_device_status.argtypes = [_vp, _vp, _int]
+_lib.bras_device_status.restype = _int
+_lib.bras_wait_selftest.argtypes = [ctypes.POINTER(_int), ctypes.POINTER(_dbl)]
+_lib.bras_wait_selftest.restype = _int
 
 
 def kernel_launches() -> int:
@@ -115,6 +119,19 @@ def kernel_launches() -> int:
 def graph_launches() -> int:
     """CUDA graph launches the library has made since it was loaded (one per graph-run solve)."""
     return int(_lib.bras_graph_launches())
+
+
+def bras_wait_selftest() -> tuple[int, float]:
+    """One bounded wait on a barrier nothing completes: (status bits recorded, duration ms)."""
+    bits, ms = _int(0), _dbl(0.0)
+    _check(_lib.bras_wait_selftest(ctypes.byref(bits), ctypes.byref(ms)), "bras_wait_selftest")
+    return int(bits.value), float(ms.value)
+
+
+def bras_device_status(ctx, stream=None, clear: bool = True) -> tuple[int, int]:
+    """(return code, status bits) of the context's device status word; BRAS_ERR_DEVICE if set."""
+    rc = int(_lib.bras_device_status(ctx, _stream(stream), 1 if clear else 0))
+    return rc, int(_lib.bras_last_error_detail()) if rc == -11 else 0
 
 
 def header_functions() -> list[str]:
@@ -331,6 +348,10 @@ class Context:
         self.n_dof, self.n_cell, self.n_loc, self.n_blocks = bras_info(self.ctx)
         self.n_mesh = len(meshes)
         return self
+
+    def device_status(self, stream=None, clear: bool = True) -> tuple[int, int]:
+        """(return code, status bits) of this context's bounded kernel waits."""
+        return bras_device_status(self.ctx, stream, clear)
 
     @property
     def block_tuning(self):

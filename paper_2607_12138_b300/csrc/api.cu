@@ -713,6 +713,22 @@ bool has_precision(const bras_ctx* c, int prec) {
 
 using namespace bras;
 
+// The context's device status word (bounded kernel waits that ran out): read after `st`
+// drains; set bits turn a result `rc` into BRAS_ERR_DEVICE (detail = bits) and are cleared
+// if `clear`.
+static int device_status(bras_ctx* c, cudaStream_t st, int rc, bool clear) {
+    int bits = 0;
+    if (cudaMemcpyAsync(&bits, c->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return BRAS_ERR_CUDA;
+    if (bits == 0) return rc;
+    if (clear && (cudaMemsetAsync(c->status, 0, sizeof(int), st) != cudaSuccess ||
+                  cudaStreamSynchronize(st) != cudaSuccess))
+        return BRAS_ERR_CUDA;
+    set_detail(bits);
+    return BRAS_ERR_DEVICE;
+}
+
 extern "C" {
 
 int bras_n_local(int dim, int space, int order, int basis) { return n_local(dim, space, order, basis); }
@@ -890,8 +906,10 @@ int bras_pcg_solve(const bras_ctx* ctx, int pc, int mode, int inner_precision, c
         return BRAS_ERR_INVALID;
     if (mode == BRAS_SOLVE_MIXED && !has_precision(ctx, inner_precision)) return BRAS_ERR_PRECISION;
     if (mode == BRAS_SOLVE_FP64 && pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
-    return pcg_solve_impl(const_cast<bras_ctx*>(ctx), pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters,
-                          relres, static_cast<cudaStream_t>(stream));
+    bras_ctx* c = const_cast<bras_ctx*>(ctx);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return device_status(c, st, pcg_solve_impl(c, pc, mode, inner_precision, b, x, nrhs, rtol, maxit, iters, relres, st),
+                         true);
 }
 
 static int slots_of(const bras_ctx* c, int nrhs) { return (c->n_mesh > 1 && c->nseg > 0) ? c->n_mesh : nrhs; }
@@ -901,7 +919,9 @@ int bras_lambda_max(const bras_ctx* ctx, int pc, const double* v0, int nrhs, int
     set_detail(-1);
     if (!ctx || !v0 || !lambda || nrhs < 1 || iters < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
     if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
-    return lambda_max_impl(const_cast<bras_ctx*>(ctx), pc, v0, nrhs, iters, lambda, static_cast<cudaStream_t>(stream));
+    bras_ctx* c = const_cast<bras_ctx*>(ctx);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return device_status(c, st, lambda_max_impl(c, pc, v0, nrhs, iters, lambda, st), true);
 }
 
 int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, double* lambda_min, double* lambda_max,
@@ -909,8 +929,9 @@ int bras_cg_lanczos(const bras_ctx* ctx, int pc, const double* b, int steps, dou
     set_detail(-1);
     if (!ctx || !b || !lambda_min || !lambda_max || steps < 1 || pc < 0 || pc > 2) return BRAS_ERR_INVALID;
     if (pc == BRAS_PC_BRAS && !has_fp64_bras(ctx)) return BRAS_ERR_PRECISION;
-    return cg_lanczos_impl(const_cast<bras_ctx*>(ctx), pc, b, steps, lambda_min, lambda_max, steps_done,
-                           static_cast<cudaStream_t>(stream));
+    bras_ctx* c = const_cast<bras_ctx*>(ctx);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return device_status(c, st, cg_lanczos_impl(c, pc, b, steps, lambda_min, lambda_max, steps_done, st), true);
 }
 
 int bras_schur_apply(const bras_ctx* ctx, int precision, const void* x, void* y, void* stream) {
@@ -931,8 +952,11 @@ int bras_fixed_point_solve(const bras_ctx* ctx, int pc, const double* omega, con
     const int S = slots_of(ctx, nrhs);
     for (int s = 0; s < S; ++s)
         if (!(omega[s] > 0) || !std::isfinite(omega[s])) { set_detail(s); return BRAS_ERR_INVALID; }
-    return stationary_solve_impl(const_cast<bras_ctx*>(ctx), 1, pc, omega, nullptr, nullptr, b, x, nrhs, rtol, maxit,
-                                 iters, relres, static_cast<cudaStream_t>(stream));
+    bras_ctx* c = const_cast<bras_ctx*>(ctx);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return device_status(
+        c, st, stationary_solve_impl(c, 1, pc, omega, nullptr, nullptr, b, x, nrhs, rtol, maxit, iters, relres, st),
+        true);
 }
 
 int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const double* lmax, const double* b,
@@ -944,8 +968,11 @@ int bras_chebyshev_solve(const bras_ctx* ctx, int pc, const double* lmin, const 
     const int S = slots_of(ctx, nrhs);
     for (int s = 0; s < S; ++s)
         if (!(lmin[s] > 0) || !(lmax[s] > lmin[s]) || !std::isfinite(lmax[s])) { set_detail(s); return BRAS_ERR_INVALID; }
-    return stationary_solve_impl(const_cast<bras_ctx*>(ctx), 2, pc, nullptr, lmin, lmax, b, x, nrhs, rtol, maxit,
-                                 iters, relres, static_cast<cudaStream_t>(stream));
+    bras_ctx* c = const_cast<bras_ctx*>(ctx);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return device_status(
+        c, st, stationary_solve_impl(c, 2, pc, nullptr, lmin, lmax, b, x, nrhs, rtol, maxit, iters, relres, st),
+        true);
 }
 
 int bras_grad_rho(const bras_ctx* ctx, const double* x, const double* lam, double* rho_bar, void* stream) {
@@ -1035,11 +1062,18 @@ const char* bras_status_string(int code) {
         case BRAS_ERR_BREAKDOWN: return "CG breakdown";
         case BRAS_ERR_PRECISION: return "precision not built in this context";
         case BRAS_ERR_TOO_LARGE: return "size above a library limit";
+        case BRAS_ERR_DEVICE: return "a kernel's bounded wait ran out";
         default: return "unknown status";
     }
 }
 
 int64_t bras_last_error_detail(void) { return g_detail; }
+
+int bras_device_status(bras_ctx* ctx, void* stream, int clear) {
+    set_detail(-1);
+    if (!ctx) return BRAS_ERR_INVALID;
+    return device_status(ctx, static_cast<cudaStream_t>(stream), BRAS_OK, clear != 0);
+}
 
 int64_t bras_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 int64_t bras_graph_launches(void) { return g_graph_launches.load(std::memory_order_relaxed); }

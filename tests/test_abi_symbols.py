@@ -42,6 +42,7 @@ def test_host_only_entry_points():
     assert nl(2, 1, 5) == -1 and nl(3, 2, 5) == -1 and nl(3, 0, 5) == -1
     lib.bras_status_string.restype = ctypes.c_char_p
     assert lib.bras_status_string(-5) == b"local mass matrix not SPD"
+    assert lib.bras_status_string(-11) == b"a kernel's bounded wait ran out"
     out = ctypes.c_void_p(1)
     # invalid arguments are rejected before any device work
     assert lib.bras_setup(ctypes.byref(out), 4, 0, 1, 0, None, 0, None, 0, None, None, None, None, None) == -1
