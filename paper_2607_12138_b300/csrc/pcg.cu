@@ -836,10 +836,46 @@ __global__ void k_seg_accum_f32(double* __restrict__ x, const float* __restrict_
     for (int64_t i = beg + threadIdx.x; i < end; i += 256) x[i] = fma((double)d[i], sc, x[i]);
 }
 
+// p = beta p + z.  One right-hand side with 16-byte aligned vectors (vec): 16-byte accesses,
+// four in flight per array and thread, the same arithmetic per element.
 template <typename T>
-__global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R) {
+__global__ void k_update_p(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ beta, int64_t nv, int R,
+                           int vec) {
     pdl_launch();
     pdl_wait();
+    if (vec) {
+        using V = typename Vec4<T>::type;
+        constexpr int W = Vec4<T>::W;
+        V* pv = reinterpret_cast<V*>(p);
+        const V* zv = reinterpret_cast<const V*>(z);
+        const T b = (T)beta[0];
+        const int64_t nvec = nv / W, stride = (int64_t)gridDim.x * blockDim.x;
+        const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t i = gid;
+        for (; i + 3 * stride < nvec; i += 4 * stride) {
+            V a[4], c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = pv[i + u * stride];
+                c[u] = zv[i + u * stride];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) vget(a[u], j) = fma(b, vget(a[u], j), vget(c[u], j));
+                pv[i + u * stride] = a[u];
+            }
+        }
+        for (; i < nvec; i += stride) {
+            V a = pv[i];
+            V c = zv[i];
+#pragma unroll
+            for (int j = 0; j < W; ++j) vget(a, j) = fma(b, vget(a, j), vget(c, j));
+            pv[i] = a;
+        }
+        if (gid < nv - nvec * W) p[nvec * W + gid] = fma(b, p[nvec * W + gid], z[nvec * W + gid]);
+        return;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fma((T)beta[R == 1 ? 0 : i % R], p[i], z[i]);
 }
@@ -1030,8 +1066,9 @@ static cudaError_t vupdate_p(bras_ctx* c, T* p, const T* z, int R, cudaStream_t 
     const int S = batched(c) ? c->n_mesh : R;
     if (batched(c)) k_seg_update_p<T><<<c->nseg, 256, 0, st>>>(p, z, w->sc + S_BETA * S, seg_args(c));
     else {
+        const int vec = (R == 1 && aligned16(p) && aligned16(z)) ? 1 : 0;
         const cudaError_t e = launch_pdl(k_update_p<T>, dim3(grid_for(c->n * R)), dim3(256), 0, st, p, z,
-                                         (const double*)(w->sc + S_BETA * S), c->n * R, R);
+                                         (const double*)(w->sc + S_BETA * S), c->n * R, R, vec);
         if (e != cudaSuccess) return e;
     }
     count_launch(1);
